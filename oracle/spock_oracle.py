@@ -503,11 +503,11 @@ class Oracle:
         self.L = sp.csr_matrix((vals, (rows, cols)), shape=(lay.n_eta, lay.n_z))
         self.LT = self.L.T.tocsr()
 
-    def _norm_L(self):
+    def _norm_L(self, dense_max=2500):
         """||L|| (Sec. 4.1 requires 0 < alpha ||L|| < 1; the paper does not say
         how alpha is chosen: alpha = 0.99/||L||). Dense SVD for small L, else the
         largest eigenvalue of L'L by Lanczos at machine tolerance."""
-        if self.lay.n_z <= 2500:
+        if self.lay.n_z <= dense_max:
             return float(np.linalg.norm(self.L.toarray(), 2))
         LtL = (self.LT @ self.L).tocsr()
         ev = spla.eigsh(LtL, k=1, which="LA", tol=1e-15, maxiter=100000,

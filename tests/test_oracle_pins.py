@@ -1,0 +1,430 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix,
+independently of the oracle's own code paths (closed forms, textbook
+recursions, dense linear algebra, LP duals, brute force)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.optimize as so
+
+from oracle import spock_oracle as so_
+from oracle.spock_oracle import Oracle
+from paper_2505_12078_b300 import synth
+from tests.problems import constrained, unconstrained
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --- problem layout -----------------------------------------------------------
+def test_sizes_match_hand_count():
+    """Vector lengths from the definitions of Sec. 4.3-4.4 (counted by hand)."""
+    g = json.load(open(os.path.join(GOLDEN, "sizes.json")))
+    for key, ref in g.items():
+        if key.startswith("_"):
+            continue
+        if key == "small_raocp":
+            p = synth.small_raocp()
+        elif key == "large_raocp":
+            p = synth.large_raocp()
+        else:
+            p = synth.tree_sweep(int(key.split("_")[-1]))
+        tr = so_.Tree(p.anc, p.prob)
+        assert (tr.n, tr.n_nl, tr.n_l) == (ref["n"], ref["n_nonleaf"], ref["n_leaf"])
+        if key in ("small_raocp",):
+            o = Oracle(p)
+            assert (o.lay.n_z, o.lay.n_eta) == (ref["n_z"], ref["n_eta"])
+        else:
+            # layout only (no factorisation needed)
+            o = Oracle.__new__(Oracle)
+            o.P, o.tree, o.n, o.nx, o.nu = p, tr, tr.n, p.nx, p.nu
+            o.has_xbox, o.has_ubox, o.has_uball = True, True, p.u_ball is not None
+            o.n_c = p.nx + p.nu + (p.nu if p.u_ball is not None else 0)
+            o.n_cN = p.nx
+            o._layout()
+            assert (o.lay.n_z, o.lay.n_eta) == (ref["n_z"], ref["n_eta"])
+
+
+def test_tree_probabilities_sum_to_one_per_stage():
+    """Sec. 3.2: sum over nodes(t) of pi^i = 1."""
+    tr = so_.Tree(*synth.tree_from_branching([3, 2, 1, 4], np.random.default_rng(0)))
+    for t in range(tr.N + 1):
+        assert abs(tr.pi[tr.nodes_at[t]].sum() - 1.0) < 1e-13
+
+
+# --- risk measures ------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(6))
+def test_avar_closed_form_vs_ambiguity_lp_and_conic_dual(seed):
+    """AV@R by sorting = max over the ambiguity set (LP) = min of the conic dual
+    with the printed b, E, K (Sec. 3.3)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 6))
+    Z = rng.standard_normal(n)
+    p = rng.dirichlet(np.ones(n))
+    a = float(rng.uniform(0.05, 1.0))
+    val = so_.avar(Z, p, a)
+    # primal: max mu'Z, sum mu = 1, 0 <= mu <= p/a
+    lp = so.linprog(-Z, A_eq=np.ones((1, n)), b_eq=[1.0],
+                    bounds=[(0.0, p[j] / a) for j in range(n)], method="highs")
+    assert lp.status == 0
+    assert abs(-lp.fun - val) < 1e-10
+    # conic dual: min y'b s.t. E'y = Z, y in K* = R^{2n}_+ x R
+    b, E = so_.conic_risk_data(p, a)
+    bounds = [(0, None)] * (2 * n) + [(None, None)]
+    dual = so.linprog(b, A_eq=E.T, b_eq=Z, bounds=bounds, method="highs")
+    assert dual.status == 0
+    assert abs(dual.fun - val) < 1e-9
+
+
+def test_avar_extremes():
+    """AV@R_1 = expectation, AV@R_0 = max (Sec. 3.3)."""
+    rng = np.random.default_rng(1)
+    Z = rng.standard_normal(5)
+    p = rng.dirichlet(np.ones(5))
+    assert abs(so_.avar(Z, p, 1.0) - p @ Z) < 1e-14
+    assert so_.avar(Z, p, 0.0) == Z.max()
+    assert abs(so_.avar(Z, p, 1e-9) - Z.max()) < 1e-12
+
+
+# --- projections ----------------------------------------------------------------
+def test_proj_soc_moreau_characterisation():
+    """Moreau: v = P(v) - P(-v) with both in SOC (self-dual) and orthogonal
+    characterises the projection onto SOC uniquely."""
+    rng = np.random.default_rng(2)
+    V = rng.standard_normal((400, 7)) * 3
+    V[:50, -1] = np.abs(V[:50, -1]) + 10           # inside
+    V[50:100, -1] = -np.abs(V[50:100, -1]) - 10    # polar
+    P = so_.proj_soc(V)
+    Qn = so_.proj_soc(-V)
+    assert np.allclose(P - Qn, V, atol=1e-12)
+    assert np.all(np.linalg.norm(P[:, :-1], axis=1) <= P[:, -1] + 1e-12)
+    assert np.all(np.linalg.norm(Qn[:, :-1], axis=1) <= Qn[:, -1] + 1e-12)
+    assert np.allclose(np.sum(P * Qn, axis=1), 0.0, atol=1e-10)
+
+
+def test_proj_S2_vs_nullspace_basis():
+    """proj_S2 equals N N' v with N an orthonormal basis of ker[E', -I, -I]
+    (Sec. 4.3), computed by SVD."""
+    p = constrained([3, 2, 1], 2, 1, seed=3, avar=0.37)
+    o = Oracle(p)
+    rng = np.random.default_rng(4)
+    z = rng.standard_normal(o.lay.n_z)
+    s0, x, u, y, tau, s = o.split_z(z)
+    y2, tau2, s2 = o.proj_S2(y, tau, s)
+    tr = o.tree
+    for i in range(tr.n_nl):
+        ch = tr.children[i]
+        m = len(ch)
+        a = o.avar_level[i]
+        Et = np.hstack([a * np.eye(m), -np.eye(m), np.ones((m, 1))])
+        G = np.hstack([Et, -np.eye(m), -np.eye(m)])
+        Nb = sla.null_space(G)
+        v = np.concatenate([y[o.yoff[i]:o.yoff[i + 1]], tau[ch - 1], s[ch - 1]])
+        ref = Nb @ (Nb.T @ v)
+        got = np.concatenate([y2[o.yoff[i]:o.yoff[i + 1]], tau2[ch - 1], s2[ch - 1]])
+        assert np.allclose(got, ref, atol=1e-12)
+
+
+def _dense_kkt_projection(o, xbar, ubar):
+    """min 1/2||x - xbar||^2 + 1/2||u - ubar||^2 s.t. x^0 = x0, x^c = A x^a + B u^a + c,
+    solved as one dense KKT system."""
+    tr = o.tree
+    nx, nu, n = o.nx, o.nu, tr.n
+    nX = n * nx + tr.n_nl * nu
+    rows = []
+    rhs = []
+    C0 = np.zeros((nx, nX)); C0[:, :nx] = np.eye(nx)
+    rows.append(C0); rhs.append(o.x0s)
+    for c in range(1, n):
+        a = tr.anc[c]
+        Cc = np.zeros((nx, nX))
+        Cc[:, c * nx:(c + 1) * nx] = np.eye(nx)
+        Cc[:, a * nx:(a + 1) * nx] = -o.At[c - 1]
+        Cc[:, n * nx + a * nu:n * nx + (a + 1) * nu] = -o.Bt[c - 1]
+        rows.append(Cc); rhs.append(o.ct[c - 1])
+    C = np.vstack(rows)
+    d = np.concatenate(rhs)
+    target = np.concatenate([xbar.ravel(), ubar.ravel()])
+    K = np.block([[np.eye(nX), C.T], [C, np.zeros((C.shape[0], C.shape[0]))]])
+    sol = np.linalg.solve(K, np.concatenate([target, d]))
+    X = sol[:nX]
+    return X[:n * nx].reshape(n, nx), X[n * nx:].reshape(tr.n_nl, nu)
+
+
+@pytest.mark.parametrize("branching,nx,nu,seed", [([2, 1, 2], 3, 2, 0), ([3, 2], 2, 2, 1),
+                                                  ([1, 1, 1, 1], 4, 1, 2), ([2, 3, 1], 3, 3, 3)])
+def test_proj_S1_equals_dense_kkt(branching, nx, nu, seed):
+    """Alg. 1-2 compute the Euclidean projection onto S1 (with affine c)."""
+    p = unconstrained(branching, nx, nu, seed, c_scale=0.5)
+    o = Oracle(p)
+    rng = np.random.default_rng(seed + 10)
+    xbar = rng.standard_normal((o.tree.n, nx)) * 2
+    ubar = rng.standard_normal((o.tree.n_nl, nu)) * 2
+    x, u = o.proj_S1(xbar, ubar)
+    xr, ur = _dense_kkt_projection(o, xbar, ubar)
+    assert np.allclose(x, xr, atol=1e-11, rtol=1e-11)
+    assert np.allclose(u, ur, atol=1e-11, rtol=1e-11)
+    x2, u2 = o.proj_S1(x, u)               # idempotent
+    assert np.allclose(x2, x, atol=1e-11) and np.allclose(u2, u, atol=1e-11)
+
+
+# --- the linear operator L --------------------------------------------------------
+def test_L_cost_blocks_encode_epigraph():
+    """Prop. 1 (q = 0): with tau^c equal to the edge cost of the UNSCALED state
+    and input, the cost block of L z minus a lies on the SOC boundary; larger
+    tau is strictly inside, smaller strictly outside. Same for the leaf's s^j
+    and the terminal cost."""
+    p = unconstrained([2, 2, 1], 3, 2, seed=7)
+    o = Oracle(p)
+    tr = o.tree
+    rng = np.random.default_rng(8)
+    z = rng.standard_normal(o.lay.n_z)
+    s0, x, u, y, tau, s = o.split_z(z)
+    xu = x / o.Snode
+    uu = u / o.Su
+    for c in range(1, tr.n):
+        a = tr.anc[c]
+        tau[c - 1] = np.sum(p.Q[c - 1] * xu[a] ** 2) + np.sum(p.R[c - 1] * uu[a] ** 2)
+    for jj in range(tr.n_l):
+        j = tr.n_nl + jj
+        s[j - 1] = np.sum(p.QN[jj] * xu[j] ** 2)
+    z = o.join_z(s0, x, u, y, tau, s)
+    w = o.nx + o.nu + 2
+    for delta, sign in ((0.0, 0), (1e-3, 1), (-1e-3, -1)):
+        zz = z.copy()
+        zz[o.lay.o_tau:o.lay.o_s] += delta
+        zz[o.lay.o_s + tr.n_nl - 1:] += delta
+        eta = o.apply_L(zz)
+        Qb = eta[o.lay.e_q:o.lay.e_cN].reshape(tr.n - 1, w)
+        aa = np.zeros(w); aa[-2], aa[-1] = 0.5, -0.5
+        d = Qb - aa
+        gap = d[:, -1] - np.linalg.norm(d[:, :-1], axis=1)
+        QN = eta[o.lay.e_qN:].reshape(tr.n_l, o.nx + 2)
+        aN = np.zeros(o.nx + 2); aN[-2], aN[-1] = 0.5, -0.5
+        dN = QN - aN
+        gapN = dN[:, -1] - np.linalg.norm(dN[:, :-1], axis=1)
+        if sign == 0:
+            assert np.allclose(gap, 0, atol=1e-12) and np.allclose(gapN, 0, atol=1e-12)
+        else:
+            assert np.all(np.sign(gap) == sign) and np.all(np.sign(gapN) == sign)
+
+
+def test_L_constraint_rows_encode_unscaled_sets():
+    """The scaled constraint rows of L z lie in the scaled sets exactly when the
+    unscaled x, u satisfy the original box and ball constraints (Sec. 5.4)."""
+    p = constrained([2, 2, 1], 4, 3, seed=9, uball=1.5)
+    o = Oracle(p)
+    tr = o.tree
+    rng = np.random.default_rng(10)
+    for trial in range(20):
+        xu = rng.uniform(-6, 6, (tr.n, o.nx))
+        uu = rng.uniform(-2.5, 2.5, (tr.n_nl, o.nu))
+        z = o.join_z(0.0, xu * o.Snode, uu * o.Su, np.zeros(o.lay.n_y),
+                     np.zeros(tr.n - 1), np.zeros(tr.n - 1))
+        eta = o.apply_L(z)
+        pe = o.proj_S3(eta)
+        C = (eta - pe)[o.lay.e_c:o.lay.e_q].reshape(tr.n_nl, o.n_c)
+        CN = (eta - pe)[o.lay.e_cN:o.lay.e_qN].reshape(tr.n_l, o.n_cN)
+        for i in range(tr.n_nl):
+            ok = (np.all(np.abs(xu[i]) <= 5) and np.all(np.abs(uu[i]) <= 2)
+                  and np.linalg.norm(uu[i]) <= 1.5)
+            assert ok == bool(np.all(np.abs(C[i]) < 1e-14))
+        for jj in range(tr.n_l):
+            ok = np.all(np.abs(xu[tr.n_nl + jj]) <= 5)
+            assert ok == bool(np.all(np.abs(CN[jj]) < 1e-14))
+
+
+def test_norm_L_dense_svd_and_step_size():
+    """alpha ||L|| = 0.99 < 1 (Sec. 4.1); the Lanczos branch agrees with dense SVD."""
+    p = constrained([2, 2, 1], 3, 2, seed=11)
+    o = Oracle(p)
+    ref = np.linalg.svd(o.L.toarray(), compute_uv=False)[0]
+    assert abs(o.normL - ref) < 1e-12 * ref
+    assert abs(o.alpha * ref - 0.99) < 1e-12
+    assert abs(o._norm_L(dense_max=0) - ref) < 1e-10 * ref
+
+
+# --- the CP operator ---------------------------------------------------------------
+def test_T_firmly_nonexpansive_in_M():
+    """T is firmly nonexpansive in the M metric (Sec. 4.1):
+    ||Tv - Tw||_M^2 <= <Tv - Tw, v - w>_M."""
+    p = constrained([2, 2, 1, 1], 3, 2, seed=12, uball=2.5)
+    o = Oracle(p)
+    rng = np.random.default_rng(13)
+    nv = o.lay.n_z + o.lay.n_eta
+    for _ in range(30):
+        v = rng.standard_normal(nv) * 3
+        w = rng.standard_normal(nv) * 3
+        d = o.T(v) - o.T(w)
+        assert o.M_inner(d, d) <= o.M_inner(d, v - w) + 1e-10
+
+
+def test_fixed_point_is_invariant():
+    """A converged iterate is (numerically) a fixed point and T(v) keeps x^0 = x0."""
+    p = constrained([2, 1], 3, 2, seed=16)
+    o = Oracle(p)
+    r = o.solve(tol=1e-6, max_iters=20000, method="spock")
+    assert r["res_inf"] <= 1e-6
+    assert np.allclose(r["x"][0], p.x0, atol=1e-13)
+    tv = o.T(r["v"])
+    assert np.max(np.abs(tv - r["Tv"])) == 0.0
+
+
+# --- Anderson's acceleration ---------------------------------------------------------
+def test_aa_direction_solves_linear_residual():
+    """For an affine residual R(v) = A v - b in R^m with m secant pairs, v + psi
+    is the zero of R (the type-II AA step is exact); kappa agrees with an
+    SVD least-squares solve."""
+    rng = np.random.default_rng(14)
+    m = 3
+    Am = rng.standard_normal((m, m)) + 3 * np.eye(m)
+    b = rng.standard_normal(m)
+    R = lambda v: Am @ v - b
+    vs = [rng.standard_normal(m) for _ in range(m + 1)]
+    S = [vs[i + 1] - vs[i] for i in range(m)]
+    Y = [R(vs[i + 1]) - R(vs[i]) for i in range(m)]
+    v = vs[-1]
+    psi = Oracle.aa_direction(R(v), S, Y, k=m + 1, m=m)
+    assert np.allclose(R(v + psi), 0.0, atol=1e-10)
+    kappa = np.linalg.lstsq(np.column_stack(Y), R(v), rcond=None)[0]
+    assert np.allclose(-R(v) - (np.column_stack(S) - np.column_stack(Y)) @ kappa, psi, atol=1e-10)
+
+
+# --- whole-solve pins ------------------------------------------------------------------
+def test_one_branch_tree_is_finite_horizon_lqr():
+    """Single scenario, AV@R_1, no constraints: the risk value is x0'P_0 x0 of
+    the time-varying Riccati recursion and u^t = K_t x^t."""
+    p = unconstrained([1, 1, 1, 1], 3, 2, seed=5)
+    o = Oracle(p)
+    r = o.solve(tol=1e-10, max_iters=20000, method="spock")
+    N = 4
+    Ps = [None] * (N + 1)
+    Ks = [None] * N
+    Ps[N] = np.diag(p.QN[0])
+    for t in range(N - 1, -1, -1):
+        A, B = p.A[t], p.B[t]
+        Q, R = np.diag(p.Q[t]), np.diag(p.R[t])
+        H = R + B.T @ Ps[t + 1] @ B
+        Ks[t] = -np.linalg.solve(H, B.T @ Ps[t + 1] @ A)
+        Ps[t] = Q + A.T @ Ps[t + 1] @ A + A.T @ Ps[t + 1] @ B @ Ks[t]
+    V = p.x0 @ Ps[0] @ p.x0
+    assert abs(r["risk"] - V) < 1e-7 * max(1.0, abs(V))
+    for t in range(N):
+        assert np.allclose(r["u"][t], Ks[t] @ r["x"][t], atol=1e-7)
+
+
+def _tree_riccati(p):
+    tr = so_.Tree(p.anc, p.prob)
+    Pm = [None] * tr.n
+    for jj in range(tr.n_l):
+        Pm[tr.n_nl + jj] = np.diag(p.QN[jj])
+    for t in range(tr.N - 1, -1, -1):
+        for i in tr.nodes_at[t]:
+            H = np.zeros((p.nu, p.nu)); G = np.zeros((p.nu, p.nx)); F = np.zeros((p.nx, p.nx))
+            for c in tr.children[i]:
+                pc = tr.prob[c]
+                A, B, P = p.A[c - 1], p.B[c - 1], Pm[c]
+                F += pc * (np.diag(p.Q[c - 1]) + A.T @ P @ A)
+                H += pc * (np.diag(p.R[c - 1]) + B.T @ P @ B)
+                G += pc * (B.T @ P @ A)
+            Pm[i] = F - G.T @ np.linalg.solve(H, G)
+    return p.x0 @ Pm[0] @ p.x0
+
+
+def _risk_neutral_qp(p):
+    """min sum_c pi^c (x^a'Q^c x^a + u^a'R^c u^a) + sum_j pi^j x^j'QN x^j s.t.
+    dynamics, as one dense equality-constrained QP."""
+    tr = so_.Tree(p.anc, p.prob)
+    nx, nu, n = p.nx, p.nu, tr.n
+    nX = n * nx + tr.n_nl * nu
+    H = np.zeros((nX, nX))
+    for c in range(1, n):
+        a = tr.anc[c]
+        H[a * nx:(a + 1) * nx, a * nx:(a + 1) * nx] += tr.pi[c] * np.diag(p.Q[c - 1])
+        o = n * nx + a * nu
+        H[o:o + nu, o:o + nu] += tr.pi[c] * np.diag(p.R[c - 1])
+    for jj in range(tr.n_l):
+        j = tr.n_nl + jj
+        H[j * nx:(j + 1) * nx, j * nx:(j + 1) * nx] += tr.pi[j] * np.diag(p.QN[jj])
+    rows, rhs = [], []
+    C0 = np.zeros((nx, nX)); C0[:, :nx] = np.eye(nx); rows.append(C0); rhs.append(p.x0)
+    for c in range(1, n):
+        a = tr.anc[c]
+        Cc = np.zeros((nx, nX))
+        Cc[:, c * nx:(c + 1) * nx] = np.eye(nx)
+        Cc[:, a * nx:(a + 1) * nx] = -p.A[c - 1]
+        Cc[:, n * nx + a * nu:n * nx + (a + 1) * nu] = -p.B[c - 1]
+        rows.append(Cc); rhs.append(p.c[c - 1])
+    C = np.vstack(rows)
+    K = np.block([[2 * H, C.T], [C, np.zeros((C.shape[0], C.shape[0]))]])
+    sol = np.linalg.solve(K, np.concatenate([np.zeros(nX), np.concatenate(rhs)]))
+    X = sol[:nX]
+    return float(X @ H @ X)
+
+
+def test_risk_neutral_tree_riccati_and_kkt():
+    """AV@R_1 and no constraints: risk-neutral multistage LQ, equal to the tree
+    Riccati value with conditional probabilities and to a dense KKT solve."""
+    p = unconstrained([2, 3, 1], 3, 2, seed=6)
+    o = Oracle(p)
+    r = o.solve(tol=1e-10, max_iters=30000, method="spock")
+    V1 = _tree_riccati(p)
+    V2 = _risk_neutral_qp(p)
+    assert abs(V1 - V2) < 1e-10 * max(1.0, abs(V1))
+    assert abs(r["risk"] - V1) < 1e-7 * max(1.0, abs(V1))
+
+
+def test_one_stage_two_children_avar_bruteforce():
+    """N = 1, two children, AV@R_a with a < 1, no constraints:
+    V* = max over the ambiguity segment of min_u sum mu_j Z_j(u) (minimax of a
+    convex-concave function), inner problem in closed form, outer by golden
+    section."""
+    p = unconstrained([2], 2, 2, seed=15, avar=0.4)
+    o = Oracle(p)
+    r = o.solve(tol=1e-10, max_iters=50000, method="spock")
+    x0 = p.x0
+    pr = p.prob[1:]
+    a = 0.4
+
+    def phi(m1):
+        mu = np.array([m1, 1 - m1])
+        H = np.zeros((p.nu, p.nu)); g = np.zeros(p.nu); const = 0.0
+        for j in range(2):
+            A, B = p.A[j], p.B[j]
+            QN = np.diag(p.QN[j])
+            H += mu[j] * (np.diag(p.R[j]) + B.T @ QN @ B)
+            g += mu[j] * (B.T @ QN @ A @ x0)
+            const += mu[j] * (x0 @ np.diag(p.Q[j]) @ x0 + (A @ x0) @ QN @ (A @ x0))
+        u = -np.linalg.solve(H, g)
+        return u @ H @ u + 2 * g @ u + const
+
+    lo = max(0.0, 1 - pr[1] / a)
+    hi = min(1.0, pr[0] / a)
+    gr = (math.sqrt(5) - 1) / 2
+    x1, x2 = hi - gr * (hi - lo), lo + gr * (hi - lo)
+    f1, f2 = phi(x1), phi(x2)
+    for _ in range(200):
+        if f1 > f2:
+            hi, x2, f2 = x2, x1, f1
+            x1 = hi - gr * (hi - lo); f1 = phi(x1)
+        else:
+            lo, x1, f1 = x1, x2, f2
+            x2 = lo + gr * (hi - lo); f2 = phi(x2)
+    V = max(phi(lo), phi(hi), f1, f2)
+    assert abs(r["risk"] - V) < 1e-7 * max(1.0, abs(V))
+
+
+def test_constrained_solution_diagnostics_vanish():
+    """On a constrained AV@R problem: residual, xi1, xi2, primal infeasibility
+    and complementarity gap vanish, the risk value equals the nested AV@R of
+    the returned trajectory (Eq. original-problem), constraints hold."""
+    p = constrained([2, 2, 1], 3, 2, seed=17, avar=0.5)
+    o = Oracle(p)
+    r = o.solve(tol=1e-7, max_iters=30000, method="spock")
+    assert r["res_inf"] <= 1e-7
+    assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
+    assert r["infeas"] < 1e-5 and r["gap"] < 1e-4
+    assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * abs(r["risk"])
+    assert np.all(np.abs(r["x"]) <= 5 + 1e-5) and np.all(np.abs(r["u"]) <= 2 + 1e-5)
