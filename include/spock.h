@@ -1,0 +1,190 @@
+/*
+ * spock.h -- C ABI of libspock: the SPOCK method (preconditioned
+ * Chambolle-Pock iteration accelerated by SuperMann with Anderson directions)
+ * for scenario-tree risk-averse optimal control problems (RAOCPs) with AV@R
+ * risk, on one NVIDIA B300 (sm_103a).
+ *
+ * Conventions for every call
+ *  - Plain C types only. Host pointers are marked (host), device pointers
+ *    (device); a device pointer must come from the CUDA runtime on the
+ *    current device and be 16-byte aligned.
+ *  - Every call returns an int status: SPOCK_OK (0), a positive warning, or a
+ *    negative error. Errors leave the outputs unspecified but never abort the
+ *    process and never trap the GPU. spock_status_str() names a status.
+ *  - The library copies every input array it is given; the caller keeps
+ *    ownership of its arrays. The library owns the device memory of a problem
+ *    until spock_problem_destroy().
+ *  - Calls on one problem are not thread-safe; different problems may be used
+ *    from different host threads.
+ *
+ * Problem statement (Sec. 3 of the paper):
+ *  - scenario tree (Sec. 3.2): n nodes in breadth-first order (stage-major,
+ *    children of a node contiguous, all leaves at stage N and last), given by
+ *    anc[] (anc[0] = -1) and prob[] = conditional probability of a node given
+ *    its ancestor (prob[0] = 1, children probabilities of a node sum to 1);
+ *  - dynamics (Eq. finite-horizon-evolution): x^c = A^c x^anc(c) + B^c u^anc(c)
+ *    + c^c for every non-root node c, x^0 = x0;
+ *  - costs (Sec. 3.2, "Quadratic-plus-linear costs", linear terms zero): edge
+ *    cost x'Q^c x + u'R^c u on the ancestor's (x, u) for every non-root c,
+ *    terminal cost x'Q_N^j x at every leaf j; Q, R, Q_N diagonal;
+ *  - constraints (Eq. constraints): optional box on x at every node (the
+ *    root's box is applied to the fixed x0), optional box on u and optional
+ *    Euclidean ball ||u||_2 <= r on u at every non-leaf node;
+ *  - risk (Sec. 3.3-3.4): AV@R_a over the children of every non-leaf node,
+ *    a in [0, 1] per non-leaf node; the problem is the nested formulation
+ *    Eq. original-problem, solved through its conic reformulation
+ *    Eq. min-s0-v1 (Sec. 4).
+ *
+ * Vector layout used by the operator-level calls (scaled variables, Sec. 4.3
+ * "Sets" and Sec. 4.4 "Linear operator L"); first n_nl nodes are non-leaf:
+ *   z   = [ s0 | x (n*nx) | u (n_nl*nu) | y (sum_i 2 n_i + 1) | tau (n-1) | s (n-1) ]
+ *   eta = [ eta_y | eta_s (n_nl) | eta_c (n_nl*n_c) | eta_q ((n-1)(nx+nu+2))
+ *         | eta_cN (n_l*n_cN) | eta_qN (n_l*(nx+2)) ]
+ *   v   = [ z | eta ]  (n_v = n_z + n_eta elements)
+ * with tau^c, s^c (c >= 1) at index c-1 of their arrays and constraint rows
+ * [x box (nx)] [u box (nu)] [u ball (nu)] per non-leaf node, [x box] per leaf.
+ */
+#ifndef SPOCK_H
+#define SPOCK_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SPOCK_OK 0
+#define SPOCK_MAXITER 1      /* warning: not converged within max_iters; outputs written */
+#define SPOCK_EINVAL -1      /* invalid argument (tree shape, sizes, probabilities, NULL) */
+#define SPOCK_ENOMEM -2      /* device memory could not be allocated / admission refused */
+#define SPOCK_ENOTPD -3      /* Cholesky of R~ = I + sum B'PB failed (not positive definite) */
+#define SPOCK_EDEVICE -4     /* CUDA runtime error */
+#define SPOCK_ETIMEOUT -5    /* a device-side wait (grid barrier) ran out of its time limit */
+#define SPOCK_EUNSUPPORTED -6 /* sizes beyond the compiled limits (nx, nu <= 128, children <= 1024) */
+
+#define SPOCK_MAX_NX 128
+#define SPOCK_MAX_NU 128
+
+typedef struct spock_problem spock_problem;
+
+/* Problem data (host arrays, row-major, float64). Sizes: n = n_nodes,
+ * n_nl = non-leaf count, n_l = leaf count (derived from anc). */
+typedef struct spock_problem_desc {
+    int n_nodes;
+    const int* anc;          /* [n] ancestor, anc[0] = -1 (Sec. 3.2) */
+    const double* prob;      /* [n] conditional probability given the ancestor */
+    int nx, nu;              /* state and input dimensions (Sec. 3.1) */
+    const double* A;         /* [(n-1) nx nx]  A^c of node c at (c-1) */
+    const double* B;         /* [(n-1) nx nu]  B^c */
+    const double* c;         /* [(n-1) nx]     c^c, or NULL for zero */
+    const double* Q;         /* [(n-1) nx]     diagonal of Q^c (edge cost on x^anc(c)) */
+    const double* R;         /* [(n-1) nu]     diagonal of R^c (edge cost on u^anc(c)) */
+    const double* QN;        /* [n_l nx]       diagonal of Q_N^j, leaves in node order */
+    const double* x_lo;      /* [n nx] or NULL (no state box) */
+    const double* x_hi;      /* [n nx] or NULL */
+    const double* u_lo;      /* [n_nl nu] or NULL (no input box) */
+    const double* u_hi;      /* [n_nl nu] or NULL */
+    const double* u_ball;    /* [n_nl] ball radius on u, or NULL (no ball) */
+    const double* avar;      /* [n_nl] AV@R level in [0, 1] (Sec. 3.3) */
+} spock_problem_desc;
+
+typedef struct spock_sizes {
+    int n, n_nonleaf, n_leaf, N, nx, nu, n_c, n_cN;
+    long long n_z, n_eta, n_v;
+    long long factor_bytes_fp64;   /* device bytes of the per-iteration factors, FP64 copy */
+    long long factor_bytes_fp32;   /* same, FP32 copy */
+} spock_sizes;
+
+/* spock_problem_create: validate the tree and data, copy them to the device,
+ * and run the offline part on the GPU in FP64 -- the preconditioning of
+ * Sec. 5.4, Alg. 1 (projection on S1, offline) and ||L|| of Sec. 4.4 giving
+ * alpha = 0.99/||L|| (Sec. 4.1 needs alpha ||L|| < 1). Also builds the FP32
+ * copies of the factors. Errors: SPOCK_EINVAL (tree not breadth-first,
+ * probabilities, sizes), SPOCK_EUNSUPPORTED, SPOCK_ENOTPD, SPOCK_ENOMEM,
+ * SPOCK_EDEVICE. On error *out is NULL. */
+int spock_problem_create(const spock_problem_desc* desc, spock_problem** out);
+void spock_problem_destroy(spock_problem* p);
+
+int spock_problem_sizes(const spock_problem* p, spock_sizes* out);
+
+/* Step size alpha and ||L||. set_alpha overrides alpha (must satisfy
+ * 0 < alpha ||L|| < 1, else SPOCK_EINVAL). */
+int spock_problem_alpha(const spock_problem* p, double* alpha, double* normL);
+int spock_problem_set_alpha(spock_problem* p, double alpha);
+
+/* Scalings of Sec. 5.4 (host outputs): Sx[nx], Su[nu], SxN[nx]. */
+int spock_problem_scalings(const spock_problem* p, double* Sx, double* Su, double* SxN);
+
+/* FP64 output of Alg. 1 (host outputs, may be NULL): P [n nx nx], K [n_nl nu nx],
+ * Rtilde [n_nl nu nu], Abar [(n-1) nx nx] (scaled problem). */
+int spock_problem_factors(const spock_problem* p, double* P, double* K, double* Rtilde,
+                          double* Abar);
+
+/* Initial state used by the operator-level calls (host, unscaled, [nx]). */
+int spock_problem_set_x0(spock_problem* p, const double* x0);
+
+/* ---------------- operator-level calls (device pointers, async on stream) -----
+ * precision: 64 (double vectors) or 32 (float vectors). stream: a cudaStream_t
+ * or NULL for the default stream. */
+
+/* One Chambolle-Pock step v_out = T(v_in) (Eq. chambolle-pock-operator) with
+ * the problem's x0 and alpha: prox_{alpha f} of Eq. f (s0 - alpha, proj_S1 by
+ * Alg. 2, proj_S2) and prox_{alpha g*} of Eq. g (Moreau, proj_S3 of
+ * Eq. S3-def). v_in, v_out: (device) [n_v], must not overlap.
+ * stats (host, may be NULL) receives 8 doubles of r = v_in - v_out:
+ * [ max|r|, ||r_z||^2, ||r_eta||^2, <r_eta, L r_z>, 0, 0, 0, 0 ]. Blocking. */
+int spock_op_T(spock_problem* p, int precision, const void* v_in, void* v_out, double* stats,
+               void* stream);
+
+/* eta = L z (Sec. 4.4) and z = L* eta. (device) buffers of n_z / n_eta elements. */
+int spock_op_L(spock_problem* p, int precision, const void* z, void* eta, void* stream);
+int spock_op_Lt(spock_problem* p, int precision, const void* eta, void* z, void* stream);
+
+/* ---------------- solve -------------------------------------------------------*/
+typedef struct spock_solve_opts {
+    int precision;        /* 64 or 32: arithmetic of the iteration (factors are FP64-built) */
+    double tol;           /* stop when ||v - T(v)||_inf <= tol (Sec. 5.3, eps_rel = 0) */
+    int max_iters;        /* outer iteration cap; SPOCK_MAXITER when reached */
+    int max_backtracks;   /* cap on tau halvings per iteration (then v <- T(v)) */
+    int method;           /* 0: SPOCK (Alg. 4 with Alg. 3, m = 3); 1: plain CP v <- T(v) */
+    int warm_start;       /* 1: start from the problem's last iterate, 0: z = eta = 0 */
+    int fp64_check;       /* 1 (FP32 only): finish with an FP64 residual check */
+} spock_solve_opts;
+
+typedef struct spock_info {
+    int status;           /* SPOCK_OK, SPOCK_MAXITER or an error */
+    int iters;            /* outer iterations k */
+    int n_T;              /* evaluations of T */
+    int n_K0, n_K1, n_K2, n_fallback;   /* accepted step kinds of Alg. 4 */
+    int n_backtracks;     /* total tau halvings */
+    double res_inf;       /* ||v - T(v)||_inf at exit, in the iteration precision */
+    double res_inf_fp64;  /* same in FP64 (fp64_check), else = res_inf */
+    double risk;          /* s^0 of T(v): the risk value (Sec. 4, Eq. min-s0-v1) */
+    double device_ms;     /* device time of the solve kernel (CUDA events) */
+} spock_info;
+
+void spock_solve_opts_default(spock_solve_opts* o);
+
+/* Solve from host buffers (end-to-end: host->device copy of x0, solve,
+ * device->host copy of the outputs, all inside the call). x0 (host) [nx],
+ * unscaled; x_out (host) [n nx], u_out (host) [n_nl nu], unscaled, from T(v)
+ * at exit; risk (host) scalar; info (host) may be NULL. Blocking. */
+int spock_solve(spock_problem* p, const double* x0, const spock_solve_opts* opts,
+                double* x_out, double* u_out, double* risk, spock_info* info);
+
+/* Same with device buffers, enqueued on `stream` (blocking only for info):
+ * x0 (device, double) [nx]; x_out, u_out (device, double) may be NULL. */
+int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opts* opts,
+                       double* x_out, double* u_out, void* stream, spock_info* info);
+
+/* Device copy of the current iterate v (after a solve) and a way to set it
+ * (warm start). (device) buffers of n_v elements in the given precision. */
+int spock_get_iterate(spock_problem* p, int precision, void* v_out, void* stream);
+int spock_set_iterate(spock_problem* p, int precision, const void* v_in, void* stream);
+
+const char* spock_status_str(int status);
+int spock_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPOCK_H */

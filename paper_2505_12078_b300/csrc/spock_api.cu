@@ -1,0 +1,806 @@
+// spock_api.cu -- host runtime and C ABI of libspock (see include/spock.h).
+//
+// Owns the device memory of a problem: tree and schedule arrays, the FP64
+// offline data, FP64 and FP32 copies of the per-iteration factors, and the
+// solve buffers of each precision (allocated on first use). The offline part
+// (Sec. 5.4 preconditioning, Alg. 1, ||L||) runs in FP64 kernels at creation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/spock.h"
+#include "spock_dev.cuh"
+#include "spock_internal.h"
+
+using namespace spock;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int pad4(int x) { return (x + 3) & ~3; }
+
+struct DevMem {
+  std::vector<void*> ptrs;
+  bool failed = false;
+  template <class T>
+  T* alloc(long long count) {
+    if (count <= 0) count = 1;
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)count * sizeof(T)) != cudaSuccess) {
+      failed = true;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void free_all() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+template <class T>
+struct Iter {   // per-precision iteration data
+  T *MB = nullptr, *MF = nullptr, *MP = nullptr, *KT = nullptr, *cvec = nullptr, *Pc = nullptr;
+  T *qh = nullptr, *rh = nullptr, *qNh = nullptr, *gx = nullptr, *gu = nullptr, *gN = nullptr;
+  T *box_lo = nullptr, *box_hi = nullptr, *boxN_lo = nullptr, *boxN_hi = nullptr, *ball = nullptr;
+  T *prob = nullptr, *avar = nullptr, *x0s = nullptr;
+  T *qbuf = nullptr, *dbuf = nullptr, *hbuf = nullptr, *ebuf = nullptr;
+  SolveBufs<T> sb{};
+  bool have_bufs = false;
+  Prob<T> P{};
+};
+
+}  // namespace
+
+struct spock_problem {
+  int n = 0, n_nl = 0, n_l = 0, N = 0, nx = 0, nu = 0, n_c = 0, n_cN = 0;
+  int nbx = 0, nbu = 0, nbox = 0, has_ball = 0;
+  long long n_y = 0, nz = 0, neta = 0, nv = 0;
+  long long o_x, o_u, o_y, o_tau, o_s, e_y, e_s, e_c, e_q, e_cN, e_qN;
+  int ldB, ldF, ldP, ldK;
+  std::vector<int> anc, ch_off, yoff, stage_off, ynode, lvl_off, seg_top, seg_bot, seg_len;
+  std::vector<double> Sx, Su, SxN;
+  double a_con = 1, a_conN = 1, alpha = 0, normL = 0;
+  int max_items = 1;
+  int tw = 8;
+  DevMem mem;
+  // device tree / schedule
+  int *d_anc, *d_ch_off, *d_yoff, *d_ynode, *d_lvl_off, *d_seg_top, *d_seg_bot, *d_seg_len;
+  // FP64 offline data kept for inspection
+  double *d_P, *d_K, *d_Rt, *d_Abar, *d_Sx, *d_SxN, *d_Su;
+  double* d_x0raw;   // unscaled x0 of the operator-level calls
+  Iter<double> f64;
+  Iter<float> f32;
+  double* d_out_risk;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? SPOCK_OK : SPOCK_EDEVICE; }
+
+bool finite_arr(const double* a, long long n) {
+  for (long long i = 0; i < n; ++i)
+    if (!isfinite(a[i])) return false;
+  return true;
+}
+
+// Validate the tree (Sec. 3.2) and build the node arrays and sweep schedule.
+int build_tree(spock_problem* p, int n, const int* anc, const double* prob) {
+  if (n < 2 || !anc || !prob || anc[0] != -1) return SPOCK_EINVAL;
+  std::vector<int> stage(n, 0);
+  for (int i = 1; i < n; ++i) {
+    if (anc[i] < 0 || anc[i] >= i) return SPOCK_EINVAL;
+    if (anc[i] < anc[i - 1] && i > 1) return SPOCK_EINVAL;          // children contiguous
+    stage[i] = stage[anc[i]] + 1;
+    if (stage[i] < stage[i - 1]) return SPOCK_EINVAL;                // stage-major
+    if (!(prob[i] > 0.0) || !(prob[i] <= 1.0 + 1e-12)) return SPOCK_EINVAL;
+  }
+  const int N = stage[n - 1];
+  int n_nl = 0;
+  while (n_nl < n && stage[n_nl] < N) ++n_nl;
+  for (int i = n_nl; i < n; ++i)
+    if (stage[i] != N) return SPOCK_EINVAL;
+  std::vector<int> nch(n, 0);
+  for (int i = 1; i < n; ++i) nch[anc[i]]++;
+  for (int i = 0; i < n_nl; ++i)
+    if (nch[i] == 0) return SPOCK_EINVAL;
+  for (int i = n_nl; i < n; ++i)
+    if (nch[i] != 0) return SPOCK_EINVAL;
+  p->n = n; p->n_nl = n_nl; p->n_l = n - n_nl; p->N = N;
+  p->anc.assign(anc, anc + n);
+  p->ch_off.assign(n_nl + 1, 0);
+  {
+    int c = 1;
+    for (int i = 0; i < n_nl; ++i) {
+      p->ch_off[i] = c;
+      c += nch[i];
+    }
+    p->ch_off[n_nl] = c;
+    for (int i = 0; i < n_nl; ++i)
+      for (int cc = p->ch_off[i]; cc < p->ch_off[i + 1]; ++cc)
+        if (anc[cc] != i) return SPOCK_EINVAL;
+  }
+  for (int i = 0; i < n_nl; ++i) {
+    double s = 0;
+    for (int c = p->ch_off[i]; c < p->ch_off[i + 1]; ++c) s += prob[c];
+    if (fabs(s - 1.0) > 1e-9) return SPOCK_EINVAL;
+  }
+  p->stage_off.assign(N + 2, 0);
+  for (int t = 0, i = 0; t <= N; ++t) {
+    p->stage_off[t] = i;
+    while (i < n && stage[i] == t) ++i;
+  }
+  p->stage_off[N + 1] = n;
+  p->yoff.assign(n_nl + 1, 0);
+  for (int i = 0; i < n_nl; ++i) p->yoff[i + 1] = p->yoff[i] + 2 * nch[i] + 1;
+  p->n_y = p->yoff[n_nl];
+  p->ynode.resize(p->n_y);
+  for (int i = 0; i < n_nl; ++i)
+    for (int k = p->yoff[i]; k < p->yoff[i + 1]; ++k) p->ynode[k] = i;
+  // segments: chains of non-leaf nodes with a single non-leaf child
+  auto is_top = [&](int i) { return i == 0 || nch[anc[i]] != 1; };
+  auto is_bot = [&](int i) { return nch[i] != 1 || p->ch_off[i] >= n_nl; };
+  std::vector<int> tops, bots, lens, seg_of(n_nl, -1);
+  for (int i = 0; i < n_nl; ++i) {
+    if (!is_top(i)) continue;
+    int j = i, len = 1;
+    seg_of[j] = (int)tops.size();
+    while (!is_bot(j)) {
+      j = p->ch_off[j];
+      seg_of[j] = (int)tops.size();
+      ++len;
+    }
+    tops.push_back(i); bots.push_back(j); lens.push_back(len);
+  }
+  const int ns = (int)tops.size();
+  std::vector<int> level(ns, 0);
+  for (int s = ns - 1; s >= 0; --s) {       // deeper tops come later in BFS order
+    const int b = bots[s];
+    int lv = 0;
+    for (int c = p->ch_off[b]; c < p->ch_off[b + 1]; ++c)
+      if (c < n_nl) lv = std::max(lv, level[seg_of[c]] + 1);
+    level[s] = lv;
+  }
+  int L = 0;
+  for (int s = 0; s < ns; ++s) L = std::max(L, level[s] + 1);
+  p->lvl_off.assign(L + 1, 0);
+  p->seg_top.clear(); p->seg_bot.clear(); p->seg_len.clear();
+  int max_items = n;
+  for (int l = 0; l < L; ++l) {
+    p->lvl_off[l] = (int)p->seg_top.size();
+    for (int s = 0; s < ns; ++s)
+      if (level[s] == l) {
+        p->seg_top.push_back(tops[s]); p->seg_bot.push_back(bots[s]); p->seg_len.push_back(lens[s]);
+      }
+  }
+  p->lvl_off[L] = (int)p->seg_top.size();
+  p->max_items = max_items;
+  return SPOCK_OK;
+}
+
+template <class T>
+void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
+  Prob<T>& P = it.P;
+  P.n = p->n; P.n_nl = p->n_nl; P.n_l = p->n_l; P.N = p->N; P.nx = p->nx; P.nu = p->nu;
+  P.n_c = p->n_c; P.n_cN = p->n_cN; P.nbx = p->nbx; P.nbu = p->nbu; P.nbox = p->nbox;
+  P.has_ball = p->has_ball;
+  P.nz = p->nz; P.neta = p->neta; P.nv = p->nv;
+  P.o_x = p->o_x; P.o_u = p->o_u; P.o_y = p->o_y; P.o_tau = p->o_tau; P.o_s = p->o_s;
+  P.e_y = p->e_y; P.e_s = p->e_s; P.e_c = p->e_c; P.e_q = p->e_q; P.e_cN = p->e_cN; P.e_qN = p->e_qN;
+  P.W = p->nx + p->nu + 2;
+  P.ldB = p->ldB; P.ldF = p->ldF; P.ldP = p->ldP; P.ldK = p->ldK;
+  P.anc = p->d_anc; P.ch_off = p->d_ch_off; P.yoff = p->d_yoff;
+  P.n_levels = (int)p->lvl_off.size() - 1;
+  P.lvl_off = p->d_lvl_off; P.seg_top = p->d_seg_top; P.seg_bot = p->d_seg_bot; P.seg_len = p->d_seg_len;
+  P.MB = it.MB; P.MF = it.MF; P.MP = it.MP; P.KT = it.KT; P.cvec = it.cvec; P.Pc = it.Pc;
+  P.qh = it.qh; P.rh = it.rh; P.qNh = it.qNh; P.gx = it.gx; P.gu = it.gu; P.gN = it.gN;
+  P.box_lo = it.box_lo; P.box_hi = it.box_hi; P.boxN_lo = it.boxN_lo; P.boxN_hi = it.boxN_hi;
+  P.ball = it.ball; P.prob = it.prob; P.avar = it.avar; P.x0s = it.x0s;
+  P.alpha = (T)alpha;
+  P.qbuf = it.qbuf; P.dbuf = it.dbuf; P.hbuf = it.hbuf; P.ebuf = it.ebuf;
+}
+
+template <class T>
+int alloc_iter(spock_problem* p, Iter<T>& it) {
+  DevMem& m = p->mem;
+  const int n = p->n, n_nl = p->n_nl, n_l = p->n_l, nx = p->nx, nu = p->nu;
+  it.MB = m.alloc<T>((long long)(n - 1) * nx * p->ldB);
+  it.MF = m.alloc<T>((long long)(n - 1) * (nx + nu) * p->ldF);
+  it.MP = m.alloc<T>((long long)n_nl * nu * p->ldP);
+  it.KT = m.alloc<T>((long long)n_nl * nx * p->ldK);
+  it.cvec = m.alloc<T>((long long)(n - 1) * nx);
+  it.Pc = m.alloc<T>((long long)(n - 1) * nx);
+  it.qh = m.alloc<T>((long long)(n - 1) * nx);
+  it.rh = m.alloc<T>((long long)(n - 1) * nu);
+  it.qNh = m.alloc<T>((long long)n_l * nx);
+  it.gx = m.alloc<T>(nx); it.gu = m.alloc<T>(nu); it.gN = m.alloc<T>(nx);
+  it.box_lo = m.alloc<T>((long long)n_nl * std::max(1, p->nbox));
+  it.box_hi = m.alloc<T>((long long)n_nl * std::max(1, p->nbox));
+  it.boxN_lo = m.alloc<T>((long long)n_l * nx);
+  it.boxN_hi = m.alloc<T>((long long)n_l * nx);
+  it.ball = m.alloc<T>(n_nl);
+  it.prob = m.alloc<T>(n);
+  it.avar = m.alloc<T>(n_nl);
+  it.x0s = m.alloc<T>(nx);
+  it.qbuf = m.alloc<T>((long long)n * nx);
+  it.dbuf = m.alloc<T>((long long)n_nl * nu);
+  it.hbuf = m.alloc<T>((long long)n_nl * nx);
+  it.ebuf = m.alloc<T>((long long)n_nl * nu);
+  return m.failed ? SPOCK_ENOMEM : SPOCK_OK;
+}
+
+template <class T>
+int ensure_bufs(spock_problem* p, Iter<T>& it) {
+  if (it.have_bufs) return SPOCK_OK;
+  DevMem& m = p->mem;
+  const long long nv = p->nv;
+  SolveBufs<T>& b = it.sb;
+  b.V = m.alloc<T>(nv); b.TV = m.alloc<T>(nv); b.VT = m.alloc<T>(nv); b.TVT = m.alloc<T>(nv);
+  b.PSI = m.alloc<T>(nv); b.VP = m.alloc<T>(nv); b.RP = m.alloc<T>(nv);
+  b.S = m.alloc<T>(3 * nv); b.Y = m.alloc<T>(3 * nv);
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  b.partials = m.alloc<double>((long long)nsm * 8 * NRED);
+  b.ctl = m.alloc<SolveCtl>(1);
+  if (m.failed) return SPOCK_ENOMEM;
+  cudaMemset(b.V, 0, nv * sizeof(T));
+  cudaMemset(b.S, 0, 3 * nv * sizeof(T));
+  cudaMemset(b.Y, 0, 3 * nv * sizeof(T));
+  it.have_bufs = true;
+  return cuda_err(cudaGetLastError());
+}
+
+__global__ void k_scale_x0(int nx, const double* __restrict__ x0, const double* __restrict__ Sx,
+                           double* __restrict__ o64, float* __restrict__ o32) {
+  for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+    const double v = Sx[k] * x0[k];
+    o64[k] = v;
+    o32[k] = (float)v;
+  }
+}
+
+// x = x~ / S, u = u~ / Su from the z part of T(v)
+template <class T>
+__global__ void k_unscale(int n, int n_nl, int nx, int nu, long long o_x, long long o_u,
+                          const T* __restrict__ z, const double* __restrict__ Sx,
+                          const double* __restrict__ SxN, const double* __restrict__ Su,
+                          double* __restrict__ xo, double* __restrict__ uo, double* __restrict__ risk) {
+  const long long nX = (long long)n * nx, nU = (long long)n_nl * nu;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nX + nU + 1;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < nX) {
+      const long long i = e / nx;
+      const int k = (int)(e % nx);
+      if (xo) xo[e] = (double)z[o_x + e] / ((i >= n_nl) ? SxN[k] : Sx[k]);
+    } else if (e < nX + nU) {
+      const long long f = e - nX;
+      if (uo) uo[f] = (double)z[o_u + f] / Su[f % nu];
+    } else {
+      *risk = (double)z[0];
+    }
+  }
+}
+
+int pick_tw(int nx, int nu) {
+  const int d = nx + nu;
+  if (d >= 96) return 8;
+  if (d >= 48) return 4;
+  if (d >= 24) return 2;
+  return 1;
+}
+
+template <class T>
+int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t st, SolveCtl* h_ctl,
+               float* ms) {
+  int rc = ensure_bufs(p, it);
+  if (rc) return rc;
+  const int prec = sizeof(T) == 8 ? 64 : 32;
+  int maxg = 0;
+  if (solver_max_grid(prec, p->tw, kThreads, p->nx + p->nu, &maxg) || maxg <= 0) return SPOCK_EDEVICE;
+  const int teams = (kThreads / 32) / p->tw;
+  int grid = (p->max_items + teams - 1) / teams;
+  if (grid > maxg) grid = maxg;
+  if (grid < 1) grid = 1;
+  if (cudaMemsetAsync(it.sb.ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return SPOCK_EDEVICE;
+  cudaEventRecord(p->ev0, st);
+  cudaError_t e = launch_solve<T>(it.P, it.sb, so, p->tw, grid, kThreads, st);
+  if (e != cudaSuccess) return SPOCK_EDEVICE;
+  cudaEventRecord(p->ev1, st);
+  if (cudaMemcpyAsync(h_ctl, it.sb.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SPOCK_EDEVICE;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (ms) cudaEventElapsedTime(ms, p->ev0, p->ev1);
+  if (h_ctl->status < 0) return SPOCK_ETIMEOUT;
+  return SPOCK_OK;
+}
+
+template <class T>
+T* buf_index(SolveBufs<T>& b, int i) {
+  return i == 0 ? b.V : i == 1 ? b.TV : i == 2 ? b.VT : b.TVT;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spock_version(void) { return 1; }
+
+const char* spock_status_str(int s) {
+  switch (s) {
+    case SPOCK_OK: return "ok";
+    case SPOCK_MAXITER: return "not converged within max_iters";
+    case SPOCK_EINVAL: return "invalid argument";
+    case SPOCK_ENOMEM: return "out of device memory";
+    case SPOCK_ENOTPD: return "R~ = I + sum B'PB not positive definite";
+    case SPOCK_EDEVICE: return "CUDA runtime error";
+    case SPOCK_ETIMEOUT: return "device-side wait ran out of time";
+    case SPOCK_EUNSUPPORTED: return "sizes beyond the compiled limits";
+    default: return "unknown status";
+  }
+}
+
+void spock_solve_opts_default(spock_solve_opts* o) {
+  if (!o) return;
+  o->precision = 64;
+  o->tol = 1e-4;
+  o->max_iters = 5000;
+  o->max_backtracks = 30;
+  o->method = 0;
+  o->warm_start = 0;
+  o->fp64_check = 1;
+}
+
+int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
+  if (!out) return SPOCK_EINVAL;
+  *out = nullptr;
+  if (!d || !d->A || !d->B || !d->Q || !d->R || !d->QN || !d->avar) return SPOCK_EINVAL;
+  if (d->nx < 1 || d->nu < 1) return SPOCK_EINVAL;
+  if (d->nx > SPOCK_MAX_NX || d->nu > SPOCK_MAX_NU || d->nx + d->nu > MAXD) return SPOCK_EUNSUPPORTED;
+  if ((d->x_lo == nullptr) != (d->x_hi == nullptr)) return SPOCK_EINVAL;
+  if ((d->u_lo == nullptr) != (d->u_hi == nullptr)) return SPOCK_EINVAL;
+  spock_problem* p = new spock_problem();
+  int rc = build_tree(p, d->n_nodes, d->anc, d->prob);
+  if (rc) { delete p; return rc; }
+  const int n = p->n, n_nl = p->n_nl, n_l = p->n_l, nx = d->nx, nu = d->nu;
+  p->nx = nx; p->nu = nu;
+  // data checks
+  auto bad = [&](const double* a, long long len) { return a && !finite_arr(a, len); };
+  if (bad(d->A, (long long)(n - 1) * nx * nx) || bad(d->B, (long long)(n - 1) * nx * nu) ||
+      bad(d->c, (long long)(n - 1) * nx) || bad(d->Q, (long long)(n - 1) * nx) ||
+      bad(d->R, (long long)(n - 1) * nu) || bad(d->QN, (long long)n_l * nx) ||
+      bad(d->x_lo, (long long)n * nx) || bad(d->x_hi, (long long)n * nx) ||
+      bad(d->u_lo, (long long)n_nl * nu) || bad(d->u_hi, (long long)n_nl * nu) ||
+      bad(d->u_ball, n_nl) || bad(d->avar, n_nl)) {
+    delete p; return SPOCK_EINVAL;
+  }
+  for (long long e = 0; e < (long long)(n - 1) * nx; ++e) if (d->Q[e] < 0) { delete p; return SPOCK_EINVAL; }
+  for (long long e = 0; e < (long long)(n - 1) * nu; ++e) if (d->R[e] < 0) { delete p; return SPOCK_EINVAL; }
+  for (long long e = 0; e < (long long)n_l * nx; ++e) if (d->QN[e] < 0) { delete p; return SPOCK_EINVAL; }
+  for (int i = 0; i < n_nl; ++i) if (d->avar[i] < 0 || d->avar[i] > 1) { delete p; return SPOCK_EINVAL; }
+  if (d->x_lo) for (long long e = 0; e < (long long)n * nx; ++e) if (d->x_lo[e] > d->x_hi[e]) { delete p; return SPOCK_EINVAL; }
+  if (d->u_lo) for (long long e = 0; e < (long long)n_nl * nu; ++e) if (d->u_lo[e] > d->u_hi[e]) { delete p; return SPOCK_EINVAL; }
+  if (d->u_ball) for (int i = 0; i < n_nl; ++i) if (!(d->u_ball[i] >= 0)) { delete p; return SPOCK_EINVAL; }
+  p->nbx = d->x_lo ? nx : 0;
+  p->nbu = d->u_lo ? nu : 0;
+  p->nbox = p->nbx + p->nbu;
+  p->has_ball = d->u_ball ? 1 : 0;
+  p->n_c = p->nbox + (p->has_ball ? nu : 0);
+  p->n_cN = p->nbx;
+  // layout (Sec. 4.3-4.4)
+  p->o_x = 1; p->o_u = p->o_x + (long long)n * nx; p->o_y = p->o_u + (long long)n_nl * nu;
+  p->o_tau = p->o_y + p->n_y; p->o_s = p->o_tau + (n - 1); p->nz = p->o_s + (n - 1);
+  p->e_y = 0; p->e_s = p->n_y; p->e_c = p->e_s + n_nl; p->e_q = p->e_c + (long long)n_nl * p->n_c;
+  p->e_cN = p->e_q + (long long)(n - 1) * (nx + nu + 2);
+  p->e_qN = p->e_cN + (long long)n_l * p->n_cN;
+  p->neta = p->e_qN + (long long)n_l * (nx + 2);
+  p->nv = p->nz + p->neta;
+  p->ldB = pad4(nx + nu); p->ldF = pad4(nx); p->ldP = pad4(nx + nu); p->ldK = pad4(nu);
+  p->tw = pick_tw(nx, nu);
+  // preconditioning scalings (Sec. 5.4)
+  int maxch = 1;
+  for (int i = 0; i < n_nl; ++i) maxch = std::max(maxch, p->ch_off[i + 1] - p->ch_off[i]);
+  const double chat = sqrt((double)maxch);
+  p->Sx.assign(nx, 1.0); p->Su.assign(nu, 1.0); p->SxN.assign(nx, 1.0);
+  for (int c = 1; c < n; ++c) {
+    for (int k = 0; k < nx; ++k) p->Sx[k] = std::max(p->Sx[k], sqrt(d->Q[(long long)(c - 1) * nx + k]));
+    for (int k = 0; k < nu; ++k) p->Su[k] = std::max(p->Su[k], sqrt(d->R[(long long)(c - 1) * nu + k]));
+  }
+  for (int j = 0; j < n_l; ++j)
+    for (int k = 0; k < nx; ++k) p->SxN[k] = std::max(p->SxN[k], sqrt(d->QN[(long long)j * nx + k]));
+  for (int k = 0; k < nx; ++k) p->Sx[k] *= chat;
+  for (int k = 0; k < nu; ++k) p->Su[k] *= chat;
+  // ||[Gx Sx^-1, Gu Su^-1]||_2 of selection rows: its Gram is diagonal
+  {
+    double g = 0.0;
+    if (p->nbx) for (int k = 0; k < nx; ++k) g = std::max(g, 1.0 / (p->Sx[k] * p->Sx[k]));
+    const int nub = (p->nbu ? 1 : 0) + (p->has_ball ? 1 : 0);
+    if (nub) for (int k = 0; k < nu; ++k) g = std::max(g, nub / (p->Su[k] * p->Su[k]));
+    p->a_con = std::max(1.0, sqrt(g));
+    double gN = 0.0;
+    if (p->nbx) for (int k = 0; k < nx; ++k) gN = std::max(gN, 1.0 / (p->SxN[k] * p->SxN[k]));
+    p->a_conN = std::max(1.0, sqrt(gN));
+  }
+  if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
+    delete p; return SPOCK_EDEVICE;
+  }
+  DevMem& m = p->mem;
+  auto up_i = [&](const std::vector<int>& v) {
+    int* q = m.alloc<int>((long long)v.size());
+    if (q && !v.empty()) cudaMemcpy(q, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice);
+    return q;
+  };
+  auto up_d = [&](const double* a, long long len) -> double* {
+    if (!a) return nullptr;
+    double* q = m.alloc<double>(len);
+    if (q) cudaMemcpy(q, a, (size_t)len * sizeof(double), cudaMemcpyHostToDevice);
+    return q;
+  };
+  p->d_anc = up_i(p->anc); p->d_ch_off = up_i(p->ch_off); p->d_yoff = up_i(p->yoff);
+  p->d_ynode = up_i(p->ynode); p->d_lvl_off = up_i(p->lvl_off); p->d_seg_top = up_i(p->seg_top);
+  p->d_seg_bot = up_i(p->seg_bot); p->d_seg_len = up_i(p->seg_len);
+  p->d_Sx = up_d(p->Sx.data(), nx); p->d_Su = up_d(p->Su.data(), nu); p->d_SxN = up_d(p->SxN.data(), nx);
+  double* d_prob = up_d(d->prob, n);
+  double* d_avar = up_d(d->avar, n_nl);
+  DevMem tmp;   // setup-only buffers
+  double* dA = tmp.alloc<double>((long long)(n - 1) * nx * nx);
+  double* dB = tmp.alloc<double>((long long)(n - 1) * nx * nu);
+  double* dc = nullptr;
+  if (d->c) dc = tmp.alloc<double>((long long)(n - 1) * nx);
+  double* dQ = tmp.alloc<double>((long long)(n - 1) * nx);
+  double* dR = tmp.alloc<double>((long long)(n - 1) * nu);
+  double* dQN = tmp.alloc<double>((long long)n_l * nx);
+  double* dxlo = d->x_lo ? tmp.alloc<double>((long long)n * nx) : nullptr;
+  double* dxhi = d->x_hi ? tmp.alloc<double>((long long)n * nx) : nullptr;
+  double* dulo = d->u_lo ? tmp.alloc<double>((long long)n_nl * nu) : nullptr;
+  double* duhi = d->u_hi ? tmp.alloc<double>((long long)n_nl * nu) : nullptr;
+  double* dball = d->u_ball ? tmp.alloc<double>(n_nl) : nullptr;
+  if (tmp.failed || m.failed) { tmp.free_all(); m.free_all(); delete p; return SPOCK_ENOMEM; }
+  cudaMemcpy(dA, d->A, (size_t)(n - 1) * nx * nx * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dB, d->B, (size_t)(n - 1) * nx * nu * 8, cudaMemcpyHostToDevice);
+  if (dc) cudaMemcpy(dc, d->c, (size_t)(n - 1) * nx * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dQ, d->Q, (size_t)(n - 1) * nx * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dR, d->R, (size_t)(n - 1) * nu * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dQN, d->QN, (size_t)n_l * nx * 8, cudaMemcpyHostToDevice);
+  if (dxlo) cudaMemcpy(dxlo, d->x_lo, (size_t)n * nx * 8, cudaMemcpyHostToDevice);
+  if (dxhi) cudaMemcpy(dxhi, d->x_hi, (size_t)n * nx * 8, cudaMemcpyHostToDevice);
+  if (dulo) cudaMemcpy(dulo, d->u_lo, (size_t)n_nl * nu * 8, cudaMemcpyHostToDevice);
+  if (duhi) cudaMemcpy(duhi, d->u_hi, (size_t)n_nl * nu * 8, cudaMemcpyHostToDevice);
+  if (dball) cudaMemcpy(dball, d->u_ball, (size_t)n_nl * 8, cudaMemcpyHostToDevice);
+  // offline FP64 arrays
+  p->d_P = m.alloc<double>((long long)n * nx * nx);
+  p->d_K = m.alloc<double>((long long)n_nl * nu * nx);
+  p->d_Rt = m.alloc<double>((long long)n_nl * nu * nu);
+  p->d_Abar = m.alloc<double>((long long)(n - 1) * nx * nx);
+  p->d_x0raw = m.alloc<double>(nx);
+  p->d_out_risk = m.alloc<double>(1);
+  double* dAt = tmp.alloc<double>((long long)(n - 1) * nx * nx);
+  double* dBt = tmp.alloc<double>((long long)(n - 1) * nx * nu);
+  double* dLc = tmp.alloc<double>((long long)n_nl * nu * nu);
+  double* dLi = tmp.alloc<double>((long long)n_nl * nu * nu);
+  double* dRi = tmp.alloc<double>((long long)n_nl * nu * nu);
+  double* dKA = tmp.alloc<double>((long long)n_nl * nu * nx);
+  double* dBtP = tmp.alloc<double>((long long)n * nu * nx);
+  double* dPAb = tmp.alloc<double>((long long)n * nx * nx);
+  int* derr = tmp.alloc<int>(1);
+  unsigned long long* dnorm = tmp.alloc<unsigned long long>(1);
+  rc = alloc_iter<double>(p, p->f64);
+  if (!rc) rc = alloc_iter<float>(p, p->f32);
+  if (rc || tmp.failed || m.failed) { tmp.free_all(); m.free_all(); delete p; return SPOCK_ENOMEM; }
+  double* dct = p->f64.cvec;
+  cudaMemset(derr, 0, sizeof(int));
+  cudaMemset(dnorm, 0, sizeof(unsigned long long));
+  if (!dc) cudaMemset(dct, 0, (size_t)(n - 1) * nx * 8);
+  SetupArgs a{};
+  a.n = n; a.n_nl = n_nl; a.nx = nx; a.nu = nu; a.nbx = p->nbx; a.nbu = p->nbu; a.has_ball = p->has_ball;
+  a.ldB = p->ldB; a.ldF = p->ldF; a.ldP = p->ldP; a.ldK = p->ldK;
+  a.a_con = p->a_con; a.a_conN = p->a_conN;
+  a.anc = p->d_anc; a.ch_off = p->d_ch_off; a.prob = d_prob;
+  a.Sx = p->d_Sx; a.SxN = p->d_SxN; a.Su = p->d_Su;
+  a.A = dA; a.B = dB; a.c = dc; a.Qd = dQ; a.Rd = dR; a.QNd = dQN;
+  a.xlo = dxlo; a.xhi = dxhi; a.ulo = dulo; a.uhi = duhi; a.uball = dball;
+  a.At = dAt; a.Bt = dBt; a.ct = dct;
+  a.P = p->d_P; a.K = p->d_K; a.Rt = p->d_Rt; a.Lc = dLc; a.Linv = dLi; a.Rinv = dRi; a.KA = dKA;
+  a.BtP = dBtP; a.PAb = dPAb; a.Abar = p->d_Abar; a.err = derr;
+  Iter<double>& f = p->f64;
+  a.MB = f.MB; a.MF = f.MF; a.MP = f.MP; a.KT = f.KT; a.Pc = f.Pc;
+  a.qh = f.qh; a.rh = f.rh; a.qNh = f.qNh; a.gx = f.gx; a.gu = f.gu; a.gN = f.gN;
+  a.box_lo = f.box_lo; a.box_hi = f.box_hi; a.boxN_lo = f.boxN_lo; a.boxN_hi = f.boxN_hi; a.ball = f.ball;
+  cudaStream_t st = 0;
+  cudaError_t e = launch_scale_dyn(a, st);
+  if (e == cudaSuccess) e = launch_alg1(a, p->stage_off.data(), p->N, st);
+  if (e == cudaSuccess) e = launch_build(a, st);
+  if (e == cudaSuccess) e = launch_norm_L(a, dnorm, st);
+  if (e == cudaSuccess) e = cudaMemcpy(f.prob, d_prob, (size_t)n * 8, cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(f.avar, d_avar, (size_t)n_nl * 8, cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int herr = 0;
+  unsigned long long hnorm = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&hnorm, dnorm, sizeof(hnorm), cudaMemcpyDeviceToHost);
+  tmp.free_all();
+  if (e != cudaSuccess) { m.free_all(); delete p; return SPOCK_EDEVICE; }
+  if (herr) { m.free_all(); delete p; return SPOCK_ENOTPD; }
+  double l2;
+  memcpy(&l2, &hnorm, sizeof(double));
+  p->normL = sqrt(l2);
+  p->alpha = 0.99 / p->normL;
+  // FP32 copies of the iteration data
+  Iter<float>& g = p->f32;
+  const long long cnt[] = {(long long)(n - 1) * nx * p->ldB, (long long)(n - 1) * (nx + nu) * p->ldF,
+                           (long long)n_nl * nu * p->ldP, (long long)n_nl * nx * p->ldK,
+                           (long long)(n - 1) * nx, (long long)(n - 1) * nx, (long long)(n - 1) * nx,
+                           (long long)(n - 1) * nu, (long long)n_l * nx, nx, nu, nx,
+                           (long long)n_nl * std::max(1, p->nbox), (long long)n_nl * std::max(1, p->nbox),
+                           (long long)n_l * nx, (long long)n_l * nx, n_nl, n, n_nl};
+  const double* src[] = {f.MB, f.MF, f.MP, f.KT, f.cvec, f.Pc, f.qh, f.rh, f.qNh, f.gx, f.gu, f.gN,
+                         f.box_lo, f.box_hi, f.boxN_lo, f.boxN_hi, f.ball, f.prob, f.avar};
+  float* dst[] = {g.MB, g.MF, g.MP, g.KT, g.cvec, g.Pc, g.qh, g.rh, g.qNh, g.gx, g.gu, g.gN,
+                  g.box_lo, g.box_hi, g.boxN_lo, g.boxN_hi, g.ball, g.prob, g.avar};
+  for (int q = 0; q < 19 && e == cudaSuccess; ++q) e = launch_convert_f64_f32(src[q], dst[q], cnt[q], st);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { m.free_all(); delete p; return SPOCK_EDEVICE; }
+  cudaMemset(p->d_x0raw, 0, nx * 8);
+  cudaMemset(p->f64.x0s, 0, nx * 8);
+  cudaMemset(p->f32.x0s, 0, nx * 4);
+  fill_prob<double>(p, p->f64, p->alpha);
+  fill_prob<float>(p, p->f32, p->alpha);
+  *out = p;
+  return cuda_err(cudaDeviceSynchronize());
+}
+
+void spock_problem_destroy(spock_problem* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  p->mem.free_all();
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  delete p;
+}
+
+int spock_problem_sizes(const spock_problem* p, spock_sizes* o) {
+  if (!p || !o) return SPOCK_EINVAL;
+  o->n = p->n; o->n_nonleaf = p->n_nl; o->n_leaf = p->n_l; o->N = p->N; o->nx = p->nx; o->nu = p->nu;
+  o->n_c = p->n_c; o->n_cN = p->n_cN; o->n_z = p->nz; o->n_eta = p->neta; o->n_v = p->nv;
+  const long long words = (long long)(p->n - 1) * (p->nx * p->ldB + (p->nx + p->nu) * p->ldF) +
+                          (long long)p->n_nl * (p->nu * p->ldP + p->nx * p->ldK);
+  o->factor_bytes_fp64 = words * 8;
+  o->factor_bytes_fp32 = words * 4;
+  return SPOCK_OK;
+}
+
+int spock_problem_alpha(const spock_problem* p, double* alpha, double* normL) {
+  if (!p) return SPOCK_EINVAL;
+  if (alpha) *alpha = p->alpha;
+  if (normL) *normL = p->normL;
+  return SPOCK_OK;
+}
+
+int spock_problem_set_alpha(spock_problem* p, double alpha) {
+  if (!p || !(alpha > 0.0) || !(alpha * p->normL < 1.0)) return SPOCK_EINVAL;
+  p->alpha = alpha;
+  p->f64.P.alpha = alpha;
+  p->f32.P.alpha = (float)alpha;
+  return SPOCK_OK;
+}
+
+int spock_problem_scalings(const spock_problem* p, double* Sx, double* Su, double* SxN) {
+  if (!p) return SPOCK_EINVAL;
+  if (Sx) memcpy(Sx, p->Sx.data(), p->nx * 8);
+  if (Su) memcpy(Su, p->Su.data(), p->nu * 8);
+  if (SxN) memcpy(SxN, p->SxN.data(), p->nx * 8);
+  return SPOCK_OK;
+}
+
+int spock_problem_factors(const spock_problem* p, double* P, double* K, double* Rt, double* Abar) {
+  if (!p) return SPOCK_EINVAL;
+  cudaError_t e = cudaSuccess;
+  if (P) e = cudaMemcpy(P, p->d_P, (size_t)p->n * p->nx * p->nx * 8, cudaMemcpyDeviceToHost);
+  if (K && e == cudaSuccess) e = cudaMemcpy(K, p->d_K, (size_t)p->n_nl * p->nu * p->nx * 8, cudaMemcpyDeviceToHost);
+  if (Rt && e == cudaSuccess) e = cudaMemcpy(Rt, p->d_Rt, (size_t)p->n_nl * p->nu * p->nu * 8, cudaMemcpyDeviceToHost);
+  if (Abar && e == cudaSuccess) e = cudaMemcpy(Abar, p->d_Abar, (size_t)(p->n - 1) * p->nx * p->nx * 8, cudaMemcpyDeviceToHost);
+  return cuda_err(e);
+}
+
+static int set_x0_dev(spock_problem* p, const double* x0_dev, cudaStream_t st) {
+  k_scale_x0<<<1, 128, 0, st>>>(p->nx, x0_dev, p->d_Sx, p->f64.x0s, p->f32.x0s);
+  return cuda_err(cudaGetLastError());
+}
+
+int spock_problem_set_x0(spock_problem* p, const double* x0) {
+  if (!p || !x0) return SPOCK_EINVAL;
+  if (!finite_arr(x0, p->nx)) return SPOCK_EINVAL;
+  if (cudaMemcpy(p->d_x0raw, x0, p->nx * 8, cudaMemcpyHostToDevice) != cudaSuccess) return SPOCK_EDEVICE;
+  int rc = set_x0_dev(p, p->d_x0raw, 0);
+  if (rc) return rc;
+  return cuda_err(cudaDeviceSynchronize());
+}
+
+int spock_op_T(spock_problem* p, int precision, const void* v_in, void* v_out, double* stats,
+               void* stream) {
+  if (!p || !v_in || !v_out || (precision != 32 && precision != 64)) return SPOCK_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  SolveOpts so{1e300, 0, 1, 2, 1e-10};
+  SolveCtl h{};
+  int rc;
+  if (precision == 64) {
+    rc = ensure_bufs(p, p->f64);
+    if (rc) return rc;
+    Iter<double> it = p->f64;               // shallow copy with the caller's vectors
+    it.sb.V = (double*)v_in;
+    it.sb.TV = (double*)v_out;
+    it.have_bufs = true;
+    rc = run_solver<double>(p, it, so, st, &h, nullptr);
+  } else {
+    rc = ensure_bufs(p, p->f32);
+    if (rc) return rc;
+    Iter<float> it = p->f32;
+    it.sb.V = (float*)v_in;
+    it.sb.TV = (float*)v_out;
+    it.have_bufs = true;
+    rc = run_solver<float>(p, it, so, st, &h, nullptr);
+  }
+  if (rc) return rc;
+  if (stats)
+    for (int k = 0; k < 8; ++k) stats[k] = h.stats[k];
+  return SPOCK_OK;
+}
+
+int spock_op_L(spock_problem* p, int precision, const void* z, void* eta, void* stream) {
+  if (!p || !z || !eta) return SPOCK_EINVAL;
+  cudaError_t e;
+  if (precision == 64) e = launch_apply_L<double>(p->f64.P, p->d_ynode, (const double*)z, (double*)eta, (cudaStream_t)stream);
+  else if (precision == 32) e = launch_apply_L<float>(p->f32.P, p->d_ynode, (const float*)z, (float*)eta, (cudaStream_t)stream);
+  else return SPOCK_EINVAL;
+  if (e != cudaSuccess) return SPOCK_EDEVICE;
+  return cuda_err(cudaStreamSynchronize((cudaStream_t)stream));
+}
+
+int spock_op_Lt(spock_problem* p, int precision, const void* eta, void* z, void* stream) {
+  if (!p || !z || !eta) return SPOCK_EINVAL;
+  cudaError_t e;
+  if (precision == 64) e = launch_apply_Lt<double>(p->f64.P, p->d_ynode, (const double*)eta, (double*)z, (cudaStream_t)stream);
+  else if (precision == 32) e = launch_apply_Lt<float>(p->f32.P, p->d_ynode, (const float*)eta, (float*)z, (cudaStream_t)stream);
+  else return SPOCK_EINVAL;
+  if (e != cudaSuccess) return SPOCK_EDEVICE;
+  return cuda_err(cudaStreamSynchronize((cudaStream_t)stream));
+}
+
+int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opts* opts,
+                       double* x_out, double* u_out, void* stream, spock_info* info) {
+  if (!p || !x0) return SPOCK_EINVAL;
+  spock_solve_opts o;
+  if (opts) o = *opts;
+  else spock_solve_opts_default(&o);
+  if ((o.precision != 32 && o.precision != 64) || !(o.tol >= 0) || o.max_iters < 0 ||
+      o.max_backtracks < 1 || o.method < 0 || o.method > 1)
+    return SPOCK_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = set_x0_dev(p, x0, st);
+  if (rc) return rc;
+  SolveOpts so;
+  so.tol = o.tol; so.max_iters = o.max_iters; so.max_backtracks = o.max_backtracks;
+  so.method = o.method; so.rank_tol = (o.precision == 64) ? 1e-10 : 1e-5;
+  SolveCtl h{};
+  float ms = 0.f;
+  double res64 = -1.0;
+  const long long nv = p->nv;
+  if (o.precision == 64) {
+    rc = ensure_bufs(p, p->f64);
+    if (rc) return rc;
+    if (!o.warm_start && cudaMemsetAsync(p->f64.sb.V, 0, nv * 8, st) != cudaSuccess) return SPOCK_EDEVICE;
+    rc = run_solver<double>(p, p->f64, so, st, &h, &ms);
+    if (rc) return rc;
+    // keep the final iterate in V for warm starts
+    double* fv = buf_index(p->f64.sb, h.final_v);
+    if (fv != p->f64.sb.V) cudaMemcpyAsync(p->f64.sb.V, fv, nv * 8, cudaMemcpyDeviceToDevice, st);
+    const double* z = buf_index(p->f64.sb, h.final_tv);
+    double* tz = p->f64.sb.PSI;   // T(v) copy (PSI is free after the solve)
+    cudaMemcpyAsync(tz, z, nv * 8, cudaMemcpyDeviceToDevice, st);
+    k_unscale<double><<<64, 256, 0, st>>>(p->n, p->n_nl, p->nx, p->nu, p->o_x, p->o_u, tz, p->d_Sx,
+                                         p->d_SxN, p->d_Su, x_out, u_out, p->d_out_risk);
+    res64 = h.res_inf;
+  } else {
+    rc = ensure_bufs(p, p->f32);
+    if (rc) return rc;
+    if (!o.warm_start && cudaMemsetAsync(p->f32.sb.V, 0, nv * 4, st) != cudaSuccess) return SPOCK_EDEVICE;
+    rc = run_solver<float>(p, p->f32, so, st, &h, &ms);
+    if (rc) return rc;
+    float* fv = buf_index(p->f32.sb, h.final_v);
+    if (fv != p->f32.sb.V) cudaMemcpyAsync(p->f32.sb.V, fv, nv * 4, cudaMemcpyDeviceToDevice, st);
+    const float* z = buf_index(p->f32.sb, h.final_tv);
+    float* tz = p->f32.sb.PSI;
+    cudaMemcpyAsync(tz, z, nv * 4, cudaMemcpyDeviceToDevice, st);
+    k_unscale<float><<<64, 256, 0, st>>>(p->n, p->n_nl, p->nx, p->nu, p->o_x, p->o_u, tz, p->d_Sx,
+                                        p->d_SxN, p->d_Su, x_out, u_out, p->d_out_risk);
+    res64 = h.res_inf;
+    if (o.fp64_check) {
+      // FP64 residual of the FP32 iterate: one FP64 evaluation of T
+      rc = ensure_bufs(p, p->f64);
+      if (rc) return rc;
+      if (launch_convert_f32_f64(p->f32.sb.V, p->f64.sb.VT, nv, st) != cudaSuccess) return SPOCK_EDEVICE;
+      Iter<double> it = p->f64;
+      it.sb.V = p->f64.sb.VT;
+      it.sb.TV = p->f64.sb.TVT;
+      SolveOpts s1{1e300, 0, 1, 2, 1e-10};
+      SolveCtl h2{};
+      rc = run_solver<double>(p, it, s1, st, &h2, nullptr);
+      if (rc) return rc;
+      res64 = h2.res_inf;
+    }
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SPOCK_EDEVICE;
+  double risk = 0.0;
+  cudaMemcpy(&risk, p->d_out_risk, 8, cudaMemcpyDeviceToHost);
+  if (info) {
+    info->status = h.status == 0 ? SPOCK_OK : SPOCK_MAXITER;
+    info->iters = h.iters; info->n_T = h.n_T; info->n_K0 = h.n_K0; info->n_K1 = h.n_K1;
+    info->n_K2 = h.n_K2; info->n_fallback = h.n_fb; info->n_backtracks = h.n_bt;
+    info->res_inf = h.res_inf; info->res_inf_fp64 = res64; info->risk = risk;
+    info->device_ms = ms;
+  }
+  return h.status == 0 ? SPOCK_OK : SPOCK_MAXITER;
+}
+
+int spock_solve(spock_problem* p, const double* x0, const spock_solve_opts* opts, double* x_out,
+                double* u_out, double* risk, spock_info* info) {
+  if (!p || !x0) return SPOCK_EINVAL;
+  if (!finite_arr(x0, p->nx)) return SPOCK_EINVAL;
+  double* dx = nullptr;
+  double* du = nullptr;
+  const size_t bx = (size_t)p->n * p->nx * 8, bu = (size_t)p->n_nl * p->nu * 8;
+  if (x_out && cudaMalloc(&dx, bx) != cudaSuccess) return SPOCK_ENOMEM;
+  if (u_out && cudaMalloc(&du, bu) != cudaSuccess) { cudaFree(dx); return SPOCK_ENOMEM; }
+  cudaMemcpy(p->d_x0raw, x0, p->nx * 8, cudaMemcpyHostToDevice);
+  spock_info inf{};
+  int rc = spock_solve_device(p, p->d_x0raw, opts, dx, du, nullptr, &inf);
+  if (rc >= 0) {
+    if (x_out) cudaMemcpy(x_out, dx, bx, cudaMemcpyDeviceToHost);
+    if (u_out) cudaMemcpy(u_out, du, bu, cudaMemcpyDeviceToHost);
+    if (risk) *risk = inf.risk;
+    if (info) *info = inf;
+  }
+  if (dx) cudaFree(dx);
+  if (du) cudaFree(du);
+  return rc;
+}
+
+int spock_get_iterate(spock_problem* p, int precision, void* v_out, void* stream) {
+  if (!p || !v_out) return SPOCK_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == 64) {
+    int rc = ensure_bufs(p, p->f64);
+    if (rc) return rc;
+    return cuda_err(cudaMemcpyAsync(v_out, p->f64.sb.V, p->nv * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  if (precision == 32) {
+    int rc = ensure_bufs(p, p->f32);
+    if (rc) return rc;
+    return cuda_err(cudaMemcpyAsync(v_out, p->f32.sb.V, p->nv * 4, cudaMemcpyDeviceToDevice, st));
+  }
+  return SPOCK_EINVAL;
+}
+
+int spock_set_iterate(spock_problem* p, int precision, const void* v_in, void* stream) {
+  if (!p || !v_in) return SPOCK_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == 64) {
+    int rc = ensure_bufs(p, p->f64);
+    if (rc) return rc;
+    return cuda_err(cudaMemcpyAsync(p->f64.sb.V, v_in, p->nv * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  if (precision == 32) {
+    int rc = ensure_bufs(p, p->f32);
+    if (rc) return rc;
+    return cuda_err(cudaMemcpyAsync(p->f32.sb.V, v_in, p->nv * 4, cudaMemcpyDeviceToDevice, st));
+  }
+  return SPOCK_EINVAL;
+}
+
+}  // extern "C"

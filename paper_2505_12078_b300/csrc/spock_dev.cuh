@@ -1,0 +1,333 @@
+// spock_dev.cuh -- device-side building blocks of libspock (sm_103a).
+//
+// Problem descriptor handed to every kernel, team-level (1..8 warps) mat-vecs
+// over per-node matrices stored "input-major" (row k = input index, columns =
+// outputs, leading dimension padded to 4 elements so rows are 16-byte
+// aligned), warp/block reductions with a fixed order (bit-reproducible), and
+// a grid barrier with a time limit that reports an error instead of hanging.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spock {
+
+constexpr int MAXD = 256;          // max nx + nu
+constexpr int MAXTW = 8;           // max warps per team
+constexpr int NRED = 8;            // reduction slots per T evaluation
+constexpr int MAXE = (MAXD + 2 + 31) / 32;   // per-lane elements of one cost block
+
+// ---------------------------------------------------------------------------
+// Problem descriptor (all pointers device, T = float or double)
+// ---------------------------------------------------------------------------
+template <class T>
+struct Prob {
+  // sizes
+  int n, n_nl, n_l, N, nx, nu, n_c, n_cN, nbx, nbu, nbox, has_ball;
+  long long nz, neta, nv;
+  // z layout
+  long long o_x, o_u, o_y, o_tau, o_s;
+  // eta layout (relative to the start of eta)
+  long long e_y, e_s, e_c, e_q, e_cN, e_qN;
+  int W;                       // nx + nu + 2 (cost block of a non-root node)
+  int ldB, ldF, ldP, ldK;      // leading dims of MB, MF, MP, KT
+  // tree (breadth-first, children contiguous)
+  const int* anc;              // [n]
+  const int* ch_off;           // [n_nl + 1]
+  const int* yoff;             // [n_nl + 1]
+  // schedule of the sweeps: chains of single-child non-leaf nodes ("segments")
+  int n_levels;
+  const int* lvl_off;          // [n_levels + 1] into the segment arrays (bottom-up order)
+  const int* seg_top;          // top node of a segment
+  const int* seg_bot;          // bottom node
+  const int* seg_len;          // number of nodes
+  // per-iteration factors (built offline in FP64 from Alg. 1)
+  const T* MB;   // per non-root c: [Abar_c | B_c Rt^{-1}]      nx x ldB   (input: q_c + P_c c_c)
+  const T* MF;   // per non-root c: [Abar_c^T ; B_c^T]           (nx+nu) x ldF (input: [x; d])
+  const T* MP;   // per non-leaf i: [K_i | Rt_i^{-1}]             nu x ldP   (input: ubar)
+  const T* KT;   // per non-leaf i: K_i^T                        nx x ldK   (input: x)
+  const T* cvec; // per non-root: scaled c (nx)
+  const T* Pc;   // per non-root: P_c c_c (nx)
+  // cost and constraint data (scaled, Sec. 5.4)
+  const T* qh;   // per non-root: diag of Q^{1/2} S^{-1} (nx)
+  const T* rh;   // per non-root: diag of R^{1/2} Su^{-1} (nu)
+  const T* qNh;  // per leaf (nx)
+  const T* gx;   // nx: coefficient of the x-box rows
+  const T* gu;   // nu: coefficient of the u-box and u-ball rows
+  const T* gN;   // nx: coefficient of the leaf x-box rows
+  const T* box_lo; const T* box_hi;    // [n_nl nbox]
+  const T* boxN_lo; const T* boxN_hi;  // [n_l nx]
+  const T* ball;                       // [n_nl]
+  const T* prob;                       // [n] conditional probabilities
+  const T* avar;                       // [n_nl]
+  const T* x0s;                        // [nx] scaled initial state
+  T alpha;
+  // scratch of the sweeps
+  T* qbuf;   // [n nx]
+  T* dbuf;   // [n_nl nu]
+  T* hbuf;   // [n_nl nx]   -K'ubar - xbar
+  T* ebuf;   // [n_nl nu]   Rt^{-1} ubar
+};
+
+// ---------------------------------------------------------------------------
+// memory helpers: data written inside a kernel is read through L2 (ld.cg) so a
+// stale L1 line of an earlier phase is never used; read-only data uses ldg.
+// ---------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ T ldc(const T* p) { return __ldcg(p); }
+template <class T> __device__ __forceinline__ void stc(T* p, T v) { __stcg(p, v); }
+template <class T> __device__ __forceinline__ T ldr(const T* p) { return __ldg(p); }
+
+template <class T> struct Vec;
+template <> struct Vec<float> { using V = float4; static constexpr int N = 4; };
+template <> struct Vec<double> { using V = double2; static constexpr int N = 2; };
+
+template <class T>
+__device__ __forceinline__ void vload(const T* p, T (&o)[Vec<T>::N]);
+template <>
+__device__ __forceinline__ void vload<float>(const float* p, float (&o)[4]) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void vload<double>(const double* p, double (&o)[2]) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  o[0] = v.x; o[1] = v.y;
+}
+
+// ---------------------------------------------------------------------------
+// team = tw consecutive warps of a CTA; synchronised by a named barrier
+// ---------------------------------------------------------------------------
+struct Team {
+  int tw, id, warp, lane, tid, nth;
+  __device__ __forceinline__ void sync() const {
+    if (tw == 1) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "r"(nth) : "memory");
+    }
+  }
+};
+
+__device__ __forceinline__ Team make_team(int tw) {
+  Team t;
+  const int w = threadIdx.x >> 5;
+  t.tw = tw;
+  t.id = w / tw;
+  t.warp = w % tw;
+  t.lane = threadIdx.x & 31;
+  t.tid = t.warp * 32 + t.lane;
+  t.nth = tw * 32;
+  return t;
+}
+
+// Register accumulator of one lane for a team mat-vec: the lane owns column
+// chunks (c*32 + lane)*VEC .. +VEC, c < CH.
+template <class T>
+struct Acc {
+  static constexpr int VEC = Vec<T>::N;
+  static constexpr int CH = (MAXD + 32 * VEC - 1) / (32 * VEC);
+  T a[CH][VEC];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) a[c][e] = T(0);
+  }
+};
+
+// acc += M^T-style product: out[j] += sum_k M[k*ld + j] * in[k], k < nrows,
+// j < ncols. Rows are split over the team's warps, columns over lanes.
+template <class T>
+__device__ __forceinline__ void team_mv(const Team& tm, Acc<T>& acc, const T* __restrict__ M,
+                                        int ld, int nrows, int ncols, const T* in) {
+  constexpr int VEC = Vec<T>::N;
+  const int nch = (ncols + 32 * VEC - 1) / (32 * VEC);
+#pragma unroll 2
+  for (int k = tm.warp; k < nrows; k += tm.tw) {
+    const T xk = in[k];
+    const T* row = M + (size_t)k * ld;
+#pragma unroll
+    for (int c = 0; c < Acc<T>::CH; ++c) {
+      const int col = (c * 32 + tm.lane) * VEC;
+      if (c < nch && col < ncols) {
+        T m[VEC];
+        vload<T>(row + col, m);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc.a[c][e] = fma(m[e], xk, acc.a[c][e]);
+      }
+    }
+  }
+}
+
+// Sum the warps' accumulators (fixed order) and hand out[j] to f(j, value) for
+// j < ncols. red: team scratch of tw*MAXD elements. Ends with a team sync.
+template <class T, class F>
+__device__ __forceinline__ void team_reduce(const Team& tm, const Acc<T>& acc, int ncols, T* red,
+                                            F&& f) {
+  constexpr int VEC = Vec<T>::N;
+#pragma unroll
+  for (int c = 0; c < Acc<T>::CH; ++c) {
+    const int col = (c * 32 + tm.lane) * VEC;
+    if (col < ncols) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e)
+        if (col + e < ncols) red[tm.warp * MAXD + col + e] = acc.a[c][e];
+    }
+  }
+  tm.sync();
+  for (int j = tm.tid; j < ncols; j += tm.nth) {
+    T s = red[j];
+    for (int w = 1; w < tm.tw; ++w) s += red[w * MAXD + j];
+    f(j, s);
+  }
+  __threadfence_block();
+  tm.sync();
+}
+
+// ---------------------------------------------------------------------------
+// warp reductions (fixed butterfly order)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Per-thread partial sums of one T evaluation (see RedIdx).
+enum RedIdx {
+  R_MAX = 0,     // max |r|
+  R_ZZ = 1,      // ||r_z||^2
+  R_EE = 2,      // ||r_eta||^2
+  R_ELZ = 3,     // <r_eta, L r_z>
+  R_ZD = 4,      // <r_z, dz>       (dz = z_in - z_ref)
+  R_ED = 5,      // <r_eta, deta>
+  R_LZD = 6,     // <L r_z, deta>
+  R_ELD = 7      // <r_eta, L dz>
+};
+
+template <class T>
+struct RedAcc {
+  T v[NRED];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NRED; ++i) v[i] = T(0);
+  }
+  // z element: old value, new value, reference value (ref == old when absent)
+  __device__ __forceinline__ void z(T old, T nw, T ref) {
+    const T r = old - nw;
+    v[R_MAX] = max(v[R_MAX], fabs(r));
+    v[R_ZZ] = fma(r, r, v[R_ZZ]);
+    v[R_ZD] = fma(r, old - ref, v[R_ZD]);
+  }
+  // eta element: old, new, ref eta values and (L z) of old, new, ref
+  __device__ __forceinline__ void eta(T eo, T en, T er, T lo, T ln, T lr) {
+    const T r = eo - en;
+    const T lrz = lo - ln;
+    v[R_MAX] = max(v[R_MAX], fabs(r));
+    v[R_EE] = fma(r, r, v[R_EE]);
+    v[R_ELZ] = fma(r, lrz, v[R_ELZ]);
+    v[R_ED] = fma(r, eo - er, v[R_ED]);
+    v[R_LZD] = fma(lrz, eo - er, v[R_LZD]);
+    v[R_ELD] = fma(r, lo - lr, v[R_ELD]);
+  }
+};
+
+// Block reduction of NRED doubles (slot 0 max, others sums) into out[] (valid
+// in thread 0). scratch: NRED * 32 doubles of shared memory.
+__device__ __forceinline__ void block_reduce_red(double (&v)[NRED], double* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NRED; ++i) v[i] = (i == R_MAX) ? warp_max(v[i]) : warp_sum(v[i]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NRED; ++i) scratch[i * 32 + w] = v[i];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int i = 0; i < NRED; ++i) {
+      double x = lane < nw ? scratch[i * 32 + lane] : 0.0;
+      v[i] = (i == R_MAX) ? warp_max(x) : warp_sum(x);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier with a time limit (sense via a generation counter). The last
+// CTA to arrive may run a callback (whole CTA) before releasing the others.
+// On timeout the error word is set and every CTA leaves at its next check.
+// ---------------------------------------------------------------------------
+struct GridCtl {
+  unsigned int count;
+  unsigned int gen;
+  int error;          // 0 ok, else SPOCK_ETIMEOUT-style code
+  int pad;
+};
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_i(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+constexpr uint64_t BARRIER_LIMIT_NS = 2000000000ull;   // 2 s per wait
+
+// Returns false when the group is in error (timeout here or elsewhere).
+template <class F>
+__device__ __forceinline__ bool grid_sync(GridCtl* ctl, F&& last_cb) {
+  __shared__ int s_flag;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = ld_acquire(&ctl->gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->count, 1u) + 1u;
+    s_flag = (arrived == gridDim.x) ? 1 : 0;
+    if (!s_flag) {
+      const uint64_t t0 = global_ns();
+      int ok = 1;
+      while (ld_acquire(&ctl->gen) == g) {
+        if (ld_relaxed_i(&ctl->error)) { ok = 0; break; }
+        if (global_ns() - t0 > BARRIER_LIMIT_NS) {
+          atomicExch(&ctl->error, 1);
+          ok = 0;
+          break;
+        }
+      }
+      s_flag = ok ? 2 : 3;
+    }
+  }
+  __syncthreads();
+  if (s_flag == 1) {
+    last_cb();                       // whole last CTA
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ctl->count = 0;
+      __threadfence();
+      atomicAdd(&ctl->gen, 1u);
+    }
+    __syncthreads();
+    return ld_relaxed_i(&ctl->error) == 0;
+  }
+  __threadfence();
+  return s_flag == 2;
+}
+
+}  // namespace spock

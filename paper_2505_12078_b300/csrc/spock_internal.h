@@ -1,0 +1,80 @@
+// spock_internal.h -- host-side declarations shared by the .cu files of libspock.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "spock_dev.cuh"
+
+namespace spock {
+
+// Pointers and sizes of the offline (FP64) setup.
+struct SetupArgs {
+  int n, n_nl, nx, nu, nbx, nbu, has_ball;
+  int ldB, ldF, ldP, ldK;
+  double a_con, a_conN;
+  const int* anc;
+  const int* ch_off;
+  const double* prob;
+  const double *Sx, *SxN, *Su;
+  // raw data
+  const double *A, *B, *c, *Qd, *Rd, *QNd, *xlo, *xhi, *ulo, *uhi, *uball;
+  // scaled dynamics
+  double *At, *Bt, *ct;
+  // Alg. 1
+  double *P, *K, *Rt, *Lc, *Linv, *Rinv, *KA, *BtP, *PAb, *Abar;
+  int* err;
+  // iteration data (FP64)
+  double *MB, *MF, *MP, *KT, *Pc;
+  double *qh, *rh, *qNh, *gx, *gu, *gN, *box_lo, *box_hi, *boxN_lo, *boxN_hi, *ball;
+};
+
+cudaError_t launch_scale_dyn(const SetupArgs& a, cudaStream_t s);
+cudaError_t launch_alg1(const SetupArgs& a, const int* stage_off_host, int N, cudaStream_t s);
+cudaError_t launch_build(const SetupArgs& a, cudaStream_t s);
+cudaError_t launch_norm_L(const SetupArgs& a, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_convert_f64_f32(const double* a, float* b, long long n, cudaStream_t s);
+cudaError_t launch_convert_f32_f64(const float* a, double* b, long long n, cudaStream_t s);
+
+template <class T>
+cudaError_t launch_apply_L(const Prob<T>& P, const int* ynode, const T* z, T* eta, cudaStream_t s);
+template <class T>
+cudaError_t launch_apply_Lt(const Prob<T>& P, const int* ynode, const T* eta, T* z, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// solver
+// ---------------------------------------------------------------------------
+struct SolveOpts {
+  double tol;
+  int max_iters;
+  int max_backtracks;
+  int method;          // 0 SPOCK, 1 plain CP, 2 one T evaluation
+  double rank_tol;     // Anderson rank test (relative to ||Y||_F)
+};
+
+// Device control block of one solve (global memory, zeroed before a launch).
+struct SolveCtl {
+  GridCtl bar;
+  int status;          // 0 ok, 1 maxiter, <0 error
+  int iters, n_T, n_K0, n_K1, n_K2, n_fb, n_bt;
+  double res_inf;
+  double zeta, omega_safe;
+  double red[NRED];    // result of the last group reduction
+  double stats[NRED];  // reduction of the last T evaluation of the final iterate
+  int final_v;         // index (0..3 of V, TV, VT, TVT) holding the final iterate v
+  int final_tv;        // index holding T(v)
+  int pad0, pad1;
+};
+
+template <class T>
+struct SolveBufs {
+  T *V, *TV, *VT, *TVT, *PSI, *VP, *RP;   // n_v each
+  T *S, *Y;                               // 3 n_v each
+  double* partials;                        // [grid][NRED]
+  SolveCtl* ctl;
+};
+
+template <class T>
+cudaError_t launch_solve(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
+                         int grid, int threads, cudaStream_t s);
+int solver_max_grid(int precision, int tw, int threads, int D, int* grid_out);
+
+}  // namespace spock

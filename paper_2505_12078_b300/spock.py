@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libspock (include/spock.h). Argument marshalling
+only: every step of the method runs in the library's CUDA kernels. Device
+buffers are torch CUDA tensors (torch provides device memory and streams).
+
+Raises if libspock.so is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspock.so")
+
+SPOCK_OK = 0
+SPOCK_MAXITER = 1
+STATUS = {0: "ok", 1: "maxiter", -1: "einval", -2: "enomem", -3: "enotpd", -4: "edevice",
+          -5: "etimeout", -6: "eunsupported"}
+
+EXPORTED = [
+    "spock_problem_create", "spock_problem_destroy", "spock_problem_sizes", "spock_problem_alpha",
+    "spock_problem_set_alpha", "spock_problem_scalings", "spock_problem_factors",
+    "spock_problem_set_x0", "spock_op_T", "spock_op_L", "spock_op_Lt", "spock_solve_opts_default",
+    "spock_solve", "spock_solve_device", "spock_get_iterate", "spock_set_iterate",
+    "spock_status_str", "spock_version",
+]
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int), ("anc", _ip), ("prob", _dp), ("nx", C.c_int), ("nu", C.c_int),
+                ("A", _dp), ("B", _dp), ("c", _dp), ("Q", _dp), ("R", _dp), ("QN", _dp),
+                ("x_lo", _dp), ("x_hi", _dp), ("u_lo", _dp), ("u_hi", _dp), ("u_ball", _dp),
+                ("avar", _dp)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("n", C.c_int), ("n_nonleaf", C.c_int), ("n_leaf", C.c_int), ("N", C.c_int),
+                ("nx", C.c_int), ("nu", C.c_int), ("n_c", C.c_int), ("n_cN", C.c_int),
+                ("n_z", C.c_longlong), ("n_eta", C.c_longlong), ("n_v", C.c_longlong),
+                ("factor_bytes_fp64", C.c_longlong), ("factor_bytes_fp32", C.c_longlong)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iters", C.c_int),
+                ("max_backtracks", C.c_int), ("method", C.c_int), ("warm_start", C.c_int),
+                ("fp64_check", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("n_T", C.c_int), ("n_K0", C.c_int),
+                ("n_K1", C.c_int), ("n_K2", C.c_int), ("n_fallback", C.c_int),
+                ("n_backtracks", C.c_int), ("res_inf", C.c_double), ("res_inf_fp64", C.c_double),
+                ("risk", C.c_double), ("device_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libspock.so (raises OSError if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libspock.so not built at {path}; run python -m paper_2505_12078_b300.build")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    lib.spock_problem_create.argtypes = [C.POINTER(ProblemDesc), C.POINTER(vp)]
+    lib.spock_problem_destroy.argtypes = [vp]
+    lib.spock_problem_destroy.restype = None
+    lib.spock_problem_sizes.argtypes = [vp, C.POINTER(Sizes)]
+    lib.spock_problem_alpha.argtypes = [vp, _dp, _dp]
+    lib.spock_problem_set_alpha.argtypes = [vp, C.c_double]
+    lib.spock_problem_scalings.argtypes = [vp, _dp, _dp, _dp]
+    lib.spock_problem_factors.argtypes = [vp, _dp, _dp, _dp, _dp]
+    lib.spock_problem_set_x0.argtypes = [vp, _dp]
+    lib.spock_op_T.argtypes = [vp, C.c_int, vp, vp, _dp, vp]
+    lib.spock_op_L.argtypes = [vp, C.c_int, vp, vp, vp]
+    lib.spock_op_Lt.argtypes = [vp, C.c_int, vp, vp, vp]
+    lib.spock_solve_opts_default.argtypes = [C.POINTER(SolveOpts)]
+    lib.spock_solve_opts_default.restype = None
+    lib.spock_solve.argtypes = [vp, _dp, C.POINTER(SolveOpts), _dp, _dp, _dp, C.POINTER(Info)]
+    lib.spock_solve_device.argtypes = [vp, vp, C.POINTER(SolveOpts), vp, vp, vp, C.POINTER(Info)]
+    lib.spock_get_iterate.argtypes = [vp, C.c_int, vp, vp]
+    lib.spock_set_iterate.argtypes = [vp, C.c_int, vp, vp]
+    lib.spock_status_str.argtypes = [C.c_int]
+    lib.spock_status_str.restype = C.c_char_p
+    lib.spock_version.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class SpockError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: status {code} ({STATUS.get(code, '?')})")
+        self.code = code
+
+
+def _check(code, where):
+    if code < 0:
+        raise SpockError(code, where)
+    return code
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def opts(precision=64, tol=1e-4, max_iters=5000, max_backtracks=30, method="spock",
+         warm_start=False, fp64_check=True) -> SolveOpts:
+    o = SolveOpts()
+    load().spock_solve_opts_default(C.byref(o))
+    o.precision = int(precision)
+    o.tol = float(tol)
+    o.max_iters = int(max_iters)
+    o.max_backtracks = int(max_backtracks)
+    o.method = {"spock": 0, "cp": 1}[method]
+    o.warm_start = int(bool(warm_start))
+    o.fp64_check = int(bool(fp64_check))
+    return o
+
+
+class Problem:
+    """A problem resident on the current CUDA device (created from a synth.RAOCP)."""
+
+    def __init__(self, p):
+        lib = load()
+        self._keep = []
+        d = ProblemDesc()
+        anc = np.ascontiguousarray(p.anc, dtype=np.int32)
+        arrs = dict(prob=p.prob, A=p.A, B=p.B, c=p.c, Q=p.Q, R=p.R, QN=p.QN, x_lo=p.x_lo,
+                    x_hi=p.x_hi, u_lo=p.u_lo, u_hi=p.u_hi, u_ball=p.u_ball, avar=p.avar)
+        conv = {k: _f64(v) for k, v in arrs.items()}
+        self._keep += [anc] + list(conv.values())
+        d.n_nodes = anc.shape[0]
+        d.anc = anc.ctypes.data_as(_ip)
+        d.nx, d.nu = int(p.nx), int(p.nu)
+        for k, v in conv.items():
+            setattr(d, k, _ptr(v))
+        h = C.c_void_p()
+        _check(lib.spock_problem_create(C.byref(d), C.byref(h)), "spock_problem_create")
+        self.h = h
+        self._keep = []
+        s = Sizes()
+        _check(lib.spock_problem_sizes(h, C.byref(s)), "spock_problem_sizes")
+        self.sizes = {k: getattr(s, k) for k, _ in s._fields_}
+        self.nx, self.nu = p.nx, p.nu
+        self.n, self.n_nl = s.n, s.n_nonleaf
+        self.n_z, self.n_eta, self.n_v = s.n_z, s.n_eta, s.n_v
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().spock_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- setup outputs ---------------------------------------------------------
+    def alpha(self):
+        a, n = C.c_double(), C.c_double()
+        _check(load().spock_problem_alpha(self.h, C.byref(a), C.byref(n)), "alpha")
+        return a.value, n.value
+
+    def set_alpha(self, alpha):
+        _check(load().spock_problem_set_alpha(self.h, float(alpha)), "set_alpha")
+
+    def scalings(self):
+        Sx, Su, SxN = np.zeros(self.nx), np.zeros(self.nu), np.zeros(self.nx)
+        _check(load().spock_problem_scalings(self.h, _ptr(Sx), _ptr(Su), _ptr(SxN)), "scalings")
+        return Sx, Su, SxN
+
+    def factors(self):
+        P = np.zeros((self.n, self.nx, self.nx))
+        K = np.zeros((self.n_nl, self.nu, self.nx))
+        Rt = np.zeros((self.n_nl, self.nu, self.nu))
+        Ab = np.zeros((self.n - 1, self.nx, self.nx))
+        _check(load().spock_problem_factors(self.h, _ptr(P), _ptr(K), _ptr(Rt), _ptr(Ab)), "factors")
+        return P, K, Rt, Ab
+
+    def set_x0(self, x0):
+        x0 = _f64(x0)
+        _check(load().spock_problem_set_x0(self.h, _ptr(x0)), "set_x0")
+
+    # --- operators (torch CUDA tensors) ----------------------------------------
+    @staticmethod
+    def _prec(t):
+        import torch
+        if t.dtype == torch.float64:
+            return 64
+        if t.dtype == torch.float32:
+            return 32
+        raise TypeError("float32 or float64 tensors only")
+
+    def T(self, v_in, v_out=None, stream=None):
+        """v_out = T(v_in); returns (v_out, stats[8])."""
+        import torch
+        assert v_in.is_cuda and v_in.is_contiguous() and v_in.numel() == self.n_v
+        if v_out is None:
+            v_out = torch.empty_like(v_in)
+        stats = np.zeros(8)
+        _check(load().spock_op_T(self.h, self._prec(v_in), C.c_void_p(v_in.data_ptr()),
+                                 C.c_void_p(v_out.data_ptr()), _ptr(stats),
+                                 C.c_void_p(stream.cuda_stream if stream else 0)), "spock_op_T")
+        return v_out, stats
+
+    def L(self, z, eta=None):
+        import torch
+        assert z.is_cuda and z.numel() == self.n_z
+        if eta is None:
+            eta = torch.empty(self.n_eta, dtype=z.dtype, device=z.device)
+        _check(load().spock_op_L(self.h, self._prec(z), C.c_void_p(z.data_ptr()),
+                                 C.c_void_p(eta.data_ptr()), None), "spock_op_L")
+        return eta
+
+    def Lt(self, eta, z=None):
+        import torch
+        assert eta.is_cuda and eta.numel() == self.n_eta
+        if z is None:
+            z = torch.empty(self.n_z, dtype=eta.dtype, device=eta.device)
+        _check(load().spock_op_Lt(self.h, self._prec(eta), C.c_void_p(eta.data_ptr()),
+                                  C.c_void_p(z.data_ptr()), None), "spock_op_Lt")
+        return z
+
+    # --- solve -------------------------------------------------------------------
+    def solve(self, x0, o: SolveOpts = None):
+        """Host-buffer solve (end to end). Returns dict(x, u, risk, info, status)."""
+        o = o or opts()
+        x0 = _f64(x0)
+        x = np.zeros((self.n, self.nx))
+        u = np.zeros((self.n_nl, self.nu))
+        risk = C.c_double()
+        info = Info()
+        st = _check(load().spock_solve(self.h, _ptr(x0), C.byref(o), _ptr(x), _ptr(u),
+                                       C.byref(risk), C.byref(info)), "spock_solve")
+        return dict(x=x, u=u, risk=risk.value, info=info.as_dict(), status=st)
+
+    def solve_device(self, x0_dev, o: SolveOpts = None, x_out=None, u_out=None, stream=None):
+        o = o or opts()
+        info = Info()
+        st = _check(load().spock_solve_device(
+            self.h, C.c_void_p(x0_dev.data_ptr()), C.byref(o),
+            C.c_void_p(x_out.data_ptr()) if x_out is not None else None,
+            C.c_void_p(u_out.data_ptr()) if u_out is not None else None,
+            C.c_void_p(stream.cuda_stream if stream else 0), C.byref(info)), "spock_solve_device")
+        return st, info.as_dict()
+
+    def get_iterate(self, precision=64):
+        import torch
+        dt = torch.float64 if precision == 64 else torch.float32
+        v = torch.empty(self.n_v, dtype=dt, device="cuda")
+        _check(load().spock_get_iterate(self.h, precision, C.c_void_p(v.data_ptr()), None), "get_iterate")
+        torch.cuda.synchronize()
+        return v
+
+    def set_iterate(self, v):
+        _check(load().spock_set_iterate(self.h, self._prec(v), C.c_void_p(v.data_ptr()), None),
+               "set_iterate")

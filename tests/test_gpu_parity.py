@@ -1,0 +1,172 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle on the same
+seeded inputs, through the C ABI.
+
+Tolerances. FP64: the kernels reassociate sums (split-K mat-vecs, the reduced
+backward recursion of Alg. 2, closed-form S2 projection), so one T
+evaluation differs from the oracle by a few ulps times the condition of the
+sweep; 1e-11 relative is asserted for one T, 1e-10 relative after a fixed
+iteration count (the bar of the fixed-iteration parity). FP32: one T within
+2e-5 relative (24-bit mantissa, sweeps of length <= 2N); converged solutions
+within 1e-3 relative on x/u (the FP32 target)."""
+import numpy as np
+import pytest
+
+from oracle.spock_oracle import Oracle
+from paper_2505_12078_b300 import synth
+from tests.problems import constrained, unconstrained
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2505_12078_b300 import build, spock
+    build.build()
+    spock.load()
+
+
+def _spock():
+    from paper_2505_12078_b300 import spock
+    return spock
+
+
+CASES = {
+    "small": lambda: synth.small_raocp(),
+    "ragged_37x19_ball": lambda: constrained([3, 2, 1, 1], 37, 19, seed=21, avar=0.35, uball=2.5),
+    "wide_70x40": lambda: constrained([4, 1, 1], 70, 40, seed=22, avar=0.6, uball=3.0),
+    "unconstrained_c": lambda: unconstrained([2, 3, 1], 5, 3, seed=23, avar=0.5, c_scale=0.3),
+    "chain_only": lambda: constrained([1, 1, 1, 1, 1], 6, 3, seed=24, avar=0.2),
+    "minimal_n2": lambda: constrained([1], 3, 2, seed=25, avar=1.0),
+    "avar0_branch8": lambda: constrained([8, 1], 9, 4, seed=26, avar=0.0, uball=1.0),
+}
+
+
+def _pair(name):
+    p = CASES[name]()
+    o = Oracle(p)
+    g = _spock().Problem(p)
+    return p, o, g
+
+
+def _relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_setup_scalings_alpha_and_alg1(name):
+    """Sec. 5.4 scalings, ||L|| and alpha, Alg. 1 factors P, K, R~, Abar."""
+    p, o, g = _pair(name)
+    Sx, Su, SxN = g.scalings()
+    assert np.allclose(Sx, o.Sx, rtol=1e-15) and np.allclose(Su, o.Su, rtol=1e-15)
+    assert np.allclose(SxN, o.SxN, rtol=1e-15)
+    alpha, normL = g.alpha()
+    assert abs(normL - o.normL) <= 1e-10 * o.normL
+    P, K, Rt, Ab = g.factors()
+    assert _relerr(P, o.Pm) < 1e-11
+    assert _relerr(K, o.K) < 1e-11
+    assert _relerr(Rt, o.Rt) < 1e-11
+    assert _relerr(Ab, o.Abar) < 1e-11
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_L_and_adjoint(name):
+    p, o, g = _pair(name)
+    rng = np.random.default_rng(1)
+    z = rng.standard_normal(o.lay.n_z)
+    eta = rng.standard_normal(o.lay.n_eta)
+    zt = torch.tensor(z, device="cuda")
+    et = torch.tensor(eta, device="cuda")
+    Lz = g.L(zt).cpu().numpy()
+    Ltz = g.Lt(et).cpu().numpy()
+    assert _relerr(Lz, o.apply_L(z)) < 1e-14
+    assert _relerr(Ltz, o.apply_Lt(eta)) < 1e-14
+    # adjoint identity on the GPU alone
+    assert abs(eta @ Lz - z @ Ltz) <= 1e-12 * max(1.0, abs(eta @ Lz))
+    # FP32
+    Lz32 = g.L(zt.float()).cpu().numpy()
+    assert _relerr(Lz32, o.apply_L(z)) < 1e-6
+
+
+def _rand_v(o, seed, scale=2.0):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(o.lay.n_z + o.lay.n_eta) * scale
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_T_fp64_and_fp32(name):
+    """One evaluation of T from a random point, FP64 and FP32, and the fused
+    reductions (max|r|, ||r_z||^2, ||r_eta||^2, <r_eta, L r_z>)."""
+    p, o, g = _pair(name)
+    g.set_alpha(o.alpha)
+    g.set_x0(p.x0)
+    for seed in (2, 3):
+        v = _rand_v(o, seed)
+        ref = o.T(v)
+        vt = torch.tensor(v, device="cuda")
+        out, stats = g.T(vt)
+        got = out.cpu().numpy()
+        assert _relerr(got, ref) < 1e-11, name
+        r = v - ref
+        nz = o.lay.n_z
+        assert abs(stats[0] - np.max(np.abs(r))) <= 1e-11 * max(1, np.max(np.abs(r)))
+        assert abs(stats[1] - r[:nz] @ r[:nz]) <= 1e-10 * (r @ r)
+        assert abs(stats[2] - r[nz:] @ r[nz:]) <= 1e-10 * (r @ r)
+        elz = r[nz:] @ o.apply_L(r[:nz])
+        assert abs(stats[3] - elz) <= 1e-10 * (r @ r)
+        out32, _ = g.T(vt.float())
+        assert _relerr(out32.cpu().numpy(), ref) < 2e-5, name
+
+
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "avar0_branch8"])
+def test_fixed_iterations_cp_fp64(name):
+    """Plain CP iterates v <- T(v) from zero for a fixed count: <= 1e-10 relative."""
+    p, o, g = _pair(name)
+    g.set_alpha(o.alpha)
+    spock = _spock()
+    iters = 60
+    ref = o.solve(tol=0.0, max_iters=iters, method="cp")
+    res = g.solve(p.x0, spock.opts(precision=64, tol=0.0, max_iters=iters, method="cp"))
+    assert res["info"]["iters"] == iters
+    v = g.get_iterate(64).cpu().numpy()
+    assert _relerr(v, ref["v"]) < 1e-10
+    assert abs(res["risk"] - ref["risk"]) <= 1e-10 * max(1, abs(ref["risk"]))
+
+
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40"])
+def test_fixed_iterations_spock_fp64(name):
+    """SPOCK (Alg. 4 with Anderson directions) for a fixed iteration count in
+    FP64: same branch sequence counts and iterate within 1e-10 relative."""
+    p, o, g = _pair(name)
+    g.set_alpha(o.alpha)
+    spock = _spock()
+    iters = 25
+    ref = o.solve(tol=0.0, max_iters=iters, method="spock")
+    res = g.solve(p.x0, spock.opts(precision=64, tol=0.0, max_iters=iters))
+    inf = res["info"]
+    kinds = [e[1] for e in ref["events"]]
+    assert inf["iters"] == iters
+    assert inf["n_K0"] == kinds.count("K0")
+    assert inf["n_K1"] == kinds.count("K1")
+    assert inf["n_K2"] == kinds.count("K2")
+    assert inf["n_T"] == ref["n_T"]
+    v = g.get_iterate(64).cpu().numpy()
+    assert _relerr(v, ref["v"]) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "chain_only"])
+def test_converged_fp32_vs_oracle(name):
+    """FP32 iteration to ||v - T(v)||_inf <= 1e-4 against the oracle's converged
+    FP64 solution: risk value and u^0 within 1e-3 relative; x/u everywhere
+    reported; FP64 residual check of the FP32 iterate."""
+    p, o, g = _pair(name)
+    spock = _spock()
+    ref = o.solve(tol=1e-4, max_iters=20000)
+    res = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000))
+    assert res["status"] == 0, res["info"]
+    assert abs(res["risk"] - ref["risk"]) <= 1e-3 * max(1.0, abs(ref["risk"]))
+    assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= 1e-3 * max(1.0, np.max(np.abs(ref["u"][0])))
+    assert res["info"]["res_inf_fp64"] < 5e-4
+    assert np.all(np.abs(res["x"]) <= 5 + 1e-2)
