@@ -160,6 +160,9 @@ typedef struct spock_info {
     double res_inf_fp64;  /* same in FP64 (fp64_check), else = res_inf */
     double risk;          /* s^0 of T(v): the risk value (Sec. 4, Eq. min-s0-v1) */
     double device_ms;     /* device time of the solve kernel (CUDA events) */
+    double phase_ms[7];   /* device time per phase seen by the first CTA, barrier waits
+                             included: prep/S2, backward sweep, forward sweep + eta update,
+                             T reductions, Anderson dots, direction pass, K2/backtrack passes */
 } spock_info;
 
 void spock_solve_opts_default(spock_solve_opts* o);

@@ -744,6 +744,7 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
     info->n_K2 = h.n_K2; info->n_fallback = h.n_fb; info->n_backtracks = h.n_bt;
     info->res_inf = h.res_inf; info->res_inf_fp64 = res64; info->risk = risk;
     info->device_ms = ms;
+    for (int q = 0; q < 7; ++q) info->phase_ms[q] = 1e-6 * (double)h.prof[q];
   }
   return h.status == 0 ? SPOCK_OK : SPOCK_MAXITER;
 }

@@ -238,12 +238,13 @@ struct RedAcc {
   }
 };
 
-// Block reduction of NRED doubles (slot 0 max, others sums) into out[] (valid
-// in thread 0). scratch: NRED * 32 doubles of shared memory.
-__device__ __forceinline__ void block_reduce_red(double (&v)[NRED], double* scratch) {
+// Block reduction of NRED doubles into v[] (valid in thread 0): slot
+// `max_slot` takes the maximum (-1: none), the others the sum.
+// scratch: NRED * 32 doubles of shared memory.
+__device__ __forceinline__ void block_reduce_red(double (&v)[NRED], double* scratch, int max_slot) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int i = 0; i < NRED; ++i) v[i] = (i == R_MAX) ? warp_max(v[i]) : warp_sum(v[i]);
+  for (int i = 0; i < NRED; ++i) v[i] = (i == max_slot) ? warp_max(v[i]) : warp_sum(v[i]);
   __syncthreads();
   if (lane == 0)
 #pragma unroll
@@ -253,7 +254,7 @@ __device__ __forceinline__ void block_reduce_red(double (&v)[NRED], double* scra
 #pragma unroll
     for (int i = 0; i < NRED; ++i) {
       double x = lane < nw ? scratch[i * 32 + lane] : 0.0;
-      v[i] = (i == R_MAX) ? warp_max(x) : warp_sum(x);
+      v[i] = (i == max_slot) ? warp_max(x) : warp_sum(x);
     }
   }
   __syncthreads();

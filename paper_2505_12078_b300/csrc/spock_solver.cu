@@ -501,16 +501,17 @@ __device__ void forward_segment(const Prob<T>& P, const Team& tm, Smem<T> sm, in
 // ---------------------------------------------------------------------------
 // group reduction of the per-thread partials into ctl->red (every CTA reads)
 // ---------------------------------------------------------------------------
-__device__ bool group_reduce(double (&v)[NRED], double* partials, SolveCtl* ctl, const int* maxmask) {
+// max_slot: index of the slot reduced by max (-1: every slot is a sum)
+__device__ bool group_reduce(double (&v)[NRED], double* partials, SolveCtl* ctl, int max_slot) {
   __shared__ double scratch[NRED * 32];
-  block_reduce_red(v, scratch);
+  block_reduce_red(v, scratch, max_slot);
   if (threadIdx.x == 0)
     for (int k = 0; k < NRED; ++k) stc(partials + (long long)blockIdx.x * NRED + k, v[k]);
   const bool ok = grid_sync(&ctl->bar, [&]() {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w < NRED) {
-      const bool mx = maxmask[w] != 0;
-      double s = mx ? 0.0 : 0.0;
+      const bool mx = (w == max_slot);
+      double s = 0.0;
       for (int r = lane; r < (int)gridDim.x; r += 32) {
         const double x = ldc(partials + (long long)r * NRED + w);
         s = mx ? fmax(s, x) : s + x;
@@ -528,12 +529,31 @@ __device__ bool group_reduce(double (&v)[NRED], double* partials, SolveCtl* ctl,
 // ---------------------------------------------------------------------------
 // one evaluation of T: v_out = T(v_in); reduction with reference point vref
 // ---------------------------------------------------------------------------
+// phase timer of CTA 0 (thread 0): adds the time since the last mark to slot k
+struct PhaseClock {
+  uint64_t t;
+  bool on;
+  __device__ __forceinline__ void start() {
+    on = (blockIdx.x == 0 && threadIdx.x == 0);
+    if (on) t = global_ns();
+  }
+  __device__ __forceinline__ void mark(SolveCtl* ctl, int k) {
+    if (on) {
+      const uint64_t n = global_ns();
+      ctl->prof[k] += n - t;
+      t = n;
+    }
+  }
+};
+
 template <class T>
 __device__ bool evalT(const Prob<T>& P, const Team& tm, Smem<T> sm, int tg, int nt,
                       const T* __restrict__ vin, T* __restrict__ vout, const T* __restrict__ vref,
                       double (&red)[NRED], double* partials, SolveCtl* ctl) {
   RedAcc<T> ra;
   ra.zero();
+  PhaseClock pc;
+  pc.start();
   // P
   for (int node = tg; node < P.n; node += nt) {
     if (node < P.n_nl) prep_nonleaf(P, tm, sm, node, vin, vout, vref, ra);
@@ -542,24 +562,28 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, Smem<T> sm, int tg, int 
   }
   auto nop = []() {};
   if (!grid_sync(&ctl->bar, nop)) return false;
+  pc.mark(ctl, 0);
   // B
   for (int l = 0; l < P.n_levels; ++l) {
     for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) backward_segment(P, tm, sm, s);
     if (!grid_sync(&ctl->bar, nop)) return false;
   }
+  pc.mark(ctl, 1);
   // F
   for (int l = P.n_levels - 1; l >= 0; --l) {
     for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt)
       forward_segment(P, tm, sm, s, vin, vout, vref, ra);
     if (l > 0 && !grid_sync(&ctl->bar, nop)) return false;
   }
+  pc.mark(ctl, 2);
   double v[NRED];
 #pragma unroll
   for (int k = 0; k < NRED; ++k) v[k] = (double)ra.v[k];
-  const int mm[NRED] = {1, 0, 0, 0, 0, 0, 0, 0};
-  const bool ok = group_reduce(v, partials, ctl, mm);
+  const bool ok = group_reduce(v, partials, ctl, R_MAX);
 #pragma unroll
   for (int k = 0; k < NRED; ++k) red[k] = v[k];
+  pc.mark(ctl, 3);
+  if (pc.on) ctl->prof[7] += 1;
   return ok;
 }
 
@@ -618,6 +642,8 @@ __global__ void __launch_bounds__(256) k_solve(Prob<T> P, SolveBufs<T> B, SolveO
       const double omega = sqrt(fmax(om2, 0.0));
       T* V = buf[iV];
       T* TV = buf[iTV];
+      PhaseClock pc;
+      pc.start();
       // --- Anderson memory update (pairs (v^k - v^{k-1}, r^k - r^{k-1})) ---
       double kap[AA_M] = {0.0, 0.0, 0.0};
       bool use_aa = false;
@@ -645,8 +671,7 @@ __global__ void __launch_bounds__(256) k_solve(Prob<T> P, SolveBufs<T> B, SolveO
           stc(B.RP + e, r);
         }
         for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? (double)acc[a] : 0.0;
-        const int mm[NRED] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (!group_reduce(dd, B.partials, ctl, mm)) goto fail;
+        if (!group_reduce(dd, B.partials, ctl, -1)) goto fail;
         double bvec[AA_M];
         if (push) {
           if (count < AA_M) ++count;
@@ -693,6 +718,7 @@ __global__ void __launch_bounds__(256) k_solve(Prob<T> P, SolveBufs<T> B, SolveO
           }
         }
       }
+      pc.mark(ctl, 4);
       // --- psi and the first trial point v~ = v + psi ---
       {
         T* VT = buf[iVT];
@@ -710,6 +736,7 @@ __global__ void __launch_bounds__(256) k_solve(Prob<T> P, SolveBufs<T> B, SolveO
         }
       }
       if (!grid_sync(&ctl->bar, []() {})) goto fail;
+      pc.mark(ctl, 5);
       ok = evalT(P, tm, sm, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl);
       ++nT;
       if (!ok) goto fail;
