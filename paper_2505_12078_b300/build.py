@@ -2,50 +2,87 @@
 
     python -m paper_2505_12078_b300.build          # build (skips if up to date)
     python -m paper_2505_12078_b300.build --force
+    python -m paper_2505_12078_b300.build -v       # print ptxas register/spill report
+
+Every translation unit (and every solver kernel variant) is compiled to an
+object in parallel, then linked into one shared library.
 """
+import concurrent.futures as cf
 import os
 import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libspock.so")
-SOURCES = ["spock_api.cu", "spock_setup.cu", "spock_solver.cu"]
-HEADERS = ["spock_dev.cuh", "spock_internal.h"]
+HEADERS = ["spock_dev.cuh", "spock_internal.h", "spock_solver_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# (object name, source, extra defines)
+UNITS = [
+    ("spock_api", "spock_api.cu", []),
+    ("spock_setup", "spock_setup.cu", []),
+    ("spock_solver", "spock_solver.cu", []),
+    ("solver_f1", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=1", "-DSPOCK_SUFFIX=f1"]),
+    ("solver_f2", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=f2"]),
+    ("solver_d2", "spock_solver_inst.cu", ["-DSPOCK_T=double", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=d2"]),
+    ("solver_d4", "spock_solver_inst.cu", ["-DSPOCK_T=double", "-DSPOCK_CH=4", "-DSPOCK_SUFFIX=d4"]),
+]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *ARCH]
 
 
 def nvcc():
-    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
-        if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
-            return c
+    c = os.environ.get("NVCC")
+    if c:
+        return c
+    if os.path.exists("/usr/local/cuda/bin/nvcc"):
+        return "/usr/local/cuda/bin/nvcc"
     return "nvcc"
 
 
-def up_to_date():
-    if not os.path.exists(OUT):
-        return False
-    t = os.path.getmtime(OUT)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
-    deps.append(os.path.join(HERE, "..", "include", "spock.h"))
-    deps.append(os.path.abspath(__file__))
-    return all(os.path.getmtime(d) <= t for d in deps if os.path.exists(d))
+def _deps(src):
+    d = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS]
+    d.append(os.path.join(HERE, "..", "include", "spock.h"))
+    d.append(os.path.abspath(__file__))
+    return [x for x in d if os.path.exists(x)]
 
 
-def build(force=False, verbose=False, extra=None):
-    if not force and up_to_date():
-        return OUT
-    cmd = [nvcc(), "-shared", "-Xcompiler", "-fPIC", "-O3", "-lineinfo", "-std=c++17",
-           *ARCH, "-Xptxas", "-v" if verbose else "-O3", "-o", OUT + ".tmp"]
-    cmd += list(extra or [])
-    cmd += [os.path.join(CSRC, f) for f in SOURCES]
+def _stale(target, deps):
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def _compile(unit, verbose):
+    name, src, defs = unit
+    obj = os.path.join(OBJ, name + ".o")
+    cmd = [nvcc(), "-c", *FLAGS, *defs, "-o", obj + ".tmp", os.path.join(CSRC, src)]
+    if verbose:
+        cmd[2:2] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, cwd=CSRC, capture_output=True, text=True)
     if r.returncode != 0:
-        sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libspock.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
-    os.replace(OUT + ".tmp", OUT)
+        raise RuntimeError(f"nvcc failed on {name}:\n{r.stdout}{r.stderr}")
+    os.replace(obj + ".tmp", obj)
+    return name, r.stderr
+
+
+def build(force=False, verbose=False):
+    os.makedirs(OBJ, exist_ok=True)
+    todo = [u for u in UNITS
+            if force or _stale(os.path.join(OBJ, u[0] + ".o"), _deps(u[1]))]
+    if todo:
+        with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
+            for name, log in ex.map(lambda u: _compile(u, verbose), todo):
+                if verbose:
+                    sys.stderr.write(f"== {name}\n{log}")
+    objs = [os.path.join(OBJ, u[0] + ".o") for u in UNITS]
+    if todo or force or _stale(OUT, objs):
+        cmd = [nvcc(), "-shared", *ARCH, "-o", OUT + ".tmp", *objs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc link failed:\n{r.stdout}{r.stderr}")
+        os.replace(OUT + ".tmp", OUT)
     return OUT
 
 

@@ -14,7 +14,6 @@ namespace spock {
 constexpr int MAXD = 256;          // max nx + nu
 constexpr int MAXTW = 8;           // max warps per team
 constexpr int NRED = 8;            // reduction slots per T evaluation
-constexpr int MAXE = (MAXD + 2 + 31) / 32;   // per-lane elements of one cost block
 
 // ---------------------------------------------------------------------------
 // Problem descriptor (all pointers device, T = float or double)
@@ -120,11 +119,11 @@ __device__ __forceinline__ Team make_team(int tw) {
 }
 
 // Register accumulator of one lane for a team mat-vec: the lane owns column
-// chunks (c*32 + lane)*VEC .. +VEC, c < CH.
-template <class T>
+// chunks (c*32 + lane)*VEC .. +VEC, c < CH; the widest output is D = 32*VEC*CH.
+template <class T, int CH>
 struct Acc {
   static constexpr int VEC = Vec<T>::N;
-  static constexpr int CH = (MAXD + 32 * VEC - 1) / (32 * VEC);
+  static constexpr int D = 32 * VEC * CH;
   T a[CH][VEC];
   __device__ __forceinline__ void zero() {
 #pragma unroll
@@ -134,50 +133,73 @@ struct Acc {
   }
 };
 
-// acc += M^T-style product: out[j] += sum_k M[k*ld + j] * in[k], k < nrows,
-// j < ncols. Rows are split over the team's warps, columns over lanes.
-template <class T>
-__device__ __forceinline__ void team_mv(const Team& tm, Acc<T>& acc, const T* __restrict__ M,
+// acc += sum_k M[k*ld + j] * in[k] for j < ncols, k < nrows. Rows are split
+// over the team's warps (warp w takes rows w, w+tw, ...), columns over lanes.
+// Loads of RB rows are issued before their FMAs so a warp has RB*CH 16-byte
+// loads in flight.
+template <class T, int CH>
+__device__ __forceinline__ void team_mv(const Team& tm, Acc<T, CH>& acc, const T* __restrict__ M,
                                         int ld, int nrows, int ncols, const T* in) {
   constexpr int VEC = Vec<T>::N;
-  const int nch = (ncols + 32 * VEC - 1) / (32 * VEC);
-#pragma unroll 2
-  for (int k = tm.warp; k < nrows; k += tm.tw) {
-    const T xk = in[k];
-    const T* row = M + (size_t)k * ld;
+  constexpr int RB = (sizeof(T) == 4) ? 8 : 4;
+  const int step = tm.tw;
+  for (int k0 = tm.warp; k0 < nrows; k0 += RB * step) {
+    T m[RB][CH][VEC];
+    T xk[RB];
 #pragma unroll
-    for (int c = 0; c < Acc<T>::CH; ++c) {
-      const int col = (c * 32 + tm.lane) * VEC;
-      if (c < nch && col < ncols) {
-        T m[VEC];
-        vload<T>(row + col, m);
+    for (int r = 0; r < RB; ++r) {
+      const int k = k0 + r * step;
+      const bool okr = k < nrows;
+      xk[r] = okr ? in[k] : T(0);
+      const T* row = M + (size_t)(okr ? k : 0) * ld;
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc.a[c][e] = fma(m[e], xk, acc.a[c][e]);
+      for (int c = 0; c < CH; ++c) {
+        const int col = (c * 32 + tm.lane) * VEC;
+        if (okr && col < ncols) {
+          vload<T>(row + col, m[r][c]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) m[r][c][e] = T(0);
+        }
       }
     }
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc.a[c][e] = fma(m[r][c][e], xk[r], acc.a[c][e]);
   }
 }
 
-// Sum the warps' accumulators (fixed order) and hand out[j] to f(j, value) for
-// j < ncols. red: team scratch of tw*MAXD elements. Ends with a team sync.
-template <class T, class F>
-__device__ __forceinline__ void team_reduce(const Team& tm, const Acc<T>& acc, int ncols, T* red,
-                                            F&& f) {
+// Sum the warps' accumulators (fixed order) and call f(j, m, value) for every
+// output j < ncols owned by this thread (j = tid + m*nth, m a compile-time
+// index so per-thread register arrays can be indexed by it). red: team
+// scratch of tw*D elements. Ends with a team sync.
+template <class T, int CH, class F>
+__device__ __forceinline__ void team_reduce(const Team& tm, const Acc<T, CH>& acc, int ncols,
+                                            T* red, F&& f) {
   constexpr int VEC = Vec<T>::N;
+  constexpr int D = Acc<T, CH>::D;
+  constexpr int PT = D / 32;
 #pragma unroll
-  for (int c = 0; c < Acc<T>::CH; ++c) {
+  for (int c = 0; c < CH; ++c) {
     const int col = (c * 32 + tm.lane) * VEC;
     if (col < ncols) {
 #pragma unroll
       for (int e = 0; e < VEC; ++e)
-        if (col + e < ncols) red[tm.warp * MAXD + col + e] = acc.a[c][e];
+        if (col + e < ncols) red[tm.warp * D + col + e] = acc.a[c][e];
     }
   }
   tm.sync();
-  for (int j = tm.tid; j < ncols; j += tm.nth) {
-    T s = red[j];
-    for (int w = 1; w < tm.tw; ++w) s += red[w * MAXD + j];
-    f(j, s);
+#pragma unroll
+  for (int m = 0; m < PT; ++m) {
+    const int j = tm.tid + m * tm.nth;
+    if (j < ncols) {
+      T s = red[j];
+      for (int w = 1; w < tm.tw; ++w) s += red[w * D + j];
+      f(j, m, s);
+    }
   }
   __threadfence_block();
   tm.sync();
@@ -261,15 +283,22 @@ __device__ __forceinline__ void block_reduce_red(double (&v)[NRED], double* scra
 }
 
 // ---------------------------------------------------------------------------
-// grid barrier with a time limit (sense via a generation counter). The last
-// CTA to arrive may run a callback (whole CTA) before releasing the others.
-// On timeout the error word is set and every CTA leaves at its next check.
+// grid barrier with a time limit. `count` counts arrivals for the whole launch
+// (never reset), so barrier number e completes when count reaches e*gridDim.x;
+// the last CTA to arrive may run a callback (whole CTA) and then publishes
+// `gen` = e with a release store, which the others wait for. On timeout the
+// error word is set and every CTA leaves at its next check.
 // ---------------------------------------------------------------------------
 struct GridCtl {
   unsigned int count;
   unsigned int gen;
-  int error;          // 0 ok, else SPOCK_ETIMEOUT-style code
+  int error;          // 0 ok, else a timeout happened
   int pad;
+};
+
+struct Grid {
+  GridCtl* ctl;
+  unsigned epoch;     // barriers passed by this CTA (identical on every CTA)
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -283,6 +312,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ int ld_relaxed_i(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -291,44 +323,50 @@ __device__ __forceinline__ int ld_relaxed_i(const int* p) {
 
 constexpr uint64_t BARRIER_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
-// Returns false when the group is in error (timeout here or elsewhere).
+// Returns false when the launch is in error (timeout here or elsewhere).
 template <class F>
-__device__ __forceinline__ bool grid_sync(GridCtl* ctl, F&& last_cb) {
+__device__ __forceinline__ bool grid_sync(Grid& g, F&& last_cb) {
   __shared__ int s_flag;
+  const unsigned e = ++g.epoch;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = ld_acquire(&ctl->gen);
     __threadfence();
-    const unsigned arrived = atomicAdd(&ctl->count, 1u) + 1u;
-    s_flag = (arrived == gridDim.x) ? 1 : 0;
-    if (!s_flag) {
-      const uint64_t t0 = global_ns();
+    const unsigned arrived = atomicAdd(&g.ctl->count, 1u) + 1u;
+    if (arrived == e * gridDim.x) {
+      __threadfence();
+      s_flag = 1;
+    } else {
       int ok = 1;
-      while (ld_acquire(&ctl->gen) == g) {
-        if (ld_relaxed_i(&ctl->error)) { ok = 0; break; }
-        if (global_ns() - t0 > BARRIER_LIMIT_NS) {
-          atomicExch(&ctl->error, 1);
-          ok = 0;
-          break;
+      uint64_t t0 = 0;
+      unsigned spins = 0;
+      while (ld_acquire(&g.ctl->gen) < e) {
+        if ((++spins & 63u) == 0u) {
+          if (ld_relaxed_i(&g.ctl->error)) { ok = 0; break; }
+          const uint64_t t = global_ns();
+          if (t0 == 0) {
+            t0 = t;
+          } else if (t - t0 > BARRIER_LIMIT_NS) {
+            atomicExch(&g.ctl->error, 1);
+            ok = 0;
+            break;
+          }
         }
       }
       s_flag = ok ? 2 : 3;
     }
   }
   __syncthreads();
-  if (s_flag == 1) {
+  const int flag = s_flag;
+  if (flag == 1) {
     last_cb();                       // whole last CTA
     __syncthreads();
     if (threadIdx.x == 0) {
-      ctl->count = 0;
       __threadfence();
-      atomicAdd(&ctl->gen, 1u);
+      st_release(&g.ctl->gen, e);
     }
-    __syncthreads();
-    return ld_relaxed_i(&ctl->error) == 0;
+    return ld_relaxed_i(&g.ctl->error) == 0;
   }
-  __threadfence();
-  return s_flag == 2;
+  return flag == 2;
 }
 
 }  // namespace spock

@@ -1,873 +1,49 @@
-// spock_solver.cu -- the SPOCK iteration as one persistent cooperative kernel.
-//
-// One evaluation of the Chambolle-Pock operator T (Eq. chambolle-pock-operator)
-// is three phases separated by grid barriers:
-//
-//  P (per node, all nodes in parallel): w = z - alpha L* eta for the node's
-//    own blocks (sibling sums of L* read the children's cost blocks), the
-//    s0 update (prox of f's linear term), the S2 projection of (y^i, tau^[i],
-//    s^[i]) in closed form (Sherman-Morrison on GG' = (a^2+3) I + 11'), and
-//    the parts of Alg. 2 that do not depend on the sweep:
-//      h^i = -K_i' ubar^i - xbar^i,  e^i = Rt_i^{-1} ubar^i,  q^leaf = -xbar.
-//  B (backward sweep of Alg. 2, bottom-up over "segments" = chains of
-//    single-child non-leaf nodes, which a team walks without a grid barrier):
-//      v_c = q_c + P_c c_c;  q^i = sum_c Abar_c' v_c + h^i;
-//      d^i = e^i - sum_c (B_c Rt_i^{-1})' v_c.
-//    (Alg. 2's qbar holds the extra term (K' + sum Abar'PB) d, which is zero
-//    because K = -Rt^{-1} sum B'PA; the kernel uses the reduced form.)
-//  F (forward rollout of Alg. 2, top-down over segments): u^i = K x^i + d^i,
-//    x^c = Abar_c x^i + B_c d^i + c_c; fused with eta+ = prox_{alpha g*}(eta
-//    + alpha L(2z+ - z)) for every block whose inputs are complete, and with
-//    the residual r = v - T(v) reductions (max|r|, ||r_z||^2, ||r_eta||^2,
-//    <r_eta, L r_z>, and the M-inner product with a reference point).
-//
-// The SuperMann driver (Alg. 4) with Anderson directions (Alg. 3, m = 3) runs
-// redundantly on every CTA from the group-reduced scalars, so all CTAs take
-// the same branch; there is no host round trip per iteration.
+// spock_solver.cu -- picks the solver kernel variant (precision, mat-vec
+// width) for a problem; the variants are compiled from spock_solver_inst.cu.
 #include <cuda_runtime.h>
-#include <math.h>
 
 #include "spock_dev.cuh"
 #include "spock_internal.h"
 
 namespace spock {
 
-constexpr int AA_M = 3;
-constexpr double C0 = 0.99, C1 = 0.99, C2 = 0.99, BETA = 0.5, SIGMA = 0.1, LAMBDA = 1.0;
+#define SPOCK_DECL(T, SUF)                                                                   \
+  cudaError_t launch_solve_##SUF(const Prob<T>&, const SolveBufs<T>&, const SolveOpts&, int, \
+                                 int, int, cudaStream_t);                                    \
+  int max_grid_##SUF(int, int, int*);
+SPOCK_DECL(float, f1)
+SPOCK_DECL(float, f2)
+SPOCK_DECL(double, d2)
+SPOCK_DECL(double, d4)
 
-template <class T>
-struct Smem {
-  T* in;    // mat-vec input
-  T* xn;    // x of the current forward node
-  T* un;    // u of the current forward node
-  T* xb;    // xbar (prep) / x carry of the next chain node (forward)
-  T* red;   // tw * MAXD
-};
-
-template <class T>
-__device__ __forceinline__ T refv(const T* vref, long long idx, T old) {
-  return vref ? ldc(vref + idx) : old;
+int solver_chunks(int precision, int width) {
+  const int vec = precision == 64 ? 2 : 4;
+  const int ch = (width + 32 * vec - 1) / (32 * vec);
+  if (precision == 32) return ch <= 1 ? 1 : 2;
+  return ch <= 2 ? 2 : 4;
 }
 
-// ---------------------------------------------------------------------------
-// Phase P
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ void s2_block(const Prob<T>& P, int lane, int i, const T* __restrict__ vin,
-                         T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
-  const int nx = P.nx, nu = P.nu;
-  const T* z = vin;
-  const T* eta = vin + P.nz;
-  const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
-  const long long yo = P.o_y + P.yoff[i];
-  const T al = P.alpha, a = P.avar[i];
-  const T eS = ldc(eta + P.e_s + i);
-  const T* ey = eta + P.e_y + P.yoff[i];
-  auto wy = [&](int k) -> T {
-    const T b = (k < m) ? P.prob[c0 + k] : (k == 2 * m ? T(1) : T(0));
-    return ldc(z + yo + k) - al * (ldc(ey + k) - b * eS);
-  };
-  auto wt = [&](int l) -> T {
-    const int c = c0 + l;
-    const T* q = eta + P.e_q + (long long)(c - 1) * P.W;
-    return ldc(z + P.o_tau + c - 1) - al * (T(0.5) * (ldc(q + nx + nu) + ldc(q + nx + nu + 1)));
-  };
-  auto ws = [&](int l) -> T {
-    const int c = c0 + l;
-    T g;
-    if (c < P.n_nl) {
-      g = ldc(eta + P.e_s + c);
-    } else {
-      const T* q = eta + P.e_qN + (long long)(c - P.n_nl) * (nx + 2);
-      g = T(0.5) * (ldc(q + nx) + ldc(q + nx + 1));
-    }
-    return ldc(z + P.o_s + c - 1) - al * g;
-  };
-  const T y3 = wy(2 * m);
-  T sg = 0;
-  for (int l = lane; l < m; l += 32) sg += a * wy(l) - wy(m + l) + y3 - wt(l) - ws(l);
-  sg = warp_sum(sg);
-  const T cc = a * a + T(3);
-  const T corr = sg / (cc + T(m));
-  T sl = 0;
-  for (int l = lane; l < m; l += 32) {
-    const T wy1 = wy(l), wy2 = wy(m + l), wtl = wt(l), wsl = ws(l);
-    const T gv = a * wy1 - wy2 + y3 - wtl - wsl;
-    const T lam = (gv - corr) / cc;
-    sl += lam;
-    const int c = c0 + l;
-    const T n1 = wy1 - a * lam, n2 = wy2 + lam, nt = wtl + lam, ns = wsl + lam;
-    long long idx;
-    idx = yo + l;           { const T o = ldc(z + idx); stc(vout + idx, n1); ra.z(o, n1, refv(vref, idx, o)); }
-    idx = yo + m + l;       { const T o = ldc(z + idx); stc(vout + idx, n2); ra.z(o, n2, refv(vref, idx, o)); }
-    idx = P.o_tau + c - 1;  { const T o = ldc(z + idx); stc(vout + idx, nt); ra.z(o, nt, refv(vref, idx, o)); }
-    idx = P.o_s + c - 1;    { const T o = ldc(z + idx); stc(vout + idx, ns); ra.z(o, ns, refv(vref, idx, o)); }
-  }
-  sl = warp_sum(sl);
-  if (lane == 0) {
-    const long long idx = yo + 2 * m;
-    const T n3 = y3 - sl;
-    const T o = ldc(z + idx);
-    stc(vout + idx, n3);
-    ra.z(o, n3, refv(vref, idx, o));
-    if (i == 0) {   // s0 <- s0 - alpha (eta_s^0) - alpha
-      const T o0 = ldc(z);
-      const T n0 = (o0 - al * eS) - al;
-      stc(vout, n0);
-      ra.z(o0, n0, refv(vref, 0, o0));
-    }
-  }
+template <>
+cudaError_t launch_solve<float>(const Prob<float>& P, const SolveBufs<float>& B, const SolveOpts& o,
+                                int tw, int grid, int threads, cudaStream_t s) {
+  if (solver_chunks(32, P.nx + P.nu) == 1) return launch_solve_f1(P, B, o, tw, grid, threads, s);
+  return launch_solve_f2(P, B, o, tw, grid, threads, s);
 }
-
-template <class T>
-__device__ void prep_nonleaf(const Prob<T>& P, const Team& tm, const Smem<T>& sm, int i,
-                             const T* __restrict__ vin, T* __restrict__ vout,
-                             const T* __restrict__ vref, RedAcc<T>& ra) {
-  const int nx = P.nx, nu = P.nu;
-  const T* z = vin;
-  const T* eta = vin + P.nz;
-  const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
-  const T al = P.alpha;
-  const T* ec = eta + P.e_c + (long long)i * P.n_c;
-  for (int k = tm.tid; k < nu; k += tm.nth) {
-    T g = 0;
-    if (P.nbu) g += P.gu[k] * ldc(ec + P.nbx + k);
-    if (P.has_ball) g += P.gu[k] * ldc(ec + P.nbox + k);
-    for (int c = c0; c < c1; ++c)
-      g += ldr(P.rh + (long long)(c - 1) * nu + k) * ldc(eta + P.e_q + (long long)(c - 1) * P.W + nx + k);
-    sm.in[k] = ldc(z + P.o_u + (long long)i * nu + k) - al * g;
-  }
-  for (int k = tm.tid; k < nx; k += tm.nth) {
-    T g = P.nbx ? P.gx[k] * ldc(ec + k) : T(0);
-    for (int c = c0; c < c1; ++c)
-      g += ldr(P.qh + (long long)(c - 1) * nx + k) * ldc(eta + P.e_q + (long long)(c - 1) * P.W + k);
-    sm.xb[k] = ldc(z + P.o_x + (long long)i * nx + k) - al * g;
-  }
-  tm.sync();
-  Acc<T> acc;
-  acc.zero();
-  team_mv(tm, acc, P.MP + (size_t)i * nu * P.ldP, P.ldP, nu, nx + nu, sm.in);
-  T* hb = P.hbuf + (long long)i * nx;
-  T* eb = P.ebuf + (long long)i * nu;
-  const T* xb = sm.xb;
-  team_reduce(tm, acc, nx + nu, sm.red, [&](int j, T s) {
-    if (j < nx) stc(hb + j, -s - xb[j]);
-    else stc(eb + (j - nx), s);
-  });
-  if (tm.warp == 0) s2_block(P, tm.lane, i, vin, vout, vref, ra);
-}
-
-template <class T>
-__device__ void prep_leaf(const Prob<T>& P, const Team& tm, int j, const T* __restrict__ vin) {
-  const int nx = P.nx;
-  const T* z = vin;
-  const T* eta = vin + P.nz;
-  const int jj = j - P.n_nl;
-  const T al = P.alpha;
-  for (int k = tm.tid; k < nx; k += tm.nth) {
-    T g = P.nbx ? P.gN[k] * ldc(eta + P.e_cN + (long long)jj * P.n_cN + k) : T(0);
-    g += ldr(P.qNh + (long long)jj * nx + k) * ldc(eta + P.e_qN + (long long)jj * (nx + 2) + k);
-    const T xbar = ldc(z + P.o_x + (long long)j * nx + k) - al * g;
-    stc(P.qbuf + (long long)j * nx + k, -xbar);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Phase B: one segment, bottom-up
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ void backward_segment(const Prob<T>& P, const Team& tm, const Smem<T>& sm, int s) {
-  const int nx = P.nx, nu = P.nu;
-  int i = P.seg_bot[s];
-  const int len = P.seg_len[s];
-  for (int step = 0; step < len; ++step) {
-    const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
-    Acc<T> acc;
-    acc.zero();
-    for (int c = c0; c < c1; ++c) {
-      for (int k = tm.tid; k < nx; k += tm.nth)
-        sm.in[k] = ldc(P.qbuf + (long long)c * nx + k) + ldr(P.Pc + (long long)(c - 1) * nx + k);
-      tm.sync();
-      team_mv(tm, acc, P.MB + (size_t)(c - 1) * nx * P.ldB, P.ldB, nx, nx + nu, sm.in);
-      tm.sync();
-    }
-    T* q = P.qbuf + (long long)i * nx;
-    T* d = P.dbuf + (long long)i * nu;
-    const T* h = P.hbuf + (long long)i * nx;
-    const T* e = P.ebuf + (long long)i * nu;
-    team_reduce(tm, acc, nx + nu, sm.red, [&](int j, T v) {
-      if (j < nx) stc(q + j, v + ldc(h + j));
-      else stc(d + (j - nx), ldc(e + (j - nx)) - v);
-    });
-    i = P.anc[i];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Phase F helpers: eta blocks (one warp each)
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restrict__ xn,
-                            const T* __restrict__ un, const T* __restrict__ vin,
-                            T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
-  const int nx = P.nx, nu = P.nu;
-  const T* z = vin;
-  const T* eta = vin + P.nz;
-  T* eo = vout + P.nz;
-  const T* er = vref ? vref + P.nz : nullptr;
-  const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
-  const T al = P.alpha;
-  const long long yo = P.o_y + P.yoff[i];
-  const long long ye = P.e_y + P.yoff[i];
-  // y part: (K^i)* = R^{2m}_+ x R
-  for (int e = lane; e < 2 * m + 1; e += 32) {
-    const T Lo = ldc(z + yo + e), Ln = ldc(vout + yo + e), Lr = refv(vref, yo + e, Lo);
-    const T eo_ = ldc(eta + ye + e);
-    const T eb = eo_ + al * (T(2) * Ln - Lo);
-    const T w = eb / al;
-    const T p = (e < 2 * m) ? max(w, T(0)) : w;
-    const T en = eb - al * p;
-    stc(eo + ye + e, en);
-    ra.eta(eo_, en, er ? ldc(er + ye + e) : eo_, Lo, Ln, Lr);
-  }
-  // s part: s^i - b'y^i in R_+
-  {
-    T bo = 0, bn = 0, br = 0;
-    for (int k = lane; k < m; k += 32) {
-      const T p = P.prob[c0 + k];
-      const T o = ldc(z + yo + k);
-      bo += p * o;
-      bn += p * ldc(vout + yo + k);
-      br += p * refv(vref, yo + k, o);
-    }
-    bo = warp_sum(bo); bn = warp_sum(bn); br = warp_sum(br);
-    if (lane == 0) {
-      const long long is = (i == 0) ? 0 : P.o_s + i - 1;
-      const T yo3 = ldc(z + yo + 2 * m);
-      const T so = ldc(z + is);
-      const T Lo = so - bo - yo3;
-      const T Ln = ldc(vout + is) - bn - ldc(vout + yo + 2 * m);
-      const T Lr = vref ? ldc(vref + is) - br - ldc(vref + yo + 2 * m) : Lo;
-      const long long ie = P.e_s + i;
-      const T eo_ = ldc(eta + ie);
-      const T eb = eo_ + al * (T(2) * Ln - Lo);
-      const T en = eb - al * max(eb / al, T(0));
-      stc(eo + ie, en);
-      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, Lo, Ln, Lr);
-    }
-  }
-  if (P.n_c == 0) return;
-  const long long ce = P.e_c + (long long)i * P.n_c;
-  const long long xo = P.o_x + (long long)i * nx;
-  const long long uo = P.o_u + (long long)i * nu;
-  // box rows
-  for (int e = lane; e < P.nbox; e += 32) {
-    T g, o, nn, rr;
-    if (e < P.nbx) {
-      g = P.gx[e]; o = ldc(z + xo + e); nn = xn[e]; rr = refv(vref, xo + e, o);
-    } else {
-      const int k = e - P.nbx;
-      g = P.gu[k]; o = ldc(z + uo + k); nn = un[k]; rr = refv(vref, uo + k, o);
-    }
-    const T Lo = g * o, Ln = g * nn, Lr = g * rr;
-    const T eo_ = ldc(eta + ce + e);
-    const T eb = eo_ + al * (T(2) * Ln - Lo);
-    const T w = eb / al;
-    const T lo = P.box_lo[(long long)i * P.nbox + e], hi = P.box_hi[(long long)i * P.nbox + e];
-    const T p = min(max(w, lo), hi);
-    const T en = eb - al * p;
-    stc(eo + ce + e, en);
-    ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, Lo, Ln, Lr);
-  }
-  // ball rows on u
-  if (P.has_ball) {
-    T n2 = 0;
-    for (int k = lane; k < nu; k += 32) {
-      const T g = P.gu[k];
-      const T eb = ldc(eta + ce + P.nbox + k) + al * (T(2) * g * un[k] - g * ldc(z + uo + k));
-      const T w = eb / al;
-      n2 += w * w;
-    }
-    const T nw = sqrt(warp_sum(n2));
-    const T r = P.ball[i];
-    const T sc = (nw > r) ? r / nw : T(1);
-    for (int k = lane; k < nu; k += 32) {
-      const T g = P.gu[k];
-      const T o = ldc(z + uo + k);
-      const T Lo = g * o, Ln = g * un[k], Lr = g * refv(vref, uo + k, o);
-      const long long ie = ce + P.nbox + k;
-      const T eo_ = ldc(eta + ie);
-      const T eb = eo_ + al * (T(2) * Ln - Lo);
-      const T w = eb / al;
-      const T en = eb - al * (w * sc);
-      stc(eo + ie, en);
-      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, Lo, Ln, Lr);
-    }
-  }
-}
-
-// translated SOC cost block: a + Pi_SOC(eb/alpha - a), a = (0.., 1/2, -1/2)
-template <class T, class FL>
-__device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, long long ebase,
-                                          const T* __restrict__ eta, T* __restrict__ eo,
-                                          const T* __restrict__ er, FL&& Lz, RedAcc<T>& ra) {
-  const T al = P.alpha;
-  T ebv[MAXE];
-  T n2 = 0, tt = 0;
-#pragma unroll
-  for (int q = 0; q < MAXE; ++q) {
-    const int e = lane + 32 * q;
-    ebv[q] = 0;
-    if (e < dim) {
-      T Lo, Ln, Lr;
-      Lz(e, Lo, Ln, Lr);
-      const T eb = ldc(eta + ebase + e) + al * (T(2) * Ln - Lo);
-      ebv[q] = eb;
-      const T ae = (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
-      const T w = eb / al - ae;
-      if (e < dim - 1) n2 += w * w;
-      else tt = w;
-    }
-  }
-  const T nw = sqrt(warp_sum(n2));
-  const T t = __shfl_sync(0xffffffffu, tt, (dim - 1) & 31);
-  // case 0: inside (keep), 1: polar (zero), 2: boundary
-  const int cs = (nw <= t) ? 0 : ((nw <= -t) ? 1 : 2);
-  const T f = (nw + t) / T(2);
-#pragma unroll
-  for (int q = 0; q < MAXE; ++q) {
-    const int e = lane + 32 * q;
-    if (e < dim) {
-      T Lo, Ln, Lr;
-      Lz(e, Lo, Ln, Lr);
-      const T eb = ebv[q];
-      const T ae = (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
-      const T w = eb / al - ae;
-      T ps;
-      if (cs == 0) ps = w;
-      else if (cs == 1) ps = T(0);
-      else ps = (e < dim - 1) ? w * (f / nw) : f;
-      const T en = eb - al * (ae + ps);
-      const T eo_ = ldc(eta + ebase + e);
-      stc(eo + ebase + e, en);
-      ra.eta(eo_, en, er ? ldc(er + ebase + e) : eo_, Lo, Ln, Lr);
-    }
-  }
-}
-
-template <class T>
-__device__ void eta_soc(const Prob<T>& P, int lane, int c, int i, const T* __restrict__ xn,
-                        const T* __restrict__ un, const T* __restrict__ vin, T* __restrict__ vout,
-                        const T* __restrict__ vref, RedAcc<T>& ra) {
-  const int nx = P.nx, nu = P.nu;
-  const T* z = vin;
-  const long long xo = P.o_x + (long long)i * nx, uo = P.o_u + (long long)i * nu;
-  const long long it = P.o_tau + c - 1;
-  const T* qh = P.qh + (long long)(c - 1) * nx;
-  const T* rh = P.rh + (long long)(c - 1) * nu;
-  auto Lz = [&](int e, T& Lo, T& Ln, T& Lr) {
-    if (e < nx) {
-      const T g = ldr(qh + e), o = ldc(z + xo + e);
-      Lo = g * o; Ln = g * xn[e]; Lr = g * refv(vref, xo + e, o);
-    } else if (e < nx + nu) {
-      const int k = e - nx;
-      const T g = ldr(rh + k), o = ldc(z + uo + k);
-      Lo = g * o; Ln = g * un[k]; Lr = g * refv(vref, uo + k, o);
-    } else {
-      const T o = ldc(z + it);
-      Lo = T(0.5) * o; Ln = T(0.5) * ldc(vout + it); Lr = T(0.5) * refv(vref, it, o);
-    }
-  };
-  soc_block(P, lane, P.W, P.e_q + (long long)(c - 1) * P.W, vin + P.nz, vout + P.nz,
-            vref ? vref + P.nz : nullptr, Lz, ra);
-}
-
-template <class T>
-__device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict__ vin,
-                         T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
-  const int nx = P.nx;
-  const T* z = vin;
-  const T* eta = vin + P.nz;
-  T* eo = vout + P.nz;
-  const T* er = vref ? vref + P.nz : nullptr;
-  const int jj = j - P.n_nl;
-  const long long xo = P.o_x + (long long)j * nx;
-  const T al = P.alpha;
-  if (P.nbx) {
-    const long long ce = P.e_cN + (long long)jj * P.n_cN;
-    for (int e = lane; e < nx; e += 32) {
-      const T g = P.gN[e], o = ldc(z + xo + e);
-      const T Lo = g * o, Ln = g * ldc(vout + xo + e), Lr = g * refv(vref, xo + e, o);
-      const T eo_ = ldc(eta + ce + e);
-      const T eb = eo_ + al * (T(2) * Ln - Lo);
-      const T w = eb / al;
-      const T p = min(max(w, P.boxN_lo[(long long)jj * nx + e]), P.boxN_hi[(long long)jj * nx + e]);
-      const T en = eb - al * p;
-      stc(eo + ce + e, en);
-      ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, Lo, Ln, Lr);
-    }
-  }
-  const long long is = P.o_s + j - 1;
-  const T* qNh = P.qNh + (long long)jj * nx;
-  auto Lz = [&](int e, T& Lo, T& Ln, T& Lr) {
-    if (e < nx) {
-      const T g = ldr(qNh + e), o = ldc(z + xo + e);
-      Lo = g * o; Ln = g * ldc(vout + xo + e); Lr = g * refv(vref, xo + e, o);
-    } else {
-      const T o = ldc(z + is);
-      Lo = T(0.5) * o; Ln = T(0.5) * ldc(vout + is); Lr = T(0.5) * refv(vref, is, o);
-    }
-  };
-  soc_block(P, lane, nx + 2, P.e_qN + (long long)jj * (nx + 2), eta, eo, er, Lz, ra);
-}
-
-// ---------------------------------------------------------------------------
-// Phase F: one segment, top-down
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ void forward_segment(const Prob<T>& P, const Team& tm, Smem<T> sm, int s,
-                                const T* __restrict__ vin, T* __restrict__ vout,
-                                const T* __restrict__ vref, RedAcc<T>& ra) {
-  const int nx = P.nx, nu = P.nu;
-  int i = P.seg_top[s];
-  const int len = P.seg_len[s];
-  const T* z = vin;
-  if (i == 0) {
-    for (int k = tm.tid; k < nx; k += tm.nth) {
-      const T xn = P.x0s[k];
-      sm.xn[k] = xn;
-      const long long idx = P.o_x + k;
-      const T o = ldc(z + idx);
-      stc(vout + idx, xn);
-      ra.z(o, xn, refv(vref, idx, o));
-    }
-  } else {
-    for (int k = tm.tid; k < nx; k += tm.nth) sm.xn[k] = ldc(vout + P.o_x + (long long)i * nx + k);
-  }
-  tm.sync();
-  for (int step = 0; step < len; ++step) {
-    const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1], m = c1 - c0;
-    // u^i = K x^i + d^i
-    Acc<T> acc;
-    acc.zero();
-    team_mv(tm, acc, P.KT + (size_t)i * nx * P.ldK, P.ldK, nx, nu, sm.xn);
-    const T* d = P.dbuf + (long long)i * nu;
-    {
-      T* un = sm.un;
-      const long long uo = P.o_u + (long long)i * nu;
-      team_reduce(tm, acc, nu, sm.red, [&](int j, T v) {
-        const T u = v + ldc(d + j);
-        un[j] = u;
-        const T o = ldc(z + uo + j);
-        stc(vout + uo + j, u);
-        ra.z(o, u, refv(vref, uo + j, o));
-      });
-    }
-    for (int k = tm.tid; k < nx; k += tm.nth) sm.in[k] = sm.xn[k];
-    for (int k = tm.tid; k < nu; k += tm.nth) sm.in[nx + k] = ldc(d + k);
-    tm.sync();
-    const bool chain = (step + 1 < len);
-    for (int c = c0; c < c1; ++c) {
-      acc.zero();
-      team_mv(tm, acc, P.MF + (size_t)(c - 1) * (nx + nu) * P.ldF, P.ldF, nx + nu, nx, sm.in);
-      const long long xo = P.o_x + (long long)c * nx;
-      const T* cv = P.cvec + (long long)(c - 1) * nx;
-      T* xb = sm.xb;
-      team_reduce(tm, acc, nx, sm.red, [&](int j, T v) {
-        const T xc = v + ldr(cv + j);
-        const T o = ldc(z + xo + j);
-        stc(vout + xo + j, xc);
-        ra.z(o, xc, refv(vref, xo + j, o));
-        if (chain) xb[j] = xc;
-      });
-    }
-    // eta blocks of node i, its children's cost blocks, leaf children's blocks
-    const bool leaves = (c0 >= P.n_nl);
-    const int nb = 1 + m + (leaves ? m : 0);
-    for (int b = tm.warp; b < nb; b += tm.tw) {
-      if (b == 0) eta_nonleaf(P, tm.lane, i, sm.xn, sm.un, vin, vout, vref, ra);
-      else if (b <= m) eta_soc(P, tm.lane, c0 + b - 1, i, sm.xn, sm.un, vin, vout, vref, ra);
-      else eta_leaf(P, tm.lane, c0 + b - 1 - m, vin, vout, vref, ra);
-    }
-    __threadfence_block();
-    tm.sync();
-    if (chain) {
-      i = c0;
-      T* t = sm.xn; sm.xn = sm.xb; sm.xb = t;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// group reduction of the per-thread partials into ctl->red (every CTA reads)
-// ---------------------------------------------------------------------------
-// max_slot: index of the slot reduced by max (-1: every slot is a sum)
-__device__ bool group_reduce(double (&v)[NRED], double* partials, SolveCtl* ctl, int max_slot) {
-  __shared__ double scratch[NRED * 32];
-  block_reduce_red(v, scratch, max_slot);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < NRED; ++k) stc(partials + (long long)blockIdx.x * NRED + k, v[k]);
-  const bool ok = grid_sync(&ctl->bar, [&]() {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w < NRED) {
-      const bool mx = (w == max_slot);
-      double s = 0.0;
-      for (int r = lane; r < (int)gridDim.x; r += 32) {
-        const double x = ldc(partials + (long long)r * NRED + w);
-        s = mx ? fmax(s, x) : s + x;
-      }
-      s = mx ? warp_max(s) : warp_sum(s);
-      if (lane == 0) stc(&ctl->red[w], s);
-    }
-    __threadfence();
-  });
-#pragma unroll
-  for (int k = 0; k < NRED; ++k) v[k] = ldc(&ctl->red[k]);
-  return ok;
-}
-
-// ---------------------------------------------------------------------------
-// one evaluation of T: v_out = T(v_in); reduction with reference point vref
-// ---------------------------------------------------------------------------
-// phase timer of CTA 0 (thread 0): adds the time since the last mark to slot k
-struct PhaseClock {
-  uint64_t t;
-  bool on;
-  __device__ __forceinline__ void start() {
-    on = (blockIdx.x == 0 && threadIdx.x == 0);
-    if (on) t = global_ns();
-  }
-  __device__ __forceinline__ void mark(SolveCtl* ctl, int k) {
-    if (on) {
-      const uint64_t n = global_ns();
-      ctl->prof[k] += n - t;
-      t = n;
-    }
-  }
-};
-
-template <class T>
-__device__ bool evalT(const Prob<T>& P, const Team& tm, Smem<T> sm, int tg, int nt,
-                      const T* __restrict__ vin, T* __restrict__ vout, const T* __restrict__ vref,
-                      double (&red)[NRED], double* partials, SolveCtl* ctl) {
-  RedAcc<T> ra;
-  ra.zero();
-  PhaseClock pc;
-  pc.start();
-  // P
-  for (int node = tg; node < P.n; node += nt) {
-    if (node < P.n_nl) prep_nonleaf(P, tm, sm, node, vin, vout, vref, ra);
-    else prep_leaf(P, tm, node, vin);
-    tm.sync();
-  }
-  auto nop = []() {};
-  if (!grid_sync(&ctl->bar, nop)) return false;
-  pc.mark(ctl, 0);
-  // B
-  for (int l = 0; l < P.n_levels; ++l) {
-    for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) backward_segment(P, tm, sm, s);
-    if (!grid_sync(&ctl->bar, nop)) return false;
-  }
-  pc.mark(ctl, 1);
-  // F
-  for (int l = P.n_levels - 1; l >= 0; --l) {
-    for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt)
-      forward_segment(P, tm, sm, s, vin, vout, vref, ra);
-    if (l > 0 && !grid_sync(&ctl->bar, nop)) return false;
-  }
-  pc.mark(ctl, 2);
-  double v[NRED];
-#pragma unroll
-  for (int k = 0; k < NRED; ++k) v[k] = (double)ra.v[k];
-  const bool ok = group_reduce(v, partials, ctl, R_MAX);
-#pragma unroll
-  for (int k = 0; k < NRED; ++k) red[k] = v[k];
-  pc.mark(ctl, 3);
-  if (pc.on) ctl->prof[7] += 1;
-  return ok;
-}
-
-// ---------------------------------------------------------------------------
-// the solve kernel
-// ---------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(256) k_solve(Prob<T> P, SolveBufs<T> B, SolveOpts o, int tw) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const Team tm = make_team(tw);
-  const int teams_per_cta = (blockDim.x >> 5) / tw;
-  const int tg = blockIdx.x * teams_per_cta + tm.id;
-  const int nt = gridDim.x * teams_per_cta;
-  Smem<T> sm;
-  {
-    T* base = reinterpret_cast<T*>(smraw) + (size_t)tm.id * (4 + tw) * MAXD;
-    sm.in = base; sm.xn = base + MAXD; sm.un = base + 2 * MAXD; sm.xb = base + 3 * MAXD;
-    sm.red = base + 4 * MAXD;
-  }
-  SolveCtl* ctl = B.ctl;
-  T* buf[4] = {B.V, B.TV, B.VT, B.TVT};
-  int iV = 0, iTV = 1, iVT = 2, iTVT = 3;
-  const long long nv = P.nv;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long gstride = (long long)gridDim.x * blockDim.x;
-  const T al = P.alpha;
-  double red[NRED];
-  int status = 0, k = 0, nT = 0, nK0 = 0, nK1 = 0, nK2 = 0, nFB = 0, nBT = 0;
-  double res, om2;
-  bool ok = evalT(P, tm, sm, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl);
-  ++nT;
-  if (!ok) goto fail;
-  res = red[R_MAX];
-  om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
-  if (o.method == 2) goto done;
-  if (o.method == 1) {
-    while (!(res <= o.tol) && k < o.max_iters) {
-      int t = iV; iV = iTV; iTV = t;
-      ok = evalT(P, tm, sm, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl);
-      ++nT; ++k;
-      if (!ok) goto fail;
-      res = red[R_MAX];
-      om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
-    }
-    status = (res <= o.tol) ? 0 : 1;
-    goto done;
-  }
-  {
-    double zeta = sqrt(fmax(om2, 0.0)), omega_safe = zeta;
-    double G[AA_M][AA_M];
-    for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) G[a][b] = 0.0;
-    int count = 0, head = 0;
-    while (true) {
-      if (res <= o.tol) { status = 0; break; }
-      if (k >= o.max_iters) { status = 1; break; }
-      const double omega = sqrt(fmax(om2, 0.0));
-      T* V = buf[iV];
-      T* TV = buf[iTV];
-      PhaseClock pc;
-      pc.start();
-      // --- Anderson memory update (pairs (v^k - v^{k-1}, r^k - r^{k-1})) ---
-      double kap[AA_M] = {0.0, 0.0, 0.0};
-      bool use_aa = false;
-      {
-        const int slot = head;
-        const bool push = (k >= 1);
-        double dd[NRED];
-        T acc[2 * AA_M];
-        for (int a = 0; a < 2 * AA_M; ++a) acc[a] = 0;
-        for (long long e = gtid; e < nv; e += gstride) {
-          const T v = ldc(V + e), r = v - ldc(TV + e);
-          if (push) {
-            const T s_ = v - ldc(B.VP + e);
-            const T y_ = r - ldc(B.RP + e);
-            stc(B.S + slot * nv + e, s_);
-            stc(B.Y + slot * nv + e, y_);
-#pragma unroll
-            for (int l = 0; l < AA_M; ++l) {
-              const T yl = (l == slot) ? y_ : ldc(B.Y + l * nv + e);
-              acc[l] = fma(y_, yl, acc[l]);
-              acc[AA_M + l] = fma(yl, r, acc[AA_M + l]);
-            }
-          }
-          stc(B.VP + e, v);
-          stc(B.RP + e, r);
-        }
-        for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? (double)acc[a] : 0.0;
-        if (!group_reduce(dd, B.partials, ctl, -1)) goto fail;
-        double bvec[AA_M];
-        if (push) {
-          if (count < AA_M) ++count;
-          head = (head + 1) % AA_M;
-          for (int l = 0; l < AA_M; ++l) { G[slot][l] = dd[l]; G[l][slot] = dd[l]; }
-        }
-        for (int l = 0; l < AA_M; ++l) bvec[l] = dd[AA_M + l];
-        if (k > AA_M && count > 0) {
-          // logical order oldest -> newest
-          int ord[AA_M];
-          const int start = (count < AA_M) ? 0 : head;
-          for (int j = 0; j < count; ++j) ord[j] = (start + j) % AA_M;
-          double Rm[AA_M][AA_M], bb[AA_M], tr = 0.0;
-          for (int j = 0; j < count; ++j) tr += G[ord[j]][ord[j]];
-          const double lim = o.rank_tol * sqrt(fmax(tr, 0.0));
-          bool good = tr > 0.0;
-          for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) Rm[a][b] = 0.0;
-          for (int j = 0; j < count && good; ++j) {
-            double dj = G[ord[j]][ord[j]];
-            for (int l = 0; l < j; ++l) dj -= Rm[l][j] * Rm[l][j];
-            if (!(dj > 0.0) || sqrt(dj) < lim) { good = false; break; }
-            Rm[j][j] = sqrt(dj);
-            for (int c = j + 1; c < count; ++c) {
-              double s = G[ord[j]][ord[c]];
-              for (int l = 0; l < j; ++l) s -= Rm[l][j] * Rm[l][c];
-              Rm[j][c] = s / Rm[j][j];
-            }
-          }
-          if (good) {
-            // R'R kappa = Y'r : forward then backward substitution
-            for (int j = 0; j < count; ++j) {
-              double s = bvec[ord[j]];
-              for (int l = 0; l < j; ++l) s -= Rm[l][j] * bb[l];
-              bb[j] = s / Rm[j][j];
-            }
-            double kl[AA_M];
-            for (int j = count - 1; j >= 0; --j) {
-              double s = bb[j];
-              for (int l = j + 1; l < count; ++l) s -= Rm[j][l] * kl[l];
-              kl[j] = s / Rm[j][j];
-            }
-            for (int j = 0; j < count; ++j) kap[ord[j]] = kl[j];
-            use_aa = true;
-          }
-        }
-      }
-      pc.mark(ctl, 4);
-      // --- psi and the first trial point v~ = v + psi ---
-      {
-        T* VT = buf[iVT];
-        const T k0 = (T)kap[0], k1 = (T)kap[1], k2 = (T)kap[2];
-        for (long long e = gtid; e < nv; e += gstride) {
-          const T v = ldc(V + e), r = v - ldc(TV + e);
-          T psi = -r;
-          if (use_aa) {
-            psi -= (ldc(B.S + e) - ldc(B.Y + e)) * k0;
-            psi -= (ldc(B.S + nv + e) - ldc(B.Y + nv + e)) * k1;
-            psi -= (ldc(B.S + 2 * nv + e) - ldc(B.Y + 2 * nv + e)) * k2;
-          }
-          stc(B.PSI + e, psi);
-          stc(VT + e, v + psi);
-        }
-      }
-      if (!grid_sync(&ctl->bar, []() {})) goto fail;
-      pc.mark(ctl, 5);
-      ok = evalT(P, tm, sm, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl);
-      ++nT;
-      if (!ok) goto fail;
-      if (omega <= C0 * zeta) {                       // K0
-        int t = iV; iV = iVT; iVT = t;
-        t = iTV; iTV = iTVT; iTVT = t;
-        zeta = omega;
-        res = red[R_MAX];
-        om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
-        ++nK0; ++k;
-        continue;
-      }
-      double tau = 1.0;
-      int bt = 0;
-      while (true) {
-        const double om2t = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
-        const double omt = sqrt(fmax(om2t, 0.0));
-        if ((omega <= omega_safe && omt <= C1 * omega) || omt == 0.0) {   // K1
-          int t = iV; iV = iVT; iVT = t;
-          t = iTV; iTV = iTVT; iTVT = t;
-          omega_safe = omt + pow(C2, (double)k);
-          res = red[R_MAX];
-          om2 = om2t;
-          ++nK1;
-          break;
-        }
-        const double mdot = red[R_ZD] + red[R_ED] - (double)al * red[R_LZD] - (double)al * red[R_ELD];
-        const double rho = om2t - mdot;
-        if (rho >= SIGMA * omt * omega) {             // K2
-          const T coef = (T)(LAMBDA * rho / om2t);
-          T* Vc = buf[iV];
-          T* VT = buf[iVT];
-          const T* TVT = buf[iTVT];
-          for (long long e = gtid; e < nv; e += gstride) {
-            const T vt = ldc(VT + e);
-            stc(VT + e, ldc(Vc + e) - coef * (vt - ldc(TVT + e)));
-          }
-          if (!grid_sync(&ctl->bar, []() {})) goto fail;
-          int t = iV; iV = iVT; iVT = t;
-          ok = evalT(P, tm, sm, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl);
-          ++nT;
-          if (!ok) goto fail;
-          res = red[R_MAX];
-          om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
-          ++nK2;
-          break;
-        }
-        ++bt; ++nBT;
-        if (bt >= o.max_backtracks) {                 // fall back to v <- T(v)
-          int t = iV; iV = iTV; iTV = t;
-          ok = evalT(P, tm, sm, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl);
-          ++nT;
-          if (!ok) goto fail;
-          res = red[R_MAX];
-          om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
-          ++nFB;
-          break;
-        }
-        tau *= BETA;
-        {
-          const T tt = (T)tau;
-          const T* Vc = buf[iV];
-          T* VT = buf[iVT];
-          for (long long e = gtid; e < nv; e += gstride) stc(VT + e, ldc(Vc + e) + tt * ldc(B.PSI + e));
-        }
-        if (!grid_sync(&ctl->bar, []() {})) goto fail;
-        ok = evalT(P, tm, sm, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl);
-        ++nT;
-        if (!ok) goto fail;
-      }
-      ++k;
-    }
-  }
-done:
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->status = status;
-    ctl->iters = k; ctl->n_T = nT; ctl->n_K0 = nK0; ctl->n_K1 = nK1; ctl->n_K2 = nK2;
-    ctl->n_fb = nFB; ctl->n_bt = nBT;
-    ctl->res_inf = res;
-    for (int q = 0; q < NRED; ++q) ctl->stats[q] = red[q];
-    ctl->final_v = iV;       // final buffer indices for the host
-    ctl->final_tv = iTV;
-  }
-  return;
-fail:
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->status = -5;
-    ctl->iters = k; ctl->n_T = nT;
-    ctl->final_v = iV;
-    ctl->final_tv = iTV;
-  }
-}
-
-template <class T>
-cudaError_t launch_solve(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
-                         int grid, int threads, cudaStream_t s) {
-  const int teams = (threads / 32) / tw;
-  const size_t smem = (size_t)teams * (4 + tw) * MAXD * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  Prob<T> Pc = P;
-  SolveBufs<T> Bc = B;
-  SolveOpts oc = o;
-  int twc = tw;
-  void* args[] = {&Pc, &Bc, &oc, &twc};
-  return cudaLaunchCooperativeKernel((void*)k_solve<T>, dim3(grid), dim3(threads), args, smem, s);
+template <>
+cudaError_t launch_solve<double>(const Prob<double>& P, const SolveBufs<double>& B, const SolveOpts& o,
+                                 int tw, int grid, int threads, cudaStream_t s) {
+  if (solver_chunks(64, P.nx + P.nu) == 2) return launch_solve_d2(P, B, o, tw, grid, threads, s);
+  return launch_solve_d4(P, B, o, tw, grid, threads, s);
 }
 
 int solver_max_grid(int precision, int tw, int threads, int D, int* grid_out) {
-  (void)D;
-  int dev = 0, nsm = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int teams = (threads / 32) / tw;
-  cudaError_t e;
+  const int ch = solver_chunks(precision, D);
   if (precision == 64) {
-    const size_t smem = (size_t)teams * (4 + tw) * MAXD * sizeof(double);
-    cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve<double>, threads, smem);
-  } else {
-    const size_t smem = (size_t)teams * (4 + tw) * MAXD * sizeof(float);
-    cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve<float>, threads, smem);
+    return ch == 2 ? max_grid_d2(tw, threads, grid_out)
+                   : max_grid_d4(tw, threads, grid_out);
   }
-  if (e != cudaSuccess) return -1;
-  *grid_out = nsm * per;
-  return 0;
+  return ch == 1 ? max_grid_f1(tw, threads, grid_out)
+                 : max_grid_f2(tw, threads, grid_out);
 }
-
-template cudaError_t launch_solve<float>(const Prob<float>&, const SolveBufs<float>&, const SolveOpts&, int, int, int, cudaStream_t);
-template cudaError_t launch_solve<double>(const Prob<double>&, const SolveBufs<double>&, const SolveOpts&, int, int, int, cudaStream_t);
 
 }  // namespace spock

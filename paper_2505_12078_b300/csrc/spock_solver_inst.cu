@@ -1,0 +1,22 @@
+// spock_solver_inst.cu -- one instantiation of the solver kernel, selected by
+// -DSPOCK_T (float | double) and -DSPOCK_CH (column chunks of the mat-vecs);
+// compiled once per variant so the variants build in parallel.
+#include "spock_solver_kernel.cuh"
+
+#define SPOCK_CAT2(a, b) a##b
+#define SPOCK_CAT(a, b) SPOCK_CAT2(a, b)
+
+namespace spock {
+
+cudaError_t SPOCK_CAT(launch_solve_, SPOCK_SUFFIX)(const Prob<SPOCK_T>& P,
+                                                    const SolveBufs<SPOCK_T>& B,
+                                                    const SolveOpts& o, int tw, int grid,
+                                                    int threads, cudaStream_t s) {
+  return launch_ch<SPOCK_T, SPOCK_CH>(P, B, o, tw, grid, threads, s);
+}
+
+int SPOCK_CAT(max_grid_, SPOCK_SUFFIX)(int tw, int threads, int* out) {
+  return max_grid_ch<SPOCK_T, SPOCK_CH>(tw, threads, out);
+}
+
+}  // namespace spock

@@ -1,0 +1,934 @@
+// spock_solver_kernel.cuh -- the SPOCK iteration as one persistent cooperative kernel.
+//
+// One evaluation of the Chambolle-Pock operator T (Eq. chambolle-pock-operator)
+// is four phases separated by grid barriers:
+//
+//  P (one warp per node): w = z - alpha L* eta for the node's own blocks
+//    (sibling sums of L* read the children's cost blocks), the s0 update
+//    (prox of f's linear term), the S2 projection of (y^i, tau^[i], s^[i]) in
+//    closed form (Sherman-Morrison on GG' = (a^2+3) I + 11'), and the parts of
+//    Alg. 2 that do not depend on the sweep:
+//      h^i = -K_i' ubar^i - xbar^i,  e^i = Rt_i^{-1} ubar^i,  q^leaf = -xbar.
+//  B (backward sweep of Alg. 2, bottom-up over "segments" = chains of
+//    single-child non-leaf nodes, which a team walks without a grid barrier,
+//    carrying q down the chain in shared memory):
+//      v_c = q_c + P_c c_c;  q^i = sum_c Abar_c' v_c + h^i;
+//      d^i = e^i - sum_c (B_c Rt_i^{-1})' v_c.
+//    (Alg. 2's qbar holds the extra term (K' + sum Abar'PB) d, which is zero
+//    because K = -Rt^{-1} sum B'PA; the kernel uses the reduced form.)
+//  F (forward rollout of Alg. 2, top-down over segments):
+//      u^i = K x^i + d^i,  x^c = Abar_c x^i + B_c d^i + c_c.
+//  E (one warp per block of eta): eta+ = prox_{alpha g*}(eta + alpha L(2z+ - z))
+//    with the S3 projections (cones, boxes, ball, translated SOCs).
+// Every phase also accumulates the reductions of r = v - T(v): max|r|,
+// ||r_z||^2, ||r_eta||^2, <r_eta, L r_z>, and the M-inner product with a
+// reference point; they are combined by one group reduction at the end.
+//
+// The SuperMann driver (Alg. 4) with Anderson directions (Alg. 3, m = 3) runs
+// redundantly on every CTA from the group-reduced scalars, so all CTAs take
+// the same branch; there is no host round trip per iteration.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#pragma once
+#include "spock_dev.cuh"
+#include "spock_internal.h"
+
+namespace spock {
+
+constexpr int AA_M = 3;
+constexpr double C0 = 0.99, C1 = 0.99, C2 = 0.99, BETA = 0.5, SIGMA = 0.1, LAMBDA = 1.0;
+
+template <class T>
+__device__ __forceinline__ T refv(const T* vref, long long idx, T old) {
+  return vref ? ldc(vref + idx) : old;
+}
+
+// phase timer of CTA 0 (thread 0): adds the time since the last mark to slot k
+struct PhaseClock {
+  uint64_t t;
+  bool on;
+  __device__ __forceinline__ void start() {
+    on = (blockIdx.x == 0 && threadIdx.x == 0);
+    if (on) t = global_ns();
+  }
+  __device__ __forceinline__ void mark(SolveCtl* ctl, int k) {
+    if (on) {
+      const uint64_t n = global_ns();
+      ctl->prof[k] += n - t;
+      t = n;
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Phase P
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ void s2_block(const Prob<T>& P, int lane, int i, const T* __restrict__ vin,
+                         T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
+  const long long yo = P.o_y + P.yoff[i];
+  const T al = P.alpha, a = P.avar[i];
+  const T eS = ldc(eta + P.e_s + i);
+  const T* ey = eta + P.e_y + P.yoff[i];
+  auto wy = [&](int k) -> T {
+    const T b = (k < m) ? P.prob[c0 + k] : (k == 2 * m ? T(1) : T(0));
+    return ldc(z + yo + k) - al * (ldc(ey + k) - b * eS);
+  };
+  auto wt = [&](int l) -> T {
+    const int c = c0 + l;
+    const T* q = eta + P.e_q + (long long)(c - 1) * P.W;
+    return ldc(z + P.o_tau + c - 1) - al * (T(0.5) * (ldc(q + nx + nu) + ldc(q + nx + nu + 1)));
+  };
+  auto ws = [&](int l) -> T {
+    const int c = c0 + l;
+    T g;
+    if (c < P.n_nl) {
+      g = ldc(eta + P.e_s + c);
+    } else {
+      const T* q = eta + P.e_qN + (long long)(c - P.n_nl) * (nx + 2);
+      g = T(0.5) * (ldc(q + nx) + ldc(q + nx + 1));
+    }
+    return ldc(z + P.o_s + c - 1) - al * g;
+  };
+  const T y3 = wy(2 * m);
+  T sg = 0;
+  for (int l = lane; l < m; l += 32) sg += a * wy(l) - wy(m + l) + y3 - wt(l) - ws(l);
+  sg = warp_sum(sg);
+  const T cc = a * a + T(3);
+  const T corr = sg / (cc + T(m));
+  T sl = 0;
+  for (int l = lane; l < m; l += 32) {
+    const T wy1 = wy(l), wy2 = wy(m + l), wtl = wt(l), wsl = ws(l);
+    const T gv = a * wy1 - wy2 + y3 - wtl - wsl;
+    const T lam = (gv - corr) / cc;
+    sl += lam;
+    const int c = c0 + l;
+    const T n1 = wy1 - a * lam, n2 = wy2 + lam, nt = wtl + lam, ns = wsl + lam;
+    long long idx;
+    idx = yo + l;           { const T o = ldc(z + idx); stc(vout + idx, n1); ra.z(o, n1, refv(vref, idx, o)); }
+    idx = yo + m + l;       { const T o = ldc(z + idx); stc(vout + idx, n2); ra.z(o, n2, refv(vref, idx, o)); }
+    idx = P.o_tau + c - 1;  { const T o = ldc(z + idx); stc(vout + idx, nt); ra.z(o, nt, refv(vref, idx, o)); }
+    idx = P.o_s + c - 1;    { const T o = ldc(z + idx); stc(vout + idx, ns); ra.z(o, ns, refv(vref, idx, o)); }
+  }
+  sl = warp_sum(sl);
+  if (lane == 0) {
+    const long long idx = yo + 2 * m;
+    const T n3 = y3 - sl;
+    const T o = ldc(z + idx);
+    stc(vout + idx, n3);
+    ra.z(o, n3, refv(vref, idx, o));
+    if (i == 0) {   // s0 <- s0 - alpha (eta_s^0) - alpha
+      const T o0 = ldc(z);
+      const T n0 = (o0 - al * eS) - al;
+      stc(vout, n0);
+      ra.z(o0, n0, refv(vref, 0, o0));
+    }
+  }
+}
+
+// one warp (a team of one warp) per non-leaf node
+template <class T, int CH>
+__device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb, T* s_red, int i,
+                             const T* __restrict__ vin, T* __restrict__ vout,
+                             const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
+  const T al = P.alpha;
+  const T* ec = eta + P.e_c + (long long)i * P.n_c;
+  for (int k = tw1.lane; k < nu; k += 32) {
+    T g = 0;
+    if (P.nbu) g += P.gu[k] * ldc(ec + P.nbx + k);
+    if (P.has_ball) g += P.gu[k] * ldc(ec + P.nbox + k);
+    for (int c = c0; c < c1; ++c)
+      g += ldr(P.rh + (long long)(c - 1) * nu + k) * ldc(eta + P.e_q + (long long)(c - 1) * P.W + nx + k);
+    s_in[k] = ldc(z + P.o_u + (long long)i * nu + k) - al * g;
+  }
+  for (int k = tw1.lane; k < nx; k += 32) {
+    T g = P.nbx ? P.gx[k] * ldc(ec + k) : T(0);
+    for (int c = c0; c < c1; ++c)
+      g += ldr(P.qh + (long long)(c - 1) * nx + k) * ldc(eta + P.e_q + (long long)(c - 1) * P.W + k);
+    s_xb[k] = ldc(z + P.o_x + (long long)i * nx + k) - al * g;
+  }
+  __syncwarp();
+  Acc<T, CH> acc;
+  acc.zero();
+  team_mv<T, CH>(tw1, acc, P.MP + (size_t)i * nu * P.ldP, P.ldP, nu, nx + nu, s_in);
+  T* hb = P.hbuf + (long long)i * nx;
+  T* eb = P.ebuf + (long long)i * nu;
+  team_reduce<T, CH>(tw1, acc, nx + nu, s_red, [&](int j, int, T s) {
+    if (j < nx) stc(hb + j, -s - s_xb[j]);
+    else stc(eb + (j - nx), s);
+  });
+  s2_block(P, tw1.lane, i, vin, vout, vref, ra);
+}
+
+template <class T>
+__device__ void prep_leaf(const Prob<T>& P, int lane, int j, const T* __restrict__ vin) {
+  const int nx = P.nx;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  const int jj = j - P.n_nl;
+  const T al = P.alpha;
+  for (int k = lane; k < nx; k += 32) {
+    T g = P.nbx ? P.gN[k] * ldc(eta + P.e_cN + (long long)jj * P.n_cN + k) : T(0);
+    g += ldr(P.qNh + (long long)jj * nx + k) * ldc(eta + P.e_qN + (long long)jj * (nx + 2) + k);
+    const T xbar = ldc(z + P.o_x + (long long)j * nx + k) - al * g;
+    stc(P.qbuf + (long long)j * nx + k, -xbar);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase B: one segment, bottom-up
+// ---------------------------------------------------------------------------
+template <class T, int CH>
+__device__ void backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_qc, T* s_red,
+                                 int s) {
+  constexpr int PT = Acc<T, CH>::D / 32;
+  const int nx = P.nx, nu = P.nu;
+  int i = P.seg_bot[s];
+  const int len = P.seg_len[s];
+  bool carry = false;
+  for (int step = 0; step < len; ++step) {
+    const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
+    const T* h = P.hbuf + (long long)i * nx;
+    const T* e = P.ebuf + (long long)i * nu;
+    T pre[PT];
+#pragma unroll
+    for (int m = 0; m < PT; ++m) {
+      const int j = tm.tid + m * tm.nth;
+      pre[m] = (j < nx) ? ldc(h + j) : ((j < nx + nu) ? ldc(e + (j - nx)) : T(0));
+    }
+    Acc<T, CH> acc;
+    acc.zero();
+    for (int c = c0; c < c1; ++c) {
+      const T* pc = P.Pc + (long long)(c - 1) * nx;
+      if (carry) {
+        for (int k = tm.tid; k < nx; k += tm.nth) s_in[k] = s_qc[k] + ldr(pc + k);
+      } else {
+        for (int k = tm.tid; k < nx; k += tm.nth)
+          s_in[k] = ldc(P.qbuf + (long long)c * nx + k) + ldr(pc + k);
+      }
+      tm.sync();
+      team_mv<T, CH>(tm, acc, P.MB + (size_t)(c - 1) * nx * P.ldB, P.ldB, nx, nx + nu, s_in);
+      tm.sync();
+    }
+    T* q = P.qbuf + (long long)i * nx;
+    T* d = P.dbuf + (long long)i * nu;
+    team_reduce<T, CH>(tm, acc, nx + nu, s_red, [&](int j, int m, T v) {
+      if (j < nx) {
+        const T qq = v + pre[m];
+        stc(q + j, qq);
+        s_qc[j] = qq;
+      } else {
+        stc(d + (j - nx), pre[m] - v);
+      }
+    });
+    carry = true;
+    i = P.anc[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase F: one segment, top-down
+// ---------------------------------------------------------------------------
+template <class T, int CH>
+__device__ void forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_xn, T* s_xb,
+                                T* s_red, int s, const T* __restrict__ vin, T* __restrict__ vout,
+                                const T* __restrict__ vref, RedAcc<T>& ra) {
+  constexpr int PT = Acc<T, CH>::D / 32;
+  const int nx = P.nx, nu = P.nu;
+  int i = P.seg_top[s];
+  const int len = P.seg_len[s];
+  const T* z = vin;
+  if (i == 0) {
+    for (int k = tm.tid; k < nx; k += tm.nth) {
+      const T xn = P.x0s[k];
+      s_xn[k] = xn;
+      const long long idx = P.o_x + k;
+      const T o = ldc(z + idx);
+      stc(vout + idx, xn);
+      ra.z(o, xn, refv(vref, idx, o));
+    }
+  } else {
+    for (int k = tm.tid; k < nx; k += tm.nth) s_xn[k] = ldc(vout + P.o_x + (long long)i * nx + k);
+  }
+  tm.sync();
+  for (int step = 0; step < len; ++step) {
+    const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
+    const T* d = P.dbuf + (long long)i * nu;
+    const long long uo = P.o_u + (long long)i * nu;
+    T dp[PT], uold[PT], uref[PT];
+#pragma unroll
+    for (int m = 0; m < PT; ++m) {
+      const int j = tm.tid + m * tm.nth;
+      const bool ok = j < nu;
+      dp[m] = ok ? ldc(d + j) : T(0);
+      uold[m] = ok ? ldc(z + uo + j) : T(0);
+      uref[m] = (ok && vref) ? ldc(vref + uo + j) : uold[m];
+    }
+    // u^i = K x^i + d^i
+    Acc<T, CH> acc;
+    acc.zero();
+    team_mv<T, CH>(tm, acc, P.KT + (size_t)i * nx * P.ldK, P.ldK, nx, nu, s_xn);
+    team_reduce<T, CH>(tm, acc, nu, s_red, [&](int j, int m, T v) {
+      const T u = v + dp[m];
+      stc(vout + uo + j, u);
+      ra.z(uold[m], u, uref[m]);
+      s_in[nx + j] = dp[m];
+    });
+    for (int k = tm.tid; k < nx; k += tm.nth) s_in[k] = s_xn[k];
+    tm.sync();
+    const bool chain = (step + 1 < len);
+    for (int c = c0; c < c1; ++c) {
+      const long long xo = P.o_x + (long long)c * nx;
+      const T* cv = P.cvec + (long long)(c - 1) * nx;
+      T cp[PT], xold[PT], xref[PT];
+#pragma unroll
+      for (int m = 0; m < PT; ++m) {
+        const int j = tm.tid + m * tm.nth;
+        const bool ok = j < nx;
+        cp[m] = ok ? ldr(cv + j) : T(0);
+        xold[m] = ok ? ldc(z + xo + j) : T(0);
+        xref[m] = (ok && vref) ? ldc(vref + xo + j) : xold[m];
+      }
+      acc.zero();
+      team_mv<T, CH>(tm, acc, P.MF + (size_t)(c - 1) * (nx + nu) * P.ldF, P.ldF, nx + nu, nx, s_in);
+      team_reduce<T, CH>(tm, acc, nx, s_red, [&](int j, int m, T v) {
+        const T xc = v + cp[m];
+        stc(vout + xo + j, xc);
+        ra.z(xold[m], xc, xref[m]);
+        if (chain) s_xb[j] = xc;
+      });
+    }
+    if (chain) {
+      i = c0;
+      T* t = s_xn; s_xn = s_xb; s_xb = t;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase E: eta blocks (one warp each); x, u, y, tau, s of z+ are read from vout
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restrict__ vin,
+                            T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  T* eo = vout + P.nz;
+  const T* er = vref ? vref + P.nz : nullptr;
+  const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
+  const T al = P.alpha;
+  const long long yo = P.o_y + P.yoff[i];
+  const long long ye = P.e_y + P.yoff[i];
+  // y part: (K^i)* = R^{2m}_+ x R
+  for (int e = lane; e < 2 * m + 1; e += 32) {
+    const T Lo = ldc(z + yo + e), Ln = ldc(vout + yo + e), Lr = refv(vref, yo + e, Lo);
+    const T eo_ = ldc(eta + ye + e);
+    const T eb = eo_ + al * (T(2) * Ln - Lo);
+    const T w = eb / al;
+    const T p = (e < 2 * m) ? max(w, T(0)) : w;
+    const T en = eb - al * p;
+    stc(eo + ye + e, en);
+    ra.eta(eo_, en, er ? ldc(er + ye + e) : eo_, Lo, Ln, Lr);
+  }
+  // s part: s^i - b'y^i in R_+
+  {
+    T bo = 0, bn = 0, br = 0;
+    for (int k = lane; k < m; k += 32) {
+      const T p = P.prob[c0 + k];
+      const T o = ldc(z + yo + k);
+      bo += p * o;
+      bn += p * ldc(vout + yo + k);
+      br += p * refv(vref, yo + k, o);
+    }
+    bo = warp_sum(bo); bn = warp_sum(bn); br = warp_sum(br);
+    if (lane == 0) {
+      const long long is = (i == 0) ? 0 : P.o_s + i - 1;
+      const T yo3 = ldc(z + yo + 2 * m);
+      const T so = ldc(z + is);
+      const T Lo = so - bo - yo3;
+      const T Ln = ldc(vout + is) - bn - ldc(vout + yo + 2 * m);
+      const T Lr = vref ? ldc(vref + is) - br - ldc(vref + yo + 2 * m) : Lo;
+      const long long ie = P.e_s + i;
+      const T eo_ = ldc(eta + ie);
+      const T eb = eo_ + al * (T(2) * Ln - Lo);
+      const T en = eb - al * max(eb / al, T(0));
+      stc(eo + ie, en);
+      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, Lo, Ln, Lr);
+    }
+  }
+  if (P.n_c == 0) return;
+  const long long ce = P.e_c + (long long)i * P.n_c;
+  const long long xo = P.o_x + (long long)i * nx;
+  const long long uo = P.o_u + (long long)i * nu;
+  // box rows
+  for (int e = lane; e < P.nbox; e += 32) {
+    T g;
+    long long idx;
+    if (e < P.nbx) {
+      g = P.gx[e]; idx = xo + e;
+    } else {
+      g = P.gu[e - P.nbx]; idx = uo + (e - P.nbx);
+    }
+    const T o = ldc(z + idx);
+    const T Lo = g * o, Ln = g * ldc(vout + idx), Lr = g * refv(vref, idx, o);
+    const T eo_ = ldc(eta + ce + e);
+    const T eb = eo_ + al * (T(2) * Ln - Lo);
+    const T w = eb / al;
+    const T lo = P.box_lo[(long long)i * P.nbox + e], hi = P.box_hi[(long long)i * P.nbox + e];
+    const T p = min(max(w, lo), hi);
+    const T en = eb - al * p;
+    stc(eo + ce + e, en);
+    ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, Lo, Ln, Lr);
+  }
+  // ball rows on u
+  if (P.has_ball) {
+    T n2 = 0;
+    for (int k = lane; k < nu; k += 32) {
+      const T g = P.gu[k];
+      const T eb = ldc(eta + ce + P.nbox + k) + al * (T(2) * g * ldc(vout + uo + k) - g * ldc(z + uo + k));
+      const T w = eb / al;
+      n2 += w * w;
+    }
+    const T nw = sqrt(warp_sum(n2));
+    const T r = P.ball[i];
+    const T sc = (nw > r) ? r / nw : T(1);
+    for (int k = lane; k < nu; k += 32) {
+      const T g = P.gu[k];
+      const T o = ldc(z + uo + k);
+      const T Lo = g * o, Ln = g * ldc(vout + uo + k), Lr = g * refv(vref, uo + k, o);
+      const long long ie = ce + P.nbox + k;
+      const T eo_ = ldc(eta + ie);
+      const T eb = eo_ + al * (T(2) * Ln - Lo);
+      const T w = eb / al;
+      const T en = eb - al * (w * sc);
+      stc(eo + ie, en);
+      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, Lo, Ln, Lr);
+    }
+  }
+}
+
+// translated SOC cost block: a + Pi_SOC(eb/alpha - a), a = (0.., 1/2, -1/2)
+template <class T, int NE, class FL>
+__device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, long long ebase,
+                                          const T* __restrict__ eta, T* __restrict__ eo,
+                                          const T* __restrict__ er, FL&& Lz, RedAcc<T>& ra) {
+  const T al = P.alpha;
+  T ebv[NE];
+  T n2 = 0, tt = 0;
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    ebv[q] = 0;
+    if (e < dim) {
+      T Lo, Ln, Lr;
+      Lz(e, Lo, Ln, Lr);
+      const T eb = ldc(eta + ebase + e) + al * (T(2) * Ln - Lo);
+      ebv[q] = eb;
+      const T ae = (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
+      const T w = eb / al - ae;
+      if (e < dim - 1) n2 += w * w;
+      else tt = w;
+    }
+  }
+  const T nw = sqrt(warp_sum(n2));
+  const T t = __shfl_sync(0xffffffffu, tt, (dim - 1) & 31);
+  // case 0: inside (keep), 1: polar (zero), 2: boundary
+  const int cs = (nw <= t) ? 0 : ((nw <= -t) ? 1 : 2);
+  const T f = (nw + t) / T(2);
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    if (e < dim) {
+      T Lo, Ln, Lr;
+      Lz(e, Lo, Ln, Lr);
+      const T eb = ebv[q];
+      const T ae = (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
+      const T w = eb / al - ae;
+      T ps;
+      if (cs == 0) ps = w;
+      else if (cs == 1) ps = T(0);
+      else ps = (e < dim - 1) ? w * (f / nw) : f;
+      const T en = eb - al * (ae + ps);
+      const T eo_ = ldc(eta + ebase + e);
+      stc(eo + ebase + e, en);
+      ra.eta(eo_, en, er ? ldc(er + ebase + e) : eo_, Lo, Ln, Lr);
+    }
+  }
+}
+
+template <class T, int NE>
+__device__ void eta_soc(const Prob<T>& P, int lane, int c, const T* __restrict__ vin,
+                        T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu;
+  const int i = P.anc[c];
+  const T* z = vin;
+  const long long xo = P.o_x + (long long)i * nx, uo = P.o_u + (long long)i * nu;
+  const long long it = P.o_tau + c - 1;
+  const T* qh = P.qh + (long long)(c - 1) * nx;
+  const T* rh = P.rh + (long long)(c - 1) * nu;
+  auto Lz = [&](int e, T& Lo, T& Ln, T& Lr) {
+    long long idx;
+    T g;
+    if (e < nx) {
+      g = ldr(qh + e); idx = xo + e;
+    } else if (e < nx + nu) {
+      g = ldr(rh + (e - nx)); idx = uo + (e - nx);
+    } else {
+      g = T(0.5); idx = it;
+    }
+    const T o = ldc(z + idx);
+    Lo = g * o; Ln = g * ldc(vout + idx); Lr = g * refv(vref, idx, o);
+  };
+  soc_block<T, NE>(P, lane, P.W, P.e_q + (long long)(c - 1) * P.W, vin + P.nz, vout + P.nz,
+                   vref ? vref + P.nz : nullptr, Lz, ra);
+}
+
+template <class T, int NE>
+__device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict__ vin,
+                         T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  T* eo = vout + P.nz;
+  const T* er = vref ? vref + P.nz : nullptr;
+  const int jj = j - P.n_nl;
+  const long long xo = P.o_x + (long long)j * nx;
+  const T al = P.alpha;
+  if (P.nbx) {
+    const long long ce = P.e_cN + (long long)jj * P.n_cN;
+    for (int e = lane; e < nx; e += 32) {
+      const T g = P.gN[e], o = ldc(z + xo + e);
+      const T Lo = g * o, Ln = g * ldc(vout + xo + e), Lr = g * refv(vref, xo + e, o);
+      const T eo_ = ldc(eta + ce + e);
+      const T eb = eo_ + al * (T(2) * Ln - Lo);
+      const T w = eb / al;
+      const T p = min(max(w, P.boxN_lo[(long long)jj * nx + e]), P.boxN_hi[(long long)jj * nx + e]);
+      const T en = eb - al * p;
+      stc(eo + ce + e, en);
+      ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, Lo, Ln, Lr);
+    }
+  }
+  const long long is = P.o_s + j - 1;
+  const T* qNh = P.qNh + (long long)jj * nx;
+  auto Lz = [&](int e, T& Lo, T& Ln, T& Lr) {
+    long long idx;
+    T g;
+    if (e < nx) {
+      g = ldr(qNh + e); idx = xo + e;
+    } else {
+      g = T(0.5); idx = is;
+    }
+    const T o = ldc(z + idx);
+    Lo = g * o; Ln = g * ldc(vout + idx); Lr = g * refv(vref, idx, o);
+  };
+  soc_block<T, NE>(P, lane, nx + 2, P.e_qN + (long long)jj * (nx + 2), eta, eo, er, Lz, ra);
+}
+
+// ---------------------------------------------------------------------------
+// group reduction of the per-thread partials into ctl->red (every CTA reads)
+// max_slot: index of the slot reduced by max (-1: every slot is a sum)
+// ---------------------------------------------------------------------------
+__device__ bool group_reduce(double (&v)[NRED], double* partials, SolveCtl* ctl, Grid& g,
+                             int max_slot) {
+  __shared__ double scratch[NRED * 32];
+  block_reduce_red(v, scratch, max_slot);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NRED; ++k) stc(partials + (long long)blockIdx.x * NRED + k, v[k]);
+  const bool ok = grid_sync(g, [&]() {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < NRED) {
+      const bool mx = (w == max_slot);
+      double s = 0.0;
+      for (int r = lane; r < (int)gridDim.x; r += 32) {
+        const double x = ldc(partials + (long long)r * NRED + w);
+        s = mx ? fmax(s, x) : s + x;
+      }
+      s = mx ? warp_max(s) : warp_sum(s);
+      if (lane == 0) stc(&ctl->red[w], s);
+    }
+  });
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) v[k] = ldc(&ctl->red[k]);
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// shared memory views: per warp (phase P) and per team (phases B, F)
+// ---------------------------------------------------------------------------
+template <class T, int CH>
+struct Views {
+  static constexpr int D = Acc<T, CH>::D;
+  T* base;
+  int tw;
+  // per warp: in, xb, red  (3 D)
+  __device__ T* w_in(int w) const { return base + (size_t)w * 3 * D; }
+  __device__ T* w_xb(int w) const { return base + (size_t)w * 3 * D + D; }
+  __device__ T* w_red(int w) const { return base + (size_t)w * 3 * D + 2 * D; }
+  // per team: in, xn, xb, qc, red (tw D)
+  __device__ T* t_base(int t) const { return base + (size_t)t * (4 + tw) * D; }
+  static size_t bytes(int threads, int tw) {
+    const int warps = threads / 32, teams = warps / tw;
+    const size_t a = (size_t)warps * 3 * D, b = (size_t)teams * (4 + tw) * D;
+    return (a > b ? a : b) * sizeof(T);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// one evaluation of T: v_out = T(v_in); reduction with reference point vref
+// ---------------------------------------------------------------------------
+template <class T, int CH>
+__device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, int tg, int nt,
+                      const T* __restrict__ vin, T* __restrict__ vout, const T* __restrict__ vref,
+                      double (&red)[NRED], double* partials, SolveCtl* ctl, Grid& g) {
+  constexpr int D = Acc<T, CH>::D;
+  constexpr int NE = (D + 2 + 31) / 32;
+  RedAcc<T> ra;
+  ra.zero();
+  PhaseClock pc;
+  pc.start();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  Team w1;
+  w1.tw = 1; w1.id = wid; w1.warp = 0; w1.lane = lane; w1.tid = lane; w1.nth = 32;
+  auto nop = []() {};
+  // P
+  for (int node = gw; node < P.n; node += nw) {
+    if (node < P.n_nl)
+      prep_nonleaf<T, CH>(P, w1, sv.w_in(wid), sv.w_xb(wid), sv.w_red(wid), node, vin, vout, vref, ra);
+    else
+      prep_leaf(P, lane, node, vin);
+    __syncwarp();
+  }
+  if (!grid_sync(g, nop)) return false;
+  pc.mark(ctl, 0);
+  // B
+  {
+    T* tb = sv.t_base(tm.id);
+    for (int l = 0; l < P.n_levels; ++l) {
+      for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt)
+        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, s);
+      if (!grid_sync(g, nop)) return false;
+    }
+  }
+  pc.mark(ctl, 1);
+  // F
+  {
+    T* tb = sv.t_base(tm.id);
+    for (int l = P.n_levels - 1; l >= 0; --l) {
+      for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt)
+        forward_segment<T, CH>(P, tm, tb, tb + D, tb + 2 * D, tb + 4 * D, s, vin, vout, vref, ra);
+      if (!grid_sync(g, nop)) return false;
+    }
+  }
+  pc.mark(ctl, 2);
+  // E
+  {
+    const long long nb = (long long)P.n_nl + (P.n - 1) + P.n_l;
+    for (long long b = gw; b < nb; b += nw) {
+      if (b < P.n_nl) {
+        eta_nonleaf(P, lane, (int)b, vin, vout, vref, ra);
+      } else if (b < P.n_nl + P.n - 1) {
+        eta_soc<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);
+      } else {
+        eta_leaf<T, NE>(P, lane, (int)(b - P.n_nl - (P.n - 1) + P.n_nl), vin, vout, vref, ra);
+      }
+    }
+  }
+  double v[NRED];
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) v[k] = (double)ra.v[k];
+  const bool ok = group_reduce(v, partials, ctl, g, R_MAX);
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) red[k] = v[k];
+  pc.mark(ctl, 3);
+  if (pc.on) ctl->prof[7] += 1;
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// the solve kernel
+// ---------------------------------------------------------------------------
+template <class T, int CH>
+__global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, SolveOpts o, int tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const Team tm = make_team(tw);
+  const int teams_per_cta = (blockDim.x >> 5) / tw;
+  const int tg = blockIdx.x * teams_per_cta + tm.id;
+  const int nt = gridDim.x * teams_per_cta;
+  Views<T, CH> sv;
+  sv.base = reinterpret_cast<T*>(smraw);
+  sv.tw = tw;
+  SolveCtl* ctl = B.ctl;
+  Grid g;
+  g.ctl = &ctl->bar;
+  g.epoch = 0;
+  T* buf[4] = {B.V, B.TV, B.VT, B.TVT};
+  int iV = 0, iTV = 1, iVT = 2, iTVT = 3;
+  const long long nv = P.nv;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  const T al = P.alpha;
+  double red[NRED];
+  int status = 0, k = 0, nT = 0, nK0 = 0, nK1 = 0, nK2 = 0, nFB = 0, nBT = 0;
+  double res, om2;
+  bool ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+  ++nT;
+  if (!ok) goto fail;
+  res = red[R_MAX];
+  om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
+  if (o.method == 2) goto done;
+  if (o.method == 1) {
+    while (!(res <= o.tol) && k < o.max_iters) {
+      int t = iV; iV = iTV; iTV = t;
+      ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+      ++nT; ++k;
+      if (!ok) goto fail;
+      res = red[R_MAX];
+      om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
+    }
+    status = (res <= o.tol) ? 0 : 1;
+    goto done;
+  }
+  {
+    double zeta = sqrt(fmax(om2, 0.0)), omega_safe = zeta;
+    double G[AA_M][AA_M];
+    for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) G[a][b] = 0.0;
+    int count = 0, head = 0;
+    while (true) {
+      if (res <= o.tol) { status = 0; break; }
+      if (k >= o.max_iters) { status = 1; break; }
+      const double omega = sqrt(fmax(om2, 0.0));
+      T* V = buf[iV];
+      T* TV = buf[iTV];
+      PhaseClock pc;
+      pc.start();
+      // --- Anderson memory update (pairs (v^k - v^{k-1}, r^k - r^{k-1})) ---
+      double kap[AA_M] = {0.0, 0.0, 0.0};
+      bool use_aa = false;
+      {
+        const int slot = head;
+        const bool push = (k >= 1);
+        double dd[NRED];
+        T acc[2 * AA_M];
+        for (int a = 0; a < 2 * AA_M; ++a) acc[a] = 0;
+        for (long long e = gtid; e < nv; e += gstride) {
+          const T v = ldc(V + e), r = v - ldc(TV + e);
+          if (push) {
+            const T s_ = v - ldc(B.VP + e);
+            const T y_ = r - ldc(B.RP + e);
+            stc(B.S + slot * nv + e, s_);
+            stc(B.Y + slot * nv + e, y_);
+#pragma unroll
+            for (int l = 0; l < AA_M; ++l) {
+              const T yl = (l == slot) ? y_ : ldc(B.Y + l * nv + e);
+              acc[l] = fma(y_, yl, acc[l]);
+              acc[AA_M + l] = fma(yl, r, acc[AA_M + l]);
+            }
+          }
+          stc(B.VP + e, v);
+          stc(B.RP + e, r);
+        }
+        for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? (double)acc[a] : 0.0;
+        if (!group_reduce(dd, B.partials, ctl, g, -1)) goto fail;
+        double bvec[AA_M];
+        if (push) {
+          if (count < AA_M) ++count;
+          head = (head + 1) % AA_M;
+          for (int l = 0; l < AA_M; ++l) { G[slot][l] = dd[l]; G[l][slot] = dd[l]; }
+        }
+        for (int l = 0; l < AA_M; ++l) bvec[l] = dd[AA_M + l];
+        if (k > AA_M && count > 0) {
+          // logical order oldest -> newest
+          int ord[AA_M];
+          const int start = (count < AA_M) ? 0 : head;
+          for (int j = 0; j < count; ++j) ord[j] = (start + j) % AA_M;
+          double Rm[AA_M][AA_M], bb[AA_M], tr = 0.0;
+          for (int j = 0; j < count; ++j) tr += G[ord[j]][ord[j]];
+          const double lim = o.rank_tol * sqrt(fmax(tr, 0.0));
+          bool good = tr > 0.0;
+          for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) Rm[a][b] = 0.0;
+          for (int j = 0; j < count && good; ++j) {
+            double dj = G[ord[j]][ord[j]];
+            for (int l = 0; l < j; ++l) dj -= Rm[l][j] * Rm[l][j];
+            if (!(dj > 0.0) || sqrt(dj) < lim) { good = false; break; }
+            Rm[j][j] = sqrt(dj);
+            for (int c = j + 1; c < count; ++c) {
+              double s = G[ord[j]][ord[c]];
+              for (int l = 0; l < j; ++l) s -= Rm[l][j] * Rm[l][c];
+              Rm[j][c] = s / Rm[j][j];
+            }
+          }
+          if (good) {
+            // R'R kappa = Y'r : forward then backward substitution
+            for (int j = 0; j < count; ++j) {
+              double s = bvec[ord[j]];
+              for (int l = 0; l < j; ++l) s -= Rm[l][j] * bb[l];
+              bb[j] = s / Rm[j][j];
+            }
+            double kl[AA_M];
+            for (int j = count - 1; j >= 0; --j) {
+              double s = bb[j];
+              for (int l = j + 1; l < count; ++l) s -= Rm[j][l] * kl[l];
+              kl[j] = s / Rm[j][j];
+            }
+            for (int j = 0; j < count; ++j) kap[ord[j]] = kl[j];
+            use_aa = true;
+          }
+        }
+      }
+      pc.mark(ctl, 4);
+      // --- psi and the first trial point v~ = v + psi ---
+      {
+        T* VT = buf[iVT];
+        const T k0 = (T)kap[0], k1 = (T)kap[1], k2 = (T)kap[2];
+        for (long long e = gtid; e < nv; e += gstride) {
+          const T v = ldc(V + e), r = v - ldc(TV + e);
+          T psi = -r;
+          if (use_aa) {
+            psi -= (ldc(B.S + e) - ldc(B.Y + e)) * k0;
+            psi -= (ldc(B.S + nv + e) - ldc(B.Y + nv + e)) * k1;
+            psi -= (ldc(B.S + 2 * nv + e) - ldc(B.Y + 2 * nv + e)) * k2;
+          }
+          stc(B.PSI + e, psi);
+          stc(VT + e, v + psi);
+        }
+      }
+      if (!grid_sync(g, []() {})) goto fail;
+      pc.mark(ctl, 5);
+      ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
+      ++nT;
+      if (!ok) goto fail;
+      if (omega <= C0 * zeta) {                       // K0
+        int t = iV; iV = iVT; iVT = t;
+        t = iTV; iTV = iTVT; iTVT = t;
+        zeta = omega;
+        res = red[R_MAX];
+        om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
+        ++nK0; ++k;
+        continue;
+      }
+      double tau = 1.0;
+      int bt = 0;
+      while (true) {
+        const double om2t = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
+        const double omt = sqrt(fmax(om2t, 0.0));
+        if ((omega <= omega_safe && omt <= C1 * omega) || omt == 0.0) {   // K1
+          int t = iV; iV = iVT; iVT = t;
+          t = iTV; iTV = iTVT; iTVT = t;
+          omega_safe = omt + pow(C2, (double)k);
+          res = red[R_MAX];
+          om2 = om2t;
+          ++nK1;
+          break;
+        }
+        const double mdot = red[R_ZD] + red[R_ED] - (double)al * red[R_LZD] - (double)al * red[R_ELD];
+        const double rho = om2t - mdot;
+        PhaseClock pk;
+        pk.start();
+        if (rho >= SIGMA * omt * omega) {             // K2
+          const T coef = (T)(LAMBDA * rho / om2t);
+          T* Vc = buf[iV];
+          T* VT = buf[iVT];
+          const T* TVT = buf[iTVT];
+          for (long long e = gtid; e < nv; e += gstride) {
+            const T vt = ldc(VT + e);
+            stc(VT + e, ldc(Vc + e) - coef * (vt - ldc(TVT + e)));
+          }
+          if (!grid_sync(g, []() {})) goto fail;
+          pk.mark(ctl, 6);
+          int t = iV; iV = iVT; iVT = t;
+          ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+          ++nT;
+          if (!ok) goto fail;
+          res = red[R_MAX];
+          om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
+          ++nK2;
+          break;
+        }
+        ++bt; ++nBT;
+        if (bt >= o.max_backtracks) {                 // fall back to v <- T(v)
+          int t = iV; iV = iTV; iTV = t;
+          ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+          ++nT;
+          if (!ok) goto fail;
+          res = red[R_MAX];
+          om2 = red[R_ZZ] + red[R_EE] - 2.0 * (double)al * red[R_ELZ];
+          ++nFB;
+          break;
+        }
+        tau *= BETA;
+        {
+          const T tt = (T)tau;
+          const T* Vc = buf[iV];
+          T* VT = buf[iVT];
+          for (long long e = gtid; e < nv; e += gstride) stc(VT + e, ldc(Vc + e) + tt * ldc(B.PSI + e));
+        }
+        if (!grid_sync(g, []() {})) goto fail;
+        pk.mark(ctl, 6);
+        ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
+        ++nT;
+        if (!ok) goto fail;
+      }
+      ++k;
+    }
+  }
+done:
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->status = status;
+    ctl->iters = k; ctl->n_T = nT; ctl->n_K0 = nK0; ctl->n_K1 = nK1; ctl->n_K2 = nK2;
+    ctl->n_fb = nFB; ctl->n_bt = nBT;
+    ctl->res_inf = res;
+    for (int q = 0; q < NRED; ++q) ctl->stats[q] = red[q];
+    ctl->final_v = iV;       // final buffer indices for the host
+    ctl->final_tv = iTV;
+  }
+  return;
+fail:
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->status = -5;
+    ctl->iters = k; ctl->n_T = nT;
+    ctl->final_v = iV;
+    ctl->final_tv = iTV;
+  }
+}
+
+template <class T, int CH>
+cudaError_t launch_ch(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
+                             int grid, int threads, cudaStream_t s) {
+  const size_t smem = Views<T, CH>::bytes(threads, tw);
+  cudaError_t e = cudaFuncSetAttribute(k_solve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  Prob<T> Pc = P;
+  SolveBufs<T> Bc = B;
+  SolveOpts oc = o;
+  int twc = tw;
+  void* args[] = {&Pc, &Bc, &oc, &twc};
+  return cudaLaunchCooperativeKernel((void*)k_solve<T, CH>, dim3(grid), dim3(threads), args, smem, s);
+}
+
+template <class T, int CH>
+int max_grid_ch(int tw, int threads, int* out) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = Views<T, CH>::bytes(threads, tw);
+  cudaFuncSetAttribute(k_solve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve<T, CH>, threads, smem) != cudaSuccess)
+    return -1;
+  *out = nsm * per;
+  return 0;
+}
+
+}  // namespace spock
