@@ -45,7 +45,7 @@ struct DevMem {
 
 template <class T>
 struct Iter {   // per-precision iteration data
-  T *MB = nullptr, *MF = nullptr, *MP = nullptr, *KT = nullptr, *cvec = nullptr, *Pc = nullptr;
+  T *MB = nullptr, *MF = nullptr, *MP = nullptr, *KT = nullptr, *cvec = nullptr, *kc = nullptr;
   T *qh = nullptr, *rh = nullptr, *qNh = nullptr, *gx = nullptr, *gu = nullptr, *gN = nullptr;
   T *box_lo = nullptr, *box_hi = nullptr, *boxN_lo = nullptr, *boxN_hi = nullptr, *ball = nullptr;
   T *prob = nullptr, *avar = nullptr, *x0s = nullptr;
@@ -68,6 +68,7 @@ struct spock_problem {
   double a_con = 1, a_conN = 1, alpha = 0, normL = 0;
   int max_items = 1;
   int tw = 8;
+  int use_pipe = 1;    // stream the sweep matrices through shared memory
   DevMem mem;
   // device tree / schedule
   int *d_anc, *d_ch_off, *d_yoff, *d_ynode, *d_lvl_off, *d_seg_top, *d_seg_bot, *d_seg_len;
@@ -198,7 +199,7 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.anc = p->d_anc; P.ch_off = p->d_ch_off; P.yoff = p->d_yoff;
   P.n_levels = (int)p->lvl_off.size() - 1;
   P.lvl_off = p->d_lvl_off; P.seg_top = p->d_seg_top; P.seg_bot = p->d_seg_bot; P.seg_len = p->d_seg_len;
-  P.MB = it.MB; P.MF = it.MF; P.MP = it.MP; P.KT = it.KT; P.cvec = it.cvec; P.Pc = it.Pc;
+  P.MB = it.MB; P.MF = it.MF; P.MP = it.MP; P.KT = it.KT; P.cvec = it.cvec; P.kc = it.kc;
   P.qh = it.qh; P.rh = it.rh; P.qNh = it.qNh; P.gx = it.gx; P.gu = it.gu; P.gN = it.gN;
   P.box_lo = it.box_lo; P.box_hi = it.box_hi; P.boxN_lo = it.boxN_lo; P.boxN_hi = it.boxN_hi;
   P.ball = it.ball; P.prob = it.prob; P.avar = it.avar; P.x0s = it.x0s;
@@ -215,7 +216,7 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
   it.MP = m.alloc<T>((long long)n_nl * nu * p->ldP);
   it.KT = m.alloc<T>((long long)n_nl * nx * p->ldK);
   it.cvec = m.alloc<T>((long long)(n - 1) * nx);
-  it.Pc = m.alloc<T>((long long)(n - 1) * nx);
+  it.kc = m.alloc<T>((long long)n_nl * (nx + nu));
   it.qh = m.alloc<T>((long long)(n - 1) * nx);
   it.rh = m.alloc<T>((long long)(n - 1) * nu);
   it.qNh = m.alloc<T>((long long)n_l * nx);
@@ -296,14 +297,32 @@ int pick_tw(int nx, int nu) {
   return 1;
 }
 
+// Bytes of the largest per-node matrix streamed through shared memory by the
+// sweeps, or 0 when two of them per team do not fit (then the sweeps read the
+// matrices from global memory).
+template <class T>
+int pipe_bytes_for(const spock_problem* p) {
+  const long long e = std::max({(long long)p->nx * p->ldB, (long long)(p->nx + p->nu) * p->ldF,
+                                (long long)p->nx * p->ldK});
+  const int b = (int)(e * (long long)sizeof(T));
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int prec = sizeof(T) == 8 ? 64 : 32;
+  const size_t need = solver_smem_bytes(prec, p->tw, kThreads, p->nx + p->nu, b) + 4096;
+  return (need <= (size_t)optin) ? b : 0;
+}
+
 template <class T>
 int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t st, SolveCtl* h_ctl,
                float* ms) {
   int rc = ensure_bufs(p, it);
   if (rc) return rc;
   const int prec = sizeof(T) == 8 ? 64 : 32;
+  it.P.pipe_bytes = p->use_pipe ? pipe_bytes_for<T>(p) : 0;
   int maxg = 0;
-  if (solver_max_grid(prec, p->tw, kThreads, p->nx + p->nu, &maxg) || maxg <= 0) return SPOCK_EDEVICE;
+  if (solver_max_grid(prec, p->tw, kThreads, p->nx + p->nu, it.P.pipe_bytes, &maxg) || maxg <= 0)
+    return SPOCK_EDEVICE;
   const int teams = (kThreads / 32) / p->tw;
   int grid = (p->max_items + teams - 1) / teams;
   if (grid > maxg) grid = maxg;
@@ -488,6 +507,7 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   double* dKA = tmp.alloc<double>((long long)n_nl * nu * nx);
   double* dBtP = tmp.alloc<double>((long long)n * nu * nx);
   double* dPAb = tmp.alloc<double>((long long)n * nx * nx);
+  double* dPcs = tmp.alloc<double>((long long)(n - 1) * nx);
   int* derr = tmp.alloc<int>(1);
   unsigned long long* dnorm = tmp.alloc<unsigned long long>(1);
   rc = alloc_iter<double>(p, p->f64);
@@ -509,7 +529,7 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   a.P = p->d_P; a.K = p->d_K; a.Rt = p->d_Rt; a.Lc = dLc; a.Linv = dLi; a.Rinv = dRi; a.KA = dKA;
   a.BtP = dBtP; a.PAb = dPAb; a.Abar = p->d_Abar; a.err = derr;
   Iter<double>& f = p->f64;
-  a.MB = f.MB; a.MF = f.MF; a.MP = f.MP; a.KT = f.KT; a.Pc = f.Pc;
+  a.MB = f.MB; a.MF = f.MF; a.MP = f.MP; a.KT = f.KT; a.Pc = dPcs; a.kc = f.kc;
   a.qh = f.qh; a.rh = f.rh; a.qNh = f.qNh; a.gx = f.gx; a.gu = f.gu; a.gN = f.gN;
   a.box_lo = f.box_lo; a.box_hi = f.box_hi; a.boxN_lo = f.boxN_lo; a.boxN_hi = f.boxN_hi; a.ball = f.ball;
   cudaStream_t st = 0;
@@ -535,13 +555,13 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   Iter<float>& g = p->f32;
   const long long cnt[] = {(long long)(n - 1) * nx * p->ldB, (long long)(n - 1) * (nx + nu) * p->ldF,
                            (long long)n_nl * nu * p->ldP, (long long)n_nl * nx * p->ldK,
-                           (long long)(n - 1) * nx, (long long)(n - 1) * nx, (long long)(n - 1) * nx,
+                           (long long)(n - 1) * nx, (long long)n_nl * (nx + nu), (long long)(n - 1) * nx,
                            (long long)(n - 1) * nu, (long long)n_l * nx, nx, nu, nx,
                            (long long)n_nl * std::max(1, p->nbox), (long long)n_nl * std::max(1, p->nbox),
                            (long long)n_l * nx, (long long)n_l * nx, n_nl, n, n_nl};
-  const double* src[] = {f.MB, f.MF, f.MP, f.KT, f.cvec, f.Pc, f.qh, f.rh, f.qNh, f.gx, f.gu, f.gN,
+  const double* src[] = {f.MB, f.MF, f.MP, f.KT, f.cvec, f.kc, f.qh, f.rh, f.qNh, f.gx, f.gu, f.gN,
                          f.box_lo, f.box_hi, f.boxN_lo, f.boxN_hi, f.ball, f.prob, f.avar};
-  float* dst[] = {g.MB, g.MF, g.MP, g.KT, g.cvec, g.Pc, g.qh, g.rh, g.qNh, g.gx, g.gu, g.gN,
+  float* dst[] = {g.MB, g.MF, g.MP, g.KT, g.cvec, g.kc, g.qh, g.rh, g.qNh, g.gx, g.gu, g.gN,
                   g.box_lo, g.box_hi, g.boxN_lo, g.boxN_hi, g.ball, g.prob, g.avar};
   for (int q = 0; q < 19 && e == cudaSuccess; ++q) e = launch_convert_f64_f32(src[q], dst[q], cnt[q], st);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

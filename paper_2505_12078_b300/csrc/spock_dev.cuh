@@ -45,7 +45,10 @@ struct Prob {
   const T* MP;   // per non-leaf i: [K_i | Rt_i^{-1}]             nu x ldP   (input: ubar)
   const T* KT;   // per non-leaf i: K_i^T                        nx x ldK   (input: x)
   const T* cvec; // per non-root: scaled c (nx)
-  const T* Pc;   // per non-root: P_c c_c (nx)
+  const T* kc;   // per non-leaf i: sum_c MB_c' (P_c c_c) (nx + nu), the constant part of
+                 // the backward recursion added to h^i and subtracted from e^i
+  int pipe_bytes;  // largest per-node matrix in bytes when it is streamed through
+                   // shared memory (0: matrices read from global memory)
   // cost and constraint data (scaled, Sec. 5.4)
   const T* qh;   // per non-root: diag of Q^{1/2} S^{-1} (nx)
   const T* rh;   // per non-root: diag of R^{1/2} Su^{-1} (nu)
@@ -137,7 +140,22 @@ struct Acc {
 // over the team's warps (warp w takes rows w, w+tw, ...), columns over lanes.
 // Loads of RB rows are issued before their FMAs so a warp has RB*CH 16-byte
 // loads in flight.
-template <class T, int CH>
+template <class T>
+__device__ __forceinline__ void vload_s(const T* p, T (&o)[Vec<T>::N]);
+template <>
+__device__ __forceinline__ void vload_s<float>(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void vload_s<double>(const double* p, double (&o)[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  o[0] = v.x; o[1] = v.y;
+}
+
+// SMEM = true: M lives in shared memory (filled by a bulk copy); false: M is
+// read-only global memory read through the non-coherent path.
+template <class T, int CH, bool SMEM = false>
 __device__ __forceinline__ void team_mv(const Team& tm, Acc<T, CH>& acc, const T* __restrict__ M,
                                         int ld, int nrows, int ncols, const T* in) {
   constexpr int VEC = Vec<T>::N;
@@ -156,7 +174,8 @@ __device__ __forceinline__ void team_mv(const Team& tm, Acc<T, CH>& acc, const T
       for (int c = 0; c < CH; ++c) {
         const int col = (c * 32 + tm.lane) * VEC;
         if (okr && col < ncols) {
-          vload<T>(row + col, m[r][c]);
+          if (SMEM) vload_s<T>(row + col, m[r][c]);
+          else vload<T>(row + col, m[r][c]);
         } else {
 #pragma unroll
           for (int e = 0; e < VEC; ++e) m[r][c][e] = T(0);
@@ -368,5 +387,89 @@ __device__ __forceinline__ bool grid_sync(Grid& g, F&& last_cb) {
   }
   return flag == 2;
 }
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk copy (cp.async.bulk, global -> shared) with a bounded wait
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the mbarrier; false (and *err set) after the
+// time limit. A second bounded wait lets a late copy land before the caller
+// leaves, so no copy into this CTA's shared memory is left in flight.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+  unsigned spins = 0;
+  uint64_t t0 = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0u) {
+      const uint64_t t = global_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > BARRIER_LIMIT_NS) {
+        atomicExch(err, 2);
+        const uint64_t t1 = global_ns();
+        while (!mbar_try_wait(bar, parity) && global_ns() - t1 < BARRIER_LIMIT_NS) {
+        }
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// Double-buffered stream of per-node matrices into a team's shared memory.
+// Thread 0 of the team issues the copies; every thread waits. par[] keeps the
+// phase of each buffer's mbarrier for the whole launch.
+template <class T>
+struct Pipe {
+  uint64_t* bar;     // 2 mbarriers
+  T* buf[2];
+  unsigned par[2];
+  int cur;
+  bool on;           // false: matrices are read from global memory
+  __device__ __forceinline__ void issue(const Team& tm, int b, const T* src, unsigned bytes) {
+    if (tm.tid == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(bar + b, bytes);
+      bulk_g2s(buf[b], src, bytes, bar + b);
+    }
+  }
+  __device__ __forceinline__ bool wait(int b, int* err) {
+    const bool ok = mbar_wait(bar + b, par[b], err);
+    par[b] ^= 1u;
+    return ok;
+  }
+};
 
 }  // namespace spock

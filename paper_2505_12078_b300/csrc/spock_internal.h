@@ -23,7 +23,7 @@ struct SetupArgs {
   double *P, *K, *Rt, *Lc, *Linv, *Rinv, *KA, *BtP, *PAb, *Abar;
   int* err;
   // iteration data (FP64)
-  double *MB, *MF, *MP, *KT, *Pc;
+  double *MB, *MF, *MP, *KT, *Pc, *kc;
   double *qh, *rh, *qNh, *gx, *gu, *gN, *box_lo, *box_hi, *boxN_lo, *boxN_hi, *ball;
 };
 
@@ -79,6 +79,8 @@ struct SolveBufs {
 template <class T>
 cudaError_t launch_solve(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
                          int grid, int threads, cudaStream_t s);
-int solver_max_grid(int precision, int tw, int threads, int D, int* grid_out);
+int solver_max_grid(int precision, int tw, int threads, int D, int pipe_bytes, int* grid_out);
+size_t solver_smem_bytes(int precision, int tw, int threads, int D, int pipe_bytes);
+int solver_chunks(int precision, int width);
 
 }  // namespace spock

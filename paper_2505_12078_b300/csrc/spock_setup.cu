@@ -294,6 +294,27 @@ __global__ void k_build_Pc(int n, int nx, const double* __restrict__ P,
   }
 }
 
+// kc_i = sum_c MB_c' (P_c c_c): the part of the backward recursion of Alg. 2
+// that does not depend on the iterate (zero when every c = 0)
+__global__ void k_build_kc(int n_nl, int nx, int nu, int ld, const int* __restrict__ ch_off,
+                           const double* __restrict__ MB, const double* __restrict__ Pc,
+                           double* __restrict__ kc) {
+  const int w = nx + nu;
+  const long long tot = (long long)n_nl * w;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / w;
+    const int j = (int)(e % w);
+    double s = 0.0;
+    for (int c = ch_off[i]; c < ch_off[i + 1]; ++c) {
+      const double* M = MB + (long long)(c - 1) * nx * ld;
+      const double* p = Pc + (long long)(c - 1) * nx;
+      for (int k = 0; k < nx; ++k) s += M[(long long)k * ld + j] * p[k];
+    }
+    kc[e] = s;
+  }
+}
+
 // cost square roots, constraint coefficients and scaled sets (Sec. 5.4)
 __global__ void k_cost_con(int n, int n_nl, int nx, int nu, int nbx, int nbu, int has_ball,
                            const int* __restrict__ anc, const double* __restrict__ Sx,
@@ -549,6 +570,8 @@ cudaError_t launch_build(const SetupArgs& a, cudaStream_t s) {
       a.n_nl, a.nx, a.nu, a.ldP, a.ldK, a.K, a.Rinv, a.MP, a.KT);
   k_build_Pc<<<grid_for((long long)(a.n - 1) * a.nx, 256), 256, 0, s>>>(a.n, a.nx, a.P, a.ct,
                                                                        a.Pc);
+  k_build_kc<<<grid_for((long long)a.n_nl * (a.nx + a.nu), 256), 256, 0, s>>>(
+      a.n_nl, a.nx, a.nu, a.ldB, a.ch_off, a.MB, a.Pc, a.kc);
   const long long tot = (long long)(a.n - 1) * (a.nx + a.nu) + (long long)(a.n - a.n_nl) * a.nx * 2 +
                         2 * a.nx + a.nu + (long long)a.n_nl * (a.nbx + a.nbu + 1);
   k_cost_con<<<grid_for(tot, 256), 256, 0, s>>>(

@@ -162,9 +162,10 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
   team_mv<T, CH>(tw1, acc, P.MP + (size_t)i * nu * P.ldP, P.ldP, nu, nx + nu, s_in);
   T* hb = P.hbuf + (long long)i * nx;
   T* eb = P.ebuf + (long long)i * nu;
+  const T* kc = P.kc + (long long)i * (nx + nu);
   team_reduce<T, CH>(tw1, acc, nx + nu, s_red, [&](int j, int, T s) {
-    if (j < nx) stc(hb + j, -s - s_xb[j]);
-    else stc(eb + (j - nx), s);
+    if (j < nx) stc(hb + j, (-s - s_xb[j]) + ldr(kc + j));
+    else stc(eb + (j - nx), s - ldr(kc + j));
   });
   s2_block(P, tw1.lane, i, vin, vout, vref, ra);
 }
@@ -185,18 +186,30 @@ __device__ void prep_leaf(const Prob<T>& P, int lane, int j, const T* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Phase B: one segment, bottom-up
+// Phase B: one segment, bottom-up. The matrix of the next (node, child) pair
+// streams into shared memory while the current one is used.
 // ---------------------------------------------------------------------------
 template <class T, int CH>
-__device__ void backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_qc, T* s_red,
-                                 int s) {
+__device__ __forceinline__ void mv_any(const Team& tm, Acc<T, CH>& acc, bool smem, const T* M, int ld,
+                                       int nrows, int ncols, const T* in) {
+  if (smem) team_mv<T, CH, true>(tm, acc, M, ld, nrows, ncols, in);
+  else team_mv<T, CH, false>(tm, acc, M, ld, nrows, ncols, in);
+}
+
+template <class T, int CH>
+__device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_qc, T* s_red,
+                                 Pipe<T>& pp, int* err, int s) {
   constexpr int PT = Acc<T, CH>::D / 32;
   const int nx = P.nx, nu = P.nu;
+  const size_t mstride = (size_t)nx * P.ldB;
+  const unsigned mbytes = (unsigned)(mstride * sizeof(T));
   int i = P.seg_bot[s];
   const int len = P.seg_len[s];
-  bool carry = false;
+  bool carry = false, ok = true;
+  if (pp.on) pp.issue(tm, pp.cur, P.MB + (size_t)(P.ch_off[i] - 1) * mstride, mbytes);
   for (int step = 0; step < len; ++step) {
     const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
+    const int inext = (step + 1 < len) ? P.anc[i] : -1;
     const T* h = P.hbuf + (long long)i * nx;
     const T* e = P.ebuf + (long long)i * nu;
     T pre[PT];
@@ -208,16 +221,25 @@ __device__ void backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
     Acc<T, CH> acc;
     acc.zero();
     for (int c = c0; c < c1; ++c) {
-      const T* pc = P.Pc + (long long)(c - 1) * nx;
-      if (carry) {
-        for (int k = tm.tid; k < nx; k += tm.nth) s_in[k] = s_qc[k] + ldr(pc + k);
-      } else {
-        for (int k = tm.tid; k < nx; k += tm.nth)
-          s_in[k] = ldc(P.qbuf + (long long)c * nx + k) + ldr(pc + k);
+      if (pp.on) {
+        // next item: the next child of i, else the only child (i) of the next node
+        const int cn = (c + 1 < c1) ? c + 1 : ((inext >= 0) ? i : -1);
+        if (cn > 0) pp.issue(tm, pp.cur ^ 1, P.MB + (size_t)(cn - 1) * mstride, mbytes);
       }
+      const T* in = s_qc;
+      if (!carry) {
+        for (int k = tm.tid; k < nx; k += tm.nth) s_in[k] = ldc(P.qbuf + (long long)c * nx + k);
+        in = s_in;
+        tm.sync();
+      }
+      const T* M = P.MB + (size_t)(c - 1) * mstride;
+      if (pp.on) {
+        ok = pp.wait(pp.cur, err) && ok;
+        M = pp.buf[pp.cur];
+      }
+      mv_any<T, CH>(tm, acc, pp.on, M, P.ldB, nx, nx + nu, in);
       tm.sync();
-      team_mv<T, CH>(tm, acc, P.MB + (size_t)(c - 1) * nx * P.ldB, P.ldB, nx, nx + nu, s_in);
-      tm.sync();
+      if (pp.on) pp.cur ^= 1;
     }
     T* q = P.qbuf + (long long)i * nx;
     T* d = P.dbuf + (long long)i * nu;
@@ -231,30 +253,31 @@ __device__ void backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
       }
     });
     carry = true;
-    i = P.anc[i];
+    i = inext;
   }
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
-// Phase F: one segment, top-down
+// Phase F: one segment, top-down (x and u of z+ only; their residuals and
+// the eta update follow in phase E)
 // ---------------------------------------------------------------------------
 template <class T, int CH>
-__device__ void forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_xn, T* s_xb,
-                                T* s_red, int s, const T* __restrict__ vin, T* __restrict__ vout,
-                                const T* __restrict__ vref, RedAcc<T>& ra) {
+__device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_xn, T* s_xb,
+                                T* s_red, Pipe<T>& pp, int* err, int s, T* __restrict__ vout) {
   constexpr int PT = Acc<T, CH>::D / 32;
   const int nx = P.nx, nu = P.nu;
+  const size_t kstride = (size_t)nx * P.ldK, fstride = (size_t)(nx + nu) * P.ldF;
+  const unsigned kbytes = (unsigned)(kstride * sizeof(T)), fbytes = (unsigned)(fstride * sizeof(T));
   int i = P.seg_top[s];
   const int len = P.seg_len[s];
-  const T* z = vin;
+  bool ok = true;
+  if (pp.on) pp.issue(tm, pp.cur, P.KT + (size_t)i * kstride, kbytes);
   if (i == 0) {
     for (int k = tm.tid; k < nx; k += tm.nth) {
       const T xn = P.x0s[k];
       s_xn[k] = xn;
-      const long long idx = P.o_x + k;
-      const T o = ldc(z + idx);
-      stc(vout + idx, xn);
-      ra.z(o, xn, refv(vref, idx, o));
+      stc(vout + P.o_x + k, xn);
     }
   } else {
     for (int k = tm.tid; k < nx; k += tm.nth) s_xn[k] = ldc(vout + P.o_x + (long long)i * nx + k);
@@ -262,55 +285,75 @@ __device__ void forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_
   tm.sync();
   for (int step = 0; step < len; ++step) {
     const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
+    const bool chain = (step + 1 < len);
     const T* d = P.dbuf + (long long)i * nu;
     const long long uo = P.o_u + (long long)i * nu;
-    T dp[PT], uold[PT], uref[PT];
+    T dp[PT];
 #pragma unroll
     for (int m = 0; m < PT; ++m) {
       const int j = tm.tid + m * tm.nth;
-      const bool ok = j < nu;
-      dp[m] = ok ? ldc(d + j) : T(0);
-      uold[m] = ok ? ldc(z + uo + j) : T(0);
-      uref[m] = (ok && vref) ? ldc(vref + uo + j) : uold[m];
+      dp[m] = (j < nu) ? ldc(d + j) : T(0);
     }
+    if (pp.on) pp.issue(tm, pp.cur ^ 1, P.MF + (size_t)(c0 - 1) * fstride, fbytes);
     // u^i = K x^i + d^i
     Acc<T, CH> acc;
     acc.zero();
-    team_mv<T, CH>(tm, acc, P.KT + (size_t)i * nx * P.ldK, P.ldK, nx, nu, s_xn);
+    const T* MK = P.KT + (size_t)i * kstride;
+    if (pp.on) {
+      ok = pp.wait(pp.cur, err) && ok;
+      MK = pp.buf[pp.cur];
+    }
+    mv_any<T, CH>(tm, acc, pp.on, MK, P.ldK, nx, nu, s_xn);
     team_reduce<T, CH>(tm, acc, nu, s_red, [&](int j, int m, T v) {
-      const T u = v + dp[m];
-      stc(vout + uo + j, u);
-      ra.z(uold[m], u, uref[m]);
+      stc(vout + uo + j, v + dp[m]);
       s_in[nx + j] = dp[m];
     });
+    if (pp.on) pp.cur ^= 1;
     for (int k = tm.tid; k < nx; k += tm.nth) s_in[k] = s_xn[k];
     tm.sync();
-    const bool chain = (step + 1 < len);
     for (int c = c0; c < c1; ++c) {
+      if (pp.on) {
+        if (c + 1 < c1) pp.issue(tm, pp.cur ^ 1, P.MF + (size_t)c * fstride, fbytes);
+        else if (chain) pp.issue(tm, pp.cur ^ 1, P.KT + (size_t)c0 * kstride, kbytes);
+      }
       const long long xo = P.o_x + (long long)c * nx;
       const T* cv = P.cvec + (long long)(c - 1) * nx;
-      T cp[PT], xold[PT], xref[PT];
+      T cp[PT];
 #pragma unroll
       for (int m = 0; m < PT; ++m) {
         const int j = tm.tid + m * tm.nth;
-        const bool ok = j < nx;
-        cp[m] = ok ? ldr(cv + j) : T(0);
-        xold[m] = ok ? ldc(z + xo + j) : T(0);
-        xref[m] = (ok && vref) ? ldc(vref + xo + j) : xold[m];
+        cp[m] = (j < nx) ? ldr(cv + j) : T(0);
       }
       acc.zero();
-      team_mv<T, CH>(tm, acc, P.MF + (size_t)(c - 1) * (nx + nu) * P.ldF, P.ldF, nx + nu, nx, s_in);
+      const T* MFc = P.MF + (size_t)(c - 1) * fstride;
+      if (pp.on) {
+        ok = pp.wait(pp.cur, err) && ok;
+        MFc = pp.buf[pp.cur];
+      }
+      mv_any<T, CH>(tm, acc, pp.on, MFc, P.ldF, nx + nu, nx, s_in);
       team_reduce<T, CH>(tm, acc, nx, s_red, [&](int j, int m, T v) {
         const T xc = v + cp[m];
         stc(vout + xo + j, xc);
-        ra.z(xold[m], xc, xref[m]);
         if (chain) s_xb[j] = xc;
       });
+      if (pp.on) pp.cur ^= 1;
     }
     if (chain) {
       i = c0;
       T* t = s_xn; s_xn = s_xb; s_xb = t;
     }
+  }
+  return ok;
+}
+
+// z residual of the x (and u) of one node, accumulated by one warp (phase E)
+template <class T>
+__device__ __forceinline__ void z_resid(const T* __restrict__ vin, const T* __restrict__ vout,
+                                        const T* __restrict__ vref, long long off, int len,
+                                        int lane, RedAcc<T>& ra) {
+  for (int k = lane; k < len; k += 32) {
+    const T o = ldc(vin + off + k);
+    ra.z(o, ldc(vout + off + k), refv(vref, off + k, o));
   }
 }
 
@@ -538,7 +581,7 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
 // group reduction of the per-thread partials into ctl->red (every CTA reads)
 // max_slot: index of the slot reduced by max (-1: every slot is a sum)
 // ---------------------------------------------------------------------------
-__device__ bool group_reduce(double (&v)[NRED], double* partials, SolveCtl* ctl, Grid& g,
+static __device__ bool group_reduce(double (&v)[NRED], double* partials, SolveCtl* ctl, Grid& g,
                              int max_slot) {
   __shared__ double scratch[NRED * 32];
   block_reduce_red(v, scratch, max_slot);
@@ -574,11 +617,19 @@ struct Views {
   __device__ T* w_in(int w) const { return base + (size_t)w * 3 * D; }
   __device__ T* w_xb(int w) const { return base + (size_t)w * 3 * D + D; }
   __device__ T* w_red(int w) const { return base + (size_t)w * 3 * D + 2 * D; }
-  // per team: in, xn, xb, qc, red (tw D)
-  __device__ T* t_base(int t) const { return base + (size_t)t * (4 + tw) * D; }
-  static size_t bytes(int threads, int tw) {
+  // per team: in, xn, xb, qc, red (tw D), then two pipe buffers of pipe_elems
+  size_t pipe_elems;   // elements of one pipe buffer (multiple of 16 bytes)
+  __device__ T* t_base(int t) const { return base + (size_t)t * ((4 + tw) * D + 2 * pipe_elems); }
+  __device__ T* t_pipe(int t, int b) const { return t_base(t) + (4 + tw) * D + b * pipe_elems; }
+  __host__ __device__ static size_t pipe_elems_for(int pipe_bytes) {
+    return (size_t)((pipe_bytes + 15) / 16) * 16 / sizeof(T);
+  }
+  // dynamic shared memory: the larger of the per-warp and per-team views; the
+  // mbarriers live in a static array
+  static size_t bytes(int threads, int tw, int pipe_bytes) {
     const int warps = threads / 32, teams = warps / tw;
-    const size_t a = (size_t)warps * 3 * D, b = (size_t)teams * (4 + tw) * D;
+    const size_t a = (size_t)warps * 3 * D;
+    const size_t b = (size_t)teams * ((4 + tw) * D + 2 * pipe_elems_for(pipe_bytes));
     return (a > b ? a : b) * sizeof(T);
   }
 };
@@ -587,9 +638,10 @@ struct Views {
 // one evaluation of T: v_out = T(v_in); reduction with reference point vref
 // ---------------------------------------------------------------------------
 template <class T, int CH>
-__device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, int tg, int nt,
-                      const T* __restrict__ vin, T* __restrict__ vout, const T* __restrict__ vref,
-                      double (&red)[NRED], double* partials, SolveCtl* ctl, Grid& g) {
+__device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, Pipe<T>& pp, int tg,
+                      int nt, const T* __restrict__ vin, T* __restrict__ vout,
+                      const T* __restrict__ vref, double (&red)[NRED], double* partials,
+                      SolveCtl* ctl, Grid& g) {
   constexpr int D = Acc<T, CH>::D;
   constexpr int NE = (D + 2 + 31) / 32;
   RedAcc<T> ra;
@@ -617,7 +669,7 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
     T* tb = sv.t_base(tm.id);
     for (int l = 0; l < P.n_levels; ++l) {
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt)
-        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, s);
+        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, pp, &g.ctl->error, s);
       if (!grid_sync(g, nop)) return false;
     }
   }
@@ -627,7 +679,7 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
     T* tb = sv.t_base(tm.id);
     for (int l = P.n_levels - 1; l >= 0; --l) {
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt)
-        forward_segment<T, CH>(P, tm, tb, tb + D, tb + 2 * D, tb + 4 * D, s, vin, vout, vref, ra);
+        forward_segment<T, CH>(P, tm, tb, tb + D, tb + 2 * D, tb + 4 * D, pp, &g.ctl->error, s, vout);
       if (!grid_sync(g, nop)) return false;
     }
   }
@@ -637,11 +689,15 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
     const long long nb = (long long)P.n_nl + (P.n - 1) + P.n_l;
     for (long long b = gw; b < nb; b += nw) {
       if (b < P.n_nl) {
+        z_resid(vin, vout, vref, P.o_x + b * P.nx, P.nx, lane, ra);
+        z_resid(vin, vout, vref, P.o_u + b * P.nu, P.nu, lane, ra);
         eta_nonleaf(P, lane, (int)b, vin, vout, vref, ra);
       } else if (b < P.n_nl + P.n - 1) {
         eta_soc<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);
       } else {
-        eta_leaf<T, NE>(P, lane, (int)(b - P.n_nl - (P.n - 1) + P.n_nl), vin, vout, vref, ra);
+        const int j = (int)(b - P.n_nl - (P.n - 1) + P.n_nl);
+        z_resid(vin, vout, vref, P.o_x + (long long)j * P.nx, P.nx, lane, ra);
+        eta_leaf<T, NE>(P, lane, j, vin, vout, vref, ra);
       }
     }
   }
@@ -669,6 +725,18 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
   Views<T, CH> sv;
   sv.base = reinterpret_cast<T*>(smraw);
   sv.tw = tw;
+  sv.pipe_elems = Views<T, CH>::pipe_elems_for(P.pipe_bytes);
+  __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
+  Pipe<T> pp;
+  pp.on = P.pipe_bytes > 0;
+  pp.bar = s_bar + 2 * tm.id;
+  pp.buf[0] = sv.t_pipe(tm.id, 0);
+  pp.buf[1] = sv.t_pipe(tm.id, 1);
+  pp.par[0] = pp.par[1] = 0u;
+  pp.cur = 0;
+  if (threadIdx.x < 2 * MAXTW) mbar_init(s_bar + threadIdx.x, 1);
+  fence_mbar_init();
+  __syncthreads();
   SolveCtl* ctl = B.ctl;
   Grid g;
   g.ctl = &ctl->bar;
@@ -682,7 +750,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
   double red[NRED];
   int status = 0, k = 0, nT = 0, nK0 = 0, nK1 = 0, nK2 = 0, nFB = 0, nBT = 0;
   double res, om2;
-  bool ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+  bool ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
   ++nT;
   if (!ok) goto fail;
   res = red[R_MAX];
@@ -691,7 +759,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
   if (o.method == 1) {
     while (!(res <= o.tol) && k < o.max_iters) {
       int t = iV; iV = iTV; iTV = t;
-      ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+      ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
       ++nT; ++k;
       if (!ok) goto fail;
       res = red[R_MAX];
@@ -806,7 +874,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
       }
       if (!grid_sync(g, []() {})) goto fail;
       pc.mark(ctl, 5);
-      ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
+      ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
       ++nT;
       if (!ok) goto fail;
       if (omega <= C0 * zeta) {                       // K0
@@ -848,7 +916,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
           if (!grid_sync(g, []() {})) goto fail;
           pk.mark(ctl, 6);
           int t = iV; iV = iVT; iVT = t;
-          ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+          ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
           ++nT;
           if (!ok) goto fail;
           res = red[R_MAX];
@@ -859,7 +927,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
         ++bt; ++nBT;
         if (bt >= o.max_backtracks) {                 // fall back to v <- T(v)
           int t = iV; iV = iTV; iTV = t;
-          ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+          ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
           ++nT;
           if (!ok) goto fail;
           res = red[R_MAX];
@@ -876,7 +944,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
         }
         if (!grid_sync(g, []() {})) goto fail;
         pk.mark(ctl, 6);
-        ok = evalT<T, CH>(P, tm, sv, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
+        ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
         ++nT;
         if (!ok) goto fail;
       }
@@ -906,7 +974,7 @@ fail:
 template <class T, int CH>
 cudaError_t launch_ch(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
                              int grid, int threads, cudaStream_t s) {
-  const size_t smem = Views<T, CH>::bytes(threads, tw);
+  const size_t smem = Views<T, CH>::bytes(threads, tw, P.pipe_bytes);
   cudaError_t e = cudaFuncSetAttribute(k_solve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -919,11 +987,11 @@ cudaError_t launch_ch(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& 
 }
 
 template <class T, int CH>
-int max_grid_ch(int tw, int threads, int* out) {
+int max_grid_ch(int tw, int threads, int pipe_bytes, int* out) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = Views<T, CH>::bytes(threads, tw);
+  const size_t smem = Views<T, CH>::bytes(threads, tw, pipe_bytes);
   cudaFuncSetAttribute(k_solve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve<T, CH>, threads, smem) != cudaSuccess)
     return -1;
