@@ -248,7 +248,8 @@ int ensure_bufs(spock_problem* p, Iter<T>& it) {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  b.partials = m.alloc<double>((long long)nsm * 8 * NRED);
+  b.partials = m.alloc<double>((long long)2 * nsm * 8 * NRED);
+  b.flags = m.alloc<unsigned>((long long)nsm * 8);
   b.ctl = m.alloc<SolveCtl>(1);
   if (m.failed) return SPOCK_ENOMEM;
   cudaMemset(b.V, 0, nv * sizeof(T));
@@ -328,6 +329,7 @@ int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t 
   if (grid > maxg) grid = maxg;
   if (grid < 1) grid = 1;
   if (cudaMemsetAsync(it.sb.ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (cudaMemsetAsync(it.sb.flags, 0, sizeof(unsigned) * grid, st) != cudaSuccess) return SPOCK_EDEVICE;
   cudaEventRecord(p->ev0, st);
   cudaError_t e = launch_solve<T>(it.P, it.sb, so, p->tw, grid, kThreads, st);
   if (e != cudaSuccess) return SPOCK_EDEVICE;

@@ -220,7 +220,6 @@ __device__ __forceinline__ void team_reduce(const Team& tm, const Acc<T, CH>& ac
       f(j, m, s);
     }
   }
-  __threadfence_block();
   tm.sync();
 }
 
@@ -316,7 +315,9 @@ struct GridCtl {
 };
 
 struct Grid {
-  GridCtl* ctl;
+  GridCtl* ctl;       // error word
+  unsigned* flags;    // one arrival flag per CTA (zeroed before the launch)
+  double* partials;   // 2 x gridDim.x x NRED reduction partials (double-buffered)
   unsigned epoch;     // barriers passed by this CTA (identical on every CTA)
 };
 
@@ -342,50 +343,78 @@ __device__ __forceinline__ int ld_relaxed_i(const int* p) {
 
 constexpr uint64_t BARRIER_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
+// Flag barrier: CTA b publishes flags[b] = epoch with a release store (after a
+// CTA barrier, so the release covers every thread's earlier writes); thread t
+// then waits with acquire loads until flags[t], flags[t + blockDim], ... reach
+// the epoch. No atomics and no central counter: two L2 round trips.
 // Returns false when the launch is in error (timeout here or elsewhere).
-template <class F>
-__device__ __forceinline__ bool grid_sync(Grid& g, F&& last_cb) {
-  __shared__ int s_flag;
-  const unsigned e = ++g.epoch;
+__device__ __forceinline__ bool poll_flags(Grid& g, unsigned e) {
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned arrived = atomicAdd(&g.ctl->count, 1u) + 1u;
-    if (arrived == e * gridDim.x) {
-      __threadfence();
-      s_flag = 1;
-    } else {
-      int ok = 1;
-      uint64_t t0 = 0;
-      unsigned spins = 0;
-      while (ld_acquire(&g.ctl->gen) < e) {
-        if ((++spins & 63u) == 0u) {
-          if (ld_relaxed_i(&g.ctl->error)) { ok = 0; break; }
-          const uint64_t t = global_ns();
-          if (t0 == 0) {
-            t0 = t;
-          } else if (t - t0 > BARRIER_LIMIT_NS) {
-            atomicExch(&g.ctl->error, 1);
-            ok = 0;
-            break;
-          }
+  for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
+    uint64_t t0 = 0;
+    unsigned spins = 0;
+    while (ld_acquire(g.flags + c) < e) {
+      if ((++spins & 63u) == 0u) {
+        if (ld_relaxed_i(&g.ctl->error)) { s_bad = 1; break; }
+        const uint64_t t = global_ns();
+        if (t0 == 0) {
+          t0 = t;
+        } else if (t - t0 > BARRIER_LIMIT_NS) {
+          atomicExch(&g.ctl->error, 1);
+          s_bad = 1;
+          break;
         }
       }
-      s_flag = ok ? 2 : 3;
     }
   }
   __syncthreads();
-  const int flag = s_flag;
-  if (flag == 1) {
-    last_cb();                       // whole last CTA
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release(&g.ctl->gen, e);
-    }
-    return ld_relaxed_i(&g.ctl->error) == 0;
+  return s_bad == 0;
+}
+
+__device__ __forceinline__ bool grid_sync(Grid& g) {
+  const unsigned e = ++g.epoch;
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(g.flags + blockIdx.x, e);
+  return poll_flags(g, e);
+}
+
+// All-reduce of NRED doubles over the grid: slot max_slot by max (-1: none),
+// the others by sum. Every CTA combines the per-CTA partials in the same
+// fixed order, so every CTA gets bit-identical results. scratch: shared
+// memory of NRED * 32 doubles. Returns false on error.
+__device__ __forceinline__ bool grid_allreduce(Grid& g, double (&v)[NRED], double* scratch,
+                                               int max_slot) {
+  block_reduce_red(v, scratch, max_slot);
+  const unsigned e = ++g.epoch;
+  double* part = g.partials + (size_t)(e & 1u) * gridDim.x * NRED;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) __stcg(part + (size_t)blockIdx.x * NRED + k, v[k]);
+    st_release(g.flags + blockIdx.x, e);
   }
-  return flag == 2;
+  const bool ok = poll_flags(g, e);
+  double x[NRED];
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) x[k] = 0.0;
+  for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) {
+      const double y = __ldcg(part + (size_t)c * NRED + k);
+      x[k] = (k == max_slot) ? fmax(x[k], y) : x[k] + y;
+    }
+  }
+  block_reduce_red(x, scratch, max_slot);
+  __shared__ double s_out[NRED];
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) s_out[k] = x[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) v[k] = s_out[k];
+  __syncthreads();
+  return ok;
 }
 
 // ---------------------------------------------------------------------------

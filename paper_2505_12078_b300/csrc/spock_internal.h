@@ -72,7 +72,8 @@ template <class T>
 struct SolveBufs {
   T *V, *TV, *VT, *TVT, *PSI, *VP, *RP;   // n_v each
   T *S, *Y;                               // 3 n_v each
-  double* partials;                        // [grid][NRED]
+  double* partials;                        // [2][grid][NRED]
+  unsigned* flags;                         // [grid] barrier flags
   SolveCtl* ctl;
 };
 

@@ -197,8 +197,20 @@ __device__ __forceinline__ void mv_any(const Team& tm, Acc<T, CH>& acc, bool sme
 }
 
 template <class T, int CH>
+__device__ __forceinline__ void issue_first_B(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int s) {
+  const size_t mstride = (size_t)P.nx * P.ldB;
+  const int i = P.seg_bot[s];
+  pp.issue(tm, pp.cur, P.MB + (size_t)(P.ch_off[i] - 1) * mstride, (unsigned)(mstride * sizeof(T)));
+}
+template <class T, int CH>
+__device__ __forceinline__ void issue_first_F(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int s) {
+  const size_t kstride = (size_t)P.nx * P.ldK;
+  pp.issue(tm, pp.cur, P.KT + (size_t)P.seg_top[s] * kstride, (unsigned)(kstride * sizeof(T)));
+}
+
+template <class T, int CH>
 __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_qc, T* s_red,
-                                 Pipe<T>& pp, int* err, int s) {
+                                 Pipe<T>& pp, int* err, int s, bool prefetched) {
   constexpr int PT = Acc<T, CH>::D / 32;
   const int nx = P.nx, nu = P.nu;
   const size_t mstride = (size_t)nx * P.ldB;
@@ -206,18 +218,24 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
   int i = P.seg_bot[s];
   const int len = P.seg_len[s];
   bool carry = false, ok = true;
-  if (pp.on) pp.issue(tm, pp.cur, P.MB + (size_t)(P.ch_off[i] - 1) * mstride, mbytes);
-  for (int step = 0; step < len; ++step) {
-    const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
-    const int inext = (step + 1 < len) ? P.anc[i] : -1;
-    const T* h = P.hbuf + (long long)i * nx;
-    const T* e = P.ebuf + (long long)i * nu;
-    T pre[PT];
+  if (pp.on && !prefetched) issue_first_B<T, CH>(P, tm, pp, s);
+  // h^i, e^i of the current node, loaded one step ahead
+  auto load_pre = [&](int node, T (&dst)[PT]) {
+    const T* h = P.hbuf + (long long)node * nx;
+    const T* e = P.ebuf + (long long)node * nu;
 #pragma unroll
     for (int m = 0; m < PT; ++m) {
       const int j = tm.tid + m * tm.nth;
-      pre[m] = (j < nx) ? ldc(h + j) : ((j < nx + nu) ? ldc(e + (j - nx)) : T(0));
+      dst[m] = (j < nx) ? ldc(h + j) : ((j < nx + nu) ? ldc(e + (j - nx)) : T(0));
     }
+  };
+  T pre[PT];
+  load_pre(i, pre);
+  for (int step = 0; step < len; ++step) {
+    const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
+    const int inext = (step + 1 < len) ? P.anc[i] : -1;
+    T pren[PT];
+    if (inext >= 0) load_pre(inext, pren);
     Acc<T, CH> acc;
     acc.zero();
     for (int c = c0; c < c1; ++c) {
@@ -253,6 +271,10 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
       }
     });
     carry = true;
+    if (inext >= 0) {
+#pragma unroll
+      for (int m = 0; m < PT; ++m) pre[m] = pren[m];
+    }
     i = inext;
   }
   return ok;
@@ -264,7 +286,8 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
 // ---------------------------------------------------------------------------
 template <class T, int CH>
 __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_xn, T* s_xb,
-                                T* s_red, Pipe<T>& pp, int* err, int s, T* __restrict__ vout) {
+                                T* s_red, Pipe<T>& pp, int* err, int s, T* __restrict__ vout,
+                                bool prefetched) {
   constexpr int PT = Acc<T, CH>::D / 32;
   const int nx = P.nx, nu = P.nu;
   const size_t kstride = (size_t)nx * P.ldK, fstride = (size_t)(nx + nu) * P.ldF;
@@ -272,7 +295,26 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_
   int i = P.seg_top[s];
   const int len = P.seg_len[s];
   bool ok = true;
-  if (pp.on) pp.issue(tm, pp.cur, P.KT + (size_t)i * kstride, kbytes);
+  if (pp.on && !prefetched) issue_first_F<T, CH>(P, tm, pp, s);
+  auto load_d = [&](int node, T (&dst)[PT]) {
+    const T* d = P.dbuf + (long long)node * nu;
+#pragma unroll
+    for (int m = 0; m < PT; ++m) {
+      const int j = tm.tid + m * tm.nth;
+      dst[m] = (j < nu) ? ldc(d + j) : T(0);
+    }
+  };
+  auto load_c = [&](int child, T (&dst)[PT]) {
+    const T* cv = P.cvec + (long long)(child - 1) * nx;
+#pragma unroll
+    for (int m = 0; m < PT; ++m) {
+      const int j = tm.tid + m * tm.nth;
+      dst[m] = (j < nx) ? ldr(cv + j) : T(0);
+    }
+  };
+  T dp[PT], cp[PT];
+  load_d(i, dp);
+  load_c(P.ch_off[i], cp);
   if (i == 0) {
     for (int k = tm.tid; k < nx; k += tm.nth) {
       const T xn = P.x0s[k];
@@ -286,13 +328,11 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_
   for (int step = 0; step < len; ++step) {
     const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
     const bool chain = (step + 1 < len);
-    const T* d = P.dbuf + (long long)i * nu;
     const long long uo = P.o_u + (long long)i * nu;
-    T dp[PT];
-#pragma unroll
-    for (int m = 0; m < PT; ++m) {
-      const int j = tm.tid + m * tm.nth;
-      dp[m] = (j < nu) ? ldc(d + j) : T(0);
+    T dpn[PT], cpn[PT];
+    if (chain) {
+      load_d(c0, dpn);
+      load_c(P.ch_off[c0], cpn);
     }
     if (pp.on) pp.issue(tm, pp.cur ^ 1, P.MF + (size_t)(c0 - 1) * fstride, fbytes);
     // u^i = K x^i + d^i
@@ -317,13 +357,7 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_
         else if (chain) pp.issue(tm, pp.cur ^ 1, P.KT + (size_t)c0 * kstride, kbytes);
       }
       const long long xo = P.o_x + (long long)c * nx;
-      const T* cv = P.cvec + (long long)(c - 1) * nx;
-      T cp[PT];
-#pragma unroll
-      for (int m = 0; m < PT; ++m) {
-        const int j = tm.tid + m * tm.nth;
-        cp[m] = (j < nx) ? ldr(cv + j) : T(0);
-      }
+      if (c > c0) load_c(c, cp);
       acc.zero();
       const T* MFc = P.MF + (size_t)(c - 1) * fstride;
       if (pp.on) {
@@ -341,6 +375,8 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_
     if (chain) {
       i = c0;
       T* t = s_xn; s_xn = s_xb; s_xb = t;
+#pragma unroll
+      for (int m = 0; m < PT; ++m) { dp[m] = dpn[m]; cp[m] = cpn[m]; }
     }
   }
   return ok;
@@ -578,34 +614,6 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// group reduction of the per-thread partials into ctl->red (every CTA reads)
-// max_slot: index of the slot reduced by max (-1: every slot is a sum)
-// ---------------------------------------------------------------------------
-static __device__ bool group_reduce(double (&v)[NRED], double* partials, SolveCtl* ctl, Grid& g,
-                             int max_slot) {
-  __shared__ double scratch[NRED * 32];
-  block_reduce_red(v, scratch, max_slot);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < NRED; ++k) stc(partials + (long long)blockIdx.x * NRED + k, v[k]);
-  const bool ok = grid_sync(g, [&]() {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w < NRED) {
-      const bool mx = (w == max_slot);
-      double s = 0.0;
-      for (int r = lane; r < (int)gridDim.x; r += 32) {
-        const double x = ldc(partials + (long long)r * NRED + w);
-        s = mx ? fmax(s, x) : s + x;
-      }
-      s = mx ? warp_max(s) : warp_sum(s);
-      if (lane == 0) stc(&ctl->red[w], s);
-    }
-  });
-#pragma unroll
-  for (int k = 0; k < NRED; ++k) v[k] = ldc(&ctl->red[k]);
-  return ok;
-}
-
-// ---------------------------------------------------------------------------
 // shared memory views: per warp (phase P) and per team (phases B, F)
 // ---------------------------------------------------------------------------
 template <class T, int CH>
@@ -617,10 +625,12 @@ struct Views {
   __device__ T* w_in(int w) const { return base + (size_t)w * 3 * D; }
   __device__ T* w_xb(int w) const { return base + (size_t)w * 3 * D + D; }
   __device__ T* w_red(int w) const { return base + (size_t)w * 3 * D + 2 * D; }
-  // per team: in, xn, xb, qc, red (tw D), then two pipe buffers of pipe_elems
+  // per team: in, xn, xb, qc, red (tw D); the two pipe buffers of every team
+  // sit in front of `base` (see bytes()) so they never overlap any scratch
   size_t pipe_elems;   // elements of one pipe buffer (multiple of 16 bytes)
-  __device__ T* t_base(int t) const { return base + (size_t)t * ((4 + tw) * D + 2 * pipe_elems); }
-  __device__ T* t_pipe(int t, int b) const { return t_base(t) + (4 + tw) * D + b * pipe_elems; }
+  T* pipe_base;
+  __device__ T* t_base(int t) const { return base + (size_t)t * (4 + tw) * D; }
+  __device__ T* t_pipe(int t, int b) const { return pipe_base + ((size_t)t * 2 + b) * pipe_elems; }
   __host__ __device__ static size_t pipe_elems_for(int pipe_bytes) {
     return (size_t)((pipe_bytes + 15) / 16) * 16 / sizeof(T);
   }
@@ -629,8 +639,8 @@ struct Views {
   static size_t bytes(int threads, int tw, int pipe_bytes) {
     const int warps = threads / 32, teams = warps / tw;
     const size_t a = (size_t)warps * 3 * D;
-    const size_t b = (size_t)teams * ((4 + tw) * D + 2 * pipe_elems_for(pipe_bytes));
-    return (a > b ? a : b) * sizeof(T);
+    const size_t b = (size_t)teams * (4 + tw) * D;
+    return ((a > b ? a : b) + (size_t)teams * 2 * pipe_elems_for(pipe_bytes)) * sizeof(T);
   }
 };
 
@@ -653,8 +663,11 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
   const int nw = gridDim.x * (blockDim.x >> 5);
   Team w1;
   w1.tw = 1; w1.id = wid; w1.warp = 0; w1.lane = lane; w1.tid = lane; w1.nth = 32;
-  auto nop = []() {};
-  // P
+  if (pp.on && P.n_levels > 0) {
+    const int s0 = P.lvl_off[0] + tg;
+    if (s0 < P.lvl_off[1]) issue_first_B<T, CH>(P, tm, pp, s0);
+  }
+    // P
   for (int node = gw; node < P.n; node += nw) {
     if (node < P.n_nl)
       prep_nonleaf<T, CH>(P, w1, sv.w_in(wid), sv.w_xb(wid), sv.w_red(wid), node, vin, vout, vref, ra);
@@ -662,25 +675,46 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
       prep_leaf(P, lane, node, vin);
     __syncwarp();
   }
-  if (!grid_sync(g, nop)) return false;
+  if (!grid_sync(g)) return false;
   pc.mark(ctl, 0);
   // B
+  const int L = P.n_levels;
   {
     T* tb = sv.t_base(tm.id);
-    for (int l = 0; l < P.n_levels; ++l) {
-      for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt)
-        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, pp, &g.ctl->error, s);
-      if (!grid_sync(g, nop)) return false;
+    for (int l = 0; l < L; ++l) {
+      bool pre = pp.on;
+      for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
+        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, pp, &g.ctl->error, s, pre);
+        pre = false;
+      }
+      if (pp.on) {   // first copy of this team's next piece of work, before the barrier
+        if (l + 1 < L) {
+          const int s1 = P.lvl_off[l + 1] + tg;
+          if (s1 < P.lvl_off[l + 2]) issue_first_B<T, CH>(P, tm, pp, s1);
+        } else {
+          const int s1 = P.lvl_off[L - 1] + tg;
+          if (s1 < P.lvl_off[L]) issue_first_F<T, CH>(P, tm, pp, s1);
+        }
+      }
+      if (!grid_sync(g)) return false;
     }
   }
   pc.mark(ctl, 1);
   // F
   {
     T* tb = sv.t_base(tm.id);
-    for (int l = P.n_levels - 1; l >= 0; --l) {
-      for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt)
-        forward_segment<T, CH>(P, tm, tb, tb + D, tb + 2 * D, tb + 4 * D, pp, &g.ctl->error, s, vout);
-      if (!grid_sync(g, nop)) return false;
+    for (int l = L - 1; l >= 0; --l) {
+      bool pre = pp.on;
+      for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
+        forward_segment<T, CH>(P, tm, tb, tb + D, tb + 2 * D, tb + 4 * D, pp, &g.ctl->error, s,
+                               vout, pre);
+        pre = false;
+      }
+      if (pp.on && l > 0) {
+        const int s1 = P.lvl_off[l - 1] + tg;
+        if (s1 < P.lvl_off[l]) issue_first_F<T, CH>(P, tm, pp, s1);
+      }
+      if (!grid_sync(g)) return false;
     }
   }
   pc.mark(ctl, 2);
@@ -704,7 +738,8 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
   double v[NRED];
 #pragma unroll
   for (int k = 0; k < NRED; ++k) v[k] = (double)ra.v[k];
-  const bool ok = group_reduce(v, partials, ctl, g, R_MAX);
+  __shared__ double scratch[NRED * 32];
+  const bool ok = grid_allreduce(g, v, scratch, R_MAX);
 #pragma unroll
   for (int k = 0; k < NRED; ++k) red[k] = v[k];
   pc.mark(ctl, 3);
@@ -723,9 +758,10 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
   const int tg = blockIdx.x * teams_per_cta + tm.id;
   const int nt = gridDim.x * teams_per_cta;
   Views<T, CH> sv;
-  sv.base = reinterpret_cast<T*>(smraw);
   sv.tw = tw;
   sv.pipe_elems = Views<T, CH>::pipe_elems_for(P.pipe_bytes);
+  sv.pipe_base = reinterpret_cast<T*>(smraw);
+  sv.base = sv.pipe_base + (size_t)teams_per_cta * 2 * sv.pipe_elems;
   __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
   Pipe<T> pp;
   pp.on = P.pipe_bytes > 0;
@@ -740,6 +776,8 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
   SolveCtl* ctl = B.ctl;
   Grid g;
   g.ctl = &ctl->bar;
+  g.flags = B.flags;
+  g.partials = B.partials;
   g.epoch = 0;
   T* buf[4] = {B.V, B.TV, B.VT, B.TVT};
   int iV = 0, iTV = 1, iVT = 2, iTVT = 3;
@@ -808,7 +846,10 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
           stc(B.RP + e, r);
         }
         for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? (double)acc[a] : 0.0;
-        if (!group_reduce(dd, B.partials, ctl, g, -1)) goto fail;
+        {
+          __shared__ double scratch2[NRED * 32];
+          if (!grid_allreduce(g, dd, scratch2, -1)) goto fail;
+        }
         double bvec[AA_M];
         if (push) {
           if (count < AA_M) ++count;
@@ -872,7 +913,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
           stc(VT + e, v + psi);
         }
       }
-      if (!grid_sync(g, []() {})) goto fail;
+      if (!grid_sync(g)) goto fail;
       pc.mark(ctl, 5);
       ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
       ++nT;
@@ -913,7 +954,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
             const T vt = ldc(VT + e);
             stc(VT + e, ldc(Vc + e) - coef * (vt - ldc(TVT + e)));
           }
-          if (!grid_sync(g, []() {})) goto fail;
+          if (!grid_sync(g)) goto fail;
           pk.mark(ctl, 6);
           int t = iV; iV = iVT; iVT = t;
           ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
@@ -942,7 +983,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
           T* VT = buf[iVT];
           for (long long e = gtid; e < nv; e += gstride) stc(VT + e, ldc(Vc + e) + tt * ldc(B.PSI + e));
         }
-        if (!grid_sync(g, []() {})) goto fail;
+        if (!grid_sync(g)) goto fail;
         pk.mark(ctl, 6);
         ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
         ++nT;
