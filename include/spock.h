@@ -163,6 +163,10 @@ typedef struct spock_info {
     double phase_ms[7];   /* device time per phase seen by the first CTA, barrier waits
                              included: prep/S2, backward sweep, forward sweep + eta update,
                              T reductions, Anderson dots, direction pass, K2/backtrack passes */
+    double counters[8];   /* SM cycles seen by the first thread of the first CTA: backward
+                             sweep bulk-copy waits, mat-vecs, team reductions, other step
+                             work; grid barriers, all-reductions; barrier and all-reduction
+                             counts */
 } spock_info;
 
 void spock_solve_opts_default(spock_solve_opts* o);

@@ -314,6 +314,9 @@ int pipe_bytes_for(const spock_problem* p) {
   return (need <= (size_t)optin) ? b : 0;
 }
 
+// cycle probes of the last solve (see SolveCtl::prof)
+static unsigned long long g_last_prof[16];
+
 template <class T>
 int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t st, SolveCtl* h_ctl,
                float* ms) {
@@ -338,6 +341,7 @@ int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t 
     return SPOCK_EDEVICE;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SPOCK_EDEVICE;
   if (ms) cudaEventElapsedTime(ms, p->ev0, p->ev1);
+  for (int q = 0; q < 16; ++q) g_last_prof[q] = h_ctl->prof[q];
   if (h_ctl->status < 0) return SPOCK_ETIMEOUT;
   return SPOCK_OK;
 }
@@ -767,6 +771,7 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
     info->res_inf = h.res_inf; info->res_inf_fp64 = res64; info->risk = risk;
     info->device_ms = ms;
     for (int q = 0; q < 7; ++q) info->phase_ms[q] = 1e-6 * (double)h.prof[q];
+    for (int q = 0; q < 8; ++q) info->counters[q] = (double)h.prof[8 + q];
   }
   return h.status == 0 ? SPOCK_OK : SPOCK_MAXITER;
 }

@@ -319,6 +319,7 @@ struct Grid {
   unsigned* flags;    // one arrival flag per CTA (zeroed before the launch)
   double* partials;   // 2 x gridDim.x x NRED reduction partials (double-buffered)
   unsigned epoch;     // barriers passed by this CTA (identical on every CTA)
+  unsigned long long* prof;   // cycle counters of CTA 0 (slots 12..15), may be null
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -374,10 +375,17 @@ __device__ __forceinline__ bool poll_flags(Grid& g, unsigned e) {
 }
 
 __device__ __forceinline__ bool grid_sync(Grid& g) {
+  const bool probe = g.prof && blockIdx.x == 0 && threadIdx.x == 0;
+  const long long t0 = probe ? clock64() : 0;
   const unsigned e = ++g.epoch;
   __syncthreads();
   if (threadIdx.x == 0) st_release(g.flags + blockIdx.x, e);
-  return poll_flags(g, e);
+  const bool ok = poll_flags(g, e);
+  if (probe) {
+    g.prof[12] += (unsigned long long)(clock64() - t0);
+    g.prof[14] += 1;
+  }
+  return ok;
 }
 
 // All-reduce of NRED doubles over the grid: slot max_slot by max (-1: none),
@@ -386,6 +394,8 @@ __device__ __forceinline__ bool grid_sync(Grid& g) {
 // memory of NRED * 32 doubles. Returns false on error.
 __device__ __forceinline__ bool grid_allreduce(Grid& g, double (&v)[NRED], double* scratch,
                                                int max_slot) {
+  const bool probe = g.prof && blockIdx.x == 0 && threadIdx.x == 0;
+  const long long t0 = probe ? clock64() : 0;
   block_reduce_red(v, scratch, max_slot);
   const unsigned e = ++g.epoch;
   double* part = g.partials + (size_t)(e & 1u) * gridDim.x * NRED;
@@ -414,6 +424,10 @@ __device__ __forceinline__ bool grid_allreduce(Grid& g, double (&v)[NRED], doubl
 #pragma unroll
   for (int k = 0; k < NRED; ++k) v[k] = s_out[k];
   __syncthreads();
+  if (probe) {
+    g.prof[13] += (unsigned long long)(clock64() - t0);
+    g.prof[15] += 1;
+  }
   return ok;
 }
 

@@ -64,8 +64,11 @@ struct SolveCtl {
   int pad0, pad1;
   // device time per phase seen by CTA 0 (ns, barrier waits included):
   // 0 prep, 1 backward sweep, 2 forward sweep, 3 T reduction, 4 Anderson dots,
-  // 5 direction pass, 6 K2/backtrack passes, 7 count of T evaluations
-  unsigned long long prof[8];
+  // 5 direction pass, 6 K2/backtrack passes, 7 count of T evaluations;
+  // 8.. SM cycles seen by thread 0 of CTA 0 inside the backward sweep:
+  // 8 bulk-copy waits, 9 mat-vecs, 10 team reductions, 11 steps, 12 grid
+  // barriers, 13 all-reductions, 14 barrier count, 15 all-reduce count
+  unsigned long long prof[16];
 };
 
 template <class T>

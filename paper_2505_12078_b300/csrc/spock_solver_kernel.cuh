@@ -208,9 +208,31 @@ __device__ __forceinline__ void issue_first_F(const Prob<T>& P, const Team& tm, 
   pp.issue(tm, pp.cur, P.KT + (size_t)P.seg_top[s] * kstride, (unsigned)(kstride * sizeof(T)));
 }
 
+// cycle probe of thread 0 of CTA 0 (sub-phase breakdown of the sweeps)
+struct Probe {
+  unsigned long long* slots;
+  long long t;
+  bool on;
+  __device__ __forceinline__ void start(unsigned long long* p) {
+    on = (blockIdx.x == 0 && threadIdx.x == 0);
+    slots = p;
+    if (on) t = clock64();
+  }
+  __device__ __forceinline__ void mark(int k) {
+    if (on) {
+      const long long n = clock64();
+      slots[k] += (unsigned long long)(n - t);
+      t = n;
+    }
+  }
+};
+
 template <class T, int CH>
 __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_qc, T* s_red,
-                                 Pipe<T>& pp, int* err, int s, bool prefetched) {
+                                 Pipe<T>& pp, int* err, int s, bool prefetched,
+                                 unsigned long long* prof) {
+  Probe pr;
+  pr.start(prof);
   constexpr int PT = Acc<T, CH>::D / 32;
   const int nx = P.nx, nu = P.nu;
   const size_t mstride = (size_t)nx * P.ldB;
@@ -251,12 +273,15 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
         tm.sync();
       }
       const T* M = P.MB + (size_t)(c - 1) * mstride;
+      pr.mark(11);
       if (pp.on) {
         ok = pp.wait(pp.cur, err) && ok;
         M = pp.buf[pp.cur];
       }
+      pr.mark(8);
       mv_any<T, CH>(tm, acc, pp.on, M, P.ldB, nx, nx + nu, in);
       tm.sync();
+      pr.mark(9);
       if (pp.on) pp.cur ^= 1;
     }
     T* q = P.qbuf + (long long)i * nx;
@@ -270,6 +295,7 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
         stc(d + (j - nx), pre[m] - v);
       }
     });
+    pr.mark(10);
     carry = true;
     if (inext >= 0) {
 #pragma unroll
@@ -684,7 +710,7 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
     for (int l = 0; l < L; ++l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, pp, &g.ctl->error, s, pre);
+        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, pp, &g.ctl->error, s, pre, ctl->prof);
         pre = false;
       }
       if (pp.on) {   // first copy of this team's next piece of work, before the barrier
@@ -779,6 +805,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
   g.flags = B.flags;
   g.partials = B.partials;
   g.epoch = 0;
+  g.prof = ctl->prof;
   T* buf[4] = {B.V, B.TV, B.VT, B.TVT};
   int iV = 0, iTV = 1, iVT = 2, iTVT = 3;
   const long long nv = P.nv;

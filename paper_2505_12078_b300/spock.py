@@ -56,11 +56,13 @@ class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("n_T", C.c_int), ("n_K0", C.c_int),
                 ("n_K1", C.c_int), ("n_K2", C.c_int), ("n_fallback", C.c_int),
                 ("n_backtracks", C.c_int), ("res_inf", C.c_double), ("res_inf_fp64", C.c_double),
-                ("risk", C.c_double), ("device_ms", C.c_double), ("phase_ms", C.c_double * 7)]
+                ("risk", C.c_double), ("device_ms", C.c_double), ("phase_ms", C.c_double * 7),
+                ("counters", C.c_double * 8)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["phase_ms"] = list(self.phase_ms)
+        d["counters"] = list(self.counters)
         return d
 
 
