@@ -63,7 +63,8 @@ struct spock_problem {
   long long n_y = 0, nz = 0, neta = 0, nv = 0;
   long long o_x, o_u, o_y, o_tau, o_s, e_y, e_s, e_c, e_q, e_cN, e_qN;
   int ldB, ldF, ldP, ldK;
-  std::vector<int> anc, ch_off, yoff, stage_off, ynode, lvl_off, seg_top, seg_bot, seg_len;
+  std::vector<int> anc, ch_off, yoff, stage_off, ynode, lvl_off, seg_top, seg_bot, seg_len, seg_off,
+      seg_nodes;
   std::vector<double> Sx, Su, SxN;
   double a_con = 1, a_conN = 1, alpha = 0, normL = 0;
   int max_items = 1;
@@ -71,7 +72,9 @@ struct spock_problem {
   int use_pipe = 1;    // stream the sweep matrices through shared memory
   DevMem mem;
   // device tree / schedule
-  int *d_anc, *d_ch_off, *d_yoff, *d_ynode, *d_lvl_off, *d_seg_top, *d_seg_bot, *d_seg_len;
+  int *d_anc, *d_ch_off, *d_yoff, *d_ynode, *d_lvl_off, *d_seg_top, *d_seg_bot, *d_seg_len,
+      *d_seg_off, *d_seg_nodes;
+  int4* d_seg_info;
   // FP64 offline data kept for inspection
   double *d_P, *d_K, *d_Rt, *d_Abar, *d_Sx, *d_SxN, *d_Su;
   double* d_x0raw;   // unscaled x0 of the operator-level calls
@@ -181,6 +184,16 @@ int build_tree(spock_problem* p, int n, const int* anc, const double* prob) {
       }
   }
   p->lvl_off[L] = (int)p->seg_top.size();
+  p->seg_off.clear(); p->seg_nodes.clear();
+  for (size_t q = 0; q < p->seg_top.size(); ++q) {
+    p->seg_off.push_back((int)p->seg_nodes.size());
+    int j = p->seg_top[q];
+    for (int k = 0; k < p->seg_len[q]; ++k) {
+      p->seg_nodes.push_back(j);
+      j = p->ch_off[j];
+    }
+  }
+  p->seg_off.push_back((int)p->seg_nodes.size());
   p->max_items = max_items;
   return SPOCK_OK;
 }
@@ -199,6 +212,7 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.anc = p->d_anc; P.ch_off = p->d_ch_off; P.yoff = p->d_yoff;
   P.n_levels = (int)p->lvl_off.size() - 1;
   P.lvl_off = p->d_lvl_off; P.seg_top = p->d_seg_top; P.seg_bot = p->d_seg_bot; P.seg_len = p->d_seg_len;
+  P.seg_off = p->d_seg_off; P.seg_nodes = p->d_seg_nodes; P.seg_info = p->d_seg_info;
   P.MB = it.MB; P.MF = it.MF; P.MP = it.MP; P.KT = it.KT; P.cvec = it.cvec; P.kc = it.kc;
   P.qh = it.qh; P.rh = it.rh; P.qNh = it.qNh; P.gx = it.gx; P.gu = it.gu; P.gN = it.gN;
   P.box_lo = it.box_lo; P.box_hi = it.box_hi; P.boxN_lo = it.boxN_lo; P.boxN_hi = it.boxN_hi;
@@ -244,7 +258,9 @@ int ensure_bufs(spock_problem* p, Iter<T>& it) {
   SolveBufs<T>& b = it.sb;
   b.V = m.alloc<T>(nv); b.TV = m.alloc<T>(nv); b.VT = m.alloc<T>(nv); b.TVT = m.alloc<T>(nv);
   b.PSI = m.alloc<T>(nv); b.VP = m.alloc<T>(nv); b.RP = m.alloc<T>(nv);
-  b.S = m.alloc<T>(3 * nv); b.Y = m.alloc<T>(3 * nv);
+  const long long nvp = (nv + 3) & ~3LL;   // 16-byte aligned slots
+  b.sstride = nvp;
+  b.S = m.alloc<T>(3 * nvp); b.Y = m.alloc<T>(3 * nvp);
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -253,8 +269,8 @@ int ensure_bufs(spock_problem* p, Iter<T>& it) {
   b.ctl = m.alloc<SolveCtl>(1);
   if (m.failed) return SPOCK_ENOMEM;
   cudaMemset(b.V, 0, nv * sizeof(T));
-  cudaMemset(b.S, 0, 3 * nv * sizeof(T));
-  cudaMemset(b.Y, 0, 3 * nv * sizeof(T));
+  cudaMemset(b.S, 0, 3 * nvp * sizeof(T));
+  cudaMemset(b.Y, 0, 3 * nvp * sizeof(T));
   it.have_bufs = true;
   return cuda_err(cudaGetLastError());
 }
@@ -470,6 +486,16 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   p->d_anc = up_i(p->anc); p->d_ch_off = up_i(p->ch_off); p->d_yoff = up_i(p->yoff);
   p->d_ynode = up_i(p->ynode); p->d_lvl_off = up_i(p->lvl_off); p->d_seg_top = up_i(p->seg_top);
   p->d_seg_bot = up_i(p->seg_bot); p->d_seg_len = up_i(p->seg_len);
+  p->d_seg_off = up_i(p->seg_off); p->d_seg_nodes = up_i(p->seg_nodes);
+  {
+    std::vector<int> info;
+    for (size_t q = 0; q < p->seg_top.size(); ++q) {
+      const int bot = p->seg_bot[q];
+      info.push_back(p->seg_off[q]); info.push_back(p->seg_len[q]);
+      info.push_back(p->ch_off[bot]); info.push_back(p->ch_off[bot + 1]);
+    }
+    p->d_seg_info = reinterpret_cast<int4*>(up_i(info));
+  }
   p->d_Sx = up_d(p->Sx.data(), nx); p->d_Su = up_d(p->Su.data(), nu); p->d_SxN = up_d(p->SxN.data(), nx);
   double* d_prob = up_d(d->prob, n);
   double* d_avar = up_d(d->avar, n_nl);

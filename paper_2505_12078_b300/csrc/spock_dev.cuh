@@ -39,6 +39,10 @@ struct Prob {
   const int* seg_top;          // top node of a segment
   const int* seg_bot;          // bottom node
   const int* seg_len;          // number of nodes
+  const int* seg_off;          // start of the segment's node list in seg_nodes
+  const int* seg_nodes;        // nodes of every segment, top to bottom, contiguous
+  const int4* seg_info;        // per segment: (list offset, length, first and one-past-last
+                               // child of the bottom node)
   // per-iteration factors (built offline in FP64 from Alg. 1)
   const T* MB;   // per non-root c: [Abar_c | B_c Rt^{-1}]      nx x ldB   (input: q_c + P_c c_c)
   const T* MF;   // per non-root c: [Abar_c^T ; B_c^T]           (nx+nu) x ldF (input: [x; d])

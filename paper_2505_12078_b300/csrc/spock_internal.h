@@ -74,7 +74,8 @@ struct SolveCtl {
 template <class T>
 struct SolveBufs {
   T *V, *TV, *VT, *TVT, *PSI, *VP, *RP;   // n_v each
-  T *S, *Y;                               // 3 n_v each
+  T *S, *Y;                               // 3 slots of sstride each
+  long long sstride;                      // n_v rounded up to a multiple of 4
   double* partials;                        // [2][grid][NRED]
   unsigned* flags;                         // [grid] barrier flags
   SolveCtl* ctl;

@@ -44,18 +44,21 @@ __device__ __forceinline__ T refv(const T* vref, long long idx, T old) {
   return vref ? ldc(vref + idx) : old;
 }
 
-// phase timer of CTA 0 (thread 0): adds the time since the last mark to slot k
+// phase timer of CTA 0 (thread 0): adds the time since the last mark to slot
+// k of a shared-memory array that is written to the control block at exit
 struct PhaseClock {
   uint64_t t;
   bool on;
-  __device__ __forceinline__ void start() {
+  unsigned long long* prof;
+  __device__ __forceinline__ void start(unsigned long long* p) {
+    prof = p;
     on = (blockIdx.x == 0 && threadIdx.x == 0);
     if (on) t = global_ns();
   }
-  __device__ __forceinline__ void mark(SolveCtl* ctl, int k) {
+  __device__ __forceinline__ void mark(SolveCtl*, int k) {
     if (on) {
       const uint64_t n = global_ns();
-      ctl->prof[k] += n - t;
+      prof[k] += n - t;
       t = n;
     }
   }
@@ -196,19 +199,8 @@ __device__ __forceinline__ void mv_any(const Team& tm, Acc<T, CH>& acc, bool sme
   else team_mv<T, CH, false>(tm, acc, M, ld, nrows, ncols, in);
 }
 
-template <class T, int CH>
-__device__ __forceinline__ void issue_first_B(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int s) {
-  const size_t mstride = (size_t)P.nx * P.ldB;
-  const int i = P.seg_bot[s];
-  pp.issue(tm, pp.cur, P.MB + (size_t)(P.ch_off[i] - 1) * mstride, (unsigned)(mstride * sizeof(T)));
-}
-template <class T, int CH>
-__device__ __forceinline__ void issue_first_F(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int s) {
-  const size_t kstride = (size_t)P.nx * P.ldK;
-  pp.issue(tm, pp.cur, P.KT + (size_t)P.seg_top[s] * kstride, (unsigned)(kstride * sizeof(T)));
-}
-
-// cycle probe of thread 0 of CTA 0 (sub-phase breakdown of the sweeps)
+// cycle probe of thread 0 of CTA 0 (sub-phase breakdown of the sweeps); the
+// slots live in shared memory and are written to the control block at exit
 struct Probe {
   unsigned long long* slots;
   long long t;
@@ -227,6 +219,35 @@ struct Probe {
   }
 };
 
+// The node list of one segment: lane k of every warp holds node k (top to
+// bottom) for k < 32; longer segments read the rest from global memory.
+struct SegList {
+  int off, len, c0b, c1b, mynode;
+  template <class T>
+  __device__ __forceinline__ void load(const Prob<T>& P, int s, int lane) {
+    const int4 inf = P.seg_info[s];
+    off = inf.x; len = inf.y; c0b = inf.z; c1b = inf.w;
+    mynode = (lane < len) ? P.seg_nodes[off + lane] : -1;
+  }
+  template <class T>
+  __device__ __forceinline__ int node(const Prob<T>& P, int k) const {
+    const int v = __shfl_sync(0xffffffffu, mynode, k & 31);
+    return (k < 32) ? v : P.seg_nodes[off + k];
+  }
+};
+
+template <class T, int CH>
+__device__ __forceinline__ void issue_first_B(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int s) {
+  const size_t mstride = (size_t)P.nx * P.ldB;
+  const int c0b = P.seg_info[s].z;
+  pp.issue(tm, pp.cur, P.MB + (size_t)(c0b - 1) * mstride, (unsigned)(mstride * sizeof(T)));
+}
+template <class T, int CH>
+__device__ __forceinline__ void issue_first_F(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int s) {
+  const size_t kstride = (size_t)P.nx * P.ldK;
+  pp.issue(tm, pp.cur, P.KT + (size_t)P.seg_top[s] * kstride, (unsigned)(kstride * sizeof(T)));
+}
+
 template <class T, int CH>
 __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_qc, T* s_red,
                                  Pipe<T>& pp, int* err, int s, bool prefetched,
@@ -237,11 +258,12 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
   const int nx = P.nx, nu = P.nu;
   const size_t mstride = (size_t)nx * P.ldB;
   const unsigned mbytes = (unsigned)(mstride * sizeof(T));
-  int i = P.seg_bot[s];
-  const int len = P.seg_len[s];
-  bool carry = false, ok = true;
+  bool ok = true;
   if (pp.on && !prefetched) issue_first_B<T, CH>(P, tm, pp, s);
-  // h^i, e^i of the current node, loaded one step ahead
+  SegList sl;
+  sl.load(P, s, tm.lane);
+  const int len = sl.len;
+  // h^i, e^i of a node, loaded one step ahead
   auto load_pre = [&](int node, T (&dst)[PT]) {
     const T* h = P.hbuf + (long long)node * nx;
     const T* e = P.ebuf + (long long)node * nu;
@@ -251,11 +273,14 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
       dst[m] = (j < nx) ? ldc(h + j) : ((j < nx + nu) ? ldc(e + (j - nx)) : T(0));
     }
   };
+  int i = sl.node(P, len - 1);
   T pre[PT];
   load_pre(i, pre);
   for (int step = 0; step < len; ++step) {
-    const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
-    const int inext = (step + 1 < len) ? P.anc[i] : -1;
+    const bool bottom = (step == 0);
+    const int c0 = bottom ? sl.c0b : sl.node(P, len - step);
+    const int c1 = bottom ? sl.c1b : c0 + 1;
+    const int inext = (step + 1 < len) ? sl.node(P, len - 2 - step) : -1;
     T pren[PT];
     if (inext >= 0) load_pre(inext, pren);
     Acc<T, CH> acc;
@@ -267,7 +292,7 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
         if (cn > 0) pp.issue(tm, pp.cur ^ 1, P.MB + (size_t)(cn - 1) * mstride, mbytes);
       }
       const T* in = s_qc;
-      if (!carry) {
+      if (bottom) {
         for (int k = tm.tid; k < nx; k += tm.nth) s_in[k] = ldc(P.qbuf + (long long)c * nx + k);
         in = s_in;
         tm.sync();
@@ -296,7 +321,6 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
       }
     });
     pr.mark(10);
-    carry = true;
     if (inext >= 0) {
 #pragma unroll
       for (int m = 0; m < PT; ++m) pre[m] = pren[m];
@@ -318,10 +342,11 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_
   const int nx = P.nx, nu = P.nu;
   const size_t kstride = (size_t)nx * P.ldK, fstride = (size_t)(nx + nu) * P.ldF;
   const unsigned kbytes = (unsigned)(kstride * sizeof(T)), fbytes = (unsigned)(fstride * sizeof(T));
-  int i = P.seg_top[s];
-  const int len = P.seg_len[s];
   bool ok = true;
   if (pp.on && !prefetched) issue_first_F<T, CH>(P, tm, pp, s);
+  SegList sl;
+  sl.load(P, s, tm.lane);
+  const int len = sl.len;
   auto load_d = [&](int node, T (&dst)[PT]) {
     const T* d = P.dbuf + (long long)node * nu;
 #pragma unroll
@@ -338,9 +363,12 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_
       dst[m] = (j < nx) ? ldr(cv + j) : T(0);
     }
   };
+  // first child of the node at list index k
+  auto first_child = [&](int k) { return (k + 1 < len) ? sl.node(P, k + 1) : sl.c0b; };
+  int i = sl.node(P, 0);
   T dp[PT], cp[PT];
   load_d(i, dp);
-  load_c(P.ch_off[i], cp);
+  load_c(first_child(0), cp);
   if (i == 0) {
     for (int k = tm.tid; k < nx; k += tm.nth) {
       const T xn = P.x0s[k];
@@ -352,13 +380,14 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_
   }
   tm.sync();
   for (int step = 0; step < len; ++step) {
-    const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
     const bool chain = (step + 1 < len);
+    const int c0 = first_child(step);
+    const int c1 = chain ? c0 + 1 : sl.c1b;
     const long long uo = P.o_u + (long long)i * nu;
     T dpn[PT], cpn[PT];
     if (chain) {
       load_d(c0, dpn);
-      load_c(P.ch_off[c0], cpn);
+      load_c(first_child(step + 1), cpn);
     }
     if (pp.on) pp.issue(tm, pp.cur ^ 1, P.MF + (size_t)(c0 - 1) * fstride, fbytes);
     // u^i = K x^i + d^i
@@ -683,7 +712,7 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
   RedAcc<T> ra;
   ra.zero();
   PhaseClock pc;
-  pc.start();
+  pc.start(g.prof);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
   const int nw = gridDim.x * (blockDim.x >> 5);
@@ -710,7 +739,7 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
     for (int l = 0; l < L; ++l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, pp, &g.ctl->error, s, pre, ctl->prof);
+        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, pp, &g.ctl->error, s, pre, g.prof);
         pre = false;
       }
       if (pp.on) {   // first copy of this team's next piece of work, before the barrier
@@ -769,8 +798,25 @@ __device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, 
 #pragma unroll
   for (int k = 0; k < NRED; ++k) red[k] = v[k];
   pc.mark(ctl, 3);
-  if (pc.on) ctl->prof[7] += 1;
+  if (pc.on) g.prof[7] += 1;
   return ok;
+}
+
+// ---------------------------------------------------------------------------
+// 16-byte vector load/store of the element-wise passes (L2 path)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void ldv(const T* p, long long q, T (&o)[Vec<T>::N]) {
+  using V = typename Vec<T>::V;
+  const V x = __ldcg(reinterpret_cast<const V*>(p) + q);
+  memcpy(o, &x, sizeof(V));
+}
+template <class T>
+__device__ __forceinline__ void stv(T* p, long long q, const T (&o)[Vec<T>::N]) {
+  using V = typename Vec<T>::V;
+  V x;
+  memcpy(&x, o, sizeof(V));
+  __stcg(reinterpret_cast<V*>(p) + q, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -805,12 +851,18 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
   g.flags = B.flags;
   g.partials = B.partials;
   g.epoch = 0;
-  g.prof = ctl->prof;
+  __shared__ unsigned long long s_prof[16];
+  if (threadIdx.x < 16) s_prof[threadIdx.x] = 0ull;
+  __syncthreads();
+  g.prof = s_prof;
   T* buf[4] = {B.V, B.TV, B.VT, B.TVT};
   int iV = 0, iTV = 1, iVT = 2, iTVT = 3;
   const long long nv = P.nv;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gstride = (long long)gridDim.x * blockDim.x;
+  constexpr int VN = Vec<T>::N;
+  const long long nvec = nv / VN;
+  const long long ss = B.sstride;
   const T al = P.alpha;
   double red[NRED];
   int status = 0, k = 0, nT = 0, nK0 = 0, nK1 = 0, nK2 = 0, nFB = 0, nBT = 0;
@@ -845,7 +897,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
       T* V = buf[iV];
       T* TV = buf[iTV];
       PhaseClock pc;
-      pc.start();
+      pc.start(g.prof);
       // --- Anderson memory update (pairs (v^k - v^{k-1}, r^k - r^{k-1})) ---
       double kap[AA_M] = {0.0, 0.0, 0.0};
       bool use_aa = false;
@@ -855,22 +907,48 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
         double dd[NRED];
         T acc[2 * AA_M];
         for (int a = 0; a < 2 * AA_M; ++a) acc[a] = 0;
-        for (long long e = gtid; e < nv; e += gstride) {
-          const T v = ldc(V + e), r = v - ldc(TV + e);
-          if (push) {
-            const T s_ = v - ldc(B.VP + e);
-            const T y_ = r - ldc(B.RP + e);
-            stc(B.S + slot * nv + e, s_);
-            stc(B.Y + slot * nv + e, y_);
+        T* Sslot = B.S + slot * ss;
+        T* Yslot = B.Y + slot * ss;
+        // one element: new pair (s, y), dots y.Y_l and Y_l.r, copies of v and r
+        auto elem = [&](T v, T tv, T vp, T rp, T y0, T y1, T y2, T& so, T& yo, T& ro) {
+          const T r = v - tv;
+          ro = r;
+          so = v - vp;
+          const T y_ = r - rp;
+          yo = y_;
+          const T yl[AA_M] = {slot == 0 ? y_ : y0, slot == 1 ? y_ : y1, slot == 2 ? y_ : y2};
 #pragma unroll
-            for (int l = 0; l < AA_M; ++l) {
-              const T yl = (l == slot) ? y_ : ldc(B.Y + l * nv + e);
-              acc[l] = fma(y_, yl, acc[l]);
-              acc[AA_M + l] = fma(yl, r, acc[AA_M + l]);
-            }
+          for (int l = 0; l < AA_M; ++l) {
+            acc[l] = fma(y_, yl[l], acc[l]);
+            acc[AA_M + l] = fma(yl[l], r, acc[AA_M + l]);
+          }
+        };
+        for (long long q = gtid; q < nvec; q += gstride) {
+          T v[VN], tv[VN], vp[VN], rp[VN], y0[VN], y1[VN], y2[VN], so[VN], yo[VN], ro[VN];
+          ldv(V, q, v); ldv(TV, q, tv);
+          if (push) {
+            ldv((const T*)B.VP, q, vp); ldv((const T*)B.RP, q, rp);
+            ldv((const T*)B.Y, q, y0); ldv((const T*)B.Y + ss, q, y1); ldv((const T*)B.Y + 2 * ss, q, y2);
+#pragma unroll
+            for (int c = 0; c < VN; ++c) elem(v[c], tv[c], vp[c], rp[c], y0[c], y1[c], y2[c], so[c], yo[c], ro[c]);
+            stv(Sslot, q, so); stv(Yslot, q, yo);
+          } else {
+#pragma unroll
+            for (int c = 0; c < VN; ++c) ro[c] = v[c] - tv[c];
+          }
+          stv(B.VP, q, v); stv(B.RP, q, ro);
+        }
+        for (long long e = nvec * VN + gtid; e < nv; e += gstride) {
+          const T v = ldc(V + e), tv = ldc(TV + e);
+          T so, yo, ro = v - tv;
+          if (push) {
+            elem(v, tv, ldc(B.VP + e), ldc(B.RP + e), ldc(B.Y + e), ldc(B.Y + ss + e),
+                 ldc(B.Y + 2 * ss + e), so, yo, ro);
+            stc(Sslot + e, so);
+            stc(Yslot + e, yo);
           }
           stc(B.VP + e, v);
-          stc(B.RP + e, r);
+          stc(B.RP + e, ro);
         }
         for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? (double)acc[a] : 0.0;
         {
@@ -928,16 +1006,39 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
       {
         T* VT = buf[iVT];
         const T k0 = (T)kap[0], k1 = (T)kap[1], k2 = (T)kap[2];
-        for (long long e = gtid; e < nv; e += gstride) {
-          const T v = ldc(V + e), r = v - ldc(TV + e);
-          T psi = -r;
+        auto elem = [&](T v, T tv, T s0, T s1, T s2, T y0, T y1, T y2, T& psi, T& vt) {
+          T p = -(v - tv);
           if (use_aa) {
-            psi -= (ldc(B.S + e) - ldc(B.Y + e)) * k0;
-            psi -= (ldc(B.S + nv + e) - ldc(B.Y + nv + e)) * k1;
-            psi -= (ldc(B.S + 2 * nv + e) - ldc(B.Y + 2 * nv + e)) * k2;
+            p -= (s0 - y0) * k0;
+            p -= (s1 - y1) * k1;
+            p -= (s2 - y2) * k2;
           }
-          stc(B.PSI + e, psi);
-          stc(VT + e, v + psi);
+          psi = p;
+          vt = v + p;
+        };
+        for (long long q = gtid; q < nvec; q += gstride) {
+          T v[VN], tv[VN], s0[VN], s1[VN], s2[VN], y0[VN], y1[VN], y2[VN], ps[VN], vt[VN];
+          ldv((const T*)V, q, v); ldv((const T*)TV, q, tv);
+          if (use_aa) {
+            ldv((const T*)B.S, q, s0); ldv((const T*)B.S + ss, q, s1); ldv((const T*)B.S + 2 * ss, q, s2);
+            ldv((const T*)B.Y, q, y0); ldv((const T*)B.Y + ss, q, y1); ldv((const T*)B.Y + 2 * ss, q, y2);
+          } else {
+#pragma unroll
+            for (int c = 0; c < VN; ++c) s0[c] = s1[c] = s2[c] = y0[c] = y1[c] = y2[c] = T(0);
+          }
+#pragma unroll
+          for (int c = 0; c < VN; ++c) elem(v[c], tv[c], s0[c], s1[c], s2[c], y0[c], y1[c], y2[c], ps[c], vt[c]);
+          stv(B.PSI, q, ps);
+          stv(VT, q, vt);
+        }
+        for (long long e = nvec * VN + gtid; e < nv; e += gstride) {
+          T ps, vt;
+          const bool u = use_aa;
+          elem(ldc(V + e), ldc(TV + e), u ? ldc(B.S + e) : T(0), u ? ldc(B.S + ss + e) : T(0),
+               u ? ldc(B.S + 2 * ss + e) : T(0), u ? ldc(B.Y + e) : T(0), u ? ldc(B.Y + ss + e) : T(0),
+               u ? ldc(B.Y + 2 * ss + e) : T(0), ps, vt);
+          stc(B.PSI + e, ps);
+          stc(VT + e, vt);
         }
       }
       if (!grid_sync(g)) goto fail;
@@ -971,13 +1072,20 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
         const double mdot = red[R_ZD] + red[R_ED] - (double)al * red[R_LZD] - (double)al * red[R_ELD];
         const double rho = om2t - mdot;
         PhaseClock pk;
-        pk.start();
+        pk.start(g.prof);
         if (rho >= SIGMA * omt * omega) {             // K2
           const T coef = (T)(LAMBDA * rho / om2t);
           T* Vc = buf[iV];
           T* VT = buf[iVT];
           const T* TVT = buf[iTVT];
-          for (long long e = gtid; e < nv; e += gstride) {
+          for (long long q = gtid; q < nvec; q += gstride) {
+            T a[VN], b[VN], c_[VN];
+            ldv((const T*)Vc, q, a); ldv((const T*)VT, q, b); ldv(TVT, q, c_);
+#pragma unroll
+            for (int c = 0; c < VN; ++c) b[c] = a[c] - coef * (b[c] - c_[c]);
+            stv(VT, q, b);
+          }
+          for (long long e = nvec * VN + gtid; e < nv; e += gstride) {
             const T vt = ldc(VT + e);
             stc(VT + e, ldc(Vc + e) - coef * (vt - ldc(TVT + e)));
           }
@@ -1008,7 +1116,14 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, Sol
           const T tt = (T)tau;
           const T* Vc = buf[iV];
           T* VT = buf[iVT];
-          for (long long e = gtid; e < nv; e += gstride) stc(VT + e, ldc(Vc + e) + tt * ldc(B.PSI + e));
+          for (long long q = gtid; q < nvec; q += gstride) {
+            T a[VN], b[VN];
+            ldv(Vc, q, a); ldv((const T*)B.PSI, q, b);
+#pragma unroll
+            for (int c = 0; c < VN; ++c) a[c] = a[c] + tt * b[c];
+            stv(VT, q, a);
+          }
+          for (long long e = nvec * VN + gtid; e < nv; e += gstride) stc(VT + e, ldc(Vc + e) + tt * ldc(B.PSI + e));
         }
         if (!grid_sync(g)) goto fail;
         pk.mark(ctl, 6);
@@ -1028,6 +1143,7 @@ done:
     for (int q = 0; q < NRED; ++q) ctl->stats[q] = red[q];
     ctl->final_v = iV;       // final buffer indices for the host
     ctl->final_tv = iTV;
+    for (int q = 0; q < 16; ++q) ctl->prof[q] = s_prof[q];
   }
   return;
 fail:
