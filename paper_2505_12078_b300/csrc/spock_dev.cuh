@@ -361,6 +361,7 @@ __device__ __forceinline__ bool poll_flags(Grid& g, unsigned e) {
     uint64_t t0 = 0;
     unsigned spins = 0;
     while (ld_acquire(g.flags + c) < e) {
+      __nanosleep(64);   // back off: idle CTAs must not flood L2 while others work
       if ((++spins & 63u) == 0u) {
         if (ld_relaxed_i(&g.ctl->error)) { s_bad = 1; break; }
         const uint64_t t = global_ns();

@@ -702,8 +702,10 @@ struct Views {
 // ---------------------------------------------------------------------------
 // one evaluation of T: v_out = T(v_in); reduction with reference point vref
 // ---------------------------------------------------------------------------
+// Not inlined: the driver calls it from six places, and six inlined copies of
+// the whole evaluation overflow the instruction cache.
 template <class T, int CH>
-__device__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, Pipe<T>& pp, int tg,
+__device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, Pipe<T>& pp, int tg,
                       int nt, const T* __restrict__ vin, T* __restrict__ vout,
                       const T* __restrict__ vref, double (&red)[NRED], double* partials,
                       SolveCtl* ctl, Grid& g) {
@@ -823,8 +825,15 @@ __device__ __forceinline__ void stv(T* p, long long q, const T (&o)[Vec<T>::N]) 
 // the solve kernel
 // ---------------------------------------------------------------------------
 template <class T, int CH>
-__global__ void __launch_bounds__(256, 1) k_solve(Prob<T> P, SolveBufs<T> B, SolveOpts o, int tw) {
+__global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, SolveOpts o, int tw) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  // the problem descriptor lives in shared memory so that the non-inlined
+  // evaluation reads it without a local-memory copy of the parameter
+  __shared__ __align__(16) unsigned char s_prob[sizeof(Prob<T>)];
+  for (int b = threadIdx.x; b < (int)sizeof(Prob<T>); b += blockDim.x)
+    s_prob[b] = reinterpret_cast<const unsigned char*>(&Pk)[b];
+  __syncthreads();
+  const Prob<T>& P = *reinterpret_cast<const Prob<T>*>(s_prob);
   const Team tm = make_team(tw);
   const int teams_per_cta = (blockDim.x >> 5) / tw;
   const int tg = blockIdx.x * teams_per_cta + tm.id;
