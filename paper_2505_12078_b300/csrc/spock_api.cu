@@ -306,6 +306,8 @@ __global__ void k_unscale(int n, int n_nl, int nx, int nu, long long o_x, long l
   }
 }
 
+// warps per team of the sweeps; the column-split mat-vecs need
+// 2 * 32 * tw >= nx + nu (at most two output columns per thread)
 int pick_tw(int nx, int nu) {
   const int d = nx + nu;
   if (d >= 96) return 8;
@@ -319,8 +321,9 @@ int pick_tw(int nx, int nu) {
 // matrices from global memory).
 template <class T>
 int pipe_bytes_for(const spock_problem* p) {
-  const long long e = std::max({(long long)p->nx * p->ldB, (long long)(p->nx + p->nu) * p->ldF,
-                                (long long)p->nx * p->ldK});
+  // backward item: MB; forward item: [KT | MF]
+  const long long e = std::max((long long)p->nx * p->ldB,
+                               (long long)(p->nx + p->nu) * p->ldF + (long long)p->nx * p->ldK);
   const int b = (int)(e * (long long)sizeof(T));
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);

@@ -467,7 +467,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
@@ -513,9 +513,13 @@ struct Pipe {
       bulk_g2s(buf[b], src, bytes, bar + b);
     }
   }
-  __device__ __forceinline__ bool wait(int b, int* err) {
-    const bool ok = mbar_wait(bar + b, par[b], err);
+  // thread 0 of the team polls the mbarrier (non-suspending test_wait); the
+  // team barrier then hands the completed copy to every thread of the team
+  __device__ __forceinline__ bool wait(const Team& tm, int b, int* err) {
+    bool ok = true;
+    if (tm.tid == 0) ok = mbar_wait(bar + b, par[b], err);
     par[b] ^= 1u;
+    tm.sync();
     return ok;
   }
 };

@@ -199,6 +199,55 @@ __device__ __forceinline__ void mv_any(const Team& tm, Acc<T, CH>& acc, bool sme
   else team_mv<T, CH, false>(tm, acc, M, ld, nrows, ncols, in);
 }
 
+// ---------------------------------------------------------------------------
+// Column-split mat-vec of the sweeps: thread t of a team owns output columns
+// j = t + m*nth (m < NP) and runs the whole dot product over the rows, from
+// shared memory, with two partial sums to halve the FMA dependency chain. No
+// cross-warp reduction is needed.
+// ---------------------------------------------------------------------------
+constexpr int NPM = 2;   // most output columns per thread in the sweeps
+
+template <class T, int NP>
+__device__ __forceinline__ void col_mv_np(const T* __restrict__ M, int ld, int nrows,
+                                          const T* __restrict__ in, int t, int nth, int ncols,
+                                          T (&acc)[NPM]) {
+  T a0[NP], a1[NP];
+#pragma unroll
+  for (int m = 0; m < NP; ++m) { a0[m] = T(0); a1[m] = T(0); }
+  int k = 0;
+  for (; k + 1 < nrows; k += 2) {
+    const T x0 = in[k], x1 = in[k + 1];
+    const T* r0 = M + (size_t)k * ld + t;
+    const T* r1 = r0 + ld;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      if (t + m * nth < ncols) {
+        a0[m] = fma(r0[m * nth], x0, a0[m]);
+        a1[m] = fma(r1[m * nth], x1, a1[m]);
+      }
+    }
+  }
+  if (k < nrows) {
+    const T x0 = in[k];
+    const T* r0 = M + (size_t)k * ld + t;
+#pragma unroll
+    for (int m = 0; m < NP; ++m)
+      if (t + m * nth < ncols) a0[m] = fma(r0[m * nth], x0, a0[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < NP; ++m) acc[m] += a0[m] + a1[m];
+}
+
+// acc[m] += sum_k M[k*ld + t + m*nth] * in[k]; ceil(ncols / nth) <= NPM (the
+// team size is chosen so that 2 * team threads >= nx + nu)
+template <class T>
+__device__ __forceinline__ void col_mv(const T* M, int ld, int nrows, const T* in, int t, int nth,
+                                       int ncols, T (&acc)[NPM]) {
+  if (t >= ncols) return;
+  if (ncols <= nth) col_mv_np<T, 1>(M, ld, nrows, in, t, nth, ncols, acc);
+  else col_mv_np<T, 2>(M, ld, nrows, in, t, nth, ncols, acc);
+}
+
 // cycle probe of thread 0 of CTA 0 (sub-phase breakdown of the sweeps); the
 // slots live in shared memory and are written to the control block at exit
 struct Probe {
@@ -236,94 +285,114 @@ struct SegList {
   }
 };
 
+// pipeline items: backward = MB of a child; forward = [KT of the node | MF of
+// its first child] or MF of a further child (KT part left unused)
+template <class T>
+__device__ __forceinline__ void issue_B(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int b, int c) {
+  const size_t st = (size_t)P.nx * P.ldB;
+  pp.issue(tm, b, P.MB + (size_t)(c - 1) * st, (unsigned)(st * sizeof(T)));
+}
+template <class T>
+__device__ __forceinline__ void issue_F(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int b, int node,
+                                        int c, bool with_kt) {
+  const size_t ks = (size_t)P.nx * P.ldK, fs = (size_t)(P.nx + P.nu) * P.ldF;
+  if (tm.tid == 0) {
+    fence_proxy_async();
+    mbar_expect_tx(pp.bar + b, (unsigned)(((with_kt ? ks : 0) + fs) * sizeof(T)));
+    if (with_kt) bulk_g2s(pp.buf[b], P.KT + (size_t)node * ks, (unsigned)(ks * sizeof(T)), pp.bar + b);
+    bulk_g2s(pp.buf[b] + ks, P.MF + (size_t)(c - 1) * fs, (unsigned)(fs * sizeof(T)), pp.bar + b);
+  }
+}
 template <class T, int CH>
 __device__ __forceinline__ void issue_first_B(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int s) {
-  const size_t mstride = (size_t)P.nx * P.ldB;
-  const int c0b = P.seg_info[s].z;
-  pp.issue(tm, pp.cur, P.MB + (size_t)(c0b - 1) * mstride, (unsigned)(mstride * sizeof(T)));
+  issue_B(P, tm, pp, pp.cur, P.seg_info[s].z);
 }
 template <class T, int CH>
 __device__ __forceinline__ void issue_first_F(const Prob<T>& P, const Team& tm, Pipe<T>& pp, int s) {
-  const size_t kstride = (size_t)P.nx * P.ldK;
-  pp.issue(tm, pp.cur, P.KT + (size_t)P.seg_top[s] * kstride, (unsigned)(kstride * sizeof(T)));
+  const int top = P.seg_top[s];
+  const int4 inf = P.seg_info[s];
+  const int c0 = (inf.y > 1) ? P.seg_nodes[inf.x + 1] : inf.z;
+  issue_F(P, tm, pp, pp.cur, top, c0, true);
 }
 
+// ---------------------------------------------------------------------------
+// Phase B: one segment, bottom-up. s_a, s_b: ping-pong carry buffers (D each).
+// ---------------------------------------------------------------------------
 template <class T, int CH>
-__device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_qc, T* s_red,
-                                 Pipe<T>& pp, int* err, int s, bool prefetched,
-                                 unsigned long long* prof) {
+__device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_b, Pipe<T>& pp,
+                                 int* err, int s, bool prefetched, unsigned long long* prof) {
   Probe pr;
   pr.start(prof);
-  constexpr int PT = Acc<T, CH>::D / 32;
-  const int nx = P.nx, nu = P.nu;
-  const size_t mstride = (size_t)nx * P.ldB;
-  const unsigned mbytes = (unsigned)(mstride * sizeof(T));
+  const int nx = P.nx, nu = P.nu, w = nx + nu, ldB = P.ldB;
+  const int t = tm.tid, nth = tm.nth;
+  const size_t mstride = (size_t)nx * ldB;
+  const T* __restrict__ MB = P.MB;
+  T* __restrict__ qbuf = P.qbuf;
+  T* __restrict__ dbuf = P.dbuf;
+  const T* __restrict__ hbuf = P.hbuf;
+  const T* __restrict__ ebuf = P.ebuf;
   bool ok = true;
   if (pp.on && !prefetched) issue_first_B<T, CH>(P, tm, pp, s);
   SegList sl;
   sl.load(P, s, tm.lane);
   const int len = sl.len;
-  // h^i, e^i of a node, loaded one step ahead
-  auto load_pre = [&](int node, T (&dst)[PT]) {
-    const T* h = P.hbuf + (long long)node * nx;
-    const T* e = P.ebuf + (long long)node * nu;
+  auto load_pre = [&](int node, T (&dst)[NPM]) {
 #pragma unroll
-    for (int m = 0; m < PT; ++m) {
-      const int j = tm.tid + m * tm.nth;
-      dst[m] = (j < nx) ? ldc(h + j) : ((j < nx + nu) ? ldc(e + (j - nx)) : T(0));
+    for (int m = 0; m < NPM; ++m) {
+      const int j = t + m * nth;
+      dst[m] = (j < nx) ? ldc(hbuf + (long long)node * nx + j)
+                        : ((j < w) ? ldc(ebuf + (long long)node * nu + (j - nx)) : T(0));
     }
   };
   int i = sl.node(P, len - 1);
-  T pre[PT];
+  T pre[NPM];
   load_pre(i, pre);
+  T* cin = s_a;    // carry read by this step
+  T* cout = s_b;   // carry written by this step
   for (int step = 0; step < len; ++step) {
     const bool bottom = (step == 0);
     const int c0 = bottom ? sl.c0b : sl.node(P, len - step);
     const int c1 = bottom ? sl.c1b : c0 + 1;
     const int inext = (step + 1 < len) ? sl.node(P, len - 2 - step) : -1;
-    T pren[PT];
+    T pren[NPM];
     if (inext >= 0) load_pre(inext, pren);
-    Acc<T, CH> acc;
-    acc.zero();
+    T acc[NPM];
+#pragma unroll
+    for (int m = 0; m < NPM; ++m) acc[m] = T(0);
     for (int c = c0; c < c1; ++c) {
-      if (pp.on) {
-        // next item: the next child of i, else the only child (i) of the next node
-        const int cn = (c + 1 < c1) ? c + 1 : ((inext >= 0) ? i : -1);
-        if (cn > 0) pp.issue(tm, pp.cur ^ 1, P.MB + (size_t)(cn - 1) * mstride, mbytes);
+      if (bottom) {   // q of the child from global memory (computed by another team or a leaf)
+        for (int k = t; k < nx; k += nth) cin[k] = ldc(qbuf + (long long)c * nx + k);
       }
-      const T* in = s_qc;
-      if (bottom) {
-        for (int k = tm.tid; k < nx; k += tm.nth) s_in[k] = ldc(P.qbuf + (long long)c * nx + k);
-        in = s_in;
-        tm.sync();
-      }
-      const T* M = P.MB + (size_t)(c - 1) * mstride;
       pr.mark(11);
-      if (pp.on) {
-        ok = pp.wait(pp.cur, err) && ok;
-        M = pp.buf[pp.cur];
-      }
+      if (pp.on) ok = pp.wait(tm, pp.cur, err) && ok;   // includes a team barrier
+      else tm.sync();
       pr.mark(8);
-      mv_any<T, CH>(tm, acc, pp.on, M, P.ldB, nx, nx + nu, in);
-      tm.sync();
-      pr.mark(9);
+      // next item into the other buffer (read before the barrier just passed)
+      const int cn = (c + 1 < c1) ? c + 1 : ((inext >= 0) ? i : -1);
+      if (pp.on && cn > 0) issue_B(P, tm, pp, pp.cur ^ 1, cn);
+      const T* Mb = pp.on ? pp.buf[pp.cur] : MB + (size_t)(c - 1) * mstride;
+      col_mv<T>(Mb, ldB, nx, cin, t, nth, w, acc);
       if (pp.on) pp.cur ^= 1;
+      pr.mark(9);
+      if (bottom && c + 1 < c1) tm.sync();       // cin is reloaded for the next child
     }
-    T* q = P.qbuf + (long long)i * nx;
-    T* d = P.dbuf + (long long)i * nu;
-    team_reduce<T, CH>(tm, acc, nx + nu, s_red, [&](int j, int m, T v) {
+#pragma unroll
+    for (int m = 0; m < NPM; ++m) {
+      const int j = t + m * nth;
       if (j < nx) {
-        const T qq = v + pre[m];
-        stc(q + j, qq);
-        s_qc[j] = qq;
-      } else {
-        stc(d + (j - nx), pre[m] - v);
+        const T qq = acc[m] + pre[m];
+        cout[j] = qq;
+        stc(qbuf + (long long)i * nx + j, qq);
+      } else if (j < w) {
+        stc(dbuf + (long long)i * nu + (j - nx), pre[m] - acc[m]);
       }
-    });
+    }
+    tm.sync();
     pr.mark(10);
+    T* tt = cin; cin = cout; cout = tt;
     if (inext >= 0) {
 #pragma unroll
-      for (int m = 0; m < PT; ++m) pre[m] = pren[m];
+      for (int m = 0; m < NPM; ++m) pre[m] = pren[m];
     }
     i = inext;
   }
@@ -331,109 +400,140 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s
 }
 
 // ---------------------------------------------------------------------------
-// Phase F: one segment, top-down (x and u of z+ only; their residuals and
-// the eta update follow in phase E)
+// Phase F: one segment, top-down (x and u of z+ only; their residuals and the
+// eta update follow in phase E). The team's input buffer holds [x^i ; d^i].
+// Threads [0, nx) compute x of the child, threads [nx, nx + nu) compute u^i
+// when the team is wide enough; otherwise every thread does both in turn.
 // ---------------------------------------------------------------------------
 template <class T, int CH>
-__device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_in, T* s_xn, T* s_xb,
-                                T* s_red, Pipe<T>& pp, int* err, int s, T* __restrict__ vout,
-                                bool prefetched) {
-  constexpr int PT = Acc<T, CH>::D / 32;
-  const int nx = P.nx, nu = P.nu;
-  const size_t kstride = (size_t)nx * P.ldK, fstride = (size_t)(nx + nu) * P.ldF;
-  const unsigned kbytes = (unsigned)(kstride * sizeof(T)), fbytes = (unsigned)(fstride * sizeof(T));
+__device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_b, Pipe<T>& pp,
+                                int* err, int s, T* __restrict__ vout, bool prefetched) {
+  const int nx = P.nx, nu = P.nu, w = nx + nu, ldF = P.ldF, ldK = P.ldK;
+  const int t = tm.tid, nth = tm.nth;
+  const size_t ks = (size_t)nx * ldK;
+  const T* __restrict__ dbuf = P.dbuf;
+  const T* __restrict__ cvec = P.cvec;
+  const long long o_x = P.o_x, o_u = P.o_u;
+  const bool wide = nth >= w;
+  const size_t fs = (size_t)w * ldF;
   bool ok = true;
   if (pp.on && !prefetched) issue_first_F<T, CH>(P, tm, pp, s);
   SegList sl;
   sl.load(P, s, tm.lane);
   const int len = sl.len;
-  auto load_d = [&](int node, T (&dst)[PT]) {
-    const T* d = P.dbuf + (long long)node * nu;
-#pragma unroll
-    for (int m = 0; m < PT; ++m) {
-      const int j = tm.tid + m * tm.nth;
-      dst[m] = (j < nu) ? ldc(d + j) : T(0);
-    }
-  };
-  auto load_c = [&](int child, T (&dst)[PT]) {
-    const T* cv = P.cvec + (long long)(child - 1) * nx;
-#pragma unroll
-    for (int m = 0; m < PT; ++m) {
-      const int j = tm.tid + m * tm.nth;
-      dst[m] = (j < nx) ? ldr(cv + j) : T(0);
-    }
-  };
-  // first child of the node at list index k
   auto first_child = [&](int k) { return (k + 1 < len) ? sl.node(P, k + 1) : sl.c0b; };
   int i = sl.node(P, 0);
-  T dp[PT], cp[PT];
-  load_d(i, dp);
-  load_c(first_child(0), cp);
-  if (i == 0) {
-    for (int k = tm.tid; k < nx; k += tm.nth) {
-      const T xn = P.x0s[k];
-      s_xn[k] = xn;
-      stc(vout + P.o_x + k, xn);
+  T* cin = s_a;
+  T* cout = s_b;
+  // input of the first step: x^i (fixed x0 at the root) and d^i
+  for (int k = t; k < w; k += nth) {
+    T v;
+    if (k < nx) {
+      if (i == 0) {
+        v = P.x0s[k];
+        stc(vout + o_x + k, v);
+      } else {
+        v = ldc(vout + o_x + (long long)i * nx + k);
+      }
+    } else {
+      v = ldc(dbuf + (long long)i * nu + (k - nx));
     }
-  } else {
-    for (int k = tm.tid; k < nx; k += tm.nth) s_xn[k] = ldc(vout + P.o_x + (long long)i * nx + k);
+    cin[k] = v;
   }
-  tm.sync();
+  T cp[NPM];
+  {
+    const int c = first_child(0);
+#pragma unroll
+    for (int m = 0; m < NPM; ++m) {
+      const int j = t + m * nth;
+      cp[m] = (j < nx) ? ldr(cvec + (long long)(c - 1) * nx + j) : T(0);
+    }
+  }
   for (int step = 0; step < len; ++step) {
     const bool chain = (step + 1 < len);
     const int c0 = first_child(step);
     const int c1 = chain ? c0 + 1 : sl.c1b;
-    const long long uo = P.o_u + (long long)i * nu;
-    T dpn[PT], cpn[PT];
+    // prefetch d of the next node and c of its first child
+    T dpn[NPM], cpn[NPM];
     if (chain) {
-      load_d(c0, dpn);
-      load_c(first_child(step + 1), cpn);
+      const int cn = first_child(step + 1);
+#pragma unroll
+      for (int m = 0; m < NPM; ++m) {
+        const int j = t + m * nth;
+        dpn[m] = (j < nu) ? ldc(dbuf + (long long)c0 * nu + j) : T(0);
+        cpn[m] = (j < nx) ? ldr(cvec + (long long)(cn - 1) * nx + j) : T(0);
+      }
     }
-    if (pp.on) pp.issue(tm, pp.cur ^ 1, P.MF + (size_t)(c0 - 1) * fstride, fbytes);
-    // u^i = K x^i + d^i
-    Acc<T, CH> acc;
-    acc.zero();
-    const T* MK = P.KT + (size_t)i * kstride;
-    if (pp.on) {
-      ok = pp.wait(pp.cur, err) && ok;
-      MK = pp.buf[pp.cur];
-    }
-    mv_any<T, CH>(tm, acc, pp.on, MK, P.ldK, nx, nu, s_xn);
-    team_reduce<T, CH>(tm, acc, nu, s_red, [&](int j, int m, T v) {
-      stc(vout + uo + j, v + dp[m]);
-      s_in[nx + j] = dp[m];
-    });
-    if (pp.on) pp.cur ^= 1;
-    for (int k = tm.tid; k < nx; k += tm.nth) s_in[k] = s_xn[k];
-    tm.sync();
     for (int c = c0; c < c1; ++c) {
       if (pp.on) {
-        if (c + 1 < c1) pp.issue(tm, pp.cur ^ 1, P.MF + (size_t)c * fstride, fbytes);
-        else if (chain) pp.issue(tm, pp.cur ^ 1, P.KT + (size_t)c0 * kstride, kbytes);
+        ok = pp.wait(tm, pp.cur, err) && ok;      // includes a team barrier
+        if (c + 1 < c1) issue_F(P, tm, pp, pp.cur ^ 1, i, c + 1, false);
+        else if (chain) issue_F(P, tm, pp, pp.cur ^ 1, c0, first_child(step + 1), true);
+      } else {
+        tm.sync();
       }
-      const long long xo = P.o_x + (long long)c * nx;
-      if (c > c0) load_c(c, cp);
-      acc.zero();
-      const T* MFc = P.MF + (size_t)(c - 1) * fstride;
-      if (pp.on) {
-        ok = pp.wait(pp.cur, err) && ok;
-        MFc = pp.buf[pp.cur];
+      const T* KTb = pp.on ? pp.buf[pp.cur] : P.KT + (size_t)i * ks;
+      const T* MFb = pp.on ? KTb + ks : P.MF + (size_t)(c - 1) * fs;
+      if (c > c0) {
+#pragma unroll
+        for (int m = 0; m < NPM; ++m) {
+          const int j = t + m * nth;
+          cp[m] = (j < nx) ? ldr(cvec + (long long)(c - 1) * nx + j) : T(0);
+        }
       }
-      mv_any<T, CH>(tm, acc, pp.on, MFc, P.ldF, nx + nu, nx, s_in);
-      team_reduce<T, CH>(tm, acc, nx, s_red, [&](int j, int m, T v) {
-        const T xc = v + cp[m];
-        stc(vout + xo + j, xc);
-        if (chain) s_xb[j] = xc;
-      });
+      // x^c = Abar_c x^i + B_c d^i + c_c
+      T ax[NPM];
+#pragma unroll
+      for (int m = 0; m < NPM; ++m) ax[m] = T(0);
+      if (wide) {
+        if (t < nx) col_mv<T>(MFb, ldF, w, cin, t, nth, nx, ax);
+      } else {
+        col_mv<T>(MFb, ldF, w, cin, t, nth, nx, ax);
+      }
+#pragma unroll
+      for (int m = 0; m < NPM; ++m) {
+        const int j = t + m * nth;
+        if (j < nx) {
+          const T xc = ax[m] + cp[m];
+          stc(vout + o_x + (long long)c * nx + j, xc);
+          if (chain) cout[j] = xc;
+        }
+      }
+      // u^i = K x^i + d^i, once per node
+      if (c == c0) {
+        T au[NPM];
+#pragma unroll
+        for (int m = 0; m < NPM; ++m) au[m] = T(0);
+        if (wide) {
+          if (t >= nx && t < w) {
+            const int tu = t - nx;
+            col_mv<T>(KTb, ldK, nx, cin, tu, nth, nu, au);
+            stc(vout + o_u + (long long)i * nu + tu, au[0] + cin[nx + tu]);
+          }
+        } else {
+          col_mv<T>(KTb, ldK, nx, cin, t, nth, nu, au);
+#pragma unroll
+          for (int m = 0; m < NPM; ++m) {
+            const int j = t + m * nth;
+            if (j < nu) stc(vout + o_u + (long long)i * nu + j, au[m] + cin[nx + j]);
+          }
+        }
+      }
       if (pp.on) pp.cur ^= 1;
     }
     if (chain) {
-      i = c0;
-      T* t = s_xn; s_xn = s_xb; s_xb = t;
 #pragma unroll
-      for (int m = 0; m < PT; ++m) { dp[m] = dpn[m]; cp[m] = cpn[m]; }
+      for (int m = 0; m < NPM; ++m) {
+        const int j = t + m * nth;
+        if (j < nu) cout[nx + j] = dpn[m];
+        cp[m] = cpn[m];
+      }
+      tm.sync();
+      T* tt = cin; cin = cout; cout = tt;
+      i = c0;
     }
   }
+  tm.sync();   // the input buffers are reused by the team's next segment
   return ok;
 }
 
@@ -741,7 +841,7 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
     for (int l = 0; l < L; ++l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        backward_segment<T, CH>(P, tm, tb, tb + 3 * D, tb + 4 * D, pp, &g.ctl->error, s, pre, g.prof);
+        backward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre, g.prof);
         pre = false;
       }
       if (pp.on) {   // first copy of this team's next piece of work, before the barrier
@@ -763,8 +863,7 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
     for (int l = L - 1; l >= 0; --l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        forward_segment<T, CH>(P, tm, tb, tb + D, tb + 2 * D, tb + 4 * D, pp, &g.ctl->error, s,
-                               vout, pre);
+        forward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
         pre = false;
       }
       if (pp.on && l > 0) {
