@@ -310,6 +310,7 @@ __global__ void k_unscale(int n, int n_nl, int nx, int nu, long long o_x, long l
 // 2 * 32 * tw >= nx + nu (at most two output columns per thread)
 int pick_tw(int nx, int nu) {
   const int d = nx + nu;
+  if (2 * d <= 256 && d >= 32) return 8;   // whole-CTA sweeps (two threads per column)
   if (d >= 96) return 8;
   if (d >= 48) return 4;
   if (d >= 24) return 2;

@@ -537,6 +537,192 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_b
   return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Whole-CTA sweeps (the team is the CTA, 256 threads): two threads per output
+// column, each over half of the rows with four independent accumulators,
+// combined by one shuffle; one CTA barrier after the matrix has landed and one
+// after the carry is written. Used when 2 * (nx + nu) <= 256.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T pair_dot(const T* __restrict__ M, int ld, int col, int r0, int r1,
+                                      const T* __restrict__ in) {
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int k = r0;
+  for (; k + 4 <= r1; k += 4) {
+    a0 = fma(M[(size_t)k * ld + col], in[k], a0);
+    a1 = fma(M[(size_t)(k + 1) * ld + col], in[k + 1], a1);
+    a2 = fma(M[(size_t)(k + 2) * ld + col], in[k + 2], a2);
+    a3 = fma(M[(size_t)(k + 3) * ld + col], in[k + 3], a3);
+  }
+  for (; k < r1; ++k) a0 = fma(M[(size_t)k * ld + col], in[k], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// mbarrier wait by one thread, then a CTA barrier
+template <class T>
+__device__ __forceinline__ bool cta_wait(Pipe<T>& pp, int b, int* err) {
+  bool ok = true;
+  if (threadIdx.x == 0) ok = mbar_wait(pp.bar + b, pp.par[b], err);
+  pp.par[b] ^= 1u;
+  __syncthreads();
+  return ok;
+}
+
+template <class T>
+__device__ bool backward_segment_cta(const Prob<T>& P, const Team& tm, T* s_a, T* s_b, Pipe<T>& pp,
+                                     int* err, int s, bool prefetched) {
+  const int nx = P.nx, nu = P.nu, w = nx + nu, ldB = P.ldB;
+  const int t = threadIdx.x, col = t >> 1, half = t & 1;
+  const int kh = (nx + 1) >> 1;
+  const int r0 = half ? kh : 0, r1 = half ? nx : kh;
+  const bool has_col = col < w;
+  const size_t mstride = (size_t)nx * ldB;
+  const T* __restrict__ MB = P.MB;
+  T* __restrict__ qbuf = P.qbuf;
+  T* __restrict__ dbuf = P.dbuf;
+  const T* __restrict__ hbuf = P.hbuf;
+  const T* __restrict__ ebuf = P.ebuf;
+  Team issuer = tm;
+  issuer.tid = (t == blockDim.x - 1) ? 0 : 1;   // the last thread issues the copies
+  bool ok = true;
+  if (pp.on && !prefetched) issue_first_B<T, 1>(P, issuer, pp, s);
+  SegList sl;
+  sl.load(P, s, t & 31);
+  const int len = sl.len;
+  auto pre_of = [&](int node) -> T {
+    if (!has_col || half) return T(0);
+    return (col < nx) ? ldc(hbuf + (long long)node * nx + col) : ldc(ebuf + (long long)node * nu + (col - nx));
+  };
+  int i = sl.node(P, len - 1);
+  T pre = pre_of(i);
+  T* cin = s_a;
+  T* cout = s_b;
+  for (int step = 0; step < len; ++step) {
+    const bool bottom = (step == 0);
+    const int c0 = bottom ? sl.c0b : sl.node(P, len - step);
+    const int c1 = bottom ? sl.c1b : c0 + 1;
+    const int inext = (step + 1 < len) ? sl.node(P, len - 2 - step) : -1;
+    const T pren = (inext >= 0) ? pre_of(inext) : T(0);
+    T acc = 0;
+    for (int c = c0; c < c1; ++c) {
+      if (bottom)
+        for (int k = t; k < nx; k += blockDim.x) cin[k] = ldc(qbuf + (long long)c * nx + k);
+      if (pp.on) ok = cta_wait(pp, pp.cur, err) && ok;
+      else __syncthreads();
+      const int cn = (c + 1 < c1) ? c + 1 : ((inext >= 0) ? i : -1);
+      if (pp.on && cn > 0) issue_B(P, issuer, pp, pp.cur ^ 1, cn);
+      const T* Mb = pp.on ? pp.buf[pp.cur] : MB + (size_t)(c - 1) * mstride;
+      T v = has_col ? pair_dot(Mb, ldB, col, r0, r1, cin) : T(0);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      acc += v;
+      if (pp.on) pp.cur ^= 1;
+      if (bottom && c + 1 < c1) __syncthreads();
+    }
+    if (has_col && !half) {
+      if (col < nx) {
+        const T qq = acc + pre;
+        cout[col] = qq;
+        stc(qbuf + (long long)i * nx + col, qq);
+      } else {
+        stc(dbuf + (long long)i * nu + (col - nx), pre - acc);
+      }
+    }
+    __syncthreads();
+    T* tt = cin; cin = cout; cout = tt;
+    pre = pren;
+    i = inext;
+  }
+  return ok;
+}
+
+template <class T>
+__device__ bool forward_segment_cta(const Prob<T>& P, const Team& tm, T* s_a, T* s_b, Pipe<T>& pp,
+                                    int* err, int s, T* __restrict__ vout, bool prefetched) {
+  const int nx = P.nx, nu = P.nu, w = nx + nu, ldF = P.ldF, ldK = P.ldK;
+  const int t = threadIdx.x, col = t >> 1, half = t & 1;
+  const bool xcol = col < nx, ucol = (col >= nx) && (col < w);
+  // x columns run over nx + nu rows of MF, u columns over nx rows of KT
+  const int nr = xcol ? w : nx;
+  const int kh = (nr + 1) >> 1;
+  const int r0 = half ? kh : 0, r1 = half ? nr : kh;
+  const size_t ks = (size_t)nx * ldK, fs = (size_t)w * ldF;
+  const T* __restrict__ dbuf = P.dbuf;
+  const T* __restrict__ cvec = P.cvec;
+  const long long o_x = P.o_x, o_u = P.o_u;
+  Team issuer = tm;
+  issuer.tid = (t == blockDim.x - 1) ? 0 : 1;
+  bool ok = true;
+  if (pp.on && !prefetched) issue_first_F<T, 1>(P, issuer, pp, s);
+  SegList sl;
+  sl.load(P, s, t & 31);
+  const int len = sl.len;
+  auto first_child = [&](int k) { return (k + 1 < len) ? sl.node(P, k + 1) : sl.c0b; };
+  int i = sl.node(P, 0);
+  T* cin = s_a;
+  T* cout = s_b;
+  for (int k = t; k < w; k += blockDim.x) {
+    T v;
+    if (k < nx) {
+      if (i == 0) {
+        v = P.x0s[k];
+        stc(vout + o_x + k, v);
+      } else {
+        v = ldc(vout + o_x + (long long)i * nx + k);
+      }
+    } else {
+      v = ldc(dbuf + (long long)i * nu + (k - nx));
+    }
+    cin[k] = v;
+  }
+  T cp = (xcol && !half) ? ldr(cvec + (long long)(first_child(0) - 1) * nx + col) : T(0);
+  for (int step = 0; step < len; ++step) {
+    const bool chain = (step + 1 < len);
+    const int c0 = first_child(step);
+    const int c1 = chain ? c0 + 1 : sl.c1b;
+    T dpn = 0, cpn = 0;
+    if (chain && !half) {
+      const int cn = first_child(step + 1);
+      if (col < nu) dpn = ldc(dbuf + (long long)c0 * nu + col);
+      if (xcol) cpn = ldr(cvec + (long long)(cn - 1) * nx + col);
+    }
+    for (int c = c0; c < c1; ++c) {
+      if (pp.on) {
+        ok = cta_wait(pp, pp.cur, err) && ok;
+        if (c + 1 < c1) issue_F(P, issuer, pp, pp.cur ^ 1, i, c + 1, false);
+        else if (chain) issue_F(P, issuer, pp, pp.cur ^ 1, c0, first_child(step + 1), true);
+      } else {
+        __syncthreads();
+      }
+      const T* KTb = pp.on ? pp.buf[pp.cur] : P.KT + (size_t)i * ks;
+      const T* MFb = pp.on ? KTb + ks : P.MF + (size_t)(c - 1) * fs;
+      if (c > c0 && xcol && !half) cp = ldr(cvec + (long long)(c - 1) * nx + col);
+      T v = 0;
+      if (xcol) v = pair_dot(MFb, ldF, col, r0, r1, cin);
+      else if (ucol && c == c0) v = pair_dot(KTb, ldK, col - nx, r0, r1, cin);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      if (!half) {
+        if (xcol) {
+          const T xc = v + cp;
+          stc(vout + o_x + (long long)c * nx + col, xc);
+          if (chain) cout[col] = xc;
+        } else if (ucol && c == c0) {
+          stc(vout + o_u + (long long)i * nu + (col - nx), v + cin[col]);
+        }
+      }
+      if (pp.on) pp.cur ^= 1;
+    }
+    if (chain) {
+      if (!half && col < nu) cout[nx + col] = dpn;
+      cp = cpn;
+      __syncthreads();
+      T* tt = cin; cin = cout; cout = tt;
+      i = c0;
+    }
+  }
+  __syncthreads();
+  return ok;
+}
+
 // z residual of the x (and u) of one node, accumulated by one warp (phase E)
 template <class T>
 __device__ __forceinline__ void z_resid(const T* __restrict__ vin, const T* __restrict__ vout,
@@ -836,12 +1022,14 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
   pc.mark(ctl, 0);
   // B
   const int L = P.n_levels;
+  const bool cta_team = (tm.nth == (int)blockDim.x) && (2 * (P.nx + P.nu) <= (int)blockDim.x);
   {
     T* tb = sv.t_base(tm.id);
     for (int l = 0; l < L; ++l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        backward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre, g.prof);
+        if (cta_team) backward_segment_cta<T>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre);
+        else backward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre, g.prof);
         pre = false;
       }
       if (pp.on) {   // first copy of this team's next piece of work, before the barrier
@@ -863,7 +1051,8 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
     for (int l = L - 1; l >= 0; --l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        forward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
+        if (cta_team) forward_segment_cta<T>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
+        else forward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
         pre = false;
       }
       if (pp.on && l > 0) {
