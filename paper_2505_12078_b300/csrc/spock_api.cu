@@ -6,6 +6,8 @@
 // (Sec. 5.4 preconditioning, Alg. 1, ||L||) runs in FP64 kernels at creation.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -362,7 +364,12 @@ int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t 
   if (cudaStreamSynchronize(st) != cudaSuccess) return SPOCK_EDEVICE;
   if (ms) cudaEventElapsedTime(ms, p->ev0, p->ev1);
   for (int q = 0; q < 16; ++q) g_last_prof[q] = h_ctl->prof[q];
-  if (h_ctl->status < 0) return SPOCK_ETIMEOUT;
+  if (h_ctl->status < 0) {
+    if (getenv("SPOCK_DEBUG"))
+      fprintf(stderr, "spock: device wait gave up: cta %d barrier 0x%x parity %d site %d\n",
+              h_ctl->diag[0], h_ctl->diag[1], h_ctl->diag[2], h_ctl->diag[3]);
+    return SPOCK_ETIMEOUT;
+  }
   return SPOCK_OK;
 }
 

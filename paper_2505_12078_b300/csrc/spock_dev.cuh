@@ -476,16 +476,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 // Wait for phase `parity` of the mbarrier; false (and *err set) after the
 // time limit. A second bounded wait lets a late copy land before the caller
 // leaves, so no copy into this CTA's shared memory is left in flight.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+// diag (may be null): 4 ints recording the first wait that gave up
+// (CTA, buffer address, parity, site)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err,
+                                          int* diag = nullptr, int site = 0) {
   unsigned spins = 0;
   uint64_t t0 = 0;
   while (!mbar_try_wait(bar, parity)) {
     if ((++spins & 255u) == 0u) {
+      if (ld_relaxed_i(err)) return false;      // the launch is already failing: leave now
       const uint64_t t = global_ns();
       if (t0 == 0) {
         t0 = t;
       } else if (t - t0 > BARRIER_LIMIT_NS) {
-        atomicExch(err, 2);
+        if (atomicCAS(err, 0, 2) == 0 && diag) {
+          diag[0] = blockIdx.x;
+          diag[1] = (int)smem_u32(bar);
+          diag[2] = (int)parity;
+          diag[3] = site;
+        }
         const uint64_t t1 = global_ns();
         while (!mbar_try_wait(bar, parity) && global_ns() - t1 < BARRIER_LIMIT_NS) {
         }
@@ -506,6 +515,8 @@ struct Pipe {
   unsigned par[2];
   int cur;
   bool on;           // false: matrices are read from global memory
+  int* okp;          // shared int of the team: result of the last wait
+  int* diag;         // where the first wait that gave up is recorded
   __device__ __forceinline__ void issue(const Team& tm, int b, const T* src, unsigned bytes) {
     if (tm.tid == 0) {
       fence_proxy_async();
@@ -515,12 +526,13 @@ struct Pipe {
   }
   // thread 0 of the team polls the mbarrier (non-suspending test_wait); the
   // team barrier then hands the completed copy to every thread of the team
-  __device__ __forceinline__ bool wait(const Team& tm, int b, int* err) {
-    bool ok = true;
-    if (tm.tid == 0) ok = mbar_wait(bar + b, par[b], err);
+  // ok_slot: shared int of this team that hands the result to every thread
+  __device__ __forceinline__ bool wait(const Team& tm, int b, int* err, int* ok_slot,
+                                       int* diag = nullptr, int site = 0) {
+    if (tm.tid == 0) *ok_slot = mbar_wait(bar + b, par[b], err, diag, site) ? 1 : 0;
     par[b] ^= 1u;
     tm.sync();
-    return ok;
+    return *ok_slot != 0;
   }
 };
 

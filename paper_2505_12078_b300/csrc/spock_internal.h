@@ -61,7 +61,7 @@ struct SolveCtl {
   double stats[NRED];  // reduction of the last T evaluation of the final iterate
   int final_v;         // index (0..3 of V, TV, VT, TVT) holding the final iterate v
   int final_tv;        // index holding T(v)
-  int pad0, pad1;
+  int diag[4];         // first bulk-copy wait that gave up: CTA, barrier, parity, site
   // device time per phase seen by CTA 0 (ns, barrier waits included):
   // 0 prep, 1 backward sweep, 2 forward sweep, 3 T reduction, 4 Anderson dots,
   // 5 direction pass, 6 K2/backtrack passes, 7 count of T evaluations;

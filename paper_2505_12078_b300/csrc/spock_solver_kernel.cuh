@@ -364,8 +364,11 @@ __device__ bool backward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_
         for (int k = t; k < nx; k += nth) cin[k] = ldc(qbuf + (long long)c * nx + k);
       }
       pr.mark(11);
-      if (pp.on) ok = pp.wait(tm, pp.cur, err) && ok;   // includes a team barrier
-      else tm.sync();
+      if (pp.on) {
+        if (!pp.wait(tm, pp.cur, err, pp.okp, pp.diag, 1)) return false;   // includes a team barrier
+      } else {
+        tm.sync();
+      }
       pr.mark(8);
       // next item into the other buffer (read before the barrier just passed)
       const int cn = (c + 1 < c1) ? c + 1 : ((inext >= 0) ? i : -1);
@@ -466,7 +469,7 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_b
     }
     for (int c = c0; c < c1; ++c) {
       if (pp.on) {
-        ok = pp.wait(tm, pp.cur, err) && ok;      // includes a team barrier
+        if (!pp.wait(tm, pp.cur, err, pp.okp, pp.diag, 2)) return false;      // includes a team barrier
         if (c + 1 < c1) issue_F(P, tm, pp, pp.cur ^ 1, i, c + 1, false);
         else if (chain) issue_F(P, tm, pp, pp.cur ^ 1, c0, first_child(step + 1), true);
       } else {
@@ -560,12 +563,11 @@ __device__ __forceinline__ T pair_dot(const T* __restrict__ M, int ld, int col, 
 
 // mbarrier wait by one thread, then a CTA barrier
 template <class T>
-__device__ __forceinline__ bool cta_wait(Pipe<T>& pp, int b, int* err) {
-  bool ok = true;
-  if (threadIdx.x == 0) ok = mbar_wait(pp.bar + b, pp.par[b], err);
+__device__ __forceinline__ bool cta_wait(Pipe<T>& pp, int b, int* err, int site) {
+  if (threadIdx.x == 0) *pp.okp = mbar_wait(pp.bar + b, pp.par[b], err, pp.diag, site) ? 1 : 0;
   pp.par[b] ^= 1u;
   __syncthreads();
-  return ok;
+  return *pp.okp != 0;
 }
 
 template <class T>
@@ -607,8 +609,11 @@ __device__ bool backward_segment_cta(const Prob<T>& P, const Team& tm, T* s_a, T
     for (int c = c0; c < c1; ++c) {
       if (bottom)
         for (int k = t; k < nx; k += blockDim.x) cin[k] = ldc(qbuf + (long long)c * nx + k);
-      if (pp.on) ok = cta_wait(pp, pp.cur, err) && ok;
-      else __syncthreads();
+      if (pp.on) {
+        if (!cta_wait(pp, pp.cur, err, 3)) return false;
+      } else {
+        __syncthreads();
+      }
       const int cn = (c + 1 < c1) ? c + 1 : ((inext >= 0) ? i : -1);
       if (pp.on && cn > 0) issue_B(P, issuer, pp, pp.cur ^ 1, cn);
       const T* Mb = pp.on ? pp.buf[pp.cur] : MB + (size_t)(c - 1) * mstride;
@@ -687,7 +692,7 @@ __device__ bool forward_segment_cta(const Prob<T>& P, const Team& tm, T* s_a, T*
     }
     for (int c = c0; c < c1; ++c) {
       if (pp.on) {
-        ok = cta_wait(pp, pp.cur, err) && ok;
+        if (!cta_wait(pp, pp.cur, err, 4)) return false;
         if (c + 1 < c1) issue_F(P, issuer, pp, pp.cur ^ 1, i, c + 1, false);
         else if (chain) issue_F(P, issuer, pp, pp.cur ^ 1, c0, first_child(step + 1), true);
       } else {
@@ -1028,8 +1033,9 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
     for (int l = 0; l < L; ++l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        if (cta_team) backward_segment_cta<T>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre);
-        else backward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre, g.prof);
+        const bool okb = cta_team ? backward_segment_cta<T>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre)
+                                  : backward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre, g.prof);
+        if (!okb) return false;
         pre = false;
       }
       if (pp.on) {   // first copy of this team's next piece of work, before the barrier
@@ -1051,8 +1057,9 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
     for (int l = L - 1; l >= 0; --l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        if (cta_team) forward_segment_cta<T>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
-        else forward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
+        const bool okf = cta_team ? forward_segment_cta<T>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre)
+                                  : forward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
+        if (!okf) return false;
         pre = false;
       }
       if (pp.on && l > 0) {
@@ -1139,6 +1146,9 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
   pp.buf[1] = sv.t_pipe(tm.id, 1);
   pp.par[0] = pp.par[1] = 0u;
   pp.cur = 0;
+  __shared__ int s_ok[MAXTW];
+  pp.okp = s_ok + tm.id;
+  pp.diag = B.ctl->diag;
   if (threadIdx.x < 2 * MAXTW) mbar_init(s_bar + threadIdx.x, 1);
   fence_mbar_init();
   __syncthreads();
