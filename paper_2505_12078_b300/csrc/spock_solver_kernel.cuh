@@ -679,14 +679,16 @@ __device__ bool forward_segment_cta(const Prob<T>& P, const Team& tm, T* s_a, T*
     }
     cin[k] = v;
   }
-  T cp = (xcol && !half) ? ldr(cvec + (long long)(first_child(0) - 1) * nx + col) : T(0);
+  // node indices come from warp shuffles: evaluate them in uniform control flow
+  const int fc0 = first_child(0);
+  T cp = (xcol && !half) ? ldr(cvec + (long long)(fc0 - 1) * nx + col) : T(0);
   for (int step = 0; step < len; ++step) {
     const bool chain = (step + 1 < len);
     const int c0 = first_child(step);
     const int c1 = chain ? c0 + 1 : sl.c1b;
+    const int cn = chain ? first_child(step + 1) : -1;
     T dpn = 0, cpn = 0;
     if (chain && !half) {
-      const int cn = first_child(step + 1);
       if (col < nu) dpn = ldc(dbuf + (long long)c0 * nu + col);
       if (xcol) cpn = ldr(cvec + (long long)(cn - 1) * nx + col);
     }
@@ -694,7 +696,7 @@ __device__ bool forward_segment_cta(const Prob<T>& P, const Team& tm, T* s_a, T*
       if (pp.on) {
         if (!cta_wait(pp, pp.cur, err, 4)) return false;
         if (c + 1 < c1) issue_F(P, issuer, pp, pp.cur ^ 1, i, c + 1, false);
-        else if (chain) issue_F(P, issuer, pp, pp.cur ^ 1, c0, first_child(step + 1), true);
+        else if (chain) issue_F(P, issuer, pp, pp.cur ^ 1, c0, cn, true);
       } else {
         __syncthreads();
       }
