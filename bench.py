@@ -16,6 +16,12 @@ method has no data-parallel split of one problem): value = iterations of all
 ranks / the slowest rank's time. --impl reference times the FP64 CPU oracle on
 the same workload (rank 0 only).
 """
+import os
+
+# the CPU oracle runs single-threaded (set before numpy is imported)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
 import math
@@ -120,17 +126,15 @@ class ClockSampler:
 
 def cpu_baseline(p, seconds=12.0):
     """The FP64 oracle as it stands, on the same workload, for a bounded sample."""
-    from threadpoolctl import threadpool_limits
     from oracle.spock_oracle import Oracle
-    with threadpool_limits(limits=1):
-        o = Oracle(p)
-        t = time.time()
-        o.T(o.initial_v())
-        per_T = time.time() - t
-        iters = max(3, int(seconds / (2.3 * per_T)))
-        t = time.time()
-        r = o.solve(tol=0.0, max_iters=iters)
-        el = time.time() - t
+    o = Oracle(p)
+    t = time.time()
+    o.T(o.initial_v())
+    per_T = time.time() - t
+    iters = max(3, int(seconds / (2.3 * per_T)))
+    t = time.time()
+    r = o.solve(tol=0.0, max_iters=iters)
+    el = time.time() - t
     return {"value": r["iters"] / el, "unit": "iter/s", "cores": 1, "kind": "oracle",
             "sample": f"{r['iters']} SPOCK iterations ({r['n_T']} T evaluations) of the same "
                       f"workload from a cold start, FP64 numpy oracle, {el:.1f} s"}
@@ -140,20 +144,18 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from paper_2505_12078_b300 import synth
-    from threadpoolctl import threadpool_limits
     from oracle.spock_oracle import Oracle
     p = synth.large_raocp()
-    with threadpool_limits(limits=1):
-        o = Oracle(p)
-        step_iters = 12
-        for _ in range(args.warmup):
-            o.solve(tol=0.0, max_iters=2)
-        times, iters = [], 0
-        for _ in range(args.steps):
-            t = time.time()
-            r = o.solve(tol=0.0, max_iters=step_iters)
-            times.append(time.time() - t)
-            iters += r["iters"]
+    o = Oracle(p)
+    step_iters = 12
+    for _ in range(args.warmup):
+        o.solve(tol=0.0, max_iters=2)
+    times, iters = [], 0
+    for _ in range(args.steps):
+        t = time.time()
+        r = o.solve(tol=0.0, max_iters=step_iters)
+        times.append(time.time() - t)
+        iters += r["iters"]
     total = sum(times)
     value = iters / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
