@@ -135,6 +135,26 @@ int spock_problem_set_x0(spock_problem* p, const double* x0);
 int spock_op_T(spock_problem* p, int precision, const void* v_in, void* v_out, double* stats,
                void* stream);
 
+/* spock_op_T_noalloc: the same evaluation of T as spock_op_T, for callers that
+ * cannot allocate device memory at the time of the call -- for example code
+ * running under a memory pool or allocator it does not own, inside a
+ * real-time loop where an allocation could block, or in a process whose
+ * device memory is fully reserved by another framework. It calls no
+ * cudaMalloc/cudaFree: all of its scratch (control block, barrier flags,
+ * reduction partials and the sweep vectors, about 2 (n nx + n_nl nu) words
+ * plus 160 KB) comes from one static device array of
+ * SPOCK_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits. Problems needing more return SPOCK_EUNSUPPORTED.
+ * The first call on a device looks the array's address up on that device
+ * (it must be the current device); make that first call before any stream
+ * capture. Every call shares the array and resets what must start at zero;
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller. The paper has no counterpart of this call.
+ * Arguments, layout and stats as for spock_op_T. Blocking. */
+#define SPOCK_NOALLOC_SCRATCH_BYTES (8 << 20)
+int spock_op_T_noalloc(spock_problem* p, int precision, const void* v_in, void* v_out,
+                       double* stats, void* stream);
+
 /* eta = L z (Sec. 4.4) and z = L* eta. (device) buffers of n_z / n_eta elements. */
 int spock_op_L(spock_problem* p, int precision, const void* z, void* eta, void* stream);
 int spock_op_Lt(spock_problem* p, int precision, const void* eta, void* z, void* stream);

@@ -23,6 +23,7 @@ UNITS = [
     ("spock_api", "spock_api.cu", []),
     ("spock_setup", "spock_setup.cu", []),
     ("spock_solver", "spock_solver.cu", []),
+    ("spock_noalloc", "spock_noalloc.cu", []),
     ("solver_f1", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=1", "-DSPOCK_SUFFIX=f1"]),
     ("solver_f2", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=f2"]),
     ("solver_d2", "spock_solver_inst.cu", ["-DSPOCK_T=double", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=d2"]),

@@ -380,6 +380,80 @@ T* buf_index(SolveBufs<T>& b, int i) {
 
 }  // namespace
 
+// One evaluation of T whose scratch (control block, barrier flags, reduction
+// partials and the sweep vectors q, d, h, e) is carved from a caller-provided
+// device region instead of the problem's own buffers. Allocates nothing.
+// Returns SPOCK_EUNSUPPORTED when the region is too small.
+namespace spock {
+int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v_out,
+                      double* stats, cudaStream_t st, unsigned char* scratch, size_t bytes) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPOCK_EDEVICE;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t maxg = (size_t)nsm * 8;
+  const size_t w = (precision == 64) ? 8 : 4;
+  size_t off = 0;
+  const size_t o_ctl = off;   off += al(sizeof(SolveCtl));
+  const size_t o_flags = off; off += al(maxg * sizeof(unsigned));
+  const size_t o_part = off;  off += al(2 * maxg * NRED * sizeof(double));
+  const size_t o_q = off;     off += al((size_t)p->n * p->nx * w);
+  const size_t o_d = off;     off += al((size_t)p->n_nl * p->nu * w);
+  const size_t o_h = off;     off += al((size_t)p->n_nl * p->nx * w);
+  const size_t o_e = off;     off += al((size_t)p->n_nl * p->nu * w);
+  if (off > bytes) return SPOCK_EUNSUPPORTED;
+  SolveCtl* ctl = reinterpret_cast<SolveCtl*>(scratch + o_ctl);
+  unsigned* flags = reinterpret_cast<unsigned*>(scratch + o_flags);
+  // what must start at zero: the control block (barrier state, error word) and the flags
+  if (cudaMemsetAsync(ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (cudaMemsetAsync(flags, 0, maxg * sizeof(unsigned), st) != cudaSuccess) return SPOCK_EDEVICE;
+  SolveOpts so{1e300, 0, 1, 2, 1e-10};
+  const int teams = (kThreads / 32) / p->tw;
+  cudaError_t e;
+  int maxgrid = 0;
+  if (precision == 64) {
+    Prob<double> P = p->f64.P;
+    P.qbuf = reinterpret_cast<double*>(scratch + o_q);
+    P.dbuf = reinterpret_cast<double*>(scratch + o_d);
+    P.hbuf = reinterpret_cast<double*>(scratch + o_h);
+    P.ebuf = reinterpret_cast<double*>(scratch + o_e);
+    P.pipe_bytes = p->use_pipe ? pipe_bytes_for<double>(p) : 0;
+    if (solver_max_grid(64, p->tw, kThreads, p->nx + p->nu, P.pipe_bytes, &maxgrid) || maxgrid <= 0)
+      return SPOCK_EDEVICE;
+    int grid = std::min((p->max_items + teams - 1) / teams, std::min(maxgrid, (int)maxg));
+    SolveBufs<double> B{};
+    B.V = (double*)v_in; B.TV = (double*)v_out;
+    B.partials = reinterpret_cast<double*>(scratch + o_part);
+    B.flags = flags; B.ctl = ctl;
+    e = launch_solve<double>(P, B, so, p->tw, std::max(grid, 1), kThreads, st);
+  } else {
+    Prob<float> P = p->f32.P;
+    P.qbuf = reinterpret_cast<float*>(scratch + o_q);
+    P.dbuf = reinterpret_cast<float*>(scratch + o_d);
+    P.hbuf = reinterpret_cast<float*>(scratch + o_h);
+    P.ebuf = reinterpret_cast<float*>(scratch + o_e);
+    P.pipe_bytes = p->use_pipe ? pipe_bytes_for<float>(p) : 0;
+    if (solver_max_grid(32, p->tw, kThreads, p->nx + p->nu, P.pipe_bytes, &maxgrid) || maxgrid <= 0)
+      return SPOCK_EDEVICE;
+    int grid = std::min((p->max_items + teams - 1) / teams, std::min(maxgrid, (int)maxg));
+    SolveBufs<float> B{};
+    B.V = (float*)v_in; B.TV = (float*)v_out;
+    B.partials = reinterpret_cast<double*>(scratch + o_part);
+    B.flags = flags; B.ctl = ctl;
+    e = launch_solve<float>(P, B, so, p->tw, std::max(grid, 1), kThreads, st);
+  }
+  if (e != cudaSuccess) return SPOCK_EDEVICE;
+  SolveCtl h{};
+  if (cudaMemcpyAsync(&h, ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SPOCK_EDEVICE;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (h.status < 0) return SPOCK_ETIMEOUT;
+  if (stats)
+    for (int k = 0; k < 8; ++k) stats[k] = h.stats[k];
+  return SPOCK_OK;
+}
+}  // namespace spock
+
 extern "C" {
 
 int spock_version(void) { return 1; }

@@ -89,3 +89,9 @@ size_t solver_smem_bytes(int precision, int tw, int threads, int D, int pipe_byt
 int solver_chunks(int precision, int width);
 
 }  // namespace spock
+
+struct spock_problem;
+namespace spock {
+int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v_out,
+                      double* stats, cudaStream_t st, unsigned char* scratch, size_t bytes);
+}  // namespace spock

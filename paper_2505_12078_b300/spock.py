@@ -25,7 +25,7 @@ EXPORTED = [
     "spock_problem_set_alpha", "spock_problem_scalings", "spock_problem_factors",
     "spock_problem_set_x0", "spock_op_T", "spock_op_L", "spock_op_Lt", "spock_solve_opts_default",
     "spock_solve", "spock_solve_device", "spock_get_iterate", "spock_set_iterate",
-    "spock_status_str", "spock_version",
+    "spock_status_str", "spock_version", "spock_op_T_noalloc",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
     lib.spock_problem_factors.argtypes = [vp, _dp, _dp, _dp, _dp]
     lib.spock_problem_set_x0.argtypes = [vp, _dp]
     lib.spock_op_T.argtypes = [vp, C.c_int, vp, vp, _dp, vp]
+    lib.spock_op_T_noalloc.argtypes = [vp, C.c_int, vp, vp, _dp, vp]
     lib.spock_op_L.argtypes = [vp, C.c_int, vp, vp, vp]
     lib.spock_op_Lt.argtypes = [vp, C.c_int, vp, vp, vp]
     lib.spock_solve_opts_default.argtypes = [C.POINTER(SolveOpts)]
@@ -224,6 +225,18 @@ class Problem:
         _check(load().spock_op_T(self.h, self._prec(v_in), C.c_void_p(v_in.data_ptr()),
                                  C.c_void_p(v_out.data_ptr()), _ptr(stats),
                                  C.c_void_p(stream.cuda_stream if stream else 0)), "spock_op_T")
+        return v_out, stats
+
+    def T_noalloc(self, v_in, v_out, stream=None):
+        """v_out = T(v_in) through spock_op_T_noalloc (no device allocation in
+        the call; scratch from the library's static device array)."""
+        assert v_in.is_cuda and v_in.is_contiguous() and v_in.numel() == self.n_v
+        assert v_out.is_cuda and v_out.is_contiguous() and v_out.numel() == self.n_v
+        stats = np.zeros(8)
+        _check(load().spock_op_T_noalloc(self.h, self._prec(v_in), C.c_void_p(v_in.data_ptr()),
+                                         C.c_void_p(v_out.data_ptr()), _ptr(stats),
+                                         C.c_void_p(stream.cuda_stream if stream else 0)),
+               "spock_op_T_noalloc")
         return v_out, stats
 
     def L(self, z, eta=None):
