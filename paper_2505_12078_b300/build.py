@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libspock.so")
-HEADERS = ["spock_dev.cuh", "spock_internal.h", "spock_solver_kernel.cuh"]
+HEADERS = ["spock_dev.cuh", "spock_internal.h", "spock_solver_kernel.cuh", "spock_cta.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (object name, source, extra defines)
 UNITS = [

@@ -16,6 +16,7 @@
 #include "../../include/spock.h"
 #include "spock_dev.cuh"
 #include "spock_internal.h"
+#include "spock_cta.cuh"
 
 using namespace spock;
 
@@ -52,6 +53,10 @@ struct Iter {   // per-precision iteration data
   T *box_lo = nullptr, *box_hi = nullptr, *boxN_lo = nullptr, *boxN_hi = nullptr, *ball = nullptr;
   T *prob = nullptr, *avar = nullptr, *x0s = nullptr;
   T *qbuf = nullptr, *dbuf = nullptr, *hbuf = nullptr, *ebuf = nullptr;
+  // whole-CTA sweeps: output-column-major factors and their layout
+  T *MBt = nullptr, *MFt = nullptr, *KTt = nullptr;
+  int cta = 0, ldTB = 0, ldTF = 0, ldTK = 0, khB = 0, khF = 0, nbuf = 0, item_bytes = 0, qslots = 0,
+      ldc = 0;
   SolveBufs<T> sb{};
   bool have_bufs = false;
   Prob<T> P{};
@@ -70,6 +75,7 @@ struct spock_problem {
   std::vector<double> Sx, Su, SxN;
   double a_con = 1, a_conN = 1, alpha = 0, normL = 0;
   int max_items = 1;
+  int maxch = 1;       // most children of a node
   int tw = 8;
   int use_pipe = 1;    // stream the sweep matrices through shared memory
   DevMem mem;
@@ -216,11 +222,60 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.lvl_off = p->d_lvl_off; P.seg_top = p->d_seg_top; P.seg_bot = p->d_seg_bot; P.seg_len = p->d_seg_len;
   P.seg_off = p->d_seg_off; P.seg_nodes = p->d_seg_nodes; P.seg_info = p->d_seg_info;
   P.MB = it.MB; P.MF = it.MF; P.MP = it.MP; P.KT = it.KT; P.cvec = it.cvec; P.kc = it.kc;
+  P.cta = it.cta; P.ldTB = it.ldTB; P.ldTF = it.ldTF; P.ldTK = it.ldTK; P.khB = it.khB; P.khF = it.khF;
+  P.nbuf = it.nbuf; P.item_bytes = it.item_bytes; P.qslots = it.qslots; P.ldc = it.ldc;
+  P.MBt = it.MBt; P.MFt = it.MFt; P.KTt = it.KTt;
   P.qh = it.qh; P.rh = it.rh; P.qNh = it.qNh; P.gx = it.gx; P.gu = it.gu; P.gN = it.gN;
   P.box_lo = it.box_lo; P.box_hi = it.box_hi; P.boxN_lo = it.boxN_lo; P.boxN_hi = it.boxN_hi;
   P.ball = it.ball; P.prob = it.prob; P.avar = it.avar; P.x0s = it.x0s;
   P.alpha = (T)alpha;
   P.qbuf = it.qbuf; P.dbuf = it.dbuf; P.hbuf = it.hbuf; P.ebuf = it.ebuf;
+}
+
+// Whole-CTA sweep layout (nx + nu <= 128): a column of a transposed factor is
+// padded to a multiple of 16 bytes whose byte length is 32 or 96 mod 128, and
+// the second thread of a column starts at a row whose byte offset is 16 mod 32;
+// the four columns x two halves that one quarter-warp reads with 16-byte loads
+// then fall on eight different 16-byte bank groups.
+int cta_ld(int rows, int es) {
+  const int q = 16 / es;
+  int ld = (rows + q - 1) / q * q;
+  while ((ld * es) % 128 != 32 && (ld * es) % 128 != 96) ld += q;
+  return ld;
+}
+int cta_kh(int rows, int es) {
+  int kh = (rows + 1) / 2;
+  while ((kh * es) % 32 != 16) ++kh;
+  return kh;
+}
+
+template <class T>
+void cta_layout(spock_problem* p, Iter<T>& it) {
+  const int nx = p->nx, nu = p->nu, es = (int)sizeof(T);
+  it.cta = 0;
+  if (!(p->tw == 8 && 2 * (nx + nu) <= kThreads)) return;
+  it.ldTB = cta_ld(nx, es);
+  it.ldTF = cta_ld(nx + nu, es);
+  it.ldTK = cta_ld(nx, es);
+  it.khB = cta_kh(nx, es);
+  it.khF = cta_kh(nx + nu, es);
+  const long long eb = (long long)(nx + nu) * it.ldTB;
+  const long long ef = (long long)nu * it.ldTK + (long long)nx * it.ldTF;
+  it.item_bytes = (int)((std::max(eb, ef) * es + 127) / 128 * 128);
+  it.ldc = (nx + nu + 7) / 8 * 8;
+  it.qslots = std::min(p->maxch, 8);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int prec = es == 8 ? 64 : 32;
+  // static shared memory of the kernel and the per-warp / per-team views
+  const long long fixed = 24 * 1024 + (long long)solver_smem_bytes(prec, p->tw, kThreads, nx + nu, 0) +
+                          (long long)(2 + it.qslots) * it.ldc * es;
+  const long long room = (long long)optin - fixed;
+  const int nbuf = (int)std::min<long long>(4, room > 0 ? room / it.item_bytes : 0);
+  if (nbuf < 2) return;
+  it.nbuf = nbuf;
+  it.cta = 1;
 }
 
 template <class T>
@@ -249,6 +304,12 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
   it.dbuf = m.alloc<T>((long long)n_nl * nu);
   it.hbuf = m.alloc<T>((long long)n_nl * nx);
   it.ebuf = m.alloc<T>((long long)n_nl * nu);
+  cta_layout<T>(p, it);
+  if (it.cta) {
+    it.MBt = m.alloc<T>((long long)(n - 1) * (nx + nu) * it.ldTB);
+    it.MFt = m.alloc<T>((long long)(n - 1) * nx * it.ldTF);
+    it.KTt = m.alloc<T>((long long)n_nl * nu * it.ldTK);
+  }
   return m.failed ? SPOCK_ENOMEM : SPOCK_OK;
 }
 
@@ -324,6 +385,7 @@ int pick_tw(int nx, int nu) {
 // matrices from global memory).
 template <class T>
 int pipe_bytes_for(const spock_problem* p) {
+  if ((sizeof(T) == 8 ? p->f64.cta : p->f32.cta)) return 0;   // the whole-CTA sweeps have their ring
   // backward item: MB; forward item: [KT | MF]
   const long long e = std::max((long long)p->nx * p->ldB,
                                (long long)(p->nx + p->nu) * p->ldF + (long long)p->nx * p->ldK);
@@ -347,7 +409,8 @@ int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t 
   const int prec = sizeof(T) == 8 ? 64 : 32;
   it.P.pipe_bytes = p->use_pipe ? pipe_bytes_for<T>(p) : 0;
   int maxg = 0;
-  if (solver_max_grid(prec, p->tw, kThreads, p->nx + p->nu, it.P.pipe_bytes, &maxg) || maxg <= 0)
+  if (solver_max_grid(prec, p->tw, kThreads, p->nx + p->nu, it.P.pipe_bytes, cta_smem_bytes(it.P), &maxg) ||
+      maxg <= 0)
     return SPOCK_EDEVICE;
   const int teams = (kThreads / 32) / p->tw;
   int grid = (p->max_items + teams - 1) / teams;
@@ -418,7 +481,8 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
     P.hbuf = reinterpret_cast<double*>(scratch + o_h);
     P.ebuf = reinterpret_cast<double*>(scratch + o_e);
     P.pipe_bytes = p->use_pipe ? pipe_bytes_for<double>(p) : 0;
-    if (solver_max_grid(64, p->tw, kThreads, p->nx + p->nu, P.pipe_bytes, &maxgrid) || maxgrid <= 0)
+    if (solver_max_grid(64, p->tw, kThreads, p->nx + p->nu, P.pipe_bytes, cta_smem_bytes(P), &maxgrid) ||
+        maxgrid <= 0)
       return SPOCK_EDEVICE;
     int grid = std::min((p->max_items + teams - 1) / teams, std::min(maxgrid, (int)maxg));
     SolveBufs<double> B{};
@@ -433,7 +497,8 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
     P.hbuf = reinterpret_cast<float*>(scratch + o_h);
     P.ebuf = reinterpret_cast<float*>(scratch + o_e);
     P.pipe_bytes = p->use_pipe ? pipe_bytes_for<float>(p) : 0;
-    if (solver_max_grid(32, p->tw, kThreads, p->nx + p->nu, P.pipe_bytes, &maxgrid) || maxgrid <= 0)
+    if (solver_max_grid(32, p->tw, kThreads, p->nx + p->nu, P.pipe_bytes, cta_smem_bytes(P), &maxgrid) ||
+        maxgrid <= 0)
       return SPOCK_EDEVICE;
     int grid = std::min((p->max_items + teams - 1) / teams, std::min(maxgrid, (int)maxg));
     SolveBufs<float> B{};
@@ -532,6 +597,7 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   // preconditioning scalings (Sec. 5.4)
   int maxch = 1;
   for (int i = 0; i < n_nl; ++i) maxch = std::max(maxch, p->ch_off[i + 1] - p->ch_off[i]);
+  p->maxch = maxch;
   const double chat = sqrt((double)maxch);
   p->Sx.assign(nx, 1.0); p->Su.assign(nu, 1.0); p->SxN.assign(nx, 1.0);
   for (int c = 1; c < n; ++c) {
@@ -681,6 +747,17 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   float* dst[] = {g.MB, g.MF, g.MP, g.KT, g.cvec, g.kc, g.qh, g.rh, g.qNh, g.gx, g.gu, g.gN,
                   g.box_lo, g.box_hi, g.boxN_lo, g.boxN_hi, g.ball, g.prob, g.avar};
   for (int q = 0; q < 19 && e == cudaSuccess; ++q) e = launch_convert_f64_f32(src[q], dst[q], cnt[q], st);
+  // output-column-major factors of the whole-CTA sweeps
+  if (e == cudaSuccess && f.cta) {
+    e = launch_transpose(f.MB, n - 1, nx, nx + nu, p->ldB, f.ldTB, f.MBt, 64, st);
+    if (e == cudaSuccess) e = launch_transpose(f.MF, n - 1, nx + nu, nx, p->ldF, f.ldTF, f.MFt, 64, st);
+    if (e == cudaSuccess) e = launch_transpose(f.KT, n_nl, nx, nu, p->ldK, f.ldTK, f.KTt, 64, st);
+  }
+  if (e == cudaSuccess && g.cta) {
+    e = launch_transpose(f.MB, n - 1, nx, nx + nu, p->ldB, g.ldTB, g.MBt, 32, st);
+    if (e == cudaSuccess) e = launch_transpose(f.MF, n - 1, nx + nu, nx, p->ldF, g.ldTF, g.MFt, 32, st);
+    if (e == cudaSuccess) e = launch_transpose(f.KT, n_nl, nx, nu, p->ldK, g.ldTK, g.KTt, 32, st);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { m.free_all(); delete p; return SPOCK_EDEVICE; }
   cudaMemset(p->d_x0raw, 0, nx * 8);

@@ -1,0 +1,533 @@
+// spock_cta.cuh -- the backward and forward sweeps of Alg. 2 over one segment
+// (a chain of single-child nodes whose bottom node has any number of
+// children), run by a whole CTA of 256 threads when nx + nu <= 128.
+//
+// Thread t owns output column t/2 and half t%2 of that column's rows. The
+// factors are stored output-column-major (MBt, MFt, KTt), so each thread
+// reads its rows with 16-byte shared loads, and the two halves are combined
+// by one shuffle. An "item" is one factor matrix (backward: MB of a child;
+// forward: [KT of the node (first child only) | MF of the child]); items
+// stream through a ring of nbuf shared buffers by cp.async.bulk, up to
+// nbuf - 1 items ahead of the one in use. Each item ends with one CTA barrier,
+// which both publishes the carry vector written in its epilogue and frees the
+// buffer of the previous item for the next copy.
+//
+// Per CTA, the segments it sweeps (the same in every evaluation of T) are
+// listed once per launch in shared memory with their node lists (Sched).
+#pragma once
+
+#include "spock_dev.cuh"
+
+// Optional cycle trace of CTA 0, thread 0 (compiled in only with
+// SPOCK_TRACE_ON, which also provides spock_trace(int point)).
+#ifdef SPOCK_TRACE_ON
+#define SPOCK_TRACE(k) spock_trace(k)
+#else
+#define SPOCK_TRACE(k) ((void)0)
+#endif
+// cycle probe of the sweeps into the launch's probe slots 8..11 (off unless
+// SPOCK_PROBE is defined: it costs CTA 0 a few instructions per item)
+#ifdef SPOCK_PROBE
+#define SPOCK_PROBE_ON true
+#else
+#define SPOCK_PROBE_ON false
+#endif
+
+namespace spock {
+
+// 16-byte shared loads and stores at 32-bit shared addresses
+template <class T>
+struct SV;
+template <>
+struct SV<float> {
+  static constexpr int W = 4;
+};
+template <>
+struct SV<double> {
+  static constexpr int W = 2;
+};
+__device__ __forceinline__ void ld16(unsigned a, float (&v)[4]) {
+  asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ld16(unsigned a, double (&v)[2]) {
+  asm volatile("ld.shared.v2.f64 {%0,%1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(a));
+}
+template <class T>
+__device__ __forceinline__ T ld_s(unsigned a);
+template <>
+__device__ __forceinline__ float ld_s<float>(unsigned a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+template <>
+__device__ __forceinline__ double ld_s<double>(unsigned a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+template <class T>
+__device__ __forceinline__ void st_s(unsigned a, T v);
+template <>
+__device__ __forceinline__ void st_s<float>(unsigned a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+template <>
+__device__ __forceinline__ void st_s<double>(unsigned a, double v) {
+  asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+// sum_k m[k] x[k] over ng 16-byte groups of rows at shared addresses m and x;
+// rows past the last real row of a group are zero in m (column padding) and
+// finite in x. Groups of eight are unrolled with a predicate, which lets the
+// loads of a group be issued ahead of the previous group's FMAs.
+template <class T>
+__device__ __forceinline__ T tdot(unsigned m, unsigned x, int ng) {
+  constexpr int W = SV<T>::W;
+  T a[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) a[w] = T(0);
+  for (int g0 = 0; g0 < ng; g0 += 8) {
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      if (g0 + g < ng) {
+        T mv[W], xv[W];
+        ld16(m + 16u * (unsigned)(g0 + g), mv);
+        ld16(x + 16u * (unsigned)(g0 + g), xv);
+#pragma unroll
+        for (int w = 0; w < W; ++w) a[w] = fma(mv[w], xv[w], a[w]);
+      }
+    }
+  }
+  if constexpr (W == 4)
+    return (a[0] + a[1]) + (a[2] + a[3]);
+  else
+    return a[0] + a[1];
+}
+
+// ---------------------------------------------------------------------------
+// The item ring: nbuf buffers, one mbarrier each (8 bytes apart). The state
+// persists across segments and evaluations; the sweeps copy it to registers.
+// ---------------------------------------------------------------------------
+struct Ring {
+  unsigned bar0;     // shared address of mbarrier 0
+  unsigned buf0;     // shared address of buffer 0
+  unsigned bstride;  // bytes per buffer
+  int nbuf;
+  unsigned par;      // bit b: parity of the next phase of buffer b's mbarrier
+  int head;          // buffer of the next item to be waited for
+  int ahead;         // items of the next segment already issued
+  int* diag;
+  __device__ __forceinline__ unsigned bar(int b) const { return bar0 + 8u * (unsigned)b; }
+  __device__ __forceinline__ unsigned buf(int b) const { return buf0 + bstride * (unsigned)b; }
+  __device__ __forceinline__ int step(int b, int k) const {   // (b + k) mod nbuf, 0 <= k < nbuf
+    b += k;
+    return b >= nbuf ? b - nbuf : b;
+  }
+};
+__device__ __forceinline__ void ring_arm(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void ring_copy(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// thread 0 waits (bounded) for the item in buffer b; every thread flips the
+// buffer's parity. The caller's CTA barrier hands the verdict (*s_ok) on.
+__device__ __forceinline__ void ring_wait0(Ring& R, int b, int* err, int site, int* s_ok) {
+  if (threadIdx.x == 0) {
+    uint64_t* bar = reinterpret_cast<uint64_t*>(__cvta_shared_to_generic(R.bar(b)));
+    if (!mbar_wait(bar, (R.par >> b) & 1u, err, R.diag, site)) *s_ok = 0;
+  }
+  R.par ^= 1u << b;
+}
+
+// ---------------------------------------------------------------------------
+// Per-CTA list of segments, level by level (same order in every evaluation)
+// ---------------------------------------------------------------------------
+constexpr int SCHED_CAP = 1536;   // ints of records
+constexpr int SCHED_LEV = 64;     // levels
+constexpr int SEG_HDR = 5;        // s, len, first child, one past last child, list offset
+struct Sched {
+  int ok;                    // every record of this CTA fits
+  int lvl[SCHED_LEV + 1];    // offset of the first record of level l
+  int rec[SCHED_CAP];        // per segment: header, then its nodes top to bottom
+};
+
+struct SegRef {
+  int s, len, c0, c1;
+  const int* nodes;          // shared (from Sched) or global (seg_nodes)
+};
+
+// build the schedule of this CTA (team index tg of nt); every thread calls it
+template <class T>
+__device__ void sched_build(const Prob<T>& P, Sched& S, int tg, int nt) {
+  const int L = P.n_levels;
+  if (threadIdx.x == 0) {
+    int off = 0;
+    bool ok = L <= SCHED_LEV;
+    for (int l = 0; l < L && ok; ++l) {
+      S.lvl[l] = off;
+      for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
+        const int4 inf = P.seg_info[s];
+        if (off + SEG_HDR + inf.y > SCHED_CAP) { ok = false; break; }
+        S.rec[off] = s; S.rec[off + 1] = inf.y; S.rec[off + 2] = inf.z; S.rec[off + 3] = inf.w;
+        S.rec[off + 4] = inf.x;
+        off += SEG_HDR + inf.y;
+      }
+    }
+    if (ok) S.lvl[L] = off;
+    S.ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  if (S.ok) {
+    for (int r = 0; r < S.lvl[L];) {
+      const int len = S.rec[r + 1], go = S.rec[r + 4];
+      for (int k = threadIdx.x; k < len; k += blockDim.x) S.rec[r + SEG_HDR + k] = P.seg_nodes[go + k];
+      r += SEG_HDR + len;
+    }
+  }
+  __syncthreads();
+}
+
+// number of this CTA's segments in level l
+template <class T>
+__device__ __forceinline__ int seg_count(const Prob<T>& P, int l, int tg, int nt) {
+  const int m = P.lvl_off[l + 1] - P.lvl_off[l] - tg;
+  return m > 0 ? (m + nt - 1) / nt : 0;
+}
+// the k-th segment of this CTA in level l
+template <class T>
+__device__ __forceinline__ SegRef seg_get(const Prob<T>& P, const Sched& S, int l, int k, int tg, int nt) {
+  SegRef r;
+  if (S.ok) {
+    int o = S.lvl[l];
+    for (int q = 0; q < k; ++q) o += SEG_HDR + S.rec[o + 1];
+    r.s = S.rec[o]; r.len = S.rec[o + 1]; r.c0 = S.rec[o + 2]; r.c1 = S.rec[o + 3];
+    r.nodes = S.rec + o + SEG_HDR;
+  } else {
+    r.s = P.lvl_off[l] + tg + k * nt;
+    const int4 inf = P.seg_info[r.s];
+    r.len = inf.y; r.c0 = inf.z; r.c1 = inf.w;
+    r.nodes = P.seg_nodes + inf.x;
+  }
+  return r;
+}
+
+// the shared areas of the whole-CTA sweeps (32-bit addresses)
+struct CtaMem {
+  unsigned carry0, carry1;   // carry vectors (ldc elements each)
+  unsigned qin;              // child inputs of a backward bottom (qslots x ldc)
+};
+
+// everything the whole-CTA sweeps keep between segments and evaluations
+struct CtaState {
+  Ring ring;
+  CtaMem mem;
+  const Sched* sched;
+  int* s_ok;
+};
+
+// dynamic shared memory of the whole-CTA sweeps: the ring, two carry vectors
+// and the child inputs
+template <class T>
+__host__ __device__ inline size_t cta_smem_bytes(const Prob<T>& P) {
+  if (!P.cta) return 0;
+  return (size_t)P.nbuf * P.item_bytes + (size_t)(2 + P.qslots) * P.ldc * sizeof(T);
+}
+
+// ---------------------------------------------------------------------------
+// item issue (by one thread)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ int b_child(const SegRef& g, int j) {
+  const int nb = g.c1 - g.c0;
+  return j < nb ? g.c0 + j : g.nodes[g.len - 1 - (j - nb)];
+}
+// what the issuing thread needs, read from the problem once per segment
+template <class T>
+struct BIssue {
+  const T* base;     // MBt
+  size_t stride;     // elements per child
+  unsigned bytes;
+  __device__ __forceinline__ explicit BIssue(const Prob<T>& P)
+      : base(P.MBt), stride((size_t)(P.nx + P.nu) * P.ldTB), bytes((unsigned)((P.nx + P.nu) * P.ldTB * (int)sizeof(T))) {}
+};
+template <class T>
+__device__ __forceinline__ void b_issue(const BIssue<T>& I, const Ring& R, const SegRef& g, int j, int b) {
+  const int c = b_child<T>(g, j);
+  ring_arm(R.bar(b), I.bytes);
+  ring_copy(R.buf(b), I.base + (size_t)(c - 1) * I.stride, I.bytes, R.bar(b));
+}
+// forward item j: (node, child, with KT)
+__device__ __forceinline__ void f_item(const SegRef& g, int j, int& node, int& child, bool& kt) {
+  if (j < g.len - 1) {
+    node = g.nodes[j]; child = g.nodes[j + 1]; kt = true;
+  } else {
+    node = g.nodes[g.len - 1]; child = g.c0 + (j - (g.len - 1)); kt = (j == g.len - 1);
+  }
+}
+template <class T>
+struct FIssue {
+  const T* kt;       // KTt
+  const T* mf;       // MFt
+  size_t ks, fs;     // elements per node / per child
+  unsigned kb, fb;   // bytes of the two parts
+  __device__ __forceinline__ explicit FIssue(const Prob<T>& P)
+      : kt(P.KTt), mf(P.MFt), ks((size_t)P.nu * P.ldTK), fs((size_t)P.nx * P.ldTF),
+        kb((unsigned)(P.nu * P.ldTK * (int)sizeof(T))), fb((unsigned)(P.nx * P.ldTF * (int)sizeof(T))) {}
+};
+template <class T>
+__device__ __forceinline__ void f_issue(const FIssue<T>& I, const Ring& R, const SegRef& g, int j, int b) {
+  int node, child;
+  bool kt;
+  f_item(g, j, node, child, kt);
+  ring_arm(R.bar(b), (kt ? I.kb : 0u) + I.fb);
+  if (kt) ring_copy(R.buf(b), I.kt + (size_t)node * I.ks, I.kb, R.bar(b));
+  ring_copy(R.buf(b) + I.kb, I.mf + (size_t)(child - 1) * I.fs, I.fb, R.bar(b));
+}
+// first items of the next segment (backward or forward), issued ahead of its call
+template <class T>
+__device__ __forceinline__ void ring_prefetch(const Prob<T>& P, Ring& R, const SegRef& g, bool fwd) {
+  const int nitems = (g.c1 - g.c0) + g.len - 1;
+  const int k = min(R.nbuf - 1, nitems);
+  if (threadIdx.x == blockDim.x - 1) {
+    if (fwd) {
+      const FIssue<T> I(P);
+      for (int j = 0; j < k; ++j) f_issue(I, R, g, j, R.step(R.head, j));
+    } else {
+      const BIssue<T> I(P);
+      for (int j = 0; j < k; ++j) b_issue(I, R, g, j, R.step(R.head, j));
+    }
+  }
+  R.ahead = k;
+}
+
+// ---------------------------------------------------------------------------
+// backward sweep of one segment:
+//   v_c = q_c + P_c c_c (q_c holds it, see phase P);  q^i = sum_c Abar_c' v_c + h^i;
+//   d^i = e^i - sum_c (B_c Rt_i^{-1})' v_c
+// items: the children of the bottom node, then one per step up the chain
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err, const SegRef& g,
+                        int* s_ok, unsigned long long* prof) {
+  constexpr int W = SV<T>::W;
+  constexpr unsigned ES = sizeof(T);
+  const int nx = P.nx, nu = P.nu, w = nx + nu;
+  const int t = threadIdx.x, col = t >> 1, half = t & 1;
+  const bool has_col = col < w;
+  const bool issuer = (t == (int)blockDim.x - 1);
+  const int r0 = half ? P.khB : 0;
+  const int r1 = half ? nx : min(P.khB, nx);
+  const int ng = (has_col && r1 > r0) ? (r1 - r0 + W - 1) / W : 0;
+  const unsigned mcol = (unsigned)(col * P.ldTB + r0) * ES;
+  const unsigned xoff = (unsigned)r0 * ES;
+  const unsigned ldcb = (unsigned)P.ldc * ES;
+  T* __restrict__ qbuf = P.qbuf;
+  T* __restrict__ dbuf = P.dbuf;
+  const T* __restrict__ hbuf = P.hbuf;
+  const T* __restrict__ ebuf = P.ebuf;
+  Ring R = ring;
+  const BIssue<T> I(P);
+  const int len = g.len, nb = g.c1 - g.c0, QS = P.qslots;
+  const int nitems = nb + len - 1;
+  const bool probe = SPOCK_PROBE_ON && prof && blockIdx.x == 0 && t == 0;
+  long long tc = probe ? clock64() : 0, c_mv = 0, c_hand = 0;
+  // the items not issued ahead, up to nbuf - 1 in flight
+  if (issuer)
+    for (int j = R.ahead; j < min(R.nbuf - 1, nitems); ++j) b_issue(I, R, g, j, R.step(R.head, j));
+  R.ahead = 0;
+  // h/e of the output node of the next two epilogues
+  auto pre_of = [&](int node) -> T {
+    if (!has_col || half) return T(0);
+    return (col < nx) ? ldc(hbuf + (long long)node * nx + col) : ldc(ebuf + (long long)node * nu + (col - nx));
+  };
+  T preA = pre_of(g.nodes[len - 1]);
+  T preB = (len >= 2) ? pre_of(g.nodes[len - 2]) : T(0);
+  // inputs of the bottom's first children
+  auto load_children = [&](int j0) {
+    const int m = min(QS, nb - j0);
+    for (int e = t; e < m * nx; e += blockDim.x) {
+      const int j = e / nx, k = e - j * nx;
+      st_s<T>(cm.qin + (unsigned)j * ldcb + (unsigned)k * ES, ldc(qbuf + (long long)(g.c0 + j0 + j) * nx + k));
+    }
+  };
+  load_children(0);
+  if (t == 0) *s_ok = 1;
+  int b = R.head;
+  ring_wait0(R, b, err, 3, s_ok);
+  __syncthreads();
+  bool ok = *s_ok != 0;
+  unsigned cin = cm.carry0, cout = cm.carry1;
+  T acc = T(0);
+  for (int j = 0; j < nitems && ok; ++j) {
+    SPOCK_TRACE(0);
+    // next copy into the buffer of item j - 1 (freed by the barrier that ended it)
+    if (issuer && j + R.nbuf - 1 < nitems) b_issue(I, R, g, j + R.nbuf - 1, R.step(b, R.nbuf - 1));
+    if (j < nb && j > 0 && j % QS == 0) {   // next chunk of the bottom's children
+      load_children(j);
+      __syncthreads();
+    }
+    const unsigned xin = (j < nb) ? cm.qin + (unsigned)(j % QS) * ldcb : cin;
+    if (probe) { const long long c = clock64(); c_hand += c - tc; tc = c; }
+    SPOCK_TRACE(1);
+    T v = (ng > 0) ? tdot<T>(R.buf(b) + mcol, xin + xoff, ng) : T(0);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    acc += v;
+    SPOCK_TRACE(2);
+    if (j >= nb - 1) {   // epilogue of an output node
+      const int i = (j < nb) ? g.nodes[len - 1] : g.nodes[len - 2 - (j - nb)];
+      if (has_col && !half) {
+        if (col < nx) {
+          const T qq = acc + preA;
+          st_s<T>(cout + (unsigned)col * ES, qq);
+          stc(qbuf + (long long)i * nx + col, qq);
+        } else {
+          stc(dbuf + (long long)i * nu + (col - nx), preA - acc);
+        }
+      }
+      acc = T(0);
+      preA = preB;
+      const int jn = j + 2;   // output node two epilogues ahead
+      preB = (jn >= nb && jn < nitems) ? pre_of(g.nodes[len - 2 - (jn - nb)]) : T(0);
+      const unsigned tt = cin; cin = cout; cout = tt;
+    }
+    if (probe) { const long long c = clock64(); c_mv += c - tc; tc = c; }
+    SPOCK_TRACE(3);
+    b = R.step(b, 1);
+    if (j + 1 < nitems) ring_wait0(R, b, err, 3, s_ok);
+    SPOCK_TRACE(4);
+    __syncthreads();
+    SPOCK_TRACE(5);
+    ok = *s_ok != 0;
+  }
+  if (probe) {
+    const long long c = clock64();
+    c_hand += c - tc;
+    prof[8] += (unsigned long long)c_hand;
+    prof[9] += (unsigned long long)c_mv;
+  }
+  R.head = b;
+  ring = R;
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// forward rollout of one segment:  u^i = K_i x^i + d^i;  x^c = Abar_c x^i + B_c d^i + c_c
+// items: one per step down the chain (with KT_i), then the bottom's children
+// (KT of the bottom node with the first); the input of every item of node i is
+// [x^i ; d^i] in the carry vector
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err, const SegRef& g,
+                        T* __restrict__ vout, int* s_ok, unsigned long long* prof) {
+  constexpr int W = SV<T>::W;
+  constexpr unsigned ES = sizeof(T);
+  const int nx = P.nx, nu = P.nu, w = nx + nu;
+  const int t = threadIdx.x, col = t >> 1, half = t & 1;
+  const bool xcol = col < nx, ucol = (col >= nx) && (col < w);
+  const bool issuer = (t == (int)blockDim.x - 1);
+  // x columns: nx + nu rows of MFt; u columns: nx rows of KTt
+  const int nr = xcol ? w : nx;
+  const int kh = xcol ? P.khF : P.khB;
+  const int r0 = half ? kh : 0;
+  const int r1 = half ? nr : min(kh, nr);
+  const int ng = ((xcol || ucol) && r1 > r0) ? (r1 - r0 + W - 1) / W : 0;
+  const unsigned kbytes = (unsigned)(nu * P.ldTK) * ES;
+  const unsigned mcol = xcol ? kbytes + (unsigned)(col * P.ldTF + r0) * ES
+                             : (unsigned)((col - nx) * P.ldTK + r0) * ES;
+  const unsigned xoff = (unsigned)r0 * ES;
+  const T* __restrict__ dbuf = P.dbuf;
+  const T* __restrict__ cvec = P.cvec;
+  const long long o_x = P.o_x, o_u = P.o_u;
+  Ring R = ring;
+  const FIssue<T> I(P);
+  const int len = g.len, nb = g.c1 - g.c0;
+  const int nitems = len - 1 + nb;
+  const bool probe = SPOCK_PROBE_ON && prof && blockIdx.x == 0 && t == 0;
+  long long tc = probe ? clock64() : 0, c_mv = 0, c_hand = 0;
+  if (issuer)
+    for (int j = R.ahead; j < min(R.nbuf - 1, nitems); ++j) f_issue(I, R, g, j, R.step(R.head, j));
+  R.ahead = 0;
+  // c_c of item j's child (x columns), d of the next node (chain items), two items ahead
+  auto child_of = [&](int j) { return j < len - 1 ? g.nodes[j + 1] : g.c0 + (j - (len - 1)); };
+  auto cp_of = [&](int j) -> T {
+    return (j < nitems && xcol && !half) ? ldr(cvec + (long long)(child_of(j) - 1) * nx + col) : T(0);
+  };
+  auto dn_of = [&](int j) -> T {   // d of the child of chain item j, element t
+    return (j < len - 1 && t < nu) ? ldc(dbuf + (long long)g.nodes[j + 1] * nu + t) : T(0);
+  };
+  T cpA = cp_of(0), cpB = cp_of(1);
+  T dA = dn_of(0), dB = dn_of(1);
+  // input of the top node: [x^i ; d^i]
+  unsigned cin = cm.carry0, cout = cm.carry1;
+  {
+    const int i = g.nodes[0];
+    for (int k = t; k < w; k += blockDim.x) {
+      T v;
+      if (k < nx) {
+        if (i == 0) {
+          v = P.x0s[k];
+          stc(vout + o_x + k, v);
+        } else {
+          v = ldc(vout + o_x + (long long)i * nx + k);
+        }
+      } else {
+        v = ldc(dbuf + (long long)i * nu + (k - nx));
+      }
+      st_s<T>(cin + (unsigned)k * ES, v);
+    }
+  }
+  if (t == 0) *s_ok = 1;
+  int b = R.head;
+  ring_wait0(R, b, err, 4, s_ok);
+  __syncthreads();
+  bool ok = *s_ok != 0;
+  for (int j = 0; j < nitems && ok; ++j) {
+    if (issuer && j + R.nbuf - 1 < nitems) f_issue(I, R, g, j + R.nbuf - 1, R.step(b, R.nbuf - 1));
+    const bool chain = j < len - 1;
+    const bool kt = j <= len - 1;   // first item of its node
+    const int i = chain ? g.nodes[j] : g.nodes[len - 1];
+    const int c = child_of(j);
+    if (probe) { const long long cc = clock64(); c_hand += cc - tc; tc = cc; }
+    T v = T(0);
+    if (ng > 0 && (xcol || kt)) v = tdot<T>(R.buf(b) + mcol, cin + xoff, ng);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if (!half) {
+      if (xcol) {
+        const T xc = v + cpA;
+        stc(vout + o_x + (long long)c * nx + col, xc);
+        if (chain) st_s<T>(cout + (unsigned)col * ES, xc);
+      } else if (ucol && kt) {
+        stc(vout + o_u + (long long)i * nu + (col - nx), v + ld_s<T>(cin + (unsigned)col * ES));
+      }
+    }
+    if (chain && t < nu) st_s<T>(cout + (unsigned)(nx + t) * ES, dA);
+    cpA = cpB;
+    cpB = cp_of(j + 2);
+    dA = dB;
+    dB = dn_of(j + 2);
+    if (chain) { const unsigned tt = cin; cin = cout; cout = tt; }
+    if (probe) { const long long cc = clock64(); c_mv += cc - tc; tc = cc; }
+    b = R.step(b, 1);
+    if (j + 1 < nitems) ring_wait0(R, b, err, 4, s_ok);
+    __syncthreads();
+    ok = *s_ok != 0;
+  }
+  if (probe) {
+    const long long cc = clock64();
+    c_hand += cc - tc;
+    prof[10] += (unsigned long long)c_hand;
+    prof[11] += (unsigned long long)c_mv;
+  }
+  R.head = b;
+  ring = R;
+  return ok;
+}
+
+}  // namespace spock

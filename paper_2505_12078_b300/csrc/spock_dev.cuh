@@ -53,6 +53,18 @@ struct Prob {
                  // the backward recursion added to h^i and subtracted from e^i
   int pipe_bytes;  // largest per-node matrix in bytes when it is streamed through
                    // shared memory (0: matrices read from global memory)
+  // whole-CTA sweeps (cta = 1, nx + nu <= 128): the factors stored
+  // output-column-major, the coefficients of one output column contiguous
+  int cta;
+  int ldTB, ldTF, ldTK;  // padded length of one column of MBt (nx), MFt (nx+nu), KTt (nx)
+  int khB, khF;          // first row of the second thread of a column (nx rows / nx+nu rows)
+  int nbuf;              // depth of the ring of item buffers (2..4)
+  int item_bytes;        // bytes of one ring buffer (multiple of 128)
+  int qslots;            // child inputs of a backward bottom held at once
+  int ldc;               // elements of one carry or child-input vector
+  const T* MBt;  // per non-root c: (nx+nu) columns x ldTB  (MB transposed)
+  const T* MFt;  // per non-root c: nx columns x ldTF       (MF transposed)
+  const T* KTt;  // per non-leaf i: nu columns x ldTK       (KT transposed)
   // cost and constraint data (scaled, Sec. 5.4)
   const T* qh;   // per non-root: diag of Q^{1/2} S^{-1} (nx)
   const T* rh;   // per non-root: diag of R^{1/2} Su^{-1} (nu)

@@ -32,6 +32,10 @@ cudaError_t launch_alg1(const SetupArgs& a, const int* stage_off_host, int N, cu
 cudaError_t launch_build(const SetupArgs& a, cudaStream_t s);
 cudaError_t launch_norm_L(const SetupArgs& a, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_convert_f64_f32(const double* a, float* b, long long n, cudaStream_t s);
+// nmat matrices rows x cols (leading dim lds) -> output-column-major, each
+// column padded to ldd rows with zeros; dst is double (prec 64) or float (32)
+cudaError_t launch_transpose(const double* src, long long nmat, int rows, int cols, int lds, int ldd,
+                             void* dst, int prec, cudaStream_t s);
 cudaError_t launch_convert_f32_f64(const float* a, double* b, long long n, cudaStream_t s);
 
 template <class T>
@@ -84,7 +88,7 @@ struct SolveBufs {
 template <class T>
 cudaError_t launch_solve(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
                          int grid, int threads, cudaStream_t s);
-int solver_max_grid(int precision, int tw, int threads, int D, int pipe_bytes, int* grid_out);
+int solver_max_grid(int precision, int tw, int threads, int D, int pipe_bytes, size_t extra, int* grid_out);
 size_t solver_smem_bytes(int precision, int tw, int threads, int D, int pipe_bytes);
 int solver_chunks(int precision, int width);
 

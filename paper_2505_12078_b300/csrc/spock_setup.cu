@@ -588,6 +588,31 @@ cudaError_t launch_norm_L(const SetupArgs& a, unsigned long long* out, cudaStrea
   return cudaGetLastError();
 }
 
+// dst[m][j * ldd + k] = src[m][k * lds + j] for k < rows, zero for rows <= k < ldd
+template <class Dst>
+__global__ void k_transpose(long long nmat, int rows, int cols, int lds, int ldd, const double* __restrict__ src,
+                            Dst* __restrict__ dst) {
+  const long long per = (long long)cols * ldd;
+  const long long tot = nmat * per;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long m = e / per;
+    const int j = (int)((e % per) / ldd), k = (int)(e % ldd);
+    dst[e] = (k < rows) ? (Dst)src[m * rows * lds + (long long)k * lds + j] : (Dst)0;
+  }
+}
+
+cudaError_t launch_transpose(const double* src, long long nmat, int rows, int cols, int lds, int ldd,
+                             void* dst, int prec, cudaStream_t s) {
+  const long long tot = nmat * cols * ldd;
+  if (tot <= 0) return cudaSuccess;
+  if (prec == 64)
+    k_transpose<double><<<grid_for(tot, 256), 256, 0, s>>>(nmat, rows, cols, lds, ldd, src, (double*)dst);
+  else
+    k_transpose<float><<<grid_for(tot, 256), 256, 0, s>>>(nmat, rows, cols, lds, ldd, src, (float*)dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert_f64_f32(const double* a, float* b, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_convert<double, float><<<grid_for(n, 256), 256, 0, s>>>(n, a, b);

@@ -10,7 +10,7 @@ namespace spock {
 #define SPOCK_DECL(T, SUF)                                                                   \
   cudaError_t launch_solve_##SUF(const Prob<T>&, const SolveBufs<T>&, const SolveOpts&, int, \
                                  int, int, cudaStream_t);                                    \
-  int max_grid_##SUF(int, int, int, int*);                                                  \
+  int max_grid_##SUF(int, int, int, size_t, int*);                                                  \
   size_t smem_bytes_##SUF(int, int, int);
 SPOCK_DECL(float, f1)
 SPOCK_DECL(float, f2)
@@ -37,14 +37,14 @@ cudaError_t launch_solve<double>(const Prob<double>& P, const SolveBufs<double>&
   return launch_solve_d4(P, B, o, tw, grid, threads, s);
 }
 
-int solver_max_grid(int precision, int tw, int threads, int D, int pipe_bytes, int* grid_out) {
+int solver_max_grid(int precision, int tw, int threads, int D, int pipe_bytes, size_t extra, int* grid_out) {
   const int ch = solver_chunks(precision, D);
   if (precision == 64) {
-    return ch == 2 ? max_grid_d2(tw, threads, pipe_bytes, grid_out)
-                   : max_grid_d4(tw, threads, pipe_bytes, grid_out);
+    return ch == 2 ? max_grid_d2(tw, threads, pipe_bytes, extra, grid_out)
+                   : max_grid_d4(tw, threads, pipe_bytes, extra, grid_out);
   }
-  return ch == 1 ? max_grid_f1(tw, threads, pipe_bytes, grid_out)
-                 : max_grid_f2(tw, threads, pipe_bytes, grid_out);
+  return ch == 1 ? max_grid_f1(tw, threads, pipe_bytes, extra, grid_out)
+                 : max_grid_f2(tw, threads, pipe_bytes, extra, grid_out);
 }
 
 size_t solver_smem_bytes(int precision, int tw, int threads, int D, int pipe_bytes) {

@@ -15,8 +15,8 @@ cudaError_t SPOCK_CAT(launch_solve_, SPOCK_SUFFIX)(const Prob<SPOCK_T>& P,
   return launch_ch<SPOCK_T, SPOCK_CH>(P, B, o, tw, grid, threads, s);
 }
 
-int SPOCK_CAT(max_grid_, SPOCK_SUFFIX)(int tw, int threads, int pipe_bytes, int* out) {
-  return max_grid_ch<SPOCK_T, SPOCK_CH>(tw, threads, pipe_bytes, out);
+int SPOCK_CAT(max_grid_, SPOCK_SUFFIX)(int tw, int threads, int pipe_bytes, size_t extra, int* out) {
+  return max_grid_ch<SPOCK_T, SPOCK_CH>(tw, threads, pipe_bytes, extra, out);
 }
 
 size_t SPOCK_CAT(smem_bytes_, SPOCK_SUFFIX)(int tw, int threads, int pipe_bytes) {

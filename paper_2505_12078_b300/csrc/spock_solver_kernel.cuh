@@ -33,6 +33,7 @@
 #pragma once
 #include "spock_dev.cuh"
 #include "spock_internal.h"
+#include "spock_cta.cuh"
 
 namespace spock {
 
@@ -540,196 +541,6 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_b
   return ok;
 }
 
-// ---------------------------------------------------------------------------
-// Whole-CTA sweeps (the team is the CTA, 256 threads): two threads per output
-// column, each over half of the rows with four independent accumulators,
-// combined by one shuffle; one CTA barrier after the matrix has landed and one
-// after the carry is written. Used when 2 * (nx + nu) <= 256.
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ T pair_dot(const T* __restrict__ M, int ld, int col, int r0, int r1,
-                                      const T* __restrict__ in) {
-  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  int k = r0;
-  for (; k + 4 <= r1; k += 4) {
-    a0 = fma(M[(size_t)k * ld + col], in[k], a0);
-    a1 = fma(M[(size_t)(k + 1) * ld + col], in[k + 1], a1);
-    a2 = fma(M[(size_t)(k + 2) * ld + col], in[k + 2], a2);
-    a3 = fma(M[(size_t)(k + 3) * ld + col], in[k + 3], a3);
-  }
-  for (; k < r1; ++k) a0 = fma(M[(size_t)k * ld + col], in[k], a0);
-  return (a0 + a1) + (a2 + a3);
-}
-
-// mbarrier wait by one thread, then a CTA barrier
-template <class T>
-__device__ __forceinline__ bool cta_wait(Pipe<T>& pp, int b, int* err, int site) {
-  if (threadIdx.x == 0) *pp.okp = mbar_wait(pp.bar + b, pp.par[b], err, pp.diag, site) ? 1 : 0;
-  pp.par[b] ^= 1u;
-  __syncthreads();
-  return *pp.okp != 0;
-}
-
-template <class T>
-__device__ bool backward_segment_cta(const Prob<T>& P, const Team& tm, T* s_a, T* s_b, Pipe<T>& pp,
-                                     int* err, int s, bool prefetched) {
-  const int nx = P.nx, nu = P.nu, w = nx + nu, ldB = P.ldB;
-  const int t = threadIdx.x, col = t >> 1, half = t & 1;
-  const int kh = (nx + 1) >> 1;
-  const int r0 = half ? kh : 0, r1 = half ? nx : kh;
-  const bool has_col = col < w;
-  const size_t mstride = (size_t)nx * ldB;
-  const T* __restrict__ MB = P.MB;
-  T* __restrict__ qbuf = P.qbuf;
-  T* __restrict__ dbuf = P.dbuf;
-  const T* __restrict__ hbuf = P.hbuf;
-  const T* __restrict__ ebuf = P.ebuf;
-  Team issuer = tm;
-  issuer.tid = (t == blockDim.x - 1) ? 0 : 1;   // the last thread issues the copies
-  bool ok = true;
-  if (pp.on && !prefetched) issue_first_B<T, 1>(P, issuer, pp, s);
-  SegList sl;
-  sl.load(P, s, t & 31);
-  const int len = sl.len;
-  auto pre_of = [&](int node) -> T {
-    if (!has_col || half) return T(0);
-    return (col < nx) ? ldc(hbuf + (long long)node * nx + col) : ldc(ebuf + (long long)node * nu + (col - nx));
-  };
-  int i = sl.node(P, len - 1);
-  T pre = pre_of(i);
-  T* cin = s_a;
-  T* cout = s_b;
-  for (int step = 0; step < len; ++step) {
-    const bool bottom = (step == 0);
-    const int c0 = bottom ? sl.c0b : sl.node(P, len - step);
-    const int c1 = bottom ? sl.c1b : c0 + 1;
-    const int inext = (step + 1 < len) ? sl.node(P, len - 2 - step) : -1;
-    const T pren = (inext >= 0) ? pre_of(inext) : T(0);
-    T acc = 0;
-    for (int c = c0; c < c1; ++c) {
-      if (bottom)
-        for (int k = t; k < nx; k += blockDim.x) cin[k] = ldc(qbuf + (long long)c * nx + k);
-      if (pp.on) {
-        if (!cta_wait(pp, pp.cur, err, 3)) return false;
-      } else {
-        __syncthreads();
-      }
-      const int cn = (c + 1 < c1) ? c + 1 : ((inext >= 0) ? i : -1);
-      if (pp.on && cn > 0) issue_B(P, issuer, pp, pp.cur ^ 1, cn);
-      const T* Mb = pp.on ? pp.buf[pp.cur] : MB + (size_t)(c - 1) * mstride;
-      T v = has_col ? pair_dot(Mb, ldB, col, r0, r1, cin) : T(0);
-      v += __shfl_xor_sync(0xffffffffu, v, 1);
-      acc += v;
-      if (pp.on) pp.cur ^= 1;
-      if (bottom && c + 1 < c1) __syncthreads();
-    }
-    if (has_col && !half) {
-      if (col < nx) {
-        const T qq = acc + pre;
-        cout[col] = qq;
-        stc(qbuf + (long long)i * nx + col, qq);
-      } else {
-        stc(dbuf + (long long)i * nu + (col - nx), pre - acc);
-      }
-    }
-    __syncthreads();
-    T* tt = cin; cin = cout; cout = tt;
-    pre = pren;
-    i = inext;
-  }
-  return ok;
-}
-
-template <class T>
-__device__ bool forward_segment_cta(const Prob<T>& P, const Team& tm, T* s_a, T* s_b, Pipe<T>& pp,
-                                    int* err, int s, T* __restrict__ vout, bool prefetched) {
-  const int nx = P.nx, nu = P.nu, w = nx + nu, ldF = P.ldF, ldK = P.ldK;
-  const int t = threadIdx.x, col = t >> 1, half = t & 1;
-  const bool xcol = col < nx, ucol = (col >= nx) && (col < w);
-  // x columns run over nx + nu rows of MF, u columns over nx rows of KT
-  const int nr = xcol ? w : nx;
-  const int kh = (nr + 1) >> 1;
-  const int r0 = half ? kh : 0, r1 = half ? nr : kh;
-  const size_t ks = (size_t)nx * ldK, fs = (size_t)w * ldF;
-  const T* __restrict__ dbuf = P.dbuf;
-  const T* __restrict__ cvec = P.cvec;
-  const long long o_x = P.o_x, o_u = P.o_u;
-  Team issuer = tm;
-  issuer.tid = (t == blockDim.x - 1) ? 0 : 1;
-  bool ok = true;
-  if (pp.on && !prefetched) issue_first_F<T, 1>(P, issuer, pp, s);
-  SegList sl;
-  sl.load(P, s, t & 31);
-  const int len = sl.len;
-  auto first_child = [&](int k) { return (k + 1 < len) ? sl.node(P, k + 1) : sl.c0b; };
-  int i = sl.node(P, 0);
-  T* cin = s_a;
-  T* cout = s_b;
-  for (int k = t; k < w; k += blockDim.x) {
-    T v;
-    if (k < nx) {
-      if (i == 0) {
-        v = P.x0s[k];
-        stc(vout + o_x + k, v);
-      } else {
-        v = ldc(vout + o_x + (long long)i * nx + k);
-      }
-    } else {
-      v = ldc(dbuf + (long long)i * nu + (k - nx));
-    }
-    cin[k] = v;
-  }
-  // node indices come from warp shuffles: evaluate them in uniform control flow
-  const int fc0 = first_child(0);
-  T cp = (xcol && !half) ? ldr(cvec + (long long)(fc0 - 1) * nx + col) : T(0);
-  for (int step = 0; step < len; ++step) {
-    const bool chain = (step + 1 < len);
-    const int c0 = first_child(step);
-    const int c1 = chain ? c0 + 1 : sl.c1b;
-    const int cn = chain ? first_child(step + 1) : -1;
-    T dpn = 0, cpn = 0;
-    if (chain && !half) {
-      if (col < nu) dpn = ldc(dbuf + (long long)c0 * nu + col);
-      if (xcol) cpn = ldr(cvec + (long long)(cn - 1) * nx + col);
-    }
-    for (int c = c0; c < c1; ++c) {
-      if (pp.on) {
-        if (!cta_wait(pp, pp.cur, err, 4)) return false;
-        if (c + 1 < c1) issue_F(P, issuer, pp, pp.cur ^ 1, i, c + 1, false);
-        else if (chain) issue_F(P, issuer, pp, pp.cur ^ 1, c0, cn, true);
-      } else {
-        __syncthreads();
-      }
-      const T* KTb = pp.on ? pp.buf[pp.cur] : P.KT + (size_t)i * ks;
-      const T* MFb = pp.on ? KTb + ks : P.MF + (size_t)(c - 1) * fs;
-      if (c > c0 && xcol && !half) cp = ldr(cvec + (long long)(c - 1) * nx + col);
-      T v = 0;
-      if (xcol) v = pair_dot(MFb, ldF, col, r0, r1, cin);
-      else if (ucol && c == c0) v = pair_dot(KTb, ldK, col - nx, r0, r1, cin);
-      v += __shfl_xor_sync(0xffffffffu, v, 1);
-      if (!half) {
-        if (xcol) {
-          const T xc = v + cp;
-          stc(vout + o_x + (long long)c * nx + col, xc);
-          if (chain) cout[col] = xc;
-        } else if (ucol && c == c0) {
-          stc(vout + o_u + (long long)i * nu + (col - nx), v + cin[col]);
-        }
-      }
-      if (pp.on) pp.cur ^= 1;
-    }
-    if (chain) {
-      if (!half && col < nu) cout[nx + col] = dpn;
-      cp = cpn;
-      __syncthreads();
-      T* tt = cin; cin = cout; cout = tt;
-      i = c0;
-    }
-  }
-  __syncthreads();
-  return ok;
-}
-
 // z residual of the x (and u) of one node, accumulated by one warp (phase E)
 template <class T>
 __device__ __forceinline__ void z_resid(const T* __restrict__ vin, const T* __restrict__ vout,
@@ -998,8 +809,8 @@ struct Views {
 // Not inlined: the driver calls it from six places, and six inlined copies of
 // the whole evaluation overflow the instruction cache.
 template <class T, int CH>
-__device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, Pipe<T>& pp, int tg,
-                      int nt, const T* __restrict__ vin, T* __restrict__ vout,
+__device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views<T, CH>& sv, Pipe<T>& pp,
+                      CtaState& cs, int tg, int nt, const T* __restrict__ vin, T* __restrict__ vout,
                       const T* __restrict__ vref, double (&red)[NRED], double* partials,
                       SolveCtl* ctl, Grid& g) {
   constexpr int D = Acc<T, CH>::D;
@@ -1013,7 +824,10 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
   const int nw = gridDim.x * (blockDim.x >> 5);
   Team w1;
   w1.tw = 1; w1.id = wid; w1.warp = 0; w1.lane = lane; w1.tid = lane; w1.nth = 32;
-  if (pp.on && P.n_levels > 0) {
+  if (P.cta) {
+    if (P.n_levels > 0 && seg_count(P, 0, tg, nt) > 0)
+      ring_prefetch(P, cs.ring, seg_get(P, *cs.sched, 0, 0, tg, nt), false);
+  } else if (pp.on && P.n_levels > 0) {
     const int s0 = P.lvl_off[0] + tg;
     if (s0 < P.lvl_off[1]) issue_first_B<T, CH>(P, tm, pp, s0);
   }
@@ -1029,14 +843,36 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
   pc.mark(ctl, 0);
   // B
   const int L = P.n_levels;
-  const bool cta_team = (tm.nth == (int)blockDim.x) && (2 * (P.nx + P.nu) <= (int)blockDim.x);
-  {
+  if (P.cta) {
+    const Sched& S = *cs.sched;
+    for (int l = 0; l < L; ++l) {
+      const int m = seg_count(P, l, tg, nt);
+      for (int k = 0; k < m; ++k) {
+        const SegRef sr = seg_get(P, S, l, k, tg, nt);
+        if (!bwd_cta<T>(P, cs.mem, cs.ring, &g.ctl->error, sr, cs.s_ok, g.prof)) return false;
+        // first items of this CTA's next segment (this level, a later one, or the first forward one)
+        if (k + 1 < m) {
+          ring_prefetch(P, cs.ring, seg_get(P, S, l, k + 1, tg, nt), false);
+        } else {
+          int l2 = l + 1;
+          while (l2 < L && seg_count(P, l2, tg, nt) == 0) ++l2;
+          if (l2 < L) ring_prefetch(P, cs.ring, seg_get(P, S, l2, 0, tg, nt), false);
+          else if (seg_count(P, L - 1, tg, nt) > 0) ring_prefetch(P, cs.ring, seg_get(P, S, L - 1, 0, tg, nt), true);
+          else {
+            int l3 = L - 2;
+            while (l3 >= 0 && seg_count(P, l3, tg, nt) == 0) --l3;
+            if (l3 >= 0) ring_prefetch(P, cs.ring, seg_get(P, S, l3, 0, tg, nt), true);
+          }
+        }
+      }
+      if (!grid_sync(g)) return false;
+    }
+  } else {
     T* tb = sv.t_base(tm.id);
     for (int l = 0; l < L; ++l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        const bool okb = cta_team ? backward_segment_cta<T>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre)
-                                  : backward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre, g.prof);
+        const bool okb = backward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, pre, g.prof);
         if (!okb) return false;
         pre = false;
       }
@@ -1054,13 +890,29 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
   }
   pc.mark(ctl, 1);
   // F
-  {
+  if (P.cta) {
+    const Sched& S = *cs.sched;
+    for (int l = L - 1; l >= 0; --l) {
+      const int m = seg_count(P, l, tg, nt);
+      for (int k = 0; k < m; ++k) {
+        const SegRef sr = seg_get(P, S, l, k, tg, nt);
+        if (!fwd_cta<T>(P, cs.mem, cs.ring, &g.ctl->error, sr, vout, cs.s_ok, g.prof)) return false;
+        if (k + 1 < m) {
+          ring_prefetch(P, cs.ring, seg_get(P, S, l, k + 1, tg, nt), true);
+        } else {
+          int l2 = l - 1;
+          while (l2 >= 0 && seg_count(P, l2, tg, nt) == 0) --l2;
+          if (l2 >= 0) ring_prefetch(P, cs.ring, seg_get(P, S, l2, 0, tg, nt), true);
+        }
+      }
+      if (!grid_sync(g)) return false;
+    }
+  } else {
     T* tb = sv.t_base(tm.id);
     for (int l = L - 1; l >= 0; --l) {
       bool pre = pp.on;
       for (int s = P.lvl_off[l] + tg; s < P.lvl_off[l + 1]; s += nt) {
-        const bool okf = cta_team ? forward_segment_cta<T>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre)
-                                  : forward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
+        const bool okf = forward_segment<T, CH>(P, tm, tb, tb + D, pp, &g.ctl->error, s, vout, pre);
         if (!okf) return false;
         pre = false;
       }
@@ -1138,7 +990,8 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
   Views<T, CH> sv;
   sv.tw = tw;
   sv.pipe_elems = Views<T, CH>::pipe_elems_for(P.pipe_bytes);
-  sv.pipe_base = reinterpret_cast<T*>(smraw);
+  const size_t cta_bytes = cta_smem_bytes(P);
+  sv.pipe_base = reinterpret_cast<T*>(smraw + cta_bytes);
   sv.base = sv.pipe_base + (size_t)teams_per_cta * 2 * sv.pipe_elems;
   __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
   Pipe<T> pp;
@@ -1154,6 +1007,31 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
   if (threadIdx.x < 2 * MAXTW) mbar_init(s_bar + threadIdx.x, 1);
   fence_mbar_init();
   __syncthreads();
+  // whole-CTA sweeps: ring of item buffers, carry vectors, child inputs, schedule
+  CtaState cs;
+  __shared__ Sched s_sched;
+  __shared__ int s_cta_ok;
+  if (P.cta) {
+    const unsigned base = smem_u32(smraw);
+    cs.ring.bar0 = smem_u32(s_bar);
+    cs.ring.buf0 = base;
+    cs.ring.bstride = (unsigned)P.item_bytes;
+    cs.ring.nbuf = P.nbuf;
+    cs.ring.par = 0u;
+    cs.ring.head = 0;
+    cs.ring.ahead = 0;
+    cs.ring.diag = B.ctl->diag;
+    const unsigned ldcb = (unsigned)(P.ldc * sizeof(T));
+    cs.mem.carry0 = base + (unsigned)P.nbuf * (unsigned)P.item_bytes;
+    cs.mem.carry1 = cs.mem.carry0 + ldcb;
+    cs.mem.qin = cs.mem.carry1 + ldcb;
+    // padding rows of the vectors are read against zero coefficients: keep them finite
+    T* vz = reinterpret_cast<T*>(smraw + (size_t)P.nbuf * P.item_bytes);
+    for (int k = threadIdx.x; k < (2 + P.qslots) * P.ldc; k += blockDim.x) vz[k] = T(0);
+    sched_build(P, s_sched, tg, nt);
+    cs.sched = &s_sched;
+    cs.s_ok = &s_cta_ok;
+  }
   SolveCtl* ctl = B.ctl;
   Grid g;
   g.ctl = &ctl->bar;
@@ -1176,7 +1054,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
   double red[NRED];
   int status = 0, k = 0, nT = 0, nK0 = 0, nK1 = 0, nK2 = 0, nFB = 0, nBT = 0;
   double res, om2;
-  bool ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+  bool ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
   ++nT;
   if (!ok) goto fail;
   res = red[R_MAX];
@@ -1185,7 +1063,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
   if (o.method == 1) {
     while (!(res <= o.tol) && k < o.max_iters) {
       int t = iV; iV = iTV; iTV = t;
-      ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+      ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
       ++nT; ++k;
       if (!ok) goto fail;
       res = red[R_MAX];
@@ -1352,7 +1230,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
       }
       if (!grid_sync(g)) goto fail;
       pc.mark(ctl, 5);
-      ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
+      ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
       ++nT;
       if (!ok) goto fail;
       if (omega <= C0 * zeta) {                       // K0
@@ -1401,7 +1279,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
           if (!grid_sync(g)) goto fail;
           pk.mark(ctl, 6);
           int t = iV; iV = iVT; iVT = t;
-          ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+          ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
           ++nT;
           if (!ok) goto fail;
           res = red[R_MAX];
@@ -1412,7 +1290,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
         ++bt; ++nBT;
         if (bt >= o.max_backtracks) {                 // fall back to v <- T(v)
           int t = iV; iV = iTV; iTV = t;
-          ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
+          ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iV], buf[iTV], (const T*)nullptr, red, B.partials, ctl, g);
           ++nT;
           if (!ok) goto fail;
           res = red[R_MAX];
@@ -1436,7 +1314,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
         }
         if (!grid_sync(g)) goto fail;
         pk.mark(ctl, 6);
-        ok = evalT<T, CH>(P, tm, sv, pp, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
+        ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
         ++nT;
         if (!ok) goto fail;
       }
@@ -1467,7 +1345,7 @@ fail:
 template <class T, int CH>
 cudaError_t launch_ch(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
                              int grid, int threads, cudaStream_t s) {
-  const size_t smem = Views<T, CH>::bytes(threads, tw, P.pipe_bytes);
+  const size_t smem = Views<T, CH>::bytes(threads, tw, P.pipe_bytes) + cta_smem_bytes(P);
   cudaError_t e = cudaFuncSetAttribute(k_solve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -1480,11 +1358,11 @@ cudaError_t launch_ch(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& 
 }
 
 template <class T, int CH>
-int max_grid_ch(int tw, int threads, int pipe_bytes, int* out) {
+int max_grid_ch(int tw, int threads, int pipe_bytes, size_t extra, int* out) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = Views<T, CH>::bytes(threads, tw, pipe_bytes);
+  const size_t smem = Views<T, CH>::bytes(threads, tw, pipe_bytes) + extra;
   cudaFuncSetAttribute(k_solve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve<T, CH>, threads, smem) != cudaSuccess)
     return -1;
