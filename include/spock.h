@@ -208,6 +208,58 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
 int spock_get_iterate(spock_problem* p, int precision, void* v_out, void* stream);
 int spock_set_iterate(spock_problem* p, int precision, const void* v_in, void* stream);
 
+/* ---------------- batched solves (many independent problems, one launch) -----
+ * Many problems of different sizes (each created with spock_problem_create,
+ * nx + nu <= 126) are solved together: one persistent launch in which every
+ * CTA takes problems from a queue, largest first, and runs the whole iteration
+ * of its problem (Sec. 5: T, Alg. 3, Alg. 4) with its barriers and reductions
+ * inside the CTA. The device work of a solve (x0 upload, scaling, the launch,
+ * unscaling, result download) is captured once into a CUDA graph and replayed.
+ * The paper solves one problem per run; the batch is this library's addition. */
+typedef struct spock_batch spock_batch;
+
+typedef struct spock_batch_info {
+    int status;           /* SPOCK_OK, SPOCK_MAXITER or SPOCK_ETIMEOUT for this problem */
+    int iters;            /* outer iterations */
+    int n_T;              /* evaluations of T */
+    int tw;               /* warps per team of the problem's sweeps */
+    double res_inf;       /* ||v - T(v)||_inf at exit, iteration precision */
+    double risk;          /* s^0 of T(v) */
+    double device_ms;     /* time the problem's CTA spent on it (SM clock) */
+} spock_batch_info;
+
+/* Bundle `count` problems (not copied: they must outlive the batch and must not
+ * be solved on their own while the batch is in use, since the batch uses their
+ * solve buffers) for iteration in `precision` (32 or 64). The batch keeps each
+ * problem's iterate between solves (warm start). EUNSUPPORTED if some problem
+ * has nx + nu > 126. */
+int spock_batch_create(spock_problem* const* problems, int count, int precision, spock_batch** out);
+void spock_batch_destroy(spock_batch* b);
+
+/* Totals of the packed host arrays of spock_batch_solve: x0 [sum nx],
+ * x_out [sum n nx], u_out [sum n_nl nu] (problem after problem). */
+int spock_batch_sizes(const spock_batch* b, long long* x0_total, long long* x_total, long long* u_total);
+
+/* Warps per team of each problem's sweeps: tw[i] in {1, 2, 4, 8} with
+ * 64 tw[i] >= nx + nu; NULL restores the default. */
+int spock_batch_set_tw(spock_batch* b, const int* tw);
+
+/* Autotuner: times `iters` plain CP iterations of every problem for each
+ * admissible warps-per-team choice, with and without streaming the factors
+ * through shared memory, and keeps the fastest per problem. Leaves every
+ * iterate at zero. tw_out [count] (may be NULL) receives the choices. */
+int spock_batch_autotune(spock_batch* b, int iters, int* tw_out);
+
+/* Solve every problem. x0 (host) packed [sum nx], unscaled; opts as for
+ * spock_solve (precision must equal the batch's; fp64_check is ignored);
+ * warm_start = 1 starts each problem from its last iterate. x_out, u_out
+ * (host, packed, may be NULL), risk (host) [count] (may be NULL), info (host)
+ * [count] (may be NULL). total_ms (may be NULL) receives the device time of
+ * the whole replay (copies included). Blocking. Returns SPOCK_OK if every
+ * problem converged, SPOCK_MAXITER if some did not, or the first error. */
+int spock_batch_solve(spock_batch* b, const double* x0, const spock_solve_opts* opts, double* x_out,
+                      double* u_out, double* risk, spock_batch_info* info, double* total_ms);
+
 const char* spock_status_str(int status);
 int spock_version(void);
 

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libspock.so")
-HEADERS = ["spock_dev.cuh", "spock_internal.h", "spock_solver_kernel.cuh", "spock_cta.cuh"]
+HEADERS = ["spock_dev.cuh", "spock_internal.h", "spock_solver_kernel.cuh", "spock_cta.cuh", "spock_problem.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (object name, source, extra defines)
 UNITS = [
@@ -24,9 +24,10 @@ UNITS = [
     ("spock_setup", "spock_setup.cu", []),
     ("spock_solver", "spock_solver.cu", []),
     ("spock_noalloc", "spock_noalloc.cu", []),
-    ("solver_f1", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=1", "-DSPOCK_SUFFIX=f1"]),
+    ("spock_batch", "spock_batch.cu", []),
+    ("solver_f1", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=1", "-DSPOCK_SUFFIX=f1", "-DSPOCK_WITH_BATCH"]),
     ("solver_f2", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=f2"]),
-    ("solver_d2", "spock_solver_inst.cu", ["-DSPOCK_T=double", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=d2"]),
+    ("solver_d2", "spock_solver_inst.cu", ["-DSPOCK_T=double", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=d2", "-DSPOCK_WITH_BATCH"]),
     ("solver_d4", "spock_solver_inst.cu", ["-DSPOCK_T=double", "-DSPOCK_CH=4", "-DSPOCK_SUFFIX=d4"]),
 ]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *ARCH]

@@ -17,80 +17,11 @@
 #include "spock_dev.cuh"
 #include "spock_internal.h"
 #include "spock_cta.cuh"
+#include "spock_problem.h"
 
 using namespace spock;
 
-namespace {
 
-constexpr int kThreads = 256;
-
-inline int pad4(int x) { return (x + 3) & ~3; }
-
-struct DevMem {
-  std::vector<void*> ptrs;
-  bool failed = false;
-  template <class T>
-  T* alloc(long long count) {
-    if (count <= 0) count = 1;
-    void* p = nullptr;
-    if (cudaMalloc(&p, (size_t)count * sizeof(T)) != cudaSuccess) {
-      failed = true;
-      return nullptr;
-    }
-    ptrs.push_back(p);
-    return static_cast<T*>(p);
-  }
-  void free_all() {
-    for (void* p : ptrs) cudaFree(p);
-    ptrs.clear();
-  }
-};
-
-template <class T>
-struct Iter {   // per-precision iteration data
-  T *MB = nullptr, *MF = nullptr, *MP = nullptr, *KT = nullptr, *cvec = nullptr, *kc = nullptr;
-  T *qh = nullptr, *rh = nullptr, *qNh = nullptr, *gx = nullptr, *gu = nullptr, *gN = nullptr;
-  T *box_lo = nullptr, *box_hi = nullptr, *boxN_lo = nullptr, *boxN_hi = nullptr, *ball = nullptr;
-  T *prob = nullptr, *avar = nullptr, *x0s = nullptr;
-  T *qbuf = nullptr, *dbuf = nullptr, *hbuf = nullptr, *ebuf = nullptr;
-  // whole-CTA sweeps: output-column-major factors and their layout
-  T *MBt = nullptr, *MFt = nullptr, *KTt = nullptr;
-  int cta = 0, ldTB = 0, ldTF = 0, ldTK = 0, khB = 0, khF = 0, nbuf = 0, item_bytes = 0, qslots = 0,
-      ldc = 0;
-  SolveBufs<T> sb{};
-  bool have_bufs = false;
-  Prob<T> P{};
-};
-
-}  // namespace
-
-struct spock_problem {
-  int n = 0, n_nl = 0, n_l = 0, N = 0, nx = 0, nu = 0, n_c = 0, n_cN = 0;
-  int nbx = 0, nbu = 0, nbox = 0, has_ball = 0;
-  long long n_y = 0, nz = 0, neta = 0, nv = 0;
-  long long o_x, o_u, o_y, o_tau, o_s, e_y, e_s, e_c, e_q, e_cN, e_qN;
-  int ldB, ldF, ldP, ldK;
-  std::vector<int> anc, ch_off, yoff, stage_off, ynode, lvl_off, seg_top, seg_bot, seg_len, seg_off,
-      seg_nodes;
-  std::vector<double> Sx, Su, SxN;
-  double a_con = 1, a_conN = 1, alpha = 0, normL = 0;
-  int max_items = 1;
-  int maxch = 1;       // most children of a node
-  int tw = 8;
-  int use_pipe = 1;    // stream the sweep matrices through shared memory
-  DevMem mem;
-  // device tree / schedule
-  int *d_anc, *d_ch_off, *d_yoff, *d_ynode, *d_lvl_off, *d_seg_top, *d_seg_bot, *d_seg_len,
-      *d_seg_off, *d_seg_nodes;
-  int4* d_seg_info;
-  // FP64 offline data kept for inspection
-  double *d_P, *d_K, *d_Rt, *d_Abar, *d_Sx, *d_SxN, *d_Su;
-  double* d_x0raw;   // unscaled x0 of the operator-level calls
-  Iter<double> f64;
-  Iter<float> f32;
-  double* d_out_risk;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
 
 namespace {
 
@@ -313,30 +244,6 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
   return m.failed ? SPOCK_ENOMEM : SPOCK_OK;
 }
 
-template <class T>
-int ensure_bufs(spock_problem* p, Iter<T>& it) {
-  if (it.have_bufs) return SPOCK_OK;
-  DevMem& m = p->mem;
-  const long long nv = p->nv;
-  SolveBufs<T>& b = it.sb;
-  b.V = m.alloc<T>(nv); b.TV = m.alloc<T>(nv); b.VT = m.alloc<T>(nv); b.TVT = m.alloc<T>(nv);
-  b.PSI = m.alloc<T>(nv); b.VP = m.alloc<T>(nv); b.RP = m.alloc<T>(nv);
-  const long long nvp = (nv + 3) & ~3LL;   // 16-byte aligned slots
-  b.sstride = nvp;
-  b.S = m.alloc<T>(3 * nvp); b.Y = m.alloc<T>(3 * nvp);
-  int dev = 0, nsm = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  b.partials = m.alloc<double>((long long)2 * nsm * 8 * NRED);
-  b.flags = m.alloc<unsigned>((long long)nsm * 8);
-  b.ctl = m.alloc<SolveCtl>(1);
-  if (m.failed) return SPOCK_ENOMEM;
-  cudaMemset(b.V, 0, nv * sizeof(T));
-  cudaMemset(b.S, 0, 3 * nvp * sizeof(T));
-  cudaMemset(b.Y, 0, 3 * nvp * sizeof(T));
-  it.have_bufs = true;
-  return cuda_err(cudaGetLastError());
-}
 
 __global__ void k_scale_x0(int nx, const double* __restrict__ x0, const double* __restrict__ Sx,
                            double* __restrict__ o64, float* __restrict__ o32) {
@@ -517,6 +424,35 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
     for (int k = 0; k < 8; ++k) stats[k] = h.stats[k];
   return SPOCK_OK;
 }
+}  // namespace spock
+
+namespace spock {
+template <class T>
+int ensure_bufs(spock_problem* p, Iter<T>& it) {
+  if (it.have_bufs) return SPOCK_OK;
+  DevMem& m = p->mem;
+  const long long nv = p->nv;
+  SolveBufs<T>& b = it.sb;
+  b.V = m.alloc<T>(nv); b.TV = m.alloc<T>(nv); b.VT = m.alloc<T>(nv); b.TVT = m.alloc<T>(nv);
+  b.PSI = m.alloc<T>(nv); b.VP = m.alloc<T>(nv); b.RP = m.alloc<T>(nv);
+  const long long nvp = (nv + 3) & ~3LL;   // 16-byte aligned slots
+  b.sstride = nvp;
+  b.S = m.alloc<T>(3 * nvp); b.Y = m.alloc<T>(3 * nvp);
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  b.partials = m.alloc<double>((long long)2 * nsm * 8 * NRED);
+  b.flags = m.alloc<unsigned>((long long)nsm * 8);
+  b.ctl = m.alloc<SolveCtl>(1);
+  if (m.failed) return SPOCK_ENOMEM;
+  cudaMemset(b.V, 0, nv * sizeof(T));
+  cudaMemset(b.S, 0, 3 * nvp * sizeof(T));
+  cudaMemset(b.Y, 0, 3 * nvp * sizeof(T));
+  it.have_bufs = true;
+  return cuda_err(cudaGetLastError());
+}
+template int ensure_bufs<float>(spock_problem*, Iter<float>&);
+template int ensure_bufs<double>(spock_problem*, Iter<double>&);
 }  // namespace spock
 
 extern "C" {

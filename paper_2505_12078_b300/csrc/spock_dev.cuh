@@ -330,12 +330,17 @@ struct GridCtl {
   int pad;
 };
 
+// The group of CTAs that iterates on one problem: the whole grid (one problem
+// per launch), or one CTA (local = true: the batched launch, where every CTA
+// works on its own problem and the barriers and reductions stay in the CTA).
 struct Grid {
   GridCtl* ctl;       // error word
-  unsigned* flags;    // one arrival flag per CTA (zeroed before the launch)
-  double* partials;   // 2 x gridDim.x x NRED reduction partials (double-buffered)
+  unsigned* flags;    // one arrival flag per CTA of the group (zeroed before the launch)
+  double* partials;   // 2 x size x NRED reduction partials (double-buffered)
   unsigned epoch;     // barriers passed by this CTA (identical on every CTA)
   unsigned long long* prof;   // cycle counters of CTA 0 (slots 12..15), may be null
+  int rank, size;     // this CTA's index in the group and the group's size
+  bool local;
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -369,7 +374,7 @@ __device__ __forceinline__ bool poll_flags(Grid& g, unsigned e) {
   __shared__ int s_bad;
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
-  for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
+  for (int c = threadIdx.x; c < g.size; c += blockDim.x) {
     uint64_t t0 = 0;
     unsigned spins = 0;
     while (ld_acquire(g.flags + c) < e) {
@@ -392,11 +397,15 @@ __device__ __forceinline__ bool poll_flags(Grid& g, unsigned e) {
 }
 
 __device__ __forceinline__ bool grid_sync(Grid& g) {
+  if (g.local) {
+    __syncthreads();
+    return true;
+  }
   const bool probe = g.prof && blockIdx.x == 0 && threadIdx.x == 0;
   const long long t0 = probe ? clock64() : 0;
   const unsigned e = ++g.epoch;
   __syncthreads();
-  if (threadIdx.x == 0) st_release(g.flags + blockIdx.x, e);
+  if (threadIdx.x == 0) st_release(g.flags + g.rank, e);
   const bool ok = poll_flags(g, e);
   if (probe) {
     g.prof[12] += (unsigned long long)(clock64() - t0);
@@ -411,21 +420,33 @@ __device__ __forceinline__ bool grid_sync(Grid& g) {
 // memory of NRED * 32 doubles. Returns false on error.
 __device__ __forceinline__ bool grid_allreduce(Grid& g, double (&v)[NRED], double* scratch,
                                                int max_slot) {
+  if (g.local) {
+    block_reduce_red(v, scratch, max_slot);
+    __shared__ double s_loc[NRED];
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NRED; ++k) s_loc[k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) v[k] = s_loc[k];
+    __syncthreads();
+    return true;
+  }
   const bool probe = g.prof && blockIdx.x == 0 && threadIdx.x == 0;
   const long long t0 = probe ? clock64() : 0;
   block_reduce_red(v, scratch, max_slot);
   const unsigned e = ++g.epoch;
-  double* part = g.partials + (size_t)(e & 1u) * gridDim.x * NRED;
+  double* part = g.partials + (size_t)(e & 1u) * g.size * NRED;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NRED; ++k) __stcg(part + (size_t)blockIdx.x * NRED + k, v[k]);
-    st_release(g.flags + blockIdx.x, e);
+    for (int k = 0; k < NRED; ++k) __stcg(part + (size_t)g.rank * NRED + k, v[k]);
+    st_release(g.flags + g.rank, e);
   }
   const bool ok = poll_flags(g, e);
   double x[NRED];
 #pragma unroll
   for (int k = 0; k < NRED; ++k) x[k] = 0.0;
-  for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
+  for (int c = threadIdx.x; c < g.size; c += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < NRED; ++k) {
       const double y = __ldcg(part + (size_t)c * NRED + k);
@@ -456,6 +477,9 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

@@ -85,6 +85,22 @@ struct SolveBufs {
   SolveCtl* ctl;
 };
 
+// Schedule of the batched launch: gangs of CTAs for large problems, single
+// CTAs for the rest (see k_batch).
+struct BatchPlan {
+  int n_gang_ctas;          // CTAs 0 .. n_gang_ctas-1 belong to gangs
+  const int* gang_of;       // [n_gang_ctas] gang of the CTA
+  const int* gang_start;    // [gangs] first CTA of the gang
+  const int* gang_size;     // [gangs]
+  const int* list_off;      // [gangs + 1] into list
+  const int* list;          // problems of every gang, in order
+  unsigned* flags;          // barrier flags: CTA c uses flags[c] (zeroed before the launch)
+  double* partials;         // 2 x n_gang_ctas x NRED per gang, at 2 NRED gang_start
+  const int* small_order;   // problems solved by single CTAs, largest first
+  int n_small;
+  int* next;                // queue position of small_order (zeroed before the launch)
+};
+
 template <class T>
 cudaError_t launch_solve(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
                          int grid, int threads, cudaStream_t s);

@@ -1,0 +1,87 @@
+// spock_problem.h -- host-side state of a problem (internal to libspock).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "spock_dev.cuh"
+#include "spock_internal.h"
+
+namespace spock {
+
+constexpr int kThreads = 256;
+
+inline int pad4(int x) { return (x + 3) & ~3; }
+
+struct DevMem {
+  std::vector<void*> ptrs;
+  bool failed = false;
+  template <class T>
+  T* alloc(long long count) {
+    if (count <= 0) count = 1;
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)count * sizeof(T)) != cudaSuccess) {
+      failed = true;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void free_all() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+template <class T>
+struct Iter {   // per-precision iteration data
+  T *MB = nullptr, *MF = nullptr, *MP = nullptr, *KT = nullptr, *cvec = nullptr, *kc = nullptr;
+  T *qh = nullptr, *rh = nullptr, *qNh = nullptr, *gx = nullptr, *gu = nullptr, *gN = nullptr;
+  T *box_lo = nullptr, *box_hi = nullptr, *boxN_lo = nullptr, *boxN_hi = nullptr, *ball = nullptr;
+  T *prob = nullptr, *avar = nullptr, *x0s = nullptr;
+  T *qbuf = nullptr, *dbuf = nullptr, *hbuf = nullptr, *ebuf = nullptr;
+  // whole-CTA sweeps: output-column-major factors and their layout
+  T *MBt = nullptr, *MFt = nullptr, *KTt = nullptr;
+  int cta = 0, ldTB = 0, ldTF = 0, ldTK = 0, khB = 0, khF = 0, nbuf = 0, item_bytes = 0, qslots = 0,
+      ldc = 0;
+  SolveBufs<T> sb{};
+  bool have_bufs = false;
+  Prob<T> P{};
+};
+
+
+}  // namespace spock
+
+struct spock_problem {
+  int n = 0, n_nl = 0, n_l = 0, N = 0, nx = 0, nu = 0, n_c = 0, n_cN = 0;
+  int nbx = 0, nbu = 0, nbox = 0, has_ball = 0;
+  long long n_y = 0, nz = 0, neta = 0, nv = 0;
+  long long o_x, o_u, o_y, o_tau, o_s, e_y, e_s, e_c, e_q, e_cN, e_qN;
+  int ldB, ldF, ldP, ldK;
+  std::vector<int> anc, ch_off, yoff, stage_off, ynode, lvl_off, seg_top, seg_bot, seg_len, seg_off,
+      seg_nodes;
+  std::vector<double> Sx, Su, SxN;
+  double a_con = 1, a_conN = 1, alpha = 0, normL = 0;
+  int max_items = 1;
+  int maxch = 1;       // most children of a node
+  int tw = 8;
+  int use_pipe = 1;    // stream the sweep matrices through shared memory
+  spock::DevMem mem;
+  // device tree / schedule
+  int *d_anc, *d_ch_off, *d_yoff, *d_ynode, *d_lvl_off, *d_seg_top, *d_seg_bot, *d_seg_len,
+      *d_seg_off, *d_seg_nodes;
+  int4* d_seg_info;
+  // FP64 offline data kept for inspection
+  double *d_P, *d_K, *d_Rt, *d_Abar, *d_Sx, *d_SxN, *d_Su;
+  double* d_x0raw;   // unscaled x0 of the operator-level calls
+  spock::Iter<double> f64;
+  spock::Iter<float> f32;
+  double* d_out_risk;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace spock {
+// solve buffers of one precision, allocated on first use
+template <class T>
+int ensure_bufs(spock_problem* p, Iter<T>& it);
+}  // namespace spock

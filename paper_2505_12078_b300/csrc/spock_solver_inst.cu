@@ -23,4 +23,18 @@ size_t SPOCK_CAT(smem_bytes_, SPOCK_SUFFIX)(int tw, int threads, int pipe_bytes)
   return Views<SPOCK_T, SPOCK_CH>::bytes(threads, tw, pipe_bytes);
 }
 
+#ifdef SPOCK_WITH_BATCH
+cudaError_t SPOCK_CAT(launch_batch_, SPOCK_SUFFIX)(const Prob<SPOCK_T>* probs, const SolveBufs<SPOCK_T>* bufs,
+                                                    const int* tws, const SolveOpts& o, const BatchPlan& plan,
+                                                    long long* cycles, size_t smem, int grid, cudaStream_t s) {
+  return launch_batch_ch<SPOCK_T, SPOCK_CH>(probs, bufs, tws, o, plan, cycles, smem, grid, s);
+}
+int SPOCK_CAT(batch_grid_, SPOCK_SUFFIX)(size_t smem, int* out) {
+  return batch_grid_ch<SPOCK_T, SPOCK_CH>(smem, out);
+}
+size_t SPOCK_CAT(views_bytes_, SPOCK_SUFFIX)(int tw, int pipe_bytes) {
+  return Views<SPOCK_T, SPOCK_CH>::bytes(256, tw, pipe_bytes);
+}
+#endif
+
 }  // namespace spock

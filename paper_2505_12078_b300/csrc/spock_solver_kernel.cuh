@@ -820,8 +820,8 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
   PhaseClock pc;
   pc.start(g.prof);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
-  const int nw = gridDim.x * (blockDim.x >> 5);
+  const int gw = g.rank * (blockDim.x >> 5) + wid;
+  const int nw = g.size * (blockDim.x >> 5);
   Team w1;
   w1.tw = 1; w1.id = wid; w1.warp = 0; w1.lane = lane; w1.tid = lane; w1.nth = 32;
   if (P.cta) {
@@ -970,83 +970,19 @@ __device__ __forceinline__ void stv(T* p, long long q, const T (&o)[Vec<T>::N]) 
   __stcg(reinterpret_cast<V*>(p) + q, x);
 }
 
-// ---------------------------------------------------------------------------
-// the solve kernel
-// ---------------------------------------------------------------------------
+// The SuperMann iteration (Alg. 4 with Anderson directions, Alg. 3) on one
+// problem by the group g: the whole grid of a single-problem launch, or one
+// CTA of the batched launch. Every CTA of the group runs the same scalar
+// control flow on the group-reduced scalars.
 template <class T, int CH>
-__global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, SolveOpts o, int tw) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  // the problem descriptor lives in shared memory so that the non-inlined
-  // evaluation reads it without a local-memory copy of the parameter
-  __shared__ __align__(16) unsigned char s_prob[sizeof(Prob<T>)];
-  for (int b = threadIdx.x; b < (int)sizeof(Prob<T>); b += blockDim.x)
-    s_prob[b] = reinterpret_cast<const unsigned char*>(&Pk)[b];
-  __syncthreads();
-  const Prob<T>& P = *reinterpret_cast<const Prob<T>*>(s_prob);
-  const Team tm = make_team(tw);
-  const int teams_per_cta = (blockDim.x >> 5) / tw;
-  const int tg = blockIdx.x * teams_per_cta + tm.id;
-  const int nt = gridDim.x * teams_per_cta;
-  Views<T, CH> sv;
-  sv.tw = tw;
-  sv.pipe_elems = Views<T, CH>::pipe_elems_for(P.pipe_bytes);
-  const size_t cta_bytes = cta_smem_bytes(P);
-  sv.pipe_base = reinterpret_cast<T*>(smraw + cta_bytes);
-  sv.base = sv.pipe_base + (size_t)teams_per_cta * 2 * sv.pipe_elems;
-  __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
-  Pipe<T> pp;
-  pp.on = P.pipe_bytes > 0;
-  pp.bar = s_bar + 2 * tm.id;
-  pp.buf[0] = sv.t_pipe(tm.id, 0);
-  pp.buf[1] = sv.t_pipe(tm.id, 1);
-  pp.par[0] = pp.par[1] = 0u;
-  pp.cur = 0;
-  __shared__ int s_ok[MAXTW];
-  pp.okp = s_ok + tm.id;
-  pp.diag = B.ctl->diag;
-  if (threadIdx.x < 2 * MAXTW) mbar_init(s_bar + threadIdx.x, 1);
-  fence_mbar_init();
-  __syncthreads();
-  // whole-CTA sweeps: ring of item buffers, carry vectors, child inputs, schedule
-  CtaState cs;
-  __shared__ Sched s_sched;
-  __shared__ int s_cta_ok;
-  if (P.cta) {
-    const unsigned base = smem_u32(smraw);
-    cs.ring.bar0 = smem_u32(s_bar);
-    cs.ring.buf0 = base;
-    cs.ring.bstride = (unsigned)P.item_bytes;
-    cs.ring.nbuf = P.nbuf;
-    cs.ring.par = 0u;
-    cs.ring.head = 0;
-    cs.ring.ahead = 0;
-    cs.ring.diag = B.ctl->diag;
-    const unsigned ldcb = (unsigned)(P.ldc * sizeof(T));
-    cs.mem.carry0 = base + (unsigned)P.nbuf * (unsigned)P.item_bytes;
-    cs.mem.carry1 = cs.mem.carry0 + ldcb;
-    cs.mem.qin = cs.mem.carry1 + ldcb;
-    // padding rows of the vectors are read against zero coefficients: keep them finite
-    T* vz = reinterpret_cast<T*>(smraw + (size_t)P.nbuf * P.item_bytes);
-    for (int k = threadIdx.x; k < (2 + P.qslots) * P.ldc; k += blockDim.x) vz[k] = T(0);
-    sched_build(P, s_sched, tg, nt);
-    cs.sched = &s_sched;
-    cs.s_ok = &s_cta_ok;
-  }
+__device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, const Team& tm,
+                           const Views<T, CH>& sv, Pipe<T>& pp, CtaState& cs, int tg, int nt, Grid& g) {
   SolveCtl* ctl = B.ctl;
-  Grid g;
-  g.ctl = &ctl->bar;
-  g.flags = B.flags;
-  g.partials = B.partials;
-  g.epoch = 0;
-  __shared__ unsigned long long s_prof[16];
-  if (threadIdx.x < 16) s_prof[threadIdx.x] = 0ull;
-  __syncthreads();
-  g.prof = s_prof;
   T* buf[4] = {B.V, B.TV, B.VT, B.TVT};
   int iV = 0, iTV = 1, iVT = 2, iTVT = 3;
   const long long nv = P.nv;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long gstride = (long long)gridDim.x * blockDim.x;
+  const long long gtid = (long long)g.rank * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)g.size * blockDim.x;
   constexpr int VN = Vec<T>::N;
   const long long nvec = nv / VN;
   const long long ss = B.sstride;
@@ -1322,7 +1258,7 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
     }
   }
 done:
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (g.rank == 0 && threadIdx.x == 0) {
     ctl->status = status;
     ctl->iters = k; ctl->n_T = nT; ctl->n_K0 = nK0; ctl->n_K1 = nK1; ctl->n_K2 = nK2;
     ctl->n_fb = nFB; ctl->n_bt = nBT;
@@ -1330,16 +1266,224 @@ done:
     for (int q = 0; q < NRED; ++q) ctl->stats[q] = red[q];
     ctl->final_v = iV;       // final buffer indices for the host
     ctl->final_tv = iTV;
-    for (int q = 0; q < 16; ++q) ctl->prof[q] = s_prof[q];
+    for (int q = 0; q < 16; ++q) ctl->prof[q] = g.prof[q];
   }
   return;
 fail:
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (g.rank == 0 && threadIdx.x == 0) {
     ctl->status = -5;
     ctl->iters = k; ctl->n_T = nT;
     ctl->final_v = iV;
     ctl->final_tv = iTV;
   }
+}
+
+// ---------------------------------------------------------------------------
+// the solve kernel
+// ---------------------------------------------------------------------------
+template <class T, int CH>
+__global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, SolveOpts o, int tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  // the problem descriptor lives in shared memory so that the non-inlined
+  // evaluation reads it without a local-memory copy of the parameter
+  __shared__ __align__(16) unsigned char s_prob[sizeof(Prob<T>)];
+  for (int b = threadIdx.x; b < (int)sizeof(Prob<T>); b += blockDim.x)
+    s_prob[b] = reinterpret_cast<const unsigned char*>(&Pk)[b];
+  __syncthreads();
+  const Prob<T>& P = *reinterpret_cast<const Prob<T>*>(s_prob);
+  const Team tm = make_team(tw);
+  const int teams_per_cta = (blockDim.x >> 5) / tw;
+  const int tg = blockIdx.x * teams_per_cta + tm.id;
+  const int nt = gridDim.x * teams_per_cta;
+  Views<T, CH> sv;
+  sv.tw = tw;
+  sv.pipe_elems = Views<T, CH>::pipe_elems_for(P.pipe_bytes);
+  const size_t cta_bytes = cta_smem_bytes(P);
+  sv.pipe_base = reinterpret_cast<T*>(smraw + cta_bytes);
+  sv.base = sv.pipe_base + (size_t)teams_per_cta * 2 * sv.pipe_elems;
+  __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
+  Pipe<T> pp;
+  pp.on = P.pipe_bytes > 0;
+  pp.bar = s_bar + 2 * tm.id;
+  pp.buf[0] = sv.t_pipe(tm.id, 0);
+  pp.buf[1] = sv.t_pipe(tm.id, 1);
+  pp.par[0] = pp.par[1] = 0u;
+  pp.cur = 0;
+  __shared__ int s_ok[MAXTW];
+  pp.okp = s_ok + tm.id;
+  pp.diag = B.ctl->diag;
+  if (threadIdx.x < 2 * MAXTW) mbar_init(s_bar + threadIdx.x, 1);
+  fence_mbar_init();
+  __syncthreads();
+  // whole-CTA sweeps: ring of item buffers, carry vectors, child inputs, schedule
+  CtaState cs;
+  __shared__ Sched s_sched;
+  __shared__ int s_cta_ok;
+  if (P.cta) {
+    const unsigned base = smem_u32(smraw);
+    cs.ring.bar0 = smem_u32(s_bar);
+    cs.ring.buf0 = base;
+    cs.ring.bstride = (unsigned)P.item_bytes;
+    cs.ring.nbuf = P.nbuf;
+    cs.ring.par = 0u;
+    cs.ring.head = 0;
+    cs.ring.ahead = 0;
+    cs.ring.diag = B.ctl->diag;
+    const unsigned ldcb = (unsigned)(P.ldc * sizeof(T));
+    cs.mem.carry0 = base + (unsigned)P.nbuf * (unsigned)P.item_bytes;
+    cs.mem.carry1 = cs.mem.carry0 + ldcb;
+    cs.mem.qin = cs.mem.carry1 + ldcb;
+    // padding rows of the vectors are read against zero coefficients: keep them finite
+    T* vz = reinterpret_cast<T*>(smraw + (size_t)P.nbuf * P.item_bytes);
+    for (int k = threadIdx.x; k < (2 + P.qslots) * P.ldc; k += blockDim.x) vz[k] = T(0);
+    sched_build(P, s_sched, tg, nt);
+    cs.sched = &s_sched;
+    cs.s_ok = &s_cta_ok;
+  }
+  SolveCtl* ctl = B.ctl;
+  Grid g;
+  g.ctl = &ctl->bar;
+  g.flags = B.flags;
+  g.partials = B.partials;
+  g.epoch = 0;
+  g.rank = blockIdx.x;
+  g.size = gridDim.x;
+  g.local = false;
+  __shared__ unsigned long long s_prof[16];
+  if (threadIdx.x < 16) s_prof[threadIdx.x] = 0ull;
+  __syncthreads();
+  g.prof = s_prof;
+  solve_loop<T, CH>(P, B, o, tm, sv, pp, cs, tg, nt, g);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launch. A persistent grid in which
+//  - the first CTAs form gangs (BatchPlan): gang k of size g solves its static
+//    list of large problems one after the other, its CTAs iterating on each
+//    problem together with barriers and reductions among the gang's CTAs;
+//  - every other CTA, and every gang CTA once its list is done, takes small
+//    problems from a queue (small_order, largest first) and solves each one
+//    alone, with the barriers and reductions inside the CTA.
+// tws[p]: warps per team of problem p's sweeps (picked by the autotuner);
+// cycles[p]: clock cycles that the first CTA of the problem spent on it.
+// ---------------------------------------------------------------------------
+
+template <class T, int CH>
+__device__ __forceinline__ void batch_one(const Prob<T>* __restrict__ probs, const SolveBufs<T>* __restrict__ bufs,
+                                          const int* __restrict__ tws, const SolveOpts& o, int pi, Grid& g,
+                                          unsigned char* smraw, unsigned char* s_prob, uint64_t* s_bar, int* s_ok,
+                                          unsigned long long* s_prof, bool first, long long* cycles) {
+  const long long t0 = clock64();
+  for (int b = threadIdx.x; b < (int)sizeof(Prob<T>); b += blockDim.x)
+    s_prob[b] = reinterpret_cast<const unsigned char*>(probs + pi)[b];
+  if (threadIdx.x < 16) s_prof[threadIdx.x] = 0ull;
+  // fresh mbarrier phases for this problem (every copy of the last one was waited for)
+  if (!first && threadIdx.x < 2 * MAXTW) {
+    mbar_inval(s_bar + threadIdx.x);
+    mbar_init(s_bar + threadIdx.x, 1);
+  }
+  fence_mbar_init();
+  __syncthreads();
+  const Prob<T>& P = *reinterpret_cast<const Prob<T>*>(s_prob);
+  const SolveBufs<T> B = bufs[pi];
+  const int tw = tws[pi];
+  const Team tm = make_team(tw);
+  const int teams = (blockDim.x >> 5) / tw;
+  Views<T, CH> sv;
+  sv.tw = tw;
+  sv.pipe_elems = Views<T, CH>::pipe_elems_for(P.pipe_bytes);
+  sv.pipe_base = reinterpret_cast<T*>(smraw);
+  sv.base = sv.pipe_base + (size_t)teams * 2 * sv.pipe_elems;
+  Pipe<T> pp;
+  pp.on = P.pipe_bytes > 0;
+  pp.bar = s_bar + 2 * tm.id;
+  pp.buf[0] = sv.t_pipe(tm.id, 0);
+  pp.buf[1] = sv.t_pipe(tm.id, 1);
+  pp.par[0] = pp.par[1] = 0u;
+  pp.cur = 0;
+  pp.okp = s_ok + tm.id;
+  pp.diag = B.ctl->diag;
+  CtaState cs{};   // the whole-CTA sweeps are not used in the batch (P.cta == 0)
+  g.ctl = &B.ctl->bar;
+  g.prof = s_prof;
+  solve_loop<T, CH>(P, B, o, tm, sv, pp, cs, g.rank * teams + tm.id, g.size * teams, g);
+  __syncthreads();
+  if (threadIdx.x == 0 && g.rank == 0 && cycles) cycles[pi] = clock64() - t0;
+}
+
+template <class T, int CH>
+__global__ void __launch_bounds__(256, 1)
+    k_batch(const Prob<T>* __restrict__ probs, const SolveBufs<T>* __restrict__ bufs,
+            const int* __restrict__ tws, SolveOpts o, BatchPlan plan, long long* __restrict__ cycles) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(16) unsigned char s_prob[sizeof(Prob<T>)];
+  __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
+  __shared__ int s_ok[MAXTW];
+  __shared__ unsigned long long s_prof[16];
+  __shared__ int s_q;
+  if (threadIdx.x < 2 * MAXTW) mbar_init(s_bar + threadIdx.x, 1);
+  fence_mbar_init();
+  __syncthreads();
+  bool first = true;
+  if ((int)blockIdx.x < plan.n_gang_ctas) {
+    const int k = plan.gang_of[blockIdx.x];
+    const int start = plan.gang_start[k];
+    Grid g;
+    g.rank = blockIdx.x - start;
+    g.size = plan.gang_size[k];
+    g.local = g.size == 1;
+    g.flags = plan.flags + start;
+    g.partials = plan.partials + (size_t)2 * NRED * start;
+    g.epoch = 0;
+    for (int q = plan.list_off[k]; q < plan.list_off[k + 1]; ++q) {
+      batch_one<T, CH>(probs, bufs, tws, o, plan.list[q], g, smraw, s_prob, s_bar, s_ok, s_prof, first, cycles);
+      first = false;
+    }
+  }
+  Grid g;
+  g.rank = 0;
+  g.size = 1;
+  g.local = true;
+  g.flags = nullptr;
+  g.partials = nullptr;
+  g.epoch = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_q = atomicAdd(plan.next, 1);
+    __syncthreads();
+    const int q = s_q;
+    __syncthreads();
+    if (q >= plan.n_small) break;
+    batch_one<T, CH>(probs, bufs, tws, o, plan.small_order[q], g, smraw, s_prob, s_bar, s_ok, s_prof, first, cycles);
+    first = false;
+  }
+}
+
+template <class T, int CH>
+cudaError_t launch_batch_ch(const Prob<T>* probs, const SolveBufs<T>* bufs, const int* tws, const SolveOpts& o,
+                            const BatchPlan& plan, long long* cycles, size_t smem, int grid, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const Prob<T>* a0 = probs;
+  const SolveBufs<T>* a1 = bufs;
+  const int* a2 = tws;
+  SolveOpts a3 = o;
+  BatchPlan a4 = plan;
+  long long* a5 = cycles;
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
+  // cooperative: the gangs' barriers need their CTAs resident together
+  return cudaLaunchCooperativeKernel((void*)k_batch<T, CH>, dim3(grid), dim3(256), args, smem, s);
+}
+
+template <class T, int CH>
+int batch_grid_ch(size_t smem, int* out) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaFuncSetAttribute(k_batch<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<T, CH>, 256, smem) != cudaSuccess) return -1;
+  *out = nsm * per;
+  return 0;
 }
 
 template <class T, int CH>

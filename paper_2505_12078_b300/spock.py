@@ -26,6 +26,8 @@ EXPORTED = [
     "spock_problem_set_x0", "spock_op_T", "spock_op_L", "spock_op_Lt", "spock_solve_opts_default",
     "spock_solve", "spock_solve_device", "spock_get_iterate", "spock_set_iterate",
     "spock_status_str", "spock_version", "spock_op_T_noalloc",
+    "spock_batch_create", "spock_batch_destroy", "spock_batch_sizes", "spock_batch_set_tw",
+    "spock_batch_autotune", "spock_batch_solve",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -66,6 +68,11 @@ class Info(C.Structure):
         return d
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("n_T", C.c_int), ("tw", C.c_int),
+                ("res_inf", C.c_double), ("risk", C.c_double), ("device_ms", C.c_double)]
+
+
 _lib = None
 
 
@@ -97,6 +104,14 @@ def load(path: str = LIB_PATH):
     lib.spock_solve_device.argtypes = [vp, vp, C.POINTER(SolveOpts), vp, vp, vp, C.POINTER(Info)]
     lib.spock_get_iterate.argtypes = [vp, C.c_int, vp, vp]
     lib.spock_set_iterate.argtypes = [vp, C.c_int, vp, vp]
+    lib.spock_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp)]
+    lib.spock_batch_destroy.argtypes = [vp]
+    lib.spock_batch_destroy.restype = None
+    _llp = C.POINTER(C.c_longlong)
+    lib.spock_batch_sizes.argtypes = [vp, _llp, _llp, _llp]
+    lib.spock_batch_set_tw.argtypes = [vp, _ip]
+    lib.spock_batch_autotune.argtypes = [vp, C.c_int, _ip]
+    lib.spock_batch_solve.argtypes = [vp, _dp, C.POINTER(SolveOpts), _dp, _dp, _dp, C.POINTER(BatchInfo), _dp]
     lib.spock_status_str.argtypes = [C.c_int]
     lib.spock_status_str.restype = C.c_char_p
     lib.spock_version.restype = C.c_int
@@ -291,3 +306,62 @@ class Problem:
     def set_iterate(self, v):
         _check(load().spock_set_iterate(self.h, self._prec(v), C.c_void_p(v.data_ptr()), None),
                "set_iterate")
+
+
+class Batch:
+    """Many problems solved together in one persistent launch (spock_batch_*).
+    The problems must stay alive and must not be solved on their own while the
+    batch is in use."""
+
+    def __init__(self, problems, precision=32):
+        lib = load()
+        self.problems = list(problems)
+        self.count = len(self.problems)
+        self.precision = int(precision)
+        arr = (C.c_void_p * self.count)(*[p.h for p in self.problems])
+        h = C.c_void_p()
+        _check(lib.spock_batch_create(arr, self.count, self.precision, C.byref(h)), "spock_batch_create")
+        self.h = h
+        a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        _check(lib.spock_batch_sizes(h, C.byref(a), C.byref(b), C.byref(c)), "spock_batch_sizes")
+        self.x0_total, self.x_total, self.u_total = a.value, b.value, c.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().spock_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tw(self, tw=None):
+        t = None if tw is None else np.ascontiguousarray(tw, dtype=np.int32)
+        _check(load().spock_batch_set_tw(self.h, None if t is None else t.ctypes.data_as(_ip)), "set_tw")
+
+    def autotune(self, iters=20):
+        tw = np.zeros(self.count, dtype=np.int32)
+        _check(load().spock_batch_autotune(self.h, int(iters), tw.ctypes.data_as(_ip)), "autotune")
+        return tw
+
+    def solve(self, x0s, o: SolveOpts = None):
+        """x0s: list of per-problem x0. Returns dict(x=[...], u=[...], risk, info=[...],
+        status, total_ms)."""
+        o = o or opts(precision=self.precision)
+        x0 = np.ascontiguousarray(np.concatenate([np.asarray(v, dtype=np.float64).ravel() for v in x0s]))
+        assert x0.size == self.x0_total
+        x = np.zeros(self.x_total)
+        u = np.zeros(self.u_total)
+        risk = np.zeros(self.count)
+        info = (BatchInfo * self.count)()
+        ms = C.c_double()
+        st = _check(load().spock_batch_solve(self.h, _ptr(x0), C.byref(o), _ptr(x), _ptr(u), _ptr(risk),
+                                             info, C.byref(ms)), "spock_batch_solve")
+        xs, us, ox, ou = [], [], 0, 0
+        for p in self.problems:
+            xs.append(x[ox:ox + p.n * p.nx].reshape(p.n, p.nx)); ox += p.n * p.nx
+            us.append(u[ou:ou + p.n_nl * p.nu].reshape(p.n_nl, p.nu)); ou += p.n_nl * p.nu
+        infos = [{k: getattr(info[i], k) for k, _ in BatchInfo._fields_} for i in range(self.count)]
+        return dict(x=xs, u=us, risk=risk, info=infos, status=st, total_ms=ms.value)
