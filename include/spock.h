@@ -54,6 +54,7 @@ extern "C" {
 /* status codes */
 #define SPOCK_OK 0
 #define SPOCK_MAXITER 1      /* warning: not converged within max_iters; outputs written */
+#define SPOCK_PARTIAL 2      /* warning: only some plants were admitted (device memory) */
 #define SPOCK_EINVAL -1      /* invalid argument (tree shape, sizes, probabilities, NULL) */
 #define SPOCK_ENOMEM -2      /* device memory could not be allocated / admission refused */
 #define SPOCK_ENOTPD -3      /* Cholesky of R~ = I + sum B'PB failed (not positive definite) */
@@ -259,6 +260,55 @@ int spock_batch_autotune(spock_batch* b, int iters, int* tw_out);
  * problem converged, SPOCK_MAXITER if some did not, or the first error. */
 int spock_batch_solve(spock_batch* b, const double* x0, const spock_solve_opts* opts, double* x_out,
                       double* u_out, double* risk, spock_batch_info* info, double* total_ms);
+
+/* ---------------- serving (MPC requests, continuous batching) ----------------
+ * Plants (problems) stay resident on the device with their factors and their
+ * last iterate. Requests (plant, x0) are published into a ring in mapped host
+ * memory; a persistent launch whose CTAs claim requests as they appear runs
+ * each one alone in a CTA, so requests that arrive while others are on the GPU
+ * start as soon as a CTA frees up, and a result does not depend on the other
+ * requests in flight. Requests of one plant run one after the other (they share
+ * the plant's iterate). The launch leaves after 1 s without requests and is
+ * restarted by the next call. The paper has no serving layer; this is the
+ * library's addition. Plants need nx <= 64, nu <= 64, nx + nu <= 126. */
+typedef struct spock_server spock_server;
+
+typedef struct spock_serve_result {
+    long long id;         /* as returned by spock_server_submit */
+    int plant;
+    int status;           /* SPOCK_OK, SPOCK_MAXITER or SPOCK_ETIMEOUT */
+    int iters;
+    int n_T;
+    double res_inf;       /* ||v - T(v)||_inf at exit, iteration precision */
+    double risk;          /* s^0 of T(v) */
+    double u0[64];        /* first control u^0 (unscaled), nu entries */
+    double device_ms;     /* time on the device from claim to result */
+    double latency_ms;    /* host time from submission to the poll that saw the result */
+} spock_serve_result;
+
+/* Admit plants in the given order while their solve buffers fit in free device
+ * memory (256 MB kept free); *admitted (may be NULL) = how many. opts as for
+ * spock_solve (precision must equal `precision`; fp64_check ignored);
+ * ring_slots >= 1 bounds the requests on the device at once. Returns
+ * SPOCK_PARTIAL if some plants were refused, SPOCK_ENOMEM if none fit. The
+ * plants must outlive the server and not be solved on their own meanwhile. */
+int spock_server_create(spock_problem* const* plants, int count, int precision, const spock_solve_opts* opts,
+                        int ring_slots, spock_server** out, int* admitted);
+
+/* Queue a request: x0 (host) [nx of the plant], unscaled; warm_start = 1
+ * starts from the plant's last iterate. *id_out (may be NULL) = request id.
+ * SPOCK_ENOMEM for a plant that was not admitted. Non-blocking. */
+int spock_server_submit(spock_server* s, int plant, const double* x0, int warm_start, long long* id_out);
+
+/* Collect up to max_out finished requests into out (host) and hand waiting
+ * requests to the device; *n_out = how many were collected. Non-blocking. */
+int spock_server_poll(spock_server* s, spock_serve_result* out, int max_out, int* n_out);
+
+/* Requests submitted and not yet collected by spock_server_poll. */
+long long spock_server_outstanding(const spock_server* s);
+
+/* Stop the persistent launch (after the requests in flight) and free. */
+void spock_server_destroy(spock_server* s);
 
 const char* spock_status_str(int status);
 int spock_version(void);

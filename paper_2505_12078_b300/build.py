@@ -25,6 +25,7 @@ UNITS = [
     ("spock_solver", "spock_solver.cu", []),
     ("spock_noalloc", "spock_noalloc.cu", []),
     ("spock_batch", "spock_batch.cu", []),
+    ("spock_serve", "spock_serve.cu", []),
     ("solver_f1", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=1", "-DSPOCK_SUFFIX=f1", "-DSPOCK_WITH_BATCH"]),
     ("solver_f2", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=f2"]),
     ("solver_d2", "spock_solver_inst.cu", ["-DSPOCK_T=double", "-DSPOCK_CH=2", "-DSPOCK_SUFFIX=d2", "-DSPOCK_WITH_BATCH"]),

@@ -463,6 +463,7 @@ const char* spock_status_str(int s) {
   switch (s) {
     case SPOCK_OK: return "ok";
     case SPOCK_MAXITER: return "not converged within max_iters";
+    case SPOCK_PARTIAL: return "only some plants admitted (device memory)";
     case SPOCK_EINVAL: return "invalid argument";
     case SPOCK_ENOMEM: return "out of device memory";
     case SPOCK_ENOTPD: return "R~ = I + sum B'PB not positive definite";

@@ -101,6 +101,42 @@ struct BatchPlan {
   int* next;                // queue position of small_order (zeroed before the launch)
 };
 
+// Serving: requests and results live in mapped host memory. The host fills a
+// request slot, then publishes it by raising `tail`; a CTA of the persistent
+// k_serve claims it, solves the plant's problem from the request's x0 (warm
+// from the plant's resident iterate if asked), writes the result slot and
+// raises its `done` word.
+constexpr int SERVE_MAX_NX = 64;
+constexpr int SERVE_MAX_NU = 64;
+struct ServeReq {
+  int plant;             // index into the server's plants
+  int warm;              // 1: start from the plant's last iterate
+  long long id;          // request id (echoed)
+  double x0[SERVE_MAX_NX];
+};
+struct ServeRes {
+  long long id;
+  int status, iters, n_T, pad;
+  double res_inf, risk;
+  double u0[SERVE_MAX_NU];   // the first control, unscaled
+  unsigned long long t_claim, t_done;   // device global timer (ns)
+  volatile int done;         // raised last (release), cleared by the host
+  int pad2;
+};
+struct ServeCtl {
+  volatile long long tail;   // requests published by the host
+  volatile int stop;         // host: leave now
+  int pad;
+};
+template <class T>
+struct ServeMeta {           // per plant: what a request needs beyond Prob / SolveBufs
+  int nx, nu;
+  long long o_u, nv;
+  const double* Sx;
+  const double* Su;
+  T* x0s;
+};
+
 template <class T>
 cudaError_t launch_solve(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, int tw,
                          int grid, int threads, cudaStream_t s);

@@ -1,0 +1,339 @@
+// spock_serve.cu -- host side of serving (include/spock.h, "serving"):
+// resident plants (problems with their factors and warm-start iterates on the
+// device), admission by device memory, a request ring in mapped host memory
+// drained by the persistent k_serve launch, and per-plant ordering of requests.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <deque>
+#include <vector>
+
+#include "../../include/spock.h"
+#include "spock_problem.h"
+
+namespace spock {
+
+cudaError_t launch_serve_f1(const Prob<float>*, const SolveBufs<float>*, const int*, const ServeMeta<float>*,
+                            const SolveOpts&, const ServeReq*, ServeRes*, int, ServeCtl*, long long*,
+                            unsigned long long, size_t, int, cudaStream_t);
+cudaError_t launch_serve_d2(const Prob<double>*, const SolveBufs<double>*, const int*, const ServeMeta<double>*,
+                            const SolveOpts&, const ServeReq*, ServeRes*, int, ServeCtl*, long long*,
+                            unsigned long long, size_t, int, cudaStream_t);
+int serve_grid_f1(size_t, int*);
+int serve_grid_d2(size_t, int*);
+size_t views_bytes_f1(int tw, int pipe_bytes);
+size_t views_bytes_d2(int tw, int pipe_bytes);
+
+}  // namespace spock
+
+using namespace spock;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr unsigned long long kIdleNs = 1000000000ull;   // k_serve leaves after 1 s without requests
+
+struct Pending {
+  long long id;
+  int warm;
+  double x0[SERVE_MAX_NX];
+  Clock::time_point t_submit;
+};
+
+}  // namespace
+
+struct spock_server {
+  int count = 0, precision = 32, admitted = 0, cap = 0;
+  std::vector<spock_problem*> plants;
+  SolveOpts so{};
+  DevMem mem;
+  void *d_probs = nullptr, *d_bufs = nullptr, *d_meta = nullptr;
+  int* d_tw = nullptr;
+  long long* d_head = nullptr;
+  ServeReq *h_ring = nullptr, *d_ring = nullptr;
+  ServeRes *h_res = nullptr, *d_res = nullptr;
+  ServeCtl *h_ctl = nullptr, *d_ctl = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+  cudaStream_t stream = nullptr;
+  bool launched = false;
+  long long tail = 0, next_id = 0;
+  std::vector<int> slot_busy;                      // ring slot holds an unfinished request
+  std::vector<int> slot_plant;
+  std::vector<Clock::time_point> slot_submit;
+  std::vector<int> plant_busy;                     // a request of the plant is on the device
+  std::vector<std::deque<Pending>> queue;          // per plant, waiting for the plant
+  long long outstanding = 0;
+};
+
+namespace {
+
+template <class T>
+Iter<T>& iter_of(spock_problem* p) {
+  if constexpr (sizeof(T) == 8) return p->f64; else return p->f32;
+}
+
+int tw_min(const spock_problem* p) {
+  const int d = p->nx + p->nu;
+  int t = 1;
+  while (64 * t < d) t *= 2;
+  return t;
+}
+
+template <class T>
+size_t views_bytes(int tw, int pipe_bytes) {
+  return sizeof(T) == 8 ? views_bytes_d2(tw, pipe_bytes) : views_bytes_f1(tw, pipe_bytes);
+}
+
+// bytes of one precision's solve buffers (what admission has to find free)
+size_t buffer_bytes(const spock_problem* p, int precision) {
+  const size_t w = precision == 64 ? 8 : 4;
+  const size_t nvp = (size_t)((p->nv + 3) & ~3LL);
+  return w * (7 * (size_t)p->nv + 6 * nvp) + sizeof(SolveCtl) + 64 * 1024;
+}
+
+template <class T>
+int serve_init(spock_server* s) {
+  const int n = s->admitted;
+  int optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  std::vector<Prob<T>> P(n);
+  std::vector<SolveBufs<T>> B(n);
+  std::vector<ServeMeta<T>> M(n);
+  std::vector<int> tw(n);
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    spock_problem* p = s->plants[i];
+    Iter<T>& it = iter_of<T>(p);
+    const int rc = ensure_bufs<T>(p, it);
+    if (rc) return rc;
+    tw[i] = tw_min(p);
+    const long long e = std::max((long long)p->nx * p->ldB,
+                                 (long long)(p->nx + p->nu) * p->ldF + (long long)p->nx * p->ldK);
+    const int pb = (int)(e * (long long)sizeof(T));
+    P[i] = it.P;
+    P[i].cta = 0;
+    P[i].pipe_bytes = (views_bytes<T>(tw[i], pb) + 16 * 1024 <= (size_t)optin) ? pb : 0;
+    smem = std::max(smem, views_bytes<T>(tw[i], P[i].pipe_bytes));
+    B[i] = it.sb;
+    M[i].nx = p->nx; M[i].nu = p->nu; M[i].o_u = p->o_u; M[i].nv = p->nv;
+    M[i].Sx = p->d_Sx; M[i].Su = p->d_Su; M[i].x0s = it.x0s;
+  }
+  DevMem& m = s->mem;
+  s->d_probs = m.alloc<Prob<T>>(n);
+  s->d_bufs = m.alloc<SolveBufs<T>>(n);
+  s->d_meta = m.alloc<ServeMeta<T>>(n);
+  s->d_tw = m.alloc<int>(n);
+  s->d_head = m.alloc<long long>(1);
+  if (m.failed) return SPOCK_ENOMEM;
+  if (cudaMemcpy(s->d_probs, P.data(), sizeof(Prob<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->d_bufs, B.data(), sizeof(SolveBufs<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->d_meta, M.data(), sizeof(ServeMeta<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->d_tw, tw.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(s->d_head, 0, sizeof(long long)) != cudaSuccess)
+    return SPOCK_EDEVICE;
+  s->smem = smem;
+  int g = 0;
+  const int rc = sizeof(T) == 8 ? serve_grid_d2(smem, &g) : serve_grid_f1(smem, &g);
+  if (rc || g <= 0) return SPOCK_EDEVICE;
+  s->grid = g;
+  return SPOCK_OK;
+}
+
+template <class T>
+cudaError_t relaunch(spock_server* s) {
+  if constexpr (sizeof(T) == 8)
+    return launch_serve_d2((const Prob<double>*)s->d_probs, (const SolveBufs<double>*)s->d_bufs, s->d_tw,
+                           (const ServeMeta<double>*)s->d_meta, s->so, s->d_ring, s->d_res, s->cap, s->d_ctl,
+                           s->d_head, kIdleNs, s->smem, s->grid, s->stream);
+  else
+    return launch_serve_f1((const Prob<float>*)s->d_probs, (const SolveBufs<float>*)s->d_bufs, s->d_tw,
+                           (const ServeMeta<float>*)s->d_meta, s->so, s->d_ring, s->d_res, s->cap, s->d_ctl,
+                           s->d_head, kIdleNs, s->smem, s->grid, s->stream);
+}
+
+// the persistent launch is running, or started (it leaves after kIdleNs idle)
+int ensure_running(spock_server* s) {
+  if (s->launched && cudaStreamQuery(s->stream) == cudaErrorNotReady) return SPOCK_OK;
+  if (s->launched && cudaStreamQuery(s->stream) != cudaSuccess) return SPOCK_EDEVICE;
+  const cudaError_t e = s->precision == 64 ? relaunch<double>(s) : relaunch<float>(s);
+  if (e != cudaSuccess) return SPOCK_EDEVICE;
+  s->launched = true;
+  return SPOCK_OK;
+}
+
+// publish request r of plant p into the next ring slot (false: slot busy)
+bool publish(spock_server* s, int p, const Pending& r) {
+  const int slot = (int)(s->tail % s->cap);
+  if (s->slot_busy[slot]) return false;
+  ServeReq& q = s->h_ring[slot];
+  q.plant = p;
+  q.warm = r.warm;
+  q.id = r.id;
+  memcpy(q.x0, r.x0, sizeof(q.x0));
+  s->h_res[slot].done = 0;
+  s->slot_busy[slot] = 1;
+  s->slot_plant[slot] = p;
+  s->slot_submit[slot] = r.t_submit;
+  s->plant_busy[p] = 1;
+  std::atomic_thread_fence(std::memory_order_release);
+  s->tail += 1;
+  s->h_ctl->tail = s->tail;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spock_server_create(spock_problem* const* plants, int count, int precision, const spock_solve_opts* opts,
+                        int ring_slots, spock_server** out, int* admitted) {
+  if (!out) return SPOCK_EINVAL;
+  *out = nullptr;
+  if (!plants || count < 1 || (precision != 32 && precision != 64) || ring_slots < 1) return SPOCK_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!plants[i]) return SPOCK_EINVAL;
+    if (plants[i]->nx > SERVE_MAX_NX || plants[i]->nu > SERVE_MAX_NU || plants[i]->nx + plants[i]->nu > 126)
+      return SPOCK_EUNSUPPORTED;
+  }
+  spock_solve_opts o;
+  if (opts) o = *opts;
+  else { spock_solve_opts_default(&o); o.precision = precision; }
+  if (o.precision != precision || !(o.tol >= 0) || o.max_iters < 0 || o.max_backtracks < 1 || o.method < 0 ||
+      o.method > 1)
+    return SPOCK_EINVAL;
+  spock_server* s = new spock_server();
+  s->count = count;
+  s->precision = precision;
+  s->plants.assign(plants, plants + count);
+  s->so.tol = o.tol; s->so.max_iters = o.max_iters; s->so.max_backtracks = o.max_backtracks;
+  s->so.method = o.method; s->so.rank_tol = precision == 64 ? 1e-10 : 1e-5;
+  // admission by device memory: plants in order while their solve buffers fit
+  // (keeping 256 MB free for the launch and the ring)
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  long long room = (long long)fr - (256ll << 20);
+  int adm = 0;
+  for (int i = 0; i < count; ++i) {
+    const Iter<double>& f = plants[i]->f64;
+    const bool have = precision == 64 ? f.have_bufs : plants[i]->f32.have_bufs;
+    const long long need = have ? 0 : (long long)buffer_bytes(plants[i], precision);
+    if (need > room) break;
+    room -= need;
+    ++adm;
+  }
+  s->admitted = adm;
+  if (admitted) *admitted = adm;
+  if (adm == 0) { delete s; return SPOCK_ENOMEM; }
+  s->cap = ring_slots;
+  s->slot_busy.assign(ring_slots, 0);
+  s->slot_plant.assign(ring_slots, -1);
+  s->slot_submit.resize(ring_slots);
+  s->plant_busy.assign(count, 0);
+  s->queue.resize(count);
+  if (cudaHostAlloc(&s->h_ring, sizeof(ServeReq) * ring_slots, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc(&s->h_res, sizeof(ServeRes) * ring_slots, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc(&s->h_ctl, sizeof(ServeCtl), cudaHostAllocMapped) != cudaSuccess) {
+    spock_server_destroy(s);
+    return SPOCK_ENOMEM;
+  }
+  memset(s->h_ring, 0, sizeof(ServeReq) * ring_slots);
+  memset(s->h_res, 0, sizeof(ServeRes) * ring_slots);
+  memset((void*)s->h_ctl, 0, sizeof(ServeCtl));
+  cudaHostGetDevicePointer((void**)&s->d_ring, s->h_ring, 0);
+  cudaHostGetDevicePointer((void**)&s->d_res, s->h_res, 0);
+  cudaHostGetDevicePointer((void**)&s->d_ctl, (void*)s->h_ctl, 0);
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    spock_server_destroy(s);
+    return SPOCK_EDEVICE;
+  }
+  const int rc = precision == 64 ? serve_init<double>(s) : serve_init<float>(s);
+  if (rc) { spock_server_destroy(s); return rc; }
+  if (cudaDeviceSynchronize() != cudaSuccess) { spock_server_destroy(s); return SPOCK_EDEVICE; }
+  *out = s;
+  return adm == count ? SPOCK_OK : SPOCK_PARTIAL;
+}
+
+int spock_server_submit(spock_server* s, int plant, const double* x0, int warm_start, long long* id_out) {
+  if (!s || !x0 || plant < 0 || plant >= s->count) return SPOCK_EINVAL;
+  if (plant >= s->admitted) return SPOCK_ENOMEM;
+  const int nx = s->plants[plant]->nx;
+  for (int k = 0; k < nx; ++k)
+    if (!isfinite(x0[k])) return SPOCK_EINVAL;
+  Pending r;
+  r.id = s->next_id++;
+  r.warm = warm_start ? 1 : 0;
+  memset(r.x0, 0, sizeof(r.x0));
+  memcpy(r.x0, x0, sizeof(double) * nx);
+  r.t_submit = Clock::now();
+  if (id_out) *id_out = r.id;
+  s->outstanding += 1;
+  if (s->plant_busy[plant] || !s->queue[plant].empty() || !publish(s, plant, r)) {
+    s->queue[plant].push_back(r);
+    return SPOCK_OK;
+  }
+  return ensure_running(s);
+}
+
+int spock_server_poll(spock_server* s, spock_serve_result* out, int max_out, int* n_out) {
+  if (!s || (max_out > 0 && !out)) return SPOCK_EINVAL;
+  int n = 0;
+  std::vector<int> freed;
+  for (int slot = 0; slot < s->cap && n < max_out; ++slot) {
+    if (!s->slot_busy[slot] || !s->h_res[slot].done) continue;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    const ServeRes& r = s->h_res[slot];
+    const int p = s->slot_plant[slot];
+    spock_serve_result& o = out[n++];
+    o.id = r.id;
+    o.plant = p;
+    o.status = r.status == 0 ? SPOCK_OK : (r.status > 0 ? SPOCK_MAXITER : SPOCK_ETIMEOUT);
+    o.iters = r.iters;
+    o.n_T = r.n_T;
+    o.res_inf = r.res_inf;
+    o.risk = r.risk;
+    memset(o.u0, 0, sizeof(o.u0));
+    memcpy(o.u0, r.u0, sizeof(double) * s->plants[p]->nu);
+    o.device_ms = 1e-6 * (double)(r.t_done - r.t_claim);
+    o.latency_ms = 1e-3 * (double)std::chrono::duration_cast<std::chrono::microseconds>(
+                               Clock::now() - s->slot_submit[slot]).count();
+    s->slot_busy[slot] = 0;
+    s->plant_busy[p] = 0;
+    s->outstanding -= 1;
+    freed.push_back(p);
+  }
+  // requests waiting for a plant that is free now
+  bool pushed = false;
+  for (int p = 0; p < s->count; ++p) {
+    if (s->plant_busy[p] || s->queue[p].empty()) continue;
+    if (!publish(s, p, s->queue[p].front())) break;
+    s->queue[p].pop_front();
+    pushed = true;
+  }
+  if (n_out) *n_out = n;
+  if (pushed || (s->outstanding > 0 && !s->launched)) return ensure_running(s);
+  if (s->outstanding > 0) return ensure_running(s);
+  return SPOCK_OK;
+}
+
+long long spock_server_outstanding(const spock_server* s) { return s ? s->outstanding : -1; }
+
+void spock_server_destroy(spock_server* s) {
+  if (!s) return;
+  if (s->h_ctl) s->h_ctl->stop = 1;
+  if (s->stream) {
+    cudaStreamSynchronize(s->stream);
+    cudaStreamDestroy(s->stream);
+  }
+  if (s->h_ring) cudaFreeHost(s->h_ring);
+  if (s->h_res) cudaFreeHost(s->h_res);
+  if (s->h_ctl) cudaFreeHost((void*)s->h_ctl);
+  s->mem.free_all();
+  delete s;
+}
+
+}  // extern "C"

@@ -1458,6 +1458,140 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Serving: a persistent grid whose CTAs claim requests from the ring in mapped
+// host memory as they are published, so requests that arrive while others run
+// start as soon as a CTA is free. Each request runs alone in its CTA (barriers
+// and reductions inside it): its result does not depend on the other requests.
+// Leaves when ctl->stop is raised or after idle_ns without a request (the host
+// relaunches it on the next submission).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long ld_acquire_sys(const volatile long long* p) {
+  long long v;
+  asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <class T, int CH>
+__global__ void __launch_bounds__(256, 1)
+    k_serve(const Prob<T>* __restrict__ probs, const SolveBufs<T>* __restrict__ bufs,
+            const int* __restrict__ tws, const ServeMeta<T>* __restrict__ meta, SolveOpts o,
+            const ServeReq* ring, ServeRes* res, int cap, ServeCtl* ctl, long long* head,
+            unsigned long long idle_ns) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(16) unsigned char s_prob[sizeof(Prob<T>)];
+  __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
+  __shared__ int s_ok[MAXTW];
+  __shared__ unsigned long long s_prof[16];
+  __shared__ long long s_q;
+  if (threadIdx.x < 2 * MAXTW) mbar_init(s_bar + threadIdx.x, 1);
+  fence_mbar_init();
+  __syncthreads();
+  Grid g;
+  g.rank = 0; g.size = 1; g.local = true; g.flags = nullptr; g.partials = nullptr; g.epoch = 0;
+  bool first = true;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      // claim the next published request (bounded idle wait)
+      long long q = -1;
+      const uint64_t t0 = global_ns();
+      for (;;) {
+        if (ctl->stop) break;
+        const long long h = *reinterpret_cast<volatile long long*>(head);
+        const long long tl = ld_acquire_sys(&ctl->tail);
+        if (h < tl) {
+          if (atomicCAS(reinterpret_cast<unsigned long long*>(head), (unsigned long long)h,
+                        (unsigned long long)(h + 1)) == (unsigned long long)h) {
+            q = h;
+            break;
+          }
+          continue;
+        }
+        if (global_ns() - t0 > idle_ns) break;
+        __nanosleep(2000);
+      }
+      s_q = q;
+    }
+    __syncthreads();
+    const long long q = s_q;
+    __syncthreads();
+    if (q < 0) break;
+    const ServeReq* rq = ring + (q % cap);
+    ServeRes* rs = res + (q % cap);
+    __shared__ int s_plant, s_warm;
+    __shared__ long long s_id;
+    __shared__ unsigned long long s_t0;
+    if (threadIdx.x == 0) {
+      s_plant = *reinterpret_cast<const volatile int*>(&rq->plant);
+      s_warm = *reinterpret_cast<const volatile int*>(&rq->warm);
+      s_id = *reinterpret_cast<const volatile long long*>(&rq->id);
+      s_t0 = global_ns();
+    }
+    __syncthreads();
+    const int pi = s_plant;
+    const ServeMeta<T> M = meta[pi];
+    const SolveBufs<T> B = bufs[pi];
+    for (int k = threadIdx.x; k < M.nx; k += blockDim.x)
+      M.x0s[k] = (T)(M.Sx[k] * *reinterpret_cast<const volatile double*>(&rq->x0[k]));
+    if (!s_warm)
+      for (long long e = threadIdx.x; e < M.nv; e += blockDim.x) B.V[e] = T(0);
+    {
+      int* c = reinterpret_cast<int*>(B.ctl);
+      for (int k = threadIdx.x; k < (int)(sizeof(SolveCtl) / sizeof(int)); k += blockDim.x) c[k] = 0;
+    }
+    __threadfence();
+    __syncthreads();
+    batch_one<T, CH>(probs, bufs, tws, o, pi, g, smraw, s_prob, s_bar, s_ok, s_prof, first, nullptr);
+    first = false;
+    // result: u0 = u~0 / Su from T(v); the final iterate moved into V (warm start)
+    const SolveCtl* c = B.ctl;
+    const int fv = c->final_v & 3, ftv = c->final_tv & 3;
+    T* bb[4] = {B.V, B.TV, B.VT, B.TVT};
+    const T* z = bb[ftv];
+    for (int k = threadIdx.x; k < M.nu; k += blockDim.x) rs->u0[k] = (double)ldc(z + M.o_u + k) / M.Su[k];
+    if (threadIdx.x == 0) {
+      rs->id = s_id;
+      rs->status = c->status; rs->iters = c->iters; rs->n_T = c->n_T;
+      rs->res_inf = c->res_inf;
+      rs->risk = (double)ldc(z);
+      rs->t_claim = s_t0;
+      rs->t_done = global_ns();
+    }
+    __syncthreads();
+    if (fv != 0)
+      for (long long e = threadIdx.x; e < M.nv; e += blockDim.x) B.V[e] = ldc(bb[fv] + e);
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence_system();
+      rs->done = 1;
+      __threadfence_system();
+    }
+  }
+}
+
+template <class T, int CH>
+cudaError_t launch_serve_ch(const Prob<T>* probs, const SolveBufs<T>* bufs, const int* tws, const ServeMeta<T>* meta,
+                            const SolveOpts& o, const ServeReq* ring, ServeRes* res, int cap, ServeCtl* ctl,
+                            long long* head, unsigned long long idle_ns, size_t smem, int grid, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_serve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_serve<T, CH><<<grid, 256, smem, s>>>(probs, bufs, tws, meta, o, ring, res, cap, ctl, head, idle_ns);
+  return cudaGetLastError();
+}
+
+template <class T, int CH>
+int serve_grid_ch(size_t smem, int* out) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaFuncSetAttribute(k_serve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_serve<T, CH>, 256, smem) != cudaSuccess) return -1;
+  *out = nsm * per;
+  return 0;
+}
+
 template <class T, int CH>
 cudaError_t launch_batch_ch(const Prob<T>* probs, const SolveBufs<T>* bufs, const int* tws, const SolveOpts& o,
                             const BatchPlan& plan, long long* cycles, size_t smem, int grid, cudaStream_t s) {

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(HERE, "libspock.so")
 
 SPOCK_OK = 0
 SPOCK_MAXITER = 1
-STATUS = {0: "ok", 1: "maxiter", -1: "einval", -2: "enomem", -3: "enotpd", -4: "edevice",
+SPOCK_PARTIAL = 2
+STATUS = {0: "ok", 1: "maxiter", 2: "partial", -1: "einval", -2: "enomem", -3: "enotpd", -4: "edevice",
           -5: "etimeout", -6: "eunsupported"}
 
 EXPORTED = [
@@ -28,6 +29,8 @@ EXPORTED = [
     "spock_status_str", "spock_version", "spock_op_T_noalloc",
     "spock_batch_create", "spock_batch_destroy", "spock_batch_sizes", "spock_batch_set_tw",
     "spock_batch_autotune", "spock_batch_solve",
+    "spock_server_create", "spock_server_submit", "spock_server_poll", "spock_server_outstanding",
+    "spock_server_destroy",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -73,6 +76,12 @@ class BatchInfo(C.Structure):
                 ("res_inf", C.c_double), ("risk", C.c_double), ("device_ms", C.c_double)]
 
 
+class ServeResult(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("plant", C.c_int), ("status", C.c_int), ("iters", C.c_int),
+                ("n_T", C.c_int), ("res_inf", C.c_double), ("risk", C.c_double), ("u0", C.c_double * 64),
+                ("device_ms", C.c_double), ("latency_ms", C.c_double)]
+
+
 _lib = None
 
 
@@ -112,6 +121,14 @@ def load(path: str = LIB_PATH):
     lib.spock_batch_set_tw.argtypes = [vp, _ip]
     lib.spock_batch_autotune.argtypes = [vp, C.c_int, _ip]
     lib.spock_batch_solve.argtypes = [vp, _dp, C.POINTER(SolveOpts), _dp, _dp, _dp, C.POINTER(BatchInfo), _dp]
+    lib.spock_server_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(SolveOpts), C.c_int,
+                                        C.POINTER(vp), _ip]
+    lib.spock_server_submit.argtypes = [vp, C.c_int, _dp, C.c_int, C.POINTER(C.c_longlong)]
+    lib.spock_server_poll.argtypes = [vp, C.POINTER(ServeResult), C.c_int, _ip]
+    lib.spock_server_outstanding.argtypes = [vp]
+    lib.spock_server_outstanding.restype = C.c_longlong
+    lib.spock_server_destroy.argtypes = [vp]
+    lib.spock_server_destroy.restype = None
     lib.spock_status_str.argtypes = [C.c_int]
     lib.spock_status_str.restype = C.c_char_p
     lib.spock_version.restype = C.c_int
@@ -365,3 +382,67 @@ class Batch:
             us.append(u[ou:ou + p.n_nl * p.nu].reshape(p.n_nl, p.nu)); ou += p.n_nl * p.nu
         infos = [{k: getattr(info[i], k) for k, _ in BatchInfo._fields_} for i in range(self.count)]
         return dict(x=xs, u=us, risk=risk, info=infos, status=st, total_ms=ms.value)
+
+
+class Server:
+    """Serving of MPC requests on resident plants (spock_server_*): requests are
+    admitted to the device as CTAs free up, each solved alone in its CTA."""
+
+    def __init__(self, plants, precision=32, o: SolveOpts = None, ring_slots=4096):
+        lib = load()
+        self.plants = list(plants)
+        self.precision = int(precision)
+        o = o or opts(precision=self.precision)
+        arr = (C.c_void_p * len(self.plants))(*[p.h for p in self.plants])
+        h = C.c_void_p()
+        adm = C.c_int()
+        self.status = _check(lib.spock_server_create(arr, len(self.plants), self.precision, C.byref(o),
+                                                     int(ring_slots), C.byref(h), C.byref(adm)),
+                             "spock_server_create")
+        self.h = h
+        self.admitted = adm.value
+        self._buf = (ServeResult * 1024)()
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().spock_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, plant, x0, warm=True):
+        x0 = _f64(x0)
+        rid = C.c_longlong()
+        _check(load().spock_server_submit(self.h, int(plant), _ptr(x0), int(bool(warm)), C.byref(rid)), "submit")
+        return rid.value
+
+    def poll(self):
+        """Finished requests as dicts (u0 trimmed to the plant's nu)."""
+        out = []
+        while True:
+            n = C.c_int()
+            _check(load().spock_server_poll(self.h, self._buf, len(self._buf), C.byref(n)), "poll")
+            for i in range(n.value):
+                r = self._buf[i]
+                d = {k: getattr(r, k) for k, _ in ServeResult._fields_ if k != "u0"}
+                d["u0"] = np.array(r.u0[: self.plants[r.plant].nu])
+                out.append(d)
+            if n.value < len(self._buf):
+                return out
+
+    def outstanding(self):
+        return load().spock_server_outstanding(self.h)
+
+    def drain(self, timeout_s=60.0):
+        import time
+        res, t0 = [], time.time()
+        while self.outstanding() > 0:
+            res += self.poll()
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError("requests still outstanding")
+            time.sleep(0.0002)
+        return res

@@ -1,0 +1,128 @@
+"""Serving (continuous batching of MPC requests on resident plants): results
+against the batched solve and the oracle, independence of a result from the
+other requests in flight, and warm starts."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle.spock_oracle import Oracle
+from paper_2505_12078_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2505_12078_b300 import build, spock
+    build.build()
+    spock.load()
+
+
+def _spock():
+    from paper_2505_12078_b300 import spock
+    return spock
+
+
+@pytest.fixture(scope="module")
+def plants():
+    spock = _spock()
+    out = []
+    for i, s in enumerate(synth.batch_specs(400, seed=4)):
+        if s["nx"] <= 12 and s["N"] <= 8 and s["b"] ** s["k"] <= 16:
+            p = synth.batch_problem(s, i)
+            out.append((p, spock.Problem(p)))
+        if len(out) == 6:
+            break
+    return out
+
+
+def _zero_iterates(plants):
+    for _, g in plants:
+        g.set_iterate(torch.zeros(g.n_v, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+
+
+def _wait(srv, n, timeout=120.0):
+    got, t0 = [], time.time()
+    while len(got) < n:
+        got += srv.poll()
+        assert time.time() - t0 < timeout, "requests did not finish"
+        time.sleep(0.0005)
+    return {r["id"]: r for r in got}
+
+
+def test_serve_equals_batch_and_oracle(plants):
+    """A cold request per plant: the same outputs as the batched FP32 solve
+    (same kernel path, one CTA per problem) and within 1e-3 of the oracle."""
+    spock = _spock()
+    o = spock.opts(precision=32, tol=1e-4, max_iters=20000)
+    _zero_iterates(plants)
+    b = spock.Batch([g for _, g in plants], precision=32)
+    rb = b.solve([p.x0 for p, _ in plants], o)
+    b.close()
+    srv = spock.Server([g for _, g in plants], precision=32, o=o)
+    assert srv.admitted == len(plants)
+    ids = [srv.submit(k, p.x0, warm=False) for k, (p, _) in enumerate(plants)]
+    res = _wait(srv, len(ids))
+    srv.close()
+    for k, (p, _) in enumerate(plants):
+        r = res[ids[k]]
+        assert r["status"] == 0
+        assert r["iters"] == rb["info"][k]["iters"]
+        assert np.array_equal(r["u0"], rb["u"][k][0])
+        assert r["risk"] == rb["risk"][k]
+        ref = Oracle(p).solve(tol=1e-4, max_iters=20000)
+        assert abs(r["risk"] - ref["risk"]) <= 1e-3 * max(1.0, abs(ref["risk"]))
+        assert np.max(np.abs(r["u0"] - ref["u"][0])) <= 1e-3 * max(1.0, np.max(np.abs(ref["u"][0])))
+
+
+def test_serve_alone_equals_mix(plants):
+    """The same cold request alone and among many others in flight: identical."""
+    spock = _spock()
+    o = spock.opts(precision=32, tol=1e-4, max_iters=5000)
+    p0, _ = plants[0]
+    srv = spock.Server([g for _, g in plants], precision=32, o=o)
+    _zero_iterates(plants)
+    a = srv.submit(0, p0.x0, warm=False)
+    alone = _wait(srv, 1)[a]
+    rng = np.random.default_rng(7)
+    ids = []
+    for rep in range(4):
+        for k, (p, _) in enumerate(plants):
+            if k == 0 and rep == 2:
+                ids.append(("probe", srv.submit(0, p0.x0, warm=False)))
+            ids.append(("other", srv.submit(k, p.x0 + 0.05 * rng.standard_normal(p.nx), warm=rep > 0)))
+    res = _wait(srv, len(ids))
+    srv.close()
+    probe = res[[i for t, i in ids if t == "probe"][0]]
+    assert np.array_equal(probe["u0"], alone["u0"])
+    assert probe["risk"] == alone["risk"] and probe["iters"] == alone["iters"]
+
+
+def test_serve_receding_horizon_warm_start(plants):
+    """MPC loop on one plant: each request starts from the plant's resident
+    iterate; after the first solve a small change of x0 needs fewer
+    iterations than a cold start."""
+    spock = _spock()
+    o = spock.opts(precision=32, tol=1e-4, max_iters=20000)
+    p, _ = plants[1]
+    srv = spock.Server([g for _, g in plants], precision=32, o=o)
+    _zero_iterates(plants)
+    assert srv.poll() == [] and srv.outstanding() == 0
+    i0 = srv.submit(1, p.x0, warm=False)
+    r0 = _wait(srv, 1)[i0]
+    rng = np.random.default_rng(3)
+    x1 = p.x0 + 0.01 * rng.standard_normal(p.nx)
+    iw = srv.submit(1, x1, warm=True)
+    rw = _wait(srv, 1)[iw]
+    ic = srv.submit(1, x1, warm=False)
+    rc = _wait(srv, 1)[ic]
+    srv.close()
+    assert r0["status"] == 0 and rw["status"] == 0 and rc["status"] == 0
+    assert rw["iters"] < rc["iters"]
+    # two FP32 approximations of the same optimum, each within the 1e-3 target
+    # of it: they agree to twice that
+    assert np.max(np.abs(rw["u0"] - rc["u0"])) <= 2e-3 * max(1.0, np.max(np.abs(rc["u0"])))
+    assert abs(rw["risk"] - rc["risk"]) <= 2e-3 * max(1.0, abs(rc["risk"]))
