@@ -170,7 +170,143 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+BATCH_COUNT = 512
+BATCH_FIXED_ITERS = 200      # fixed-work throughput on the whole draw
+SMALL_COUNT = 64             # the draw's problems with the fewest nodes: solves to 1e-4 and serving
+MAX_ITERS = 20000
+
+
+def _gen(i):
+    from paper_2505_12078_b300 import synth
+    return synth.batch_problem(synth.batch_specs(BATCH_COUNT, seed=4)[i], i)
+
+
+def batch_draw():
+    """The uneven 512-problem draw (seed 4), generated by a pool of spawned
+    host processes (before this process touches the GPU for the batch)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen, range(BATCH_COUNT), chunksize=8)
+
+
+def _plain_fp64(spock, G, probs, idx, max_iters, tol, warm=False, x0s=None):
+    t = time.time()
+    conv = iters = 0
+    for k in idx:
+        r = G[k].solve(x0s[k] if x0s else probs[k].x0,
+                       spock.opts(precision=64, tol=tol, max_iters=max_iters, warm_start=warm, fp64_check=False))
+        conv += r["status"] == 0
+        iters += r["info"]["iters"]
+    return time.time() - t, int(conv), int(iters)
+
+
+def bench_batched(spock, probs, G, small):
+    """Batched FP32 (one persistent graph-captured launch) against the plain
+    single-problem FP64 method (one cooperative launch per problem, the whole
+    GPU each): (1) fixed work, BATCH_FIXED_ITERS SPOCK iterations of every
+    problem of the draw; (2) the SMALL_COUNT smallest problems solved to
+    ||v - T(v)||_inf <= 1e-4. The plain method runs on every 8th problem (its
+    time is linear in the number of problems)."""
+    res = {"workload": "uneven draw of 512 problems (seed 4): nx~U{4..64}, nu=nx/2, N~U{5..20}, "
+                       "b~U{2..4}-way branching at the first k~U{1..4} stages, AV@R~U[0.2,1], box + ball; "
+                       f"{sum(len(p.anc) for p in probs)} nodes"}
+    o = spock.opts(precision=32, tol=0.0, max_iters=BATCH_FIXED_ITERS)
+    b = spock.Batch(G, precision=32)
+    x0s = [p.x0 for p in probs]
+    r = b.solve(x0s, o)
+    b.close()
+    it = sum(i["iters"] for i in r["info"])
+    pw, _, pit = _plain_fp64(spock, G, probs, range(0, len(probs), 8), BATCH_FIXED_ITERS, 0.0)
+    res["fixed_work"] = {"iters_per_problem": BATCH_FIXED_ITERS,
+                         "batched_fp32_iters_per_s": it / (r["total_ms"] / 1000.0),
+                         "batched_device_ms": r["total_ms"],
+                         "plain_fp64_iters_per_s": pit / pw,
+                         "ratio": (it / (r["total_ms"] / 1000.0)) / (pit / pw)}
+    sG = [G[k] for k in small]
+    sp = [probs[k] for k in small]
+    o = spock.opts(precision=32, tol=TOL, max_iters=MAX_ITERS)
+    b = spock.Batch(sG, precision=32)
+    r = b.solve([p.x0 for p in sp], o)
+    b.close()
+    conv = sum(1 for i in r["info"] if i["status"] == 0)
+    pw, pc, _ = _plain_fp64(spock, sG, sp, range(0, len(sp), 8), MAX_ITERS, TOL)
+    res["to_tol"] = {"problems": f"the {SMALL_COUNT} problems of the draw with the fewest nodes "
+                                 f"({sum(len(p.anc) for p in sp)} nodes)",
+                     "tol": TOL, "max_iters": MAX_ITERS,
+                     "batched_fp32_solves_per_s": conv / (r["total_ms"] / 1000.0), "converged": conv,
+                     "batched_device_ms": r["total_ms"],
+                     "plain_fp64_solves_per_s": pc / pw, "plain_converged": pc,
+                     "plain_problems": len(range(0, len(sp), 8)),
+                     "ratio": (conv / (r["total_ms"] / 1000.0)) / max(pc / pw, 1e-12)}
+    return res
+
+
+def bench_serving(spock, probs, G, rate=2000.0, seconds=0.2, seed=5):
+    """MPC serving on the SMALL_COUNT smallest plants: Poisson arrivals at
+    `rate` for `seconds`; a request carries the plant's next state (x1 = A x0 +
+    B u0 at a child drawn by its probability, plus N(0, 0.01 I) noise, clipped
+    into the state box) and is warm-started from the plant's resident iterate.
+    Latency = submission to collection on the host."""
+    import numpy as np
+    o32 = spock.opts(precision=32, tol=TOL, max_iters=MAX_ITERS)
+    srv = spock.Server(G, precision=32, o=o32)
+    x = [p.x0.copy() for p in probs]
+    u = [None] * len(probs)
+    for k, p in enumerate(probs):             # one cold solve per plant first
+        srv.submit(k, x[k], warm=False)
+    for r in srv.drain(600):
+        u[r["plant"]] = r["u0"]
+    rng = np.random.default_rng(seed)
+
+    def next_state(k):
+        p = probs[k]
+        ch = [c for c in range(1, len(p.anc)) if p.anc[c] == 0]
+        pr = np.array([p.prob[c] for c in ch])
+        c = ch[int(rng.choice(len(ch), p=pr / pr.sum()))]
+        x1 = p.A[c - 1] @ x[k] + p.B[c - 1] @ u[k] + p.c[c - 1]
+        return np.clip(x1 + 0.1 * rng.standard_normal(p.nx), -4.5, 4.5)
+
+    got, sub = [], 0
+    t0 = time.time()
+    t_next = t0
+    while time.time() - t0 < seconds:
+        now = time.time()
+        while t_next <= now:
+            k = int(rng.integers(0, len(probs)))
+            x[k] = next_state(k)
+            srv.submit(k, x[k], warm=True)
+            sub += 1
+            t_next += rng.exponential(1.0 / rate)
+        for r in srv.poll():
+            got.append(r)
+            u[r["plant"]] = r["u0"]
+    got += srv.drain(600)
+    wall = time.time() - t0
+    srv.close()
+    lat = np.array([r["latency_ms"] for r in got])
+    dev = np.array([r["device_ms"] for r in got])
+    conv = sum(1 for r in got if r["status"] == 0)
+    # the plain FP64 method, one warm-started request at a time on a sample of plants
+    pl = []
+    for k in range(0, len(probs), 16):
+        t = time.time()
+        G[k].solve(x[k], spock.opts(precision=64, tol=TOL, max_iters=MAX_ITERS, warm_start=True,
+                                     fp64_check=False))
+        pl.append(1000 * (time.time() - t))
+    return {"plants": f"the {SMALL_COUNT} problems of the draw with the fewest nodes",
+            "arrival_rate_per_s": rate, "arrival_seconds": seconds, "submitted": sub, "completed": len(got),
+            "converged": conv, "solves_per_s": len(got) / wall,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "device_ms_p50": float(np.percentile(dev, 50)), "device_ms_p99": float(np.percentile(dev, 99)),
+            "plain_fp64_solve_ms_p50": float(np.percentile(pl, 50)),
+            "plain_fp64_solve_ms_p99": float(np.percentile(pl, 99)),
+            "note": "plain = the single-problem FP64 method on one warm-started request at a time "
+                    "(solve time, no queueing)"}
+
+
 def run_ours(args, rank, world, local_rank, dist):
+    # the batched draw is generated before this process touches the GPU
+    bprobs = batch_draw() if (not args.no_batch and rank == 0) else None
     import torch
 
     from paper_2505_12078_b300 import spock, synth
@@ -265,6 +401,12 @@ def run_ours(args, rank, world, local_rank, dist):
            "time_to_tol_ms": statistics.mean(e2e_ms)}
     launches_per_step = 3 + (2 if prec == 32 else 0)   # x0 scaling, solve, unscale (+ FP64 check)
     cpu = cpu_baseline(p) if world == 1 else None
+    batched = serving = None
+    if bprobs is not None:
+        bG = [spock.Problem(q) for q in bprobs]
+        small = sorted(range(len(bprobs)), key=lambda k: (len(bprobs[k].anc), k))[:SMALL_COUNT]
+        batched = bench_batched(spock, bprobs, bG, small)
+        serving = bench_serving(spock, [bprobs[k] for k in small], [bG[k] for k in small])
     line = {"metric": METRIC, "value": value * 1.0, "unit": "iter/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -279,7 +421,8 @@ def run_ours(args, rank, world, local_rank, dist):
                        "l2": "flushed (256 MB write) before every step",
                        "parallelism": f"replicas x{world}"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "fp64": fp64}
+            "roofline": roofline, "cpu_baseline": cpu, "fp64": fp64,
+            "batched": batched, "serving": serving}
     print(json.dumps(line), flush=True)
 
 
@@ -290,6 +433,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="run one solve of this many SPOCK iterations and exit (for ncu captures)")
     args = ap.parse_args()

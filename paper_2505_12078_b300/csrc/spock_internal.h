@@ -128,6 +128,12 @@ struct ServeCtl {
   volatile int stop;         // host: leave now
   int pad;
 };
+struct ServeDev {             // device-side state of the serving launch
+  long long head;              // requests claimed
+  unsigned long long last_ns;  // global timer at the last claim or completion
+  int busy;                    // CTAs solving a request
+  int pad;
+};
 template <class T>
 struct ServeMeta {           // per plant: what a request needs beyond Prob / SolveBufs
   int nx, nu;

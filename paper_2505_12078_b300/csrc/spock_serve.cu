@@ -17,10 +17,10 @@
 namespace spock {
 
 cudaError_t launch_serve_f1(const Prob<float>*, const SolveBufs<float>*, const int*, const ServeMeta<float>*,
-                            const SolveOpts&, const ServeReq*, ServeRes*, int, ServeCtl*, long long*,
+                            const SolveOpts&, const ServeReq*, ServeRes*, int, ServeCtl*, ServeDev*,
                             unsigned long long, size_t, int, cudaStream_t);
 cudaError_t launch_serve_d2(const Prob<double>*, const SolveBufs<double>*, const int*, const ServeMeta<double>*,
-                            const SolveOpts&, const ServeReq*, ServeRes*, int, ServeCtl*, long long*,
+                            const SolveOpts&, const ServeReq*, ServeRes*, int, ServeCtl*, ServeDev*,
                             unsigned long long, size_t, int, cudaStream_t);
 int serve_grid_f1(size_t, int*);
 int serve_grid_d2(size_t, int*);
@@ -52,7 +52,7 @@ struct spock_server {
   DevMem mem;
   void *d_probs = nullptr, *d_bufs = nullptr, *d_meta = nullptr;
   int* d_tw = nullptr;
-  long long* d_head = nullptr;
+  ServeDev* d_dev = nullptr;
   ServeReq *h_ring = nullptr, *d_ring = nullptr;
   ServeRes *h_res = nullptr, *d_res = nullptr;
   ServeCtl *h_ctl = nullptr, *d_ctl = nullptr;
@@ -128,13 +128,13 @@ int serve_init(spock_server* s) {
   s->d_bufs = m.alloc<SolveBufs<T>>(n);
   s->d_meta = m.alloc<ServeMeta<T>>(n);
   s->d_tw = m.alloc<int>(n);
-  s->d_head = m.alloc<long long>(1);
+  s->d_dev = m.alloc<ServeDev>(1);
   if (m.failed) return SPOCK_ENOMEM;
   if (cudaMemcpy(s->d_probs, P.data(), sizeof(Prob<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_bufs, B.data(), sizeof(SolveBufs<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_meta, M.data(), sizeof(ServeMeta<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_tw, tw.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(s->d_head, 0, sizeof(long long)) != cudaSuccess)
+      cudaMemset(s->d_dev, 0, sizeof(ServeDev)) != cudaSuccess)
     return SPOCK_EDEVICE;
   s->smem = smem;
   int g = 0;
@@ -149,11 +149,11 @@ cudaError_t relaunch(spock_server* s) {
   if constexpr (sizeof(T) == 8)
     return launch_serve_d2((const Prob<double>*)s->d_probs, (const SolveBufs<double>*)s->d_bufs, s->d_tw,
                            (const ServeMeta<double>*)s->d_meta, s->so, s->d_ring, s->d_res, s->cap, s->d_ctl,
-                           s->d_head, kIdleNs, s->smem, s->grid, s->stream);
+                           s->d_dev, kIdleNs, s->smem, s->grid, s->stream);
   else
     return launch_serve_f1((const Prob<float>*)s->d_probs, (const SolveBufs<float>*)s->d_bufs, s->d_tw,
                            (const ServeMeta<float>*)s->d_meta, s->so, s->d_ring, s->d_res, s->cap, s->d_ctl,
-                           s->d_head, kIdleNs, s->smem, s->grid, s->stream);
+                           s->d_dev, kIdleNs, s->smem, s->grid, s->stream);
 }
 
 // the persistent launch is running, or started (it leaves after kIdleNs idle)

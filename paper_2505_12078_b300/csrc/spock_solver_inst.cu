@@ -35,9 +35,9 @@ int SPOCK_CAT(batch_grid_, SPOCK_SUFFIX)(size_t smem, int* out) {
 cudaError_t SPOCK_CAT(launch_serve_, SPOCK_SUFFIX)(const Prob<SPOCK_T>* probs, const SolveBufs<SPOCK_T>* bufs,
                                                     const int* tws, const ServeMeta<SPOCK_T>* meta,
                                                     const SolveOpts& o, const ServeReq* ring, ServeRes* res, int cap,
-                                                    ServeCtl* ctl, long long* head, unsigned long long idle_ns,
+                                                    ServeCtl* ctl, ServeDev* dev, unsigned long long idle_ns,
                                                     size_t smem, int grid, cudaStream_t s) {
-  return launch_serve_ch<SPOCK_T, SPOCK_CH>(probs, bufs, tws, meta, o, ring, res, cap, ctl, head, idle_ns, smem,
+  return launch_serve_ch<SPOCK_T, SPOCK_CH>(probs, bufs, tws, meta, o, ring, res, cap, ctl, dev, idle_ns, smem,
                                             grid, s);
 }
 int SPOCK_CAT(serve_grid_, SPOCK_SUFFIX)(size_t smem, int* out) {

@@ -1464,7 +1464,9 @@ __global__ void __launch_bounds__(256, 1)
 // start as soon as a CTA is free. Each request runs alone in its CTA (barriers
 // and reductions inside it): its result does not depend on the other requests.
 // Leaves when ctl->stop is raised or after idle_ns without a request (the host
-// relaunches it on the next submission).
+// relaunches it on the next submission). The grid leaves together: a CTA
+// leaves only when no CTA is solving and no request was claimed for idle_ns,
+// so a request published later never finds only a few CTAs alive.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ long long ld_acquire_sys(const volatile long long* p) {
   long long v;
@@ -1476,7 +1478,7 @@ template <class T, int CH>
 __global__ void __launch_bounds__(256, 1)
     k_serve(const Prob<T>* __restrict__ probs, const SolveBufs<T>* __restrict__ bufs,
             const int* __restrict__ tws, const ServeMeta<T>* __restrict__ meta, SolveOpts o,
-            const ServeReq* ring, ServeRes* res, int cap, ServeCtl* ctl, long long* head,
+            const ServeReq* ring, ServeRes* res, int cap, ServeCtl* ctl, ServeDev* dev,
             unsigned long long idle_ns) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(16) unsigned char s_prob[sizeof(Prob<T>)];
@@ -1497,17 +1499,22 @@ __global__ void __launch_bounds__(256, 1)
       const uint64_t t0 = global_ns();
       for (;;) {
         if (ctl->stop) break;
-        const long long h = *reinterpret_cast<volatile long long*>(head);
+        const long long h = *reinterpret_cast<volatile long long*>(&dev->head);
         const long long tl = ld_acquire_sys(&ctl->tail);
         if (h < tl) {
-          if (atomicCAS(reinterpret_cast<unsigned long long*>(head), (unsigned long long)h,
+          if (atomicCAS(reinterpret_cast<unsigned long long*>(&dev->head), (unsigned long long)h,
                         (unsigned long long)(h + 1)) == (unsigned long long)h) {
             q = h;
+            atomicAdd(&dev->busy, 1);
+            atomicMax(&dev->last_ns, (unsigned long long)global_ns());
             break;
           }
           continue;
         }
-        if (global_ns() - t0 > idle_ns) break;
+        const uint64_t now = global_ns();
+        const unsigned long long last = *reinterpret_cast<volatile unsigned long long*>(&dev->last_ns);
+        const int busy = *reinterpret_cast<volatile int*>(&dev->busy);
+        if (busy == 0 && now - (last > t0 ? last : t0) > idle_ns) break;
         __nanosleep(2000);
       }
       s_q = q;
@@ -1566,6 +1573,8 @@ __global__ void __launch_bounds__(256, 1)
       __threadfence_system();
       rs->done = 1;
       __threadfence_system();
+      atomicMax(&dev->last_ns, (unsigned long long)global_ns());
+      atomicSub(&dev->busy, 1);
     }
   }
 }
@@ -1573,10 +1582,10 @@ __global__ void __launch_bounds__(256, 1)
 template <class T, int CH>
 cudaError_t launch_serve_ch(const Prob<T>* probs, const SolveBufs<T>* bufs, const int* tws, const ServeMeta<T>* meta,
                             const SolveOpts& o, const ServeReq* ring, ServeRes* res, int cap, ServeCtl* ctl,
-                            long long* head, unsigned long long idle_ns, size_t smem, int grid, cudaStream_t s) {
+                            ServeDev* dev, unsigned long long idle_ns, size_t smem, int grid, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_serve<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_serve<T, CH><<<grid, 256, smem, s>>>(probs, bufs, tws, meta, o, ring, res, cap, ctl, head, idle_ns);
+  k_serve<T, CH><<<grid, 256, smem, s>>>(probs, bufs, tws, meta, o, ring, res, cap, ctl, dev, idle_ns);
   return cudaGetLastError();
 }
 

@@ -111,10 +111,9 @@ def _spectral_rescale(G: np.ndarray, rho: float) -> np.ndarray:
 
 def _dyn_identity_plus(rng, n_edges, nx, nu):
     """A = I + 0.1 G, G ~ N(0,1) rescaled to spectral radius 1.05; B ~ N(0,1)/sqrt(nu)."""
-    A = np.empty((n_edges, nx, nx))
-    for e in range(n_edges):
-        G = _spectral_rescale(rng.standard_normal((nx, nx)), 1.05)
-        A[e] = np.eye(nx) + 0.1 * G
+    G = rng.standard_normal((n_edges, nx, nx))          # the same draws, edge after edge
+    r = np.max(np.abs(np.linalg.eigvals(G)), axis=-1)   # spectral radius of every G at once
+    A = np.eye(nx) + 0.1 * G * (1.05 / r)[:, None, None]
     B = rng.standard_normal((n_edges, nx, nu)) / math.sqrt(nu)
     return A, B
 
