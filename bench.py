@@ -304,6 +304,17 @@ def bench_serving(spock, probs, G, rate=2000.0, seconds=0.2, seed=5):
                     "(solve time, no queueing)"}
 
 
+def combine_ranks(dist, total_ms, iters, device):
+    """Replicas: the slowest rank's time and the iterations of all ranks."""
+    import torch
+    t = torch.tensor([total_ms, float(iters)], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    n = t[1:].clone()
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), int(n.item())
+
+
 def run_ours(args, rank, world, local_rank, dist):
     # the batched draw is generated before this process touches the GPU
     bprobs = batch_draw() if (not args.no_batch and rank == 0) else None
@@ -350,11 +361,7 @@ def run_ours(args, rank, world, local_rank, dist):
     total_ms = sum(times)
     iters = sum(i["iters"] for i in infos)
     if dist:
-        t = torch.tensor([total_ms, float(iters)], dtype=torch.float64, device="cuda")
-        tmax = t[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, iters = float(tmax.item()), int(t[1].item())
+        total_ms, iters = combine_ranks(dist, total_ms, iters, "cuda")
     if rank != 0:
         return
     value = iters / (total_ms / 1000.0)
