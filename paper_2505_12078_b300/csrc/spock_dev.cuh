@@ -281,16 +281,18 @@ struct RedAcc {
     v[R_ZZ] = fma(r, r, v[R_ZZ]);
     v[R_ZD] = fma(r, old - ref, v[R_ZD]);
   }
-  // eta element: old, new, ref eta values and (L z) of old, new, ref
-  __device__ __forceinline__ void eta(T eo, T en, T er, T lo, T ln, T lr) {
+  // eta element: old, new, ref eta values, lrz = L(z_old - z_new) and
+  // lod = L(z_old - z_ref) of the element's row (L applied to the differences,
+  // not differences of L applied: near convergence z_old and z_new agree to
+  // many digits and the difference of two rounded products would be noise)
+  __device__ __forceinline__ void eta(T eo, T en, T er, T lrz, T lod) {
     const T r = eo - en;
-    const T lrz = lo - ln;
     v[R_MAX] = max(v[R_MAX], fabs(r));
     v[R_EE] = fma(r, r, v[R_EE]);
     v[R_ELZ] = fma(r, lrz, v[R_ELZ]);
     v[R_ED] = fma(r, eo - er, v[R_ED]);
     v[R_LZD] = fma(lrz, eo - er, v[R_LZD]);
-    v[R_ELD] = fma(r, lo - lr, v[R_ELD]);
+    v[R_ELD] = fma(r, lod, v[R_ELD]);
   }
 };
 

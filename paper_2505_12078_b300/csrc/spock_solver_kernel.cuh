@@ -576,32 +576,35 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     const T p = (e < 2 * m) ? max(w, T(0)) : w;
     const T en = eb - al * p;
     stc(eo + ye + e, en);
-    ra.eta(eo_, en, er ? ldc(er + ye + e) : eo_, Lo, Ln, Lr);
+    ra.eta(eo_, en, er ? ldc(er + ye + e) : eo_, Lo - Ln, Lo - Lr);
   }
   // s part: s^i - b'y^i in R_+
   {
-    T bo = 0, bn = 0, br = 0;
+    T bo = 0, bn = 0, bd = 0, brd = 0;   // b'y of old and new, b'(y_old - y_new), b'(y_old - y_ref)
     for (int k = lane; k < m; k += 32) {
       const T p = P.prob[c0 + k];
-      const T o = ldc(z + yo + k);
+      const T o = ldc(z + yo + k), nn = ldc(vout + yo + k);
       bo += p * o;
-      bn += p * ldc(vout + yo + k);
-      br += p * refv(vref, yo + k, o);
+      bn += p * nn;
+      bd += p * (o - nn);
+      brd += p * (o - refv(vref, yo + k, o));
     }
-    bo = warp_sum(bo); bn = warp_sum(bn); br = warp_sum(br);
+    bo = warp_sum(bo); bn = warp_sum(bn); bd = warp_sum(bd); brd = warp_sum(brd);
     if (lane == 0) {
       const long long is = (i == 0) ? 0 : P.o_s + i - 1;
       const T yo3 = ldc(z + yo + 2 * m);
       const T so = ldc(z + is);
+      const T sn = ldc(vout + is), yn3 = ldc(vout + yo + 2 * m);
       const T Lo = so - bo - yo3;
-      const T Ln = ldc(vout + is) - bn - ldc(vout + yo + 2 * m);
-      const T Lr = vref ? ldc(vref + is) - br - ldc(vref + yo + 2 * m) : Lo;
+      const T Ln = sn - bn - yn3;
+      const T lrz = (so - sn) - bd - (yo3 - yn3);
+      const T lod = vref ? (so - ldc(vref + is)) - brd - (yo3 - ldc(vref + yo + 2 * m)) : T(0);
       const long long ie = P.e_s + i;
       const T eo_ = ldc(eta + ie);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
       const T en = eb - al * max(eb / al, T(0));
       stc(eo + ie, en);
-      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, Lo, Ln, Lr);
+      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, lrz, lod);
     }
   }
   if (P.n_c == 0) return;
@@ -617,8 +620,8 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     } else {
       g = P.gu[e - P.nbx]; idx = uo + (e - P.nbx);
     }
-    const T o = ldc(z + idx);
-    const T Lo = g * o, Ln = g * ldc(vout + idx), Lr = g * refv(vref, idx, o);
+    const T o = ldc(z + idx), nn = ldc(vout + idx);
+    const T Lo = g * o, Ln = g * nn;
     const T eo_ = ldc(eta + ce + e);
     const T eb = eo_ + al * (T(2) * Ln - Lo);
     const T w = eb / al;
@@ -626,7 +629,7 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     const T p = min(max(w, lo), hi);
     const T en = eb - al * p;
     stc(eo + ce + e, en);
-    ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, Lo, Ln, Lr);
+    ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, g * (o - nn), g * (o - refv(vref, idx, o)));
   }
   // ball rows on u
   if (P.has_ball) {
@@ -642,15 +645,15 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     const T sc = (nw > r) ? r / nw : T(1);
     for (int k = lane; k < nu; k += 32) {
       const T g = P.gu[k];
-      const T o = ldc(z + uo + k);
-      const T Lo = g * o, Ln = g * ldc(vout + uo + k), Lr = g * refv(vref, uo + k, o);
+      const T o = ldc(z + uo + k), nn = ldc(vout + uo + k);
+      const T Lo = g * o, Ln = g * nn;
       const long long ie = ce + P.nbox + k;
       const T eo_ = ldc(eta + ie);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
       const T w = eb / al;
       const T en = eb - al * (w * sc);
       stc(eo + ie, en);
-      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, Lo, Ln, Lr);
+      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, g * (o - nn), g * (o - refv(vref, uo + k, o)));
     }
   }
 }
@@ -668,8 +671,8 @@ __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, l
     const int e = lane + 32 * q;
     ebv[q] = 0;
     if (e < dim) {
-      T Lo, Ln, Lr;
-      Lz(e, Lo, Ln, Lr);
+      T Lo, Ln, Ld, Lrd;
+      Lz(e, Lo, Ln, Ld, Lrd);
       const T eb = ldc(eta + ebase + e) + al * (T(2) * Ln - Lo);
       ebv[q] = eb;
       const T ae = (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
@@ -687,8 +690,8 @@ __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, l
   for (int q = 0; q < NE; ++q) {
     const int e = lane + 32 * q;
     if (e < dim) {
-      T Lo, Ln, Lr;
-      Lz(e, Lo, Ln, Lr);
+      T Lo, Ln, Ld, Lrd;
+      Lz(e, Lo, Ln, Ld, Lrd);
       const T eb = ebv[q];
       const T ae = (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
       const T w = eb / al - ae;
@@ -699,7 +702,7 @@ __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, l
       const T en = eb - al * (ae + ps);
       const T eo_ = ldc(eta + ebase + e);
       stc(eo + ebase + e, en);
-      ra.eta(eo_, en, er ? ldc(er + ebase + e) : eo_, Lo, Ln, Lr);
+      ra.eta(eo_, en, er ? ldc(er + ebase + e) : eo_, Ld, Lrd);
     }
   }
 }
@@ -714,7 +717,7 @@ __device__ void eta_soc(const Prob<T>& P, int lane, int c, const T* __restrict__
   const long long it = P.o_tau + c - 1;
   const T* qh = P.qh + (long long)(c - 1) * nx;
   const T* rh = P.rh + (long long)(c - 1) * nu;
-  auto Lz = [&](int e, T& Lo, T& Ln, T& Lr) {
+  auto Lz = [&](int e, T& Lo, T& Ln, T& Ld, T& Lrd) {
     long long idx;
     T g;
     if (e < nx) {
@@ -724,8 +727,8 @@ __device__ void eta_soc(const Prob<T>& P, int lane, int c, const T* __restrict__
     } else {
       g = T(0.5); idx = it;
     }
-    const T o = ldc(z + idx);
-    Lo = g * o; Ln = g * ldc(vout + idx); Lr = g * refv(vref, idx, o);
+    const T o = ldc(z + idx), nn = ldc(vout + idx);
+    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * (o - refv(vref, idx, o));
   };
   soc_block<T, NE>(P, lane, P.W, P.e_q + (long long)(c - 1) * P.W, vin + P.nz, vout + P.nz,
                    vref ? vref + P.nz : nullptr, Lz, ra);
@@ -745,20 +748,20 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
   if (P.nbx) {
     const long long ce = P.e_cN + (long long)jj * P.n_cN;
     for (int e = lane; e < nx; e += 32) {
-      const T g = P.gN[e], o = ldc(z + xo + e);
-      const T Lo = g * o, Ln = g * ldc(vout + xo + e), Lr = g * refv(vref, xo + e, o);
+      const T g = P.gN[e], o = ldc(z + xo + e), nn = ldc(vout + xo + e);
+      const T Lo = g * o, Ln = g * nn;
       const T eo_ = ldc(eta + ce + e);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
       const T w = eb / al;
       const T p = min(max(w, P.boxN_lo[(long long)jj * nx + e]), P.boxN_hi[(long long)jj * nx + e]);
       const T en = eb - al * p;
       stc(eo + ce + e, en);
-      ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, Lo, Ln, Lr);
+      ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, g * (o - nn), g * (o - refv(vref, xo + e, o)));
     }
   }
   const long long is = P.o_s + j - 1;
   const T* qNh = P.qNh + (long long)jj * nx;
-  auto Lz = [&](int e, T& Lo, T& Ln, T& Lr) {
+  auto Lz = [&](int e, T& Lo, T& Ln, T& Ld, T& Lrd) {
     long long idx;
     T g;
     if (e < nx) {
@@ -766,8 +769,8 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
     } else {
       g = T(0.5); idx = is;
     }
-    const T o = ldc(z + idx);
-    Lo = g * o; Ln = g * ldc(vout + idx); Lr = g * refv(vref, idx, o);
+    const T o = ldc(z + idx), nn = ldc(vout + idx);
+    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * (o - refv(vref, idx, o));
   };
   soc_block<T, NE>(P, lane, nx + 2, P.e_qN + (long long)jj * (nx + 2), eta, eo, er, Lz, ra);
 }
