@@ -156,6 +156,13 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.cta = it.cta; P.ldTB = it.ldTB; P.ldTF = it.ldTF; P.ldTK = it.ldTK; P.khB = it.khB; P.khF = it.khF;
   P.nbuf = it.nbuf; P.item_bytes = it.item_bytes; P.qslots = it.qslots; P.ldc = it.ldc;
   P.MBt = it.MBt; P.MFt = it.MFt; P.KTt = it.KTt;
+  P.top_seg = p->d_top_seg; P.bot_seg = p->d_bot_seg;
+  {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    P.seg_flag_off = nsm * 8;
+  }
   P.qh = it.qh; P.rh = it.rh; P.qNh = it.qNh; P.gx = it.gx; P.gu = it.gu; P.gN = it.gN;
   P.box_lo = it.box_lo; P.box_hi = it.box_hi; P.boxN_lo = it.boxN_lo; P.boxN_hi = it.boxN_hi;
   P.ball = it.ball; P.prob = it.prob; P.avar = it.avar; P.x0s = it.x0s;
@@ -324,7 +331,9 @@ int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t 
   if (grid > maxg) grid = maxg;
   if (grid < 1) grid = 1;
   if (cudaMemsetAsync(it.sb.ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return SPOCK_EDEVICE;
-  if (cudaMemsetAsync(it.sb.flags, 0, sizeof(unsigned) * grid, st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (cudaMemsetAsync(it.sb.flags, 0, sizeof(unsigned) * (it.P.seg_flag_off + p->seg_top.size()), st) !=
+      cudaSuccess)
+    return SPOCK_EDEVICE;
   cudaEventRecord(p->ev0, st);
   cudaError_t e = launch_solve<T>(it.P, it.sb, so, p->tw, grid, kThreads, st);
   if (e != cudaSuccess) return SPOCK_EDEVICE;
@@ -365,7 +374,8 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
   const size_t w = (precision == 64) ? 8 : 4;
   size_t off = 0;
   const size_t o_ctl = off;   off += al(sizeof(SolveCtl));
-  const size_t o_flags = off; off += al(maxg * sizeof(unsigned));
+  const size_t nflags = maxg + p->seg_top.size();   // barrier flags, then segment flags
+  const size_t o_flags = off; off += al(nflags * sizeof(unsigned));
   const size_t o_part = off;  off += al(2 * maxg * NRED * sizeof(double));
   const size_t o_q = off;     off += al((size_t)p->n * p->nx * w);
   const size_t o_d = off;     off += al((size_t)p->n_nl * p->nu * w);
@@ -376,7 +386,7 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
   unsigned* flags = reinterpret_cast<unsigned*>(scratch + o_flags);
   // what must start at zero: the control block (barrier state, error word) and the flags
   if (cudaMemsetAsync(ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return SPOCK_EDEVICE;
-  if (cudaMemsetAsync(flags, 0, maxg * sizeof(unsigned), st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (cudaMemsetAsync(flags, 0, nflags * sizeof(unsigned), st) != cudaSuccess) return SPOCK_EDEVICE;
   SolveOpts so{1e300, 0, 1, 2, 1e-10};
   const int teams = (kThreads / 32) / p->tw;
   cudaError_t e;
@@ -442,7 +452,7 @@ int ensure_bufs(spock_problem* p, Iter<T>& it) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   b.partials = m.alloc<double>((long long)2 * nsm * 8 * NRED);
-  b.flags = m.alloc<unsigned>((long long)nsm * 8);
+  b.flags = m.alloc<unsigned>((long long)nsm * 8 + (long long)p->seg_top.size());   // + segment flags
   b.ctl = m.alloc<SolveCtl>(1);
   if (m.failed) return SPOCK_ENOMEM;
   cudaMemset(b.V, 0, nv * sizeof(T));
@@ -574,6 +584,15 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   p->d_anc = up_i(p->anc); p->d_ch_off = up_i(p->ch_off); p->d_yoff = up_i(p->yoff);
   p->d_ynode = up_i(p->ynode); p->d_lvl_off = up_i(p->lvl_off); p->d_seg_top = up_i(p->seg_top);
   p->d_seg_bot = up_i(p->seg_bot); p->d_seg_len = up_i(p->seg_len);
+  {
+    std::vector<int> ts(n, -1), bs(n, -1);
+    for (size_t q = 0; q < p->seg_top.size(); ++q) {
+      ts[p->seg_top[q]] = (int)q;
+      bs[p->seg_bot[q]] = (int)q;
+    }
+    p->d_top_seg = up_i(ts);
+    p->d_bot_seg = up_i(bs);
+  }
   p->d_seg_off = up_i(p->seg_off); p->d_seg_nodes = up_i(p->seg_nodes);
   {
     std::vector<int> info;

@@ -230,7 +230,48 @@ struct CtaState {
   CtaMem mem;
   const Sched* sched;
   int* s_ok;
+  unsigned* seg_flags;   // per segment: 2e when its backward sweep of evaluation e is
+                         // done, 2e + 1 when its forward sweep is (zeroed at launch)
+  unsigned epoch;        // evaluations of T so far in this launch
 };
+
+// Dataflow between the sweeps' levels: a segment's backward sweep waits for
+// the segments headed by its bottom's children, its forward sweep for the
+// segment that ends in its top's parent; both publish a flag when done. The
+// waits point to deeper (backward) or higher (forward) levels, which every CTA
+// sweeps first, so they cannot form a cycle. Thread 0 waits (bounded).
+__device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned e, int* err) {
+  uint64_t t0 = 0;
+  unsigned spins = 0;
+  while (ld_acquire(f) < e) {
+    __nanosleep(32);
+    if ((++spins & 63u) == 0u) {
+      if (ld_relaxed_i(err)) return false;
+      const uint64_t t = global_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > BARRIER_LIMIT_NS) {
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+// after a failed wait: let the copies already issued into the ring land
+// (bounded) before the CTA leaves
+__device__ __forceinline__ void ring_settle(Ring& R, int issued) {
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < issued; ++j) {
+      const int b = R.step(R.head, j);
+      const uint64_t t0 = global_ns();
+      while (!mbar_try_wait(reinterpret_cast<uint64_t*>(__cvta_shared_to_generic(R.bar(b))), (R.par >> b) & 1u) &&
+             global_ns() - t0 < 200000000ull) {
+      }
+    }
+  }
+  __syncthreads();
+}
 
 // dynamic shared memory of the whole-CTA sweeps: the ring, two carry vectors
 // and the child inputs
@@ -315,7 +356,7 @@ __device__ __forceinline__ void ring_prefetch(const Prob<T>& P, Ring& R, const S
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err, const SegRef& g,
-                        int* s_ok, unsigned long long* prof) {
+                        int* s_ok, unsigned long long* prof, unsigned* flags, unsigned eB) {
   constexpr int W = SV<T>::W;
   constexpr unsigned ES = sizeof(T);
   const int nx = P.nx, nu = P.nu, w = nx + nu;
@@ -342,6 +383,21 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   if (issuer)
     for (int j = R.ahead; j < min(R.nbuf - 1, nitems); ++j) b_issue(I, R, g, j, R.step(R.head, j));
   R.ahead = 0;
+  // the children that head other segments must be swept
+  if (t == 0) {
+    bool okw = true;
+    for (int c = g.c0; c < g.c1 && okw; ++c) {
+      const int ts = P.top_seg[c];
+      if (ts >= 0) okw = flag_wait(flags + ts, eB, err);
+    }
+    *s_ok = okw ? 1 : 0;
+  }
+  __syncthreads();
+  if (!*s_ok) {
+    ring_settle(R, min(R.nbuf - 1, nitems));
+    ring = R;
+    return false;
+  }
   // h/e of the output node of the next two epilogues
   auto pre_of = [&](int node) -> T {
     if (!has_col || half) return T(0);
@@ -412,6 +468,10 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
     prof[8] += (unsigned long long)c_hand;
     prof[9] += (unsigned long long)c_mv;
   }
+  if (ok && t == 0) {   // q and d of the segment's nodes are written (CTA barrier above)
+    __threadfence();
+    st_release(flags + g.s, eB);
+  }
   R.head = b;
   ring = R;
   return ok;
@@ -425,7 +485,8 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err, const SegRef& g,
-                        T* __restrict__ vout, int* s_ok, unsigned long long* prof) {
+                        T* __restrict__ vout, int* s_ok, unsigned long long* prof, unsigned* flags,
+                        unsigned eF) {
   constexpr int W = SV<T>::W;
   constexpr unsigned ES = sizeof(T);
   const int nx = P.nx, nu = P.nu, w = nx + nu;
@@ -454,6 +515,22 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   if (issuer)
     for (int j = R.ahead; j < min(R.nbuf - 1, nitems); ++j) f_issue(I, R, g, j, R.step(R.head, j));
   R.ahead = 0;
+  // x of the top node comes from the segment that ends in its parent
+  if (t == 0) {
+    bool okw = true;
+    const int top = g.nodes[0];
+    if (top != 0) {
+      const int ps = P.bot_seg[P.anc[top]];
+      if (ps >= 0) okw = flag_wait(flags + ps, eF, err);
+    }
+    *s_ok = okw ? 1 : 0;
+  }
+  __syncthreads();
+  if (!*s_ok) {
+    ring_settle(R, min(R.nbuf - 1, nitems));
+    ring = R;
+    return false;
+  }
   // c_c of item j's child (x columns), d of the next node (chain items), two items ahead
   auto child_of = [&](int j) { return j < len - 1 ? g.nodes[j + 1] : g.c0 + (j - (len - 1)); };
   auto cp_of = [&](int j) -> T {
@@ -524,6 +601,10 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
     c_hand += cc - tc;
     prof[10] += (unsigned long long)c_hand;
     prof[11] += (unsigned long long)c_mv;
+  }
+  if (ok && t == 0) {   // x of the children and u of the nodes are written (CTA barrier above)
+    __threadfence();
+    st_release(flags + g.s, eF);
   }
   R.head = b;
   ring = R;

@@ -62,6 +62,9 @@ struct Prob {
   int item_bytes;        // bytes of one ring buffer (multiple of 128)
   int qslots;            // child inputs of a backward bottom held at once
   int ldc;               // elements of one carry or child-input vector
+  const int* top_seg;  // [n] segment whose top node is i, or -1
+  const int* bot_seg;  // [n] segment whose bottom node is i, or -1
+  int seg_flag_off;    // segment flags start at flags + seg_flag_off (after the barrier flags)
   const T* MBt;  // per non-root c: (nx+nu) columns x ldTB  (MB transposed)
   const T* MFt;  // per non-root c: nx columns x ldTF       (MF transposed)
   const T* KTt;  // per non-leaf i: nu columns x ldTK       (KT transposed)

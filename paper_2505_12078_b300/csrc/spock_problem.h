@@ -71,6 +71,7 @@ struct spock_problem {
   int *d_anc, *d_ch_off, *d_yoff, *d_ynode, *d_lvl_off, *d_seg_top, *d_seg_bot, *d_seg_len,
       *d_seg_off, *d_seg_nodes;
   int4* d_seg_info;
+  int *d_top_seg, *d_bot_seg;   // segment of a top / bottom node (or -1)
   // FP64 offline data kept for inspection
   double *d_P, *d_K, *d_Rt, *d_Abar, *d_Sx, *d_SxN, *d_Su;
   double* d_x0raw;   // unscaled x0 of the operator-level calls

@@ -828,6 +828,7 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
   Team w1;
   w1.tw = 1; w1.id = wid; w1.warp = 0; w1.lane = lane; w1.tid = lane; w1.nth = 32;
   if (P.cta) {
+    ++cs.epoch;
     if (P.n_levels > 0 && seg_count(P, 0, tg, nt) > 0)
       ring_prefetch(P, cs.ring, seg_get(P, *cs.sched, 0, 0, tg, nt), false);
   } else if (pp.on && P.n_levels > 0) {
@@ -852,7 +853,8 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
       const int m = seg_count(P, l, tg, nt);
       for (int k = 0; k < m; ++k) {
         const SegRef sr = seg_get(P, S, l, k, tg, nt);
-        if (!bwd_cta<T>(P, cs.mem, cs.ring, &g.ctl->error, sr, cs.s_ok, g.prof)) return false;
+        if (!bwd_cta<T>(P, cs.mem, cs.ring, &g.ctl->error, sr, cs.s_ok, g.prof, cs.seg_flags, 2u * cs.epoch))
+          return false;
         // first items of this CTA's next segment (this level, a later one, or the first forward one)
         if (k + 1 < m) {
           ring_prefetch(P, cs.ring, seg_get(P, S, l, k + 1, tg, nt), false);
@@ -868,8 +870,8 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
           }
         }
       }
-      if (!grid_sync(g)) return false;
     }
+    // no barrier between levels or before the forward sweep: segment flags order them
   } else {
     T* tb = sv.t_base(tm.id);
     for (int l = 0; l < L; ++l) {
@@ -899,7 +901,9 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
       const int m = seg_count(P, l, tg, nt);
       for (int k = 0; k < m; ++k) {
         const SegRef sr = seg_get(P, S, l, k, tg, nt);
-        if (!fwd_cta<T>(P, cs.mem, cs.ring, &g.ctl->error, sr, vout, cs.s_ok, g.prof)) return false;
+        if (!fwd_cta<T>(P, cs.mem, cs.ring, &g.ctl->error, sr, vout, cs.s_ok, g.prof, cs.seg_flags,
+                        2u * cs.epoch + 1u))
+          return false;
         if (k + 1 < m) {
           ring_prefetch(P, cs.ring, seg_get(P, S, l, k + 1, tg, nt), true);
         } else {
@@ -908,8 +912,8 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
           if (l2 >= 0) ring_prefetch(P, cs.ring, seg_get(P, S, l2, 0, tg, nt), true);
         }
       }
-      if (!grid_sync(g)) return false;
     }
+    if (!grid_sync(g)) return false;   // phase E reads every node's x and u
   } else {
     T* tb = sv.t_base(tm.id);
     for (int l = L - 1; l >= 0; --l) {
@@ -1342,6 +1346,8 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
     sched_build(P, s_sched, tg, nt);
     cs.sched = &s_sched;
     cs.s_ok = &s_cta_ok;
+    cs.seg_flags = B.flags + P.seg_flag_off;
+    cs.epoch = 0;
   }
   SolveCtl* ctl = B.ctl;
   Grid g;
