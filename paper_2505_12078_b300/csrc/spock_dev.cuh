@@ -277,24 +277,26 @@ struct RedAcc {
 #pragma unroll
     for (int i = 0; i < NRED; ++i) v[i] = T(0);
   }
-  // z element: old value, new value, reference value (ref == old when absent)
-  __device__ __forceinline__ void z(T old, T nw, T ref) {
+  // z element: old value, new value, direction value (0 when absent)
+  __device__ __forceinline__ void z(T old, T nw, T dir) {
     const T r = old - nw;
     v[R_MAX] = max(v[R_MAX], fabs(r));
     v[R_ZZ] = fma(r, r, v[R_ZZ]);
-    v[R_ZD] = fma(r, old - ref, v[R_ZD]);
+    v[R_ZD] = fma(r, dir, v[R_ZD]);
   }
-  // eta element: old, new, ref eta values, lrz = L(z_old - z_new) and
-  // lod = L(z_old - z_ref) of the element's row (L applied to the differences,
-  // not differences of L applied: near convergence z_old and z_new agree to
-  // many digits and the difference of two rounded products would be noise)
-  __device__ __forceinline__ void eta(T eo, T en, T er, T lrz, T lod) {
+  // eta element: old and new eta values, the direction's eta value ed,
+  // lrz = L(z_old - z_new) and lod = L(d_z) of the element's row. L is applied
+  // to the differences (not differences of L applied: near convergence z_old
+  // and z_new agree to many digits and the difference of two rounded products
+  // would be noise), and the direction d is read as stored instead of being
+  // recovered as v~ - v.
+  __device__ __forceinline__ void eta(T eo, T en, T ed, T lrz, T lod) {
     const T r = eo - en;
     v[R_MAX] = max(v[R_MAX], fabs(r));
     v[R_EE] = fma(r, r, v[R_EE]);
     v[R_ELZ] = fma(r, lrz, v[R_ELZ]);
-    v[R_ED] = fma(r, eo - er, v[R_ED]);
-    v[R_LZD] = fma(lrz, eo - er, v[R_LZD]);
+    v[R_ED] = fma(r, ed, v[R_ED]);
+    v[R_LZD] = fma(lrz, ed, v[R_LZD]);
     v[R_ELD] = fma(r, lod, v[R_ELD]);
   }
 };

@@ -41,8 +41,8 @@ constexpr int AA_M = 3;
 constexpr double C0 = 0.99, C1 = 0.99, C2 = 0.99, BETA = 0.5, SIGMA = 0.1, LAMBDA = 1.0;
 
 template <class T>
-__device__ __forceinline__ T refv(const T* vref, long long idx, T old) {
-  return vref ? ldc(vref + idx) : old;
+__device__ __forceinline__ T dirv(const T* vdir, long long idx) {
+  return vdir ? ldc(vdir + idx) : T(0);
 }
 
 // phase timer of CTA 0 (thread 0): adds the time since the last mark to slot
@@ -114,10 +114,10 @@ __device__ void s2_block(const Prob<T>& P, int lane, int i, const T* __restrict_
     const int c = c0 + l;
     const T n1 = wy1 - a * lam, n2 = wy2 + lam, nt = wtl + lam, ns = wsl + lam;
     long long idx;
-    idx = yo + l;           { const T o = ldc(z + idx); stc(vout + idx, n1); ra.z(o, n1, refv(vref, idx, o)); }
-    idx = yo + m + l;       { const T o = ldc(z + idx); stc(vout + idx, n2); ra.z(o, n2, refv(vref, idx, o)); }
-    idx = P.o_tau + c - 1;  { const T o = ldc(z + idx); stc(vout + idx, nt); ra.z(o, nt, refv(vref, idx, o)); }
-    idx = P.o_s + c - 1;    { const T o = ldc(z + idx); stc(vout + idx, ns); ra.z(o, ns, refv(vref, idx, o)); }
+    idx = yo + l;           { const T o = ldc(z + idx); stc(vout + idx, n1); ra.z(o, n1, dirv(vref, idx)); }
+    idx = yo + m + l;       { const T o = ldc(z + idx); stc(vout + idx, n2); ra.z(o, n2, dirv(vref, idx)); }
+    idx = P.o_tau + c - 1;  { const T o = ldc(z + idx); stc(vout + idx, nt); ra.z(o, nt, dirv(vref, idx)); }
+    idx = P.o_s + c - 1;    { const T o = ldc(z + idx); stc(vout + idx, ns); ra.z(o, ns, dirv(vref, idx)); }
   }
   sl = warp_sum(sl);
   if (lane == 0) {
@@ -125,12 +125,12 @@ __device__ void s2_block(const Prob<T>& P, int lane, int i, const T* __restrict_
     const T n3 = y3 - sl;
     const T o = ldc(z + idx);
     stc(vout + idx, n3);
-    ra.z(o, n3, refv(vref, idx, o));
+    ra.z(o, n3, dirv(vref, idx));
     if (i == 0) {   // s0 <- s0 - alpha (eta_s^0) - alpha
       const T o0 = ldc(z);
       const T n0 = (o0 - al * eS) - al;
       stc(vout, n0);
-      ra.z(o0, n0, refv(vref, 0, o0));
+      ra.z(o0, n0, dirv(vref, 0));
     }
   }
 }
@@ -548,7 +548,7 @@ __device__ __forceinline__ void z_resid(const T* __restrict__ vin, const T* __re
                                         int lane, RedAcc<T>& ra) {
   for (int k = lane; k < len; k += 32) {
     const T o = ldc(vin + off + k);
-    ra.z(o, ldc(vout + off + k), refv(vref, off + k, o));
+    ra.z(o, ldc(vout + off + k), dirv(vref, off + k));
   }
 }
 
@@ -569,25 +569,25 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
   const long long ye = P.e_y + P.yoff[i];
   // y part: (K^i)* = R^{2m}_+ x R
   for (int e = lane; e < 2 * m + 1; e += 32) {
-    const T Lo = ldc(z + yo + e), Ln = ldc(vout + yo + e), Lr = refv(vref, yo + e, Lo);
+    const T Lo = ldc(z + yo + e), Ln = ldc(vout + yo + e);
     const T eo_ = ldc(eta + ye + e);
     const T eb = eo_ + al * (T(2) * Ln - Lo);
     const T w = eb / al;
     const T p = (e < 2 * m) ? max(w, T(0)) : w;
     const T en = eb - al * p;
     stc(eo + ye + e, en);
-    ra.eta(eo_, en, er ? ldc(er + ye + e) : eo_, Lo - Ln, Lo - Lr);
+    ra.eta(eo_, en, er ? ldc(er + ye + e) : T(0), Lo - Ln, dirv(vref, yo + e));
   }
   // s part: s^i - b'y^i in R_+
   {
-    T bo = 0, bn = 0, bd = 0, brd = 0;   // b'y of old and new, b'(y_old - y_new), b'(y_old - y_ref)
+    T bo = 0, bn = 0, bd = 0, brd = 0;   // b'y of old and new, b'(y_old - y_new), b'(direction y)
     for (int k = lane; k < m; k += 32) {
       const T p = P.prob[c0 + k];
       const T o = ldc(z + yo + k), nn = ldc(vout + yo + k);
       bo += p * o;
       bn += p * nn;
       bd += p * (o - nn);
-      brd += p * (o - refv(vref, yo + k, o));
+      brd += p * dirv(vref, yo + k);
     }
     bo = warp_sum(bo); bn = warp_sum(bn); bd = warp_sum(bd); brd = warp_sum(brd);
     if (lane == 0) {
@@ -598,13 +598,13 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
       const T Lo = so - bo - yo3;
       const T Ln = sn - bn - yn3;
       const T lrz = (so - sn) - bd - (yo3 - yn3);
-      const T lod = vref ? (so - ldc(vref + is)) - brd - (yo3 - ldc(vref + yo + 2 * m)) : T(0);
+      const T lod = vref ? ldc(vref + is) - brd - ldc(vref + yo + 2 * m) : T(0);
       const long long ie = P.e_s + i;
       const T eo_ = ldc(eta + ie);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
       const T en = eb - al * max(eb / al, T(0));
       stc(eo + ie, en);
-      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, lrz, lod);
+      ra.eta(eo_, en, er ? ldc(er + ie) : T(0), lrz, lod);
     }
   }
   if (P.n_c == 0) return;
@@ -629,7 +629,7 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     const T p = min(max(w, lo), hi);
     const T en = eb - al * p;
     stc(eo + ce + e, en);
-    ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, g * (o - nn), g * (o - refv(vref, idx, o)));
+    ra.eta(eo_, en, er ? ldc(er + ce + e) : T(0), g * (o - nn), g * dirv(vref, idx));
   }
   // ball rows on u
   if (P.has_ball) {
@@ -653,7 +653,7 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
       const T w = eb / al;
       const T en = eb - al * (w * sc);
       stc(eo + ie, en);
-      ra.eta(eo_, en, er ? ldc(er + ie) : eo_, g * (o - nn), g * (o - refv(vref, uo + k, o)));
+      ra.eta(eo_, en, er ? ldc(er + ie) : T(0), g * (o - nn), g * dirv(vref, uo + k));
     }
   }
 }
@@ -702,7 +702,7 @@ __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, l
       const T en = eb - al * (ae + ps);
       const T eo_ = ldc(eta + ebase + e);
       stc(eo + ebase + e, en);
-      ra.eta(eo_, en, er ? ldc(er + ebase + e) : eo_, Ld, Lrd);
+      ra.eta(eo_, en, er ? ldc(er + ebase + e) : T(0), Ld, Lrd);
     }
   }
 }
@@ -728,7 +728,7 @@ __device__ void eta_soc(const Prob<T>& P, int lane, int c, const T* __restrict__
       g = T(0.5); idx = it;
     }
     const T o = ldc(z + idx), nn = ldc(vout + idx);
-    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * (o - refv(vref, idx, o));
+    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * dirv(vref, idx);
   };
   soc_block<T, NE>(P, lane, P.W, P.e_q + (long long)(c - 1) * P.W, vin + P.nz, vout + P.nz,
                    vref ? vref + P.nz : nullptr, Lz, ra);
@@ -756,7 +756,7 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
       const T p = min(max(w, P.boxN_lo[(long long)jj * nx + e]), P.boxN_hi[(long long)jj * nx + e]);
       const T en = eb - al * p;
       stc(eo + ce + e, en);
-      ra.eta(eo_, en, er ? ldc(er + ce + e) : eo_, g * (o - nn), g * (o - refv(vref, xo + e, o)));
+      ra.eta(eo_, en, er ? ldc(er + ce + e) : T(0), g * (o - nn), g * dirv(vref, xo + e));
     }
   }
   const long long is = P.o_s + j - 1;
@@ -770,7 +770,7 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
       g = T(0.5); idx = is;
     }
     const T o = ldc(z + idx), nn = ldc(vout + idx);
-    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * (o - refv(vref, idx, o));
+    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * dirv(vref, idx);
   };
   soc_block<T, NE>(P, lane, nx + 2, P.e_qN + (long long)jj * (nx + 2), eta, eo, er, Lz, ra);
 }
@@ -807,7 +807,8 @@ struct Views {
 };
 
 // ---------------------------------------------------------------------------
-// one evaluation of T: v_out = T(v_in); reduction with reference point vref
+// one evaluation of T: v_out = T(v_in); the reductions include the M-inner
+// products of r = v_in - T(v_in) with the direction vref (none when null)
 // ---------------------------------------------------------------------------
 // Not inlined: the driver calls it from six places, and six inlined copies of
 // the whole evaluation overflow the instruction cache.
@@ -1173,7 +1174,7 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
       }
       if (!grid_sync(g)) goto fail;
       pc.mark(ctl, 5);
-      ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
+      ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iVT], buf[iTVT], B.PSI, red, B.partials, ctl, g);
       ++nT;
       if (!ok) goto fail;
       if (omega <= C0 * zeta) {                       // K0
@@ -1199,7 +1200,8 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
           ++nK1;
           break;
         }
-        const double mdot = red[R_ZD] + red[R_ED] - (double)al * red[R_LZD] - (double)al * red[R_ELD];
+        // <r~, v~ - v>_M with v~ - v = tau psi (psi as stored, not recovered by a subtraction)
+        const double mdot = tau * (red[R_ZD] + red[R_ED] - (double)al * red[R_LZD] - (double)al * red[R_ELD]);
         const double rho = om2t - mdot;
         PhaseClock pk;
         pk.start(g.prof);
@@ -1257,7 +1259,7 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
         }
         if (!grid_sync(g)) goto fail;
         pk.mark(ctl, 6);
-        ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iVT], buf[iTVT], buf[iV], red, B.partials, ctl, g);
+        ok = evalT<T, CH>(P, tm, sv, pp, cs, tg, nt, buf[iVT], buf[iTVT], B.PSI, red, B.partials, ctl, g);
         ++nT;
         if (!ok) goto fail;
       }
