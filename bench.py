@@ -216,12 +216,19 @@ def bench_batched(spock, probs, G, small):
     r = b.solve(x0s, o)
     b.close()
     it = sum(i["iters"] for i in r["info"])
+    # algorithmic bytes of the launch (same counting as the single-problem roofline)
+    alg = sum(algorithmic_bytes(g.sizes, i["n_T"], i["iters"], 4)[0] for g, i in zip(G, r["info"]))
+    peak, peak_kind = measured_peak()
+    achieved = alg / (r["total_ms"] / 1000.0) / 1e9
     pw, _, pit = _plain_fp64(spock, G, probs, range(0, len(probs), 8), BATCH_FIXED_ITERS, 0.0)
     res["fixed_work"] = {"iters_per_problem": BATCH_FIXED_ITERS,
                          "batched_fp32_iters_per_s": it / (r["total_ms"] / 1000.0),
                          "batched_device_ms": r["total_ms"],
                          "plain_fp64_iters_per_s": pit / pw,
-                         "ratio": (it / (r["total_ms"] / 1000.0)) / (pit / pw)}
+                         "ratio": (it / (r["total_ms"] / 1000.0)) / (pit / pw),
+                         "roofline": {"bound": "hbm", "kernel": "k_batch (one persistent launch, graph replay)",
+                                      "algorithmic_bytes": alg, "achieved": achieved, "peak": peak,
+                                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind}}
     sG = [G[k] for k in small]
     sp = [probs[k] for k in small]
     o = spock.opts(precision=32, tol=TOL, max_iters=MAX_ITERS)
