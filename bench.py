@@ -201,20 +201,23 @@ def _plain_fp64(spock, G, probs, idx, max_iters, tol, warm=False, x0s=None):
 
 
 def bench_batched(spock, probs, G, small):
-    """Batched FP32 (one persistent graph-captured launch) against the plain
-    single-problem FP64 method (one cooperative launch per problem, the whole
-    GPU each): (1) fixed work, BATCH_FIXED_ITERS SPOCK iterations of every
-    problem of the draw; (2) the SMALL_COUNT smallest problems solved to
-    ||v - T(v)||_inf <= 1e-4. The plain method runs on every 8th problem (its
-    time is linear in the number of problems)."""
+    """Batched FP32 (one persistent graph-captured launch, warps per team from
+    the autotuner) against the plain single-problem FP64 method (one
+    cooperative launch per problem, the whole GPU each): (1) fixed work,
+    BATCH_FIXED_ITERS SPOCK iterations of every problem of the draw; (2) the
+    SMALL_COUNT smallest problems solved to ||v - T(v)||_inf <= 1e-4. The plain
+    method runs on every 8th problem (its time is linear in the number of
+    problems)."""
     res = {"workload": "uneven draw of 512 problems (seed 4): nx~U{4..64}, nu=nx/2, N~U{5..20}, "
                        "b~U{2..4}-way branching at the first k~U{1..4} stages, AV@R~U[0.2,1], box + ball; "
                        f"{sum(len(p.anc) for p in probs)} nodes"}
     o = spock.opts(precision=32, tol=0.0, max_iters=BATCH_FIXED_ITERS)
     b = spock.Batch(G, precision=32)
+    tw = b.autotune(iters=20)                   # warps per team of every problem's sweeps
     x0s = [p.x0 for p in probs]
     r = b.solve(x0s, o)
     b.close()
+    res["autotuned_tw"] = {str(t): int((tw == t).sum()) for t in (1, 2, 4, 8)}
     it = sum(i["iters"] for i in r["info"])
     # algorithmic bytes of the launch (same counting as the single-problem roofline)
     alg = sum(algorithmic_bytes(g.sizes, i["n_T"], i["iters"], 4)[0] for g, i in zip(G, r["info"]))
@@ -233,6 +236,7 @@ def bench_batched(spock, probs, G, small):
     sp = [probs[k] for k in small]
     o = spock.opts(precision=32, tol=TOL, max_iters=MAX_ITERS)
     b = spock.Batch(sG, precision=32)
+    b.autotune(iters=20)
     r = b.solve([p.x0 for p in sp], o)
     b.close()
     conv = sum(1 for i in r["info"] if i["status"] == 0)
