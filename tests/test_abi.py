@@ -94,3 +94,37 @@ def test_invalid_problems_rejected_on_host(lib, case):
     rc, h = _desc_call(p, mutate)
     assert rc in (-1, -6), rc
     assert not h.value
+
+
+def test_batch_and_server_reject_bad_arguments_on_host(lib):
+    """Batch and server creation validate their arguments before any device call."""
+    out = C.c_void_p()
+    assert lib.spock_batch_create(None, 1, 32, C.byref(out)) == -1
+    arr = (C.c_void_p * 1)(None)
+    assert lib.spock_batch_create(arr, 1, 32, C.byref(out)) == -1        # NULL problem
+    assert lib.spock_batch_create(arr, 0, 32, C.byref(out)) == -1        # empty batch
+    assert lib.spock_batch_create(arr, 1, 16, C.byref(out)) == -1        # precision
+    assert lib.spock_batch_create(arr, 1, 32, None) == -1
+    adm = C.c_int()
+    assert lib.spock_server_create(None, 1, 32, None, 16, C.byref(out), C.byref(adm)) == -1
+    assert lib.spock_server_create(arr, 1, 32, None, 16, C.byref(out), C.byref(adm)) == -1
+    assert lib.spock_server_create(arr, 1, 32, None, 0, C.byref(out), C.byref(adm)) == -1
+    assert lib.spock_server_submit(None, 0, None, 0, None) == -1
+    assert lib.spock_server_poll(None, None, 0, None) == -1
+    assert lib.spock_server_outstanding(None) == -1
+    lib.spock_batch_destroy(None)
+    lib.spock_server_destroy(None)
+    assert lib.spock_status_str(2)
+
+
+def test_algorithmic_bytes_counting():
+    """The roofline's byte count on the 31-node problem, by hand: per T the
+    factors MB (nx(nx+nu)) and MF ((nx+nu)nx) of every non-root node and MP
+    (nu(nx+nu)) and KT (nx nu) of every non-leaf node, plus 8 passes over v;
+    per iteration 21 passes over v."""
+    import bench
+    sizes = dict(n=31, n_nonleaf=23, nx=4, nu=2, n_v=878)
+    total, per_T = bench.algorithmic_bytes(sizes, n_T=10, iters=7, word=4)
+    factors = 30 * (4 * 6 + 6 * 4) + 23 * (2 * 6 + 4 * 2)
+    assert per_T == 4 * (factors + 8 * 878)
+    assert total == 10 * per_T + 7 * 4 * 21 * 878
