@@ -490,14 +490,32 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   constexpr int W = SV<T>::W;
   constexpr unsigned ES = sizeof(T);
   const int nx = P.nx, nu = P.nu, w = nx + nu;
-  const int t = threadIdx.x, col = t >> 1, half = t & 1;
-  const bool xcol = col < nx, ucol = (col >= nx) && (col < w);
+  const int t = threadIdx.x;
+  // x columns run over the nx + nu rows of MFt, u columns over the nx rows of
+  // KTt. In FP32, when 4 nx + 2 nu threads fit, an x column gets four threads
+  // (a quarter of its rows each) and a u column two, which evens out the two
+  // critical paths. Otherwise (and in FP64, whose items are bound by the FP64
+  // pipe and whose column layout is tuned for two threads) two threads per
+  // column of either kind.
+  const int XP = (sizeof(T) == 4 && 4 * nx + 2 * nu <= (int)blockDim.x) ? 4 : 2;
+  const int nxt = XP * nx;
+  const bool xcol = t < nxt, ucol = !xcol && t < nxt + 2 * nu;
+  const int col = xcol ? t / XP : (ucol ? nx + ((t - nxt) >> 1) : w);
+  const int part = xcol ? t % XP : ((t - nxt) & 1);
+  const bool lead = part == 0;   // the thread that writes the column's result
   const bool issuer = (t == (int)blockDim.x - 1);
-  // x columns: nx + nu rows of MFt; u columns: nx rows of KTt
-  const int nr = xcol ? w : nx;
-  const int kh = xcol ? P.khF : P.khB;
-  const int r0 = half ? kh : 0;
-  const int r1 = half ? nr : min(kh, nr);
+  int r0 = 0, r1 = 0;
+  if (xcol && XP == 4) {
+    const int kq = ((w + 3) / 4 + W - 1) / W * W;   // rows per quarter, whole 16-byte groups
+    r0 = part * kq;
+    r1 = min(r0 + kq, w);
+  } else if (xcol) {
+    r0 = part ? P.khF : 0;
+    r1 = part ? w : min(P.khF, w);
+  } else if (ucol) {
+    r0 = part ? P.khB : 0;
+    r1 = part ? nx : min(P.khB, nx);
+  }
   const int ng = ((xcol || ucol) && r1 > r0) ? (r1 - r0 + W - 1) / W : 0;
   const unsigned kbytes = (unsigned)(nu * P.ldTK) * ES;
   const unsigned mcol = xcol ? kbytes + (unsigned)(col * P.ldTF + r0) * ES
@@ -534,7 +552,7 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   // c_c of item j's child (x columns), d of the next node (chain items), two items ahead
   auto child_of = [&](int j) { return j < len - 1 ? g.nodes[j + 1] : g.c0 + (j - (len - 1)); };
   auto cp_of = [&](int j) -> T {
-    return (j < nitems && xcol && !half) ? ldr(cvec + (long long)(child_of(j) - 1) * nx + col) : T(0);
+    return (j < nitems && xcol && lead) ? ldr(cvec + (long long)(child_of(j) - 1) * nx + col) : T(0);
   };
   auto dn_of = [&](int j) -> T {   // d of the child of chain item j, element t
     return (j < len - 1 && t < nu) ? ldc(dbuf + (long long)g.nodes[j + 1] * nu + t) : T(0);
@@ -575,7 +593,11 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
     T v = T(0);
     if (ng > 0 && (xcol || kt)) v = tdot<T>(R.buf(b) + mcol, cin + xoff, ng);
     v += __shfl_xor_sync(0xffffffffu, v, 1);
-    if (!half) {
+    {
+      const T v2 = __shfl_xor_sync(0xffffffffu, v, 2);   // groups of four are lane-aligned
+      if (XP == 4 && xcol) v += v2;
+    }
+    if (lead) {
       if (xcol) {
         const T xc = v + cpA;
         stc(vout + o_x + (long long)c * nx + col, xc);
