@@ -11,6 +11,14 @@ Plain, slow, obviously-correct numpy in float64. Every function cites the
 paper passage it follows. Where the paper is silent, garbled or inconsistent
 the reading taken is stated at the function.
 
+Pins (tests/test_oracle_pins.py): every step is checked against something
+other than itself (closed forms, dense KKT solves, LP solves of the risk,
+brute force on tiny trees, invariants). The converged solution of a
+constrained problem with AV@R level below 1 has no closed form: its parity is
+unpinned beyond the invariants that every run satisfies (residual, xi1, xi2
+and the complementarity gap vanish; the nested risk of the returned
+trajectory equals s0).
+
 Variable layout (scaled variables, Sec. 4.3 "Sets" and Sec. 4.4 "Linear
 operator L"). Nodes are in breadth-first order, children contiguous; the
 first n_nl nodes are the non-leaf nodes, the last n_l the leaves.
