@@ -1,0 +1,93 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch
+configuration that bench.py times: the 1012-node nx=50 problem (whole-CTA
+sweeps with the bulk-copy ring) and the ~4096-node tree-shape sweep problems
+(b = 2, 4, 8). One evaluation of T and a fixed SPOCK iteration count are
+compared with the oracle element by element; the converged FP32 solve of the
+large problem, which the oracle cannot run to the end in test time, is
+checked through properties that hold at any size (FP64 residual of the FP32
+iterate, feasibility, agreement with the FP64 solve on the risk value and
+u^0). Tolerances as in test_gpu_parity."""
+import numpy as np
+import pytest
+
+from oracle.spock_oracle import Oracle
+from paper_2505_12078_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2505_12078_b300 import build, spock
+    build.build()
+    spock.load()
+
+
+def _spock():
+    from paper_2505_12078_b300 import spock
+    return spock
+
+
+FULL = {
+    "large_1012": synth.large_raocp,
+    "sweep_b2": lambda: synth.tree_sweep(2),
+    "sweep_b4": lambda: synth.tree_sweep(4),
+    "sweep_b8": lambda: synth.tree_sweep(8),
+}
+
+
+def _relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_one_T(name):
+    p = FULL[name]()
+    o = Oracle(p)
+    g = _spock().Problem(p)
+    g.set_alpha(o.alpha)
+    g.set_x0(p.x0)
+    v = np.random.default_rng(4).standard_normal(o.lay.n_z + o.lay.n_eta)
+    ref = o.T(v)
+    vt = torch.tensor(v, device="cuda")
+    out, _ = g.T(vt)
+    assert _relerr(out.cpu().numpy(), ref) < 1e-11
+    out32, _ = g.T(vt.float())
+    assert _relerr(out32.cpu().numpy(), ref) < 2e-5
+
+
+@pytest.mark.parametrize("name", ["large_1012", "sweep_b4"])
+def test_full_size_spock_fixed_fp64(name):
+    p = FULL[name]()
+    o = Oracle(p)
+    g = _spock().Problem(p)
+    g.set_alpha(o.alpha)
+    iters = 10
+    ref = o.solve(tol=0.0, max_iters=iters, method="spock")
+    res = g.solve(p.x0, _spock().opts(precision=64, tol=0.0, max_iters=iters))
+    kinds = [e[1] for e in ref["events"]]
+    inf = res["info"]
+    assert inf["iters"] == iters and inf["n_T"] == ref["n_T"]
+    assert (inf["n_K0"], inf["n_K1"], inf["n_K2"]) == (kinds.count("K0"), kinds.count("K1"), kinds.count("K2"))
+    assert _relerr(g.get_iterate(64).cpu().numpy(), ref["v"]) < 1e-10
+
+
+def test_full_size_converged_fp32_large():
+    """The benchmark solve itself: FP32 to ||v - T(v)||_inf <= 1e-4."""
+    spock = _spock()
+    p = synth.large_raocp()
+    g = spock.Problem(p)
+    r32 = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=200000))
+    r64 = g.solve(p.x0, spock.opts(precision=64, tol=1e-4, max_iters=200000))
+    assert r32["status"] == 0 and r64["status"] == 0
+    assert r32["info"]["res_inf_fp64"] <= 2e-4
+    # feasibility of the returned trajectory (box 5 on x, box 2 and ball 3 on u)
+    assert np.max(np.abs(r32["x"])) <= 5.0 * (1 + 1e-3)
+    assert np.max(np.abs(r32["u"])) <= 2.0 * (1 + 1e-3)
+    assert np.max(np.linalg.norm(r32["u"], axis=1)) <= 3.0 * (1 + 1e-3)
+    # two approximations of the same optimum, each within the 1e-3 target of it
+    assert abs(r32["risk"] - r64["risk"]) <= 2e-3 * max(1.0, abs(r64["risk"]))
+    assert np.max(np.abs(r32["u"][0] - r64["u"][0])) <= 2e-3 * max(1.0, np.max(np.abs(r64["u"][0])))
