@@ -452,9 +452,27 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="run one batched launch of this many iterations on every 32nd problem of the "
+                         "uneven draw and exit (for ncu captures)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="run one solve of this many SPOCK iterations and exit (for ncu captures)")
     args = ap.parse_args()
+    if args.profile_batch:
+        from paper_2505_12078_b300 import spock, synth
+        spock.load()
+        specs = synth.batch_specs(BATCH_COUNT, seed=4)
+        probs = [synth.batch_problem(specs[i], i) for i in range(0, BATCH_COUNT, 32)]
+        G = [spock.Problem(q) for q in probs]
+        b = spock.Batch(G, precision=32)
+        r = b.solve([q.x0 for q in probs], spock.opts(precision=32, tol=0.0, max_iters=args.profile_batch))
+        it = sum(i["iters"] for i in r["info"])
+        nT = sum(i["n_T"] for i in r["info"])
+        alg = sum(algorithmic_bytes(g.sizes, i["n_T"], i["iters"], 4)[0] for g, i in zip(G, r["info"]))
+        print(json.dumps({"problems": len(probs), "nodes": sum(len(q.anc) for q in probs), "iters": it,
+                          "n_T": nT, "algorithmic_bytes": alg, "device_ms": r["total_ms"],
+                          "source_hash": solver_source_hash()}))
+        return
     if args.profile_iters:
         import torch
         from paper_2505_12078_b300 import spock, synth
