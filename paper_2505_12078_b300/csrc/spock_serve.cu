@@ -282,7 +282,6 @@ int spock_server_submit(spock_server* s, int plant, const double* x0, int warm_s
 int spock_server_poll(spock_server* s, spock_serve_result* out, int max_out, int* n_out) {
   if (!s || (max_out > 0 && !out)) return SPOCK_EINVAL;
   int n = 0;
-  std::vector<int> freed;
   for (int slot = 0; slot < s->cap && n < max_out; ++slot) {
     if (!s->slot_busy[slot] || !s->h_res[slot].done) continue;
     std::atomic_thread_fence(std::memory_order_acquire);
@@ -304,20 +303,16 @@ int spock_server_poll(spock_server* s, spock_serve_result* out, int max_out, int
     s->slot_busy[slot] = 0;
     s->plant_busy[p] = 0;
     s->outstanding -= 1;
-    freed.push_back(p);
   }
   // requests waiting for a plant that is free now
-  bool pushed = false;
   for (int p = 0; p < s->count; ++p) {
     if (s->plant_busy[p] || s->queue[p].empty()) continue;
     if (!publish(s, p, s->queue[p].front())) break;
     s->queue[p].pop_front();
-    pushed = true;
   }
   if (n_out) *n_out = n;
-  if (pushed || (s->outstanding > 0 && !s->launched)) return ensure_running(s);
-  if (s->outstanding > 0) return ensure_running(s);
-  return SPOCK_OK;
+  // work left: make sure the persistent launch is there to take it
+  return s->outstanding > 0 ? ensure_running(s) : SPOCK_OK;
 }
 
 long long spock_server_outstanding(const spock_server* s) { return s ? s->outstanding : -1; }
