@@ -41,14 +41,18 @@ WORKLOAD = ("large_raocp: nx=50 nu=25 N=15, 3-way branching at stages 0-3 (81 sc
 TOL = 1e-4
 
 
+KSOLVE_SOURCES = ("spock_dev.cuh", "spock_internal.h", "spock_cta.cuh", "spock_solver_kernel.cuh",
+                  "spock_solver_inst.cu")
+
+
 def solver_source_hash():
-    """Hash of the CUDA sources: DRAM counters recorded for another build are not used."""
+    """Hash of the sources that define the solve kernel: DRAM counters recorded
+    for another build of it are not used."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2505_12078_b300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, name), "rb").read())
+    for name in KSOLVE_SOURCES:
+        h.update(open(os.path.join(d, name), "rb").read())
     return h.hexdigest()[:16]
 
 
