@@ -1,7 +1,10 @@
 // spock_solver_kernel.cuh -- the SPOCK iteration as one persistent cooperative kernel.
 //
 // One evaluation of the Chambolle-Pock operator T (Eq. chambolle-pock-operator)
-// is four phases separated by grid barriers:
+// is four phases. Grid barriers follow P and F, and an all-reduce ends E; the
+// tree levels inside B and F are ordered by per-segment flags in the
+// whole-CTA sweeps (spock_cta.cuh) and by a barrier per level in the team
+// sweeps:
 //
 //  P (one warp per node): w = z - alpha L* eta for the node's own blocks
 //    (sibling sums of L* read the children's cost blocks), the s0 update
@@ -22,11 +25,16 @@
 //    with the S3 projections (cones, boxes, ball, translated SOCs).
 // Every phase also accumulates the reductions of r = v - T(v): max|r|,
 // ||r_z||^2, ||r_eta||^2, <r_eta, L r_z>, and the M-inner product with a
-// reference point; they are combined by one group reduction at the end.
+// direction (the SuperMann candidate's psi); they are combined by one group
+// reduction at the end.
 //
 // The SuperMann driver (Alg. 4) with Anderson directions (Alg. 3, m = 3) runs
 // redundantly on every CTA from the group-reduced scalars, so all CTAs take
 // the same branch; there is no host round trip per iteration.
+//
+// Three kernels run that iteration: k_solve (one problem, the whole grid),
+// k_batch (many problems: gangs of CTAs for large ones, single CTAs for the
+// rest) and k_serve (requests claimed from a ring in mapped host memory).
 #include <cuda_runtime.h>
 #include <math.h>
 
