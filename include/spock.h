@@ -286,14 +286,16 @@ typedef struct spock_serve_result {
     double latency_ms;    /* host time from submission to the poll that saw the result */
 } spock_serve_result;
 
-/* Admit plants in the given order while their solve buffers fit in free device
- * memory (256 MB kept free); *admitted (may be NULL) = how many. opts as for
- * spock_solve (precision must equal `precision`; fp64_check ignored);
- * ring_slots >= 1 bounds the requests on the device at once. Returns
- * SPOCK_PARTIAL if some plants were refused, SPOCK_ENOMEM if none fit. The
- * plants must outlive the server and not be solved on their own meanwhile. */
+/* Admit plants in the given order while their solve buffers fit in the
+ * admission budget: mem_budget bytes if mem_budget > 0, else the free device
+ * memory less 256 MB (plants whose buffers already exist cost nothing);
+ * *admitted (may be NULL) = how many. opts as for spock_solve (precision must
+ * equal `precision`; fp64_check ignored); ring_slots >= 1 bounds the requests
+ * on the device at once. Returns SPOCK_PARTIAL if some plants were refused,
+ * SPOCK_ENOMEM if none fit. The plants must outlive the server and not be
+ * solved on their own meanwhile. */
 int spock_server_create(spock_problem* const* plants, int count, int precision, const spock_solve_opts* opts,
-                        int ring_slots, spock_server** out, int* admitted);
+                        int ring_slots, long long mem_budget, spock_server** out, int* admitted);
 
 /* Queue a request: x0 (host) [nx of the plant], unscaled; warm_start = 1
  * starts from the plant's last iterate. *id_out (may be NULL) = request id.

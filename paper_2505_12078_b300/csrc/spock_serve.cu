@@ -191,7 +191,7 @@ bool publish(spock_server* s, int p, const Pending& r) {
 extern "C" {
 
 int spock_server_create(spock_problem* const* plants, int count, int precision, const spock_solve_opts* opts,
-                        int ring_slots, spock_server** out, int* admitted) {
+                        int ring_slots, long long mem_budget, spock_server** out, int* admitted) {
   if (!out) return SPOCK_EINVAL;
   *out = nullptr;
   if (!plants || count < 1 || (precision != 32 && precision != 64) || ring_slots < 1) return SPOCK_EINVAL;
@@ -213,10 +213,14 @@ int spock_server_create(spock_problem* const* plants, int count, int precision, 
   s->so.tol = o.tol; s->so.max_iters = o.max_iters; s->so.max_backtracks = o.max_backtracks;
   s->so.method = o.method; s->so.rank_tol = precision == 64 ? 1e-10 : 1e-5;
   // admission by device memory: plants in order while their solve buffers fit
-  // (keeping 256 MB free for the launch and the ring)
-  size_t fr = 0, tot = 0;
-  cudaMemGetInfo(&fr, &tot);
-  long long room = (long long)fr - (256ll << 20);
+  // in the budget (by default the free memory, keeping 256 MB for the launch
+  // and the ring)
+  long long room = mem_budget;
+  if (room <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    room = (long long)fr - (256ll << 20);
+  }
   int adm = 0;
   for (int i = 0; i < count; ++i) {
     const Iter<double>& f = plants[i]->f64;

@@ -122,7 +122,7 @@ def load(path: str = LIB_PATH):
     lib.spock_batch_autotune.argtypes = [vp, C.c_int, _ip]
     lib.spock_batch_solve.argtypes = [vp, _dp, C.POINTER(SolveOpts), _dp, _dp, _dp, C.POINTER(BatchInfo), _dp]
     lib.spock_server_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(SolveOpts), C.c_int,
-                                        C.POINTER(vp), _ip]
+                                        C.c_longlong, C.POINTER(vp), _ip]
     lib.spock_server_submit.argtypes = [vp, C.c_int, _dp, C.c_int, C.POINTER(C.c_longlong)]
     lib.spock_server_poll.argtypes = [vp, C.POINTER(ServeResult), C.c_int, _ip]
     lib.spock_server_outstanding.argtypes = [vp]
@@ -388,7 +388,7 @@ class Server:
     """Serving of MPC requests on resident plants (spock_server_*): requests are
     admitted to the device as CTAs free up, each solved alone in its CTA."""
 
-    def __init__(self, plants, precision=32, o: SolveOpts = None, ring_slots=4096):
+    def __init__(self, plants, precision=32, o: SolveOpts = None, ring_slots=4096, mem_budget=0):
         lib = load()
         self.plants = list(plants)
         self.precision = int(precision)
@@ -397,7 +397,7 @@ class Server:
         h = C.c_void_p()
         adm = C.c_int()
         self.status = _check(lib.spock_server_create(arr, len(self.plants), self.precision, C.byref(o),
-                                                     int(ring_slots), C.byref(h), C.byref(adm)),
+                                                     int(ring_slots), int(mem_budget), C.byref(h), C.byref(adm)),
                              "spock_server_create")
         self.h = h
         self.admitted = adm.value

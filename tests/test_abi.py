@@ -106,9 +106,9 @@ def test_batch_and_server_reject_bad_arguments_on_host(lib):
     assert lib.spock_batch_create(arr, 1, 16, C.byref(out)) == -1        # precision
     assert lib.spock_batch_create(arr, 1, 32, None) == -1
     adm = C.c_int()
-    assert lib.spock_server_create(None, 1, 32, None, 16, C.byref(out), C.byref(adm)) == -1
-    assert lib.spock_server_create(arr, 1, 32, None, 16, C.byref(out), C.byref(adm)) == -1
-    assert lib.spock_server_create(arr, 1, 32, None, 0, C.byref(out), C.byref(adm)) == -1
+    assert lib.spock_server_create(None, 1, 32, None, 16, 0, C.byref(out), C.byref(adm)) == -1
+    assert lib.spock_server_create(arr, 1, 32, None, 16, 0, C.byref(out), C.byref(adm)) == -1
+    assert lib.spock_server_create(arr, 1, 32, None, 0, 0, C.byref(out), C.byref(adm)) == -1
     assert lib.spock_server_submit(None, 0, None, 0, None) == -1
     assert lib.spock_server_poll(None, None, 0, None) == -1
     assert lib.spock_server_outstanding(None) == -1

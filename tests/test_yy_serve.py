@@ -126,3 +126,31 @@ def test_serve_receding_horizon_warm_start(plants):
     # of it: they agree to twice that
     assert np.max(np.abs(rw["u0"] - rc["u0"])) <= 2e-3 * max(1.0, np.max(np.abs(rc["u0"])))
     assert abs(rw["risk"] - rc["risk"]) <= 2e-3 * max(1.0, abs(rc["risk"]))
+
+
+def test_serve_admission_by_memory_budget():
+    """Plants are admitted in order while their solve buffers fit the budget;
+    a request for a refused plant gets ENOMEM, the admitted ones are served."""
+    spock = _spock()
+    fresh = []
+    for i, sp in enumerate(synth.batch_specs(400, seed=4)):
+        if sp["nx"] <= 12 and sp["N"] <= 8 and sp["b"] ** sp["k"] <= 16:
+            fresh.append(synth.batch_problem(sp, i))
+        if len(fresh) == 2:
+            break
+    G = [spock.Problem(p) for p in fresh]          # no solve buffers yet
+    o = spock.opts(precision=32, tol=1e-4, max_iters=20000)
+    with pytest.raises(spock.SpockError) as e:
+        spock.Server(G, precision=32, o=o, mem_budget=1)
+    assert e.value.code == -2
+    w = 4
+    need0 = w * (7 * G[0].n_v + 6 * ((G[0].n_v + 3) // 4 * 4)) + 2000 + 64 * 1024
+    srv = spock.Server(G, precision=32, o=o, mem_budget=need0 + 1024)
+    assert srv.status == 2 and srv.admitted == 1
+    with pytest.raises(spock.SpockError) as e2:
+        srv.submit(1, fresh[1].x0, warm=False)
+    assert e2.value.code == -2
+    rid = srv.submit(0, fresh[0].x0, warm=False)
+    res = _wait(srv, 1)
+    srv.close()
+    assert res[rid]["status"] == 0
