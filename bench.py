@@ -427,10 +427,16 @@ def run_ours(args, rank, world, local_rank, dist):
     cpu = cpu_baseline(p) if world == 1 else None
     batched = serving = None
     if bprobs is not None:
-        bG = [spock.Problem(q) for q in bprobs]
-        small = sorted(range(len(bprobs)), key=lambda k: (len(bprobs[k].anc), k))[:SMALL_COUNT]
-        batched = bench_batched(spock, bprobs, bG, small)
-        serving = bench_serving(spock, [bprobs[k] for k in small], [bG[k] for k in small])
+        # a failure here must not cost the headline line: it is reported in place
+        try:
+            bG = [spock.Problem(q) for q in bprobs]
+            small = sorted(range(len(bprobs)), key=lambda k: (len(bprobs[k].anc), k))[:SMALL_COUNT]
+            batched = bench_batched(spock, bprobs, bG, small)
+            serving = bench_serving(spock, [bprobs[k] for k in small], [bG[k] for k in small])
+        except Exception as e:   # noqa: BLE001
+            err = {"error": f"{type(e).__name__}: {e}"}
+            batched = batched or err
+            serving = serving or err
     line = {"metric": METRIC, "value": value * 1.0, "unit": "iter/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
