@@ -132,6 +132,28 @@ def avar(Z, p, a):
     return float(val)
 
 
+def avar_maximiser(Z, p, a):
+    """The maximising mu of AV@R_a[Z] over the ambiguity set
+    {sum mu = 1, 0 <= mu <= p/a} (Sec. 3.3, "Average-value-at-risk"): mass
+    p_j/a goes to the largest costs first until one unit is placed; a = 0 puts
+    the unit on the largest cost."""
+    Z = np.asarray(Z, dtype=np.float64)
+    p = np.asarray(p, dtype=np.float64)
+    mu = np.zeros_like(Z)
+    order = np.argsort(-Z, kind="stable")
+    if a <= 0.0:
+        mu[order[0]] = 1.0
+        return mu
+    left = 1.0
+    for j in order:
+        w = min(p[j] / a, left)
+        mu[j] = w
+        left -= w
+        if left <= 0.0:
+            break
+    return mu
+
+
 def conic_risk_data(p, a):
     """b and E of the conic representation of AV@R_a on the probability space
     ch(i) (Sec. 3.3, "Conic representation"): b = [p; 0_n; 1],
@@ -633,7 +655,7 @@ class Oracle:
         return np.zeros(self.lay.n_z + self.lay.n_eta)
 
     def solve(self, v0=None, tol=1e-4, max_iters=5000, method="spock", m=AA_MEMORY,
-              max_backtracks=30, rank_tol=1e-10):
+              max_backtracks=30, rank_tol=1e-10, log=None):
         """Alg. 4 (SPOCK) or, with method="cp", plain CP iterates v <- T(v).
 
         Readings: the averagedness constant in rho is that of a firmly
@@ -642,6 +664,8 @@ class Oracle:
         step falls back to v <- T(v); c2^k uses the outer counter k;
         termination when ||v - T(v)||_inf <= tol (eps_rel = 0). After a K1 step
         the residual r~ of the accepted point is the next iterate's residual.
+        `log` (a list, optional) receives (k, n_T, ||r||_inf) at every outer
+        iteration.
         """
         v = self.initial_v() if v0 is None else np.array(v0, dtype=np.float64)
         tv = self.T(v)
@@ -663,6 +687,8 @@ class Oracle:
         v_prev = r_prev = None
         k = 0
         while True:
+            if log is not None:
+                log.append((k, n_T, float(np.max(np.abs(r)))))
             if np.max(np.abs(r)) <= tol or k >= max_iters:
                 break
             if v_prev is not None:
@@ -753,6 +779,44 @@ class Oracle:
         QN = eta[lay.e_qN:].reshape(tr.n_l, nx + 2)
         val += float(np.sum(0.5 * QN[:, -2] - 0.5 * QN[:, -1]))
         return val
+
+    def nested_values(self, x, u):
+        """Cost-to-go V^i of a trajectory under the nested risk (Eq.
+        original-problem) with the original (unscaled) costs, and the
+        maximising conditional weights mu^c of every non-root node (the
+        AV@R maximiser over the children of its ancestor, Sec. 3.3-3.4)."""
+        P, tr = self.P, self.tree
+        V = np.zeros(tr.n)
+        mu = np.zeros(tr.n)
+        mu[0] = 1.0
+        dense = np.ndim(P.Q) == 3
+        for jj in range(tr.n_l):
+            j = tr.n_nl + jj
+            QN = P.QN[jj] if np.ndim(P.QN) == 3 else np.diag(P.QN[jj])
+            V[j] = x[j] @ QN @ x[j]
+        for t in range(tr.N - 1, -1, -1):
+            for i in tr.nodes_at[t]:
+                ch = tr.children[i]
+                Z = []
+                for c in ch:
+                    Qc = P.Q[c - 1] if dense else np.diag(P.Q[c - 1])
+                    Rc = P.R[c - 1] if np.ndim(P.R) == 3 else np.diag(P.R[c - 1])
+                    Z.append(x[i] @ Qc @ x[i] + u[i] @ Rc @ u[i] + V[c])
+                Z = np.asarray(Z)
+                V[i] = avar(Z, tr.prob[ch], self.avar_level[i])
+                mu[ch] = avar_maximiser(Z, tr.prob[ch], self.avar_level[i])
+        return V, mu
+
+    def path_weights(self, x, u):
+        """Product of the maximising conditional weights mu along the path from
+        the root to every node: the nodes with positive weight are those whose
+        costs enter the nested risk value; elsewhere the optimal inputs need
+        not be unique (an AV@R level below one can give children weight 0)."""
+        _, mu = self.nested_values(x, u)
+        w = np.ones(self.tree.n)
+        for i in range(1, self.tree.n):
+            w[i] = w[self.tree.anc[i]] * mu[i]
+        return w
 
     def nested_risk(self, x, u):
         """Nested risk of a trajectory (Eq. original-problem) with the original

@@ -34,3 +34,27 @@ def constrained(branching, nx, nu, seed, avar=0.5, uball=None):
     p = synth.random_tree_raocp(rng, nx, nu, N, b, k, avar, name=f"constrained_{branching}",
                                 uball=uball)
     return p
+
+
+def from_spec(d, name="golden"):
+    """Problem of a golden-file spec: tree (anc, prob), the same A and B on
+    every edge, per-node diagonal weights, x/u boxes, u ball, one AV@R level."""
+    anc = np.asarray(d["anc"], dtype=np.int32)
+    prob = np.asarray(d["prob"], dtype=np.float64)
+    n = len(anc)
+    nx, nu = int(d["nx"]), int(d["nu"])
+    st = np.zeros(n, dtype=np.int64)
+    for i in range(1, n):
+        st[i] = st[anc[i]] + 1
+    n_leaf = int(np.sum(st == st.max()))
+    n_nl = n - n_leaf
+    A = np.broadcast_to(np.asarray(d["A_all"], dtype=np.float64), (n - 1, nx, nx)).copy()
+    B = np.broadcast_to(np.asarray(d["B_all"], dtype=np.float64), (n - 1, nx, nu)).copy()
+    xb, ub = float(d["x_bound"]), float(d["u_bound"])
+    return synth.RAOCP(
+        name, anc, prob, nx, nu, A, B, np.zeros((n - 1, nx)),
+        np.asarray(d["Q"], dtype=np.float64), np.asarray(d["R"], dtype=np.float64),
+        np.asarray(d["QN"], dtype=np.float64),
+        np.full((n, nx), -xb), np.full((n, nx), xb), np.full((n_nl, nu), -ub), np.full((n_nl, nu), ub),
+        np.full(n_nl, float(d["u_ball"])), np.full(n_nl, float(d["avar"])),
+        np.asarray(d["x0"], dtype=np.float64), meta=dict(N=int(st.max())))

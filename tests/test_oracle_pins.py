@@ -428,3 +428,156 @@ def test_constrained_solution_diagnostics_vanish():
     assert r["infeas"] < 1e-5 and r["gap"] < 1e-4
     assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * abs(r["risk"])
     assert np.all(np.abs(r["x"]) <= 5 + 1e-5) and np.all(np.abs(r["u"]) <= 2 + 1e-5)
+
+
+# --- preconditioning (Sec. 5.4), values worked out by hand ----------------------
+def _golden_precond():
+    return json.load(open(os.path.join(GOLDEN, "precondition_tiny.json")))
+
+
+@pytest.mark.parametrize("case", ["branchy", "chain"])
+def test_preconditioning_hand_values(case):
+    """c_hat, S^x, S^u, S^x_N, a_con, the scaled dynamics at a non-leaf and a
+    leaf node, the scaled cost factors, x0 and the scaled sets against values
+    derived by hand from the formulas of Sec. 5.4 (tests/golden)."""
+    from tests.problems import from_spec
+    spec = _golden_precond()[case]
+    o = Oracle(from_spec(spec))
+    ex = spec["expect"]
+    chk = lambda got, key: np.testing.assert_allclose(np.asarray(got, dtype=float),  # noqa: E731
+                                                      np.asarray(ex[key]["value"], dtype=float),
+                                                      rtol=1e-14, atol=1e-15, err_msg=key)
+    chk(o.c_hat, "c_hat"); chk(o.Sx, "Sx"); chk(o.Su, "Su"); chk(o.SxN, "SxN")
+    chk(o.a_con, "a_con"); chk(o.a_conN, "a_conN")
+    nx = spec["nx"]
+    if case == "branchy":
+        chk(o.At[3], "At_node4"); chk(o.At[7], "At_node8")
+        chk(o.Bt[3], "Bt_node4"); chk(o.Bt[7], "Bt_node8")
+        chk(o.Qh[7], "Qh_node8"); chk(o.Rh[7], "Rh_node8"); chk(o.QNh[0], "QNh_leaf8")
+        chk(o.x0s, "x0s")
+        chk(o.box_hi[0], "box_hi_node0")
+        chk(o.ball_r[0], "ball_r")
+    else:
+        nb = o.n_box
+        row = np.concatenate([o.Gx[nb], o.Gu[nb]])
+        chk(row, "Gu_ball_row0")
+        chk(o.box_hi[0], "box_hi_node0")
+        chk(o.ball_r[0], "ball_r")
+        chk(o.boxN_hi[0], "boxN_hi")
+        assert o.Gx.shape == (2 * spec["nu"] + nx, nx)
+
+
+# --- the Euclidean ball of S3 --------------------------------------------------------
+def test_proj_ball_outside_points_closed_form():
+    """Projection on {||w|| <= r}: points outside go to r w/||w||, points inside
+    stay (hand values: (3, 4) with r = 1 -> (0.6, 0.8), with r = 2.5 ->
+    (1.5, 2.0); (0.3, 0.4) and 0 unchanged for r = 1)."""
+    got = so_.proj_ball(np.array([[3.0, 4.0], [3.0, 4.0], [0.3, 0.4], [0.0, 0.0]]),
+                        np.array([1.0, 2.5, 1.0, 1.0]))
+    np.testing.assert_allclose(got, [[0.6, 0.8], [1.5, 2.0], [0.3, 0.4], [0.0, 0.0]], rtol=1e-15, atol=0)
+
+
+def test_S3_ball_block_projection_and_support():
+    """The ball rows of S3 (Eq. S3-def): an eta that is zero except for the u
+    ball rows of node 0 projects onto the ball of radius 3/sqrt(2) (chain
+    golden problem, a_con = sqrt(2)), and the support function of S3 there
+    is r ||eta_ball|| (hand values)."""
+    from tests.problems import from_spec
+    o = Oracle(from_spec(_golden_precond()["chain"]))
+    lay = o.lay
+    eta = np.zeros(lay.n_eta)
+    base = lay.e_c + o.n_box                  # node 0's ball rows
+    eta[base:base + 2] = [3.0, 4.0]
+    # keep every translated SOC block at its apex a = (0.., 1/2, -1/2) so it is fixed
+    w = o.nx + o.nu + 2
+    for c in range(1, o.tree.n):
+        eta[lay.e_q + (c - 1) * w + w - 2] = 0.5
+        eta[lay.e_q + (c - 1) * w + w - 1] = -0.5
+    for j in range(o.tree.n_l):
+        eta[lay.e_qN + j * (o.nx + 2) + o.nx] = 0.5
+        eta[lay.e_qN + j * (o.nx + 2) + o.nx + 1] = -0.5
+    p = o.proj_S3(eta)
+    r = 3.0 / math.sqrt(2.0)
+    np.testing.assert_allclose(p[base:base + 2], [0.6 * r, 0.8 * r], rtol=1e-15)
+    assert np.array_equal(np.delete(p, [base, base + 1]), np.delete(eta, [base, base + 1]))
+    # support: ball term r * 5; each apex block contributes <eta, a> = 1/4 + 1/4 = 1/2
+    n_soc = (o.tree.n - 1) + o.tree.n_l
+    assert abs(o.support_S3(eta) - (5.0 * r + 0.5 * n_soc)) < 1e-13
+
+
+def test_constrained_solution_diagnostics_vanish_with_ball():
+    """As test_constrained_solution_diagnostics_vanish with an active Euclidean
+    ball on u, so the ball term of the support function of S3 enters the
+    complementarity gap."""
+    p = constrained([2, 2, 1], 3, 2, seed=17, avar=0.5, uball=0.6)
+    o = Oracle(p)
+    r = o.solve(tol=1e-7, max_iters=60000, method="spock")
+    assert r["res_inf"] <= 1e-7
+    assert np.max(np.linalg.norm(r["u"], axis=1)) >= 0.6 * (1 - 1e-4)   # the ball is active
+    assert np.all(np.linalg.norm(r["u"], axis=1) <= 0.6 * (1 + 1e-5))
+    assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
+    assert r["infeas"] < 1e-5 and r["gap"] < 1e-4
+    assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * abs(r["risk"])
+
+
+# --- Alg. 4 branch logic on hand-worked maps ---------------------------------------
+class _Affine2D(Oracle):
+    """Alg. 4 run on a 2-D map instead of the CP operator: Oracle.solve only
+    needs T, the M-inner product (here the Euclidean one, M = I) and a start."""
+
+    def __init__(self, T, v0):
+        self._T = T
+        self._v0 = np.asarray(v0, dtype=np.float64)
+
+    def T(self, v):
+        return self._T(v)
+
+    def initial_v(self):
+        return self._v0.copy()
+
+    def M_inner(self, a, b):
+        return float(a @ b)
+
+    def _result(self, v, tv, iters, n_T, events):
+        return dict(v=v, Tv=tv, iters=iters, n_T=n_T, events=events)
+
+
+def test_supermann_branches_on_averaged_rotation():
+    """T = (I + R_theta)/2 (firmly nonexpansive, fixed point 0), theta = 10
+    degrees, v0 = (1, 0). With s = sin(theta/2), c = cos(theta/2), worked out by
+    hand (Alg. 4, psi = -r while k <= m):
+      k=0: omega = zeta = s, so no K0; v~ = T(v0) has residual s c, ratio
+           c = 0.9962 > c1, so no K1; rho = ||r~||^2 + <r~, r> = 2 s^2 c^2
+           >= sigma s^2 c, so K2: v1 = v0 - (rho/||r~||^2) r~ = v0 - 2 r~ =
+           cos(theta) R v0;
+      k=1: omega = s cos(theta) <= 0.99 zeta (cos 10 deg = 0.985), K0:
+           v2 = T(v1), zeta = s cos(theta);
+      k=2: omega/zeta = c > 0.99: no K0; K1 fails on the ratio c again; K2:
+           v3 = cos(theta) R v2;
+      k=3: omega/zeta = c cos(theta) = 0.981 <= 0.99: K0, v4 = T(v3).
+    T evaluations: 1 + 2 + 1 + 2 + 1 = 7."""
+    th = math.radians(10.0)
+    Rm = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    Tm = 0.5 * (np.eye(2) + Rm)
+    o = _Affine2D(lambda v: Tm @ v, [1.0, 0.0])
+    r = o.solve(tol=0.0, max_iters=4)
+    assert [e[1] for e in r["events"]] == ["K2", "K0", "K2", "K0"]
+    assert [e[2] for e in r["events"]] == [0, 0, 0, 0]
+    assert r["n_T"] == 7
+    v1 = math.cos(th) * Rm @ np.array([1.0, 0.0])
+    v2 = Tm @ v1
+    v3 = math.cos(th) * Rm @ v2
+    v4 = Tm @ v3
+    np.testing.assert_allclose(r["v"], v4, rtol=1e-13, atol=1e-15)
+
+
+def test_supermann_k1_then_k0_on_half_map():
+    """T(v) = v/2 (firmly nonexpansive). k=0: omega = zeta, no K0; v~ = T(v0)
+    halves the residual (0.5 <= c1) and omega <= omega_safe = zeta: K1, and
+    omega_safe becomes ||r~|| + c2^0. k=1..3: each residual is half the last,
+    below 0.99 zeta: K0. T evaluations 1 + 1 + 3 = 5; v4 = v0/16."""
+    o = _Affine2D(lambda v: 0.5 * v, [4.0, -2.0])
+    r = o.solve(tol=0.0, max_iters=4)
+    assert [e[1] for e in r["events"]] == ["K1", "K0", "K0", "K0"]
+    assert r["n_T"] == 5
+    np.testing.assert_allclose(r["v"], np.array([4.0, -2.0]) / 16.0, rtol=1e-15)
