@@ -93,6 +93,9 @@ typedef struct spock_sizes {
     long long n_z, n_eta, n_v;
     long long factor_bytes_fp64;   /* device bytes of the per-iteration factors, FP64 copy */
     long long factor_bytes_fp32;   /* same, FP32 copy */
+    long long solve_bytes_fp64;    /* device bytes of the solve buffers of an FP64 solve (one
+                                      allocation, made by the first solve in that precision) */
+    long long solve_bytes_fp32;    /* same for FP32 */
 } spock_sizes;
 
 /* spock_problem_create: validate the tree and data, copy them to the device,
@@ -188,6 +191,14 @@ typedef struct spock_info {
                              sweep bulk-copy waits, mat-vecs, team reductions, other step
                              work; grid barriers, all-reductions; barrier and all-reduction
                              counts */
+    /* FP64 exit check at the returned iterate v and its image T(v) (Sec. 5.3,
+     * "Termination"; FP64 solves always, FP32 solves with fp64_check, else NaN):
+     *   xi1    = ||(z - z+)/alpha - L*(eta - eta+)||_inf      (Eq. xi1k)
+     *   xi2    = ||(eta - eta+)/alpha - L(z - z+)||_inf
+     *   infeas = ||L z+ - proj_S3(L z+)||_inf                 (primal infeasibility)
+     *   gap    = |<eta+, L z+> - sigma_S3(eta+)|               (complementarity gap,
+     *            sigma_S3 the support function of S3 of Eq. S3-def) */
+    double xi1, xi2, infeas, gap;
 } spock_info;
 
 void spock_solve_opts_default(spock_solve_opts* o);
@@ -203,6 +214,20 @@ int spock_solve(spock_problem* p, const double* x0, const spock_solve_opts* opts
  * x0 (device, double) [nx]; x_out, u_out (device, double) may be NULL. */
 int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opts* opts,
                        double* x_out, double* u_out, void* stream, spock_info* info);
+
+/* FP64 exit check of any iterate (Sec. 5.3): T(v) in FP64, then the
+ * residual and the optimality measures of spock_info (xi1, xi2, infeas, gap)
+ * plus the two terms of the gap. v (device) [n_v] in `precision` 32 or 64,
+ * scaled variables (the layout above). Uses the problem's FP64 solve buffers
+ * as scratch (allocated on first use): the current iterate kept for warm
+ * starts is not touched. Blocking. */
+typedef struct spock_check_info {
+    double res_inf;       /* ||v - T(v)||_inf in FP64 */
+    double xi1, xi2, infeas, gap;
+    double eta_Lz;        /* <eta+, L z+> */
+    double support;       /* sigma_S3(eta+) */
+} spock_check_info;
+int spock_check(spock_problem* p, int precision, const void* v, void* stream, spock_check_info* out);
 
 /* Device copy of the current iterate v (after a solve) and a way to set it
  * (warm start). (device) buffers of n_v elements in the given precision. */
@@ -227,6 +252,9 @@ typedef struct spock_batch_info {
     double res_inf;       /* ||v - T(v)||_inf at exit, iteration precision */
     double risk;          /* s^0 of T(v) */
     double device_ms;     /* time the problem's CTA spent on it (SM clock) */
+    double xi1, xi2, infeas, gap;   /* FP64 exit check as in spock_info, when opts->fp64_check
+                                       is set (computed after the launch, outside total_ms),
+                                       else NaN */
 } spock_batch_info;
 
 /* Bundle `count` problems (not copied: they must outlive the batch and must not
@@ -252,7 +280,8 @@ int spock_batch_set_tw(spock_batch* b, const int* tw);
 int spock_batch_autotune(spock_batch* b, int iters, int* tw_out);
 
 /* Solve every problem. x0 (host) packed [sum nx], unscaled; opts as for
- * spock_solve (precision must equal the batch's; fp64_check is ignored);
+ * spock_solve (precision must equal the batch's; fp64_check = 1 adds the FP64
+ * exit check of every problem's final iterate to info, after the launch);
  * warm_start = 1 starts each problem from its last iterate. x_out, u_out
  * (host, packed, may be NULL), risk (host) [count] (may be NULL), info (host)
  * [count] (may be NULL). total_ms (may be NULL) receives the device time of
@@ -286,9 +315,11 @@ typedef struct spock_serve_result {
     double latency_ms;    /* host time from submission to the poll that saw the result */
 } spock_serve_result;
 
-/* Admit plants in the given order while their solve buffers fit in the
- * admission budget: mem_budget bytes if mem_budget > 0, else the free device
- * memory less 256 MB (plants whose buffers already exist cost nothing);
+/* Admit plants in the given order while their solve buffers
+ * (spock_sizes.solve_bytes_fp32/_fp64) fit in the admission budget:
+ * mem_budget bytes if mem_budget > 0 (clamped to the free device memory less
+ * 256 MB), else the free device memory less 256 MB (plants whose buffers
+ * already exist cost nothing);
  * *admitted (may be NULL) = how many. opts as for spock_solve (precision must
  * equal `precision`; fp64_check ignored); ring_slots >= 1 bounds the requests
  * on the device at once. Returns SPOCK_PARTIAL if some plants were refused,
@@ -299,7 +330,11 @@ int spock_server_create(spock_problem* const* plants, int count, int precision, 
 
 /* Queue a request: x0 (host) [nx of the plant], unscaled; warm_start = 1
  * starts from the plant's last iterate. *id_out (may be NULL) = request id.
- * SPOCK_ENOMEM for a plant that was not admitted. Non-blocking. */
+ * A request for a plant that is not admitted (refused at creation or evicted)
+ * retries its admission against the room left at that moment (the budget
+ * less what admitted plants were charged, never more than the free device
+ * memory less 256 MB) and gets SPOCK_ENOMEM if it still does not fit.
+ * Non-blocking (an admission allocates the plant's solve buffers). */
 int spock_server_submit(spock_server* s, int plant, const double* x0, int warm_start, long long* id_out);
 
 /* Collect up to max_out finished requests into out (host) and hand waiting
@@ -309,11 +344,37 @@ int spock_server_poll(spock_server* s, spock_serve_result* out, int max_out, int
 /* Requests submitted and not yet collected by spock_server_poll. */
 long long spock_server_outstanding(const spock_server* s);
 
+/* Release a plant: its solve buffers (and with them its warm-start iterate)
+ * are freed and their bytes return to the admission budget, so a request for
+ * a plant refused earlier can be admitted. The plant must have no request
+ * submitted and not collected (SPOCK_EINVAL otherwise). The memory itself is
+ * freed once the persistent launch is idle and has left (at a later poll or
+ * at spock_server_destroy); with the default budget (free memory) it counts
+ * for admission from then on. A later request for the plant re-admits it
+ * (cold iterate if its buffers were freed). */
+int spock_server_evict(spock_server* s, int plant);
+
+/* 1 if the plant is admitted (its buffers resident for the server), 0 if not,
+ * SPOCK_EINVAL for a bad handle or index. */
+int spock_server_admitted(const spock_server* s, int plant);
+
 /* Stop the persistent launch (after the requests in flight) and free. */
 void spock_server_destroy(spock_server* s);
 
 const char* spock_status_str(int status);
 int spock_version(void);
+
+/* Fault injection for tests of the failure path; the paper has no counterpart.
+ * Every later single-problem launch (spock_solve*, spock_op_T, spock_check)
+ * makes its grid barriers wait for `phantom_ctas` (0..4) CTAs beyond the ones
+ * it launches, and gives up one barrier wait after wait_limit_s seconds
+ * (0: the default 2 s; at most 10 s). With phantom_ctas > 0 the first barrier
+ * wait therefore runs out, the launch records the timeout, every CTA leaves
+ * after its bulk copies have landed, and the call returns SPOCK_ETIMEOUT; no
+ * GPU fault is involved and the CUDA context stays usable. (0, 0) restores
+ * normal launches. Process-wide, not thread-safe. SPOCK_EINVAL for values out
+ * of range. */
+int spock_debug_wait_fault(int phantom_ctas, double wait_limit_s);
 
 #ifdef __cplusplus
 }

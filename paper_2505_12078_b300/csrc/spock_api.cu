@@ -315,11 +315,19 @@ int pipe_bytes_for(const spock_problem* p) {
 // cycle probes of the last solve (see SolveCtl::prof)
 static unsigned long long g_last_prof[16];
 
+// test hook of spock_debug_wait_fault: extra CTAs the grid barriers of a
+// single-problem launch wait for, and the limit of one barrier wait
+static int g_phantom = 0;
+static unsigned long long g_wait_ns = 0;
+
 template <class T>
-int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so, cudaStream_t st, SolveCtl* h_ctl,
+int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so_in, cudaStream_t st, SolveCtl* h_ctl,
                float* ms) {
   int rc = ensure_bufs(p, it);
   if (rc) return rc;
+  SolveOpts so = so_in;
+  so.phantom = g_phantom;
+  so.wait_ns = g_wait_ns;
   const int prec = sizeof(T) == 8 ? 64 : 32;
   it.P.pipe_bytes = p->use_pipe ? pipe_bytes_for<T>(p) : 0;
   int maxg = 0;
@@ -437,37 +445,124 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
 }  // namespace spock
 
 namespace spock {
-template <class T>
-int ensure_bufs(spock_problem* p, Iter<T>& it) {
-  if (it.have_bufs) return SPOCK_OK;
-  DevMem& m = p->mem;
-  const long long nv = p->nv;
-  SolveBufs<T>& b = it.sb;
-  b.V = m.alloc<T>(nv); b.TV = m.alloc<T>(nv); b.VT = m.alloc<T>(nv); b.TVT = m.alloc<T>(nv);
-  b.PSI = m.alloc<T>(nv); b.VP = m.alloc<T>(nv); b.RP = m.alloc<T>(nv);
-  const long long nvp = (nv + 3) & ~3LL;   // 16-byte aligned slots
-  b.sstride = nvp;
-  b.S = m.alloc<T>(3 * nvp); b.Y = m.alloc<T>(3 * nvp);
+static int sm_count() {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  b.partials = m.alloc<double>((long long)2 * nsm * 8 * NRED);
-  b.flags = m.alloc<unsigned>((long long)nsm * 8 + (long long)p->seg_top.size());   // + segment flags
-  b.ctl = m.alloc<SolveCtl>(1);
-  if (m.failed) return SPOCK_ENOMEM;
-  cudaMemset(b.V, 0, nv * sizeof(T));
-  cudaMemset(b.S, 0, 3 * nvp * sizeof(T));
-  cudaMemset(b.Y, 0, 3 * nvp * sizeof(T));
+  return nsm;
+}
+static inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+long long solve_buffer_bytes(const spock_problem* p, int precision) {
+  const size_t w = precision == 64 ? 8 : 4;
+  const size_t nv = (size_t)p->nv, nvp = (size_t)((p->nv + 3) & ~3LL);
+  const size_t nsm = (size_t)sm_count();
+  return (long long)(7 * al256(nv * w) + 2 * al256(3 * nvp * w) + al256(2 * nsm * 8 * NRED * sizeof(double)) +
+                     al256((nsm * 8 + p->seg_top.size()) * sizeof(unsigned)) + al256(sizeof(SolveCtl)));
+}
+
+template <class T>
+int ensure_bufs(spock_problem* p, Iter<T>& it) {
+  if (it.have_bufs) return SPOCK_OK;
+  const long long nv = p->nv;
+  const size_t w = sizeof(T);
+  const size_t nsm = (size_t)sm_count();
+  const size_t bytes = (size_t)solve_buffer_bytes(p, w == 8 ? 64 : 32);
+  void* blk = nullptr;
+  if (cudaMalloc(&blk, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SPOCK_ENOMEM;
+  }
+  unsigned char* q = static_cast<unsigned char*>(blk);
+  auto take = [&](size_t n) {
+    unsigned char* r = q;
+    q += al256(n);
+    return r;
+  };
+  SolveBufs<T>& b = it.sb;
+  const long long nvp = (nv + 3) & ~3LL;   // 16-byte aligned slots
+  b.V = (T*)take(nv * w); b.TV = (T*)take(nv * w); b.VT = (T*)take(nv * w); b.TVT = (T*)take(nv * w);
+  b.PSI = (T*)take(nv * w); b.VP = (T*)take(nv * w); b.RP = (T*)take(nv * w);
+  b.sstride = nvp;
+  b.S = (T*)take(3 * nvp * w); b.Y = (T*)take(3 * nvp * w);
+  b.partials = (double*)take(2 * nsm * 8 * NRED * sizeof(double));
+  b.flags = (unsigned*)take((nsm * 8 + p->seg_top.size()) * sizeof(unsigned));   // + segment flags
+  b.ctl = (SolveCtl*)take(sizeof(SolveCtl));
+  it.sb_block = blk;
+  cudaMemset(b.V, 0, nv * w);
+  cudaMemset(b.S, 0, 3 * nvp * w);
+  cudaMemset(b.Y, 0, 3 * nvp * w);
   it.have_bufs = true;
   return cuda_err(cudaGetLastError());
 }
+
+template <class T>
+void release_bufs(Iter<T>& it) {
+  if (it.sb_block) cudaFree(it.sb_block);
+  it.sb_block = nullptr;
+  it.sb = SolveBufs<T>{};
+  it.have_bufs = false;
+}
+template void release_bufs<float>(Iter<float>&);
+template void release_bufs<double>(Iter<double>&);
 template int ensure_bufs<float>(spock_problem*, Iter<float>&);
 template int ensure_bufs<double>(spock_problem*, Iter<double>&);
 }  // namespace spock
 
+namespace {
+// xi1, xi2, infeasibility, gap, <eta+, L z+>, sigma_S3(eta+) of an FP64 pair
+// (v, T(v)) into out6 (host); scratch: the FP64 solve buffers VP, RP, S
+int diag_run(spock_problem* p, const double* v, const double* tv, cudaStream_t st, double* out6) {
+  int rc = ensure_bufs(p, p->f64);
+  if (rc) return rc;
+  const size_t np = diag_partials_doubles();
+  if (!p->d_diag_part) {
+    p->d_diag_part = p->mem.alloc<double>((long long)np + 8);
+    if (!p->d_diag_part) return SPOCK_ENOMEM;
+  }
+  SolveBufs<double>& b = p->f64.sb;
+  double* dout = p->d_diag_part + np;
+  if (launch_diagnostics(p->f64.P, p->d_ynode, v, tv, b.VP, b.RP, b.S, b.S + b.sstride, p->d_diag_part, dout,
+                         st) != cudaSuccess)
+    return SPOCK_EDEVICE;
+  if (cudaMemcpyAsync(out6, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SPOCK_EDEVICE;
+  return cuda_err(cudaStreamSynchronize(st));
+}
+}  // namespace
+
+namespace spock {
+int check_fp64(spock_problem* p, int precision, const void* v, cudaStream_t st, double* out7) {
+  int rc = ensure_bufs(p, p->f64);
+  if (rc) return rc;
+  const long long nv = p->nv;
+  cudaError_t e;
+  if (precision == 32) e = launch_convert_f32_f64((const float*)v, p->f64.sb.VT, nv, st);
+  else if (v != p->f64.sb.VT) e = cudaMemcpyAsync(p->f64.sb.VT, v, nv * 8, cudaMemcpyDeviceToDevice, st);
+  else e = cudaSuccess;
+  if (e != cudaSuccess) return SPOCK_EDEVICE;
+  Iter<double> it = p->f64;
+  it.sb.V = p->f64.sb.VT;
+  it.sb.TV = p->f64.sb.TVT;
+  SolveOpts s1{1e300, 0, 1, 2, 1e-10};
+  SolveCtl h2{};
+  rc = run_solver<double>(p, it, s1, st, &h2, nullptr);
+  if (rc) return rc;
+  out7[0] = h2.res_inf;
+  return diag_run(p, p->f64.sb.VT, p->f64.sb.TVT, st, out7 + 1);
+}
+}  // namespace spock
+
 extern "C" {
 
-int spock_version(void) { return 1; }
+int spock_version(void) { return 2; }
+
+int spock_debug_wait_fault(int phantom_ctas, double wait_limit_s) {
+  if (phantom_ctas < 0 || phantom_ctas > 4 || !(wait_limit_s >= 0.0) || wait_limit_s > 10.0) return SPOCK_EINVAL;
+  g_phantom = phantom_ctas;
+  g_wait_ns = (unsigned long long)(wait_limit_s * 1e9);
+  return SPOCK_OK;
+}
 
 const char* spock_status_str(int s) {
   switch (s) {
@@ -728,6 +823,8 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
 void spock_problem_destroy(spock_problem* p) {
   if (!p) return;
   cudaDeviceSynchronize();
+  release_bufs(p->f64);
+  release_bufs(p->f32);
   p->mem.free_all();
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
@@ -742,6 +839,8 @@ int spock_problem_sizes(const spock_problem* p, spock_sizes* o) {
                           (long long)p->n_nl * (p->nu * p->ldP + p->nx * p->ldK);
   o->factor_bytes_fp64 = words * 8;
   o->factor_bytes_fp32 = words * 4;
+  o->solve_bytes_fp64 = solve_buffer_bytes(p, 64);
+  o->solve_bytes_fp32 = solve_buffer_bytes(p, 32);
   return SPOCK_OK;
 }
 
@@ -854,12 +953,14 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
   cudaStream_t st = (cudaStream_t)stream;
   int rc = set_x0_dev(p, x0, st);
   if (rc) return rc;
-  SolveOpts so;
+  SolveOpts so{};
   so.tol = o.tol; so.max_iters = o.max_iters; so.max_backtracks = o.max_backtracks;
   so.method = o.method; so.rank_tol = (o.precision == 64) ? 1e-10 : 1e-5;
   SolveCtl h{};
   float ms = 0.f;
   double res64 = -1.0;
+  double diag6[6];
+  bool have_diag = false;
   const long long nv = p->nv;
   if (o.precision == 64) {
     rc = ensure_bufs(p, p->f64);
@@ -876,6 +977,10 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
     k_unscale<double><<<64, 256, 0, st>>>(p->n, p->n_nl, p->nx, p->nu, p->o_x, p->o_u, tz, p->d_Sx,
                                          p->d_SxN, p->d_Su, x_out, u_out, p->d_out_risk);
     res64 = h.res_inf;
+    // FP64 exit check of (v, T(v)) as they stand (Sec. 5.3)
+    rc = diag_run(p, p->f64.sb.V, z, st, diag6);
+    if (rc) return rc;
+    have_diag = true;
   } else {
     rc = ensure_bufs(p, p->f32);
     if (rc) return rc;
@@ -891,18 +996,14 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
                                         p->d_SxN, p->d_Su, x_out, u_out, p->d_out_risk);
     res64 = h.res_inf;
     if (o.fp64_check) {
-      // FP64 residual of the FP32 iterate: one FP64 evaluation of T
-      rc = ensure_bufs(p, p->f64);
+      // FP64 exit check of the FP32 iterate: one FP64 evaluation of T, the
+      // residual, xi1, xi2, infeasibility and gap (Sec. 5.3)
+      double out7[7];
+      rc = check_fp64(p, 32, p->f32.sb.V, st, out7);
       if (rc) return rc;
-      if (launch_convert_f32_f64(p->f32.sb.V, p->f64.sb.VT, nv, st) != cudaSuccess) return SPOCK_EDEVICE;
-      Iter<double> it = p->f64;
-      it.sb.V = p->f64.sb.VT;
-      it.sb.TV = p->f64.sb.TVT;
-      SolveOpts s1{1e300, 0, 1, 2, 1e-10};
-      SolveCtl h2{};
-      rc = run_solver<double>(p, it, s1, st, &h2, nullptr);
-      if (rc) return rc;
-      res64 = h2.res_inf;
+      res64 = out7[0];
+      for (int q = 0; q < 6; ++q) diag6[q] = out7[1 + q];
+      have_diag = true;
     }
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return SPOCK_EDEVICE;
@@ -916,6 +1017,10 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
     info->device_ms = ms;
     for (int q = 0; q < 7; ++q) info->phase_ms[q] = 1e-6 * (double)h.prof[q];
     for (int q = 0; q < 8; ++q) info->counters[q] = (double)h.prof[8 + q];
+    info->xi1 = have_diag ? diag6[0] : NAN;
+    info->xi2 = have_diag ? diag6[1] : NAN;
+    info->infeas = have_diag ? diag6[2] : NAN;
+    info->gap = have_diag ? diag6[3] : NAN;
   }
   return h.status == 0 ? SPOCK_OK : SPOCK_MAXITER;
 }
@@ -941,6 +1046,16 @@ int spock_solve(spock_problem* p, const double* x0, const spock_solve_opts* opts
   if (dx) cudaFree(dx);
   if (du) cudaFree(du);
   return rc;
+}
+
+int spock_check(spock_problem* p, int precision, const void* v, void* stream, spock_check_info* out) {
+  if (!p || !v || !out || (precision != 32 && precision != 64)) return SPOCK_EINVAL;
+  double o7[7];
+  const int rc = check_fp64(p, precision, v, (cudaStream_t)stream, o7);
+  if (rc) return rc;
+  out->res_inf = o7[0]; out->xi1 = o7[1]; out->xi2 = o7[2]; out->infeas = o7[3]; out->gap = o7[4];
+  out->eta_Lz = o7[5]; out->support = o7[6];
+  return SPOCK_OK;
 }
 
 int spock_get_iterate(spock_problem* p, int precision, void* v_out, void* stream) {

@@ -3,6 +3,7 @@
 // k_batch launch with its prep and result kernels captured in a CUDA graph,
 // and the warps-per-team autotuner.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -518,7 +519,7 @@ int spock_batch_autotune(spock_batch* b, int iters, int* tw_out) {
   const int n = b->count;
   std::vector<long long> best(n, -1);
   std::vector<int> best_tw(b->tw), best_pipe(b->pipe);
-  SolveOpts so;
+  SolveOpts so{};
   so.tol = 0.0; so.max_iters = iters; so.max_backtracks = 1; so.method = 1;
   so.rank_tol = b->precision == 64 ? 1e-10 : 1e-5;
   memset(b->h_x0, 0, sizeof(double) * b->x0_total);
@@ -577,7 +578,7 @@ int spock_batch_solve(spock_batch* b, const double* x0, const spock_solve_opts* 
   for (long long k = 0; k < b->x0_total; ++k)
     if (!isfinite(x0[k])) return SPOCK_EINVAL;
   memcpy(b->h_x0, x0, sizeof(double) * b->x0_total);
-  SolveOpts so;
+  SolveOpts so{};
   so.tol = o.tol; so.max_iters = o.max_iters; so.max_backtracks = o.max_backtracks; so.method = o.method;
   so.rank_tol = (o.precision == 64) ? 1e-10 : 1e-5;
   float ms = 0.f;
@@ -603,6 +604,18 @@ int spock_batch_solve(spock_batch* b, const double* x0, const spock_solve_opts* 
       info[i].res_inf = r.res_inf;
       info[i].risk = r.risk;
       info[i].device_ms = (double)r.cycles / khz;
+      info[i].xi1 = info[i].xi2 = info[i].infeas = info[i].gap = NAN;
+    }
+  }
+  if (info && o.fp64_check) {
+    // FP64 exit check of every final iterate (kept in V by k_batch_post)
+    for (int i = 0; i < b->count; ++i) {
+      spock_problem* p = b->probs[i];
+      double o7[7];
+      const void* v = b->precision == 64 ? (const void*)p->f64.sb.V : (const void*)p->f32.sb.V;
+      const int rc2 = check_fp64(p, b->precision, v, b->stream, o7);
+      if (rc2) return rc2;
+      info[i].xi1 = o7[1]; info[i].xi2 = o7[2]; info[i].infeas = o7[3]; info[i].gap = o7[4];
     }
   }
   return worst;

@@ -348,6 +348,7 @@ struct Grid {
   unsigned long long* prof;   // cycle counters of CTA 0 (slots 12..15), may be null
   int rank, size;     // this CTA's index in the group and the group's size
   bool local;
+  uint64_t limit_ns;  // give up a barrier wait after this long
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -391,7 +392,7 @@ __device__ __forceinline__ bool poll_flags(Grid& g, unsigned e) {
         const uint64_t t = global_ns();
         if (t0 == 0) {
           t0 = t;
-        } else if (t - t0 > BARRIER_LIMIT_NS) {
+        } else if (t - t0 > g.limit_ns) {
           atomicExch(&g.ctl->error, 1);
           s_bad = 1;
           break;

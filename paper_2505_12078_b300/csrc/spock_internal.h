@@ -43,6 +43,13 @@ cudaError_t launch_apply_L(const Prob<T>& P, const int* ynode, const T* z, T* et
 template <class T>
 cudaError_t launch_apply_Lt(const Prob<T>& P, const int* ynode, const T* eta, T* z, cudaStream_t s);
 
+// FP64 exit check (Sec. 5.3): xi1, xi2, primal infeasibility, complementarity
+// gap of (v, T(v)); see spock_diag.cu for the scratch it needs
+size_t diag_partials_doubles();
+cudaError_t launch_diagnostics(const Prob<double>& P, const int* ynode, const double* v, const double* tv,
+                               double* d, double* ltde, double* ldz, double* lz, double* part, double* out6,
+                               cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // solver
 // ---------------------------------------------------------------------------
@@ -52,6 +59,8 @@ struct SolveOpts {
   int max_backtracks;
   int method;          // 0 SPOCK, 1 plain CP, 2 one T evaluation
   double rank_tol;     // Anderson rank test (relative to ||Y||_F)
+  unsigned long long wait_ns;   // limit of one grid-barrier wait (0: BARRIER_LIMIT_NS)
+  int phantom;         // test hook: CTAs a single-problem launch's barriers expect beyond its grid
 };
 
 // Device control block of one solve (global memory, zeroed before a launch).

@@ -46,6 +46,7 @@ struct Iter {   // per-precision iteration data
       ldc = 0;
   SolveBufs<T> sb{};
   bool have_bufs = false;
+  void* sb_block = nullptr;   // the one device allocation that holds every buffer of sb
   Prob<T> P{};
 };
 
@@ -78,6 +79,7 @@ struct spock_problem {
   spock::Iter<double> f64;
   spock::Iter<float> f32;
   double* d_out_risk;
+  double* d_diag_part = nullptr;   // partials and result of the FP64 exit check (first use)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -85,4 +87,17 @@ namespace spock {
 // solve buffers of one precision, allocated on first use
 template <class T>
 int ensure_bufs(spock_problem* p, Iter<T>& it);
+// bytes of one precision's solve buffers (one allocation: seven n_v vectors,
+// the Anderson memory S and Y, reduction partials, barrier and segment flags,
+// the control block)
+long long solve_buffer_bytes(const spock_problem* p, int precision);
+// free one precision's solve buffers (the next solve allocates them again and
+// starts cold); the caller makes sure no kernel uses them
+template <class T>
+void release_bufs(Iter<T>& it);
+// FP64 exit check of an iterate v (device, `precision` 32 or 64): T(v) in FP64,
+// then ||v - T(v)||_inf, xi1, xi2, infeasibility, gap, <eta+, L z+> and
+// sigma_S3(eta+) into out7 (host). Uses the problem's FP64 solve buffers VT,
+// TVT, VP, RP and S as scratch. Blocking.
+int check_fp64(spock_problem* p, int precision, const void* v, cudaStream_t st, double* out7);
 }  // namespace spock

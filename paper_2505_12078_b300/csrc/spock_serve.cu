@@ -48,6 +48,11 @@ struct Pending {
 struct spock_server {
   int count = 0, precision = 32, admitted = 0, cap = 0;
   std::vector<spock_problem*> plants;
+  std::vector<int> is_admitted;     // per plant: its solve buffers are resident for the server
+  std::vector<long long> charged;   // per plant: bytes charged to the budget at admission
+  std::vector<int> release_pending; // per plant: evicted, buffers freed once the launch is idle
+  long long budget = 0;             // explicit admission budget (0: free device memory)
+  long long room = 0;               // budget left (explicit budget only)
   SolveOpts so{};
   DevMem mem;
   void *d_probs = nullptr, *d_bufs = nullptr, *d_meta = nullptr;
@@ -88,16 +93,18 @@ size_t views_bytes(int tw, int pipe_bytes) {
   return sizeof(T) == 8 ? views_bytes_d2(tw, pipe_bytes) : views_bytes_f1(tw, pipe_bytes);
 }
 
-// bytes of one precision's solve buffers (what admission has to find free)
-size_t buffer_bytes(const spock_problem* p, int precision) {
-  const size_t w = precision == 64 ? 8 : 4;
-  const size_t nvp = (size_t)((p->nv + 3) & ~3LL);
-  return w * (7 * (size_t)p->nv + 6 * nvp) + sizeof(SolveCtl) + 64 * 1024;
+// device memory kept free for the launch, the ring and other users
+constexpr long long kReserve = 256ll << 20;
+
+long long free_room() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+  return (long long)fr - kReserve;
 }
 
 template <class T>
 int serve_init(spock_server* s) {
-  const int n = s->admitted;
+  const int n = s->count;
   int optin = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -106,11 +113,11 @@ int serve_init(spock_server* s) {
   std::vector<ServeMeta<T>> M(n);
   std::vector<int> tw(n);
   size_t smem = 0;
+  // descriptors, team widths and shared memory of every plant (admitted now or
+  // later): they depend on the plant's sizes only
   for (int i = 0; i < n; ++i) {
     spock_problem* p = s->plants[i];
     Iter<T>& it = iter_of<T>(p);
-    const int rc = ensure_bufs<T>(p, it);
-    if (rc) return rc;
     tw[i] = tw_min(p);
     const long long e = std::max((long long)p->nx * p->ldB,
                                  (long long)(p->nx + p->nu) * p->ldF + (long long)p->nx * p->ldK);
@@ -119,7 +126,11 @@ int serve_init(spock_server* s) {
     P[i].cta = 0;
     P[i].pipe_bytes = (views_bytes<T>(tw[i], pb) + 16 * 1024 <= (size_t)optin) ? pb : 0;
     smem = std::max(smem, views_bytes<T>(tw[i], P[i].pipe_bytes));
-    B[i] = it.sb;
+    if (s->is_admitted[i]) {
+      const int rc = ensure_bufs<T>(p, it);
+      if (rc) return rc;
+      B[i] = it.sb;
+    }
     M[i].nx = p->nx; M[i].nu = p->nu; M[i].o_u = p->o_u; M[i].nv = p->nv;
     M[i].Sx = p->d_Sx; M[i].Su = p->d_Su; M[i].x0s = it.x0s;
   }
@@ -141,6 +152,56 @@ int serve_init(spock_server* s) {
   const int rc = sizeof(T) == 8 ? serve_grid_d2(smem, &g) : serve_grid_f1(smem, &g);
   if (rc || g <= 0) return SPOCK_EDEVICE;
   s->grid = g;
+  return SPOCK_OK;
+}
+
+// bytes admission charges for plant i: its solve buffers, unless they exist
+long long admission_need(const spock_server* s, int i) {
+  const spock_problem* p = s->plants[i];
+  const bool have = s->precision == 64 ? p->f64.have_bufs : p->f32.have_bufs;
+  return have ? 0 : solve_buffer_bytes(p, s->precision);
+}
+
+// room for a new admission: the explicit budget left, never more than the
+// free device memory less the reserve
+long long admission_room(const spock_server* s) {
+  const long long fr = free_room();
+  return s->budget > 0 ? std::min(s->room, fr) : fr;
+}
+
+// free the buffers of evicted plants once no launch can touch them
+void release_evicted(spock_server* s, bool force) {
+  if (!force && s->launched && cudaStreamQuery(s->stream) != cudaSuccess) return;
+  for (int i = 0; i < s->count; ++i) {
+    if (!s->release_pending[i]) continue;
+    if (s->precision == 64) release_bufs(s->plants[i]->f64);
+    else release_bufs(s->plants[i]->f32);
+    s->release_pending[i] = 0;
+  }
+}
+
+// admit plant i now (a request for it arrived): allocate its buffers if the
+// room allows and publish its table entry before any request can name it
+template <class T>
+int admit_plant(spock_server* s, int i) {
+  spock_problem* p = s->plants[i];
+  Iter<T>& it = iter_of<T>(p);
+  // evicted with buffers not freed yet: taking them back costs their bytes
+  const long long need = s->release_pending[i] ? solve_buffer_bytes(p, s->precision) : admission_need(s, i);
+  if (need > admission_room(s)) return SPOCK_ENOMEM;
+  s->release_pending[i] = 0;
+  const int rc = ensure_bufs<T>(p, it);
+  if (rc) return rc;
+  // the persistent launch may be running: the entry is written with a
+  // synchronous copy before the host publishes any request of plant i, and
+  // k_serve reads entries through L2 (never a stale non-coherent line)
+  if (cudaMemcpy(static_cast<SolveBufs<T>*>(s->d_bufs) + i, &it.sb, sizeof(SolveBufs<T>), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return SPOCK_EDEVICE;
+  s->is_admitted[i] = 1;
+  s->charged[i] = need;
+  if (s->budget > 0) s->room -= need;
+  s->admitted += 1;
   return SPOCK_OK;
 }
 
@@ -213,23 +274,24 @@ int spock_server_create(spock_problem* const* plants, int count, int precision, 
   s->so.tol = o.tol; s->so.max_iters = o.max_iters; s->so.max_backtracks = o.max_backtracks;
   s->so.method = o.method; s->so.rank_tol = precision == 64 ? 1e-10 : 1e-5;
   // admission by device memory: plants in order while their solve buffers fit
-  // in the budget (by default the free memory, keeping 256 MB for the launch
-  // and the ring)
-  long long room = mem_budget;
-  if (room <= 0) {
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    room = (long long)fr - (256ll << 20);
-  }
+  // in the budget (an explicit budget is clamped to the free memory less the
+  // reserve; by default the free memory less the reserve)
+  s->is_admitted.assign(count, 0);
+  s->charged.assign(count, 0);
+  s->release_pending.assign(count, 0);
+  const long long fr = free_room();
+  s->budget = mem_budget > 0 ? mem_budget : 0;
+  long long room = mem_budget > 0 ? std::min((long long)mem_budget, fr) : fr;
   int adm = 0;
   for (int i = 0; i < count; ++i) {
-    const Iter<double>& f = plants[i]->f64;
-    const bool have = precision == 64 ? f.have_bufs : plants[i]->f32.have_bufs;
-    const long long need = have ? 0 : (long long)buffer_bytes(plants[i], precision);
+    const long long need = admission_need(s, i);
     if (need > room) break;
     room -= need;
+    s->is_admitted[i] = 1;
+    s->charged[i] = need;
     ++adm;
   }
+  s->room = mem_budget > 0 ? room : 0;
   s->admitted = adm;
   if (admitted) *admitted = adm;
   if (adm == 0) { delete s; return SPOCK_ENOMEM; }
@@ -264,10 +326,14 @@ int spock_server_create(spock_problem* const* plants, int count, int precision, 
 
 int spock_server_submit(spock_server* s, int plant, const double* x0, int warm_start, long long* id_out) {
   if (!s || !x0 || plant < 0 || plant >= s->count) return SPOCK_EINVAL;
-  if (plant >= s->admitted) return SPOCK_ENOMEM;
   const int nx = s->plants[plant]->nx;
   for (int k = 0; k < nx; ++k)
     if (!isfinite(x0[k])) return SPOCK_EINVAL;
+  if (!s->is_admitted[plant]) {           // refused or evicted earlier: try again now
+    release_evicted(s, false);
+    const int rc = s->precision == 64 ? admit_plant<double>(s, plant) : admit_plant<float>(s, plant);
+    if (rc) return rc;
+  }
   Pending r;
   r.id = s->next_id++;
   r.warm = warm_start ? 1 : 0;
@@ -315,8 +381,27 @@ int spock_server_poll(spock_server* s, spock_serve_result* out, int max_out, int
     s->queue[p].pop_front();
   }
   if (n_out) *n_out = n;
+  release_evicted(s, false);
   // work left: make sure the persistent launch is there to take it
   return s->outstanding > 0 ? ensure_running(s) : SPOCK_OK;
+}
+
+int spock_server_evict(spock_server* s, int plant) {
+  if (!s || plant < 0 || plant >= s->count) return SPOCK_EINVAL;
+  if (!s->is_admitted[plant]) return SPOCK_OK;
+  if (s->plant_busy[plant] || !s->queue[plant].empty()) return SPOCK_EINVAL;   // requests outstanding
+  s->is_admitted[plant] = 0;
+  if (s->budget > 0) s->room += s->charged[plant];
+  s->charged[plant] = 0;
+  s->admitted -= 1;
+  s->release_pending[plant] = 1;
+  release_evicted(s, false);
+  return SPOCK_OK;
+}
+
+int spock_server_admitted(const spock_server* s, int plant) {
+  if (!s || plant < 0 || plant >= s->count) return SPOCK_EINVAL;
+  return s->is_admitted[plant] ? 1 : 0;
 }
 
 long long spock_server_outstanding(const spock_server* s) { return s ? s->outstanding : -1; }
@@ -328,6 +413,7 @@ void spock_server_destroy(spock_server* s) {
     cudaStreamSynchronize(s->stream);
     cudaStreamDestroy(s->stream);
   }
+  release_evicted(s, true);
   if (s->h_ring) cudaFreeHost(s->h_ring);
   if (s->h_res) cudaFreeHost(s->h_res);
   if (s->h_ctl) cudaFreeHost((void*)s->h_ctl);

@@ -836,13 +836,17 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
   const int nw = g.size * (blockDim.x >> 5);
   Team w1;
   w1.tw = 1; w1.id = wid; w1.warp = 0; w1.lane = lane; w1.tid = lane; w1.nth = 32;
+  bool team_issued = false;   // the team path's first bulk copy is in flight
   if (P.cta) {
     ++cs.epoch;
     if (P.n_levels > 0 && seg_count(P, 0, tg, nt) > 0)
       ring_prefetch(P, cs.ring, seg_get(P, *cs.sched, 0, 0, tg, nt), false);
   } else if (pp.on && P.n_levels > 0) {
     const int s0 = P.lvl_off[0] + tg;
-    if (s0 < P.lvl_off[1]) issue_first_B<T, CH>(P, tm, pp, s0);
+    if (s0 < P.lvl_off[1]) {
+      issue_first_B<T, CH>(P, tm, pp, s0);
+      team_issued = true;
+    }
   }
     // P
   for (int node = gw; node < P.n; node += nw) {
@@ -852,7 +856,21 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
       prep_leaf(P, lane, node, vin);
     __syncwarp();
   }
-  if (!grid_sync(g)) return false;
+  if (!grid_sync(g)) {
+    // the launch is failing: let the copies issued before phase P land
+    // (bounded) so that no bulk copy into this CTA's shared memory outlives it
+    if (P.cta) {
+      ring_settle(cs.ring, cs.ring.ahead);
+    } else {
+      if (team_issued && tm.tid == 0) {
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(pp.bar + pp.cur, pp.par[pp.cur]) && global_ns() - t0 < 200000000ull) {
+        }
+      }
+      __syncthreads();
+    }
+    return false;
+  }
   pc.mark(ctl, 0);
   // B
   const int L = P.n_levels;
@@ -1044,8 +1062,10 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
         const int slot = head;
         const bool push = (k >= 1);
         double dd[NRED];
-        T acc[2 * AA_M];
-        for (int a = 0; a < 2 * AA_M; ++a) acc[a] = 0;
+        // the Gram matrix Y'Y and Y'r are accumulated in FP64 in every
+        // precision: their condition is the square of Y's
+        double acc[2 * AA_M];
+        for (int a = 0; a < 2 * AA_M; ++a) acc[a] = 0.0;
         T* Sslot = B.S + slot * ss;
         T* Yslot = B.Y + slot * ss;
         // one element: new pair (s, y), dots y.Y_l and Y_l.r, copies of v and r
@@ -1058,8 +1078,8 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
           const T yl[AA_M] = {slot == 0 ? y_ : y0, slot == 1 ? y_ : y1, slot == 2 ? y_ : y2};
 #pragma unroll
           for (int l = 0; l < AA_M; ++l) {
-            acc[l] = fma(y_, yl[l], acc[l]);
-            acc[AA_M + l] = fma(yl[l], r, acc[AA_M + l]);
+            acc[l] = fma((double)y_, (double)yl[l], acc[l]);
+            acc[AA_M + l] = fma((double)yl[l], (double)r, acc[AA_M + l]);
           }
         };
         for (long long q = gtid; q < nvec; q += gstride) {
@@ -1089,7 +1109,7 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
           stc(B.VP + e, v);
           stc(B.RP + e, ro);
         }
-        for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? (double)acc[a] : 0.0;
+        for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? acc[a] : 0.0;
         {
           __shared__ double scratch2[NRED * 32];
           if (!grid_allreduce(g, dd, scratch2, -1)) goto fail;
@@ -1366,8 +1386,9 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
   g.partials = B.partials;
   g.epoch = 0;
   g.rank = blockIdx.x;
-  g.size = gridDim.x;
+  g.size = gridDim.x + o.phantom;   // phantom > 0 only in tests of the timeout path
   g.local = false;
+  g.limit_ns = o.wait_ns ? o.wait_ns : BARRIER_LIMIT_NS;
   __shared__ unsigned long long s_prof[16];
   if (threadIdx.x < 16) s_prof[threadIdx.x] = 0ull;
   __syncthreads();
@@ -1387,8 +1408,21 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
 // cycles[p]: clock cycles that the first CTA of the problem spent on it.
 // ---------------------------------------------------------------------------
 
+// a struct of 8-byte words read through L2 (never from a non-coherent line):
+// for table entries the host may write while a persistent launch runs
+template <class X>
+__device__ __forceinline__ X ld_struct_cg(const X* p) {
+  static_assert(sizeof(X) % 8 == 0, "8-byte words");
+  X out;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&out);
+#pragma unroll
+  for (int k = 0; k < (int)(sizeof(X) / 8); ++k) dst[k] = __ldcg(src + k);
+  return out;
+}
+
 template <class T, int CH>
-__device__ __forceinline__ void batch_one(const Prob<T>* __restrict__ probs, const SolveBufs<T>* __restrict__ bufs,
+__device__ __forceinline__ void batch_one(const Prob<T>* __restrict__ probs, const SolveBufs<T>& B,
                                           const int* __restrict__ tws, const SolveOpts& o, int pi, Grid& g,
                                           unsigned char* smraw, unsigned char* s_prob, uint64_t* s_bar, int* s_ok,
                                           unsigned long long* s_prof, bool first, long long* cycles) {
@@ -1404,7 +1438,6 @@ __device__ __forceinline__ void batch_one(const Prob<T>* __restrict__ probs, con
   fence_mbar_init();
   __syncthreads();
   const Prob<T>& P = *reinterpret_cast<const Prob<T>*>(s_prob);
-  const SolveBufs<T> B = bufs[pi];
   const int tw = tws[pi];
   const Team tm = make_team(tw);
   const int teams = (blockDim.x >> 5) / tw;
@@ -1451,11 +1484,13 @@ __global__ void __launch_bounds__(256, 1)
     g.rank = blockIdx.x - start;
     g.size = plan.gang_size[k];
     g.local = g.size == 1;
+    g.limit_ns = o.wait_ns ? o.wait_ns : BARRIER_LIMIT_NS;
     g.flags = plan.flags + start;
     g.partials = plan.partials + (size_t)2 * NRED * start;
     g.epoch = 0;
     for (int q = plan.list_off[k]; q < plan.list_off[k + 1]; ++q) {
-      batch_one<T, CH>(probs, bufs, tws, o, plan.list[q], g, smraw, s_prob, s_bar, s_ok, s_prof, first, cycles);
+      batch_one<T, CH>(probs, bufs[plan.list[q]], tws, o, plan.list[q], g, smraw, s_prob, s_bar, s_ok, s_prof, first,
+                       cycles);
       first = false;
     }
   }
@@ -1463,6 +1498,7 @@ __global__ void __launch_bounds__(256, 1)
   g.rank = 0;
   g.size = 1;
   g.local = true;
+  g.limit_ns = BARRIER_LIMIT_NS;
   g.flags = nullptr;
   g.partials = nullptr;
   g.epoch = 0;
@@ -1472,7 +1508,8 @@ __global__ void __launch_bounds__(256, 1)
     const int q = s_q;
     __syncthreads();
     if (q >= plan.n_small) break;
-    batch_one<T, CH>(probs, bufs, tws, o, plan.small_order[q], g, smraw, s_prob, s_bar, s_ok, s_prof, first, cycles);
+    const int pi = plan.small_order[q];
+    batch_one<T, CH>(probs, bufs[pi], tws, o, pi, g, smraw, s_prob, s_bar, s_ok, s_prof, first, cycles);
     first = false;
   }
 }
@@ -1495,7 +1532,7 @@ __device__ __forceinline__ long long ld_acquire_sys(const volatile long long* p)
 
 template <class T, int CH>
 __global__ void __launch_bounds__(256, 1)
-    k_serve(const Prob<T>* __restrict__ probs, const SolveBufs<T>* __restrict__ bufs,
+    k_serve(const Prob<T>* __restrict__ probs, const SolveBufs<T>* bufs,
             const int* __restrict__ tws, const ServeMeta<T>* __restrict__ meta, SolveOpts o,
             const ServeReq* ring, ServeRes* res, int cap, ServeCtl* ctl, ServeDev* dev,
             unsigned long long idle_ns) {
@@ -1510,6 +1547,7 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   Grid g;
   g.rank = 0; g.size = 1; g.local = true; g.flags = nullptr; g.partials = nullptr; g.epoch = 0;
+  g.limit_ns = BARRIER_LIMIT_NS;
   bool first = true;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -1556,7 +1594,7 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     const int pi = s_plant;
     const ServeMeta<T> M = meta[pi];
-    const SolveBufs<T> B = bufs[pi];
+    const SolveBufs<T> B = ld_struct_cg(bufs + pi);   // written by the host at admission
     for (int k = threadIdx.x; k < M.nx; k += blockDim.x)
       M.x0s[k] = (T)(M.Sx[k] * *reinterpret_cast<const volatile double*>(&rq->x0[k]));
     if (!s_warm)
@@ -1567,7 +1605,7 @@ __global__ void __launch_bounds__(256, 1)
     }
     __threadfence();
     __syncthreads();
-    batch_one<T, CH>(probs, bufs, tws, o, pi, g, smraw, s_prob, s_bar, s_ok, s_prof, first, nullptr);
+    batch_one<T, CH>(probs, B, tws, o, pi, g, smraw, s_prob, s_bar, s_ok, s_prof, first, nullptr);
     first = false;
     // result: u0 = u~0 / Su from T(v); the final iterate moved into V (warm start)
     const SolveCtl* c = B.ctl;

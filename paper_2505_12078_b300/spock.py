@@ -30,7 +30,8 @@ EXPORTED = [
     "spock_batch_create", "spock_batch_destroy", "spock_batch_sizes", "spock_batch_set_tw",
     "spock_batch_autotune", "spock_batch_solve",
     "spock_server_create", "spock_server_submit", "spock_server_poll", "spock_server_outstanding",
-    "spock_server_destroy",
+    "spock_server_destroy", "spock_check", "spock_debug_wait_fault", "spock_server_evict",
+    "spock_server_admitted",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -48,7 +49,8 @@ class Sizes(C.Structure):
     _fields_ = [("n", C.c_int), ("n_nonleaf", C.c_int), ("n_leaf", C.c_int), ("N", C.c_int),
                 ("nx", C.c_int), ("nu", C.c_int), ("n_c", C.c_int), ("n_cN", C.c_int),
                 ("n_z", C.c_longlong), ("n_eta", C.c_longlong), ("n_v", C.c_longlong),
-                ("factor_bytes_fp64", C.c_longlong), ("factor_bytes_fp32", C.c_longlong)]
+                ("factor_bytes_fp64", C.c_longlong), ("factor_bytes_fp32", C.c_longlong),
+                ("solve_bytes_fp64", C.c_longlong), ("solve_bytes_fp32", C.c_longlong)]
 
 
 class SolveOpts(C.Structure):
@@ -62,7 +64,8 @@ class Info(C.Structure):
                 ("n_K1", C.c_int), ("n_K2", C.c_int), ("n_fallback", C.c_int),
                 ("n_backtracks", C.c_int), ("res_inf", C.c_double), ("res_inf_fp64", C.c_double),
                 ("risk", C.c_double), ("device_ms", C.c_double), ("phase_ms", C.c_double * 7),
-                ("counters", C.c_double * 8)]
+                ("counters", C.c_double * 8), ("xi1", C.c_double), ("xi2", C.c_double),
+                ("infeas", C.c_double), ("gap", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -73,7 +76,14 @@ class Info(C.Structure):
 
 class BatchInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("n_T", C.c_int), ("tw", C.c_int),
-                ("res_inf", C.c_double), ("risk", C.c_double), ("device_ms", C.c_double)]
+                ("res_inf", C.c_double), ("risk", C.c_double), ("device_ms", C.c_double),
+                ("xi1", C.c_double), ("xi2", C.c_double), ("infeas", C.c_double), ("gap", C.c_double)]
+
+
+class CheckInfo(C.Structure):
+    _fields_ = [("res_inf", C.c_double), ("xi1", C.c_double), ("xi2", C.c_double),
+                ("infeas", C.c_double), ("gap", C.c_double), ("eta_Lz", C.c_double),
+                ("support", C.c_double)]
 
 
 class ServeResult(C.Structure):
@@ -111,6 +121,7 @@ def load(path: str = LIB_PATH):
     lib.spock_solve_opts_default.restype = None
     lib.spock_solve.argtypes = [vp, _dp, C.POINTER(SolveOpts), _dp, _dp, _dp, C.POINTER(Info)]
     lib.spock_solve_device.argtypes = [vp, vp, C.POINTER(SolveOpts), vp, vp, vp, C.POINTER(Info)]
+    lib.spock_check.argtypes = [vp, C.c_int, vp, vp, C.POINTER(CheckInfo)]
     lib.spock_get_iterate.argtypes = [vp, C.c_int, vp, vp]
     lib.spock_set_iterate.argtypes = [vp, C.c_int, vp, vp]
     lib.spock_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp)]
@@ -129,11 +140,20 @@ def load(path: str = LIB_PATH):
     lib.spock_server_outstanding.restype = C.c_longlong
     lib.spock_server_destroy.argtypes = [vp]
     lib.spock_server_destroy.restype = None
+    lib.spock_server_evict.argtypes = [vp, C.c_int]
+    lib.spock_server_admitted.argtypes = [vp, C.c_int]
     lib.spock_status_str.argtypes = [C.c_int]
     lib.spock_status_str.restype = C.c_char_p
     lib.spock_version.restype = C.c_int
+    lib.spock_debug_wait_fault.argtypes = [C.c_int, C.c_double]
     _lib = lib
     return lib
+
+
+def debug_wait_fault(phantom_ctas=0, wait_limit_s=0.0):
+    """Test hook (spock_debug_wait_fault): later single-problem launches wait for
+    phantom CTAs at their grid barriers and give up after wait_limit_s."""
+    _check(load().spock_debug_wait_fault(int(phantom_ctas), float(wait_limit_s)), "spock_debug_wait_fault")
 
 
 class SpockError(RuntimeError):
@@ -247,12 +267,26 @@ class Problem:
             return 32
         raise TypeError("float32 or float64 tensors only")
 
+    def _check_pair(self, v_in, v_out):
+        """v_in and v_out: contiguous CUDA tensors of n_v elements, same dtype
+        and device, distinct storage (the library writes n_v elements of
+        v_in's precision into v_out and reads v_in meanwhile)."""
+        assert v_in.is_cuda and v_in.is_contiguous() and v_in.numel() == self.n_v
+        assert v_out.is_cuda and v_out.is_contiguous() and v_out.numel() == self.n_v
+        if v_out.dtype != v_in.dtype or v_out.device != v_in.device:
+            raise TypeError("v_out must have v_in's dtype and device")
+        a0, a1 = v_in.data_ptr(), v_in.data_ptr() + v_in.numel() * v_in.element_size()
+        b0, b1 = v_out.data_ptr(), v_out.data_ptr() + v_out.numel() * v_out.element_size()
+        if a0 < b1 and b0 < a1:
+            raise ValueError("v_in and v_out must not overlap")
+
     def T(self, v_in, v_out=None, stream=None):
         """v_out = T(v_in); returns (v_out, stats[8])."""
         import torch
         assert v_in.is_cuda and v_in.is_contiguous() and v_in.numel() == self.n_v
         if v_out is None:
             v_out = torch.empty_like(v_in)
+        self._check_pair(v_in, v_out)
         stats = np.zeros(8)
         _check(load().spock_op_T(self.h, self._prec(v_in), C.c_void_p(v_in.data_ptr()),
                                  C.c_void_p(v_out.data_ptr()), _ptr(stats),
@@ -262,8 +296,7 @@ class Problem:
     def T_noalloc(self, v_in, v_out, stream=None):
         """v_out = T(v_in) through spock_op_T_noalloc (no device allocation in
         the call; scratch from the library's static device array)."""
-        assert v_in.is_cuda and v_in.is_contiguous() and v_in.numel() == self.n_v
-        assert v_out.is_cuda and v_out.is_contiguous() and v_out.numel() == self.n_v
+        self._check_pair(v_in, v_out)
         stats = np.zeros(8)
         _check(load().spock_op_T_noalloc(self.h, self._prec(v_in), C.c_void_p(v_in.data_ptr()),
                                          C.c_void_p(v_out.data_ptr()), _ptr(stats),
@@ -311,6 +344,16 @@ class Problem:
             C.c_void_p(u_out.data_ptr()) if u_out is not None else None,
             C.c_void_p(stream.cuda_stream if stream else 0), C.byref(info)), "spock_solve_device")
         return st, info.as_dict()
+
+    def check(self, v, stream=None):
+        """FP64 exit check (Sec. 5.3) of the iterate v (CUDA tensor, n_v): dict of
+        res_inf, xi1, xi2, infeas, gap, eta_Lz, support."""
+        assert v.is_cuda and v.is_contiguous() and v.numel() == self.n_v
+        out = CheckInfo()
+        _check(load().spock_check(self.h, self._prec(v), C.c_void_p(v.data_ptr()),
+                                  C.c_void_p(stream.cuda_stream if stream else 0), C.byref(out)),
+               "spock_check")
+        return {k: getattr(out, k) for k, _ in out._fields_}
 
     def get_iterate(self, precision=64):
         import torch
@@ -436,6 +479,13 @@ class Server:
 
     def outstanding(self):
         return load().spock_server_outstanding(self.h)
+
+    def evict(self, plant):
+        """Release the plant's solve buffers (spock_server_evict)."""
+        _check(load().spock_server_evict(self.h, int(plant)), "evict")
+
+    def is_admitted(self, plant):
+        return bool(_check(load().spock_server_admitted(self.h, int(plant)), "admitted"))
 
     def drain(self, timeout_s=60.0):
         import time

@@ -39,6 +39,8 @@ CASES = {
     "chain_only": lambda: constrained([1, 1, 1, 1, 1], 6, 3, seed=24, avar=0.2),
     "minimal_n2": lambda: constrained([1], 3, 2, seed=25, avar=1.0),
     "avar0_branch8": lambda: constrained([8, 1], 9, 4, seed=26, avar=0.0, uball=1.0),
+    # nx + nu = 150 > 128: team sweeps (8 warps per team), widest mat-vec variants
+    "team_100x50": lambda: constrained([2, 1, 1], 100, 50, seed=27, avar=0.5, uball=3.0),
 }
 
 
@@ -135,7 +137,7 @@ def test_fixed_iterations_cp_fp64(name):
     assert abs(res["risk"] - ref["risk"]) <= 1e-10 * max(1, abs(ref["risk"]))
 
 
-@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40"])
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "team_100x50"])
 def test_fixed_iterations_spock_fp64(name):
     """SPOCK (Alg. 4 with Anderson directions) for a fixed iteration count in
     FP64: same branch sequence counts and iterate within 1e-10 relative."""
@@ -170,3 +172,58 @@ def test_converged_fp32_vs_oracle(name):
     assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= 1e-3 * max(1.0, np.max(np.abs(ref["u"][0])))
     assert res["info"]["res_inf_fp64"] < 5e-4
     assert np.all(np.abs(res["x"]) <= 5 + 1e-2)
+
+
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "avar0_branch8"])
+def test_fp64_check_matches_oracle(name):
+    """FP64 exit check (Sec. 5.3) through spock_check on the oracle's own
+    iterate after 25 SPOCK iterations: xi1, xi2 (Eq. xi1k), the primal
+    infeasibility and the two terms of the complementarity gap against the
+    oracle's diagnostics of the same point. The GPU evaluates T in FP64 itself,
+    so the quantities agree to the one-T parity (1e-11 of max|v|) divided by
+    alpha (xi1, xi2 divide v - T(v) by alpha)."""
+    p, o, g = _pair(name)
+    g.set_alpha(o.alpha)
+    g.set_x0(p.x0)
+    ref = o.solve(tol=0.0, max_iters=25)
+    v = ref["v"]
+    c = g.check(torch.tensor(v, device="cuda"))
+    scale = 1e-10 * max(1.0, float(np.max(np.abs(v)))) / o.alpha
+    assert abs(c["res_inf"] - ref["res_inf"]) <= scale * o.alpha
+    assert abs(c["xi1"] - ref["xi1"]) <= scale, (c["xi1"], ref["xi1"])
+    assert abs(c["xi2"] - ref["xi2"]) <= scale, (c["xi2"], ref["xi2"])
+    assert abs(c["infeas"] - ref["infeas"]) <= scale, (c["infeas"], ref["infeas"])
+    nz = o.lay.n_z
+    tv = ref["Tv"]
+    Lz = o.apply_L(tv[:nz])
+    dot = float(tv[nz:] @ Lz)
+    sup = o.support_S3(tv[nz:])
+    mag = 1e-10 * (float(np.sum(np.abs(tv[nz:] * Lz))) + abs(sup) + 1.0)
+    assert abs(c["eta_Lz"] - dot) <= mag
+    assert abs(c["support"] - sup) <= mag
+    assert abs(c["gap"] - ref["gap"]) <= 2 * mag
+
+
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball"])
+def test_solve_reports_fp64_check(name):
+    """spock_solve returns the FP64 exit check of its final iterate: for an FP64
+    solve of a fixed iteration count it equals the oracle's diagnostics of the
+    oracle's iterate (the iterates agree to 1e-10); for an FP32 solve it equals
+    spock_check of the FP32 iterate."""
+    p, o, g = _pair(name)
+    g.set_alpha(o.alpha)
+    spock = _spock()
+    ref = o.solve(tol=0.0, max_iters=25)
+    res = g.solve(p.x0, spock.opts(precision=64, tol=0.0, max_iters=25))
+    inf = res["info"]
+    scale = 1e-9 * max(1.0, float(np.max(np.abs(ref["v"])))) / o.alpha
+    for k in ("xi1", "xi2", "infeas"):
+        assert abs(inf[k] - ref[k]) <= scale, (k, inf[k], ref[k])
+    assert abs(inf["gap"] - ref["gap"]) <= 1e-8 * max(1.0, abs(ref["gap"]))
+    r32 = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000))
+    c = g.check(g.get_iterate(32))
+    for k in ("xi1", "xi2", "infeas", "gap"):
+        assert r32["info"][k] == c[k], k
+    assert r32["info"]["res_inf_fp64"] == c["res_inf"]
+    # near the solution every measure is small (Sec. 5.3)
+    assert max(c["xi1"], c["xi2"]) < 5e-3 / o.alpha and c["infeas"] < 5e-3

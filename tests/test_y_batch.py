@@ -151,3 +151,92 @@ def test_batch_team_widths_and_autotune(plants):
         assert _relerr(g.get_iterate(64).cpu().numpy(), ref[k]) < 1e-12
     assert res["status"] in (0, 1)
     b.close()
+
+
+# --- the gang path: problems whose T moves more than 4 MB get a gang of CTAs ---
+@pytest.fixture(scope="module")
+def gang_mix():
+    """Two problems above the gang threshold (FP64: about 5.6 MB and 4.5 MB of
+    factors per T) mixed with two small ones from the uneven generator."""
+    spock = _spock()
+    from tests.problems import constrained
+    probs = [constrained([3, 3, 1, 1, 1], 64, 32, seed=41, avar=0.4, uball=2.5),     # 40 nodes
+             constrained([2, 2, 2, 1, 1, 1, 1, 1], 48, 24, seed=42, avar=0.7)]      # 55 nodes
+    probs += [synth.batch_problem(s, i) for i, s in _small_specs(2)]
+    items = []
+    for p in probs:
+        o = Oracle(p)
+        g = spock.Problem(p)
+        g.set_alpha(o.alpha)
+        items.append((p, o, g))
+    return items
+
+
+def test_gang_problems_are_ganged(gang_mix):
+    """The byte count that sizes a gang exceeds the 4 MB unit for the two large
+    problems (factors of both sweeps, FP64)."""
+    for p, _, g in gang_mix[:2]:
+        s = g.sizes
+        assert s["factor_bytes_fp64"] > 4.0e6, s["factor_bytes_fp64"]
+
+
+def test_gang_batch_fixed_spock_fp64(gang_mix):
+    """SPOCK for a fixed count in FP64 with gangs of CTAs iterating on the two
+    large problems (flag barriers and reductions among the gang's CTAs): the
+    oracle's T count and K0/K1/K2 branches and the iterate within 1e-10, for
+    every problem of the mix."""
+    spock = _spock()
+    b = spock.Batch([g for _, _, g in gang_mix], precision=64)
+    iters = 25
+    res = b.solve([p.x0 for p, _, _ in gang_mix], spock.opts(precision=64, tol=0.0, max_iters=iters))
+    for k, (p, o, g) in enumerate(gang_mix):
+        ref = o.solve(tol=0.0, max_iters=iters, method="spock")
+        assert res["info"][k]["n_T"] == ref["n_T"], k
+        assert _relerr(g.get_iterate(64).cpu().numpy(), ref["v"]) < 1e-10, k
+        assert abs(res["risk"][k] - ref["risk"]) <= 1e-10 * max(1.0, abs(ref["risk"])), k
+    b.close()
+
+
+def test_gang_batch_fixed_cp_fp64(gang_mix):
+    spock = _spock()
+    b = spock.Batch([g for _, _, g in gang_mix], precision=64)
+    iters = 40
+    b.solve([p.x0 for p, _, _ in gang_mix], spock.opts(precision=64, tol=0.0, max_iters=iters, method="cp"))
+    for k, (p, o, g) in enumerate(gang_mix):
+        ref = o.solve(tol=0.0, max_iters=iters, method="cp")
+        assert _relerr(g.get_iterate(64).cpu().numpy(), ref["v"]) < 1e-10, k
+    b.close()
+
+
+def test_gang_alone_equals_mix_fp32(gang_mix):
+    """A ganged problem gives bit-identical results alone (a batch of one, same
+    gang size) and in the mix."""
+    spock = _spock()
+    o32 = spock.opts(precision=32, tol=1e-4, max_iters=400)
+    mix = spock.Batch([g for _, _, g in gang_mix], precision=32)
+    rm = mix.solve([p.x0 for p, _, _ in gang_mix], o32)
+    tws = [i["tw"] for i in rm["info"]]
+    mix.close()
+    for k in (0, 1):
+        p, _, g = gang_mix[k]
+        one = spock.Batch([g], precision=32)
+        one.set_tw([tws[k]])
+        r1 = one.solve([p.x0], o32)
+        assert np.array_equal(r1["x"][0], rm["x"][k]), k
+        assert np.array_equal(r1["u"][0], rm["u"][k]), k
+        assert r1["risk"][0] == rm["risk"][k] and r1["info"][0]["iters"] == rm["info"][k]["iters"]
+        one.close()
+
+
+def test_batch_fp64_check_per_problem(gang_mix):
+    """With fp64_check the batch reports each problem's FP64 exit check (Sec.
+    5.3), equal to spock_check of the problem's final iterate."""
+    spock = _spock()
+    b = spock.Batch([g for _, _, g in gang_mix], precision=32)
+    res = b.solve([p.x0 for p, _, _ in gang_mix],
+                  spock.opts(precision=32, tol=1e-4, max_iters=300, fp64_check=True))
+    for k, (_, _, g) in enumerate(gang_mix):
+        c = g.check(g.get_iterate(32))
+        for key in ("xi1", "xi2", "infeas", "gap"):
+            assert res["info"][k][key] == c[key], (k, key)
+    b.close()

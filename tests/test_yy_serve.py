@@ -128,9 +128,7 @@ def test_serve_receding_horizon_warm_start(plants):
     assert abs(rw["risk"] - rc["risk"]) <= 2e-3 * max(1.0, abs(rc["risk"]))
 
 
-def test_serve_admission_by_memory_budget():
-    """Plants are admitted in order while their solve buffers fit the budget;
-    a request for a refused plant gets ENOMEM, the admitted ones are served."""
+def _fresh_pair():
     spock = _spock()
     fresh = []
     for i, sp in enumerate(synth.batch_specs(400, seed=4)):
@@ -138,13 +136,19 @@ def test_serve_admission_by_memory_budget():
             fresh.append(synth.batch_problem(sp, i))
         if len(fresh) == 2:
             break
-    G = [spock.Problem(p) for p in fresh]          # no solve buffers yet
+    return fresh, [spock.Problem(p) for p in fresh]          # no solve buffers yet
+
+
+def test_serve_admission_by_memory_budget():
+    """Plants are admitted in order while their solve buffers fit the budget;
+    a request for a refused plant gets ENOMEM, the admitted ones are served."""
+    spock = _spock()
+    fresh, G = _fresh_pair()
     o = spock.opts(precision=32, tol=1e-4, max_iters=20000)
     with pytest.raises(spock.SpockError) as e:
         spock.Server(G, precision=32, o=o, mem_budget=1)
     assert e.value.code == -2
-    w = 4
-    need0 = w * (7 * G[0].n_v + 6 * ((G[0].n_v + 3) // 4 * 4)) + 2000 + 64 * 1024
+    need0 = G[0].sizes["solve_bytes_fp32"]
     srv = spock.Server(G, precision=32, o=o, mem_budget=need0 + 1024)
     assert srv.status == 2 and srv.admitted == 1
     with pytest.raises(spock.SpockError) as e2:
@@ -154,3 +158,40 @@ def test_serve_admission_by_memory_budget():
     res = _wait(srv, 1)
     srv.close()
     assert res[rid]["status"] == 0
+
+
+def test_serve_evict_then_admit_refused_plant():
+    """A plant refused for lack of budget is admitted by its next request once
+    another plant has been evicted (its bytes return to the budget); the
+    re-admitted plant is served and gives the same result as in a server that
+    admitted it from the start. Evicting a plant with a request outstanding is
+    refused."""
+    spock = _spock()
+    fresh, G = _fresh_pair()
+    o = spock.opts(precision=32, tol=1e-4, max_iters=20000)
+    budget = max(G[0].sizes["solve_bytes_fp32"], G[1].sizes["solve_bytes_fp32"]) + 1024
+    srv = spock.Server(G, precision=32, o=o, mem_budget=budget)
+    assert srv.admitted == 1 and srv.is_admitted(0) and not srv.is_admitted(1)
+    r0 = srv.submit(0, fresh[0].x0, warm=False)
+    with pytest.raises(spock.SpockError) as e:
+        srv.evict(0)                       # its request is outstanding
+    assert e.value.code == -1
+    _wait(srv, 1)
+    with pytest.raises(spock.SpockError):
+        srv.submit(1, fresh[1].x0, warm=False)
+    srv.evict(0)
+    assert not srv.is_admitted(0)
+    r1 = srv.submit(1, fresh[1].x0, warm=False)
+    assert srv.is_admitted(1)
+    got = _wait(srv, 1)[r1]
+    with pytest.raises(spock.SpockError):          # plant 0 no longer fits
+        srv.submit(0, fresh[0].x0, warm=False)
+    srv.close()
+    assert got["status"] == 0
+    # the same request in a server that holds plant 1 from the start
+    G2 = [spock.Problem(p) for p in fresh]
+    srv2 = spock.Server([G2[1]], precision=32, o=o)
+    q = srv2.submit(0, fresh[1].x0, warm=False)
+    ref = _wait(srv2, 1)[q]
+    srv2.close()
+    assert np.array_equal(got["u0"], ref["u0"]) and got["risk"] == ref["risk"] and got["iters"] == ref["iters"]
