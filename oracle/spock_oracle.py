@@ -31,8 +31,12 @@ first n_nl nodes are the non-leaf nodes, the last n_l the leaves.
         eta_y^i  = y^i, eta_s^i = s^i - b^i'y^i, eta_c^i = Gx x^i + Gu u^i,
         eta_q^c  = (Q^c^(1/2) x^anc, R^c^(1/2) u^anc, tau^c/2, tau^c/2),
         eta_cN^j = GN x^j, eta_qN^j = (QN^j^(1/2) x^j, s^j/2, s^j/2).
-  Constraint rows of a non-leaf node: [x box (nx)] [u box (nu)] [u ball (nu)],
-  each kind present or absent for the whole problem; leaf rows: [x box (nx)].
+  Constraint rows of a non-leaf node: [x box (nx)] [u box (nu)] [u ball (nu)]
+  [general rows Gx x + Gu u (n_g)], each kind present or absent for the whole
+  problem; leaf rows: [x box (nx)] [general rows GN x (n_gN)]. Q^(1/2) is the
+  elementwise root of a diagonal weight or the upper Cholesky factor of a
+  full one. Linear cost terms q, r, q_N enter only through the translation a
+  of each cost cone (Prop. 1), not through L.
 """
 from __future__ import annotations
 
@@ -228,9 +232,11 @@ class Oracle:
         self.has_xbox = prob.x_lo is not None
         self.has_ubox = prob.u_lo is not None
         self.has_uball = prob.u_ball is not None
+        self.n_g = 0 if getattr(prob, "Gx", None) is None else int(np.asarray(prob.Gx).shape[0])
+        self.n_gN = 0 if getattr(prob, "GN", None) is None else int(np.asarray(prob.GN).shape[0])
         self.n_c = (nx if self.has_xbox else 0) + (nu if self.has_ubox else 0) + \
-                   (nu if self.has_uball else 0)
-        self.n_cN = nx if self.has_xbox else 0
+                   (nu if self.has_uball else 0) + self.n_g
+        self.n_cN = (nx if self.has_xbox else 0) + self.n_gN
         self._layout()
         self._precondition()
         self._offline_s1()
@@ -317,7 +323,8 @@ class Oracle:
             self.QNh = self._sqrt_weight(P.QN) / SxN_leaf[:, None, :]
         else:
             self.QNh = np.sqrt(QNd) / SxN_leaf
-        # constraint matrices of a non-leaf node (unscaled): selection rows
+        # constraint matrices of a non-leaf node (unscaled, Eq. constraints):
+        # selection rows of the boxes and the ball, then the general rows
         Gx, Gu = [], []
         if self.has_xbox:
             Gx.append(np.eye(nx)); Gu.append(np.zeros((nx, nu)))
@@ -325,6 +332,8 @@ class Oracle:
             Gx.append(np.zeros((nu, nx))); Gu.append(np.eye(nu))
         if self.has_uball:
             Gx.append(np.zeros((nu, nx))); Gu.append(np.eye(nu))
+        if self.n_g:
+            Gx.append(np.asarray(P.Gx, dtype=np.float64)); Gu.append(np.asarray(P.Gu, dtype=np.float64))
         if self.n_c:
             Gx = np.vstack(Gx)
             Gu = np.vstack(Gu)
@@ -337,7 +346,12 @@ class Oracle:
             self.Gx = np.zeros((0, nx))
             self.Gu = np.zeros((0, nu))
         if self.n_cN:
-            MN = np.eye(nx) / self.SxN[None, :]
+            GN = []
+            if self.has_xbox:
+                GN.append(np.eye(nx))
+            if self.n_gN:
+                GN.append(np.asarray(P.GN, dtype=np.float64))
+            MN = np.vstack(GN) / self.SxN[None, :]
             self.a_conN = max(1.0, float(np.linalg.norm(MN, 2)))
             self.GN = MN / self.a_conN
         else:
@@ -353,11 +367,70 @@ class Oracle:
         self.box_hi = (np.hstack(hi) / self.a_con) if hi else np.zeros((n_nl, 0))
         self.n_box = self.box_lo.shape[1]
         self.ball_r = (np.asarray(P.u_ball, dtype=np.float64) / self.a_con) if self.has_uball else None
+        if self.n_g:
+            self.gen_lo = np.asarray(P.g_lo, dtype=np.float64) / self.a_con
+            self.gen_hi = np.asarray(P.g_hi, dtype=np.float64) / self.a_con
         if self.n_cN:
-            self.boxN_lo = P.x_lo[n_nl:] / self.a_conN
-            self.boxN_hi = P.x_hi[n_nl:] / self.a_conN
+            lo, hi = [], []
+            if self.has_xbox:
+                lo.append(P.x_lo[n_nl:]); hi.append(P.x_hi[n_nl:])
+            if self.n_gN:
+                lo.append(np.asarray(P.gN_lo, dtype=np.float64)); hi.append(np.asarray(P.gN_hi, dtype=np.float64))
+            self.boxN_lo = np.hstack(lo) / self.a_conN
+            self.boxN_hi = np.hstack(hi) / self.a_conN
+        self._cost_translations()
         self.avar_level = np.asarray(P.avar, dtype=np.float64)
         self.x0s = self.Sx * np.asarray(P.x0, dtype=np.float64)
+
+    def _cost_translations(self):
+        """Translation vectors of the cost cones (Prop. 1, quadratic-plus-linear
+        costs, Q positive definite so S = I): the epigraph of z'Qz + q'z is
+        {(z, tau) : (F z, tau/2, tau/2) - a in SOC} with F any factor with
+        F'F = Q (the one L uses) and a = (-F^{-T} q / 2, -kappa/8 + 1/2,
+        -kappa/8 - 1/2), kappa = q'Q^{-1}q = ||F^{-T} q||^2. For an edge cost
+        F = blockdiag(F_Q, F_R) acts on (x, u). The diagonal scalings of Sec. 5.4
+        leave a unchanged (F S^{-1} and S^{-1} q give the same F^{-T} q). Without
+        linear terms a = (0, 1/2, -1/2)."""
+        P, tr = self.P, self.tree
+        nx, nu, n = self.nx, self.nu, tr.n
+        W = nx + nu + 2
+        self.a_q = np.zeros((n - 1, W))
+        self.a_q[:, -2] = 0.5
+        self.a_q[:, -1] = -0.5
+        self.a_qN = np.zeros((tr.n_l, nx + 2))
+        self.a_qN[:, -2] = 0.5
+        self.a_qN[:, -1] = -0.5
+        q = getattr(P, "q", None)
+        r = getattr(P, "r", None)
+        qN = getattr(P, "qN", None)
+
+        def ftq(Wm, lin):
+            # F^{-T} lin with F the factor of Wm used by L (upper Cholesky factor
+            # for full matrices, elementwise root for diagonals)
+            Wm = np.asarray(Wm, dtype=np.float64)
+            if Wm.ndim == 2:
+                return lin / np.sqrt(Wm)
+            Lc = np.linalg.cholesky(Wm)                    # Wm = Lc Lc', F = Lc', F^{-T} = Lc^{-1}
+            return np.linalg.solve(Lc, lin[..., None])[..., 0]
+
+        if q is not None or r is not None:
+            kap = np.zeros(n - 1)
+            if q is not None:
+                w = ftq(P.Q, np.asarray(q, dtype=np.float64))
+                self.a_q[:, :nx] = -0.5 * w
+                kap += np.sum(w * w, axis=1)
+            if r is not None:
+                w = ftq(P.R, np.asarray(r, dtype=np.float64))
+                self.a_q[:, nx:nx + nu] = -0.5 * w
+                kap += np.sum(w * w, axis=1)
+            self.a_q[:, -2] -= kap / 8.0
+            self.a_q[:, -1] -= kap / 8.0
+        if qN is not None:
+            w = ftq(P.QN, np.asarray(qN, dtype=np.float64))
+            self.a_qN[:, :nx] = -0.5 * w
+            kap = np.sum(w * w, axis=1)
+            self.a_qN[:, -2] -= kap / 8.0
+            self.a_qN[:, -1] -= kap / 8.0
 
     @staticmethod
     def _diag(W):
@@ -588,19 +661,20 @@ class Oracle:
             C = v[lay.e_c:lay.e_q].reshape(tr.n_nl, self.n_c).copy()
             nb = self.n_box
             C[:, :nb] = np.clip(C[:, :nb], self.box_lo, self.box_hi)
+            nbl = nb + (nu if self.has_uball else 0)
             if self.has_uball:
-                C[:, nb:] = proj_ball(C[:, nb:], self.ball_r)
+                C[:, nb:nbl] = proj_ball(C[:, nb:nbl], self.ball_r)
+            if self.n_g:
+                C[:, nbl:] = np.clip(C[:, nbl:], self.gen_lo, self.gen_hi)
             out[lay.e_c:lay.e_q] = C.ravel()
         w = nx + nu + 2
-        a = np.zeros(w); a[-2] = 0.5; a[-1] = -0.5
         Qb = v[lay.e_q:lay.e_cN].reshape(tr.n - 1, w)
-        out[lay.e_q:lay.e_cN] = (a + proj_soc(Qb - a)).ravel()
+        out[lay.e_q:lay.e_cN] = (self.a_q + proj_soc(Qb - self.a_q)).ravel()
         if self.n_cN:
             CN = v[lay.e_cN:lay.e_qN].reshape(tr.n_l, self.n_cN)
             out[lay.e_cN:lay.e_qN] = np.clip(CN, self.boxN_lo, self.boxN_hi).ravel()
-        aN = np.zeros(nx + 2); aN[-2] = 0.5; aN[-1] = -0.5
         QN = v[lay.e_qN:].reshape(tr.n_l, nx + 2)
-        out[lay.e_qN:] = (aN + proj_soc(QN - aN)).ravel()
+        out[lay.e_qN:] = (self.a_qN + proj_soc(QN - self.a_qN)).ravel()
         return out
 
     def prox_gconj(self, v):
@@ -768,16 +842,19 @@ class Oracle:
             C = eta[lay.e_c:lay.e_q].reshape(tr.n_nl, self.n_c)
             nb = self.n_box
             val += float(np.sum(np.maximum(C[:, :nb] * self.box_lo, C[:, :nb] * self.box_hi)))
+            nbl = nb + (nu if self.has_uball else 0)
             if self.has_uball:
-                val += float(np.sum(self.ball_r * np.linalg.norm(C[:, nb:], axis=1)))
+                val += float(np.sum(self.ball_r * np.linalg.norm(C[:, nb:nbl], axis=1)))
+            if self.n_g:
+                val += float(np.sum(np.maximum(C[:, nbl:] * self.gen_lo, C[:, nbl:] * self.gen_hi)))
         w = nx + nu + 2
         Qb = eta[lay.e_q:lay.e_cN].reshape(tr.n - 1, w)
-        val += float(np.sum(0.5 * Qb[:, -2] - 0.5 * Qb[:, -1]))
+        val += float(np.sum(Qb * self.a_q))
         if self.n_cN:
             CN = eta[lay.e_cN:lay.e_qN].reshape(tr.n_l, self.n_cN)
             val += float(np.sum(np.maximum(CN * self.boxN_lo, CN * self.boxN_hi)))
         QN = eta[lay.e_qN:].reshape(tr.n_l, nx + 2)
-        val += float(np.sum(0.5 * QN[:, -2] - 0.5 * QN[:, -1]))
+        val += float(np.sum(QN * self.a_qN))
         return val
 
     def nested_values(self, x, u):
@@ -789,19 +866,15 @@ class Oracle:
         V = np.zeros(tr.n)
         mu = np.zeros(tr.n)
         mu[0] = 1.0
-        dense = np.ndim(P.Q) == 3
         for jj in range(tr.n_l):
             j = tr.n_nl + jj
-            QN = P.QN[jj] if np.ndim(P.QN) == 3 else np.diag(P.QN[jj])
-            V[j] = x[j] @ QN @ x[j]
+            V[j] = self.terminal_cost(jj, x[j])
         for t in range(tr.N - 1, -1, -1):
             for i in tr.nodes_at[t]:
                 ch = tr.children[i]
                 Z = []
                 for c in ch:
-                    Qc = P.Q[c - 1] if dense else np.diag(P.Q[c - 1])
-                    Rc = P.R[c - 1] if np.ndim(P.R) == 3 else np.diag(P.R[c - 1])
-                    Z.append(x[i] @ Qc @ x[i] + u[i] @ Rc @ u[i] + V[c])
+                    Z.append(self.edge_cost(c, x[i], u[i]) + V[c])
                 Z = np.asarray(Z)
                 V[i] = avar(Z, tr.prob[ch], self.avar_level[i])
                 mu[ch] = avar_maximiser(Z, tr.prob[ch], self.avar_level[i])
@@ -818,24 +891,31 @@ class Oracle:
             w[i] = w[self.tree.anc[i]] * mu[i]
         return w
 
+    def edge_cost(self, c, x, u):
+        """l^c(x, u) = x'Q^c x + u'R^c u + q^c'x + r^c'u on the ancestor's state
+        and input (Sec. 3.2, quadratic-plus-linear costs), original data."""
+        P = self.P
+        Qc = P.Q[c - 1] if np.ndim(P.Q) == 3 else np.diag(P.Q[c - 1])
+        Rc = P.R[c - 1] if np.ndim(P.R) == 3 else np.diag(P.R[c - 1])
+        val = x @ Qc @ x + u @ Rc @ u
+        if getattr(P, "q", None) is not None:
+            val += P.q[c - 1] @ x
+        if getattr(P, "r", None) is not None:
+            val += P.r[c - 1] @ u
+        return float(val)
+
+    def terminal_cost(self, jj, x):
+        """l_N^j(x) = x'Q_N^j x + q_N^j'x for the jj-th leaf."""
+        P = self.P
+        QN = P.QN[jj] if np.ndim(P.QN) == 3 else np.diag(P.QN[jj])
+        val = x @ QN @ x
+        if getattr(P, "qN", None) is not None:
+            val += P.qN[jj] @ x
+        return float(val)
+
     def nested_risk(self, x, u):
         """Nested risk of a trajectory (Eq. original-problem) with the original
-        (unscaled) costs: leaves V = x'Q_N x; a non-leaf node takes
-        AV@R_{a_i} over its children of l^c(x^i, u^i) + V^c (Sec. 3.4)."""
-        P, tr = self.P, self.tree
-        V = np.zeros(tr.n)
-        dense = np.ndim(P.Q) == 3
-        for jj in range(tr.n_l):
-            j = tr.n_nl + jj
-            QN = P.QN[jj] if np.ndim(P.QN) == 3 else np.diag(P.QN[jj])
-            V[j] = x[j] @ QN @ x[j]
-        for t in range(tr.N - 1, -1, -1):
-            for i in tr.nodes_at[t]:
-                ch = tr.children[i]
-                Z = []
-                for c in ch:
-                    Qc = P.Q[c - 1] if dense else np.diag(P.Q[c - 1])
-                    Rc = P.R[c - 1] if np.ndim(P.R) == 3 else np.diag(P.R[c - 1])
-                    Z.append(x[i] @ Qc @ x[i] + u[i] @ Rc @ u[i] + V[c])
-                V[i] = avar(np.asarray(Z), tr.prob[ch], self.avar_level[i])
+        (unscaled) costs: leaves V = l_N(x); a non-leaf node takes AV@R_{a_i}
+        over its children of l^c(x^i, u^i) + V^c (Sec. 3.4)."""
+        V, _ = self.nested_values(x, u)
         return float(V[0])

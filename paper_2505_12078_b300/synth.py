@@ -57,6 +57,19 @@ class RAOCP:
     avar: np.ndarray         # float64 [n_nonleaf], AV@R level in [0, 1]
     x0: np.ndarray           # float64 [nx]
     meta: dict = field(default_factory=dict)
+    # Optional parts of the problem statement (Sec. 3.1-3.2); None = absent.
+    # Q, R, QN above may also be full matrices [.., nx, nx] / [.., nu, nu]
+    # (symmetric positive definite) instead of diagonals.
+    q: Optional[np.ndarray] = None      # float64 [n-1, nx] linear edge cost on x^anc(c)
+    r: Optional[np.ndarray] = None      # float64 [n-1, nu] linear edge cost on u^anc(c)
+    qN: Optional[np.ndarray] = None     # float64 [n_leaf, nx] linear terminal cost
+    Gx: Optional[np.ndarray] = None     # float64 [n_g, nx] general rows at every non-leaf node:
+    Gu: Optional[np.ndarray] = None     # float64 [n_g, nu]   g_lo <= Gx x + Gu u <= g_hi
+    g_lo: Optional[np.ndarray] = None   # float64 [n_nonleaf, n_g]
+    g_hi: Optional[np.ndarray] = None
+    GN: Optional[np.ndarray] = None     # float64 [n_gN, nx] general rows at every leaf:
+    gN_lo: Optional[np.ndarray] = None  # float64 [n_leaf, n_gN]   gN_lo <= GN x <= gN_hi
+    gN_hi: Optional[np.ndarray] = None
 
     @property
     def n(self) -> int:

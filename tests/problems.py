@@ -1,5 +1,7 @@
 """Small hand-built problems used by the tests (built from the seeded
 generators' building blocks; no solver arithmetic here)."""
+import math
+
 import numpy as np
 
 from paper_2505_12078_b300 import synth
@@ -58,3 +60,56 @@ def from_spec(d, name="golden"):
         np.full((n, nx), -xb), np.full((n, nx), xb), np.full((n_nl, nu), -ub), np.full((n_nl, nu), ub),
         np.full(n_nl, float(d["u_ball"])), np.full(n_nl, float(d["avar"])),
         np.asarray(d["x0"], dtype=np.float64), meta=dict(N=int(st.max())))
+
+
+def general(branching, nx, nu, seed, avar=1.0, dense=True, linear=True, n_g=0, n_gN=0, box=False,
+            spread=0.1, g_scale=0.6, lin_scale=0.3):
+    """Tree with dense positive definite Q, R, Q_N (or random diagonals),
+    linear cost terms q, r, q_N, and optional general constraint rows
+    g_lo <= Gx x + Gu u <= g_hi (non-leaf) and gN_lo <= GN x <= gN_hi (leaves)
+    with random Gx, Gu, GN and bounds of random width around zero."""
+    rng = np.random.default_rng(seed)
+    anc, prob = synth.tree_from_branching(branching, rng)
+    n = len(anc)
+    n_leaf = int(np.prod(branching))
+    n_nl = n - n_leaf
+
+    def spd(k, m):
+        M = rng.standard_normal((k, m, m)) / math.sqrt(m)
+        return M @ np.transpose(M, (0, 2, 1)) + 0.5 * np.eye(m)[None]
+
+    A = np.eye(nx) + spread * rng.standard_normal((n - 1, nx, nx))
+    B = rng.standard_normal((n - 1, nx, nu))
+    if dense:
+        Q, R, QN = spd(n - 1, nx), spd(n - 1, nu), spd(n_leaf, nx)
+    else:
+        Q, R, QN = rng.uniform(0.5, 2.0, (n - 1, nx)), rng.uniform(0.5, 2.0, (n - 1, nu)), \
+            rng.uniform(0.5, 2.0, (n_leaf, nx))
+    x0 = rng.uniform(-1.0, 1.0, nx)
+    p = synth.RAOCP(f"general_{branching}", anc, prob, nx, nu, A, B, np.zeros((n - 1, nx)), Q, R, QN,
+                    None, None, None, None, None, np.full(n_nl, float(avar)), x0, meta=dict(N=len(branching)))
+    if box:
+        p.x_lo, p.x_hi = np.full((n, nx), -5.0), np.full((n, nx), 5.0)
+        p.u_lo, p.u_hi = np.full((n_nl, nu), -2.0), np.full((n_nl, nu), 2.0)
+    if linear:
+        p.q = lin_scale * rng.standard_normal((n - 1, nx))
+        p.r = lin_scale * rng.standard_normal((n - 1, nu))
+        p.qN = lin_scale * rng.standard_normal((n_leaf, nx))
+    # general rows: bounds of random width around the rows' values on the
+    # trajectory with u = 0 (so every problem is feasible)
+    xr = np.zeros((n, nx))
+    xr[0] = x0
+    for c in range(1, n):
+        xr[c] = A[c - 1] @ xr[anc[c]]
+    if n_g:
+        p.Gx = rng.standard_normal((n_g, nx))
+        p.Gu = rng.standard_normal((n_g, nu))
+        mid = xr[:n_nl] @ p.Gx.T
+        p.g_lo = mid - g_scale * rng.uniform(0.5, 1.5, (n_nl, n_g))
+        p.g_hi = mid + g_scale * rng.uniform(0.5, 1.5, (n_nl, n_g))
+    if n_gN:
+        p.GN = rng.standard_normal((n_gN, nx))
+        mid = xr[n_nl:] @ p.GN.T
+        p.gN_lo = mid - g_scale * rng.uniform(0.5, 1.5, (n_leaf, n_gN))
+        p.gN_hi = mid + g_scale * rng.uniform(0.5, 1.5, (n_leaf, n_gN))
+    return p

@@ -13,7 +13,7 @@ import scipy.optimize as so
 from oracle import spock_oracle as so_
 from oracle.spock_oracle import Oracle
 from paper_2505_12078_b300 import synth
-from tests.problems import constrained, unconstrained
+from tests.problems import constrained, general, unconstrained
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -581,3 +581,197 @@ def test_supermann_k1_then_k0_on_half_map():
     assert [e[1] for e in r["events"]] == ["K1", "K0", "K0", "K0"]
     assert r["n_T"] == 5
     np.testing.assert_allclose(r["v"], np.array([4.0, -2.0]) / 16.0, rtol=1e-15)
+
+
+# --- quadratic-plus-linear costs, full weights, general constraint rows ----------
+def _qp_interior_point(Pq, qq, Gq, hq, tol=1e-12, iters=300):
+    """min 1/2 u'Pq u + qq'u s.t. Gq u <= hq by a primal-dual interior-point
+    method with Mehrotra's predictor-corrector (slacks s, multipliers z):
+    Newton steps on Pq u + qq + Gq'z = 0, Gq u + s = hq, s z = sigma mu."""
+    n, m = Pq.shape[0], Gq.shape[0]
+    u = np.zeros(n)
+    s_ = np.maximum(hq - Gq @ u, 1.0)
+    z = np.ones(m)
+    sd = 1.0 + np.max(np.abs(qq))
+    sp = 1.0 + np.max(np.abs(hq))
+    for _ in range(iters):
+        rd = Pq @ u + qq + Gq.T @ z
+        rp = Gq @ u + s_ - hq
+        mu = s_ @ z / m
+        if np.max(np.abs(rd)) < tol * sd and np.max(np.abs(rp)) < tol * sp and mu < tol * sd * sp:
+            return u
+        Kmat = Pq + Gq.T @ ((z / s_)[:, None] * Gq)
+
+        def step(rc):
+            du = np.linalg.solve(Kmat, -rd - Gq.T @ ((z / s_) * rp) + Gq.T @ (rc / s_))
+            dz = (z / s_) * (Gq @ du + rp) - rc / s_
+            ds = -(rc + s_ * dz) / z
+            return du, ds, dz
+
+        def maxstep(x, dx):
+            neg = dx < 0
+            return min(1.0, float(np.min(-x[neg] / dx[neg]))) if np.any(neg) else 1.0
+
+        du, ds, dz = step(s_ * z)
+        a_aff = min(maxstep(s_, ds), maxstep(z, dz))
+        mu_aff = (s_ + a_aff * ds) @ (z + a_aff * dz) / m
+        sigma = (mu_aff / mu) ** 3
+        du, ds, dz = step(s_ * z + ds * dz - sigma * mu)
+        a = 0.99 * min(maxstep(s_, ds), maxstep(z, dz))
+        u, s_, z = u + a * du, s_ + a * ds, z + a * dz
+    raise AssertionError("interior point did not converge")
+
+
+def _risk_neutral_qp_general(p):
+    """min sum_c pi^c l^c(x^a, u^a) + sum_j pi^j l_N^j(x^j) with the full
+    quadratic-plus-linear costs of Sec. 3.2, s.t. the dynamics and x^0 = x0
+    (equalities) and the general rows g_lo <= Gx x + Gu u <= g_hi,
+    gN_lo <= GN x <= gN_hi (inequalities): solved as one dense QP, by a KKT
+    solve without inequalities, else by SLSQP. Returns (value, x, u)."""
+    tr = so_.Tree(p.anc, p.prob)
+    nx, nu, n = p.nx, p.nu, tr.n
+    nX = n * nx + tr.n_nl * nu
+    H = np.zeros((nX, nX))
+    f = np.zeros(nX)
+    full = lambda W, k: W[k] if np.ndim(W) == 3 else np.diag(W[k])   # noqa: E731
+    for c in range(1, n):
+        a = tr.anc[c]
+        H[a * nx:(a + 1) * nx, a * nx:(a + 1) * nx] += tr.pi[c] * full(p.Q, c - 1)
+        o = n * nx + a * nu
+        H[o:o + nu, o:o + nu] += tr.pi[c] * full(p.R, c - 1)
+        if p.q is not None:
+            f[a * nx:(a + 1) * nx] += tr.pi[c] * p.q[c - 1]
+        if p.r is not None:
+            f[o:o + nu] += tr.pi[c] * p.r[c - 1]
+    for jj in range(tr.n_l):
+        j = tr.n_nl + jj
+        H[j * nx:(j + 1) * nx, j * nx:(j + 1) * nx] += tr.pi[j] * full(p.QN, jj)
+        if p.qN is not None:
+            f[j * nx:(j + 1) * nx] += tr.pi[j] * p.qN[jj]
+    rows, rhs = [], []
+    C0 = np.zeros((nx, nX)); C0[:, :nx] = np.eye(nx); rows.append(C0); rhs.append(p.x0)
+    for c in range(1, n):
+        a = tr.anc[c]
+        Cc = np.zeros((nx, nX))
+        Cc[:, c * nx:(c + 1) * nx] = np.eye(nx)
+        Cc[:, a * nx:(a + 1) * nx] = -p.A[c - 1]
+        Cc[:, n * nx + a * nu:n * nx + (a + 1) * nu] = -p.B[c - 1]
+        rows.append(Cc); rhs.append(p.c[c - 1])
+    C = np.vstack(rows)
+    d = np.concatenate(rhs)
+    G, lo, hi = [], [], []
+    if p.Gx is not None:
+        for i in range(tr.n_nl):
+            Gi = np.zeros((p.Gx.shape[0], nX))
+            Gi[:, i * nx:(i + 1) * nx] = p.Gx
+            Gi[:, n * nx + i * nu:n * nx + (i + 1) * nu] = p.Gu
+            G.append(Gi); lo.append(p.g_lo[i]); hi.append(p.g_hi[i])
+    if p.GN is not None:
+        for jj in range(tr.n_l):
+            j = tr.n_nl + jj
+            Gj = np.zeros((p.GN.shape[0], nX))
+            Gj[:, j * nx:(j + 1) * nx] = p.GN
+            G.append(Gj); lo.append(p.gN_lo[jj]); hi.append(p.gN_hi[jj])
+    K = np.block([[2 * H, C.T], [C, np.zeros((C.shape[0], C.shape[0]))]])
+    X = np.linalg.solve(K, np.concatenate([-f, d]))[:nX]
+    if G:
+        G = np.vstack(G); lo = np.concatenate(lo); hi = np.concatenate(hi)
+        # eliminate the dynamics: X = Pm u + p0 (forward simulation from x0)
+        nU = tr.n_nl * nu
+        Pm = np.zeros((nX, nU)); p0 = np.zeros(nX)
+        Pm[n * nx:, :] = np.eye(nU)
+        p0[:nx] = p.x0
+        for c in range(1, n):
+            a = tr.anc[c]
+            Pm[c * nx:(c + 1) * nx] = p.A[c - 1] @ Pm[a * nx:(a + 1) * nx]
+            Pm[c * nx:(c + 1) * nx, a * nu:(a + 1) * nu] += p.B[c - 1]
+            p0[c * nx:(c + 1) * nx] = p.A[c - 1] @ p0[a * nx:(a + 1) * nx] + p.c[c - 1]
+        Hu = Pm.T @ H @ Pm
+        fu = Pm.T @ (2 * H @ p0 + f)
+        Gu_, g0 = G @ Pm, G @ p0
+        u = _qp_interior_point(2 * Hu, fu, np.vstack([Gu_, -Gu_]), np.concatenate([hi - g0, g0 - lo]))
+        X = Pm @ u + p0
+    return float(X @ H @ X + f @ X), X[:n * nx].reshape(n, nx), X[n * nx:].reshape(tr.n_nl, nu)
+
+
+def test_prop1_translation_with_linear_term_is_the_epigraph():
+    """Prop. 1 (Q positive definite, S = I): (z, tau) is in the epigraph of
+    z'Qz + q'z exactly when (F z, tau/2, tau/2) minus the oracle's translation
+    a lies in the second-order cone, for the scaled factor F that L applies to
+    the scaled variables (Sec. 5.4 scalings included). Checked on random
+    points just above and just below the epigraph's boundary, edge costs and
+    terminal costs."""
+    p = general([2, 1], 3, 2, seed=51)
+    o = Oracle(p)
+    rng = np.random.default_rng(52)
+    inside = lambda v: np.linalg.norm(v[:-1]) <= v[-1]   # noqa: E731
+    for c in range(1, o.tree.n):
+        a = o.tree.anc[c]
+        S = o.Snode[a]
+        for _ in range(20):
+            x, u = rng.standard_normal(p.nx), rng.standard_normal(p.nu)
+            ell = o.edge_cost(c, x, u)
+            for tau, want in ((ell + 1e-6 * (1 + abs(ell)), True), (ell - 1e-6 * (1 + abs(ell)), False)):
+                v = np.concatenate([o.Qh[c - 1] @ (S * x), o.Rh[c - 1] @ (o.Su * u), [tau / 2, tau / 2]])
+                assert inside(v - o.a_q[c - 1]) == want
+    for jj in range(o.tree.n_l):
+        for _ in range(20):
+            x = rng.standard_normal(p.nx)
+            ell = o.terminal_cost(jj, x)
+            for s_, want in ((ell + 1e-6 * (1 + abs(ell)), True), (ell - 1e-6 * (1 + abs(ell)), False)):
+                v = np.concatenate([o.QNh[jj] @ (o.SxN * x), [s_ / 2, s_ / 2]])
+                assert inside(v - o.a_qN[jj]) == want
+
+
+def _check_on_likely_nodes(o, r, X, U, tol, pmin=0.05):
+    """x and u of the nodes whose path probability is at least pmin (a node
+    of probability ~0 barely enters the risk-neutral objective, so its
+    trajectory converges far more slowly than the value)."""
+    pi = o.tree.pi
+    sel = pi >= pmin
+    assert np.max(np.abs(r["x"][sel] - X[sel])) < tol
+    seln = sel[:o.tree.n_nl]
+    assert np.max(np.abs(r["u"][seln] - U[seln])) < tol
+
+
+def test_risk_neutral_full_weights_linear_terms_kkt():
+    """AV@R_1, no constraints, full Q, R, Q_N and linear terms q, r, q_N: the
+    oracle's SPOCK solution equals the dense KKT solution of the risk-neutral
+    QP (value; trajectory on the likely nodes)."""
+    p = general([2, 2, 1], 3, 2, seed=53)
+    o = Oracle(p)
+    r = o.solve(tol=1e-9, max_iters=20000)
+    V, X, U = _risk_neutral_qp_general(p)
+    assert abs(r["risk"] - V) < 1e-7 * max(1.0, abs(V))
+    _check_on_likely_nodes(o, r, X, U, 1e-5)
+
+
+def test_risk_neutral_general_rows_vs_qp_solver():
+    """AV@R_1 with general rows at every node (Eq. constraints with dense
+    Gamma_x, Gamma_u, Gamma_N and box sets), full weights and linear terms:
+    the oracle's solution equals the convex QP solved by SLSQP; some rows are
+    active."""
+    p = general([2, 2, 1], 3, 2, seed=54, n_g=2, n_gN=1, g_scale=0.4)
+    o = Oracle(p)
+    r = o.solve(tol=1e-9, max_iters=30000)
+    V, X, U = _risk_neutral_qp_general(p)
+    assert abs(r["risk"] - V) < 1e-6 * max(1.0, abs(V))
+    _check_on_likely_nodes(o, r, X, U, 1e-4)
+    tr = o.tree
+    gx = np.array([p.Gx @ r["x"][i] + p.Gu @ r["u"][i] for i in range(tr.n_nl)])
+    act = np.isclose(gx, p.g_lo, atol=1e-6) | np.isclose(gx, p.g_hi, atol=1e-6)
+    assert act.any()
+
+
+def test_general_problem_diagnostics_vanish():
+    """AV@R 0.5 with full weights, linear terms, boxes and general rows: the
+    residual, xi1, xi2, infeasibility and the complementarity gap (with the
+    support function of the translated cones and the general rows) vanish, and
+    s0 equals the nested risk of the trajectory with the linear costs."""
+    p = general([2, 2, 1], 3, 2, seed=55, avar=0.5, n_g=2, n_gN=1, box=True, g_scale=0.5)
+    o = Oracle(p)
+    r = o.solve(tol=1e-8, max_iters=30000)
+    assert r["res_inf"] <= 1e-8
+    assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
+    assert r["infeas"] < 1e-6 and r["gap"] < 1e-5
+    assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * max(1.0, abs(r["risk"]))
