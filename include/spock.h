@@ -24,16 +24,23 @@
  *    its ancestor (prob[0] = 1, children probabilities of a node sum to 1);
  *  - dynamics (Eq. finite-horizon-evolution): x^c = A^c x^anc(c) + B^c u^anc(c)
  *    + c^c for every non-root node c, x^0 = x0;
- *  - costs (Sec. 3.2, "Quadratic-plus-linear costs", linear terms zero): edge
- *    cost x'Q^c x + u'R^c u on the ancestor's (x, u) for every non-root c,
- *    terminal cost x'Q_N^j x at every leaf j; Q, R, Q_N diagonal;
+ *  - costs (Sec. 3.2, "Quadratic-plus-linear costs"): edge cost
+ *    x'Q^c x + u'R^c u + q^c'x + r^c'u on the ancestor's (x, u) for every
+ *    non-root c, terminal cost x'Q_N^j x + q_N^j'x at every leaf j; Q, R, Q_N
+ *    diagonal or full, linear terms optional;
  *  - constraints (Eq. constraints): optional box on x at every node (the
  *    root's box is applied to the fixed x0), optional box on u and optional
- *    Euclidean ball ||u||_2 <= r on u at every non-leaf node;
+ *    Euclidean ball ||u||_2 <= r on u at every non-leaf node, and optional
+ *    general rows Gx x + Gu u in a box at every non-leaf node and GN x in a
+ *    box at every leaf;
  *  - risk (Sec. 3.3-3.4): AV@R_a over the children of every non-leaf node,
  *    a in [0, 1] per non-leaf node; the problem is the nested formulation
  *    Eq. original-problem, solved through its conic reformulation
  *    Eq. min-s0-v1 (Sec. 4).
+ *
+ * The preconditioning of Sec. 5.4 uses the diagonal entries of full weights
+ * and scales every constraint row of a node, general rows included, by one
+ * a = max{1, ||[Gx Sx^-1, Gu Su^-1]||_2}.
  *
  * Vector layout used by the operator-level calls (scaled variables, Sec. 4.3
  * "Sets" and Sec. 4.4 "Linear operator L"); first n_nl nodes are non-leaf:
@@ -42,7 +49,8 @@
  *         | eta_cN (n_l*n_cN) | eta_qN (n_l*(nx+2)) ]
  *   v   = [ z | eta ]  (n_v = n_z + n_eta elements)
  * with tau^c, s^c (c >= 1) at index c-1 of their arrays and constraint rows
- * [x box (nx)] [u box (nu)] [u ball (nu)] per non-leaf node, [x box] per leaf.
+ * [x box (nx)] [u box (nu)] [u ball (nu)] [general (n_g)] per non-leaf node,
+ * [x box (nx)] [general (n_gN)] per leaf.
  */
 #ifndef SPOCK_H
 #define SPOCK_H
@@ -86,6 +94,28 @@ typedef struct spock_problem_desc {
     const double* u_hi;      /* [n_nl nu] or NULL */
     const double* u_ball;    /* [n_nl] ball radius on u, or NULL (no ball) */
     const double* avar;      /* [n_nl] AV@R level in [0, 1] (Sec. 3.3) */
+    /* ---- optional parts of the problem statement; zero-initialise the struct
+     *      (memset or = {0}) so that absent parts read as 0 / NULL ---------- */
+    int weights_full;        /* 1: Q [(n-1) nx nx], R [(n-1) nu nu], QN [n_l nx nx] are full
+                                symmetric positive definite matrices (Sec. 3.2); 0: diagonals
+                                as above. L applies their upper Cholesky factors (SPOCK_ENOTPD
+                                if one is not positive definite) */
+    const double* q;         /* [(n-1) nx] linear edge cost q^c'x^anc(c), or NULL */
+    const double* r;         /* [(n-1) nu] linear edge cost r^c'u^anc(c), or NULL */
+    const double* qN;        /* [n_l nx]   linear terminal cost, or NULL. Linear terms enter
+                                through the translation of the cost cones (Prop. 1 with
+                                S = I): the weight must be positive definite where a linear
+                                term is nonzero (SPOCK_EINVAL otherwise) */
+    int n_g;                 /* general rows at every non-leaf node (Eq. constraints):
+                                g_lo <= Gx x^i + Gu u^i <= g_hi, 0 <= n_g <= 256 */
+    const double* Gx;        /* [n_g nx] (the same rows at every non-leaf node) */
+    const double* Gu;        /* [n_g nu] */
+    const double* g_lo;      /* [n_nl n_g] */
+    const double* g_hi;      /* [n_nl n_g] */
+    int n_gN;                /* general rows at every leaf: gN_lo <= GN x^j <= gN_hi, <= 256 */
+    const double* GN;        /* [n_gN nx] */
+    const double* gN_lo;     /* [n_l n_gN] */
+    const double* gN_hi;     /* [n_l n_gN] */
 } spock_problem_desc;
 
 typedef struct spock_sizes {

@@ -22,6 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = [
     ("spock_api", "spock_api.cu", []),
     ("spock_setup", "spock_setup.cu", []),
+    ("spock_setup_ext", "spock_setup_ext.cu", []),
     ("spock_solver", "spock_solver.cu", []),
     ("spock_noalloc", "spock_noalloc.cu", []),
     ("spock_diag", "spock_diag.cu", []),

@@ -33,6 +33,62 @@ bool finite_arr(const double* a, long long n) {
   return true;
 }
 
+// device copy of a host array in a setup-only allocation (nullptr for nullptr)
+double* up_tmp(DevMem& tmp, const double* a, long long len) {
+  if (!a) return nullptr;
+  double* q = tmp.alloc<double>(len);
+  if (q) cudaMemcpy(q, a, (size_t)len * sizeof(double), cudaMemcpyHostToDevice);
+  return q;
+}
+
+// Largest eigenvalue of a symmetric m x m matrix (row-major) by cyclic Jacobi
+// rotations (host, FP64; m <= 256, used once per problem).
+double sym_max_eig(std::vector<double> a, int m) {
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        tot += a[(size_t)i * m + j] * a[(size_t)i * m + j];
+        if (i != j) off += a[(size_t)i * m + j] * a[(size_t)i * m + j];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = a[(size_t)p * m + q];
+        if (apq == 0.0) continue;
+        const double app = a[(size_t)p * m + p], aqq = a[(size_t)q * m + q];
+        const double th = (aqq - app) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < m; ++k) {   // columns p, q
+          const double akp = a[(size_t)k * m + p], akq = a[(size_t)k * m + q];
+          a[(size_t)k * m + p] = c * akp - sn * akq;
+          a[(size_t)k * m + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {   // rows p, q
+          const double apk = a[(size_t)p * m + k], aqk = a[(size_t)q * m + k];
+          a[(size_t)p * m + k] = c * apk - sn * aqk;
+          a[(size_t)q * m + k] = sn * apk + c * aqk;
+        }
+      }
+  }
+  double mx = 0.0;
+  for (int i = 0; i < m; ++i) mx = std::max(mx, a[(size_t)i * m + i]);
+  return mx;
+}
+
+// ||M||_2 of a rows x cols row-major matrix: sqrt of the largest eigenvalue of M'M
+double mat_norm2(const std::vector<double>& M, int rows, int cols) {
+  std::vector<double> g((size_t)cols * cols, 0.0);
+  for (int i = 0; i < cols; ++i)
+    for (int j = 0; j < cols; ++j) {
+      double s = 0.0;
+      for (int r = 0; r < rows; ++r) s += M[(size_t)r * cols + i] * M[(size_t)r * cols + j];
+      g[(size_t)i * cols + j] = s;
+    }
+  return sqrt(std::max(0.0, sym_max_eig(g, cols)));
+}
+
 // Validate the tree (Sec. 3.2) and build the node arrays and sweep schedule.
 int build_tree(spock_problem* p, int n, const int* anc, const double* prob) {
   if (n < 2 || !anc || !prob || anc[0] != -1) return SPOCK_EINVAL;
@@ -166,6 +222,12 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.qh = it.qh; P.rh = it.rh; P.qNh = it.qNh; P.gx = it.gx; P.gu = it.gu; P.gN = it.gN;
   P.box_lo = it.box_lo; P.box_hi = it.box_hi; P.boxN_lo = it.boxN_lo; P.boxN_hi = it.boxN_hi;
   P.ball = it.ball; P.prob = it.prob; P.avar = it.avar; P.x0s = it.x0s;
+  P.full = p->full;
+  P.FQ = it.FQ; P.FQT = it.FQT; P.FR = it.FR; P.FRT = it.FRT; P.FN = it.FN; P.FNT = it.FNT;
+  P.acost = it.acost; P.acostN = it.acostN;
+  P.n_g = p->n_g; P.n_gN = p->n_gN;
+  P.Gg = it.Gg; P.GgT = it.GgT; P.GgN = it.GgN; P.GgNT = it.GgNT;
+  P.gen_lo = it.gen_lo; P.gen_hi = it.gen_hi; P.genN_lo = it.genN_lo; P.genN_hi = it.genN_hi;
   P.alpha = (T)alpha;
   P.qbuf = it.qbuf; P.dbuf = it.dbuf; P.hbuf = it.hbuf; P.ebuf = it.ebuf;
 }
@@ -242,6 +304,23 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
   it.dbuf = m.alloc<T>((long long)n_nl * nu);
   it.hbuf = m.alloc<T>((long long)n_nl * nx);
   it.ebuf = m.alloc<T>((long long)n_nl * nu);
+  if (p->full) {
+    it.FQ = m.alloc<T>((long long)(n - 1) * nx * nx); it.FQT = m.alloc<T>((long long)(n - 1) * nx * nx);
+    it.FR = m.alloc<T>((long long)(n - 1) * nu * nu); it.FRT = m.alloc<T>((long long)(n - 1) * nu * nu);
+    it.FN = m.alloc<T>((long long)n_l * nx * nx); it.FNT = m.alloc<T>((long long)n_l * nx * nx);
+  }
+  if (p->has_lin) {
+    it.acost = m.alloc<T>((long long)(n - 1) * (nx + nu + 2));
+    it.acostN = m.alloc<T>((long long)n_l * (nx + 2));
+  }
+  if (p->n_g) {
+    it.Gg = m.alloc<T>((long long)p->n_g * (nx + nu)); it.GgT = m.alloc<T>((long long)p->n_g * (nx + nu));
+    it.gen_lo = m.alloc<T>((long long)n_nl * p->n_g); it.gen_hi = m.alloc<T>((long long)n_nl * p->n_g);
+  }
+  if (p->n_gN) {
+    it.GgN = m.alloc<T>((long long)p->n_gN * nx); it.GgNT = m.alloc<T>((long long)p->n_gN * nx);
+    it.genN_lo = m.alloc<T>((long long)n_l * p->n_gN); it.genN_hi = m.alloc<T>((long long)n_l * p->n_gN);
+  }
   cta_layout<T>(p, it);
   if (it.cta) {
     it.MBt = m.alloc<T>((long long)(n - 1) * (nx + nu) * it.ldTB);
@@ -604,18 +683,84 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   const int n = p->n, n_nl = p->n_nl, n_l = p->n_l, nx = d->nx, nu = d->nu;
   p->nx = nx; p->nu = nu;
   // data checks
+  const int full = d->weights_full ? 1 : 0;
+  const long long wq = full ? (long long)nx * nx : nx, wr = full ? (long long)nu * nu : nu;
   auto bad = [&](const double* a, long long len) { return a && !finite_arr(a, len); };
   if (bad(d->A, (long long)(n - 1) * nx * nx) || bad(d->B, (long long)(n - 1) * nx * nu) ||
-      bad(d->c, (long long)(n - 1) * nx) || bad(d->Q, (long long)(n - 1) * nx) ||
-      bad(d->R, (long long)(n - 1) * nu) || bad(d->QN, (long long)n_l * nx) ||
+      bad(d->c, (long long)(n - 1) * nx) || bad(d->Q, (long long)(n - 1) * wq) ||
+      bad(d->R, (long long)(n - 1) * wr) || bad(d->QN, (long long)n_l * wq) ||
       bad(d->x_lo, (long long)n * nx) || bad(d->x_hi, (long long)n * nx) ||
       bad(d->u_lo, (long long)n_nl * nu) || bad(d->u_hi, (long long)n_nl * nu) ||
-      bad(d->u_ball, n_nl) || bad(d->avar, n_nl)) {
+      bad(d->u_ball, n_nl) || bad(d->avar, n_nl) || bad(d->q, (long long)(n - 1) * nx) ||
+      bad(d->r, (long long)(n - 1) * nu) || bad(d->qN, (long long)n_l * nx)) {
     delete p; return SPOCK_EINVAL;
   }
-  for (long long e = 0; e < (long long)(n - 1) * nx; ++e) if (d->Q[e] < 0) { delete p; return SPOCK_EINVAL; }
-  for (long long e = 0; e < (long long)(n - 1) * nu; ++e) if (d->R[e] < 0) { delete p; return SPOCK_EINVAL; }
-  for (long long e = 0; e < (long long)n_l * nx; ++e) if (d->QN[e] < 0) { delete p; return SPOCK_EINVAL; }
+  // diagonals of the weights (all the preconditioning of Sec. 5.4 uses); full
+  // weights must be symmetric with a positive diagonal (the Cholesky factor
+  // on the device decides positive definiteness)
+  std::vector<double> Qd((size_t)(n - 1) * nx), Rd((size_t)(n - 1) * nu), QNd((size_t)n_l * nx);
+  {
+    auto take = [&](const double* W, long long nb, int m, std::vector<double>& out) -> bool {
+      for (long long b = 0; b < nb; ++b) {
+        if (!full) {
+          for (int k = 0; k < m; ++k) {
+            const double v = W[b * m + k];
+            if (v < 0) return false;
+            out[(size_t)(b * m + k)] = v;
+          }
+          continue;
+        }
+        const double* M = W + b * (long long)m * m;
+        double mx = 0.0;
+        for (long long e = 0; e < (long long)m * m; ++e) mx = std::max(mx, fabs(M[e]));
+        for (int i = 0; i < m; ++i) {
+          if (!(M[(size_t)i * m + i] > 0)) return false;
+          out[(size_t)(b * m + i)] = M[(size_t)i * m + i];
+          for (int j = i + 1; j < m; ++j)
+            if (fabs(M[(size_t)i * m + j] - M[(size_t)j * m + i]) > 1e-12 * mx) return false;
+        }
+      }
+      return true;
+    };
+    if (!take(d->Q, n - 1, nx, Qd) || !take(d->R, n - 1, nu, Rd) || !take(d->QN, n_l, nx, QNd)) {
+      delete p; return SPOCK_EINVAL;
+    }
+    // a linear term needs a positive weight where it is nonzero (Prop. 1, S = I)
+    auto lin_ok = [&](const double* w, const std::vector<double>& dg, long long len) {
+      if (!w) return true;
+      for (long long e = 0; e < len; ++e)
+        if (w[e] != 0.0 && !(dg[(size_t)e] > 0)) return false;
+      return true;
+    };
+    if (!lin_ok(d->q, Qd, (long long)(n - 1) * nx) || !lin_ok(d->r, Rd, (long long)(n - 1) * nu) ||
+        !lin_ok(d->qN, QNd, (long long)n_l * nx)) {
+      delete p; return SPOCK_EINVAL;
+    }
+  }
+  // general rows
+  if (d->n_g < 0 || d->n_gN < 0) { delete p; return SPOCK_EINVAL; }
+  if (d->n_g > MAXD || d->n_gN > MAXD) { delete p; return SPOCK_EUNSUPPORTED; }
+  if (d->n_g > 0) {
+    if (!d->Gx || !d->Gu || !d->g_lo || !d->g_hi || bad(d->Gx, (long long)d->n_g * nx) ||
+        bad(d->Gu, (long long)d->n_g * nu) || bad(d->g_lo, (long long)n_nl * d->n_g) ||
+        bad(d->g_hi, (long long)n_nl * d->n_g)) {
+      delete p; return SPOCK_EINVAL;
+    }
+    for (long long e = 0; e < (long long)n_nl * d->n_g; ++e)
+      if (d->g_lo[e] > d->g_hi[e]) { delete p; return SPOCK_EINVAL; }
+  }
+  if (d->n_gN > 0) {
+    if (!d->GN || !d->gN_lo || !d->gN_hi || bad(d->GN, (long long)d->n_gN * nx) ||
+        bad(d->gN_lo, (long long)n_l * d->n_gN) || bad(d->gN_hi, (long long)n_l * d->n_gN)) {
+      delete p; return SPOCK_EINVAL;
+    }
+    for (long long e = 0; e < (long long)n_l * d->n_gN; ++e)
+      if (d->gN_lo[e] > d->gN_hi[e]) { delete p; return SPOCK_EINVAL; }
+  }
+  p->full = full;
+  p->has_lin = (d->q || d->r || d->qN) ? 1 : 0;
+  p->n_g = d->n_g;
+  p->n_gN = d->n_gN;
   for (int i = 0; i < n_nl; ++i) if (d->avar[i] < 0 || d->avar[i] > 1) { delete p; return SPOCK_EINVAL; }
   if (d->x_lo) for (long long e = 0; e < (long long)n * nx; ++e) if (d->x_lo[e] > d->x_hi[e]) { delete p; return SPOCK_EINVAL; }
   if (d->u_lo) for (long long e = 0; e < (long long)n_nl * nu; ++e) if (d->u_lo[e] > d->u_hi[e]) { delete p; return SPOCK_EINVAL; }
@@ -624,8 +769,8 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   p->nbu = d->u_lo ? nu : 0;
   p->nbox = p->nbx + p->nbu;
   p->has_ball = d->u_ball ? 1 : 0;
-  p->n_c = p->nbox + (p->has_ball ? nu : 0);
-  p->n_cN = p->nbx;
+  p->n_c = p->nbox + (p->has_ball ? nu : 0) + p->n_g;
+  p->n_cN = p->nbx + p->n_gN;
   // layout (Sec. 4.3-4.4)
   p->o_x = 1; p->o_u = p->o_x + (long long)n * nx; p->o_y = p->o_u + (long long)n_nl * nu;
   p->o_tau = p->o_y + p->n_y; p->o_s = p->o_tau + (n - 1); p->nz = p->o_s + (n - 1);
@@ -643,11 +788,11 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   const double chat = sqrt((double)maxch);
   p->Sx.assign(nx, 1.0); p->Su.assign(nu, 1.0); p->SxN.assign(nx, 1.0);
   for (int c = 1; c < n; ++c) {
-    for (int k = 0; k < nx; ++k) p->Sx[k] = std::max(p->Sx[k], sqrt(d->Q[(long long)(c - 1) * nx + k]));
-    for (int k = 0; k < nu; ++k) p->Su[k] = std::max(p->Su[k], sqrt(d->R[(long long)(c - 1) * nu + k]));
+    for (int k = 0; k < nx; ++k) p->Sx[k] = std::max(p->Sx[k], sqrt(Qd[(size_t)(c - 1) * nx + k]));
+    for (int k = 0; k < nu; ++k) p->Su[k] = std::max(p->Su[k], sqrt(Rd[(size_t)(c - 1) * nu + k]));
   }
   for (int j = 0; j < n_l; ++j)
-    for (int k = 0; k < nx; ++k) p->SxN[k] = std::max(p->SxN[k], sqrt(d->QN[(long long)j * nx + k]));
+    for (int k = 0; k < nx; ++k) p->SxN[k] = std::max(p->SxN[k], sqrt(QNd[(size_t)j * nx + k]));
   for (int k = 0; k < nx; ++k) p->Sx[k] *= chat;
   for (int k = 0; k < nu; ++k) p->Su[k] *= chat;
   // ||[Gx Sx^-1, Gu Su^-1]||_2 of selection rows: its Gram is diagonal
@@ -660,6 +805,55 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
     double gN = 0.0;
     if (p->nbx) for (int k = 0; k < nx; ++k) gN = std::max(gN, 1.0 / (p->SxN[k] * p->SxN[k]));
     p->a_conN = std::max(1.0, sqrt(gN));
+  }
+  // with general rows the Gram of the scaled rows is full: its norm by Jacobi
+  std::vector<double> hGg, hGgT, hglo, hghi, hGgN, hGgNT, hgNlo, hgNhi;
+  if (p->n_g) {
+    const int w = nx + nu, ng = p->n_g;
+    const int rows = p->n_c;
+    std::vector<double> M((size_t)rows * w, 0.0);
+    int r = 0;
+    for (int k = 0; k < p->nbx; ++k, ++r) M[(size_t)r * w + k] = 1.0 / p->Sx[k];
+    for (int k = 0; k < p->nbu; ++k, ++r) M[(size_t)r * w + nx + k] = 1.0 / p->Su[k];
+    if (p->has_ball) for (int k = 0; k < nu; ++k, ++r) M[(size_t)r * w + nx + k] = 1.0 / p->Su[k];
+    for (int g = 0; g < ng; ++g, ++r) {
+      for (int k = 0; k < nx; ++k) M[(size_t)r * w + k] = d->Gx[(size_t)g * nx + k] / p->Sx[k];
+      for (int k = 0; k < nu; ++k) M[(size_t)r * w + nx + k] = d->Gu[(size_t)g * nu + k] / p->Su[k];
+    }
+    p->a_con = std::max(1.0, mat_norm2(M, rows, w));
+    hGg.resize((size_t)ng * w); hGgT.resize((size_t)ng * w);
+    for (int g = 0; g < ng; ++g)
+      for (int k = 0; k < w; ++k) {
+        const double v = M[(size_t)(rows - ng + g) * w + k] / p->a_con;
+        hGg[(size_t)g * w + k] = v;
+        hGgT[(size_t)k * ng + g] = v;
+      }
+    hglo.resize((size_t)n_nl * ng); hghi.resize((size_t)n_nl * ng);
+    for (long long e = 0; e < (long long)n_nl * ng; ++e) {
+      hglo[(size_t)e] = d->g_lo[e] / p->a_con;
+      hghi[(size_t)e] = d->g_hi[e] / p->a_con;
+    }
+  }
+  if (p->n_gN) {
+    const int ng = p->n_gN, rows = p->n_cN;
+    std::vector<double> M((size_t)rows * nx, 0.0);
+    int r = 0;
+    for (int k = 0; k < p->nbx; ++k, ++r) M[(size_t)r * nx + k] = 1.0 / p->SxN[k];
+    for (int g = 0; g < ng; ++g, ++r)
+      for (int k = 0; k < nx; ++k) M[(size_t)r * nx + k] = d->GN[(size_t)g * nx + k] / p->SxN[k];
+    p->a_conN = std::max(1.0, mat_norm2(M, rows, nx));
+    hGgN.resize((size_t)ng * nx); hGgNT.resize((size_t)ng * nx);
+    for (int g = 0; g < ng; ++g)
+      for (int k = 0; k < nx; ++k) {
+        const double v = M[(size_t)(rows - ng + g) * nx + k] / p->a_conN;
+        hGgN[(size_t)g * nx + k] = v;
+        hGgNT[(size_t)k * ng + g] = v;
+      }
+    hgNlo.resize((size_t)n_l * ng); hgNhi.resize((size_t)n_l * ng);
+    for (long long e = 0; e < (long long)n_l * ng; ++e) {
+      hgNlo[(size_t)e] = d->gN_lo[e] / p->a_conN;
+      hgNhi[(size_t)e] = d->gN_hi[e] / p->a_conN;
+    }
   }
   if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
     delete p; return SPOCK_EDEVICE;
@@ -718,9 +912,9 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   cudaMemcpy(dA, d->A, (size_t)(n - 1) * nx * nx * 8, cudaMemcpyHostToDevice);
   cudaMemcpy(dB, d->B, (size_t)(n - 1) * nx * nu * 8, cudaMemcpyHostToDevice);
   if (dc) cudaMemcpy(dc, d->c, (size_t)(n - 1) * nx * 8, cudaMemcpyHostToDevice);
-  cudaMemcpy(dQ, d->Q, (size_t)(n - 1) * nx * 8, cudaMemcpyHostToDevice);
-  cudaMemcpy(dR, d->R, (size_t)(n - 1) * nu * 8, cudaMemcpyHostToDevice);
-  cudaMemcpy(dQN, d->QN, (size_t)n_l * nx * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dQ, Qd.data(), (size_t)(n - 1) * nx * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dR, Rd.data(), (size_t)(n - 1) * nu * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dQN, QNd.data(), (size_t)n_l * nx * 8, cudaMemcpyHostToDevice);
   if (dxlo) cudaMemcpy(dxlo, d->x_lo, (size_t)n * nx * 8, cudaMemcpyHostToDevice);
   if (dxhi) cudaMemcpy(dxhi, d->x_hi, (size_t)n * nx * 8, cudaMemcpyHostToDevice);
   if (dulo) cudaMemcpy(dulo, d->u_lo, (size_t)n_nl * nu * 8, cudaMemcpyHostToDevice);
@@ -771,6 +965,68 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   if (e == cudaSuccess) e = launch_alg1(a, p->stage_off.data(), p->N, st);
   if (e == cudaSuccess) e = launch_build(a, st);
   if (e == cudaSuccess) e = launch_norm_L(a, dnorm, st);
+  // full weights: upper Cholesky factors, the cone translations of the
+  // linear terms (from the unscaled factors), then the scaled factors
+  int* derr2 = tmp.alloc<int>(1);
+  if (tmp.failed) { tmp.free_all(); m.free_all(); delete p; return SPOCK_ENOMEM; }
+  cudaMemset(derr2, 0, sizeof(int));
+  {
+    double* dQf = nullptr; double* dRf = nullptr; double* dQNf = nullptr;
+    if (full && e == cudaSuccess) {
+      dQf = up_tmp(tmp, d->Q, (long long)(n - 1) * nx * nx);
+      dRf = up_tmp(tmp, d->R, (long long)(n - 1) * nu * nu);
+      dQNf = up_tmp(tmp, d->QN, (long long)n_l * nx * nx);
+      if (tmp.failed) { tmp.free_all(); m.free_all(); delete p; return SPOCK_ENOMEM; }
+      e = launch_chol_upper(n - 1, nx, dQf, derr2, st);
+      if (e == cudaSuccess) e = launch_chol_upper(n - 1, nu, dRf, derr2, st);
+      if (e == cudaSuccess) e = launch_chol_upper(n_l, nx, dQNf, derr2, st);
+    }
+    if (p->has_lin && e == cudaSuccess) {
+      double* wq_ = d->q ? tmp.alloc<double>((long long)(n - 1) * nx) : nullptr;
+      double* wr_ = d->r ? tmp.alloc<double>((long long)(n - 1) * nu) : nullptr;
+      double* wqN = d->qN ? tmp.alloc<double>((long long)n_l * nx) : nullptr;
+      double* kap = tmp.alloc<double>(n - 1);
+      double* kapN = tmp.alloc<double>(n_l);
+      double* dq = up_tmp(tmp, d->q, (long long)(n - 1) * nx);
+      double* dr = up_tmp(tmp, d->r, (long long)(n - 1) * nu);
+      double* dqN = up_tmp(tmp, d->qN, (long long)n_l * nx);
+      if (tmp.failed) { tmp.free_all(); m.free_all(); delete p; return SPOCK_ENOMEM; }
+      cudaMemset(kap, 0, (size_t)(n - 1) * 8);
+      cudaMemset(kapN, 0, (size_t)n_l * 8);
+      if (dq) e = launch_ftinv(n - 1, nx, full, full ? dQf : dQ, dq, wq_, kap, st);
+      if (e == cudaSuccess && dr) e = launch_ftinv(n - 1, nu, full, full ? dRf : dR, dr, wr_, kap, st);
+      if (e == cudaSuccess && dqN) e = launch_ftinv(n_l, nx, full, full ? dQNf : dQN, dqN, wqN, kapN, st);
+      if (e == cudaSuccess) e = launch_translation(n - 1, nx, nu, wq_, wr_, kap, p->f64.acost, st);
+      if (e == cudaSuccess) e = launch_translation(n_l, nx, 0, wqN, nullptr, kapN, p->f64.acostN, st);
+    }
+    if (full && e == cudaSuccess) {
+      Iter<double>& f = p->f64;
+      e = launch_scale_factor(n - 1, nx, dQf, p->d_Sx, f.FQ, f.FQT, st);
+      if (e == cudaSuccess) e = launch_scale_factor(n - 1, nu, dRf, p->d_Su, f.FR, f.FRT, st);
+      if (e == cudaSuccess) e = launch_scale_factor(n_l, nx, dQNf, p->d_SxN, f.FN, f.FNT, st);
+    }
+    if (p->n_g && e == cudaSuccess) {
+      Iter<double>& f = p->f64;
+      e = cudaMemcpy(f.Gg, hGg.data(), hGg.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(f.GgT, hGgT.data(), hGgT.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(f.gen_lo, hglo.data(), hglo.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(f.gen_hi, hghi.data(), hghi.size() * 8, cudaMemcpyHostToDevice);
+    }
+    if (p->n_gN && e == cudaSuccess) {
+      Iter<double>& f = p->f64;
+      e = cudaMemcpy(f.GgN, hGgN.data(), hGgN.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(f.GgNT, hGgNT.data(), hGgNT.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(f.genN_lo, hgNlo.data(), hgNlo.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(f.genN_hi, hgNhi.data(), hgNhi.size() * 8, cudaMemcpyHostToDevice);
+    }
+  }
+  // ||L|| over the blocks of L'L that are not diagonal: (x^i, u^i) of every
+  // non-leaf node and x^j of every leaf (the diagonal estimates above are
+  // lower bounds of those blocks' largest eigenvalues)
+  if ((full || p->n_g || p->n_gN) && e == cudaSuccess) {
+    fill_prob<double>(p, p->f64, 1.0);
+    e = launch_norm_L_blocks(p->f64.P, dnorm, st);
+  }
   if (e == cudaSuccess) e = cudaMemcpy(f.prob, d_prob, (size_t)n * 8, cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(f.avar, d_avar, (size_t)n_nl * 8, cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -778,9 +1034,11 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   unsigned long long hnorm = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&hnorm, dnorm, sizeof(hnorm), cudaMemcpyDeviceToHost);
+  int herr2 = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr2, derr2, sizeof(int), cudaMemcpyDeviceToHost);
   tmp.free_all();
   if (e != cudaSuccess) { m.free_all(); delete p; return SPOCK_EDEVICE; }
-  if (herr) { m.free_all(); delete p; return SPOCK_ENOTPD; }
+  if (herr || herr2) { m.free_all(); delete p; return SPOCK_ENOTPD; }
   double l2;
   memcpy(&l2, &hnorm, sizeof(double));
   p->normL = sqrt(l2);
@@ -798,6 +1056,21 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   float* dst[] = {g.MB, g.MF, g.MP, g.KT, g.cvec, g.kc, g.qh, g.rh, g.qNh, g.gx, g.gu, g.gN,
                   g.box_lo, g.box_hi, g.boxN_lo, g.boxN_hi, g.ball, g.prob, g.avar};
   for (int q = 0; q < 19 && e == cudaSuccess; ++q) e = launch_convert_f64_f32(src[q], dst[q], cnt[q], st);
+  {
+    const long long wW = nx + nu + 2;
+    const long long cnt2[] = {(long long)(n - 1) * nx * nx, (long long)(n - 1) * nx * nx,
+                              (long long)(n - 1) * nu * nu, (long long)(n - 1) * nu * nu,
+                              (long long)n_l * nx * nx, (long long)n_l * nx * nx, (long long)(n - 1) * wW,
+                              (long long)n_l * (nx + 2), (long long)p->n_g * (nx + nu), (long long)p->n_g * (nx + nu),
+                              (long long)p->n_gN * nx, (long long)p->n_gN * nx, (long long)n_nl * p->n_g,
+                              (long long)n_nl * p->n_g, (long long)n_l * p->n_gN, (long long)n_l * p->n_gN};
+    const double* src2[] = {f.FQ, f.FQT, f.FR, f.FRT, f.FN, f.FNT, f.acost, f.acostN, f.Gg, f.GgT, f.GgN, f.GgNT,
+                            f.gen_lo, f.gen_hi, f.genN_lo, f.genN_hi};
+    float* dst2[] = {g.FQ, g.FQT, g.FR, g.FRT, g.FN, g.FNT, g.acost, g.acostN, g.Gg, g.GgT, g.GgN, g.GgNT,
+                     g.gen_lo, g.gen_hi, g.genN_lo, g.genN_hi};
+    for (int q = 0; q < 16 && e == cudaSuccess; ++q)
+      if (src2[q]) e = launch_convert_f64_f32(src2[q], dst2[q], cnt2[q], st);
+  }
   // output-column-major factors of the whole-CTA sweeps
   if (e == cudaSuccess && f.cta) {
     e = launch_transpose(f.MB, n - 1, nx, nx + nu, p->ldB, f.ldTB, f.MBt, 64, st);

@@ -81,6 +81,26 @@ struct Prob {
   const T* prob;                       // [n] conditional probabilities
   const T* avar;                       // [n_nl]
   const T* x0s;                        // [nx] scaled initial state
+  // full weights (full = 1): scaled upper Cholesky factors F S^{-1} of every
+  // Q^c, R^c (non-root c) and Q_N^j (leaf j), row-major, and their transposes
+  int full;
+  const T *FQ, *FQT;   // [(n-1) nx nx]
+  const T *FR, *FRT;   // [(n-1) nu nu]
+  const T *FN, *FNT;   // [n_l nx nx]
+  // translation of each cost cone (Prop. 1 with linear terms), or null for
+  // (0, .., 1/2, -1/2): per non-root node W entries, per leaf nx + 2
+  const T* acost;
+  const T* acostN;
+  // general constraint rows (scaled, Sec. 5.4): n_g rows G = [Gx Gu] at every
+  // non-leaf node after the box and ball rows, n_gN rows GN at every leaf after
+  // the x box rows; the sets are boxes per node
+  int n_g, n_gN;
+  const T* Gg;         // [n_g (nx + nu)]
+  const T* GgT;        // [(nx + nu) n_g]
+  const T* GgN;        // [n_gN nx]
+  const T* GgNT;       // [nx n_gN]
+  const T *gen_lo, *gen_hi;     // [n_nl n_g]
+  const T *genN_lo, *genN_hi;   // [n_l n_gN]
   T alpha;
   // scratch of the sweeps
   T* qbuf;   // [n nx]

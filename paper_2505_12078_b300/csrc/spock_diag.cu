@@ -60,11 +60,17 @@ __global__ void k_xi(long long nz, long long neta, double alpha, const double* _
 // A translated second-order cone block of length dim at offset base of eta
 // (a = (0.., 1/2, -1/2), last entry the scalar part): infeasibility of the
 // block of L z+ and the block's terms of <eta+, L z+> and sigma(eta+).
+__device__ __forceinline__ double cone_a(const double* acst, int e, int dim) {
+  if (acst) return acst[e];
+  return (e == dim - 2) ? 0.5 : ((e == dim - 1) ? -0.5 : 0.0);
+}
+
 __device__ void soc_diag(int lane, int dim, long long base, const double* __restrict__ lz,
-                         const double* __restrict__ ep, double& inf, double& dot, double& sig) {
+                         const double* __restrict__ ep, const double* acst, double& inf, double& dot,
+                         double& sig) {
   double n2 = 0.0, tt = 0.0;
   for (int e = lane; e < dim; e += 32) {
-    const double a = (e == dim - 2) ? 0.5 : ((e == dim - 1) ? -0.5 : 0.0);
+    const double a = cone_a(acst, e, dim);
     const double w = lz[base + e] - a;
     if (e < dim - 1) n2 += w * w;
     else tt = w;
@@ -74,7 +80,7 @@ __device__ void soc_diag(int lane, int dim, long long base, const double* __rest
   const int cs = (nw <= t) ? 0 : ((nw <= -t) ? 1 : 2);
   const double f = 0.5 * (nw + t);
   for (int e = lane; e < dim; e += 32) {
-    const double a = (e == dim - 2) ? 0.5 : ((e == dim - 1) ? -0.5 : 0.0);
+    const double a = cone_a(acst, e, dim);
     const double w = lz[base + e] - a;
     double p;
     if (cs == 0) p = w;
@@ -141,20 +147,32 @@ __global__ void k_S3_diag(Prob<double> P, const double* __restrict__ lz, const d
           if (lane == 0) inf = fmax(inf, mx);
         }
       }
+      const long long ge = ce + P.nbox + (P.has_ball ? P.nu : 0);
+      for (int e = lane; e < P.n_g; e += 32) {              // general rows: boxes
+        const double x = lz[ge + e], h = ep[ge + e];
+        const double lo = P.gen_lo[(long long)i * P.n_g + e], hi = P.gen_hi[(long long)i * P.n_g + e];
+        inf = fmax(inf, fabs(x - fmin(fmax(x, lo), hi)));
+        dot += h * x;
+        sig += fmax(h * lo, h * hi);
+      }
     } else if (b < P.n_nl + P.n - 1) {
       const long long c = b - P.n_nl + 1;
-      soc_diag(lane, P.W, P.e_q + (c - 1) * P.W, lz, ep, inf, dot, sig);
+      soc_diag(lane, P.W, P.e_q + (c - 1) * P.W, lz, ep, P.acost ? P.acost + (c - 1) * P.W : nullptr, inf, dot,
+               sig);
     } else {
       const long long jj = b - P.n_nl - (P.n - 1);
       const long long ce = P.e_cN + jj * P.n_cN;
       for (int e = lane; e < P.n_cN; e += 32) {
         const double x = lz[ce + e], h = ep[ce + e];
-        const double lo = P.boxN_lo[jj * P.nx + e], hi = P.boxN_hi[jj * P.nx + e];
+        const bool bx = e < P.nbx;
+        const double lo = bx ? P.boxN_lo[jj * P.nx + e] : P.genN_lo[jj * P.n_gN + (e - P.nbx)];
+        const double hi = bx ? P.boxN_hi[jj * P.nx + e] : P.genN_hi[jj * P.n_gN + (e - P.nbx)];
         inf = fmax(inf, fabs(x - fmin(fmax(x, lo), hi)));
         dot += h * x;
         sig += fmax(h * lo, h * hi);
       }
-      soc_diag(lane, P.nx + 2, P.e_qN + jj * (P.nx + 2), lz, ep, inf, dot, sig);
+      soc_diag(lane, P.nx + 2, P.e_qN + jj * (P.nx + 2), lz, ep,
+               P.acostN ? P.acostN + jj * (P.nx + 2) : nullptr, inf, dot, sig);
     }
   }
   inf = warp_max(inf);

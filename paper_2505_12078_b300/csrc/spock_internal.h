@@ -43,6 +43,16 @@ cudaError_t launch_apply_L(const Prob<T>& P, const int* ynode, const T* z, T* et
 template <class T>
 cudaError_t launch_apply_Lt(const Prob<T>& P, const int* ynode, const T* eta, T* z, cudaStream_t s);
 
+// full weights, linear terms, ||L|| with full blocks (spock_setup_ext.cu)
+cudaError_t launch_chol_upper(int nmat, int m, double* W, int* err, cudaStream_t s);
+cudaError_t launch_ftinv(int nblk, int m, int full, const double* F, const double* lin, double* w, double* kap,
+                         cudaStream_t s);
+cudaError_t launch_translation(int nblk, int mx, int mu, const double* wx, const double* wu, const double* kap,
+                               double* a, cudaStream_t s);
+cudaError_t launch_scale_factor(long long nblk, int m, const double* F, const double* S, double* Ft, double* FtT,
+                                cudaStream_t s);
+cudaError_t launch_norm_L_blocks(const Prob<double>& P, unsigned long long* out, cudaStream_t s);
+
 // FP64 exit check (Sec. 5.3): xi1, xi2, primal infeasibility, complementarity
 // gap of (v, T(v)); see spock_diag.cu for the scratch it needs
 size_t diag_partials_doubles();

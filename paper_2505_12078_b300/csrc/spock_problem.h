@@ -40,6 +40,11 @@ struct Iter {   // per-precision iteration data
   T *box_lo = nullptr, *box_hi = nullptr, *boxN_lo = nullptr, *boxN_hi = nullptr, *ball = nullptr;
   T *prob = nullptr, *avar = nullptr, *x0s = nullptr;
   T *qbuf = nullptr, *dbuf = nullptr, *hbuf = nullptr, *ebuf = nullptr;
+  // full weights, cone translations, general rows (see Prob)
+  T *FQ = nullptr, *FQT = nullptr, *FR = nullptr, *FRT = nullptr, *FN = nullptr, *FNT = nullptr;
+  T *acost = nullptr, *acostN = nullptr;
+  T *Gg = nullptr, *GgT = nullptr, *GgN = nullptr, *GgNT = nullptr;
+  T *gen_lo = nullptr, *gen_hi = nullptr, *genN_lo = nullptr, *genN_hi = nullptr;
   // whole-CTA sweeps: output-column-major factors and their layout
   T *MBt = nullptr, *MFt = nullptr, *KTt = nullptr;
   int cta = 0, ldTB = 0, ldTF = 0, ldTK = 0, khB = 0, khF = 0, nbuf = 0, item_bytes = 0, qslots = 0,
@@ -56,6 +61,9 @@ struct Iter {   // per-precision iteration data
 struct spock_problem {
   int n = 0, n_nl = 0, n_l = 0, N = 0, nx = 0, nu = 0, n_c = 0, n_cN = 0;
   int nbx = 0, nbu = 0, nbox = 0, has_ball = 0;
+  int full = 0;        // Q, R, QN given as full matrices
+  int has_lin = 0;     // some linear cost term present
+  int n_g = 0, n_gN = 0;   // general constraint rows (non-leaf, leaf)
   long long n_y = 0, nz = 0, neta = 0, nv = 0;
   long long o_x, o_u, o_y, o_tau, o_s, e_y, e_s, e_c, e_q, e_cN, e_qN;
   int ldB, ldF, ldP, ldK;

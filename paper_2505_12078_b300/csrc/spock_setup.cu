@@ -444,29 +444,63 @@ __global__ void k_apply_L(Prob<T> P, const int* __restrict__ ynode, const T* __r
       const long long f = e - P.e_c;
       const long long i = f / P.n_c;
       const int r = (int)(f % P.n_c);
+      const int nball = P.has_ball ? nu : 0;
       if (r < P.nbx) v = P.gx[r] * z[P.o_x + i * nx + r];
       else if (r < P.nbx + P.nbu) v = P.gu[r - P.nbx] * z[P.o_u + i * nu + (r - P.nbx)];
-      else v = P.gu[r - P.nbox] * z[P.o_u + i * nu + (r - P.nbox)];
+      else if (r < P.nbox + nball) v = P.gu[r - P.nbox] * z[P.o_u + i * nu + (r - P.nbox)];
+      else {                               // general row: [Gx Gu] (x^i, u^i)
+        const T* G = P.Gg + (size_t)(r - P.nbox - nball) * (nx + nu);
+        for (int k = 0; k < nx; ++k) v += G[k] * z[P.o_x + i * nx + k];
+        for (int k = 0; k < nu; ++k) v += G[nx + k] * z[P.o_u + i * nu + k];
+      }
     } else if (e < P.e_cN) {               // cost blocks of non-root nodes
       const long long f = e - P.e_q;
       const long long cm1 = f / P.W;
       const int k = (int)(f % P.W);
       const int a = P.anc[cm1 + 1];
-      if (k < nx) v = P.qh[cm1 * nx + k] * z[P.o_x + (long long)a * nx + k];
-      else if (k < nx + nu) v = P.rh[cm1 * nu + (k - nx)] * z[P.o_u + (long long)a * nu + (k - nx)];
-      else v = T(0.5) * z[P.o_tau + cm1];
+      if (k < nx) {
+        if (P.full) {
+          const T* F = P.FQ + (size_t)cm1 * nx * nx + (size_t)k * nx;
+          for (int q = 0; q < nx; ++q) v += F[q] * z[P.o_x + (long long)a * nx + q];
+        } else {
+          v = P.qh[cm1 * nx + k] * z[P.o_x + (long long)a * nx + k];
+        }
+      } else if (k < nx + nu) {
+        if (P.full) {
+          const T* F = P.FR + (size_t)cm1 * nu * nu + (size_t)(k - nx) * nu;
+          for (int q = 0; q < nu; ++q) v += F[q] * z[P.o_u + (long long)a * nu + q];
+        } else {
+          v = P.rh[cm1 * nu + (k - nx)] * z[P.o_u + (long long)a * nu + (k - nx)];
+        }
+      } else {
+        v = T(0.5) * z[P.o_tau + cm1];
+      }
     } else if (e < P.e_qN) {               // leaf constraint rows
       const long long f = e - P.e_cN;
       const long long j = f / P.n_cN;
       const int k = (int)(f % P.n_cN);
-      v = P.gN[k] * z[P.o_x + (P.n_nl + j) * nx + k];
+      const T* x = z + P.o_x + (P.n_nl + j) * nx;
+      if (k < P.nbx) {
+        v = P.gN[k] * x[k];
+      } else {
+        const T* G = P.GgN + (size_t)(k - P.nbx) * nx;
+        for (int q = 0; q < nx; ++q) v += G[q] * x[q];
+      }
     } else {                               // leaf cost blocks
       const long long f = e - P.e_qN;
       const long long j = f / (nx + 2);
       const int k = (int)(f % (nx + 2));
       const long long node = P.n_nl + j;
-      if (k < nx) v = P.qNh[j * nx + k] * z[P.o_x + node * nx + k];
-      else v = T(0.5) * z[P.o_s + node - 1];
+      if (k < nx) {
+        if (P.full) {
+          const T* F = P.FN + (size_t)j * nx * nx + (size_t)k * nx;
+          for (int q = 0; q < nx; ++q) v += F[q] * z[P.o_x + node * nx + q];
+        } else {
+          v = P.qNh[j * nx + k] * z[P.o_x + node * nx + k];
+        }
+      } else {
+        v = T(0.5) * z[P.o_s + node - 1];
+      }
     }
     eta[e] = v;
   }
@@ -494,12 +528,26 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
       const int k = (int)(f % nx);
       if (i < P.n_nl) {
         if (P.nbx) v = P.gx[k] * ec[i * P.n_c + k];
-        for (int c = P.ch_off[i]; c < P.ch_off[i + 1]; ++c)
-          v += P.qh[(long long)(c - 1) * nx + k] * eq[(long long)(c - 1) * P.W + k];
+        for (int c = P.ch_off[i]; c < P.ch_off[i + 1]; ++c) {
+          if (P.full) {
+            const T* F = P.FQ + (size_t)(c - 1) * nx * nx + k;
+            for (int q = 0; q < nx; ++q) v += F[(size_t)q * nx] * eq[(long long)(c - 1) * P.W + q];
+          } else {
+            v += P.qh[(long long)(c - 1) * nx + k] * eq[(long long)(c - 1) * P.W + k];
+          }
+        }
+        const T* eg = ec + i * P.n_c + P.nbox + (P.has_ball ? nu : 0);
+        for (int r = 0; r < P.n_g; ++r) v += P.GgT[(size_t)k * P.n_g + r] * eg[r];
       } else {
         const long long j = i - P.n_nl;
         if (P.nbx) v = P.gN[k] * ecN[j * P.n_cN + k];
-        v += P.qNh[j * nx + k] * eqN[j * (nx + 2) + k];
+        if (P.full) {
+          const T* F = P.FN + (size_t)j * nx * nx + k;
+          for (int q = 0; q < nx; ++q) v += F[(size_t)q * nx] * eqN[j * (nx + 2) + q];
+        } else {
+          v += P.qNh[j * nx + k] * eqN[j * (nx + 2) + k];
+        }
+        for (int r = 0; r < P.n_gN; ++r) v += P.GgNT[(size_t)k * P.n_gN + r] * ecN[j * P.n_cN + P.nbx + r];
       }
     } else if (e < P.o_y) {                // u
       const long long f = e - P.o_u;
@@ -507,8 +555,16 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
       const int k = (int)(f % nu);
       if (P.nbu) v += P.gu[k] * ec[i * P.n_c + P.nbx + k];
       if (P.has_ball) v += P.gu[k] * ec[i * P.n_c + P.nbox + k];
-      for (int c = P.ch_off[i]; c < P.ch_off[i + 1]; ++c)
-        v += P.rh[(long long)(c - 1) * nu + k] * eq[(long long)(c - 1) * P.W + nx + k];
+      for (int c = P.ch_off[i]; c < P.ch_off[i + 1]; ++c) {
+        if (P.full) {
+          const T* F = P.FR + (size_t)(c - 1) * nu * nu + k;
+          for (int q = 0; q < nu; ++q) v += F[(size_t)q * nu] * eq[(long long)(c - 1) * P.W + nx + q];
+        } else {
+          v += P.rh[(long long)(c - 1) * nu + k] * eq[(long long)(c - 1) * P.W + nx + k];
+        }
+      }
+      const T* eg = ec + i * P.n_c + P.nbox + (P.has_ball ? nu : 0);
+      for (int r = 0; r < P.n_g; ++r) v += P.GgT[(size_t)(nx + k) * P.n_g + r] * eg[r];
     } else if (e < P.o_tau) {              // y
       const long long f = e - P.o_y;
       const int i = ynode[f];

@@ -154,18 +154,35 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
   const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
   const T al = P.alpha;
   const T* ec = eta + P.e_c + (long long)i * P.n_c;
+  const T* eg = ec + P.nbox + (P.has_ball ? nu : 0);   // general rows of node i
   for (int k = tw1.lane; k < nu; k += 32) {
     T g = 0;
     if (P.nbu) g += P.gu[k] * ldc(ec + P.nbx + k);
     if (P.has_ball) g += P.gu[k] * ldc(ec + P.nbox + k);
-    for (int c = c0; c < c1; ++c)
-      g += ldr(P.rh + (long long)(c - 1) * nu + k) * ldc(eta + P.e_q + (long long)(c - 1) * P.W + nx + k);
+    for (int c = c0; c < c1; ++c) {
+      const T* eq = eta + P.e_q + (long long)(c - 1) * P.W + nx;
+      if (P.full) {   // (F_R^c)' eta_R^c
+        const T* F = P.FR + (size_t)(c - 1) * nu * nu + k;
+        for (int e = 0; e < nu; ++e) g = fma(ldr(F + (size_t)e * nu), ldc(eq + e), g);
+      } else {
+        g += ldr(P.rh + (long long)(c - 1) * nu + k) * ldc(eq + k);
+      }
+    }
+    for (int r = 0; r < P.n_g; ++r) g = fma(ldr(P.GgT + (size_t)(nx + k) * P.n_g + r), ldc(eg + r), g);
     s_in[k] = ldc(z + P.o_u + (long long)i * nu + k) - al * g;
   }
   for (int k = tw1.lane; k < nx; k += 32) {
     T g = P.nbx ? P.gx[k] * ldc(ec + k) : T(0);
-    for (int c = c0; c < c1; ++c)
-      g += ldr(P.qh + (long long)(c - 1) * nx + k) * ldc(eta + P.e_q + (long long)(c - 1) * P.W + k);
+    for (int c = c0; c < c1; ++c) {
+      const T* eq = eta + P.e_q + (long long)(c - 1) * P.W;
+      if (P.full) {   // (F_Q^c)' eta_Q^c
+        const T* F = P.FQ + (size_t)(c - 1) * nx * nx + k;
+        for (int e = 0; e < nx; ++e) g = fma(ldr(F + (size_t)e * nx), ldc(eq + e), g);
+      } else {
+        g += ldr(P.qh + (long long)(c - 1) * nx + k) * ldc(eq + k);
+      }
+    }
+    for (int r = 0; r < P.n_g; ++r) g = fma(ldr(P.GgT + (size_t)k * P.n_g + r), ldc(eg + r), g);
     s_xb[k] = ldc(z + P.o_x + (long long)i * nx + k) - al * g;
   }
   __syncwarp();
@@ -189,9 +206,17 @@ __device__ void prep_leaf(const Prob<T>& P, int lane, int j, const T* __restrict
   const T* eta = vin + P.nz;
   const int jj = j - P.n_nl;
   const T al = P.alpha;
+  const T* ecN = eta + P.e_cN + (long long)jj * P.n_cN;
+  const T* eqN = eta + P.e_qN + (long long)jj * (nx + 2);
   for (int k = lane; k < nx; k += 32) {
-    T g = P.nbx ? P.gN[k] * ldc(eta + P.e_cN + (long long)jj * P.n_cN + k) : T(0);
-    g += ldr(P.qNh + (long long)jj * nx + k) * ldc(eta + P.e_qN + (long long)jj * (nx + 2) + k);
+    T g = P.nbx ? P.gN[k] * ldc(ecN + k) : T(0);
+    if (P.full) {   // (F_N^j)' eta_QN^j
+      const T* F = P.FN + (size_t)jj * nx * nx + k;
+      for (int e = 0; e < nx; ++e) g = fma(ldr(F + (size_t)e * nx), ldc(eqN + e), g);
+    } else {
+      g += ldr(P.qNh + (long long)jj * nx + k) * ldc(eqN + k);
+    }
+    for (int r = 0; r < P.n_gN; ++r) g = fma(ldr(P.GgNT + (size_t)k * P.n_gN + r), ldc(ecN + P.nbx + r), g);
     const T xbar = ldc(z + P.o_x + (long long)j * nx + k) - al * g;
     stc(P.qbuf + (long long)j * nx + k, -xbar);
   }
@@ -664,13 +689,45 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
       ra.eta(eo_, en, er ? ldc(er + ie) : T(0), g * (o - nn), g * dirv(vref, uo + k));
     }
   }
+  // general rows Gx x^i + Gu u^i in a box
+  if (P.n_g) {
+    const long long ge = ce + P.nbox + (P.has_ball ? nu : 0);
+    for (int r = lane; r < P.n_g; r += 32) {
+      const T* G = P.Gg + (size_t)r * (nx + nu);
+      T Lo = 0, Ln = 0, Ld = 0, Lrd = 0;
+      for (int k = 0; k < nx + nu; ++k) {
+        const long long idx = (k < nx) ? xo + k : uo + (k - nx);
+        const T g = ldr(G + k);
+        const T o = ldc(z + idx), nn = ldc(vout + idx);
+        Lo = fma(g, o, Lo);
+        Ln = fma(g, nn, Ln);
+        Ld = fma(g, o - nn, Ld);
+        Lrd = fma(g, dirv(vref, idx), Lrd);
+      }
+      const T eo_ = ldc(eta + ge + r);
+      const T eb = eo_ + al * (T(2) * Ln - Lo);
+      const T w = eb / al;
+      const T p = min(max(w, P.gen_lo[(long long)i * P.n_g + r]), P.gen_hi[(long long)i * P.n_g + r]);
+      const T en = eb - al * p;
+      stc(eo + ge + r, en);
+      ra.eta(eo_, en, er ? ldc(er + ge + r) : T(0), Ld, Lrd);
+    }
+  }
 }
 
 // translated SOC cost block: a + Pi_SOC(eb/alpha - a), a = (0.., 1/2, -1/2)
+// acst: the block's translation a (null: (0, .., 1/2, -1/2))
+template <class T>
+__device__ __forceinline__ T soc_a(const T* acst, int e, int dim) {
+  if (acst) return ldr(acst + e);
+  return (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
+}
+
 template <class T, int NE, class FL>
 __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, long long ebase,
                                           const T* __restrict__ eta, T* __restrict__ eo,
-                                          const T* __restrict__ er, FL&& Lz, RedAcc<T>& ra) {
+                                          const T* __restrict__ er, FL&& Lz, RedAcc<T>& ra,
+                                          const T* acst = nullptr) {
   const T al = P.alpha;
   T ebv[NE];
   T n2 = 0, tt = 0;
@@ -683,7 +740,7 @@ __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, l
       Lz(e, Lo, Ln, Ld, Lrd);
       const T eb = ldc(eta + ebase + e) + al * (T(2) * Ln - Lo);
       ebv[q] = eb;
-      const T ae = (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
+      const T ae = soc_a(acst, e, dim);
       const T w = eb / al - ae;
       if (e < dim - 1) n2 += w * w;
       else tt = w;
@@ -701,7 +758,7 @@ __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, l
       T Lo, Ln, Ld, Lrd;
       Lz(e, Lo, Ln, Ld, Lrd);
       const T eb = ebv[q];
-      const T ae = (e == dim - 2) ? T(0.5) : ((e == dim - 1) ? T(-0.5) : T(0));
+      const T ae = soc_a(acst, e, dim);
       const T w = eb / al - ae;
       T ps;
       if (cs == 0) ps = w;
@@ -713,6 +770,134 @@ __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, l
       ra.eta(eo_, en, er ? ldc(er + ebase + e) : T(0), Ld, Lrd);
     }
   }
+}
+
+// Translated cost cone of a block with full factors: the caller has the
+// block's eta_bar = eta + alpha L(2 z+ - z) (ebv), L(z - z+) (ldv) and
+// L(direction) (lrv) per lane element e = lane + 32 q.
+template <class T, int NE>
+__device__ __forceinline__ void soc_block_vals(const Prob<T>& P, int lane, int dim, long long ebase,
+                                               const T* __restrict__ eta, T* __restrict__ eo,
+                                               const T* __restrict__ er, const T (&ebv)[NE], const T (&ldv)[NE],
+                                               const T (&lrv)[NE], const T* acst, RedAcc<T>& ra) {
+  const T al = P.alpha;
+  T n2 = 0, tt = 0;
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    if (e < dim) {
+      const T w = ebv[q] / al - soc_a(acst, e, dim);
+      if (e < dim - 1) n2 += w * w;
+      else tt = w;
+    }
+  }
+  const T nw = sqrt(warp_sum(n2));
+  const T t = __shfl_sync(0xffffffffu, tt, (dim - 1) & 31);
+  const int cs = (nw <= t) ? 0 : ((nw <= -t) ? 1 : 2);
+  const T f = (nw + t) / T(2);
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    if (e < dim) {
+      const T ae = soc_a(acst, e, dim);
+      const T w = ebv[q] / al - ae;
+      T ps;
+      if (cs == 0) ps = w;
+      else if (cs == 1) ps = T(0);
+      else ps = (e < dim - 1) ? w * (f / nw) : f;
+      const T en = ebv[q] - al * (ae + ps);
+      const T eo_ = ldc(eta + ebase + e);
+      stc(eo + ebase + e, en);
+      ra.eta(eo_, en, er ? ldc(er + ebase + e) : T(0), ldv[q], lrv[q]);
+    }
+  }
+}
+
+// per lane element e = lane + 32 q < m: acc1 += F (2 z_new - z_old),
+// acc2 += F (z_old - z_new), acc3 += F dir, for F given by its transpose FT
+// (m x m row-major: FT[k m + e] = F[e][k]) acting on z at offset zo; elements
+// are placed at e + shift of the arrays
+template <class T, int NE>
+__device__ __forceinline__ void full_mv3(int lane, int m, int shift, const T* __restrict__ FT, const T* __restrict__ z,
+                                         const T* __restrict__ vout, const T* __restrict__ vref, long long zo,
+                                         T (&a1)[NE], T (&a2)[NE], T (&a3)[NE]) {
+  for (int k = 0; k < m; ++k) {
+    const T o = ldc(z + zo + k), nn = ldc(vout + zo + k);
+    const T x1 = T(2) * nn - o, x2 = o - nn, x3 = dirv(vref, zo + k);
+    const T* Fk = FT + (size_t)k * m;
+#pragma unroll
+    for (int q = 0; q < NE; ++q) {
+      const int e = lane + 32 * q - shift;
+      if (e >= 0 && e < m) {
+        const T f = ldr(Fk + e);
+        a1[q] = fma(f, x1, a1[q]);
+        a2[q] = fma(f, x2, a2[q]);
+        a3[q] = fma(f, x3, a3[q]);
+      }
+    }
+  }
+}
+
+template <class T, int NE>
+__device__ void eta_soc_full(const Prob<T>& P, int lane, int c, const T* __restrict__ vin,
+                             T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu, W = P.W;
+  const int i = P.anc[c];
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  const long long ebase = P.e_q + (long long)(c - 1) * W;
+  T a1[NE], a2[NE], a3[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) { a1[q] = T(0); a2[q] = T(0); a3[q] = T(0); }
+  full_mv3<T, NE>(lane, nx, 0, P.FQT + (size_t)(c - 1) * nx * nx, z, vout, vref, P.o_x + (long long)i * nx, a1, a2, a3);
+  full_mv3<T, NE>(lane, nu, nx, P.FRT + (size_t)(c - 1) * nu * nu, z, vout, vref, P.o_u + (long long)i * nu, a1, a2,
+                  a3);
+  const long long it = P.o_tau + c - 1;
+  const T to = ldc(z + it), tn = ldc(vout + it), td = dirv(vref, it);
+  const T al = P.alpha;
+  T ebv[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    if (e >= nx + nu && e < W) {   // tau/2 twice
+      a1[q] = T(0.5) * (T(2) * tn - to);
+      a2[q] = T(0.5) * (to - tn);
+      a3[q] = T(0.5) * td;
+    }
+    ebv[q] = (e < W) ? ldc(eta + ebase + e) + al * a1[q] : T(0);
+  }
+  soc_block_vals<T, NE>(P, lane, W, ebase, eta, vout + P.nz, vref ? vref + P.nz : nullptr, ebv, a2, a3,
+                        P.acost ? P.acost + (size_t)(c - 1) * W : nullptr, ra);
+}
+
+template <class T, int NE>
+__device__ void eta_leaf_full_cone(const Prob<T>& P, int lane, int j, const T* __restrict__ vin,
+                                   T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, dim = nx + 2;
+  const int jj = j - P.n_nl;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  const long long ebase = P.e_qN + (long long)jj * dim;
+  T a1[NE], a2[NE], a3[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) { a1[q] = T(0); a2[q] = T(0); a3[q] = T(0); }
+  full_mv3<T, NE>(lane, nx, 0, P.FNT + (size_t)jj * nx * nx, z, vout, vref, P.o_x + (long long)j * nx, a1, a2, a3);
+  const long long is = P.o_s + j - 1;
+  const T so = ldc(z + is), sn = ldc(vout + is), sd = dirv(vref, is);
+  const T al = P.alpha;
+  T ebv[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    if (e >= nx && e < dim) {   // s/2 twice
+      a1[q] = T(0.5) * (T(2) * sn - so);
+      a2[q] = T(0.5) * (so - sn);
+      a3[q] = T(0.5) * sd;
+    }
+    ebv[q] = (e < dim) ? ldc(eta + ebase + e) + al * a1[q] : T(0);
+  }
+  soc_block_vals<T, NE>(P, lane, dim, ebase, eta, vout + P.nz, vref ? vref + P.nz : nullptr, ebv, a2, a3,
+                        P.acostN ? P.acostN + (size_t)jj * dim : nullptr, ra);
 }
 
 template <class T, int NE>
@@ -739,7 +924,7 @@ __device__ void eta_soc(const Prob<T>& P, int lane, int c, const T* __restrict__
     Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * dirv(vref, idx);
   };
   soc_block<T, NE>(P, lane, P.W, P.e_q + (long long)(c - 1) * P.W, vin + P.nz, vout + P.nz,
-                   vref ? vref + P.nz : nullptr, Lz, ra);
+                   vref ? vref + P.nz : nullptr, Lz, ra, P.acost ? P.acost + (size_t)(c - 1) * P.W : nullptr);
 }
 
 template <class T, int NE>
@@ -767,6 +952,33 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
       ra.eta(eo_, en, er ? ldc(er + ce + e) : T(0), g * (o - nn), g * dirv(vref, xo + e));
     }
   }
+  // general rows GN x^j in a box
+  if (P.n_gN) {
+    const long long ge = P.e_cN + (long long)jj * P.n_cN + P.nbx;
+    for (int r = lane; r < P.n_gN; r += 32) {
+      const T* G = P.GgN + (size_t)r * nx;
+      T Lo = 0, Ln = 0, Ld = 0, Lrd = 0;
+      for (int k = 0; k < nx; ++k) {
+        const T g = ldr(G + k);
+        const T o = ldc(z + xo + k), nn = ldc(vout + xo + k);
+        Lo = fma(g, o, Lo);
+        Ln = fma(g, nn, Ln);
+        Ld = fma(g, o - nn, Ld);
+        Lrd = fma(g, dirv(vref, xo + k), Lrd);
+      }
+      const T eo_ = ldc(eta + ge + r);
+      const T eb = eo_ + al * (T(2) * Ln - Lo);
+      const T w = eb / al;
+      const T p = min(max(w, P.genN_lo[(long long)jj * P.n_gN + r]), P.genN_hi[(long long)jj * P.n_gN + r]);
+      const T en = eb - al * p;
+      stc(eo + ge + r, en);
+      ra.eta(eo_, en, er ? ldc(er + ge + r) : T(0), Ld, Lrd);
+    }
+  }
+  if (P.full) {
+    eta_leaf_full_cone<T, NE>(P, lane, j, vin, vout, vref, ra);
+    return;
+  }
   const long long is = P.o_s + j - 1;
   const T* qNh = P.qNh + (long long)jj * nx;
   auto Lz = [&](int e, T& Lo, T& Ln, T& Ld, T& Lrd) {
@@ -780,7 +992,8 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
     const T o = ldc(z + idx), nn = ldc(vout + idx);
     Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * dirv(vref, idx);
   };
-  soc_block<T, NE>(P, lane, nx + 2, P.e_qN + (long long)jj * (nx + 2), eta, eo, er, Lz, ra);
+  soc_block<T, NE>(P, lane, nx + 2, P.e_qN + (long long)jj * (nx + 2), eta, eo, er, Lz, ra,
+                   P.acostN ? P.acostN + (size_t)jj * (nx + 2) : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -967,7 +1180,8 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
         z_resid(vin, vout, vref, P.o_u + b * P.nu, P.nu, lane, ra);
         eta_nonleaf(P, lane, (int)b, vin, vout, vref, ra);
       } else if (b < P.n_nl + P.n - 1) {
-        eta_soc<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);
+        if (P.full) eta_soc_full<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);
+        else eta_soc<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);
       } else {
         const int j = (int)(b - P.n_nl - (P.n - 1) + P.n_nl);
         z_resid(vin, vout, vref, P.o_x + (long long)j * P.nx, P.nx, lane, ra);

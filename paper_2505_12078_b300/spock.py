@@ -42,7 +42,9 @@ class ProblemDesc(C.Structure):
     _fields_ = [("n_nodes", C.c_int), ("anc", _ip), ("prob", _dp), ("nx", C.c_int), ("nu", C.c_int),
                 ("A", _dp), ("B", _dp), ("c", _dp), ("Q", _dp), ("R", _dp), ("QN", _dp),
                 ("x_lo", _dp), ("x_hi", _dp), ("u_lo", _dp), ("u_hi", _dp), ("u_ball", _dp),
-                ("avar", _dp)]
+                ("avar", _dp), ("weights_full", C.c_int), ("q", _dp), ("r", _dp), ("qN", _dp),
+                ("n_g", C.c_int), ("Gx", _dp), ("Gu", _dp), ("g_lo", _dp), ("g_hi", _dp),
+                ("n_gN", C.c_int), ("GN", _dp), ("gN_lo", _dp), ("gN_hi", _dp)]
 
 
 class Sizes(C.Structure):
@@ -202,11 +204,16 @@ class Problem:
         anc = np.ascontiguousarray(p.anc, dtype=np.int32)
         arrs = dict(prob=p.prob, A=p.A, B=p.B, c=p.c, Q=p.Q, R=p.R, QN=p.QN, x_lo=p.x_lo,
                     x_hi=p.x_hi, u_lo=p.u_lo, u_hi=p.u_hi, u_ball=p.u_ball, avar=p.avar)
+        for k in ("q", "r", "qN", "Gx", "Gu", "g_lo", "g_hi", "GN", "gN_lo", "gN_hi"):
+            arrs[k] = getattr(p, k, None)
         conv = {k: _f64(v) for k, v in arrs.items()}
         self._keep += [anc] + list(conv.values())
         d.n_nodes = anc.shape[0]
         d.anc = anc.ctypes.data_as(_ip)
         d.nx, d.nu = int(p.nx), int(p.nu)
+        d.weights_full = int(np.ndim(p.Q) == 3)
+        d.n_g = 0 if arrs["Gx"] is None else int(np.asarray(arrs["Gx"]).shape[0])
+        d.n_gN = 0 if arrs["GN"] is None else int(np.asarray(arrs["GN"]).shape[0])
         for k, v in conv.items():
             setattr(d, k, _ptr(v))
         h = C.c_void_p()

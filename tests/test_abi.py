@@ -128,3 +128,66 @@ def test_algorithmic_bytes_counting():
     factors = 30 * (4 * 6 + 6 * 4) + 23 * (2 * 6 + 4 * 2)
     assert per_T == 4 * (factors + 8 * 878)
     assert total == 10 * per_T + 7 * 4 * 21 * 878
+
+
+def _desc_call_general(p, mutate):
+    """As _desc_call for a problem with full weights, linear terms and
+    general rows (every optional field of spock_problem_desc set)."""
+    anc = np.array(p.anc, dtype=np.int32)
+    prob = np.array(p.prob, dtype=np.float64)
+    keys = ("A", "B", "c", "Q", "R", "QN", "x_lo", "x_hi", "u_lo", "u_hi", "u_ball", "avar",
+            "q", "r", "qN", "Gx", "Gu", "g_lo", "g_hi", "GN", "gN_lo", "gN_hi")
+    f = {k: (None if getattr(p, k) is None else np.array(getattr(p, k), dtype=np.float64)) for k in keys}
+    ints = dict(weights_full=int(np.ndim(p.Q) == 3), n_g=f["Gx"].shape[0] if f["Gx"] is not None else 0,
+                n_gN=f["GN"].shape[0] if f["GN"] is not None else 0)
+    mutate(f, ints)
+    d = spock.ProblemDesc()
+    d.n_nodes = anc.shape[0]
+    d.anc = anc.ctypes.data_as(C.POINTER(C.c_int))
+    d.prob = prob.ctypes.data_as(C.POINTER(C.c_double))
+    d.nx, d.nu = p.nx, p.nu
+    for k, v in f.items():
+        setattr(d, k, None if v is None else v.ctypes.data_as(C.POINTER(C.c_double)))
+    for k, v in ints.items():
+        setattr(d, k, v)
+    h = C.c_void_p()
+    rc = spock.load().spock_problem_create(C.byref(d), C.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("case", ["asym_Q", "nonpos_R_diag", "nan_q", "neg_n_g", "g_lo_gt_hi", "too_many_rows",
+                                  "null_Gx", "gN_lo_gt_hi", "lin_on_zero_weight"])
+def test_invalid_general_problems_rejected_on_host(lib, case):
+    """Full weights must be symmetric with a positive diagonal, linear terms
+    finite and zero where a diagonal weight is zero, general rows well formed
+    with lower bounds below upper bounds (checked before any device call)."""
+    from tests.problems import general
+    p = general([2, 1], 3, 2, seed=71, n_g=2, n_gN=1, box=True)
+
+    def mutate(f, ints):
+        if case == "asym_Q":
+            f["Q"][1, 0, 2] += 0.5
+        elif case == "nonpos_R_diag":
+            f["R"][0, 1, 1] = 0.0
+        elif case == "nan_q":
+            f["q"][2, 1] = np.nan
+        elif case == "neg_n_g":
+            ints["n_g"] = -1
+        elif case == "g_lo_gt_hi":
+            f["g_lo"][1, 0] = f["g_hi"][1, 0] + 1.0
+        elif case == "too_many_rows":
+            ints["n_g"] = 300
+        elif case == "null_Gx":
+            f["Gx"] = None
+        elif case == "gN_lo_gt_hi":
+            f["gN_lo"][0, 0] = f["gN_hi"][0, 0] + 1.0
+        elif case == "lin_on_zero_weight":
+            ints["weights_full"] = 0
+            f["Q"] = np.ones((len(p.anc) - 1, p.nx))
+            f["Q"][3, 1] = 0.0
+            f["R"] = np.ones((len(p.anc) - 1, p.nu))
+            f["QN"] = np.ones((p.n_leaf, p.nx))
+
+    rc, h = _desc_call_general(p, mutate)
+    assert rc == (-6 if case == "too_many_rows" else -1), rc
+    assert not h.value

@@ -13,7 +13,7 @@ import pytest
 
 from oracle.spock_oracle import Oracle
 from paper_2505_12078_b300 import synth
-from tests.problems import constrained, unconstrained
+from tests.problems import constrained, general, unconstrained
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,7 +41,30 @@ CASES = {
     "avar0_branch8": lambda: constrained([8, 1], 9, 4, seed=26, avar=0.0, uball=1.0),
     # nx + nu = 150 > 128: team sweeps (8 warps per team), widest mat-vec variants
     "team_100x50": lambda: constrained([2, 1, 1], 100, 50, seed=27, avar=0.5, uball=3.0),
+    # full weights, linear cost terms, general constraint rows (Sec. 3.1-3.2, Prop. 1)
+    "full_lin_box": lambda: general([2, 2, 1], 5, 3, seed=61, avar=0.5, box=True),
+    "rows_ball_diag_lin": lambda: _with_ball(general([3, 1, 1], 6, 3, seed=62, avar=0.4, dense=False, n_g=3,
+                                                     n_gN=2, box=True), 1.2),
+    "full_rows_cta": lambda: general([2, 1, 1], 24, 12, seed=63, avar=0.6, n_g=4, n_gN=2, box=True),
+    "full_rows_100x50": lambda: general([2, 1], 100, 50, seed=64, avar=0.5, n_g=3, n_gN=1),
+    # correlated full weights on a chain: the (x, u) block of L'L sets ||L||
+    "full_corr_chain": lambda: _correlated(general([1, 1, 1], 6, 2, seed=65, avar=1.0, n_g=1, box=True)),
 }
+
+
+def _correlated(p):
+    """Q^c = 11' + 0.1 I and Q_N = 11' + 0.1 I: the scaled cost factor's Gram has
+    an eigenvalue near nx / 1.1, above the (y, s) blocks' (about 3.7)."""
+    nx = p.nx
+    W = np.ones((nx, nx)) + 0.1 * np.eye(nx)
+    p.Q = np.broadcast_to(W, (len(p.anc) - 1, nx, nx)).copy()
+    p.QN = np.broadcast_to(W, (p.n_leaf, nx, nx)).copy()
+    return p
+
+
+def _with_ball(p, r):
+    p.u_ball = np.full(p.n_nonleaf, float(r))
+    return p
 
 
 def _pair(name):
@@ -137,7 +160,8 @@ def test_fixed_iterations_cp_fp64(name):
     assert abs(res["risk"] - ref["risk"]) <= 1e-10 * max(1, abs(ref["risk"]))
 
 
-@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "team_100x50"])
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "team_100x50",
+                                  "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "full_rows_100x50"])
 def test_fixed_iterations_spock_fp64(name):
     """SPOCK (Alg. 4 with Anderson directions) for a fixed iteration count in
     FP64: same branch sequence counts and iterate within 1e-10 relative."""
@@ -158,7 +182,7 @@ def test_fixed_iterations_spock_fp64(name):
     assert _relerr(v, ref["v"]) < 1e-10
 
 
-@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "chain_only"])
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "chain_only", "full_lin_box", "rows_ball_diag_lin"])
 def test_converged_fp32_vs_oracle(name):
     """FP32 iteration to ||v - T(v)||_inf <= 1e-4 against the oracle's converged
     FP64 solution: risk value and u^0 within 1e-3 relative; x/u everywhere
@@ -174,7 +198,8 @@ def test_converged_fp32_vs_oracle(name):
     assert np.all(np.abs(res["x"]) <= 5 + 1e-2)
 
 
-@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "avar0_branch8"])
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "avar0_branch8",
+                                  "full_lin_box", "rows_ball_diag_lin", "full_rows_cta"])
 def test_fp64_check_matches_oracle(name):
     """FP64 exit check (Sec. 5.3) through spock_check on the oracle's own
     iterate after 25 SPOCK iterations: xi1, xi2 (Eq. xi1k), the primal
