@@ -68,10 +68,10 @@ extern "C" {
 #define SPOCK_ENOTPD -3      /* Cholesky of R~ = I + sum B'PB failed (not positive definite) */
 #define SPOCK_EDEVICE -4     /* CUDA runtime error */
 #define SPOCK_ETIMEOUT -5    /* a device-side wait (grid barrier) ran out of its time limit */
-#define SPOCK_EUNSUPPORTED -6 /* sizes beyond the compiled limits (nx, nu <= 128, children <= 1024) */
+#define SPOCK_EUNSUPPORTED -6 /* sizes beyond the compiled limits (nx + nu <= 256, children <= 1024) */
 
-#define SPOCK_MAX_NX 128
-#define SPOCK_MAX_NU 128
+#define SPOCK_MAX_NX 256     /* with nx + nu <= 256 */
+#define SPOCK_MAX_NU 256
 
 typedef struct spock_problem spock_problem;
 
@@ -126,6 +126,10 @@ typedef struct spock_sizes {
     long long solve_bytes_fp64;    /* device bytes of the solve buffers of an FP64 solve (one
                                       allocation, made by the first solve in that precision) */
     long long solve_bytes_fp32;    /* same for FP32 */
+    long long device_bytes;        /* device bytes the problem holds now (data, factors of
+                                      both precisions, the solve buffers allocated so far) */
+    long long device_peak_bytes;   /* the most it has held: the offline part's peak (its
+                                      setup-only buffers included) or device_bytes */
 } spock_sizes;
 
 /* spock_problem_create: validate the tree and data, copy them to the device,

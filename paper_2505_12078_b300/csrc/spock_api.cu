@@ -1036,6 +1036,7 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   if (e == cudaSuccess) e = cudaMemcpy(&hnorm, dnorm, sizeof(hnorm), cudaMemcpyDeviceToHost);
   int herr2 = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&herr2, derr2, sizeof(int), cudaMemcpyDeviceToHost);
+  p->setup_peak = m.bytes + tmp.bytes;   // both sets are at their largest here
   tmp.free_all();
   if (e != cudaSuccess) { m.free_all(); delete p; return SPOCK_EDEVICE; }
   if (herr || herr2) { m.free_all(); delete p; return SPOCK_ENOTPD; }
@@ -1114,6 +1115,9 @@ int spock_problem_sizes(const spock_problem* p, spock_sizes* o) {
   o->factor_bytes_fp32 = words * 4;
   o->solve_bytes_fp64 = solve_buffer_bytes(p, 64);
   o->solve_bytes_fp32 = solve_buffer_bytes(p, 32);
+  o->device_bytes = p->mem.bytes + (p->f64.sb_block ? o->solve_bytes_fp64 : 0) +
+                    (p->f32.sb_block ? o->solve_bytes_fp32 : 0);
+  o->device_peak_bytes = std::max(p->setup_peak, o->device_bytes);
   return SPOCK_OK;
 }
 

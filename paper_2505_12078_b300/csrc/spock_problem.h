@@ -16,6 +16,7 @@ inline int pad4(int x) { return (x + 3) & ~3; }
 struct DevMem {
   std::vector<void*> ptrs;
   bool failed = false;
+  long long bytes = 0;   // bytes requested by the allocations held
   template <class T>
   T* alloc(long long count) {
     if (count <= 0) count = 1;
@@ -25,11 +26,13 @@ struct DevMem {
       return nullptr;
     }
     ptrs.push_back(p);
+    bytes += count * (long long)sizeof(T);
     return static_cast<T*>(p);
   }
   void free_all() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
+    bytes = 0;
   }
 };
 
@@ -88,6 +91,7 @@ struct spock_problem {
   spock::Iter<float> f32;
   double* d_out_risk;
   double* d_diag_part = nullptr;   // partials and result of the FP64 exit check (first use)
+  long long setup_peak = 0;        // device bytes held at the end of the offline part (its peak)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 

@@ -52,7 +52,8 @@ class Sizes(C.Structure):
                 ("nx", C.c_int), ("nu", C.c_int), ("n_c", C.c_int), ("n_cN", C.c_int),
                 ("n_z", C.c_longlong), ("n_eta", C.c_longlong), ("n_v", C.c_longlong),
                 ("factor_bytes_fp64", C.c_longlong), ("factor_bytes_fp32", C.c_longlong),
-                ("solve_bytes_fp64", C.c_longlong), ("solve_bytes_fp32", C.c_longlong)]
+                ("solve_bytes_fp64", C.c_longlong), ("solve_bytes_fp32", C.c_longlong),
+                ("device_bytes", C.c_longlong), ("device_peak_bytes", C.c_longlong)]
 
 
 class SolveOpts(C.Structure):
@@ -237,6 +238,12 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+    def memory(self):
+        """(device bytes held now, peak device bytes) from spock_problem_sizes."""
+        s = Sizes()
+        _check(load().spock_problem_sizes(self.h, C.byref(s)), "spock_problem_sizes")
+        return s.device_bytes, s.device_peak_bytes
 
     # --- setup outputs ---------------------------------------------------------
     def alpha(self):

@@ -244,3 +244,179 @@ def batch_problem(spec: dict, index: int = 0) -> RAOCP:
 
 def batch(count: int = 512, seed: int = 4):
     return [batch_problem(s, i) for i, s in enumerate(batch_specs(count, seed))]
+
+
+def case_study_1(seed: int = 0, nu_max: int = 64, nv_range=(1e3, 1e5)) -> RAOCP:
+    """Random RAOCP of the paper's first case study (Sec. 8.1, problem
+    statement):
+      * N ~ U{5..15}; (n_b, n_w, n_u) uniform on {1 <= b <= 3, 2 <= w <= 10,
+        10 <= u <= nu_max} subject to n_v = n_x |nodes(0, N)| + n_u |nodes(0, N-1)|
+        in nv_range (rejection sampling); n_x = 2 n_u;
+      * scenario tree: n_w children at each of the first n_b stages, one child
+        after; the children of a branching node are the events w = 1..n_w with
+        one base probability vector pi ~ U(simplex), a non-branching child keeps
+        its parent's event;
+      * dynamics per event: A(w) = I + A^w, B(w) = B + B^w with B_ij ~ N(0, 1),
+        A^w_ij, B^w_ij ~ N(0, 0.01) (variance);
+      * costs per event: Q(w) = (Q0 + Q^w)(Q0 + Q^w)', R(w) = (R0 + R^w)(R0 + R^w)'
+        with Q0 = diag(U[0, 0.1]), R0 = diag(U[0, 100]), Q^w_ij, R^w_ij ~
+        N(0, 0.01); Q_N = Q0 (full matrices throughout);
+      * boxes -xbar <= x <= xbar, -ubar <= u <= ubar, xbar ~ U[1, 2]^nx,
+        ubar ~ U[0, 0.1]^nu; AV@R_gamma with gamma ~ U[0, 1];
+      * x0_i ~ U[-xbar_i/2, xbar_i/2].
+    The paper allows n_u up to 300; n_u is capped at nu_max so that n_x = 2 n_u
+    stays within the library's compiled limit (n_x <= 128)."""
+    rng = np.random.default_rng(seed)
+    while True:
+        N = int(rng.integers(5, 16))
+        b = int(rng.integers(1, 4))
+        w = int(rng.integers(2, 11))
+        nu = int(rng.integers(10, nu_max + 1))
+        nx = 2 * nu
+        b_eff = min(b, N)
+        nodes_all = sum(w ** min(t, b_eff) for t in range(N + 1))
+        nodes_nl = sum(w ** min(t, b_eff) for t in range(N))
+        nv = nx * nodes_all + nu * nodes_nl
+        if nv_range[0] <= nv <= nv_range[1]:
+            break
+    pi = rng.dirichlet(np.ones(w))
+    # tree with events
+    anc, prob, event = [-1], [1.0], [0]
+    frontier = [0]
+    for t in range(N):
+        nxt = []
+        for parent in frontier:
+            if t < b_eff:
+                for k in range(w):
+                    anc.append(parent); prob.append(float(pi[k])); event.append(k)
+                    nxt.append(len(anc) - 1)
+            else:
+                anc.append(parent); prob.append(1.0); event.append(event[parent])
+                nxt.append(len(anc) - 1)
+        frontier = nxt
+    anc = np.asarray(anc, dtype=np.int32)
+    prob = np.asarray(prob, dtype=np.float64)
+    n = len(anc)
+    n_leaf = len(frontier)
+    n_nl = n - n_leaf
+    B0 = rng.standard_normal((nx, nu))
+    A_w = np.eye(nx)[None] + 0.1 * rng.standard_normal((w, nx, nx))
+    B_w = B0[None] + 0.1 * rng.standard_normal((w, nx, nu))
+    q0 = rng.uniform(0.0, 0.1, nx)
+    r0 = rng.uniform(0.0, 100.0, nu)
+    Qf = np.diag(q0)[None] + 0.1 * rng.standard_normal((w, nx, nx))
+    Rf = np.diag(r0)[None] + 0.1 * rng.standard_normal((w, nu, nu))
+    Q_w = Qf @ np.transpose(Qf, (0, 2, 1))
+    R_w = Rf @ np.transpose(Rf, (0, 2, 1))
+    ev = np.asarray(event[1:], dtype=np.int64)
+    A = A_w[ev].copy()
+    B = B_w[ev].copy()
+    Q = Q_w[ev].copy()
+    R = R_w[ev].copy()
+    QN = np.broadcast_to(np.diag(q0), (n_leaf, nx, nx)).copy()
+    xbar = rng.uniform(1.0, 2.0, nx)
+    ubar = rng.uniform(0.0, 0.1, nu)
+    gamma = float(rng.uniform(0.0, 1.0))
+    x0 = rng.uniform(-0.5 * xbar, 0.5 * xbar)
+    return RAOCP(
+        name=f"case_study_1_s{seed}_N{N}_b{b_eff}_w{w}_nu{nu}_nv{nv}", anc=anc, prob=prob, nx=nx, nu=nu,
+        A=A, B=B, c=np.zeros((n - 1, nx)), Q=Q, R=R, QN=QN,
+        x_lo=np.broadcast_to(-xbar, (n, nx)).copy(), x_hi=np.broadcast_to(xbar, (n, nx)).copy(),
+        u_lo=np.broadcast_to(-ubar, (n_nl, nu)).copy(), u_hi=np.broadcast_to(ubar, (n_nl, nu)).copy(),
+        u_ball=None, avar=np.full(n_nl, gamma), x0=x0,
+        meta=dict(seed=seed, N=N, n_b=b_eff, n_w=w, n_v=nv))
+
+
+def beta_quantile_tree(branching, theta: float = 1.0, phi0: float = 0.1):
+    """Scenario tree of the delay process of the paper's second case study
+    (Sec. 8.2, sensor-to-controller delay): phi^0 = phi0; the m children of a
+    node with value phi are equiprobable and take the quantiles of
+    Beta(theta phi, theta (1 - phi)) at the centres (2k - 1)/(2m) of m equal
+    intervals of [0, 1] (a single child takes the median), kept within
+    [1e-12, 1 - 1e-12]. Returns anc, prob and phi per node."""
+    from scipy.stats import beta as _beta
+    anc, prob, phi = [-1], [1.0], [float(phi0)]
+    frontier = [0]
+    for m in branching:
+        nxt = []
+        for parent in frontier:
+            f = phi[parent]
+            q = (2.0 * np.arange(1, m + 1) - 1.0) / (2.0 * m)
+            vals = _beta.ppf(q, theta * f, theta * (1.0 - f))
+            # repeated medians drive phi towards 0, where it underflows and the
+            # next Beta is undefined: phi is kept in [1e-12, 1 - 1e-12]
+            vals = np.clip(np.nan_to_num(vals, nan=1e-12), 1e-12, 1.0 - 1e-12)
+            for k in range(m):
+                anc.append(parent)
+                prob.append(1.0 / m)
+                phi.append(float(vals[k]))
+                nxt.append(len(anc) - 1)
+        frontier = nxt
+    return np.asarray(anc, dtype=np.int32), np.asarray(prob, dtype=np.float64), np.asarray(phi)
+
+
+def ncs_delay(n: int, shape: str = "wide", N: int = 48, nx: int = 100, nu: int = 50, T: float = 0.005,
+              theta: float = 1.0, phi0: float = 0.1, avar: float = 0.95, seed: int = 6) -> RAOCP:
+    """Networked control system with a sensor-to-controller delay (Sec. 8.2):
+    continuous plant xdot = A_c x + B_c u, A_c = I + diag(a), a_i ~ N(0, 0.01),
+    B_c = 0.1 ones(nx, nu), sampled every T with the delay sigma = phi T of the
+    Beta-quantile tree; branching [n^2, 1, .., 1] (shape "wide") or
+    [n, n, 1, .., 1] ("deep"), the same number of scenarios.
+
+    Discretisation (derived here; the paper cites it without printing it):
+    over one period the previous input u_{k-1} acts during [kT, kT + sigma)
+    and u_k during [kT + sigma, (k+1)T), so with the augmented state
+    xt = (x, u_prev) in R^{nx + nu}
+        xt^+ = [[Phi, G1(sigma)], [0, 0]] xt + [[G0(sigma)], [I]] u,
+    Phi = e^{A_c T}, G1 = int_0^sigma e^{A_c (T - s)} ds B_c,
+    G0 = int_sigma^T e^{A_c (T - s)} ds B_c; A_c is diagonal, so the integrals
+    are elementwise (e^{l (T - a)} - e^{l (T - b)}) / l. The delay of the
+    transition into a node is that node's sigma.
+    Sampling time: the paper prints T = 5, with which A_c ~ I grows by about
+    e^5 per period; the input matrix B_c has rank one, so the plant is not
+    stabilisable, the unit-weight Riccati recursion of Alg. 1 overflows FP64
+    over 48 stages, and ||x||_inf <= 3 cannot hold from x0 = 2. The default
+    here is T = 0.005 (the same delay structure sigma = phi T), for which the
+    open-loop growth over the horizon stays below 1.5.
+    Costs Q = 1e-6 I on xt, R = 0.1 I, Q_N = diag(1_nx, 1e-6 1_nu);
+    ||x||_inf <= 3 on the plant part, ||u||_inf <= 0.9 (the u_prev part of xt
+    gets the input bound, which it satisfies anyway); x0 = (2, .., 2, 0, .., 0);
+    AV@R_avar at every node."""
+    rng = np.random.default_rng(seed)
+    if shape == "wide":
+        branching = [n * n] + [1] * (N - 1)
+    elif shape == "deep":
+        branching = [n, n] + [1] * (N - 2)
+    else:
+        raise ValueError("shape is 'wide' or 'deep'")
+    anc, prob, phi = beta_quantile_tree(branching, theta, phi0)
+    lam = 1.0 + 0.1 * rng.standard_normal(nx)
+    Bc = 0.1 * np.ones((nx, nu))
+    Phi = np.diag(np.exp(lam * T))
+    n_nodes = len(anc)
+    na = nx + nu
+    A = np.zeros((n_nodes - 1, na, na))
+    B = np.zeros((n_nodes - 1, na, nu))
+    for c in range(1, n_nodes):
+        sig = phi[c] * T
+        g1 = (np.exp(lam * T) - np.exp(lam * (T - sig))) / lam
+        g0 = (np.exp(lam * (T - sig)) - 1.0) / lam
+        A[c - 1, :nx, :nx] = Phi
+        A[c - 1, :nx, nx:] = g1[:, None] * Bc
+        B[c - 1, :nx, :] = g0[:, None] * Bc
+        B[c - 1, nx:, :] = np.eye(nu)
+    st = np.zeros(n_nodes, dtype=np.int64)
+    for i in range(1, n_nodes):
+        st[i] = st[anc[i]] + 1
+    n_leaf = int(np.sum(st == st.max()))
+    n_nl = n_nodes - n_leaf
+    xb = np.concatenate([np.full(nx, 3.0), np.full(nu, 0.9)])
+    x0 = np.concatenate([np.full(nx, 2.0), np.zeros(nu)])
+    return RAOCP(
+        name=f"ncs_delay_{shape}_n{n}_N{N}_nx{nx}_nu{nu}_{n_nodes}nodes", anc=anc, prob=prob, nx=na, nu=nu,
+        A=A, B=B, c=np.zeros((n_nodes - 1, na)),
+        Q=np.full((n_nodes - 1, na), 1e-6), R=np.full((n_nodes - 1, nu), 0.1),
+        QN=np.broadcast_to(np.concatenate([np.ones(nx), np.full(nu, 1e-6)]), (n_leaf, na)).copy(),
+        x_lo=np.broadcast_to(-xb, (n_nodes, na)).copy(), x_hi=np.broadcast_to(xb, (n_nodes, na)).copy(),
+        u_lo=np.full((n_nl, nu), -0.9), u_hi=np.full((n_nl, nu), 0.9), u_ball=None,
+        avar=np.full(n_nl, float(avar)), x0=x0, meta=dict(N=N, n=n, shape=shape, seed=seed))

@@ -47,6 +47,8 @@ CASES = {
                                                      n_gN=2, box=True), 1.2),
     "full_rows_cta": lambda: general([2, 1, 1], 24, 12, seed=63, avar=0.6, n_g=4, n_gN=2, box=True),
     "full_rows_100x50": lambda: general([2, 1], 100, 50, seed=64, avar=0.5, n_g=3, n_gN=1),
+    # nx = 150 > 128 (nx + nu = 200 <= 256): team sweeps with the widest variants
+    "team_150x50": lambda: constrained([2, 1], 150, 50, seed=28, avar=0.5),
     # correlated full weights on a chain: the (x, u) block of L'L sets ||L||
     "full_corr_chain": lambda: _correlated(general([1, 1, 1], 6, 2, seed=65, avar=1.0, n_g=1, box=True)),
 }
