@@ -91,3 +91,30 @@ def test_full_size_converged_fp32_large():
     # two approximations of the same optimum, each within the 1e-3 target of it
     assert abs(r32["risk"] - r64["risk"]) <= 2e-3 * max(1.0, abs(r64["risk"]))
     assert np.max(np.abs(r32["u"][0] - r64["u"][0])) <= 2e-3 * max(1.0, np.max(np.abs(r64["u"][0])))
+
+
+def test_full_size_converged_against_oracle_golden():
+    """The benchmark solve against the oracle's own solve of the same problem to
+    ||v - T(v)||_inf <= 1e-4 (tests/golden/large_raocp_converged.npz, written by
+    tests/golden/make_converged.py from the oracle alone): the FP32 solve's x
+    and u within 1e-3 (relative to max(1, max|.|)) on the nodes whose path
+    weight under the oracle's maximising AV@R weights is positive (elsewhere
+    the optimal inputs need not be unique, reading C-19), the risk value
+    within 1e-3; the FP64 solve likewise. The whole-vector errors are printed."""
+    import os
+    spock = _spock()
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "large_raocp_converged.npz"))
+    p = synth.large_raocp()
+    g = spock.Problem(p)
+    sel = d["path_weight"] > 1e-9
+    seln = sel[:g.n_nl]
+    assert sel.sum() > 10
+    for prec in (32, 64):
+        r = g.solve(p.x0, spock.opts(precision=prec, tol=1e-4, max_iters=200000))
+        assert r["status"] == 0
+        ex = float(np.max(np.abs(r["x"][sel] - d["x"][sel]))) / max(1.0, float(np.max(np.abs(d["x"][sel]))))
+        eu = float(np.max(np.abs(r["u"][seln] - d["u"][seln]))) / max(1.0, float(np.max(np.abs(d["u"][seln]))))
+        er = abs(r["risk"] - float(d["risk"])) / max(1.0, abs(float(d["risk"])))
+        print(f"FP{prec}: x err {ex:.2e} u err {eu:.2e} on {int(sel.sum())} support nodes, risk err {er:.2e}, "
+              f"all-node x err {np.max(np.abs(r['x'] - d['x'])):.2e} u err {np.max(np.abs(r['u'] - d['u'])):.2e}")
+        assert ex <= 1e-3 and eu <= 1e-3 and er <= 1e-3, (prec, ex, eu, er)
