@@ -724,12 +724,79 @@ class Oracle:
         kappa = sla.solve_triangular(Rf, Qf.T @ r, lower=False)
         return -r - (Sm - Ym) @ kappa
 
+    class QRMemory:
+        """Anderson memory whose least-squares factorisation Y = Q R is updated
+        as pairs arrive and leave instead of being recomputed (the improvement
+        Sec. 6.2 suggests, with Givens rotations): dropping the oldest column
+        leaves R upper Hessenberg, which Givens rotations of neighbouring rows
+        make triangular again (the same rotations applied to the columns of
+        Q); a new column y is appended by Gram-Schmidt against Q with one
+        re-orthogonalisation, giving R's new last column (Q'y, ||y - QQ'y||)."""
+
+        def __init__(self, m):
+            self.m = m
+            self.S = []
+            self.Q = None          # n x k, orthonormal columns
+            self.R = np.zeros((0, 0))
+
+        def push(self, s, y):
+            if len(self.S) == self.m:
+                self._drop_oldest()
+            if self.Q is None:
+                h = np.zeros(0)
+                w = y.copy()
+            else:
+                h = self.Q.T @ y
+                w = y - self.Q @ h
+                h2 = self.Q.T @ w
+                w = w - self.Q @ h2
+                h = h + h2
+            rho = float(np.linalg.norm(w))
+            k = self.R.shape[0]
+            R = np.zeros((k + 1, k + 1))
+            R[:k, :k] = self.R
+            R[:k, k] = h
+            R[k, k] = rho
+            self.R = R
+            col = (w / rho if rho > 0 else w)[:, None]
+            self.Q = col if self.Q is None else np.hstack([self.Q, col])
+            self.S.append(s)
+
+        def _drop_oldest(self):
+            H = self.R[:, 1:].copy()            # k x (k-1), upper Hessenberg
+            Q = self.Q.copy()
+            k = H.shape[0]
+            for j in range(k - 1):
+                a, b = H[j, j], H[j + 1, j]
+                r = math.hypot(a, b)
+                c, sn = (1.0, 0.0) if r == 0.0 else (a / r, b / r)
+                Hj, Hj1 = H[j].copy(), H[j + 1].copy()
+                H[j], H[j + 1] = c * Hj + sn * Hj1, -sn * Hj + c * Hj1
+                Qj, Qj1 = Q[:, j].copy(), Q[:, j + 1].copy()
+                Q[:, j], Q[:, j + 1] = c * Qj + sn * Qj1, -sn * Qj + c * Qj1
+            self.R = H[:k - 1, :]
+            self.Q = Q[:, :k - 1]
+            self.S.pop(0)
+
+        def direction(self, r, k, rank_tol=1e-10):
+            """psi of Alg. 3 (type-II reading): kappa = R^{-1} Q'r, psi = -r -
+            (S - Y) kappa with Y kappa = Q Q'r; psi = -r for k <= m or when a
+            diagonal entry of R is below rank_tol ||Y||_F."""
+            if k <= self.m or not self.S:
+                return -r
+            fro = float(np.linalg.norm(self.R))
+            if fro == 0.0 or np.min(np.abs(np.diag(self.R))) < rank_tol * fro:
+                return -r
+            g = self.Q.T @ r
+            kappa = sla.solve_triangular(self.R, g, lower=False)
+            return -r - np.column_stack(self.S) @ kappa + self.Q @ g
+
     # -- SPOCK (Alg. 4) -------------------------------------------------------
     def initial_v(self):
         return np.zeros(self.lay.n_z + self.lay.n_eta)
 
     def solve(self, v0=None, tol=1e-4, max_iters=5000, method="spock", m=AA_MEMORY,
-              max_backtracks=30, rank_tol=1e-10, log=None):
+              max_backtracks=30, rank_tol=1e-10, log=None, aa="householder"):
         """Alg. 4 (SPOCK) or, with method="cp", plain CP iterates v <- T(v).
 
         Readings: the averagedness constant in rho is that of a firmly
@@ -739,7 +806,9 @@ class Oracle:
         termination when ||v - T(v)||_inf <= tol (eps_rel = 0). After a K1 step
         the residual r~ of the accepted point is the next iterate's residual.
         `log` (a list, optional) receives (k, n_T, ||r||_inf) at every outer
-        iteration.
+        iteration. aa="householder" factorises the Anderson least-squares
+        problem afresh at every iteration, aa="qr_update" keeps its QR
+        factorisation and updates it (QRMemory).
         """
         v = self.initial_v() if v0 is None else np.array(v0, dtype=np.float64)
         tv = self.T(v)
@@ -758,6 +827,7 @@ class Oracle:
         zeta = self.M_norm(r)
         omega_safe = zeta
         S, Y = [], []
+        qrm = self.QRMemory(m) if aa == "qr_update" else None
         v_prev = r_prev = None
         k = 0
         while True:
@@ -766,11 +836,17 @@ class Oracle:
             if np.max(np.abs(r)) <= tol or k >= max_iters:
                 break
             if v_prev is not None:
-                S.append(v - v_prev)
-                Y.append(r - r_prev)
-                if len(S) > m:
-                    S.pop(0); Y.pop(0)
-            psi = self.aa_direction(r, S, Y, k, m, rank_tol)
+                if qrm is not None:
+                    qrm.push(v - v_prev, r - r_prev)
+                else:
+                    S.append(v - v_prev)
+                    Y.append(r - r_prev)
+                    if len(S) > m:
+                        S.pop(0); Y.pop(0)
+            if qrm is not None:
+                psi = qrm.direction(r, k, rank_tol)
+            else:
+                psi = self.aa_direction(r, S, Y, k, m, rank_tol)
             omega = self.M_norm(r)
             v_prev, r_prev = v, r
             if omega <= C0 * zeta:

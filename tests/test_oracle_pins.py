@@ -775,3 +775,42 @@ def test_general_problem_diagnostics_vanish():
     assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
     assert r["infeas"] < 1e-6 and r["gap"] < 1e-5
     assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * max(1.0, abs(r["risk"]))
+
+
+# --- Anderson least squares with an updated QR factorisation (Sec. 6.2) ---------------
+def test_aa_qr_update_matches_a_fresh_least_squares_solve():
+    """The QR memory (Givens rotations to drop the oldest pair, Gram-Schmidt
+    to append) keeps Y = QR with Q orthonormal and R upper triangular through
+    many pushes, and its direction equals -r - (S - Y) kappa with kappa from a
+    fresh least-squares solve (numpy lstsq) of the last m pairs."""
+    rng = np.random.default_rng(81)
+    n, m = 40, 3
+    mem = Oracle.QRMemory(m)
+    S, Y = [], []
+    for it in range(12):
+        s_, y = rng.standard_normal(n), rng.standard_normal(n)
+        mem.push(s_, y)
+        S.append(s_); Y.append(y)
+        S, Y = S[-m:], Y[-m:]
+        Ym = np.column_stack(Y)
+        assert np.allclose(mem.Q @ mem.R, Ym, atol=1e-12)
+        assert np.allclose(mem.Q.T @ mem.Q, np.eye(len(Y)), atol=1e-12)
+        assert np.allclose(np.tril(mem.R, -1), 0.0)
+        r = rng.standard_normal(n)
+        kappa = np.linalg.lstsq(Ym, r, rcond=None)[0]
+        want = -r - (np.column_stack(S) - Ym) @ kappa
+        got = mem.direction(r, k=it + m + 1)
+        assert np.allclose(got, want, atol=1e-10)
+
+
+def test_spock_with_qr_update_follows_the_same_branches():
+    """SPOCK with the updated QR and with a fresh Householder factorisation
+    take the same K0/K1/K2 branches and reach the same iterate (FP64, a fixed
+    iteration count; the two factorisations differ only by rounding)."""
+    p = constrained([2, 2, 1], 3, 2, seed=82, avar=0.5, uball=2.0)
+    o = Oracle(p)
+    a = o.solve(tol=0.0, max_iters=60)
+    b = o.solve(tol=0.0, max_iters=60, aa="qr_update")
+    assert [e[1] for e in a["events"]] == [e[1] for e in b["events"]]
+    assert a["n_T"] == b["n_T"]
+    assert np.max(np.abs(a["v"] - b["v"])) < 1e-9 * max(1.0, np.max(np.abs(a["v"])))
