@@ -206,6 +206,11 @@ typedef struct spock_solve_opts {
     int method;           /* 0: SPOCK (Alg. 4 with Alg. 3, m = 3); 1: plain CP v <- T(v) */
     int warm_start;       /* 1: start from the problem's last iterate, 0: z = eta = 0 */
     int fp64_check;       /* 1 (FP32 only): finish with an FP64 residual check */
+    int aa_mode;          /* Anderson least squares (Alg. 3): 0 the 3 x 3 normal equations
+                             (Gram matrix accumulated in FP64, Cholesky; the default),
+                             1 a QR factorisation of Y kept up to date as pairs enter and
+                             leave (Givens rotations, Gram-Schmidt; Sec. 6.2), one more
+                             pass over the vectors per iteration */
 } spock_solve_opts;
 
 typedef struct spock_info {

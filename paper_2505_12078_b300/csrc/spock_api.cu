@@ -667,6 +667,7 @@ void spock_solve_opts_default(spock_solve_opts* o) {
   o->method = 0;
   o->warm_start = 0;
   o->fp64_check = 1;
+  o->aa_mode = 0;
 }
 
 int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
@@ -1225,7 +1226,7 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
   if (opts) o = *opts;
   else spock_solve_opts_default(&o);
   if ((o.precision != 32 && o.precision != 64) || !(o.tol >= 0) || o.max_iters < 0 ||
-      o.max_backtracks < 1 || o.method < 0 || o.method > 1)
+      o.max_backtracks < 1 || o.method < 0 || o.method > 1 || o.aa_mode < 0 || o.aa_mode > 1)
     return SPOCK_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = set_x0_dev(p, x0, st);
@@ -1233,6 +1234,7 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
   SolveOpts so{};
   so.tol = o.tol; so.max_iters = o.max_iters; so.max_backtracks = o.max_backtracks;
   so.method = o.method; so.rank_tol = (o.precision == 64) ? 1e-10 : 1e-5;
+  so.aa_qr = o.aa_mode == 1 ? 1 : 0;
   SolveCtl h{};
   float ms = 0.f;
   double res64 = -1.0;

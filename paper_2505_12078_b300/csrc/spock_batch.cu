@@ -351,7 +351,7 @@ cudaError_t enqueue(spock_batch* b, const SolveOpts& so, int warm, cudaStream_t 
 
 bool same_opts(const SolveOpts& a, const SolveOpts& b) {
   return a.tol == b.tol && a.max_iters == b.max_iters && a.max_backtracks == b.max_backtracks &&
-         a.method == b.method && a.rank_tol == b.rank_tol;
+         a.method == b.method && a.rank_tol == b.rank_tol && a.aa_qr == b.aa_qr;
 }
 
 // one replay of the captured graph (captured anew when the options change)
@@ -581,6 +581,7 @@ int spock_batch_solve(spock_batch* b, const double* x0, const spock_solve_opts* 
   SolveOpts so{};
   so.tol = o.tol; so.max_iters = o.max_iters; so.max_backtracks = o.max_backtracks; so.method = o.method;
   so.rank_tol = (o.precision == 64) ? 1e-10 : 1e-5;
+  so.aa_qr = o.aa_mode == 1 ? 1 : 0;
   float ms = 0.f;
   const int rc = b->precision == 64 ? run_graph<double>(b, so, o.warm_start ? 1 : 0, &ms)
                                     : run_graph<float>(b, so, o.warm_start ? 1 : 0, &ms);

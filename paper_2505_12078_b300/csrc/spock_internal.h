@@ -71,6 +71,7 @@ struct SolveOpts {
   double rank_tol;     // Anderson rank test (relative to ||Y||_F)
   unsigned long long wait_ns;   // limit of one grid-barrier wait (0: BARRIER_LIMIT_NS)
   int phantom;         // test hook: CTAs a single-problem launch's barriers expect beyond its grid
+  int aa_qr;           // 1: Anderson least squares by an updated QR factorisation (Y slots hold Q)
 };
 
 // Device control block of one solve (global memory, zeroed before a launch).

@@ -273,6 +273,7 @@ int spock_server_create(spock_problem* const* plants, int count, int precision, 
   s->plants.assign(plants, plants + count);
   s->so.tol = o.tol; s->so.max_iters = o.max_iters; s->so.max_backtracks = o.max_backtracks;
   s->so.method = o.method; s->so.rank_tol = precision == 64 ? 1e-10 : 1e-5;
+  s->so.aa_qr = o.aa_mode == 1 ? 1 : 0;
   // admission by device memory: plants in order while their solve buffers fit
   // in the budget (an explicit budget is clamped to the free memory less the
   // reserve; by default the free memory less the reserve)

@@ -1218,6 +1218,193 @@ __device__ __forceinline__ void stv(T* p, long long q, const T (&o)[Vec<T>::N]) 
   __stcg(reinterpret_cast<V*>(p) + q, x);
 }
 
+// Anderson memory with the least-squares factorisation Y = Q R kept up to
+// date (the improvement suggested in Sec. 6.2): pass A writes the new pair's s
+// into the S ring, parks y = r - r_prev in PSI and reduces Q'y, Q'r and y'r;
+// when the memory is full the oldest column is dropped by two Givens
+// rotations of R's rows (applied to Q's columns in pass B); pass B appends
+// w = y - Q h, h = Q'y (classical Gram-Schmidt), and reduces ||w||^2. Every
+// CTA then holds R (3 x 3, FP64) and g = Q'r; kappa = R^{-1} g, and the
+// direction is psi = -r - S kappa + Q g. Returns false when the launch fails.
+template <class T>
+__device__ bool aa_qr_update(const Prob<T>& P, const SolveBufs<T>& B, const SolveOpts& o, Grid& g, int k,
+                             const T* V, const T* TV, int& head, int& count, double (&Rq)[AA_M][AA_M],
+                             double (&qsc)[AA_M], int& qcount, double (&kap)[AA_M], double (&kapY)[AA_M],
+                             bool& use_aa) {
+  constexpr int VN = Vec<T>::N;
+  const long long nv = P.nv, nvec = nv / VN, ss = B.sstride;
+  const long long gtid = (long long)g.rank * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)g.size * blockDim.x;
+  const bool push = k >= 1;
+  const int slot = head;
+  T* Sslot = B.S + slot * ss;
+  // pass A
+  double acc[NRED];
+#pragma unroll
+  for (int a = 0; a < NRED; ++a) acc[a] = 0.0;
+  auto elemA = [&](T v, T tv, T vp, T rp, T q0, T q1, T q2, T& so, T& yo, T& ro) {
+    const T r = v - tv;
+    ro = r;
+    so = v - vp;
+    const T y = r - rp;
+    yo = y;
+    const T ql[AA_M] = {q0, q1, q2};
+#pragma unroll
+    for (int l = 0; l < AA_M; ++l) {
+      acc[l] = fma((double)ql[l], (double)y, acc[l]);
+      acc[AA_M + l] = fma((double)ql[l], (double)r, acc[AA_M + l]);
+    }
+    acc[2 * AA_M] = fma((double)y, (double)r, acc[2 * AA_M]);
+  };
+  for (long long q = gtid; q < nvec; q += gstride) {
+    T v[VN], tv[VN], vp[VN], rp[VN], q0[VN], q1[VN], q2[VN], so[VN], yo[VN], ro[VN];
+    ldv(V, q, v); ldv(TV, q, tv);
+    if (push) {
+      ldv((const T*)B.VP, q, vp); ldv((const T*)B.RP, q, rp);
+      ldv((const T*)B.Y, q, q0); ldv((const T*)B.Y + ss, q, q1); ldv((const T*)B.Y + 2 * ss, q, q2);
+#pragma unroll
+      for (int c = 0; c < VN; ++c) elemA(v[c], tv[c], vp[c], rp[c], q0[c], q1[c], q2[c], so[c], yo[c], ro[c]);
+      stv(Sslot, q, so); stv(B.PSI, q, yo);
+    } else {
+#pragma unroll
+      for (int c = 0; c < VN; ++c) ro[c] = v[c] - tv[c];
+    }
+    stv(B.VP, q, v); stv(B.RP, q, ro);
+  }
+  for (long long e = nvec * VN + gtid; e < nv; e += gstride) {
+    const T v = ldc(V + e), tv = ldc(TV + e);
+    T so, yo, ro = v - tv;
+    if (push) {
+      elemA(v, tv, ldc(B.VP + e), ldc(B.RP + e), ldc(B.Y + e), ldc(B.Y + ss + e), ldc(B.Y + 2 * ss + e), so, yo, ro);
+      stc(Sslot + e, so);
+      stc(B.PSI + e, yo);
+    }
+    stc(B.VP + e, v);
+    stc(B.RP + e, ro);
+  }
+  {
+    __shared__ double scr[NRED * 32];
+    if (!grid_allreduce(g, acc, scr, -1)) return false;
+  }
+  if (!push) return true;
+  double hy[AA_M], hr[AA_M];
+  for (int l = 0; l < AA_M; ++l) {
+    hy[l] = l < qcount ? acc[l] * qsc[l] : 0.0;
+    hr[l] = l < qcount ? acc[AA_M + l] * qsc[l] : 0.0;
+  }
+  const double yr = acc[2 * AA_M];
+  // new basis b_j = sum_i cm[j][i] slot_i for the kept columns
+  double cm[AA_M][AA_M];
+  for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) cm[a][b] = (a == b && a < qcount) ? qsc[a] : 0.0;
+  int kept = qcount;
+  if (qcount == AA_M) {   // drop the oldest column: R[:, 1:] is Hessenberg, two rotations
+    double H[AA_M][AA_M - 1];
+    for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M - 1; ++b) H[a][b] = Rq[a][b + 1];
+    double rot[AA_M][AA_M];   // rows of the product of rotations (applied to Q's columns)
+    for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) rot[a][b] = (a == b) ? 1.0 : 0.0;
+    for (int j = 0; j < AA_M - 1; ++j) {
+      const double a = H[j][j], b = H[j + 1][j];
+      const double r = hypot(a, b);
+      const double c = r == 0.0 ? 1.0 : a / r, sn = r == 0.0 ? 0.0 : b / r;
+      for (int q = 0; q < AA_M - 1; ++q) {
+        const double x0 = H[j][q], x1 = H[j + 1][q];
+        H[j][q] = c * x0 + sn * x1;
+        H[j + 1][q] = -sn * x0 + c * x1;
+      }
+      for (int q = 0; q < AA_M; ++q) {
+        const double x0 = rot[j][q], x1 = rot[j + 1][q];
+        rot[j][q] = c * x0 + sn * x1;
+        rot[j + 1][q] = -sn * x0 + c * x1;
+      }
+    }
+    kept = AA_M - 1;
+    for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) Rq[a][b] = 0.0;
+    for (int a = 0; a < kept; ++a) for (int b = a; b < kept; ++b) Rq[a][b] = H[a][b];
+    double hy2[AA_M] = {0.0, 0.0, 0.0}, hr2[AA_M] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < kept; ++a)
+      for (int b = 0; b < AA_M; ++b) {
+        cm[a][b] = rot[a][b] * qsc[b];
+        hy2[a] += rot[a][b] * hy[b];
+        hr2[a] += rot[a][b] * hr[b];
+      }
+    for (int b = 0; b < AA_M; ++b) cm[kept][b] = 0.0;
+    for (int a = 0; a < AA_M; ++a) { hy[a] = hy2[a]; hr[a] = hr2[a]; }
+  }
+  // pass B: rotated basis and w = y - sum_j hy_j b_j into slot `kept`
+  const T c00 = (T)cm[0][0], c01 = (T)cm[0][1], c02 = (T)cm[0][2];
+  const T c10 = (T)cm[1][0], c11 = (T)cm[1][1], c12 = (T)cm[1][2];
+  const T h0 = (T)hy[0], h1 = (T)hy[1];
+  double wacc[NRED];
+#pragma unroll
+  for (int a = 0; a < NRED; ++a) wacc[a] = 0.0;
+  T* Yk = B.Y + kept * ss;
+  auto elemB = [&](T q0, T q1, T q2, T y, T& b0, T& b1, T& w) {
+    b0 = kept > 0 ? c00 * q0 + c01 * q1 + c02 * q2 : T(0);
+    b1 = kept > 1 ? c10 * q0 + c11 * q1 + c12 * q2 : T(0);
+    w = y - h0 * b0 - h1 * b1;
+    wacc[0] = fma((double)w, (double)w, wacc[0]);
+  };
+  for (long long q = gtid; q < nvec; q += gstride) {
+    T q0[VN], q1[VN], q2[VN], y[VN], b0[VN], b1[VN], w[VN];
+    ldv((const T*)B.Y, q, q0); ldv((const T*)B.Y + ss, q, q1); ldv((const T*)B.Y + 2 * ss, q, q2);
+    ldv((const T*)B.PSI, q, y);
+#pragma unroll
+    for (int c = 0; c < VN; ++c) elemB(q0[c], q1[c], q2[c], y[c], b0[c], b1[c], w[c]);
+    if (kept > 0) stv(B.Y, q, b0);
+    if (kept > 1) stv(B.Y + ss, q, b1);
+    stv(Yk, q, w);
+  }
+  for (long long e = nvec * VN + gtid; e < nv; e += gstride) {
+    T b0, b1, w;
+    elemB(ldc(B.Y + e), ldc(B.Y + ss + e), ldc(B.Y + 2 * ss + e), ldc(B.PSI + e), b0, b1, w);
+    if (kept > 0) stc(B.Y + e, b0);
+    if (kept > 1) stc(B.Y + ss + e, b1);
+    stc(Yk + e, w);
+  }
+  {
+    __shared__ double scr2[NRED * 32];
+    if (!grid_allreduce(g, wacc, scr2, -1)) return false;
+  }
+  const double rho = sqrt(fmax(wacc[0], 0.0));
+  for (int a = 0; a < kept; ++a) { Rq[a][kept] = hy[a]; qsc[a] = 1.0; }
+  Rq[kept][kept] = rho;
+  qsc[kept] = rho > 0.0 ? 1.0 / rho : 0.0;
+  qcount = kept + 1;
+  // Q'r in the new basis: w'r / rho = (y'r - h . hr) / rho
+  double gq[AA_M] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < kept; ++a) gq[a] = hr[a];
+  {
+    double wr = yr;
+    for (int a = 0; a < kept; ++a) wr -= hy[a] * hr[a];
+    gq[kept] = rho > 0.0 ? wr / rho : 0.0;
+  }
+  if (count < AA_M) ++count;
+  head = (head + 1) % AA_M;
+  if (k > AA_M && qcount > 0) {
+    double fro = 0.0;
+    for (int a = 0; a < qcount; ++a) for (int b = a; b < qcount; ++b) fro += Rq[a][b] * Rq[a][b];
+    fro = sqrt(fro);
+    bool good = fro > 0.0;
+    for (int a = 0; a < qcount && good; ++a) good = fabs(Rq[a][a]) >= o.rank_tol * fro;
+    if (good) {
+      double kl[AA_M];
+      for (int j = qcount - 1; j >= 0; --j) {
+        double sacc = gq[j];
+        for (int l = j + 1; l < qcount; ++l) sacc -= Rq[j][l] * kl[l];
+        kl[j] = sacc / Rq[j][j];
+      }
+      // logical column j of Q pairs with the j-th oldest s in the S ring
+      const int start = (count < AA_M) ? 0 : head;
+      for (int j = 0; j < qcount; ++j) {
+        kap[(start + j) % AA_M] = kl[j];
+        kapY[j] = gq[j] * qsc[j];
+      }
+      use_aa = true;
+    }
+  }
+  return true;
+}
+
 // The SuperMann iteration (Alg. 4 with Anderson directions, Alg. 3) on one
 // problem by the group g: the whole grid of a single-problem launch, or one
 // CTA of the batched launch. Every CTA of the group runs the same scalar
@@ -1261,6 +1448,11 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
     double G[AA_M][AA_M];
     for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) G[a][b] = 0.0;
     int count = 0, head = 0;
+    // updated-QR mode: Y = Q R with the columns of Q in the Y slots in logical
+    // order (oldest first), slot j holding Q's column j divided by qsc[j]
+    double Rq[AA_M][AA_M], qsc[AA_M];
+    for (int a = 0; a < AA_M; ++a) { qsc[a] = 1.0; for (int b = 0; b < AA_M; ++b) Rq[a][b] = 0.0; }
+    int qcount = 0;
     while (true) {
       if (res <= o.tol) { status = 0; break; }
       if (k >= o.max_iters) { status = 1; break; }
@@ -1270,9 +1462,12 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
       PhaseClock pc;
       pc.start(g.prof);
       // --- Anderson memory update (pairs (v^k - v^{k-1}, r^k - r^{k-1})) ---
-      double kap[AA_M] = {0.0, 0.0, 0.0};
+      double kap[AA_M] = {0.0, 0.0, 0.0};    // coefficients of the S slots
+      double kapY[AA_M] = {0.0, 0.0, 0.0};   // coefficients of the Y slots
       bool use_aa = false;
-      {
+      if (o.aa_qr) {
+        if (!aa_qr_update<T>(P, B, o, g, k, V, TV, head, count, Rq, qsc, qcount, kap, kapY, use_aa)) goto fail;
+      } else {
         const int slot = head;
         const bool push = (k >= 1);
         double dd[NRED];
@@ -1370,6 +1565,7 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
               kl[j] = s / Rm[j][j];
             }
             for (int j = 0; j < count; ++j) kap[ord[j]] = kl[j];
+            for (int j = 0; j < AA_M; ++j) kapY[j] = kap[j];
             use_aa = true;
           }
         }
@@ -1379,12 +1575,13 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
       {
         T* VT = buf[iVT];
         const T k0 = (T)kap[0], k1 = (T)kap[1], k2 = (T)kap[2];
+        const T j0 = (T)kapY[0], j1 = (T)kapY[1], j2 = (T)kapY[2];
         auto elem = [&](T v, T tv, T s0, T s1, T s2, T y0, T y1, T y2, T& psi, T& vt) {
           T p = -(v - tv);
-          if (use_aa) {
-            p -= (s0 - y0) * k0;
-            p -= (s1 - y1) * k1;
-            p -= (s2 - y2) * k2;
+          if (use_aa) {   // psi = -r - S kappa + Y kappaY (kappaY = kappa, or Q'r in the QR mode)
+            p -= s0 * k0 - y0 * j0;
+            p -= s1 * k1 - y1 * j1;
+            p -= s2 * k2 - y2 * j2;
           }
           psi = p;
           vt = v + p;

@@ -59,7 +59,7 @@ class Sizes(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iters", C.c_int),
                 ("max_backtracks", C.c_int), ("method", C.c_int), ("warm_start", C.c_int),
-                ("fp64_check", C.c_int)]
+                ("fp64_check", C.c_int), ("aa_mode", C.c_int)]
 
 
 class Info(C.Structure):
@@ -182,7 +182,7 @@ def _f64(a):
 
 
 def opts(precision=64, tol=1e-4, max_iters=5000, max_backtracks=30, method="spock",
-         warm_start=False, fp64_check=True) -> SolveOpts:
+         warm_start=False, fp64_check=True, aa="gram") -> SolveOpts:
     o = SolveOpts()
     load().spock_solve_opts_default(C.byref(o))
     o.precision = int(precision)
@@ -192,6 +192,7 @@ def opts(precision=64, tol=1e-4, max_iters=5000, max_backtracks=30, method="spoc
     o.method = {"spock": 0, "cp": 1}[method]
     o.warm_start = int(bool(warm_start))
     o.fp64_check = int(bool(fp64_check))
+    o.aa_mode = {"gram": 0, "qr_update": 1}[aa]
     return o
 
 

@@ -254,3 +254,36 @@ def test_solve_reports_fp64_check(name):
     assert r32["info"]["res_inf_fp64"] == c["res_inf"]
     # near the solution every measure is small (Sec. 5.3)
     assert max(c["xi1"], c["xi2"]) < 5e-3 / o.alpha and c["infeas"] < 5e-3
+
+
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "wide_70x40", "full_rows_cta"])
+def test_fixed_iterations_spock_qr_update_fp64(name):
+    """SPOCK with the Anderson least squares solved by an updated QR
+    factorisation (Givens rotations to drop the oldest pair, Gram-Schmidt to
+    append; Sec. 6.2) against the oracle's own QR-updating memory: the same
+    K0/K1/K2 counts and T evaluations, the iterate within 1e-10 (FP64, 25
+    iterations)."""
+    p, o, g = _pair(name)
+    g.set_alpha(o.alpha)
+    spock = _spock()
+    iters = 25
+    ref = o.solve(tol=0.0, max_iters=iters, aa="qr_update")
+    res = g.solve(p.x0, spock.opts(precision=64, tol=0.0, max_iters=iters, aa="qr_update"))
+    inf = res["info"]
+    kinds = [e[1] for e in ref["events"]]
+    assert (inf["n_K0"], inf["n_K1"], inf["n_K2"]) == (kinds.count("K0"), kinds.count("K1"), kinds.count("K2"))
+    assert inf["n_T"] == ref["n_T"]
+    assert _relerr(g.get_iterate(64).cpu().numpy(), ref["v"]) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball"])
+def test_converged_fp32_qr_update(name):
+    """FP32 SPOCK with the QR-updated Anderson memory to 1e-4: risk value and u^0
+    within 1e-3 of the oracle's converged solution."""
+    p, o, g = _pair(name)
+    spock = _spock()
+    ref = o.solve(tol=1e-4, max_iters=20000)
+    res = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000, aa="qr_update"))
+    assert res["status"] == 0, res["info"]
+    assert abs(res["risk"] - ref["risk"]) <= 1e-3 * max(1.0, abs(ref["risk"]))
+    assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= 1e-3 * max(1.0, np.max(np.abs(ref["u"][0])))
