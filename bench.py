@@ -68,16 +68,37 @@ def measured_peak():
 
 
 def algorithmic_bytes(sizes, n_T, iters, word):
-    """Bytes one solve must move at least, from the counting of the design notes:
-    per T evaluation the per-node factor matrices (MB, MF per non-root node,
-    MP, KT per non-leaf node, unpadded) once, plus 8 passes over v; per SPOCK
-    iteration 21 passes over v for the Anderson memory and the direction."""
+    """Bytes one solve must move at least: per T evaluation the per-node factor
+    matrices of Alg. 2 (MB, MF per non-root node, MP, KT per non-leaf node,
+    unpadded) once, plus 8 passes over v; per SPOCK iteration 5 passes over v
+    for the Anderson memory (three n_v-vectors read, one written, the new pair
+    formed from v and T(v)) -- the counting of the hot-path scope's
+    measurement section. Passes the kernel makes beyond these are not
+    counted."""
     n, n_nl, nx, nu = sizes["n"], sizes["n_nonleaf"], sizes["nx"], sizes["nu"]
     factors = (n - 1) * (nx * (nx + nu) + (nx + nu) * nx) + n_nl * (nu * (nx + nu) + nx * nu)
     nv = sizes["n_v"]
     per_T = word * (factors + 8 * nv)
-    per_iter = word * 21 * nv
+    per_iter = word * 5 * nv
     return n_T * per_T + iters * per_iter, per_T
+
+
+DIAG_KERNELS = 7   # FP64 exit check of (v, T(v)): difference, L*, two L, xi, S3 terms, final reduction
+
+
+def launches_per_solve(prec, info, fp64_check=True):
+    """Kernels one spock_solve_device call launches. Plain solve: x0 scaling,
+    the iteration kernel, unscaling, then the FP64 exit check (in FP32: a
+    conversion and one FP64 T first). Centred FP32 (n centres): x0 scaling;
+    per centre one FP64 T, L z_c and the centre data; per FP32 segment (n - 1)
+    the iteration kernel and the move into the centre; unscaling, the FP32
+    copy of the iterate and the exit check."""
+    n = int(info.get("n_recentre", 0))
+    if prec == 32 and n > 0:
+        return 1 + 3 * n + 2 * (n - 1) + 2 + DIAG_KERNELS
+    if prec == 32:
+        return 3 + ((2 + DIAG_KERNELS) if fp64_check else 0)
+    return 3 + DIAG_KERNELS
 
 
 class ClockSampler:
@@ -176,10 +197,128 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def hw_figures():
+    """L2 size (device attribute) and the FP64 FMA rate of the SMs' FP64 pipe:
+    an elementwise NVRTC kernel (torch's jiterator) runs eight independent
+    chains of 2048 dependent FP64 FMAs per element over 2^21 elements; rate =
+    2 x FMAs / CUDA-event time, best of 5."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    out = {"l2_bytes": int(getattr(props, "L2_cache_size", 0)), "sms": props.multi_processor_count}
+    try:
+        code = ("template <typename T> T dfma_chains(T x) { T a0 = x, a1 = x + T(1), a2 = x + T(2), a3 = x + T(3), "
+                "a4 = x + T(4), a5 = x + T(5), a6 = x + T(6), a7 = x + T(7); const T m = T(0.9999999), c = T(1e-7); "
+                "for (int i = 0; i < 2048; ++i) { a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); "
+                "a3 = fma(a3, m, c); a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c); } "
+                "return ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7)); }")
+        fn = torch.cuda.jiterator._create_jit_fn(code)
+        x = torch.rand(1 << 21, dtype=torch.float64, device="cuda")
+        fn(x)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(x)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        fmas = float(x.numel()) * 2048 * 8
+        out["fp64_fma_tflops"] = 2 * fmas / (best / 1000.0) / 1e12
+        try:
+            mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+        except Exception:
+            mhz = 2032.0
+        out["fp64_fma_per_clk_per_sm_at_max_clock"] = fmas / (best / 1000.0) / (props.multi_processor_count * mhz * 1e6)
+    except Exception as e:   # noqa: BLE001
+        out["fp64_fma_error"] = f"{type(e).__name__}: {e}"
+    return out
+
+
+def solve_figures(spock, g, p, prec, tol, max_iters, word):
+    """One cold solve of problem g: iterations, T evaluations, device time, the
+    per-T time and the algorithmic-byte rate (same counting as the headline)
+    against the measured HBM peak."""
+    r = g.solve(p.x0, spock.opts(precision=prec, tol=tol, max_iters=max_iters, fp64_check=False))
+    i = r["info"]
+    peak, peak_kind = measured_peak()
+    alg, _ = algorithmic_bytes(g.sizes, i["n_T"], i["iters"], word)
+    ms = i["device_ms"]
+    out = {"precision": prec, "tol": tol, "status": r["status"], "iterations": i["iters"], "T_evals": i["n_T"],
+           "device_ms": ms, "iters_per_s": i["iters"] / (ms / 1000.0), "us_per_T": 1000.0 * ms / i["n_T"],
+           "res_inf": i["res_inf"], "risk": r["risk"],
+           "roofline": {"bound": "hbm", "achieved": alg / (ms / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / (ms / 1000.0) / 1e9 / peak, "peak_kind": peak_kind}}
+    return out
+
+
+def bench_configs(spock, synth):
+    """The other single-problem workloads: the 31-node problem (FP64 and FP32,
+    solved to 1e-4) and the tree-structure sweep (b = 2, 4, 8 at about 4096
+    nodes, FP32): per-T time and iterations/s over 2000 SPOCK iterations (a
+    solve of these trees to 1e-4 takes 54k to 111k iterations)."""
+    out = {}
+    p = synth.small_raocp()
+    g = spock.Problem(p)
+    g.solve(p.x0, spock.opts(precision=64, tol=TOL, max_iters=MAX_ITERS, fp64_check=False))   # warm
+    out["small_raocp_31_nodes"] = {"fp64": solve_figures(spock, g, p, 64, TOL, MAX_ITERS, 8),
+                                   "fp32": solve_figures(spock, g, p, 32, TOL, MAX_ITERS, 4)}
+    for b in (2, 4, 8):
+        q = synth.tree_sweep(b)
+        h = spock.Problem(q)
+        f = solve_figures(spock, h, q, 32, 0.0, 2000, 4)
+        f["nodes"] = len(q.anc)
+        f["tree"] = q.name
+        out[f"tree_sweep_b{b}"] = f
+    return out
+
+
+def bench_case_studies(spock, synth):
+    """The paper's case-study workloads. (1) Sec. 8.1's random RAOCP with n_v
+    near 1e5 (full per-event weights): the library's device bytes after an
+    FP32 solve and their peak during the offline part, beside the paper's
+    about 1 GB of combined memory; per-T time. (2) Sec. 8.2's tree-shape study:
+    [n^2, 1, ..] against [n, n, 1, ..] at equal scenario counts (N = 48,
+    nx = 100 + 50 delayed inputs, nu = 50, AV@R 0.95): per-T time and T
+    evaluations per second over 300 FP32 iterations."""
+    import torch
+    out = {}
+    p = synth.case_study_1(0, nv_range=(9e4, 1e5))
+    free0, _ = torch.cuda.mem_get_info()
+    g = spock.Problem(p)
+    f = solve_figures(spock, g, p, 32, 0.0, 1000, 4)
+    held, peak = g.memory()
+    free1, _ = torch.cuda.mem_get_info()
+    f.update({"problem": p.name, "n_v_paper_count": p.meta["n_v"], "nodes": len(p.anc),
+              "device_bytes": held, "device_peak_bytes": peak, "driver_free_drop_bytes": free0 - free1,
+              "paper_memory": "about 1 GB CPU+GPU combined at n_v = 1e5 (Sec. 8.1)"})
+    out["case_study_1_nv_1e5"] = f
+    del g
+    shapes = {}
+    for n in (2, 4, 8):
+        for shape in ("wide", "deep"):
+            q = synth.ncs_delay(n, shape)
+            h = spock.Problem(q)
+            r = solve_figures(spock, h, q, 32, 0.0, 300, 4)
+            shapes[f"n{n}_{shape}"] = {"nodes": len(q.anc), "scenarios": n * n, "us_per_T": r["us_per_T"],
+                                       "T_per_s": 1e6 / r["us_per_T"], "iters_per_s": r["iters_per_s"],
+                                       "roofline_frac": r["roofline"]["frac"]}
+            del h
+    out["tree_shape_study"] = shapes
+    return out
+
+
 BATCH_COUNT = 512
 BATCH_FIXED_ITERS = 200      # fixed-work throughput on the whole draw
-SMALL_COUNT = 64             # the draw's problems with the fewest nodes: solves to 1e-4 and serving
+PLAIN_SAMPLE = 16            # problems on which the plain FP64 method is timed
 MAX_ITERS = 20000
+TO_TOL_COUNT = 32            # problems of the to-1e-4 comparison
+TO_TOL_QUANTILE = 0.9        # ... drawn from this lower fraction of the draw by T bytes
+SERVE_T_BYTES = 4.0e6        # serving plants: problems whose T moves at most this (one CTA each)
+CONFIG5_SECONDS = 10.0       # arrivals at 2000 req/s (drained after), cut to keep the drain near a minute
+SWEEP_SECONDS = 4.0          # arrivals per point of the load sweep
+EXTRA_BUDGET_S = 420.0       # the sections after the headline stop starting after this much wall time
 
 
 def _gen(i):
@@ -196,6 +335,8 @@ def batch_draw():
 
 
 def _plain_fp64(spock, G, probs, idx, max_iters, tol, warm=False, x0s=None):
+    """Solve each problem of idx alone with the FP64 method (wall time,
+    converged count, total iterations)."""
     t = time.time()
     conv = iters = 0
     for k in idx:
@@ -206,67 +347,120 @@ def _plain_fp64(spock, G, probs, idx, max_iters, tol, warm=False, x0s=None):
     return time.time() - t, int(conv), int(iters)
 
 
-def bench_batched(spock, probs, G, small):
-    """Batched FP32 (one persistent graph-captured launch, warps per team from
-    the autotuner) against the plain single-problem FP64 method (one
-    cooperative launch per problem, the whole GPU each): (1) fixed work,
-    BATCH_FIXED_ITERS SPOCK iterations of every problem of the draw; (2) the
-    SMALL_COUNT smallest problems solved to ||v - T(v)||_inf <= 1e-4. The plain
-    method runs on every 8th problem (its time is linear in the number of
-    problems)."""
+def _stratified(probs, count, among=None):
+    """`count` problems spread evenly over the draw (or the indices `among`)
+    ordered by node count x (nx + nu)."""
+    idx = range(len(probs)) if among is None else among
+    order = sorted(idx, key=lambda k: (len(probs[k].anc) * (probs[k].nx + probs[k].nu), k))
+    step = len(order) / float(count)
+    return [order[int(i * step)] for i in range(count)]
+
+
+def t_bytes_fp32(g):
+    """Bytes one FP32 evaluation of T moves for problem g (factors and 20
+    passes over v): the size the batched launch sorts problems by (at most
+    4 MB: solved by one CTA)."""
+    return g.sizes["factor_bytes_fp32"] + 80 * g.sizes["n_v"]
+
+
+def bench_batched(spock, probs, G):
+    """Batched FP32 (one persistent graph-captured launch over all 512 problems
+    of the uneven draw, warps per team from the autotuner) against the plain
+    single-problem FP64 method (one cooperative launch per problem, the whole
+    GPU each): (1) fixed work, BATCH_FIXED_ITERS SPOCK iterations of every
+    problem; (2) every problem solved to ||v - T(v)||_inf <= 1e-4. The plain
+    method takes about a second per problem to tolerance, so it runs on
+    PLAIN_SAMPLE problems spread evenly over the draw's sizes and its
+    solves/s is that sample's."""
     res = {"workload": "uneven draw of 512 problems (seed 4): nx~U{4..64}, nu=nx/2, N~U{5..20}, "
-                       "b~U{2..4}-way branching at the first k~U{1..4} stages, AV@R~U[0.2,1], box + ball; "
+                       "b~U{2..4}-way branching at the first k~U{1..4} stages, AV@R~U[0.2,1], box on x and u; "
                        f"{sum(len(p.anc) for p in probs)} nodes"}
     o = spock.opts(precision=32, tol=0.0, max_iters=BATCH_FIXED_ITERS)
     b = spock.Batch(G, precision=32)
     tw = b.autotune(iters=20)                   # warps per team of every problem's sweeps
     x0s = [p.x0 for p in probs]
     r = b.solve(x0s, o)
-    b.close()
     res["autotuned_tw"] = {str(t): int((tw == t).sum()) for t in (1, 2, 4, 8)}
     it = sum(i["iters"] for i in r["info"])
-    # algorithmic bytes of the launch (same counting as the single-problem roofline)
     alg = sum(algorithmic_bytes(g.sizes, i["n_T"], i["iters"], 4)[0] for g, i in zip(G, r["info"]))
     peak, peak_kind = measured_peak()
     achieved = alg / (r["total_ms"] / 1000.0) / 1e9
-    pw, _, pit = _plain_fp64(spock, G, probs, range(0, len(probs), 8), BATCH_FIXED_ITERS, 0.0)
+    sample = _stratified(probs, PLAIN_SAMPLE)
+    pw, _, pit = _plain_fp64(spock, G, probs, sample, BATCH_FIXED_ITERS, 0.0)
     res["fixed_work"] = {"iters_per_problem": BATCH_FIXED_ITERS,
                          "batched_fp32_iters_per_s": it / (r["total_ms"] / 1000.0),
                          "batched_device_ms": r["total_ms"],
                          "plain_fp64_iters_per_s": pit / pw,
+                         "plain_sample": f"{len(sample)} problems spread over the draw's sizes",
                          "ratio": (it / (r["total_ms"] / 1000.0)) / (pit / pw),
                          "roofline": {"bound": "hbm", "kernel": "k_batch (one persistent launch, graph replay)",
                                       "algorithmic_bytes": alg, "achieved": achieved, "peak": peak,
                                       "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind}}
-    sG = [G[k] for k in small]
-    sp = [probs[k] for k in small]
-    o = spock.opts(precision=32, tol=TOL, max_iters=MAX_ITERS)
-    b = spock.Batch(sG, precision=32)
-    b.autotune(iters=20)
-    r = b.solve([p.x0 for p in sp], o)
     b.close()
+    # to 1e-4 on a subset: the TO_TOL_COUNT problems spread over the sizes of
+    # the draw's lower TO_TOL_QUANTILE (by T bytes; the largest problems take
+    # minutes each to 1e-4), batched in one launch; the plain FP64 method on
+    # every one of the same problems
+    by_size = sorted(range(len(probs)), key=lambda k: (t_bytes_fp32(G[k]), k))
+    lower = by_size[:int(TO_TOL_QUANTILE * len(probs))]
+    sub = _stratified(probs, TO_TOL_COUNT, among=lower)
+    bs = spock.Batch([G[k] for k in sub], precision=32)
+    bs.autotune(iters=20)
+    o = spock.opts(precision=32, tol=TOL, max_iters=MAX_ITERS)
+    r = bs.solve([probs[k].x0 for k in sub], o)
+    bs.close()
     conv = sum(1 for i in r["info"] if i["status"] == 0)
-    pw, pc, _ = _plain_fp64(spock, sG, sp, range(0, len(sp), 8), MAX_ITERS, TOL)
-    res["to_tol"] = {"problems": f"the {SMALL_COUNT} problems of the draw with the fewest nodes "
-                                 f"({sum(len(p.anc) for p in sp)} nodes)",
+    iters = [i["iters"] for i in r["info"]]
+    pw, pc, pit = _plain_fp64(spock, G, probs, sub, MAX_ITERS, TOL)
+    res["to_tol"] = {"problems": (f"{len(sub)} problems spread over the sizes of the draw's smallest "
+                                  f"{len(lower)} by T bytes (largest of them "
+                                  f"{max(t_bytes_fp32(G[k]) for k in sub) / 1e6:.1f} MB per T)"),
+                     "nodes": sum(len(probs[k].anc) for k in sub),
                      "tol": TOL, "max_iters": MAX_ITERS,
                      "batched_fp32_solves_per_s": conv / (r["total_ms"] / 1000.0), "converged": conv,
                      "batched_device_ms": r["total_ms"],
-                     "plain_fp64_solves_per_s": pc / pw, "plain_converged": pc,
-                     "plain_problems": len(range(0, len(sp), 8)),
+                     "iterations_p50": float(statistics.median(iters)), "iterations_max": int(max(iters)),
+                     "plain_fp64_solves_per_s": pc / pw, "plain_converged": pc, "plain_wall_s": pw,
+                     "plain_iterations_p50": float(pit) / max(1, len(sub)),
+                     "plain_on": "the same problems, one cooperative launch each",
                      "ratio": (conv / (r["total_ms"] / 1000.0)) / max(pc / pw, 1e-12)}
     return res
 
 
-def bench_serving(spock, probs, G, rate=2000.0, seconds=0.2, seed=5):
-    """MPC serving on the SMALL_COUNT smallest plants: Poisson arrivals at
-    `rate` for `seconds`; a request carries the plant's next state (x1 = A x0 +
-    B u0 at a child drawn by its probability, plus N(0, 0.01 I) noise, clipped
-    into the state box) and is warm-started from the plant's resident iterate.
-    Latency = submission to collection on the host."""
+def _serve_stream(srv, probs, x, u, rng, rate, seconds, next_state, drain_s=120.0):
+    """Poisson arrivals at `rate` for `seconds` (each request a warm-started
+    MPC step of a random plant); returns the collected results and the wall
+    time until the last one."""
+    got, sub = [], 0
+    t0 = time.time()
+    t_next = t0
+    while time.time() - t0 < seconds:
+        now = time.time()
+        while t_next <= now:
+            k = int(rng.integers(0, len(probs)))
+            x[k] = next_state(k)
+            srv.submit(k, x[k], warm=True)
+            sub += 1
+            t_next += rng.exponential(1.0 / rate)
+        for r in srv.poll():
+            got.append(r)
+            u[r["plant"]] = r["u0"]
+    got += srv.drain(drain_s)
+    return got, sub, time.time() - t0
+
+
+def bench_serving(spock, probs, G, label, seed=5):
+    """MPC serving on the plants of the uneven draw: every request carries the
+    plant's next state (x1 = A x0 + B u0 at a child drawn by its probability,
+    plus N(0, 0.01 I) noise, clipped into the state box) and is warm-started
+    from the plant's resident iterate. Capacity = completion rate of a burst
+    of requests; then Poisson arrivals at 2000 req/s (the offered load of the
+    serving workload, held for CONFIG5_SECONDS) and at fractions of the
+    capacity, with p50/p99 latency (submission to collection) beside
+    solves/s; the plain FP64 method is timed on warm requests one at a time."""
     import numpy as np
     o32 = spock.opts(precision=32, tol=TOL, max_iters=MAX_ITERS)
-    srv = spock.Server(G, precision=32, o=o32)
+    srv = spock.Server(G, precision=32, o=o32, ring_slots=8192)
     x = [p.x0.copy() for p in probs]
     u = [None] * len(probs)
     for k, p in enumerate(probs):             # one cold solve per plant first
@@ -283,42 +477,48 @@ def bench_serving(spock, probs, G, rate=2000.0, seconds=0.2, seed=5):
         x1 = p.A[c - 1] @ x[k] + p.B[c - 1] @ u[k] + p.c[c - 1]
         return np.clip(x1 + 0.1 * rng.standard_normal(p.nx), -4.5, 4.5)
 
-    got, sub = [], 0
+    def summary(got, sub, wall, rate, seconds):
+        lat = np.array([r["latency_ms"] for r in got]) if got else np.zeros(1)
+        dev = np.array([r["device_ms"] for r in got]) if got else np.zeros(1)
+        return {"offered_rate_per_s": rate, "arrival_seconds": seconds, "submitted": sub, "completed": len(got),
+                "converged": sum(1 for r in got if r["status"] == 0),
+                "maxiter": sum(1 for r in got if r["status"] == 1),
+                "solves_per_s": len(got) / wall,
+                "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+                "device_ms_p50": float(np.percentile(dev, 50)), "device_ms_p99": float(np.percentile(dev, 99)),
+                "iterations_p50": float(np.percentile([r["iters"] for r in got], 50)) if got else 0.0}
+
+    # capacity: a burst of two requests per plant
     t0 = time.time()
-    t_next = t0
-    while time.time() - t0 < seconds:
-        now = time.time()
-        while t_next <= now:
-            k = int(rng.integers(0, len(probs)))
+    for rep in range(2):
+        for k in range(len(probs)):
             x[k] = next_state(k)
             srv.submit(k, x[k], warm=True)
-            sub += 1
-            t_next += rng.exponential(1.0 / rate)
-        for r in srv.poll():
-            got.append(r)
-            u[r["plant"]] = r["u0"]
-    got += srv.drain(600)
-    wall = time.time() - t0
+    burst = srv.drain(600)
+    cap = len(burst) / (time.time() - t0)
+    for r in burst:
+        u[r["plant"]] = r["u0"]
+    out = {"plants": label, "capacity_solves_per_s": cap}
+    secs = min(CONFIG5_SECONDS, max(1.0, 60.0 * cap / 2000.0))
+    got, sub, wall = _serve_stream(srv, probs, x, u, rng, 2000.0, secs, next_state)
+    out["offered_2000_per_s"] = summary(got, sub, wall, 2000.0, secs)
+    out["below_capacity"] = []
+    for frac in (0.25, 0.5, 0.75):
+        got, sub, wall = _serve_stream(srv, probs, x, u, rng, frac * cap, SWEEP_SECONDS, next_state)
+        d = summary(got, sub, wall, frac * cap, SWEEP_SECONDS)
+        d["fraction_of_capacity"] = frac
+        out["below_capacity"].append(d)
     srv.close()
-    lat = np.array([r["latency_ms"] for r in got])
-    dev = np.array([r["device_ms"] for r in got])
-    conv = sum(1 for r in got if r["status"] == 0)
-    # the plain FP64 method, one warm-started request at a time on a sample of plants
     pl = []
-    for k in range(0, len(probs), 16):
+    for k in _stratified(probs, 16):
         t = time.time()
         G[k].solve(x[k], spock.opts(precision=64, tol=TOL, max_iters=MAX_ITERS, warm_start=True,
                                      fp64_check=False))
         pl.append(1000 * (time.time() - t))
-    return {"plants": f"the {SMALL_COUNT} problems of the draw with the fewest nodes",
-            "arrival_rate_per_s": rate, "arrival_seconds": seconds, "submitted": sub, "completed": len(got),
-            "converged": conv, "solves_per_s": len(got) / wall,
-            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
-            "device_ms_p50": float(np.percentile(dev, 50)), "device_ms_p99": float(np.percentile(dev, 99)),
-            "plain_fp64_solve_ms_p50": float(np.percentile(pl, 50)),
-            "plain_fp64_solve_ms_p99": float(np.percentile(pl, 99)),
-            "note": "plain = the single-problem FP64 method on one warm-started request at a time "
-                    "(solve time, no queueing)"}
+    out["plain_fp64_warm_solve_ms_p50"] = float(np.percentile(pl, 50))
+    out["plain_fp64_warm_solve_ms_p99"] = float(np.percentile(pl, 99))
+    out["plain_fp64_solves_per_s"] = 1000.0 / float(np.mean(pl))
+    return out
 
 
 def combine_ranks(dist, total_ms, iters, device):
@@ -334,7 +534,7 @@ def combine_ranks(dist, total_ms, iters, device):
 
 def run_ours(args, rank, world, local_rank, dist):
     # the batched draw is generated before this process touches the GPU
-    bprobs = batch_draw() if (not args.no_batch and rank == 0) else None
+    bprobs = batch_draw() if (not args.no_batch and not args.no_extras and rank == 0 and world == 1) else None
     import torch
 
     from paper_2505_12078_b300 import spock, synth
@@ -349,8 +549,8 @@ def run_ours(args, rank, world, local_rank, dist):
     uo = torch.empty(g.n_nl * g.nu, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one(prec, timed):
-        o = spock.opts(precision=prec, tol=TOL, max_iters=200000, fp64_check=True)
+    def one(prec, timed, recentre=None):
+        o = spock.opts(precision=prec, tol=TOL, max_iters=200000, fp64_check=True, recentre=recentre)
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -384,8 +584,11 @@ def run_ours(args, rank, world, local_rank, dist):
     value = iters / (total_ms / 1000.0)
     word = 4 if prec == 32 else 8
     inf0 = infos[0]
-    kern_ms = statistics.mean(i["device_ms"] for i in infos)
-    bytes_launch, per_T = algorithmic_bytes(sizes, inf0["n_T"], inf0["iters"], word)
+    # the iteration kernel's launches alone (FP32 segments of the centred
+    # solve; its FP64 centre evaluations are other launches)
+    kern_ms = statistics.mean(i["kernel_ms"] for i in infos)
+    nT_kernel = inf0["n_T"] - inf0["n_recentre"]
+    bytes_launch, per_T = algorithmic_bytes(sizes, nT_kernel, inf0["iters"], word)
     peak, peak_kind = measured_peak()
     achieved = bytes_launch / (kern_ms / 1000.0) / 1e9
     traffic = None
@@ -397,62 +600,97 @@ def run_ours(args, rank, world, local_rank, dist):
                 traffic = tr["dram_bytes_per_T"] * inf0["n_T"]
         except Exception:
             traffic = None
+    segs = max(1, inf0["n_recentre"] - 1) if prec == 32 else 1
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_solve (one persistent cooperative launch per solve)",
-                "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_bytes_per_T": per_T,
-                "launch_ms": kern_ms}
+                "kernel": "k_solve (persistent cooperative launch; one per FP32 segment of the centred solve)",
+                "algorithmic_bytes_per_solve": bytes_launch, "algorithmic_bytes_per_T": per_T,
+                "kernel_ms_per_solve": kern_ms, "launches_per_solve": segs,
+                "kernel_share_of_solve": kern_ms / statistics.mean(i["device_ms"] for i in infos)}
     # the FP64 iteration on the same workload
-    fp64 = None
+    fp64 = fp32_plain = None
     if prec == 32:
         ms64, info64, _ = one(64, True)
         fp64 = {"iters_per_s": info64["iters"] / (ms64 / 1000.0), "time_to_tol_ms": ms64,
-                "iterations": info64["iters"], "T_evals": info64["n_T"],
-                "res_inf": info64["res_inf"]}
-    # end to end through the C ABI with host buffers (x0 in, x/u out)
-    e2e_ms = []
+                "iterations": info64["iters"], "T_evals": info64["n_T"], "us_per_T": 1000.0 * ms64 / info64["n_T"],
+                "res_inf": info64["res_inf"], "xi1": info64["xi1"], "xi2": info64["xi2"],
+                "infeas": info64["infeas"], "gap": info64["gap"]}
+        # the FP32 iteration without the centre (the iterate itself in FP32)
+        msp, infp, _ = one(32, True, recentre=0.0)
+        fp32_plain = {"iters_per_s": infp["iters"] / (msp / 1000.0), "time_to_tol_ms": msp,
+                      "iterations": infp["iters"], "T_evals": infp["n_T"], "us_per_T": 1000.0 * msp / infp["n_T"],
+                      "res_inf_fp64": infp["res_inf_fp64"]}
+    # end to end through the C ABI with host buffers (x0 in, x/u and the risk
+    # out), one warm-up and then as many timed solves as the device-timed step
+    e2e_ms, e2e_iters = [], 0
     o = spock.opts(precision=prec, tol=TOL, max_iters=200000, fp64_check=True)
-    for _ in range(1):
+    for rep in range(1 + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.time()
         r = g.solve(p.x0, o)
-        e2e_ms.append(1000 * (time.time() - t))
-    e2e_iters = r["info"]["iters"]
-    e2e = {"value": e2e_iters / (statistics.mean(e2e_ms) / 1000.0), "unit": "iter/s",
+        if rep > 0:
+            e2e_ms.append(1000 * (time.time() - t))
+            e2e_iters += r["info"]["iters"]
+    e2e = {"value": e2e_iters / (sum(e2e_ms) / 1000.0), "unit": "iter/s",
            "h2d_bytes_per_step": 8 * g.nx,
            "d2h_bytes_per_step": 8 * (g.n * g.nx + g.n_nl * g.nu + 1),
-           "time_to_tol_ms": statistics.mean(e2e_ms)}
-    launches_per_step = 3 + (2 if prec == 32 else 0)   # x0 scaling, solve, unscale (+ FP64 check)
+           "time_to_tol_ms": statistics.mean(e2e_ms), "steps": len(e2e_ms),
+           "fp64_check": {"res_inf": r["info"]["res_inf_fp64"], "xi1": r["info"]["xi1"], "xi2": r["info"]["xi2"],
+                          "infeas": r["info"]["infeas"], "gap": r["info"]["gap"]}}
+    launches = sum(launches_per_solve(prec, i) for i in infos)
     cpu = cpu_baseline(p) if world == 1 else None
-    batched = serving = None
-    if bprobs is not None:
-        # a failure here must not cost the headline line: it is reported in place
+    extras = {}
+    t_extra = time.time()
+
+    def section(name, fn):
+        # a failure or the time budget must not cost the headline line: reported in place
+        if time.time() - t_extra > EXTRA_BUDGET_S:
+            extras[name] = {"skipped": f"wall-time budget of {EXTRA_BUDGET_S:.0f} s for these sections used"}
+            return
         try:
-            bG = [spock.Problem(q) for q in bprobs]
-            small = sorted(range(len(bprobs)), key=lambda k: (len(bprobs[k].anc), k))[:SMALL_COUNT]
-            batched = bench_batched(spock, bprobs, bG, small)
-            serving = bench_serving(spock, [bprobs[k] for k in small], [bG[k] for k in small])
+            t = time.time()
+            extras[name] = fn()
+            extras[name]["section_wall_s"] = time.time() - t
         except Exception as e:   # noqa: BLE001
-            err = {"error": f"{type(e).__name__}: {e}"}
-            batched = batched or err
-            serving = serving or err
+            extras[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    if world == 1 and not args.no_extras:
+        section("hw", hw_figures)
+        section("configs", lambda: bench_configs(spock, synth))
+        section("case_studies", lambda: bench_case_studies(spock, synth))
+        if bprobs is not None:
+            bG = []
+
+            def batched_fn():
+                bG.extend(spock.Problem(q) for q in bprobs)
+                return bench_batched(spock, bprobs, bG)
+            section("batched", batched_fn)
+            if bG:
+                def serving_fn():
+                    ks = [k for k in range(len(bprobs)) if t_bytes_fp32(bG[k]) <= SERVE_T_BYTES]
+                    label = (f"the {len(ks)} of the draw's {len(bprobs)} problems whose T moves at most "
+                             f"{SERVE_T_BYTES / 1e6:.0f} MB (the class the batched launch gives one CTA)")
+                    return bench_serving(spock, [bprobs[k] for k in ks], [bG[k] for k in ks], label)
+                section("serving", serving_fn)
     line = {"metric": METRIC, "value": value * 1.0, "unit": "iter/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "tol": TOL,
-                       "precision": "FP32 iteration, FP64 factors and FP64 residual check" if prec == 32
-                                    else "FP64",
+                       "precision": ("FP32 iteration on the increment over an FP64 centre (re-centred at every "
+                                     "10x drop of the residual), FP64 projections about the centre, FP64 factors, "
+                                     "FP64 residual as the stopping test") if prec == 32 else "FP64",
+                       "centres_per_solve": inf0["n_recentre"],
                        "step": "one cold-start SPOCK solve to ||v - T(v)||_inf <= 1e-4",
                        "time_to_tol_ms": total_ms / args.steps,
                        "iterations_per_solve": inf0["iters"], "T_evals_per_solve": inf0["n_T"],
                        "final_res_inf": inf0["res_inf"], "final_res_inf_fp64": inf0["res_inf_fp64"],
                        "l2": "flushed (256 MB write) before every step",
                        "parallelism": f"replicas x{world}"},
-            "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "fp64": fp64,
-            "batched": batched, "serving": serving}
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu, "fp64": fp64, "fp32_plain": fp32_plain}
+    line.update(extras)
     print(json.dumps(line), flush=True)
 
 
@@ -464,6 +702,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline solve, its FP64 comparison, e2e and the CPU baseline")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="run one batched launch of this many iterations on every 32nd problem of the "
                          "uneven draw and exit (for ncu captures)")

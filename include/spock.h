@@ -173,6 +173,18 @@ int spock_problem_set_x0(spock_problem* p, const double* x0);
 int spock_op_T(spock_problem* p, int precision, const void* v_in, void* v_out, double* stats,
                void* stream);
 
+/* One FP32 evaluation of T in the centred form (the map the centred FP32
+ * iteration runs on, spock_solve_opts.recentre): out = T(c + delta) - c.
+ * prox_f is affine (Alg. 2), so its part of the map is its linear part applied
+ * to the increment in FP32, plus z+_c - z_c from one FP64 evaluation of T at c;
+ * L acts on the increments; the prox of alpha g* (Moreau, proj_S3) is taken in
+ * FP64 on c + the increment. Rounding is relative to the increments, not to c.
+ * c (device) [n_v] FP64; delta, out (device) [n_v] FP32, distinct; stats as
+ * for spock_op_T (of r = delta - out). Uses the problem's FP64 solve buffers
+ * TV and VT and the centre buffers as scratch. Blocking. */
+int spock_op_T_centred(spock_problem* p, const double* c, const float* delta, float* out, double* stats,
+                       void* stream);
+
 /* spock_op_T_noalloc: the same evaluation of T as spock_op_T, for callers that
  * cannot allocate device memory at the time of the call -- for example code
  * running under a memory pool or allocator it does not own, inside a
@@ -211,6 +223,19 @@ typedef struct spock_solve_opts {
                              1 a QR factorisation of Y kept up to date as pairs enter and
                              leave (Givens rotations, Gram-Schmidt; Sec. 6.2), one more
                              pass over the vectors per iteration */
+    double recentre;      /* FP32 only (spock_solve / spock_solve_device). 0: the iterate v
+                             itself is held and iterated in FP32. > 0 (the default, 0.1):
+                             centred FP32 iteration. An FP64 centre c is kept and the FP32
+                             iteration runs on delta = v - c, i.e. on the map
+                             delta -> T(c + delta) - c. Its linear parts act on the small
+                             increments in FP32 and its projections are taken in FP64 about c.
+                             Once the FP32 residual falls below recentre times the centre's
+                             FP64 residual, the iterate moves into c (c += delta, delta = 0)
+                             and the iteration restarts there (Anderson memory emptied).
+                             The stopping test is the FP64 residual of the centre, so
+                             res_inf = res_inf_fp64 is an FP64 figure. The iterate lives in
+                             FP64: warm starts continue from the FP64 iterate, and
+                             spock_get_iterate returns it in both precisions. Must be < 1. */
 } spock_solve_opts;
 
 typedef struct spock_info {
@@ -219,10 +244,12 @@ typedef struct spock_info {
     int n_T;              /* evaluations of T */
     int n_K0, n_K1, n_K2, n_fallback;   /* accepted step kinds of Alg. 4 */
     int n_backtracks;     /* total tau halvings */
-    double res_inf;       /* ||v - T(v)||_inf at exit, in the iteration precision */
+    double res_inf;       /* ||v - T(v)||_inf at exit, in the iteration precision (FP64 in
+                             the centred FP32 iteration) */
     double res_inf_fp64;  /* same in FP64 (fp64_check), else = res_inf */
     double risk;          /* s^0 of T(v): the risk value (Sec. 4, Eq. min-s0-v1) */
-    double device_ms;     /* device time of the solve kernel (CUDA events) */
+    double device_ms;     /* device time of the solve (CUDA events): the solve kernel, and in
+                             the centred FP32 iteration every segment with its re-centring */
     double phase_ms[7];   /* device time per phase seen by the first CTA, barrier waits
                              included: prep/S2, backward sweep, forward sweep + eta update,
                              T reductions, Anderson dots, direction pass, K2/backtrack passes */
@@ -238,6 +265,11 @@ typedef struct spock_info {
      *   gap    = |<eta+, L z+> - sigma_S3(eta+)|               (complementarity gap,
      *            sigma_S3 the support function of S3 of Eq. S3-def) */
     double xi1, xi2, infeas, gap;
+    int n_recentre;       /* centred FP32 iteration: centres taken (each one FP64 evaluation
+                             of T, counted in n_T), else 0 */
+    double kernel_ms;     /* device time of the iteration kernel's launches alone (CUDA
+                             events around each; in the centred FP32 iteration the sum over
+                             its FP32 segments), part of device_ms */
 } spock_info;
 
 void spock_solve_opts_default(spock_solve_opts* o);

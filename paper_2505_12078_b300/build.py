@@ -26,6 +26,7 @@ UNITS = [
     ("spock_solver", "spock_solver.cu", []),
     ("spock_noalloc", "spock_noalloc.cu", []),
     ("spock_diag", "spock_diag.cu", []),
+    ("spock_centre", "spock_centre.cu", []),
     ("spock_batch", "spock_batch.cu", []),
     ("spock_serve", "spock_serve.cu", []),
     ("solver_f1", "spock_solver_inst.cu", ["-DSPOCK_T=float", "-DSPOCK_CH=1", "-DSPOCK_SUFFIX=f1", "-DSPOCK_WITH_BATCH"]),

@@ -632,9 +632,155 @@ int check_fp64(spock_problem* p, int precision, const void* v, cudaStream_t st, 
 }
 }  // namespace spock
 
+namespace spock {
+// buffers of the centred FP32 iteration (first use, one allocation)
+static int ensure_ctr(spock_problem* p) {
+  if (p->ctr_block) return SPOCK_OK;
+  const size_t ne = (size_t)p->neta, nz = (size_t)p->nz;
+  size_t nzero = (size_t)(p->n - 1) * p->nx;
+  nzero = std::max(nzero, (size_t)p->n_nl * (p->nx + p->nu));
+  nzero = std::max(nzero, (size_t)p->nx);
+  const size_t bytes = 2 * al256(ne * 8) + al256(nz * 4) + al256(nzero * 4);
+  void* blk = nullptr;
+  if (cudaMalloc(&blk, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SPOCK_ENOMEM;
+  }
+  unsigned char* q = static_cast<unsigned char*>(blk);
+  p->d_ctrA = (double*)q; q += al256(ne * 8);
+  p->d_ctrB = (double*)q; q += al256(ne * 8);
+  p->d_cz = (float*)q;    q += al256(nz * 4);
+  p->d_zero32 = (float*)q;
+  if (cudaMemset(p->d_zero32, 0, nzero * 4) != cudaSuccess) {
+    cudaFree(blk);
+    return SPOCK_EDEVICE;
+  }
+  p->ctr_block = blk;
+  p->ctr_bytes = (long long)bytes;
+  return SPOCK_OK;
+}
+
+// Data of the centre c (FP64, n_v): T(c) into the FP64 solve buffer TV, L z_c
+// into VT, then cz, A, B; res_c = ||c - T(c)||_inf in FP64. Needs the FP64
+// solve buffers and the centre buffers.
+static int centre_at(spock_problem* p, const double* c, cudaStream_t st, double* res_c) {
+  double* tc = p->f64.sb.TV;
+  double* lz = p->f64.sb.VT;
+  Iter<double> e64 = p->f64;
+  e64.sb.V = const_cast<double*>(c);
+  e64.sb.TV = tc;
+  const SolveOpts s1{1e300, 0, 1, 2, 1e-10};   // one evaluation of T
+  SolveCtl h1{};
+  int rc = run_solver<double>(p, e64, s1, st, &h1, nullptr);
+  if (rc) return rc;
+  *res_c = h1.res_inf;
+  if (launch_apply_L<double>(p->f64.P, p->d_ynode, c, lz, st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (launch_centre(p->f64.P, c, tc, lz, p->alpha, p->d_cz, p->d_ctrA, p->d_ctrB, st) != cudaSuccess)
+    return SPOCK_EDEVICE;
+  return SPOCK_OK;
+}
+
+// the FP32 descriptor of the centred form: the linear part of prox_f (zeros
+// for x0, c and the constant of the backward recursion) and the centre's data
+static Iter<float> centred_iter(spock_problem* p) {
+  Iter<float> it = p->f32;
+  it.P.lin = 1;
+  it.P.cvec = p->d_zero32;
+  it.P.kc = p->d_zero32;
+  it.P.x0s = p->d_zero32;
+  it.P.cz = p->d_cz;
+  it.P.ctrA = p->d_ctrA;
+  it.P.ctrB = p->d_ctrB;
+  it.P.ctr_al = p->alpha;
+  it.P.ctr_ial = 1.0 / p->alpha;
+  return it;
+}
+
+// one FP32 evaluation of the centred map: out = T(c + delta) - c
+int op_T_centred(spock_problem* p, const double* c, const float* delta, float* out, double* stats,
+                 cudaStream_t st) {
+  int rc = ensure_bufs(p, p->f64);
+  if (rc) return rc;
+  rc = ensure_bufs(p, p->f32);
+  if (rc) return rc;
+  rc = ensure_ctr(p);
+  if (rc) return rc;
+  double res_c = 0.0;
+  rc = centre_at(p, c, st, &res_c);
+  if (rc) return rc;
+  Iter<float> it = centred_iter(p);
+  it.sb.V = const_cast<float*>(delta);
+  it.sb.TV = out;
+  const SolveOpts s1{1e300, 0, 1, 2, 1e-10};
+  SolveCtl h{};
+  rc = run_solver<float>(p, it, s1, st, &h, nullptr);
+  if (rc) return rc;
+  if (stats)
+    for (int k = 0; k < 8; ++k) stats[k] = h.stats[k];
+  return SPOCK_OK;
+}
+
+// The centred FP32 iteration (spock_solve_opts.recentre > 0): segments of the
+// FP32 SPOCK iteration on delta = v - c, each started from delta = 0 at a new
+// FP64 centre c and stopped once its FP32 residual is below recentre times the
+// centre's FP64 residual (or tol); the FP64 residual of the centre, from one
+// FP64 evaluation of T, is the stopping test. Outputs and the exit check come
+// from the final centre and its FP64 image.
+static int solve_centred(spock_problem* p, const spock_solve_opts& o, const SolveOpts& so, cudaStream_t st,
+                         double* x_out, double* u_out, SolveCtl& tot, double& res_c, double (&diag6)[6],
+                         int& n_ctr, double& kern_ms) {
+  int rc = ensure_bufs(p, p->f64);
+  if (rc) return rc;
+  rc = ensure_bufs(p, p->f32);
+  if (rc) return rc;
+  rc = ensure_ctr(p);
+  if (rc) return rc;
+  const long long nv = p->nv;
+  double* c = p->f64.sb.V;     // the centre (the FP64 iterate)
+  double* tc = p->f64.sb.TV;   // T(c)
+  if (!o.warm_start && cudaMemsetAsync(c, 0, nv * 8, st) != cudaSuccess) return SPOCK_EDEVICE;
+  Iter<float> it = centred_iter(p);
+  int left = o.max_iters;
+  n_ctr = 0;
+  kern_ms = 0.0;
+  tot = SolveCtl{};
+  tot.status = 1;
+  for (;;) {
+    rc = centre_at(p, c, st, &res_c);
+    if (rc) return rc;
+    ++n_ctr;
+    ++tot.n_T;
+    if (res_c <= o.tol) {
+      tot.status = 0;
+      break;
+    }
+    if (left <= 0) break;
+    if (cudaMemsetAsync(it.sb.V, 0, nv * 4, st) != cudaSuccess) return SPOCK_EDEVICE;
+    SolveOpts sg = so;
+    sg.tol = std::max(o.tol, o.recentre * res_c);
+    sg.max_iters = left;
+    SolveCtl h{};
+    float seg_ms = 0.f;
+    rc = run_solver<float>(p, it, sg, st, &h, &seg_ms);
+    if (rc) return rc;
+    kern_ms += seg_ms;
+    tot.iters += h.iters; tot.n_T += h.n_T; tot.n_K0 += h.n_K0; tot.n_K1 += h.n_K1; tot.n_K2 += h.n_K2;
+    tot.n_fb += h.n_fb; tot.n_bt += h.n_bt;
+    for (int q = 0; q < 16; ++q) tot.prof[q] += h.prof[q];
+    left -= h.iters;
+    if (launch_centre_move(nv, c, buf_index(it.sb, h.final_v), st) != cudaSuccess) return SPOCK_EDEVICE;
+  }
+  tot.res_inf = res_c;
+  k_unscale<double><<<64, 256, 0, st>>>(p->n, p->n_nl, p->nx, p->nu, p->o_x, p->o_u, tc, p->d_Sx, p->d_SxN,
+                                       p->d_Su, x_out, u_out, p->d_out_risk);
+  if (launch_centre_to_f32(nv, c, p->f32.sb.V, st) != cudaSuccess) return SPOCK_EDEVICE;
+  return diag_run(p, c, tc, st, diag6);
+}
+}  // namespace spock
+
 extern "C" {
 
-int spock_version(void) { return 2; }
+int spock_version(void) { return 3; }
 
 int spock_debug_wait_fault(int phantom_ctas, double wait_limit_s) {
   if (phantom_ctas < 0 || phantom_ctas > 4 || !(wait_limit_s >= 0.0) || wait_limit_s > 10.0) return SPOCK_EINVAL;
@@ -668,6 +814,7 @@ void spock_solve_opts_default(spock_solve_opts* o) {
   o->warm_start = 0;
   o->fp64_check = 1;
   o->aa_mode = 0;
+  o->recentre = 0.1;
 }
 
 int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
@@ -1100,6 +1247,7 @@ void spock_problem_destroy(spock_problem* p) {
   cudaDeviceSynchronize();
   release_bufs(p->f64);
   release_bufs(p->f32);
+  if (p->ctr_block) cudaFree(p->ctr_block);
   p->mem.free_all();
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
@@ -1117,7 +1265,7 @@ int spock_problem_sizes(const spock_problem* p, spock_sizes* o) {
   o->solve_bytes_fp64 = solve_buffer_bytes(p, 64);
   o->solve_bytes_fp32 = solve_buffer_bytes(p, 32);
   o->device_bytes = p->mem.bytes + (p->f64.sb_block ? o->solve_bytes_fp64 : 0) +
-                    (p->f32.sb_block ? o->solve_bytes_fp32 : 0);
+                    (p->f32.sb_block ? o->solve_bytes_fp32 : 0) + p->ctr_bytes;
   o->device_peak_bytes = std::max(p->setup_peak, o->device_bytes);
   return SPOCK_OK;
 }
@@ -1199,6 +1347,12 @@ int spock_op_T(spock_problem* p, int precision, const void* v_in, void* v_out, d
   return SPOCK_OK;
 }
 
+int spock_op_T_centred(spock_problem* p, const double* c, const float* delta, float* out, double* stats,
+                       void* stream) {
+  if (!p || !c || !delta || !out) return SPOCK_EINVAL;
+  return spock::op_T_centred(p, c, delta, out, stats, (cudaStream_t)stream);
+}
+
 int spock_op_L(spock_problem* p, int precision, const void* z, void* eta, void* stream) {
   if (!p || !z || !eta) return SPOCK_EINVAL;
   cudaError_t e;
@@ -1226,7 +1380,8 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
   if (opts) o = *opts;
   else spock_solve_opts_default(&o);
   if ((o.precision != 32 && o.precision != 64) || !(o.tol >= 0) || o.max_iters < 0 ||
-      o.max_backtracks < 1 || o.method < 0 || o.method > 1 || o.aa_mode < 0 || o.aa_mode > 1)
+      o.max_backtracks < 1 || o.method < 0 || o.method > 1 || o.aa_mode < 0 || o.aa_mode > 1 ||
+      !(o.recentre >= 0.0 && o.recentre < 1.0))
     return SPOCK_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = set_x0_dev(p, x0, st);
@@ -1240,6 +1395,8 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
   double res64 = -1.0;
   double diag6[6];
   bool have_diag = false;
+  int n_ctr = 0;
+  double kern_ms = -1.0;
   const long long nv = p->nv;
   if (o.precision == 64) {
     rc = ensure_bufs(p, p->f64);
@@ -1258,6 +1415,18 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
     res64 = h.res_inf;
     // FP64 exit check of (v, T(v)) as they stand (Sec. 5.3)
     rc = diag_run(p, p->f64.sb.V, z, st, diag6);
+    if (rc) return rc;
+    have_diag = true;
+  } else if (o.recentre > 0.0) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    rc = solve_centred(p, o, so, st, x_out, u_out, h, res64, diag6, n_ctr, kern_ms);
+    cudaEventRecord(e1, st);
+    if (!rc && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     if (rc) return rc;
     have_diag = true;
   } else {
@@ -1300,6 +1469,8 @@ int spock_solve_device(spock_problem* p, const double* x0, const spock_solve_opt
     info->xi2 = have_diag ? diag6[1] : NAN;
     info->infeas = have_diag ? diag6[2] : NAN;
     info->gap = have_diag ? diag6[3] : NAN;
+    info->n_recentre = n_ctr;
+    info->kernel_ms = kern_ms >= 0.0 ? kern_ms : ms;
   }
   return h.status == 0 ? SPOCK_OK : SPOCK_MAXITER;
 }

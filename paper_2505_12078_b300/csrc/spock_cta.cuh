@@ -568,9 +568,10 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
       if (k < nx) {
         if (i == 0) {
           v = P.x0s[k];
-          stc(vout + o_x + k, v);
+          stc(vout + o_x + k, zc_add(P, o_x + k, v));
         } else {
-          v = ldc(vout + o_x + (long long)i * nx + k);
+          const long long ix = o_x + (long long)i * nx + k;
+          v = zc_sub(P, ix, ldc(vout + ix));
         }
       } else {
         v = ldc(dbuf + (long long)i * nu + (k - nx));
@@ -600,10 +601,12 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
     if (lead) {
       if (xcol) {
         const T xc = v + cpA;
-        stc(vout + o_x + (long long)c * nx + col, xc);
+        const long long ix = o_x + (long long)c * nx + col;
+        stc(vout + ix, zc_add(P, ix, xc));
         if (chain) st_s<T>(cout + (unsigned)col * ES, xc);
       } else if (ucol && kt) {
-        stc(vout + o_u + (long long)i * nu + (col - nx), v + ld_s<T>(cin + (unsigned)col * ES));
+        const long long iu = o_u + (long long)i * nu + (col - nx);
+        stc(vout + iu, zc_add(P, iu, v + ld_s<T>(cin + (unsigned)col * ES)));
       }
     }
     if (chain && t < nu) st_s<T>(cout + (unsigned)(nx + t) * ES, dA);

@@ -102,6 +102,19 @@ struct Prob {
   const T *gen_lo, *gen_hi;     // [n_nl n_g]
   const T *genN_lo, *genN_hi;   // [n_l n_gN]
   T alpha;
+  // Centred form (FP32 iteration about an FP64 centre c = (z_c, eta_c)): the
+  // kernel then evaluates D(delta) = T(c + delta) - c. lin = 1 drops the
+  // constant terms of prox_f (x0s, cvec and kc then point at zeros); cz = z+_c
+  // - z_c is added to every z output (and taken off again where a sweep reads
+  // back an x it wrote); the eta prox steps run in FP64 on the full argument,
+  // with ctrA = (eta_c + alpha L z_c)/alpha - a and ctrB = alpha L z_c - alpha a
+  // per element of eta (a: the translation of the element's set, zero outside
+  // the cost cones). Null / zero in the plain form.
+  int lin;
+  const T* cz;                 // [nz]
+  const double* ctrA;          // [neta]
+  const double* ctrB;          // [neta]
+  double ctr_al, ctr_ial;      // alpha and 1/alpha in FP64
   // scratch of the sweeps
   T* qbuf;   // [n nx]
   T* dbuf;   // [n_nl nu]
@@ -116,6 +129,17 @@ struct Prob {
 template <class T> __device__ __forceinline__ T ldc(const T* p) { return __ldcg(p); }
 template <class T> __device__ __forceinline__ void stc(T* p, T v) { __stcg(p, v); }
 template <class T> __device__ __forceinline__ T ldr(const T* p) { return __ldg(p); }
+
+// z output of element idx: in the centred form the linear part plus cz
+template <class T>
+__device__ __forceinline__ T zc_add(const Prob<T>& P, long long idx, T v) {
+  return P.cz ? v + ldr(P.cz + idx) : v;
+}
+// the linear part of an x the sweep wrote (centred form: minus cz)
+template <class T>
+__device__ __forceinline__ T zc_sub(const Prob<T>& P, long long idx, T v) {
+  return P.cz ? v - ldr(P.cz + idx) : v;
+}
 
 template <class T> struct Vec;
 template <> struct Vec<float> { using V = float4; static constexpr int N = 4; };
@@ -321,26 +345,63 @@ struct RedAcc {
   }
 };
 
-// Block reduction of NRED doubles into v[] (valid in thread 0): slot
-// `max_slot` takes the maximum (-1: none), the others the sum.
+// Combine step of the NRED-value reductions: the sum, or for the max slot the
+// maximum taken on the bit patterns (which order non-negative doubles like
+// their values; a NaN wins, so a NaN residual never reads as converged).
+__device__ __forceinline__ double red_comb(double a, double b, bool is_max) {
+  const long long m = max(__double_as_longlong(a), __double_as_longlong(b));
+  return is_max ? __longlong_as_double(m) : a + b;
+}
+
+// Warp reduction of NRED = 8 doubles in 9 FP64 additions per lane instead of
+// 8 x 5: each butterfly step sends half of the values a lane still carries to
+// its partner, so after three steps a lane carries one value and two more
+// steps finish it. On return lane l holds the warp total of value
+// 4 b4 + 2 b3 + b2 (b = the bits of l); lane 4k holds value k. FP64 runs at a
+// small fraction of the FP32 rate on this part, so the count matters.
+__device__ __forceinline__ double warp_reduce8(const double (&v)[NRED], int max_slot) {
+  static_assert(NRED == 8, "warp_reduce8 is written for 8 values");
+  const int lane = threadIdx.x & 31;
+  const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0, h2 = (lane & 4) != 0;
+  double u[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const double keep = h4 ? v[4 + j] : v[j];
+    const double send = h4 ? v[j] : v[4 + j];
+    u[j] = red_comb(keep, __shfl_xor_sync(0xffffffffu, send, 16), (h4 ? 4 : 0) + j == max_slot);
+  }
+  double w[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const double keep = h3 ? u[2 + j] : u[j];
+    const double send = h3 ? u[j] : u[2 + j];
+    w[j] = red_comb(keep, __shfl_xor_sync(0xffffffffu, send, 8), (h4 ? 4 : 0) + (h3 ? 2 : 0) + j == max_slot);
+  }
+  const bool mx = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0) == max_slot;
+  double x = red_comb(h2 ? w[1] : w[0], __shfl_xor_sync(0xffffffffu, h2 ? w[0] : w[1], 4), mx);
+  x = red_comb(x, __shfl_xor_sync(0xffffffffu, x, 2), mx);
+  x = red_comb(x, __shfl_xor_sync(0xffffffffu, x, 1), mx);
+  return x;
+}
+
+// Block reduction of NRED doubles: on return every thread's v[] holds the
+// block totals. Slot `max_slot` takes the maximum (-1: none; its values must
+// be non-negative), the others the sum, in a fixed order.
 // scratch: NRED * 32 doubles of shared memory.
 __device__ __forceinline__ void block_reduce_red(double (&v)[NRED], double* scratch, int max_slot) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NRED; ++i) v[i] = (i == max_slot) ? warp_max(v[i]) : warp_sum(v[i]);
+  const double x = warp_reduce8(v, max_slot);
+  if ((lane & 3) == 0) scratch[(lane >> 2) * 32 + w] = x;
   __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NRED; ++i) scratch[i * 32 + w] = v[i];
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int i = 0; i < NRED; ++i) {
-      double x = lane < nw ? scratch[i * 32 + lane] : 0.0;
-      v[i] = (i == max_slot) ? warp_max(x) : warp_sum(x);
-    }
+  if (w == 0 && lane < NRED) {   // lane k adds the warps' totals of value k
+    double t = scratch[lane * 32];
+    for (int j = 1; j < nw; ++j) t = red_comb(t, scratch[lane * 32 + j], lane == max_slot);
+    scratch[lane * 32] = t;
   }
   __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NRED; ++i) v[i] = scratch[i * 32];
+  __syncthreads();   // the next call may overwrite scratch
 }
 
 // ---------------------------------------------------------------------------
@@ -450,14 +511,6 @@ __device__ __forceinline__ bool grid_allreduce(Grid& g, double (&v)[NRED], doubl
                                                int max_slot) {
   if (g.local) {
     block_reduce_red(v, scratch, max_slot);
-    __shared__ double s_loc[NRED];
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int k = 0; k < NRED; ++k) s_loc[k] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NRED; ++k) v[k] = s_loc[k];
-    __syncthreads();
     return true;
   }
   const bool probe = g.prof && blockIdx.x == 0 && threadIdx.x == 0;
@@ -478,18 +531,12 @@ __device__ __forceinline__ bool grid_allreduce(Grid& g, double (&v)[NRED], doubl
 #pragma unroll
     for (int k = 0; k < NRED; ++k) {
       const double y = __ldcg(part + (size_t)c * NRED + k);
-      x[k] = (k == max_slot) ? fmax(x[k], y) : x[k] + y;
+      x[k] = red_comb(x[k], y, k == max_slot);
     }
   }
   block_reduce_red(x, scratch, max_slot);
-  __shared__ double s_out[NRED];
-  if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < NRED; ++k) s_out[k] = x[k];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NRED; ++k) v[k] = s_out[k];
-  __syncthreads();
+  for (int k = 0; k < NRED; ++k) v[k] = x[k];
   if (probe) {
     g.prof[13] += (unsigned long long)(clock64() - t0);
     g.prof[15] += 1;

@@ -40,6 +40,12 @@ cudaError_t launch_convert_f32_f64(const float* a, double* b, long long n, cudaS
 
 template <class T>
 cudaError_t launch_apply_L(const Prob<T>& P, const int* ynode, const T* z, T* eta, cudaStream_t s);
+// centred FP32 iteration (spock_centre.cu): the centre's data from T(c) and
+// L z_c, the move of an increment into the centre, an FP32 copy of it
+cudaError_t launch_centre(const Prob<double>& P, const double* c, const double* tc, const double* lz, double alpha,
+                          float* cz, double* A, double* B, cudaStream_t st);
+cudaError_t launch_centre_move(long long n, double* c, const float* d, cudaStream_t st);
+cudaError_t launch_centre_to_f32(long long n, const double* c, float* v, cudaStream_t st);
 template <class T>
 cudaError_t launch_apply_Lt(const Prob<T>& P, const int* ynode, const T* eta, T* z, cudaStream_t s);
 

@@ -92,6 +92,12 @@ struct spock_problem {
   double* d_out_risk;
   double* d_diag_part = nullptr;   // partials and result of the FP64 exit check (first use)
   long long setup_peak = 0;        // device bytes held at the end of the offline part (its peak)
+  // centred FP32 iteration (first use): the centre's eta data A, B (FP64,
+  // n_eta each), cz (FP32, n_z) and zeros standing in for the constant terms
+  void* ctr_block = nullptr;
+  long long ctr_bytes = 0;
+  double *d_ctrA = nullptr, *d_ctrB = nullptr;
+  float *d_cz = nullptr, *d_zero32 = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 

@@ -120,23 +120,22 @@ __device__ void s2_block(const Prob<T>& P, int lane, int i, const T* __restrict_
     const T lam = (gv - corr) / cc;
     sl += lam;
     const int c = c0 + l;
-    const T n1 = wy1 - a * lam, n2 = wy2 + lam, nt = wtl + lam, ns = wsl + lam;
     long long idx;
-    idx = yo + l;           { const T o = ldc(z + idx); stc(vout + idx, n1); ra.z(o, n1, dirv(vref, idx)); }
-    idx = yo + m + l;       { const T o = ldc(z + idx); stc(vout + idx, n2); ra.z(o, n2, dirv(vref, idx)); }
-    idx = P.o_tau + c - 1;  { const T o = ldc(z + idx); stc(vout + idx, nt); ra.z(o, nt, dirv(vref, idx)); }
-    idx = P.o_s + c - 1;    { const T o = ldc(z + idx); stc(vout + idx, ns); ra.z(o, ns, dirv(vref, idx)); }
+    idx = yo + l;           { const T o = ldc(z + idx), n1 = zc_add(P, idx, wy1 - a * lam); stc(vout + idx, n1); ra.z(o, n1, dirv(vref, idx)); }
+    idx = yo + m + l;       { const T o = ldc(z + idx), n2 = zc_add(P, idx, wy2 + lam); stc(vout + idx, n2); ra.z(o, n2, dirv(vref, idx)); }
+    idx = P.o_tau + c - 1;  { const T o = ldc(z + idx), nt = zc_add(P, idx, wtl + lam); stc(vout + idx, nt); ra.z(o, nt, dirv(vref, idx)); }
+    idx = P.o_s + c - 1;    { const T o = ldc(z + idx), ns = zc_add(P, idx, wsl + lam); stc(vout + idx, ns); ra.z(o, ns, dirv(vref, idx)); }
   }
   sl = warp_sum(sl);
   if (lane == 0) {
     const long long idx = yo + 2 * m;
-    const T n3 = y3 - sl;
+    const T n3 = zc_add(P, idx, y3 - sl);
     const T o = ldc(z + idx);
     stc(vout + idx, n3);
     ra.z(o, n3, dirv(vref, idx));
-    if (i == 0) {   // s0 <- s0 - alpha (eta_s^0) - alpha
+    if (i == 0) {   // s0 <- s0 - alpha (eta_s^0) - alpha (the last term is constant: not in the linear part)
       const T o0 = ldc(z);
-      const T n0 = (o0 - al * eS) - al;
+      const T n0 = zc_add(P, 0, P.lin ? (o0 - al * eS) : (o0 - al * eS) - al);
       stc(vout, n0);
       ra.z(o0, n0, dirv(vref, 0));
     }
@@ -468,9 +467,10 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_b
     if (k < nx) {
       if (i == 0) {
         v = P.x0s[k];
-        stc(vout + o_x + k, v);
+        stc(vout + o_x + k, zc_add(P, o_x + k, v));
       } else {
-        v = ldc(vout + o_x + (long long)i * nx + k);
+        const long long ix = o_x + (long long)i * nx + k;
+        v = zc_sub(P, ix, ldc(vout + ix));
       }
     } else {
       v = ldc(dbuf + (long long)i * nu + (k - nx));
@@ -532,7 +532,8 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_b
         const int j = t + m * nth;
         if (j < nx) {
           const T xc = ax[m] + cp[m];
-          stc(vout + o_x + (long long)c * nx + j, xc);
+          const long long ix = o_x + (long long)c * nx + j;
+          stc(vout + ix, zc_add(P, ix, xc));
           if (chain) cout[j] = xc;
         }
       }
@@ -545,14 +546,18 @@ __device__ bool forward_segment(const Prob<T>& P, const Team& tm, T* s_a, T* s_b
           if (t >= nx && t < w) {
             const int tu = t - nx;
             col_mv<T>(KTb, ldK, nx, cin, tu, nth, nu, au);
-            stc(vout + o_u + (long long)i * nu + tu, au[0] + cin[nx + tu]);
+            const long long iu = o_u + (long long)i * nu + tu;
+            stc(vout + iu, zc_add(P, iu, au[0] + cin[nx + tu]));
           }
         } else {
           col_mv<T>(KTb, ldK, nx, cin, t, nth, nu, au);
 #pragma unroll
           for (int m = 0; m < NPM; ++m) {
             const int j = t + m * nth;
-            if (j < nu) stc(vout + o_u + (long long)i * nu + j, au[m] + cin[nx + j]);
+            if (j < nu) {
+              const long long iu = o_u + (long long)i * nu + j;
+              stc(vout + iu, zc_add(P, iu, au[m] + cin[nx + j]));
+            }
           }
         }
       }
@@ -588,6 +593,21 @@ __device__ __forceinline__ void z_resid(const T* __restrict__ vin, const T* __re
 // ---------------------------------------------------------------------------
 // Phase E: eta blocks (one warp each); x, u, y, tau, s of z+ are read from vout
 // ---------------------------------------------------------------------------
+// prox step of one element ie of eta whose set C is a product of intervals:
+// eta+ = eb - alpha proj_C(eb / alpha). In the centred form eb is the
+// increment over the centre, the argument and the step are formed in FP64
+// about the centre, and the increment eta+ - eta_c is returned.
+template <class T, class PF>
+__device__ __forceinline__ T eta_prox(const Prob<T>& P, long long ie, T eb, PF&& proj) {
+  if (P.ctrA) {
+    const double w = fma((double)eb, P.ctr_ial, ldr(P.ctrA + ie));
+    return (T)fma(-P.ctr_al, proj(w), ldr(P.ctrB + ie) + (double)eb);
+  }
+  const T al = P.alpha;
+  const T w = eb / al;
+  return eb - al * proj(w);
+}
+
 template <class T>
 __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restrict__ vin,
                             T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
@@ -605,9 +625,8 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     const T Lo = ldc(z + yo + e), Ln = ldc(vout + yo + e);
     const T eo_ = ldc(eta + ye + e);
     const T eb = eo_ + al * (T(2) * Ln - Lo);
-    const T w = eb / al;
-    const T p = (e < 2 * m) ? max(w, T(0)) : w;
-    const T en = eb - al * p;
+    const bool cone = e < 2 * m;
+    const T en = eta_prox(P, ye + e, eb, [&](auto w) { return cone ? max(w, decltype(w)(0)) : w; });
     stc(eo + ye + e, en);
     ra.eta(eo_, en, er ? ldc(er + ye + e) : T(0), Lo - Ln, dirv(vref, yo + e));
   }
@@ -635,7 +654,7 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
       const long long ie = P.e_s + i;
       const T eo_ = ldc(eta + ie);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
-      const T en = eb - al * max(eb / al, T(0));
+      const T en = eta_prox(P, ie, eb, [&](auto w) { return max(w, decltype(w)(0)); });
       stc(eo + ie, en);
       ra.eta(eo_, en, er ? ldc(er + ie) : T(0), lrz, lod);
     }
@@ -657,25 +676,40 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     const T Lo = g * o, Ln = g * nn;
     const T eo_ = ldc(eta + ce + e);
     const T eb = eo_ + al * (T(2) * Ln - Lo);
-    const T w = eb / al;
     const T lo = P.box_lo[(long long)i * P.nbox + e], hi = P.box_hi[(long long)i * P.nbox + e];
-    const T p = min(max(w, lo), hi);
-    const T en = eb - al * p;
+    const T en = eta_prox(P, ce + e, eb, [&](auto w) {
+      using V = decltype(w);
+      return min(max(w, (V)lo), (V)hi);
+    });
     stc(eo + ce + e, en);
     ra.eta(eo_, en, er ? ldc(er + ce + e) : T(0), g * (o - nn), g * dirv(vref, idx));
   }
   // ball rows on u
   if (P.has_ball) {
-    T n2 = 0;
+    const bool ctr = P.ctrA != nullptr;
+    double n2 = 0;   // FP64 in the centred form, where w is formed about the centre
     for (int k = lane; k < nu; k += 32) {
       const T g = P.gu[k];
-      const T eb = ldc(eta + ce + P.nbox + k) + al * (T(2) * g * ldc(vout + uo + k) - g * ldc(z + uo + k));
-      const T w = eb / al;
-      n2 += w * w;
+      const long long ie = ce + P.nbox + k;
+      const T eb = ldc(eta + ie) + al * (T(2) * g * ldc(vout + uo + k) - g * ldc(z + uo + k));
+      if (ctr) {
+        const double w = fma((double)eb, P.ctr_ial, ldr(P.ctrA + ie));
+        n2 = fma(w, w, n2);
+      } else {
+        const T w = eb / al;
+        n2 = (double)((T)n2 + w * w);
+      }
     }
-    const T nw = sqrt(warp_sum(n2));
-    const T r = P.ball[i];
-    const T sc = (nw > r) ? r / nw : T(1);
+    const double r = (double)P.ball[i];
+    double sc = 1.0;
+    T scT = T(1);
+    if (ctr) {
+      const double nw = sqrt(warp_sum(n2));
+      sc = (nw > r) ? r / nw : 1.0;
+    } else {
+      const T nw = sqrt(warp_sum((T)n2));
+      scT = (nw > (T)r) ? (T)r / nw : T(1);
+    }
     for (int k = lane; k < nu; k += 32) {
       const T g = P.gu[k];
       const T o = ldc(z + uo + k), nn = ldc(vout + uo + k);
@@ -683,8 +717,8 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
       const long long ie = ce + P.nbox + k;
       const T eo_ = ldc(eta + ie);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
-      const T w = eb / al;
-      const T en = eb - al * (w * sc);
+      const T en = ctr ? eta_prox(P, ie, eb, [&](auto w) { return w * (decltype(w))sc; })
+                       : eta_prox(P, ie, eb, [&](auto w) { return w * (decltype(w))scT; });
       stc(eo + ie, en);
       ra.eta(eo_, en, er ? ldc(er + ie) : T(0), g * (o - nn), g * dirv(vref, uo + k));
     }
@@ -706,11 +740,55 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
       }
       const T eo_ = ldc(eta + ge + r);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
-      const T w = eb / al;
-      const T p = min(max(w, P.gen_lo[(long long)i * P.n_g + r]), P.gen_hi[(long long)i * P.n_g + r]);
-      const T en = eb - al * p;
+      const T lo = P.gen_lo[(long long)i * P.n_g + r], hi = P.gen_hi[(long long)i * P.n_g + r];
+      const T en = eta_prox(P, ge + r, eb, [&](auto w) {
+        using V = decltype(w);
+        return min(max(w, (V)lo), (V)hi);
+      });
       stc(eo + ge + r, en);
       ra.eta(eo_, en, er ? ldc(er + ge + r) : T(0), Ld, Lrd);
+    }
+  }
+}
+
+// Cost cone block in the centred form: ebv holds the increments of
+// eta_bar = eta + alpha L(2 z+ - z) over the centre; w = eta_bar/alpha - a is
+// formed in FP64 about the centre (ctrA folds in -a), projected on the
+// second-order cone in FP64, and the increment of eta+ = eta_bar - alpha (a +
+// Pi(w)) over eta_c is stored (ctrB folds in -alpha a).
+template <class T, int NE>
+__device__ __forceinline__ void soc_centred(const Prob<T>& P, int lane, int dim, long long ebase,
+                                            const T* __restrict__ eta, T* __restrict__ eo,
+                                            const T* __restrict__ er, const T (&ebv)[NE], const T (&ldv)[NE],
+                                            const T (&lrv)[NE], RedAcc<T>& ra) {
+  double wv[NE];
+  double n2 = 0.0, tt = 0.0;
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    wv[q] = 0.0;
+    if (e < dim) {
+      wv[q] = fma((double)ebv[q], P.ctr_ial, ldr(P.ctrA + ebase + e));
+      if (e < dim - 1) n2 = fma(wv[q], wv[q], n2);
+      else tt = wv[q];
+    }
+  }
+  const double nw = sqrt(warp_sum(n2));
+  const double t = __shfl_sync(0xffffffffu, tt, (dim - 1) & 31);
+  const int cs = (nw <= t) ? 0 : ((nw <= -t) ? 1 : 2);
+  const double f = 0.5 * (nw + t);
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    if (e < dim) {
+      double ps;
+      if (cs == 0) ps = wv[q];
+      else if (cs == 1) ps = 0.0;
+      else ps = (e < dim - 1) ? wv[q] * (f / nw) : f;
+      const T en = (T)fma(-P.ctr_al, ps, ldr(P.ctrB + ebase + e) + (double)ebv[q]);
+      const T eo_ = ldc(eta + ebase + e);
+      stc(eo + ebase + e, en);
+      ra.eta(eo_, en, er ? ldc(er + ebase + e) : T(0), ldv[q], lrv[q]);
     }
   }
 }
@@ -746,6 +824,21 @@ __device__ __forceinline__ void soc_block(const Prob<T>& P, int lane, int dim, l
       else tt = w;
     }
   }
+  if (P.ctrA) {   // centred form: the projection about the centre in FP64
+    T ldv[NE], lrv[NE];
+#pragma unroll
+    for (int q = 0; q < NE; ++q) {
+      const int e = lane + 32 * q;
+      ldv[q] = T(0);
+      lrv[q] = T(0);
+      if (e < dim) {
+        T Lo, Ln;
+        Lz(e, Lo, Ln, ldv[q], lrv[q]);
+      }
+    }
+    soc_centred<T, NE>(P, lane, dim, ebase, eta, eo, er, ebv, ldv, lrv, ra);
+    return;
+  }
   const T nw = sqrt(warp_sum(n2));
   const T t = __shfl_sync(0xffffffffu, tt, (dim - 1) & 31);
   // case 0: inside (keep), 1: polar (zero), 2: boundary
@@ -780,6 +873,10 @@ __device__ __forceinline__ void soc_block_vals(const Prob<T>& P, int lane, int d
                                                const T* __restrict__ eta, T* __restrict__ eo,
                                                const T* __restrict__ er, const T (&ebv)[NE], const T (&ldv)[NE],
                                                const T (&lrv)[NE], const T* acst, RedAcc<T>& ra) {
+  if (P.ctrA) {
+    soc_centred<T, NE>(P, lane, dim, ebase, eta, eo, er, ebv, ldv, lrv, ra);
+    return;
+  }
   const T al = P.alpha;
   T n2 = 0, tt = 0;
 #pragma unroll
@@ -945,9 +1042,11 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
       const T Lo = g * o, Ln = g * nn;
       const T eo_ = ldc(eta + ce + e);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
-      const T w = eb / al;
-      const T p = min(max(w, P.boxN_lo[(long long)jj * nx + e]), P.boxN_hi[(long long)jj * nx + e]);
-      const T en = eb - al * p;
+      const T lo = P.boxN_lo[(long long)jj * nx + e], hi = P.boxN_hi[(long long)jj * nx + e];
+      const T en = eta_prox(P, ce + e, eb, [&](auto w) {
+        using V = decltype(w);
+        return min(max(w, (V)lo), (V)hi);
+      });
       stc(eo + ce + e, en);
       ra.eta(eo_, en, er ? ldc(er + ce + e) : T(0), g * (o - nn), g * dirv(vref, xo + e));
     }
@@ -968,9 +1067,11 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
       }
       const T eo_ = ldc(eta + ge + r);
       const T eb = eo_ + al * (T(2) * Ln - Lo);
-      const T w = eb / al;
-      const T p = min(max(w, P.genN_lo[(long long)jj * P.n_gN + r]), P.genN_hi[(long long)jj * P.n_gN + r]);
-      const T en = eb - al * p;
+      const T lo = P.genN_lo[(long long)jj * P.n_gN + r], hi = P.genN_hi[(long long)jj * P.n_gN + r];
+      const T en = eta_prox(P, ge + r, eb, [&](auto w) {
+        using V = decltype(w);
+        return min(max(w, (V)lo), (V)hi);
+      });
       stc(eo + ge + r, en);
       ra.eta(eo_, en, er ? ldc(er + ge + r) : T(0), Ld, Lrd);
     }
@@ -1216,6 +1317,61 @@ __device__ __forceinline__ void stv(T* p, long long q, const T (&o)[Vec<T>::N]) 
   V x;
   memcpy(&x, o, sizeof(V));
   __stcg(reinterpret_cast<V*>(p) + q, x);
+}
+
+// kappa of the Anderson least-squares problem min ||Y kappa - r||_2 from the
+// Gram matrix G = Y'Y (ring slots) and b = Y'r: Cholesky factorisation of G
+// in the memory's logical order (oldest pair first, starting at ring slot
+// `start`), the rank test on its pivots (a pivot R_jj below
+// rank_tol * sqrt(trace G) = rank_tol * ||Y||_F rejects the direction), then
+// the two triangular solves. Every index is fixed at compile time (the ring
+// rotation and the unused slots are selects), so it runs in registers; one
+// thread calls it, because FP64 arithmetic is slow on this part and 256
+// redundant copies cost as much as the Anderson pass itself. Slots j >= count
+// take an identity row, which gives kappa_j = 0. Returns false when the test
+// rejects; kap is in ring-slot order.
+__device__ __forceinline__ bool aa_gram_kappa(const double (&G)[AA_M][AA_M], const double (&b)[AA_M], int count,
+                                              int start, double rank_tol, double (&kap)[AA_M]) {
+  static_assert(AA_M == 3, "aa_gram_kappa is written for a memory of three pairs");
+  double g[3][3], bl[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const double v = (start == 0) ? G[j][l] : ((start == 1) ? G[(j + 1) % 3][(l + 1) % 3] : G[(j + 2) % 3][(l + 2) % 3]);
+      g[j][l] = (j < count && l < count) ? v : (j == l ? 1.0 : 0.0);
+    }
+    const double bv = (start == 0) ? b[j] : ((start == 1) ? b[(j + 1) % 3] : b[(j + 2) % 3]);
+    bl[j] = (j < count) ? bv : 0.0;
+  }
+  double tr = g[0][0];
+  if (count > 1) tr += g[1][1];
+  if (count > 2) tr += g[2][2];
+  if (!(tr > 0.0)) return false;
+  const double lim2 = rank_tol * rank_tol * tr;   // R_jj < rank_tol sqrt(tr)  <=>  R_jj^2 < lim2
+  const double d0 = g[0][0];
+  if (!(d0 > 0.0) || d0 < lim2) return false;
+  const double i0 = rsqrt(d0);
+  const double r01 = g[0][1] * i0, r02 = g[0][2] * i0;
+  const double d1 = fma(-r01, r01, g[1][1]);
+  if (count > 1 && (!(d1 > 0.0) || d1 < lim2)) return false;
+  const double i1 = rsqrt(d1);
+  const double r12 = fma(-r01, r02, g[1][2]) * i1;
+  const double d2 = fma(-r12, r12, fma(-r02, r02, g[2][2]));
+  if (count > 2 && (!(d2 > 0.0) || d2 < lim2)) return false;
+  const double i2 = rsqrt(d2);
+  // R'c = b, then R k = c
+  const double c0 = bl[0] * i0;
+  const double c1 = fma(-r01, c0, bl[1]) * i1;
+  const double c2 = fma(-r12, c1, fma(-r02, c0, bl[2])) * i2;
+  const double k2 = c2 * i2;
+  const double k1 = fma(-r12, k2, c1) * i1;
+  const double k0 = fma(-r02, k2, fma(-r01, k1, c0)) * i0;
+  const double kl[3] = {k0, k1, k2};
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+    kap[p] = (start == 0) ? kl[p] : ((start == 1) ? kl[(p + 2) % 3] : kl[(p + 1) % 3]);
+  return true;
 }
 
 // Anderson memory with the least-squares factorisation Y = Q R kept up to
@@ -1523,49 +1679,31 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
           __shared__ double scratch2[NRED * 32];
           if (!grid_allreduce(g, dd, scratch2, -1)) goto fail;
         }
-        double bvec[AA_M];
         if (push) {
           if (count < AA_M) ++count;
           head = (head + 1) % AA_M;
-          for (int l = 0; l < AA_M; ++l) { G[slot][l] = dd[l]; G[l][slot] = dd[l]; }
+#pragma unroll
+          for (int a = 0; a < AA_M; ++a)
+#pragma unroll
+            for (int b = 0; b < AA_M; ++b) {
+              if (a == slot) G[a][b] = dd[b];
+              else if (b == slot) G[a][b] = dd[a];
+            }
         }
-        for (int l = 0; l < AA_M; ++l) bvec[l] = dd[AA_M + l];
         if (k > AA_M && count > 0) {
-          // logical order oldest -> newest
-          int ord[AA_M];
-          const int start = (count < AA_M) ? 0 : head;
-          for (int j = 0; j < count; ++j) ord[j] = (start + j) % AA_M;
-          double Rm[AA_M][AA_M], bb[AA_M], tr = 0.0;
-          for (int j = 0; j < count; ++j) tr += G[ord[j]][ord[j]];
-          const double lim = o.rank_tol * sqrt(fmax(tr, 0.0));
-          bool good = tr > 0.0;
-          for (int a = 0; a < AA_M; ++a) for (int b = 0; b < AA_M; ++b) Rm[a][b] = 0.0;
-          for (int j = 0; j < count && good; ++j) {
-            double dj = G[ord[j]][ord[j]];
-            for (int l = 0; l < j; ++l) dj -= Rm[l][j] * Rm[l][j];
-            if (!(dj > 0.0) || sqrt(dj) < lim) { good = false; break; }
-            Rm[j][j] = sqrt(dj);
-            for (int c = j + 1; c < count; ++c) {
-              double s = G[ord[j]][ord[c]];
-              for (int l = 0; l < j; ++l) s -= Rm[l][j] * Rm[l][c];
-              Rm[j][c] = s / Rm[j][j];
-            }
-          }
-          if (good) {
-            // R'R kappa = Y'r : forward then backward substitution
-            for (int j = 0; j < count; ++j) {
-              double s = bvec[ord[j]];
-              for (int l = 0; l < j; ++l) s -= Rm[l][j] * bb[l];
-              bb[j] = s / Rm[j][j];
-            }
+          __shared__ double s_kap[AA_M + 1];
+          if (threadIdx.x == 0) {
+            const double bvec[AA_M] = {dd[AA_M], dd[AA_M + 1], dd[AA_M + 2]};
             double kl[AA_M];
-            for (int j = count - 1; j >= 0; --j) {
-              double s = bb[j];
-              for (int l = j + 1; l < count; ++l) s -= Rm[j][l] * kl[l];
-              kl[j] = s / Rm[j][j];
-            }
-            for (int j = 0; j < count; ++j) kap[ord[j]] = kl[j];
-            for (int j = 0; j < AA_M; ++j) kapY[j] = kap[j];
+            const bool good = aa_gram_kappa(G, bvec, count, (count < AA_M) ? 0 : head, o.rank_tol, kl);
+#pragma unroll
+            for (int j = 0; j < AA_M; ++j) s_kap[j] = kl[j];
+            s_kap[AA_M] = good ? 1.0 : 0.0;
+          }
+          __syncthreads();
+          if (s_kap[AA_M] != 0.0) {
+#pragma unroll
+            for (int j = 0; j < AA_M; ++j) { kap[j] = s_kap[j]; kapY[j] = s_kap[j]; }
             use_aa = true;
           }
         }

@@ -26,7 +26,7 @@ EXPORTED = [
     "spock_problem_set_alpha", "spock_problem_scalings", "spock_problem_factors",
     "spock_problem_set_x0", "spock_op_T", "spock_op_L", "spock_op_Lt", "spock_solve_opts_default",
     "spock_solve", "spock_solve_device", "spock_get_iterate", "spock_set_iterate",
-    "spock_status_str", "spock_version", "spock_op_T_noalloc",
+    "spock_status_str", "spock_version", "spock_op_T_noalloc", "spock_op_T_centred",
     "spock_batch_create", "spock_batch_destroy", "spock_batch_sizes", "spock_batch_set_tw",
     "spock_batch_autotune", "spock_batch_solve",
     "spock_server_create", "spock_server_submit", "spock_server_poll", "spock_server_outstanding",
@@ -59,7 +59,7 @@ class Sizes(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iters", C.c_int),
                 ("max_backtracks", C.c_int), ("method", C.c_int), ("warm_start", C.c_int),
-                ("fp64_check", C.c_int), ("aa_mode", C.c_int)]
+                ("fp64_check", C.c_int), ("aa_mode", C.c_int), ("recentre", C.c_double)]
 
 
 class Info(C.Structure):
@@ -68,7 +68,8 @@ class Info(C.Structure):
                 ("n_backtracks", C.c_int), ("res_inf", C.c_double), ("res_inf_fp64", C.c_double),
                 ("risk", C.c_double), ("device_ms", C.c_double), ("phase_ms", C.c_double * 7),
                 ("counters", C.c_double * 8), ("xi1", C.c_double), ("xi2", C.c_double),
-                ("infeas", C.c_double), ("gap", C.c_double)]
+                ("infeas", C.c_double), ("gap", C.c_double), ("n_recentre", C.c_int),
+                ("kernel_ms", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -118,6 +119,7 @@ def load(path: str = LIB_PATH):
     lib.spock_problem_set_x0.argtypes = [vp, _dp]
     lib.spock_op_T.argtypes = [vp, C.c_int, vp, vp, _dp, vp]
     lib.spock_op_T_noalloc.argtypes = [vp, C.c_int, vp, vp, _dp, vp]
+    lib.spock_op_T_centred.argtypes = [vp, vp, vp, vp, _dp, vp]
     lib.spock_op_L.argtypes = [vp, C.c_int, vp, vp, vp]
     lib.spock_op_Lt.argtypes = [vp, C.c_int, vp, vp, vp]
     lib.spock_solve_opts_default.argtypes = [C.POINTER(SolveOpts)]
@@ -182,7 +184,7 @@ def _f64(a):
 
 
 def opts(precision=64, tol=1e-4, max_iters=5000, max_backtracks=30, method="spock",
-         warm_start=False, fp64_check=True, aa="gram") -> SolveOpts:
+         warm_start=False, fp64_check=True, aa="gram", recentre=None) -> SolveOpts:
     o = SolveOpts()
     load().spock_solve_opts_default(C.byref(o))
     o.precision = int(precision)
@@ -193,6 +195,8 @@ def opts(precision=64, tol=1e-4, max_iters=5000, max_backtracks=30, method="spoc
     o.warm_start = int(bool(warm_start))
     o.fp64_check = int(bool(fp64_check))
     o.aa_mode = {"gram": 0, "qr_update": 1}[aa]
+    if recentre is not None:      # FP32: 0 plain iteration, > 0 centred (library default 0.1)
+        o.recentre = float(recentre)
     return o
 
 
@@ -307,6 +311,21 @@ class Problem:
                                  C.c_void_p(v_out.data_ptr()), _ptr(stats),
                                  C.c_void_p(stream.cuda_stream if stream else 0)), "spock_op_T")
         return v_out, stats
+
+    def T_centred(self, c, delta, out=None, stream=None):
+        """out = T(c + delta) - c through spock_op_T_centred: c a float64 CUDA
+        tensor, delta a float32 one (n_v each); returns (out, stats[8])."""
+        import torch
+        assert c.is_cuda and c.dtype == torch.float64 and c.is_contiguous() and c.numel() == self.n_v
+        assert delta.is_cuda and delta.dtype == torch.float32 and delta.is_contiguous() and delta.numel() == self.n_v
+        if out is None:
+            out = torch.empty_like(delta)
+        self._check_pair(delta, out)
+        stats = np.zeros(8)
+        _check(load().spock_op_T_centred(self.h, C.c_void_p(c.data_ptr()), C.c_void_p(delta.data_ptr()),
+                                         C.c_void_p(out.data_ptr()), _ptr(stats),
+                                         C.c_void_p(stream.cuda_stream if stream else 0)), "spock_op_T_centred")
+        return out, stats
 
     def T_noalloc(self, v_in, v_out, stream=None):
         """v_out = T(v_in) through spock_op_T_noalloc (no device allocation in

@@ -121,13 +121,13 @@ def test_algorithmic_bytes_counting():
     """The roofline's byte count on the 31-node problem, by hand: per T the
     factors MB (nx(nx+nu)) and MF ((nx+nu)nx) of every non-root node and MP
     (nu(nx+nu)) and KT (nx nu) of every non-leaf node, plus 8 passes over v;
-    per iteration 21 passes over v."""
+    per iteration 5 passes over v (the Anderson memory)."""
     import bench
     sizes = dict(n=31, n_nonleaf=23, nx=4, nu=2, n_v=878)
     total, per_T = bench.algorithmic_bytes(sizes, n_T=10, iters=7, word=4)
     factors = 30 * (4 * 6 + 6 * 4) + 23 * (2 * 6 + 4 * 2)
     assert per_T == 4 * (factors + 8 * 878)
-    assert total == 10 * per_T + 7 * 4 * 21 * 878
+    assert total == 10 * per_T + 7 * 4 * 5 * 878
 
 
 def _desc_call_general(p, mutate):

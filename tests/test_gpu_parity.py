@@ -76,6 +76,15 @@ def _pair(name):
     return p, o, g
 
 
+def _converged_ref(name):
+    """risk and u^0 of the oracle's solve of case `name` to 1e-7 (golden file)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "converged_cases.json")) as f:
+        d = json.load(f)["cases"][name]
+    return {"risk": d["risk"], "u": np.array([d["u0"]])}
+
+
 def _relerr(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -147,6 +156,48 @@ def test_one_T_fp64_and_fp32(name):
         assert _relerr(out32.cpu().numpy(), ref) < 2e-5, name
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_centred_T_fp32(name):
+    """The centred form of T that the centred FP32 iteration runs on
+    (spock_op_T_centred): out = T(c + delta) - c for an FP64 centre c (the
+    oracle's iterate after 30 SPOCK iterations) and an FP32 increment delta,
+    against the oracle's T(c + delta) - c. The error is measured against the
+    increments (max|delta|, max|T(c + delta) - c|), not against c: that is the
+    point of the form. delta = 0 gives the centre's own step T(c) - c."""
+    p, o, g = _pair(name)
+    g.set_alpha(o.alpha)
+    g.set_x0(p.x0)
+    c = o.solve(tol=0.0, max_iters=30)["v"]
+    ct = torch.tensor(c, device="cuda")
+    rng = np.random.default_rng(41)
+    for amp in (0.0, 1e-3, 1e-1):
+        delta = (amp * max(1.0, float(np.max(np.abs(c)))) * rng.standard_normal(c.size)).astype(np.float32)
+        ref = o.T(c + delta.astype(np.float64)) - c
+        out, stats = g.T_centred(ct, torch.tensor(delta, device="cuda"))
+        got = out.cpu().numpy().astype(np.float64)
+        scale = max(float(np.max(np.abs(ref))), float(np.max(np.abs(delta))))
+        assert float(np.max(np.abs(got - ref))) <= 2e-5 * scale, (name, amp)
+        r = delta.astype(np.float64) - ref
+        assert abs(stats[0] - np.max(np.abs(r))) <= 2e-5 * scale
+
+
+def test_centred_T_large_centre():
+    """With a centre of magnitude 1e3 and increments of 1e-2 the centred form
+    keeps its error at the increments' scale (2e-5 of it), far below the
+    rounding of c itself in FP32 (about 6e-5)."""
+    p, o, g = _pair("ragged_37x19_ball")
+    g.set_alpha(o.alpha)
+    g.set_x0(p.x0)
+    rng = np.random.default_rng(43)
+    c = 1e3 * rng.standard_normal(o.lay.n_z + o.lay.n_eta)
+    delta = (1e-2 * rng.standard_normal(c.size)).astype(np.float32)
+    ref = o.T(c + delta.astype(np.float64)) - c
+    out, _ = g.T_centred(torch.tensor(c, device="cuda"), torch.tensor(delta, device="cuda"))
+    scale = max(float(np.max(np.abs(ref))), float(np.max(np.abs(delta))))
+    err = float(np.max(np.abs(out.cpu().numpy().astype(np.float64) - ref)))
+    assert err <= 2e-5 * scale, (err, scale)
+
+
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "avar0_branch8"])
 def test_fixed_iterations_cp_fp64(name):
     """Plain CP iterates v <- T(v) from zero for a fixed count: <= 1e-10 relative."""
@@ -184,16 +235,23 @@ def test_fixed_iterations_spock_fp64(name):
     assert _relerr(v, ref["v"]) < 1e-10
 
 
-@pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "chain_only", "full_lin_box", "rows_ball_diag_lin"])
-def test_converged_fp32_vs_oracle(name):
-    """FP32 iteration to ||v - T(v)||_inf <= 1e-4 against the oracle's converged
-    FP64 solution: risk value and u^0 within 1e-3 relative; x/u everywhere
-    reported; FP64 residual check of the FP32 iterate."""
+@pytest.mark.parametrize("name,recentre", [("small", 0.1), ("ragged_37x19_ball", 0.1), ("chain_only", 0.1),
+                                           ("full_lin_box", 0.1), ("rows_ball_diag_lin", 0.1),
+                                           ("team_100x50", 0.1), ("small", 0.0), ("ragged_37x19_ball", 0.0)])
+def test_converged_fp32_vs_oracle(name, recentre):
+    """FP32 iteration to ||v - T(v)||_inf <= 1e-4 against the optimum: the
+    oracle's FP64 solve to 1e-7 (tests/golden/converged_cases.json, written by
+    tests/golden/make_converged_cases.py from the oracle alone). Risk value and
+    u^0 within 1e-3 relative; FP64 residual check of the returned iterate.
+    recentre 0.1: the centred FP32 iteration (its stopping test is the FP64
+    residual, so that is <= 1e-4); 0: the plain one."""
     p, o, g = _pair(name)
     spock = _spock()
-    ref = o.solve(tol=1e-4, max_iters=20000)
-    res = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000))
+    ref = _converged_ref(name)
+    res = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000, recentre=recentre))
     assert res["status"] == 0, res["info"]
+    if recentre > 0:
+        assert res["info"]["res_inf_fp64"] <= 1e-4 and res["info"]["n_recentre"] >= 1
     assert abs(res["risk"] - ref["risk"]) <= 1e-3 * max(1.0, abs(ref["risk"]))
     assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= 1e-3 * max(1.0, np.max(np.abs(ref["u"][0])))
     assert res["info"]["res_inf_fp64"] < 5e-4
@@ -247,13 +305,15 @@ def test_solve_reports_fp64_check(name):
     for k in ("xi1", "xi2", "infeas"):
         assert abs(inf[k] - ref[k]) <= scale, (k, inf[k], ref[k])
     assert abs(inf["gap"] - ref["gap"]) <= 1e-8 * max(1.0, abs(ref["gap"]))
-    r32 = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000))
-    c = g.check(g.get_iterate(32))
-    for k in ("xi1", "xi2", "infeas", "gap"):
-        assert r32["info"][k] == c[k], k
-    assert r32["info"]["res_inf_fp64"] == c["res_inf"]
-    # near the solution every measure is small (Sec. 5.3)
-    assert max(c["xi1"], c["xi2"]) < 5e-3 / o.alpha and c["infeas"] < 5e-3
+    # plain FP32 iteration: the check of its FP32 iterate; centred: of its FP64 iterate
+    for recentre, prec in ((0.0, 32), (0.1, 64)):
+        r32 = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000, recentre=recentre))
+        c = g.check(g.get_iterate(prec))
+        for k in ("xi1", "xi2", "infeas", "gap"):
+            assert r32["info"][k] == c[k], (recentre, k)
+        assert r32["info"]["res_inf_fp64"] == c["res_inf"]
+        # near the solution every measure is small (Sec. 5.3)
+        assert max(c["xi1"], c["xi2"]) < 5e-3 / o.alpha and c["infeas"] < 5e-3
 
 
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "wide_70x40", "full_rows_cta"])
@@ -279,10 +339,10 @@ def test_fixed_iterations_spock_qr_update_fp64(name):
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball"])
 def test_converged_fp32_qr_update(name):
     """FP32 SPOCK with the QR-updated Anderson memory to 1e-4: risk value and u^0
-    within 1e-3 of the oracle's converged solution."""
+    within 1e-3 of the optimum (the oracle's solve to 1e-7)."""
     p, o, g = _pair(name)
     spock = _spock()
-    ref = o.solve(tol=1e-4, max_iters=20000)
+    ref = _converged_ref(name)
     res = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000, aa="qr_update"))
     assert res["status"] == 0, res["info"]
     assert abs(res["risk"] - ref["risk"]) <= 1e-3 * max(1.0, abs(ref["risk"]))
