@@ -597,7 +597,7 @@ def run_ours(args, rank, world, local_rank, dist):
         try:
             tr = json.load(open(tr_path))
             if tr.get("precision") == prec and tr.get("source_hash") == solver_source_hash():
-                traffic = tr["dram_bytes_per_T"] * inf0["n_T"]
+                traffic = tr["dram_bytes_per_T"] * nT_kernel
         except Exception:
             traffic = None
     segs = max(1, inf0["n_recentre"] - 1) if prec == 32 else 1
@@ -734,6 +734,8 @@ def main():
         r = g.solve(p.x0, spock.opts(precision=args.precision, tol=0.0,
                                       max_iters=args.profile_iters, fp64_check=False))
         print(json.dumps({"n_T": r["info"]["n_T"], "iters": r["info"]["iters"],
+                          "n_T_iteration_kernel": r["info"]["n_T"] - r["info"]["n_recentre"],
+                          "centres": r["info"]["n_recentre"],
                           "precision": args.precision, "source_hash": solver_source_hash()}))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -77,12 +77,21 @@ def _pair(name):
 
 
 def _converged_ref(name):
-    """risk and u^0 of the oracle's solve of case `name` to 1e-7 (golden file)."""
+    """risk and u^0 of the oracle's solve of case `name` to 1e-7 (the optimum,
+    golden file), and the bounds a 1e-4 point is held to: 1e-3 relative, or
+    1.25 x the distance of the oracle's own 1e-4 point from the optimum where
+    that is larger (the residual tolerance bounds that distance only up to a
+    problem-dependent factor)."""
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", "converged_cases.json")) as f:
         d = json.load(f)["cases"][name]
-    return {"risk": d["risk"], "u": np.array([d["u0"]])}
+    u0 = np.array(d["u0"])
+    su, sr = max(1.0, float(np.max(np.abs(u0)))), max(1.0, abs(d["risk"]))
+    e_u = float(np.max(np.abs(np.array(d["at_1e-4"]["u0"]) - u0))) / su
+    e_r = abs(d["at_1e-4"]["risk"] - d["risk"]) / sr
+    return {"risk": d["risk"], "u": u0[None, :], "tol_u": max(1e-3, 1.25 * e_u) * su,
+            "tol_risk": max(1e-3, 1.25 * e_r) * sr}
 
 
 def _relerr(a, b):
@@ -242,7 +251,8 @@ def test_converged_fp32_vs_oracle(name, recentre):
     """FP32 iteration to ||v - T(v)||_inf <= 1e-4 against the optimum: the
     oracle's FP64 solve to 1e-7 (tests/golden/converged_cases.json, written by
     tests/golden/make_converged_cases.py from the oracle alone). Risk value and
-    u^0 within 1e-3 relative; FP64 residual check of the returned iterate.
+    u^0 within 1e-3 relative, or within 1.25 x the oracle's own 1e-4 point's
+    distance where that is larger; FP64 residual check of the returned iterate.
     recentre 0.1: the centred FP32 iteration (its stopping test is the FP64
     residual, so that is <= 1e-4); 0: the plain one."""
     p, o, g = _pair(name)
@@ -252,8 +262,8 @@ def test_converged_fp32_vs_oracle(name, recentre):
     assert res["status"] == 0, res["info"]
     if recentre > 0:
         assert res["info"]["res_inf_fp64"] <= 1e-4 and res["info"]["n_recentre"] >= 1
-    assert abs(res["risk"] - ref["risk"]) <= 1e-3 * max(1.0, abs(ref["risk"]))
-    assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= 1e-3 * max(1.0, np.max(np.abs(ref["u"][0])))
+    assert abs(res["risk"] - ref["risk"]) <= ref["tol_risk"]
+    assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= ref["tol_u"]
     assert res["info"]["res_inf_fp64"] < 5e-4
     assert np.all(np.abs(res["x"]) <= 5 + 1e-2)
 
@@ -339,11 +349,12 @@ def test_fixed_iterations_spock_qr_update_fp64(name):
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball"])
 def test_converged_fp32_qr_update(name):
     """FP32 SPOCK with the QR-updated Anderson memory to 1e-4: risk value and u^0
-    within 1e-3 of the optimum (the oracle's solve to 1e-7)."""
+    within the bounds of test_converged_fp32_vs_oracle of the optimum (the
+    oracle's solve to 1e-7)."""
     p, o, g = _pair(name)
     spock = _spock()
     ref = _converged_ref(name)
     res = g.solve(p.x0, spock.opts(precision=32, tol=1e-4, max_iters=20000, aa="qr_update"))
     assert res["status"] == 0, res["info"]
-    assert abs(res["risk"] - ref["risk"]) <= 1e-3 * max(1.0, abs(ref["risk"]))
-    assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= 1e-3 * max(1.0, np.max(np.abs(ref["u"][0])))
+    assert abs(res["risk"] - ref["risk"]) <= ref["tol_risk"]
+    assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= ref["tol_u"]
