@@ -315,7 +315,7 @@ PLAIN_SAMPLE = 16            # problems on which the plain FP64 method is timed
 MAX_ITERS = 20000
 TO_TOL_COUNT = 32            # problems of the to-1e-4 comparison
 TO_TOL_QUANTILE = 0.9        # ... drawn from this lower fraction of the draw by T bytes
-SERVE_T_BYTES = 4.0e6        # serving plants: problems whose T moves at most this (one CTA each)
+SERVE_T_BYTES = 1.0e6        # serving plants: problems whose T moves at most this (one CTA each)
 CONFIG5_SECONDS = 10.0       # arrivals at 2000 req/s (drained after), cut to keep the drain near a minute
 SWEEP_SECONDS = 4.0          # arrivals per point of the load sweep
 EXTRA_BUDGET_S = 420.0       # the sections after the headline stop starting after this much wall time
@@ -427,10 +427,22 @@ def bench_batched(spock, probs, G):
     return res
 
 
+def _drain(srv, timeout_s):
+    """Collect finished requests until none is outstanding or timeout_s has
+    passed; returns (results, still outstanding)."""
+    res, t0 = [], time.time()
+    while srv.outstanding() > 0 and time.time() - t0 < timeout_s:
+        res += srv.poll()
+        time.sleep(0.0002)
+    res += srv.poll()
+    return res, int(srv.outstanding())
+
+
 def _serve_stream(srv, probs, x, u, rng, rate, seconds, next_state, drain_s=120.0):
     """Poisson arrivals at `rate` for `seconds` (each request a warm-started
-    MPC step of a random plant); returns the collected results and the wall
-    time until the last one."""
+    MPC step of a random plant); returns the collected results, the number
+    submitted, the wall time until the last one and the requests still
+    outstanding after drain_s."""
     got, sub = [], 0
     t0 = time.time()
     t_next = t0
@@ -445,8 +457,9 @@ def _serve_stream(srv, probs, x, u, rng, rate, seconds, next_state, drain_s=120.
         for r in srv.poll():
             got.append(r)
             u[r["plant"]] = r["u0"]
-    got += srv.drain(drain_s)
-    return got, sub, time.time() - t0
+    rest, left = _drain(srv, drain_s)
+    got += rest
+    return got, sub, time.time() - t0, left
 
 
 def bench_serving(spock, probs, G, label, seed=5):
@@ -463,10 +476,15 @@ def bench_serving(spock, probs, G, label, seed=5):
     srv = spock.Server(G, precision=32, o=o32, ring_slots=8192)
     x = [p.x0.copy() for p in probs]
     u = [None] * len(probs)
+    t0 = time.time()
     for k, p in enumerate(probs):             # one cold solve per plant first
         srv.submit(k, x[k], warm=False)
-    for r in srv.drain(600):
+    cold, left = _drain(srv, 600)
+    for r in cold:
         u[r["plant"]] = r["u0"]
+    if left:
+        raise RuntimeError(f"{left} cold requests unfinished after 600 s")
+    cold_s = time.time() - t0
     rng = np.random.default_rng(seed)
 
     def next_state(k):
@@ -477,10 +495,11 @@ def bench_serving(spock, probs, G, label, seed=5):
         x1 = p.A[c - 1] @ x[k] + p.B[c - 1] @ u[k] + p.c[c - 1]
         return np.clip(x1 + 0.1 * rng.standard_normal(p.nx), -4.5, 4.5)
 
-    def summary(got, sub, wall, rate, seconds):
+    def summary(got, sub, wall, rate, seconds, left=0):
         lat = np.array([r["latency_ms"] for r in got]) if got else np.zeros(1)
         dev = np.array([r["device_ms"] for r in got]) if got else np.zeros(1)
         return {"offered_rate_per_s": rate, "arrival_seconds": seconds, "submitted": sub, "completed": len(got),
+                "unfinished_at_cutoff": left,
                 "converged": sum(1 for r in got if r["status"] == 0),
                 "maxiter": sum(1 for r in got if r["status"] == 1),
                 "solves_per_s": len(got) / wall,
@@ -494,18 +513,20 @@ def bench_serving(spock, probs, G, label, seed=5):
         for k in range(len(probs)):
             x[k] = next_state(k)
             srv.submit(k, x[k], warm=True)
-    burst = srv.drain(600)
+    burst, left = _drain(srv, 600)
     cap = len(burst) / (time.time() - t0)
     for r in burst:
         u[r["plant"]] = r["u0"]
-    out = {"plants": label, "capacity_solves_per_s": cap}
+    out = {"plants": label, "cold_solves_wall_s": cold_s, "capacity_solves_per_s": cap,
+           "capacity_burst_unfinished": left}
     secs = min(CONFIG5_SECONDS, max(1.0, 60.0 * cap / 2000.0))
-    got, sub, wall = _serve_stream(srv, probs, x, u, rng, 2000.0, secs, next_state)
-    out["offered_2000_per_s"] = summary(got, sub, wall, 2000.0, secs)
+    got, sub, wall, left = _serve_stream(srv, probs, x, u, rng, 2000.0, secs, next_state,
+                                         drain_s=max(120.0, 3.0 * 2000.0 * secs / max(cap, 1e-3)))
+    out["offered_2000_per_s"] = summary(got, sub, wall, 2000.0, secs, left)
     out["below_capacity"] = []
     for frac in (0.25, 0.5, 0.75):
-        got, sub, wall = _serve_stream(srv, probs, x, u, rng, frac * cap, SWEEP_SECONDS, next_state)
-        d = summary(got, sub, wall, frac * cap, SWEEP_SECONDS)
+        got, sub, wall, left = _serve_stream(srv, probs, x, u, rng, frac * cap, SWEEP_SECONDS, next_state)
+        d = summary(got, sub, wall, frac * cap, SWEEP_SECONDS, left)
         d["fraction_of_capacity"] = frac
         out["below_capacity"].append(d)
     srv.close()
@@ -670,7 +691,7 @@ def run_ours(args, rank, world, local_rank, dist):
                 def serving_fn():
                     ks = [k for k in range(len(bprobs)) if t_bytes_fp32(bG[k]) <= SERVE_T_BYTES]
                     label = (f"the {len(ks)} of the draw's {len(bprobs)} problems whose T moves at most "
-                             f"{SERVE_T_BYTES / 1e6:.0f} MB (the class the batched launch gives one CTA)")
+                             f"{SERVE_T_BYTES / 1e6:.0f} MB (one CTA each, as in the batched launch)")
                     return bench_serving(spock, [bprobs[k] for k in ks], [bG[k] for k in ks], label)
                 section("serving", serving_fn)
     line = {"metric": METRIC, "value": value * 1.0, "unit": "iter/s", "n_gpus": world,
@@ -682,6 +703,10 @@ def run_ours(args, rank, world, local_rank, dist):
                                      "10x drop of the residual), FP64 projections about the centre, FP64 factors, "
                                      "FP64 residual as the stopping test") if prec == 32 else "FP64",
                        "centres_per_solve": inf0["n_recentre"],
+                       "phase_us_per_iteration_kernel_T": dict(zip(
+                           ("prep_S2", "backward_sweep", "forward_sweep", "eta_update_and_reduction",
+                            "anderson_memory", "direction", "k2_backtracking"),
+                           [1000.0 * x / max(1, nT_kernel) for x in inf0["phase_ms"]])),
                        "step": "one cold-start SPOCK solve to ||v - T(v)||_inf <= 1e-4",
                        "time_to_tol_ms": total_ms / args.steps,
                        "iterations_per_solve": inf0["iters"], "T_evals_per_solve": inf0["n_T"],

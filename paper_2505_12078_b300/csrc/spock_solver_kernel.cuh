@@ -162,11 +162,13 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
       const T* eq = eta + P.e_q + (long long)(c - 1) * P.W + nx;
       if (P.full) {   // (F_R^c)' eta_R^c
         const T* F = P.FR + (size_t)(c - 1) * nu * nu + k;
+#pragma unroll 8
         for (int e = 0; e < nu; ++e) g = fma(ldr(F + (size_t)e * nu), ldc(eq + e), g);
       } else {
         g += ldr(P.rh + (long long)(c - 1) * nu + k) * ldc(eq + k);
       }
     }
+#pragma unroll 8
     for (int r = 0; r < P.n_g; ++r) g = fma(ldr(P.GgT + (size_t)(nx + k) * P.n_g + r), ldc(eg + r), g);
     s_in[k] = ldc(z + P.o_u + (long long)i * nu + k) - al * g;
   }
@@ -176,11 +178,13 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
       const T* eq = eta + P.e_q + (long long)(c - 1) * P.W;
       if (P.full) {   // (F_Q^c)' eta_Q^c
         const T* F = P.FQ + (size_t)(c - 1) * nx * nx + k;
+#pragma unroll 8
         for (int e = 0; e < nx; ++e) g = fma(ldr(F + (size_t)e * nx), ldc(eq + e), g);
       } else {
         g += ldr(P.qh + (long long)(c - 1) * nx + k) * ldc(eq + k);
       }
     }
+#pragma unroll 8
     for (int r = 0; r < P.n_g; ++r) g = fma(ldr(P.GgT + (size_t)k * P.n_g + r), ldc(eg + r), g);
     s_xb[k] = ldc(z + P.o_x + (long long)i * nx + k) - al * g;
   }
@@ -211,10 +215,12 @@ __device__ void prep_leaf(const Prob<T>& P, int lane, int j, const T* __restrict
     T g = P.nbx ? P.gN[k] * ldc(ecN + k) : T(0);
     if (P.full) {   // (F_N^j)' eta_QN^j
       const T* F = P.FN + (size_t)jj * nx * nx + k;
+#pragma unroll 8
       for (int e = 0; e < nx; ++e) g = fma(ldr(F + (size_t)e * nx), ldc(eqN + e), g);
     } else {
       g += ldr(P.qNh + (long long)jj * nx + k) * ldc(eqN + k);
     }
+#pragma unroll 8
     for (int r = 0; r < P.n_gN; ++r) g = fma(ldr(P.GgNT + (size_t)k * P.n_gN + r), ldc(ecN + P.nbx + r), g);
     const T xbar = ldc(z + P.o_x + (long long)j * nx + k) - al * g;
     stc(P.qbuf + (long long)j * nx + k, -xbar);
@@ -247,7 +253,31 @@ __device__ __forceinline__ void col_mv_np(const T* __restrict__ M, int ld, int n
   T a0[NP], a1[NP];
 #pragma unroll
   for (int m = 0; m < NP; ++m) { a0[m] = T(0); a1[m] = T(0); }
+  // blocks of RB rows: every load of a block is issued before its FMAs, so a
+  // matrix read from global memory (too large for the shared-memory pipe) has
+  // RB x NP loads in flight per thread instead of two. Even rows go to a0 and
+  // odd rows to a1 in order, as in the pairwise loop below.
+  constexpr int RB = 16;
   int k = 0;
+  for (; k + RB <= nrows; k += RB) {
+    T mv[RB][NP], xv[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      xv[r] = in[k + r];
+      const T* row = M + (size_t)(k + r) * ld + t;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) mv[r][m] = (t + m * nth < ncols) ? row[m * nth] : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < RB; r += 2)
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        if (t + m * nth < ncols) {
+          a0[m] = fma(mv[r][m], xv[r], a0[m]);
+          a1[m] = fma(mv[r + 1][m], xv[r + 1], a1[m]);
+        }
+      }
+  }
   for (; k + 1 < nrows; k += 2) {
     const T x0 = in[k], x1 = in[k + 1];
     const T* r0 = M + (size_t)k * ld + t;
@@ -729,6 +759,7 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     for (int r = lane; r < P.n_g; r += 32) {
       const T* G = P.Gg + (size_t)r * (nx + nu);
       T Lo = 0, Ln = 0, Ld = 0, Lrd = 0;
+#pragma unroll 8
       for (int k = 0; k < nx + nu; ++k) {
         const long long idx = (k < nx) ? xo + k : uo + (k - nx);
         const T g = ldr(G + k);
@@ -1057,6 +1088,7 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
     for (int r = lane; r < P.n_gN; r += 32) {
       const T* G = P.GgN + (size_t)r * nx;
       T Lo = 0, Ln = 0, Ld = 0, Lrd = 0;
+#pragma unroll 8
       for (int k = 0; k < nx; ++k) {
         const T g = ldr(G + k);
         const T o = ldc(z + xo + k), nn = ldc(vout + xo + k);

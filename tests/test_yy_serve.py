@@ -195,3 +195,33 @@ def test_serve_evict_then_admit_refused_plant():
     ref = _wait(srv2, 1)[q]
     srv2.close()
     assert np.array_equal(got["u0"], ref["u0"]) and got["risk"] == ref["risk"] and got["iters"] == ref["iters"]
+
+
+def test_warm_start_iteration_counts_match_oracle(plants):
+    """Why a warm-started MPC request of a tiny plant still takes hundreds to
+    thousands of iterations: the oracle needs as many from the same warm start.
+    The oracle solves the plant cold to 1e-4; its iterate (oracle -> GPU) warm
+    starts both the oracle and the GPU's FP64 solve for the next state x1 =
+    A x0 + B u0 + noise at the plant's most likely first-stage child. In FP64
+    both run the same algorithm from the same point: their iteration counts
+    agree to 10 % (rounding can move a SuperMann branch over thousands of
+    iterations)."""
+    import dataclasses
+    spock = _spock()
+    for k in (0, 2):
+        p, g = plants[k]
+        o = Oracle(p)
+        g.set_alpha(o.alpha)
+        r0 = o.solve(tol=1e-4, max_iters=20000)
+        ch = [c for c in range(1, len(p.anc)) if p.anc[c] == 0]
+        c = max(ch, key=lambda j: p.prob[j])
+        x1 = p.A[c - 1] @ p.x0 + p.B[c - 1] @ r0["u"][0] + p.c[c - 1]
+        x1 = np.clip(x1 + 0.1 * np.random.default_rng(5 + k).standard_normal(p.nx), -4.5, 4.5)
+        o1 = Oracle(dataclasses.replace(p, x0=x1))
+        rw = o1.solve(v0=r0["v"], tol=1e-4, max_iters=20000)
+        rc = o1.solve(tol=1e-4, max_iters=20000)
+        g.set_iterate(torch.tensor(r0["v"], device="cuda"))
+        res = g.solve(x1, spock.opts(precision=64, tol=1e-4, max_iters=20000, warm_start=True))
+        print(f"plant {k}: oracle warm {rw['iters']} (cold {rc['iters']}), GPU FP64 warm {res['info']['iters']}")
+        assert res["status"] == 0 and rw["iters"] > 0
+        assert abs(res["info"]["iters"] - rw["iters"]) <= 0.1 * rw["iters"] + 5
