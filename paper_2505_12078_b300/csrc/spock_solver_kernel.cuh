@@ -1659,10 +1659,29 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
         const int slot = head;
         const bool push = (k >= 1);
         double dd[NRED];
-        // the Gram matrix Y'Y and Y'r are accumulated in FP64 in every
-        // precision: their condition is the square of Y's
+        // the Gram matrix Y'Y and Y'r are accumulated to FP64 accuracy in
+        // every precision: their condition is the square of Y's
         double acc[2 * AA_M];
         for (int a = 0; a < 2 * AA_M; ++a) acc[a] = 0.0;
+        // FP32: the same sums in compensated single precision (the dot product
+        // of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005: the
+        // exact product p + ep by an FMA, the running sum hi + lo by an
+        // error-free two-sum), as accurate as an FP64 accumulation of the FP32
+        // products but on the FP32 pipe -- B300's FP64 pipe issues about 1/77
+        // of the FP32 rate
+        float chi[2 * AA_M], clo[2 * AA_M];
+        for (int a = 0; a < 2 * AA_M; ++a) { chi[a] = 0.0f; clo[a] = 0.0f; }
+        // (the _rn intrinsics keep the compiler from contracting the
+        // transformation's products and sums into FMAs)
+        auto dot2 = [&](int a, float x, float y) {
+          const float pr = __fmul_rn(x, y);
+          const float ep = fmaf(x, y, -pr);
+          const float sm = __fadd_rn(chi[a], pr);
+          const float bb = __fsub_rn(sm, chi[a]);
+          const float es = __fadd_rn(__fsub_rn(chi[a], __fsub_rn(sm, bb)), __fsub_rn(pr, bb));
+          chi[a] = sm;
+          clo[a] = __fadd_rn(clo[a], __fadd_rn(ep, es));
+        };
         T* Sslot = B.S + slot * ss;
         T* Yslot = B.Y + slot * ss;
         // one element: new pair (s, y), dots y.Y_l and Y_l.r, copies of v and r
@@ -1675,8 +1694,13 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
           const T yl[AA_M] = {slot == 0 ? y_ : y0, slot == 1 ? y_ : y1, slot == 2 ? y_ : y2};
 #pragma unroll
           for (int l = 0; l < AA_M; ++l) {
-            acc[l] = fma((double)y_, (double)yl[l], acc[l]);
-            acc[AA_M + l] = fma((double)yl[l], (double)r, acc[AA_M + l]);
+            if constexpr (sizeof(T) == 4) {
+              dot2(l, y_, yl[l]);
+              dot2(AA_M + l, yl[l], r);
+            } else {
+              acc[l] = fma((double)y_, (double)yl[l], acc[l]);
+              acc[AA_M + l] = fma((double)yl[l], (double)r, acc[AA_M + l]);
+            }
           }
         };
         for (long long q = gtid; q < nvec; q += gstride) {
@@ -1705,6 +1729,9 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
           }
           stc(B.VP + e, v);
           stc(B.RP + e, ro);
+        }
+        if constexpr (sizeof(T) == 4) {
+          for (int a = 0; a < 2 * AA_M; ++a) acc[a] = (double)chi[a] + (double)clo[a];
         }
         for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? acc[a] : 0.0;
         {
