@@ -31,6 +31,11 @@ first n_nl nodes are the non-leaf nodes, the last n_l the leaves.
         eta_y^i  = y^i, eta_s^i = s^i - b^i'y^i, eta_c^i = Gx x^i + Gu u^i,
         eta_q^c  = (Q^c^(1/2) x^anc, R^c^(1/2) u^anc, tau^c/2, tau^c/2),
         eta_cN^j = GN x^j, eta_qN^j = (QN^j^(1/2) x^j, s^j/2, s^j/2).
+  With an l1 term lambda_0 ||(x^anc, u^anc)||_1 in the edge costs (Prop. 2)
+  z ends with [ theta (n_nl) | lambda (n_nl*(nx+nu)) ] and eta with the rows
+  (theta^i - sum lambda^i/s, lambda^i - (x^i, u^i), lambda^i + (x^i, u^i)) per
+  non-leaf node, n_nl*(1 + 2(nx+nu)); the cost cone of every child c of i
+  carries (tau^c - lambda_0 theta^i)/2 in its last two entries.
   Constraint rows of a non-leaf node: [x box (nx)] [u box (nu)] [u ball (nu)]
   [general rows Gx x + Gu u (n_g)], each kind present or absent for the whole
   problem; leaf rows: [x box (nx)] [general rows GN x (n_gN)]. Q^(1/2) is the
@@ -237,6 +242,7 @@ class Oracle:
         self.n_c = (nx if self.has_xbox else 0) + (nu if self.has_ubox else 0) + \
                    (nu if self.has_uball else 0) + self.n_g
         self.n_cN = (nx if self.has_xbox else 0) + self.n_gN
+        self.l1 = float(getattr(prob, "l1", None) or 0.0)
         self._layout()
         self._precondition()
         self._offline_s1()
@@ -264,6 +270,15 @@ class Oracle:
         e_cN = e_q + (n - 1) * (nx + nu + 2)
         e_qN = e_cN + n_l * self.n_cN
         n_eta = e_qN + n_l * (nx + 2)
+        # l1 stage costs (Prop. 2): theta^i and lambda^i (nx + nu) per non-leaf
+        # node at the end of z; the rows theta - sum lambda, lambda - z,
+        # lambda + z (z = (x^i, u^i)) per non-leaf node at the end of eta
+        self.o_th = n_z
+        self.o_lam = n_z + (n_nl if self.l1 else 0)
+        self.e_l1 = n_eta
+        if self.l1:
+            n_z = self.o_lam + n_nl * (nx + nu)
+            n_eta = self.e_l1 + n_nl * (1 + 2 * (nx + nu))
         self.lay = Layout(n_y, n_z, n_eta, o_x, o_u, o_y, o_tau, o_s,
                           e_y, e_s, e_c, e_q, e_cN, e_qN)
         # entries of eta_y that lie in R_+ (all but the last entry of each block)
@@ -602,6 +617,30 @@ class Oracle:
             QNh = self.QNh[jj]
             add_block(base, lay.o_x + j * nx, np.diag(QNh) if QNh.ndim == 1 else QNh)
             add_block(base + nx, lay.o_s + j - 1, np.array([[0.5], [0.5]]))
+        if self.l1:
+            # Prop. 2 with the auxiliaries shared by the children of a node (the
+            # l1 term of the edge costs of node i's children is the same function
+            # of (x^i, u^i) for every child): tau^c - lambda_0 theta^i replaces
+            # tau^c in the cone of every child c, and theta^i >= sum_k lambda_k,
+            # -lambda_k <= z_k <= lambda_k on the unscaled z = (x^i, u^i). Here
+            # lambda is kept scaled like z (lambda~_k = s_k lambda_k), so the rows
+            # are theta - sum_k lambda~_k / s_k, lambda~ - z~, lambda~ + z~, all in R_+.
+            d = nx + nu
+            for c in range(1, n):
+                base = lay.e_q + (c - 1) * w
+                add_block(base + nx + nu, self.o_th + tr.anc[c], np.array([[-0.5 * self.l1], [-0.5 * self.l1]]))
+            for i in range(tr.n_nl):
+                sc = np.concatenate([self.Snode[i], self.Su])
+                r0 = self.e_l1 + i * (1 + 2 * d)
+                ol = self.o_lam + i * d
+                add_block(r0, self.o_th + i, np.ones((1, 1)))
+                add_block(r0, ol, -(1.0 / sc)[None, :])
+                add_block(r0 + 1, ol, np.eye(d))
+                add_block(r0 + 1, lay.o_x + i * nx, -np.eye(d)[:, :nx])
+                add_block(r0 + 1, lay.o_u + i * nu, -np.eye(d)[:, nx:])
+                add_block(r0 + 1 + d, ol, np.eye(d))
+                add_block(r0 + 1 + d, lay.o_x + i * nx, np.eye(d)[:, :nx])
+                add_block(r0 + 1 + d, lay.o_u + i * nu, np.eye(d)[:, nx:])
         rows = np.concatenate(rows); cols = np.concatenate(cols); vals = np.concatenate(vals)
         self.L = sp.csr_matrix((vals, (rows, cols)), shape=(lay.n_eta, lay.n_z))
         self.LT = self.L.T.tocsr()
@@ -631,20 +670,21 @@ class Oracle:
         u = z[lay.o_u:lay.o_y].reshape(tr.n_nl, self.nu)
         y = z[lay.o_y:lay.o_tau]
         tau = z[lay.o_tau:lay.o_s]
-        s = z[lay.o_s:]
+        s = z[lay.o_s:lay.o_s + tr.n - 1]
         return s0, x, u, y, tau, s
 
     @staticmethod
-    def join_z(s0, x, u, y, tau, s):
-        return np.concatenate([[s0], x.ravel(), u.ravel(), y, tau, s])
+    def join_z(s0, x, u, y, tau, s, aux=()):
+        return np.concatenate([[s0], x.ravel(), u.ravel(), y, tau, s, aux])
 
     def prox_f(self, w):
         """prox_{alpha f} with f(z) = s0 + delta_S1(z_1) + delta_S2(z_2)
-        (Eq. f): s0 - alpha, proj_S1 (Alg. 2), proj_S2."""
+        (Eq. f): s0 - alpha, proj_S1 (Alg. 2), proj_S2. The auxiliaries of the
+        l1 costs (Prop. 2) do not enter f: their prox is the identity."""
         s0, x, u, y, tau, s = self.split_z(w)
         x2, u2 = self.proj_S1(x, u)
         y2, tau2, s2 = self.proj_S2(y, tau, s)
-        return self.join_z(s0 - self.alpha, x2, u2, y2, tau2, s2)
+        return self.join_z(s0 - self.alpha, x2, u2, y2, tau2, s2, w[self.o_th:])
 
     def proj_S3(self, v):
         """Projection onto S3 (Eq. S3-def): (K^i)* = R^{2n_i}_+ x R, R_+, C^i per
@@ -673,8 +713,9 @@ class Oracle:
         if self.n_cN:
             CN = v[lay.e_cN:lay.e_qN].reshape(tr.n_l, self.n_cN)
             out[lay.e_cN:lay.e_qN] = np.clip(CN, self.boxN_lo, self.boxN_hi).ravel()
-        QN = v[lay.e_qN:].reshape(tr.n_l, nx + 2)
-        out[lay.e_qN:] = (self.a_qN + proj_soc(QN - self.a_qN)).ravel()
+        QN = v[lay.e_qN:self.e_l1].reshape(tr.n_l, nx + 2)
+        out[lay.e_qN:self.e_l1] = (self.a_qN + proj_soc(QN - self.a_qN)).ravel()
+        out[self.e_l1:] = np.maximum(v[self.e_l1:], 0.0)     # l1 rows (Prop. 2): R_+
         return out
 
     def prox_gconj(self, v):
@@ -929,9 +970,9 @@ class Oracle:
         if self.n_cN:
             CN = eta[lay.e_cN:lay.e_qN].reshape(tr.n_l, self.n_cN)
             val += float(np.sum(np.maximum(CN * self.boxN_lo, CN * self.boxN_hi)))
-        QN = eta[lay.e_qN:].reshape(tr.n_l, nx + 2)
+        QN = eta[lay.e_qN:self.e_l1].reshape(tr.n_l, nx + 2)
         val += float(np.sum(QN * self.a_qN))
-        return val
+        return val                 # the l1 rows are a cone: they contribute 0
 
     def nested_values(self, x, u):
         """Cost-to-go V^i of a trajectory under the nested risk (Eq.
@@ -968,8 +1009,9 @@ class Oracle:
         return w
 
     def edge_cost(self, c, x, u):
-        """l^c(x, u) = x'Q^c x + u'R^c u + q^c'x + r^c'u on the ancestor's state
-        and input (Sec. 3.2, quadratic-plus-linear costs), original data."""
+        """l^c(x, u) = x'Q^c x + u'R^c u + q^c'x + r^c'u (+ lambda_0 ||(x, u)||_1,
+        Prop. 2) on the ancestor's state and input (Sec. 3.2,
+        quadratic-plus-linear costs), original data."""
         P = self.P
         Qc = P.Q[c - 1] if np.ndim(P.Q) == 3 else np.diag(P.Q[c - 1])
         Rc = P.R[c - 1] if np.ndim(P.R) == 3 else np.diag(P.R[c - 1])
@@ -978,6 +1020,8 @@ class Oracle:
             val += P.q[c - 1] @ x
         if getattr(P, "r", None) is not None:
             val += P.r[c - 1] @ u
+        if self.l1:
+            val += self.l1 * (np.sum(np.abs(x)) + np.sum(np.abs(u)))
         return float(val)
 
     def terminal_cost(self, jj, x):

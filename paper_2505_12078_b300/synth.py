@@ -70,6 +70,8 @@ class RAOCP:
     GN: Optional[np.ndarray] = None     # float64 [n_gN, nx] general rows at every leaf:
     gN_lo: Optional[np.ndarray] = None  # float64 [n_leaf, n_gN]   gN_lo <= GN x <= gN_hi
     gN_hi: Optional[np.ndarray] = None
+    l1: Optional[float] = None          # lambda_0 >= 0 of an l1 term lambda_0 ||(x^anc, u^anc)||_1 added
+                                        # to every edge cost (Prop. 2); None or 0 = none
 
     @property
     def n(self) -> int:

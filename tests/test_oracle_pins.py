@@ -43,6 +43,7 @@ def test_sizes_match_hand_count():
             o.has_xbox, o.has_ubox, o.has_uball = True, True, p.u_ball is not None
             o.n_c = p.nx + p.nu + (p.nu if p.u_ball is not None else 0)
             o.n_cN = p.nx
+            o.l1 = 0.0
             o._layout()
             assert (o.lay.n_z, o.lay.n_eta) == (ref["n_z"], ref["n_eta"])
 
@@ -814,3 +815,136 @@ def test_spock_with_qr_update_follows_the_same_branches():
     assert [e[1] for e in a["events"]] == [e[1] for e in b["events"]]
     assert a["n_T"] == b["n_T"]
     assert np.max(np.abs(a["v"] - b["v"])) < 1e-9 * max(1.0, np.max(np.abs(a["v"])))
+
+
+# --- l1 stage costs (Prop. 2) ------------------------------------------------------------
+
+
+def _l1_problem(seed, avar=1.0, box=False, lam=0.3, ball=None):
+    p = general([2, 2, 1], 3, 2, seed=seed, avar=avar, box=box)
+    p.l1 = lam
+    if ball is not None:
+        p.u_ball = np.full(p.n_nonleaf, ball)
+    return p
+
+
+def test_l1_rows_encode_prop2_epigraph():
+    """Prop. 2: (z, tau) lies in the epigraph of z'Qz + q'z + lambda_0 ||z||_1
+    exactly when some theta, lambda with sum lambda <= theta and
+    -lambda <= z <= lambda put (z, tau - lambda_0 theta) in the epigraph of the
+    quadratic part. With theta = ||z||_1 and lambda = |z| (the smallest
+    choice), the rows L gives the child's cost cone and the parent's l1 block
+    lie in S3 exactly when the full cost is at most tau; with theta below
+    ||z||_1 no lambda satisfies the l1 rows."""
+    p = _l1_problem(61)
+    o = Oracle(p)
+    tr, lay = o.tree, o.lay
+    nx, nu, d = o.nx, o.nu, o.nx + o.nu
+    rng = np.random.default_rng(3)
+    i = 1
+    c = tr.children[i][0]
+    sc = np.concatenate([o.Snode[i], o.Su])
+    for trial in range(40):
+        x = rng.standard_normal(nx)
+        u = rng.standard_normal(nu)
+        cost = o.edge_cost(c, x, u)
+        tau = cost + rng.uniform(-0.5, 0.5)
+        z = np.zeros(lay.n_z)
+        z[lay.o_x + i * nx:lay.o_x + (i + 1) * nx] = o.Snode[i] * x
+        z[lay.o_u + i * nu:lay.o_u + (i + 1) * nu] = o.Su * u
+        z[lay.o_tau + c - 1] = tau
+        zu = np.concatenate([x, u])
+        z[o.o_th + i] = np.sum(np.abs(zu))
+        z[o.o_lam + i * d:o.o_lam + (i + 1) * d] = sc * np.abs(zu)
+        Lz = o.apply_L(z)
+        P3 = o.proj_S3(Lz)
+        w = nx + nu + 2
+        cone = slice(lay.e_q + (c - 1) * w, lay.e_q + c * w)
+        rows = slice(o.e_l1 + i * (1 + 2 * d), o.e_l1 + (i + 1) * (1 + 2 * d))
+        inside = np.allclose(P3[cone], Lz[cone], atol=1e-12) and np.allclose(P3[rows], Lz[rows], atol=1e-12)
+        assert inside == (cost <= tau), (trial, cost, tau)
+        # theta below ||z||_1: the first l1 row is negative for the smallest lambda
+        z[o.o_th + i] = 0.9 * np.sum(np.abs(zu))
+        assert o.apply_L(z)[o.e_l1 + i * (1 + 2 * d)] < 0
+
+
+def _risk_neutral_l1_qp(p):
+    """min sum_c pi^c l^c + sum_j pi^j l_N^j with l^c = x'Qx + u'Ru + q'x + r'u
+    + lambda_0 ||(x, u)||_1 on the ancestor's (x, u), s.t. the dynamics and
+    x^0 = x0: the l1 term of node i's children weighs pi^i; written with
+    t^i >= |(x^i, u^i)| as a QP in (u, t) after eliminating the dynamics and
+    solved by the interior-point method above. Returns (value, x, u)."""
+    tr = so_.Tree(p.anc, p.prob)
+    nx, nu, n = p.nx, p.nu, tr.n
+    nX = n * nx + tr.n_nl * nu
+    H = np.zeros((nX, nX))
+    f = np.zeros(nX)
+    full = lambda W, k: W[k] if np.ndim(W) == 3 else np.diag(W[k])   # noqa: E731
+    for c in range(1, n):
+        a = tr.anc[c]
+        H[a * nx:(a + 1) * nx, a * nx:(a + 1) * nx] += tr.pi[c] * full(p.Q, c - 1)
+        o = n * nx + a * nu
+        H[o:o + nu, o:o + nu] += tr.pi[c] * full(p.R, c - 1)
+        if p.q is not None:
+            f[a * nx:(a + 1) * nx] += tr.pi[c] * p.q[c - 1]
+        if p.r is not None:
+            f[o:o + nu] += tr.pi[c] * p.r[c - 1]
+    for jj in range(tr.n_l):
+        j = tr.n_nl + jj
+        H[j * nx:(j + 1) * nx, j * nx:(j + 1) * nx] += tr.pi[j] * full(p.QN, jj)
+        if p.qN is not None:
+            f[j * nx:(j + 1) * nx] += tr.pi[j] * p.qN[jj]
+    nU = tr.n_nl * nu
+    Pm = np.zeros((nX, nU)); p0 = np.zeros(nX)
+    Pm[n * nx:, :] = np.eye(nU)
+    p0[:nx] = p.x0
+    for c in range(1, n):
+        a = tr.anc[c]
+        Pm[c * nx:(c + 1) * nx] = p.A[c - 1] @ Pm[a * nx:(a + 1) * nx]
+        Pm[c * nx:(c + 1) * nx, a * nu:(a + 1) * nu] += p.B[c - 1]
+        p0[c * nx:(c + 1) * nx] = p.A[c - 1] @ p0[a * nx:(a + 1) * nx] + p.c[c - 1]
+    d = nx + nu
+    nT = tr.n_nl * d
+    Sel = np.zeros((nT, nX))                    # z^i = (x^i, u^i) for every non-leaf node
+    wt = np.zeros(nT)
+    for i in range(tr.n_nl):
+        Sel[i * d:i * d + nx, i * nx:(i + 1) * nx] = np.eye(nx)
+        Sel[i * d + nx:(i + 1) * d, n * nx + i * nu:n * nx + (i + 1) * nu] = np.eye(nu)
+        wt[i * d:(i + 1) * d] = p.l1 * tr.pi[i]
+    Hw = np.zeros((nU + nT, nU + nT))
+    Hw[:nU, :nU] = 2 * Pm.T @ H @ Pm
+    fw = np.concatenate([Pm.T @ (2 * H @ p0 + f), wt])
+    Zu = Sel @ Pm
+    G = np.vstack([np.hstack([Zu, -np.eye(nT)]), np.hstack([-Zu, -np.eye(nT)])])
+    h = np.concatenate([-Sel @ p0, Sel @ p0])
+    wsol = _qp_interior_point(Hw, fw, G, h)
+    X = Pm @ wsol[:nU] + p0
+    val = float(X @ H @ X + f @ X + wt @ np.abs(Sel @ X))
+    return val, X[:n * nx].reshape(n, nx), X[n * nx:].reshape(tr.n_nl, nu)
+
+
+def test_risk_neutral_l1_costs_vs_qp():
+    """AV@R_1, no constraints, full weights, linear terms and an l1 term
+    lambda_0 ||(x, u)||_1 in every edge cost (Prop. 2): the oracle's SPOCK
+    solution equals the QP with t >= |(x, u)| (value; trajectory on the likely
+    nodes); the l1 term is strong enough that some inputs sit at zero."""
+    p = _l1_problem(62, lam=0.8)
+    o = Oracle(p)
+    r = o.solve(tol=1e-9, max_iters=40000)
+    V, X, U = _risk_neutral_l1_qp(p)
+    assert abs(r["risk"] - V) < 1e-6 * max(1.0, abs(V))
+    _check_on_likely_nodes(o, r, X, U, 1e-4)
+    assert np.any(np.abs(U) < 1e-6)
+
+
+def test_l1_problem_diagnostics_vanish():
+    """AV@R 0.5 with boxes, a ball, full weights, linear terms and l1 costs: the
+    residual, xi1, xi2, infeasibility and the complementarity gap vanish, and
+    s0 equals the nested risk of the trajectory with the l1 costs."""
+    p = _l1_problem(63, avar=0.5, box=True, lam=0.4, ball=1.5)
+    o = Oracle(p)
+    r = o.solve(tol=1e-8, max_iters=40000)
+    assert r["res_inf"] <= 1e-8
+    assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
+    assert r["infeas"] < 1e-6 and r["gap"] < 1e-5
+    assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * max(1.0, abs(r["risk"]))
