@@ -191,8 +191,10 @@ int spock_op_T_centred(spock_problem* p, const double* c, const float* delta, fl
  * real-time loop where an allocation could block, or in a process whose
  * device memory is fully reserved by another framework. It calls no
  * cudaMalloc/cudaFree: all of its scratch (control block, barrier flags,
- * reduction partials and the sweep vectors, about 2 (n nx + n_nl nu) words
- * plus 160 KB) comes from one static device array of
+ * reduction partials, the sweep vectors and, when nx + nu <= 128, the sweep
+ * mailboxes: 2 (n nx + n_nl nu) values, 2 n (nx + nu) mailbox entries of
+ * 8 bytes (FP32) or 16 bytes (FP64), plus about 160 KB) comes from one
+ * static device array of
  * SPOCK_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
  * until the process exits. Problems needing more return SPOCK_EUNSUPPORTED.
  * The first call on a device looks the array's address up on that device

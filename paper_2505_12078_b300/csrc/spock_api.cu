@@ -230,6 +230,7 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.gen_lo = it.gen_lo; P.gen_hi = it.gen_hi; P.genN_lo = it.genN_lo; P.genN_hi = it.genN_hi;
   P.alpha = (T)alpha;
   P.qbuf = it.qbuf; P.dbuf = it.dbuf; P.hbuf = it.hbuf; P.ebuf = it.ebuf;
+  P.mbb = it.mbb; P.mbf = it.mbf;
 }
 
 // Whole-CTA sweep layout (nx + nu <= 128): a column of a transposed factor is
@@ -326,6 +327,9 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
     it.MBt = m.alloc<T>((long long)(n - 1) * (nx + nu) * it.ldTB);
     it.MFt = m.alloc<T>((long long)(n - 1) * nx * it.ldTF);
     it.KTt = m.alloc<T>((long long)n_nl * nu * it.ldTK);
+    it.mb_bytes = mailbox_bytes(n, nx + nu, sizeof(T));
+    it.mbb = m.alloc<unsigned long long>((long long)(it.mb_bytes / 8));
+    it.mbf = m.alloc<unsigned long long>((long long)(it.mb_bytes / 8));
   }
   return m.failed ? SPOCK_ENOMEM : SPOCK_OK;
 }
@@ -421,6 +425,9 @@ int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so_in, cudaStream
   if (cudaMemsetAsync(it.sb.flags, 0, sizeof(unsigned) * (it.P.seg_flag_off + p->seg_top.size()), st) !=
       cudaSuccess)
     return SPOCK_EDEVICE;
+  if (it.mbb && (cudaMemsetAsync(it.mbb, 0, it.mb_bytes, st) != cudaSuccess ||
+                 cudaMemsetAsync(it.mbf, 0, it.mb_bytes, st) != cudaSuccess))
+    return SPOCK_EDEVICE;
   cudaEventRecord(p->ev0, st);
   cudaError_t e = launch_solve<T>(it.P, it.sb, so, p->tw, grid, kThreads, st);
   if (e != cudaSuccess) return SPOCK_EDEVICE;
@@ -468,12 +475,15 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
   const size_t o_d = off;     off += al((size_t)p->n_nl * p->nu * w);
   const size_t o_h = off;     off += al((size_t)p->n_nl * p->nx * w);
   const size_t o_e = off;     off += al((size_t)p->n_nl * p->nu * w);
+  const size_t mbx = mailbox_bytes(p->n, p->nx + p->nu, w);
+  const size_t o_mb = off;    off += al(2 * mbx);   // sweep mailboxes (zeroed below)
   if (off > bytes) return SPOCK_EUNSUPPORTED;
   SolveCtl* ctl = reinterpret_cast<SolveCtl*>(scratch + o_ctl);
   unsigned* flags = reinterpret_cast<unsigned*>(scratch + o_flags);
   // what must start at zero: the control block (barrier state, error word) and the flags
   if (cudaMemsetAsync(ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return SPOCK_EDEVICE;
   if (cudaMemsetAsync(flags, 0, nflags * sizeof(unsigned), st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (cudaMemsetAsync(scratch + o_mb, 0, 2 * mbx, st) != cudaSuccess) return SPOCK_EDEVICE;
   SolveOpts so{1e300, 0, 1, 2, 1e-10};
   const int teams = (kThreads / 32) / p->tw;
   cudaError_t e;
@@ -484,6 +494,8 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
     P.dbuf = reinterpret_cast<double*>(scratch + o_d);
     P.hbuf = reinterpret_cast<double*>(scratch + o_h);
     P.ebuf = reinterpret_cast<double*>(scratch + o_e);
+    P.mbb = reinterpret_cast<unsigned long long*>(scratch + o_mb);
+    P.mbf = reinterpret_cast<unsigned long long*>(scratch + o_mb + mbx);
     P.pipe_bytes = p->use_pipe ? pipe_bytes_for<double>(p) : 0;
     if (solver_max_grid(64, p->tw, kThreads, p->nx + p->nu, P.pipe_bytes, cta_smem_bytes(P), &maxgrid) ||
         maxgrid <= 0)
@@ -500,6 +512,8 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
     P.dbuf = reinterpret_cast<float*>(scratch + o_d);
     P.hbuf = reinterpret_cast<float*>(scratch + o_h);
     P.ebuf = reinterpret_cast<float*>(scratch + o_e);
+    P.mbb = reinterpret_cast<unsigned long long*>(scratch + o_mb);
+    P.mbf = reinterpret_cast<unsigned long long*>(scratch + o_mb + mbx);
     P.pipe_bytes = p->use_pipe ? pipe_bytes_for<float>(p) : 0;
     if (solver_max_grid(32, p->tw, kThreads, p->nx + p->nu, P.pipe_bytes, cta_smem_bytes(P), &maxgrid) ||
         maxgrid <= 0)

@@ -6,7 +6,8 @@
 // factors are stored output-column-major (MBt, MFt, KTt), so each thread
 // reads its rows with 16-byte shared loads, and the two halves are combined
 // by one shuffle. An "item" is one factor matrix (backward: MB of a child;
-// forward: [KT of the node (first child only) | MF of the child]); items
+// forward: [KT of the node | MF of the child], either part alone where the
+// other has no output; see "item issue" below for the item lists); items
 // stream through a ring of nbuf shared buffers by cp.async.bulk, up to
 // nbuf - 1 items ahead of the one in use. Each item ends with one CTA barrier,
 // which both publishes the carry vector written in its epilogue and frees the
@@ -230,34 +231,18 @@ struct CtaState {
   CtaMem mem;
   const Sched* sched;
   int* s_ok;
-  unsigned* seg_flags;   // per segment: 2e when its backward sweep of evaluation e is
-                         // done, 2e + 1 when its forward sweep is (zeroed at launch)
-  unsigned epoch;        // evaluations of T so far in this launch
+  unsigned* seg_flags;   // per-segment flags (zeroed at launch; the sweeps hand over
+                         // through the tagged mailboxes instead)
+  unsigned epoch;        // evaluations of T so far in this launch; the sweep tags
+                         // are 2 epoch (backward) and 2 epoch + 1 (forward)
 };
 
 // Dataflow between the sweeps' levels: a segment's backward sweep waits for
-// the segments headed by its bottom's children, its forward sweep for the
-// segment that ends in its top's parent; both publish a flag when done. The
-// waits point to deeper (backward) or higher (forward) levels, which every CTA
-// sweeps first, so they cannot form a cycle. Thread 0 waits (bounded).
-__device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned e, int* err) {
-  uint64_t t0 = 0;
-  unsigned spins = 0;
-  while (ld_acquire(f) < e) {
-    __nanosleep(32);
-    if ((++spins & 63u) == 0u) {
-      if (ld_relaxed_i(err)) return false;
-      const uint64_t t = global_ns();
-      if (t0 == 0) {
-        t0 = t;
-      } else if (t - t0 > BARRIER_LIMIT_NS) {
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-  return true;
-}
+// the shares of the segments headed by its bottom's children, its forward
+// sweep for the [x; d] of the segment that ends in its top's parent, both
+// through tagged mailboxes (below). The waits point to deeper (backward) or
+// higher (forward) levels, which every CTA sweeps first, so they cannot form
+// a cycle. Every wait is bounded.
 // after a failed wait: let the copies already issued into the ring land
 // (bounded) before the CTA leaves
 __device__ __forceinline__ void ring_settle(Ring& R, int issued) {
@@ -273,6 +258,76 @@ __device__ __forceinline__ void ring_settle(Ring& R, int issued) {
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Mailboxes between the CTAs of the sweeps. Every 32-bit piece of a value goes
+// into one 64-bit word beside a 32-bit tag (the sweep epoch of the current
+// evaluation: 2e backward, 2e + 1 forward; the mailboxes are zeroed before a
+// launch and e >= 1, so no stale word carries a current tag). A 64-bit word
+// is written and read in one access, so a reader that sees the tag also sees
+// the value: the hand-over between segments needs neither a fence nor a
+// separate flag, and costs one round trip to L2 once the value has landed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mb_st64(unsigned long long* p, unsigned tag, unsigned bits) {
+  const unsigned long long v = ((unsigned long long)tag << 32) | (unsigned long long)bits;
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long mb_ld64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+template <class T>
+struct MB;
+template <>
+struct MB<float> {
+  static constexpr int WPV = 1;   // words per value
+  static __device__ __forceinline__ void put(unsigned long long* p, float v, unsigned tag) {
+    mb_st64(p, tag, __float_as_uint(v));
+  }
+  static __device__ __forceinline__ bool get(const unsigned long long* p, unsigned tag, float& v) {
+    const unsigned long long w = mb_ld64(p);
+    if ((unsigned)(w >> 32) != tag) return false;
+    v = __uint_as_float((unsigned)w);
+    return true;
+  }
+};
+template <>
+struct MB<double> {
+  static constexpr int WPV = 2;
+  static __device__ __forceinline__ void put(unsigned long long* p, double v, unsigned tag) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    mb_st64(p, tag, (unsigned)b);
+    mb_st64(p + 1, tag, (unsigned)(b >> 32));
+  }
+  static __device__ __forceinline__ bool get(const unsigned long long* p, unsigned tag, double& v) {
+    const unsigned long long lo = mb_ld64(p), hi = mb_ld64(p + 1);
+    if ((unsigned)(lo >> 32) != tag || (unsigned)(hi >> 32) != tag) return false;
+    v = __longlong_as_double((long long)((hi << 32) | (lo & 0xffffffffull)));
+    return true;
+  }
+};
+// wait (bounded, as the barriers) until the word(s) at p carry tag; false on
+// a timeout or when the launch is already failing
+template <class T>
+__device__ __forceinline__ bool mb_wait(const unsigned long long* p, unsigned tag, T& v, int* err) {
+  uint64_t t0 = 0;
+  unsigned spins = 0;
+  while (!MB<T>::get(p, tag, v)) {
+    if (++spins > 32u) __nanosleep(32);
+    if ((spins & 31u) == 0u) {
+      if (ld_relaxed_i(err)) return false;
+      const uint64_t t = global_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > BARRIER_LIMIT_NS) {
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 // dynamic shared memory of the whole-CTA sweeps: the ring, two carry vectors
 // and the child inputs
 template <class T>
@@ -283,11 +338,45 @@ __host__ __device__ inline size_t cta_smem_bytes(const Prob<T>& P) {
 
 // ---------------------------------------------------------------------------
 // item issue (by one thread)
+//
+// The items of a segment. A node's children that head segments of their own
+// (its non-leaf children) are not items of the node's segment: in the
+// backward sweep every segment ends with an uplink item that forms its top's
+// share of the parent's step, MB_top' v_top, and the parent adds these shares;
+// in the forward sweep every segment starts with a downlink item that forms
+// its top's state from the parent's [x; d]. The children of a branching node
+// therefore run their items on their own CTAs at the same time, and the
+// parent's segment has no per-child item left on the critical path.
+//   backward: the bottom's leaf children (inputs from phase P), one item per
+//             step up the chain, then the uplink (not for the root);
+//   forward:  the downlink (not for the root), one item per step down the
+//             chain ([KT_i | MF_child]), then the bottom's leaf children
+//             ([KT | MF] for the first, MF for the rest), or KT alone when the
+//             bottom has no leaf child.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ __forceinline__ int b_child(const SegRef& g, int j) {
-  const int nb = g.c1 - g.c0;
-  return j < nb ? g.c0 + j : g.nodes[g.len - 1 - (j - nb)];
+__device__ __forceinline__ int seg_leaf0(const Prob<T>& P, const SegRef& g) {   // first leaf child of the bottom
+  return max(g.c0, P.n_nl);
+}
+template <class T>
+__device__ __forceinline__ int seg_nleaf(const Prob<T>& P, const SegRef& g) {   // leaf children of the bottom
+  return max(0, g.c1 - max(g.c0, P.n_nl));
+}
+template <class T>
+__device__ __forceinline__ int b_items(const Prob<T>& P, const SegRef& g) {
+  return seg_nleaf(P, g) + g.len - 1 + (g.nodes[0] != 0 ? 1 : 0);
+}
+template <class T>
+__device__ __forceinline__ int f_items(const Prob<T>& P, const SegRef& g) {
+  return (g.nodes[0] != 0 ? 1 : 0) + g.len - 1 + max(1, seg_nleaf(P, g));
+}
+// the child whose MB the backward item j uses
+template <class T>
+__device__ __forceinline__ int b_child(const Prob<T>& P, const SegRef& g, int j) {
+  const int nbl = seg_nleaf(P, g);
+  if (j < nbl) return seg_leaf0(P, g) + j;
+  j -= nbl;
+  return (j < g.len - 1) ? g.nodes[g.len - 1 - j] : g.nodes[0];
 }
 // what the issuing thread needs, read from the problem once per segment
 template <class T>
@@ -299,18 +388,30 @@ struct BIssue {
       : base(P.MBt), stride((size_t)(P.nx + P.nu) * P.ldTB), bytes((unsigned)((P.nx + P.nu) * P.ldTB * (int)sizeof(T))) {}
 };
 template <class T>
-__device__ __forceinline__ void b_issue(const BIssue<T>& I, const Ring& R, const SegRef& g, int j, int b) {
-  const int c = b_child<T>(g, j);
+__device__ __forceinline__ void b_issue(const Prob<T>& P, const BIssue<T>& I, const Ring& R, const SegRef& g, int j,
+                                        int b) {
+  const int c = b_child(P, g, j);
   ring_arm(R.bar(b), I.bytes);
   ring_copy(R.buf(b), I.base + (size_t)(c - 1) * I.stride, I.bytes, R.bar(b));
 }
-// forward item j: (node, child, with KT)
-__device__ __forceinline__ void f_item(const SegRef& g, int j, int& node, int& child, bool& kt) {
+// forward item j: the node whose [x; d] is the input, the child whose x is an
+// output (-1: none), and whether the node's u (KT) is an output
+template <class T>
+__device__ __forceinline__ void f_item(const Prob<T>& P, const SegRef& g, int j, int& node, int& child, bool& kt) {
+  const int top = g.nodes[0];
+  if (top != 0) {
+    if (j == 0) { node = -1; child = top; kt = false; return; }   // downlink (node: the parent)
+    --j;
+  }
   if (j < g.len - 1) {
     node = g.nodes[j]; child = g.nodes[j + 1]; kt = true;
-  } else {
-    node = g.nodes[g.len - 1]; child = g.c0 + (j - (g.len - 1)); kt = (j == g.len - 1);
+    return;
   }
+  j -= g.len - 1;
+  node = g.nodes[g.len - 1];
+  const int nbl = seg_nleaf(P, g);
+  child = (nbl > 0) ? seg_leaf0(P, g) + j : -1;
+  kt = (j == 0);
 }
 template <class T>
 struct FIssue {
@@ -322,27 +423,29 @@ struct FIssue {
       : kt(P.KTt), mf(P.MFt), ks((size_t)P.nu * P.ldTK), fs((size_t)P.nx * P.ldTF),
         kb((unsigned)(P.nu * P.ldTK * (int)sizeof(T))), fb((unsigned)(P.nx * P.ldTF * (int)sizeof(T))) {}
 };
+// the buffer holds [KT part | MF part], the MF part at byte offset kb
 template <class T>
-__device__ __forceinline__ void f_issue(const FIssue<T>& I, const Ring& R, const SegRef& g, int j, int b) {
+__device__ __forceinline__ void f_issue(const Prob<T>& P, const FIssue<T>& I, const Ring& R, const SegRef& g, int j,
+                                        int b) {
   int node, child;
   bool kt;
-  f_item(g, j, node, child, kt);
-  ring_arm(R.bar(b), (kt ? I.kb : 0u) + I.fb);
+  f_item(P, g, j, node, child, kt);
+  ring_arm(R.bar(b), (kt ? I.kb : 0u) + (child >= 0 ? I.fb : 0u));
   if (kt) ring_copy(R.buf(b), I.kt + (size_t)node * I.ks, I.kb, R.bar(b));
-  ring_copy(R.buf(b) + I.kb, I.mf + (size_t)(child - 1) * I.fs, I.fb, R.bar(b));
+  if (child >= 0) ring_copy(R.buf(b) + I.kb, I.mf + (size_t)(child - 1) * I.fs, I.fb, R.bar(b));
 }
 // first items of the next segment (backward or forward), issued ahead of its call
 template <class T>
 __device__ __forceinline__ void ring_prefetch(const Prob<T>& P, Ring& R, const SegRef& g, bool fwd) {
-  const int nitems = (g.c1 - g.c0) + g.len - 1;
+  const int nitems = fwd ? f_items(P, g) : b_items(P, g);
   const int k = min(R.nbuf - 1, nitems);
   if (threadIdx.x == blockDim.x - 1) {
     if (fwd) {
       const FIssue<T> I(P);
-      for (int j = 0; j < k; ++j) f_issue(I, R, g, j, R.step(R.head, j));
+      for (int j = 0; j < k; ++j) f_issue(P, I, R, g, j, R.step(R.head, j));
     } else {
       const BIssue<T> I(P);
-      for (int j = 0; j < k; ++j) b_issue(I, R, g, j, R.step(R.head, j));
+      for (int j = 0; j < k; ++j) b_issue(P, I, R, g, j, R.step(R.head, j));
     }
   }
   R.ahead = k;
@@ -352,7 +455,10 @@ __device__ __forceinline__ void ring_prefetch(const Prob<T>& P, Ring& R, const S
 // backward sweep of one segment:
 //   v_c = q_c + P_c c_c (q_c holds it, see phase P);  q^i = sum_c Abar_c' v_c + h^i;
 //   d^i = e^i - sum_c (B_c Rt_i^{-1})' v_c
-// items: the children of the bottom node, then one per step up the chain
+// items: the bottom's leaf children, one per step up the chain, then the
+// uplink (the top's share MB_top' v_top of its parent's step, into the
+// mailbox mbb); the shares of the bottom's non-leaf children come from their
+// segments' uplinks
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err, const SegRef& g,
@@ -362,6 +468,7 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   const int nx = P.nx, nu = P.nu, w = nx + nu;
   const int t = threadIdx.x, col = t >> 1, half = t & 1;
   const bool has_col = col < w;
+  const bool owner = has_col && !half;   // writes the column's result
   const bool issuer = (t == (int)blockDim.x - 1);
   const int r0 = half ? P.khB : 0;
   const int r1 = half ? nx : min(P.khB, nx);
@@ -375,91 +482,108 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   const T* __restrict__ ebuf = P.ebuf;
   Ring R = ring;
   const BIssue<T> I(P);
-  const int len = g.len, nb = g.c1 - g.c0, QS = P.qslots;
-  const int nitems = nb + len - 1;
+  const int len = g.len, QS = P.qslots, top = g.nodes[0];
+  const int nbl = seg_nleaf(P, g), leaf0 = seg_leaf0(P, g);
+  const int nbn = max(0, min(g.c1, P.n_nl) - g.c0);   // non-leaf children: shares from their uplinks
+  const int nchain = len - 1;
+  const int nitems = nbl + nchain + (top != 0 ? 1 : 0);
   const bool probe = SPOCK_PROBE_ON && prof && blockIdx.x == 0 && t == 0;
   long long tc = probe ? clock64() : 0, c_mv = 0, c_hand = 0;
   // the items not issued ahead, up to nbuf - 1 in flight
   if (issuer)
-    for (int j = R.ahead; j < min(R.nbuf - 1, nitems); ++j) b_issue(I, R, g, j, R.step(R.head, j));
+    for (int j = R.ahead; j < min(R.nbuf - 1, nitems); ++j) b_issue(P, I, R, g, j, R.step(R.head, j));
   R.ahead = 0;
-  // the children that head other segments must be swept
-  if (t == 0) {
-    bool okw = true;
-    for (int c = g.c0; c < g.c1 && okw; ++c) {
-      const int ts = P.top_seg[c];
-      if (ts >= 0) okw = flag_wait(flags + ts, eB, err);
-    }
-    *s_ok = okw ? 1 : 0;
-  }
+  if (t == 0) *s_ok = 1;
   __syncthreads();
-  if (!*s_ok) {
-    ring_settle(R, min(R.nbuf - 1, nitems));
-    ring = R;
-    return false;
-  }
-  // h/e of the output node of the next two epilogues
+  // h/e of the output nodes (bottom first, then up the chain), two ahead
   auto pre_of = [&](int node) -> T {
-    if (!has_col || half) return T(0);
+    if (!owner) return T(0);
     return (col < nx) ? ldc(hbuf + (long long)node * nx + col) : ldc(ebuf + (long long)node * nu + (col - nx));
   };
   T preA = pre_of(g.nodes[len - 1]);
   T preB = (len >= 2) ? pre_of(g.nodes[len - 2]) : T(0);
-  // inputs of the bottom's first children
+  // the shares of the bottom's non-leaf children, from their segments'
+  // uplinks (mailbox mbb), summed in child order
+  T share = T(0);
+  if (owner) {
+    for (int c = g.c0; c < g.c0 + nbn; ++c) {
+      T sv;
+      if (!mb_wait<T>(P.mbb + ((long long)c * w + col) * MB<T>::WPV, eB, sv, err)) {
+        *s_ok = 0;
+        break;
+      }
+      share += sv;
+    }
+  }
+  // inputs of the bottom's first leaf children
   auto load_children = [&](int j0) {
-    const int m = min(QS, nb - j0);
+    const int m = min(QS, nbl - j0);
     for (int e = t; e < m * nx; e += blockDim.x) {
       const int j = e / nx, k = e - j * nx;
-      st_s<T>(cm.qin + (unsigned)j * ldcb + (unsigned)k * ES, ldc(qbuf + (long long)(g.c0 + j0 + j) * nx + k));
+      st_s<T>(cm.qin + (unsigned)j * ldcb + (unsigned)k * ES, ldc(qbuf + (long long)(leaf0 + j0 + j) * nx + k));
     }
   };
-  load_children(0);
-  if (t == 0) *s_ok = 1;
+  if (nbl > 0) load_children(0);
+  unsigned cin = cm.carry0, cout = cm.carry1;
+  int nout = 0;   // output nodes done (bottom = 0, then up the chain)
+  auto epilogue = [&](T s) {
+    const int i = g.nodes[len - 1 - nout];
+    if (owner) {
+      if (col < nx) {
+        const T qq = s + preA;
+        st_s<T>(cout + (unsigned)col * ES, qq);
+        stc(qbuf + (long long)i * nx + col, qq);
+      } else {
+        stc(dbuf + (long long)i * nu + (col - nx), preA - s);
+      }
+    }
+    ++nout;
+    preA = preB;
+    preB = (len - 2 - nout >= 0) ? pre_of(g.nodes[len - 2 - nout]) : T(0);
+    const unsigned tt = cin; cin = cout; cout = tt;
+  };
+  if (nbl == 0) epilogue(share);   // the bottom's step is its children's shares alone
   int b = R.head;
-  ring_wait0(R, b, err, 3, s_ok);
+  if (nitems > 0) ring_wait0(R, b, err, 3, s_ok);
   __syncthreads();
   bool ok = *s_ok != 0;
-  unsigned cin = cm.carry0, cout = cm.carry1;
+  if (!ok) {   // let the other copies in flight land before the CTA leaves
+    if (nitems > 1) {
+      R.head = R.step(b, 1);
+      ring_settle(R, min(R.nbuf - 1, nitems) - 1);
+    }
+    ring = R;
+    return false;
+  }
   T acc = T(0);
   for (int j = 0; j < nitems && ok; ++j) {
-    SPOCK_TRACE(0);
     // next copy into the buffer of item j - 1 (freed by the barrier that ended it)
-    if (issuer && j + R.nbuf - 1 < nitems) b_issue(I, R, g, j + R.nbuf - 1, R.step(b, R.nbuf - 1));
-    if (j < nb && j > 0 && j % QS == 0) {   // next chunk of the bottom's children
+    if (issuer && j + R.nbuf - 1 < nitems) b_issue(P, I, R, g, j + R.nbuf - 1, R.step(b, R.nbuf - 1));
+    if (j < nbl && j > 0 && j % QS == 0) {   // next chunk of the bottom's leaf children
       load_children(j);
       __syncthreads();
     }
-    const unsigned xin = (j < nb) ? cm.qin + (unsigned)(j % QS) * ldcb : cin;
+    const unsigned xin = (j < nbl) ? cm.qin + (unsigned)(j % QS) * ldcb : cin;
     if (probe) { const long long c = clock64(); c_hand += c - tc; tc = c; }
-    SPOCK_TRACE(1);
     T v = (ng > 0) ? tdot<T>(R.buf(b) + mcol, xin + xoff, ng) : T(0);
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     acc += v;
-    SPOCK_TRACE(2);
-    if (j >= nb - 1) {   // epilogue of an output node
-      const int i = (j < nb) ? g.nodes[len - 1] : g.nodes[len - 2 - (j - nb)];
-      if (has_col && !half) {
-        if (col < nx) {
-          const T qq = acc + preA;
-          st_s<T>(cout + (unsigned)col * ES, qq);
-          stc(qbuf + (long long)i * nx + col, qq);
-        } else {
-          stc(dbuf + (long long)i * nu + (col - nx), preA - acc);
-        }
+    if (j < nbl) {
+      if (j == nbl - 1) {
+        epilogue(acc + share);
+        acc = T(0);
       }
+    } else if (j < nbl + nchain) {
+      epilogue(acc);
       acc = T(0);
-      preA = preB;
-      const int jn = j + 2;   // output node two epilogues ahead
-      preB = (jn >= nb && jn < nitems) ? pre_of(g.nodes[len - 2 - (jn - nb)]) : T(0);
-      const unsigned tt = cin; cin = cout; cout = tt;
+    } else {   // uplink: the top's share of its parent's step, to the parent's segment
+      if (owner) MB<T>::put(P.mbb + ((long long)top * w + col) * MB<T>::WPV, acc, eB);
+      acc = T(0);
     }
     if (probe) { const long long c = clock64(); c_mv += c - tc; tc = c; }
-    SPOCK_TRACE(3);
     b = R.step(b, 1);
     if (j + 1 < nitems) ring_wait0(R, b, err, 3, s_ok);
-    SPOCK_TRACE(4);
     __syncthreads();
-    SPOCK_TRACE(5);
     ok = *s_ok != 0;
   }
   if (probe) {
@@ -468,10 +592,6 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
     prof[8] += (unsigned long long)c_hand;
     prof[9] += (unsigned long long)c_mv;
   }
-  if (ok && t == 0) {   // q and d of the segment's nodes are written (CTA barrier above)
-    __threadfence();
-    st_release(flags + g.s, eB);
-  }
   R.head = b;
   ring = R;
   return ok;
@@ -479,9 +599,13 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
 
 // ---------------------------------------------------------------------------
 // forward rollout of one segment:  u^i = K_i x^i + d^i;  x^c = Abar_c x^i + B_c d^i + c_c
-// items: one per step down the chain (with KT_i), then the bottom's children
-// (KT of the bottom node with the first); the input of every item of node i is
-// [x^i ; d^i] in the carry vector
+// items: the downlink (x of the top from its parent's [x; d]), one per step
+// down the chain (KT_i with the child's MF), then the bottom's leaf children
+// (KT of the bottom with the first), or KT alone; the input of an item is
+// [x; d] of its node in the carry vector. [x; d] of the bottom goes to the
+// mailbox as soon as x of the bottom is known, so that the segments of its
+// non-leaf children start while this one finishes u of the bottom and the
+// leaves.
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err, const SegRef& g,
@@ -526,110 +650,113 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   const long long o_x = P.o_x, o_u = P.o_u;
   Ring R = ring;
   const FIssue<T> I(P);
-  const int len = g.len, nb = g.c1 - g.c0;
-  const int nitems = len - 1 + nb;
+  const int len = g.len, top = g.nodes[0];
+  const int down = (top != 0) ? 1 : 0;
+  const int ncont = down + len - 1;   // items whose child is the next item's node
+  const int nitems = ncont + max(1, seg_nleaf(P, g));
+  // x of the bottom is stored by item jx (-1: before the first item)
+  const int jx = ncont - 1;
   const bool probe = SPOCK_PROBE_ON && prof && blockIdx.x == 0 && t == 0;
   long long tc = probe ? clock64() : 0, c_mv = 0, c_hand = 0;
   if (issuer)
-    for (int j = R.ahead; j < min(R.nbuf - 1, nitems); ++j) f_issue(I, R, g, j, R.step(R.head, j));
+    for (int j = R.ahead; j < min(R.nbuf - 1, nitems); ++j) f_issue(P, I, R, g, j, R.step(R.head, j));
   R.ahead = 0;
-  // x of the top node comes from the segment that ends in its parent
-  if (t == 0) {
-    bool okw = true;
-    const int top = g.nodes[0];
-    if (top != 0) {
-      const int ps = P.bot_seg[P.anc[top]];
-      if (ps >= 0) okw = flag_wait(flags + ps, eF, err);
-    }
-    *s_ok = okw ? 1 : 0;
-  }
+  const int par = down ? P.anc[top] : 0;
+  const int bottom = g.nodes[len - 1];
+  if (t == 0) *s_ok = 1;
   __syncthreads();
-  if (!*s_ok) {
-    ring_settle(R, min(R.nbuf - 1, nitems));
-    ring = R;
-    return false;
-  }
-  // c_c of item j's child (x columns), d of the next node (chain items), two items ahead
-  auto child_of = [&](int j) { return j < len - 1 ? g.nodes[j + 1] : g.c0 + (j - (len - 1)); };
-  auto cp_of = [&](int j) -> T {
-    return (j < nitems && xcol && lead) ? ldr(cvec + (long long)(child_of(j) - 1) * nx + col) : T(0);
+  // c_c of item j's child (x columns), d of the child of a continuing item, two items ahead
+  auto child_of = [&](int j) {
+    int nd, ch;
+    bool kt;
+    f_item(P, g, j, nd, ch, kt);
+    return ch;
   };
-  auto dn_of = [&](int j) -> T {   // d of the child of chain item j, element t
-    return (j < len - 1 && t < nu) ? ldc(dbuf + (long long)g.nodes[j + 1] * nu + t) : T(0);
+  auto cp_of = [&](int j) -> T {
+    if (j >= nitems || !(xcol && lead)) return T(0);
+    const int c = child_of(j);
+    return c >= 0 ? ldr(cvec + (long long)(c - 1) * nx + col) : T(0);
+  };
+  auto dn_of = [&](int j) -> T {   // d of the child of continuing item j, element t
+    return (j < ncont && t < nu) ? ldc(dbuf + (long long)child_of(j) * nu + t) : T(0);
   };
   T cpA = cp_of(0), cpB = cp_of(1);
   T dA = dn_of(0), dB = dn_of(1);
-  // input of the top node: [x^i ; d^i]
+  // input of the first item: [x; d] of the parent (downlink, from the parent's
+  // segment through the mailbox mbf) or of the root
   unsigned cin = cm.carry0, cout = cm.carry1;
-  {
-    const int i = g.nodes[0];
-    for (int k = t; k < w; k += blockDim.x) {
-      T v;
-      if (k < nx) {
-        if (i == 0) {
-          v = P.x0s[k];
-          stc(vout + o_x + k, zc_add(P, o_x + k, v));
-        } else {
-          const long long ix = o_x + (long long)i * nx + k;
-          v = zc_sub(P, ix, ldc(vout + ix));
-        }
-      } else {
-        v = ldc(dbuf + (long long)i * nu + (k - nx));
-      }
-      st_s<T>(cin + (unsigned)k * ES, v);
+  for (int k = t; k < w; k += blockDim.x) {
+    T v = T(0);
+    if (down) {
+      if (!mb_wait<T>(P.mbf + ((long long)par * w + k) * MB<T>::WPV, eF, v, err)) *s_ok = 0;
+    } else if (k < nx) {
+      v = P.x0s[k];
+      stc(vout + o_x + k, zc_add(P, o_x + k, v));
+    } else {
+      v = ldc(dbuf + (k - nx));
     }
+    st_s<T>(cin + (unsigned)k * ES, v);
   }
-  if (t == 0) *s_ok = 1;
   int b = R.head;
   ring_wait0(R, b, err, 4, s_ok);
   __syncthreads();
   bool ok = *s_ok != 0;
+  if (!ok) {   // let the other copies in flight land before the CTA leaves
+    if (nitems > 1) {
+      R.head = R.step(b, 1);
+      ring_settle(R, min(R.nbuf - 1, nitems) - 1);
+    }
+    ring = R;
+    return false;
+  }
+  // [x; d] of the bottom for the segments of its children
+  auto publish = [&]() {
+    if (t < w) MB<T>::put(P.mbf + ((long long)bottom * w + t) * MB<T>::WPV, ld_s<T>(cin + (unsigned)t * ES), eF);
+  };
+  if (jx < 0) publish();   // the root alone: x0
   for (int j = 0; j < nitems && ok; ++j) {
-    if (issuer && j + R.nbuf - 1 < nitems) f_issue(I, R, g, j + R.nbuf - 1, R.step(b, R.nbuf - 1));
-    const bool chain = j < len - 1;
-    const bool kt = j <= len - 1;   // first item of its node
-    const int i = chain ? g.nodes[j] : g.nodes[len - 1];
-    const int c = child_of(j);
+    if (issuer && j + R.nbuf - 1 < nitems) f_issue(P, I, R, g, j + R.nbuf - 1, R.step(b, R.nbuf - 1));
+    int nd, c;
+    bool kt;
+    f_item(P, g, j, nd, c, kt);
+    const bool cont = j < ncont;
     if (probe) { const long long cc = clock64(); c_hand += cc - tc; tc = cc; }
     T v = T(0);
-    if (ng > 0 && (xcol || kt)) v = tdot<T>(R.buf(b) + mcol, cin + xoff, ng);
+    if (ng > 0 && ((xcol && c >= 0) || (ucol && kt))) v = tdot<T>(R.buf(b) + mcol, cin + xoff, ng);
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     {
       const T v2 = __shfl_xor_sync(0xffffffffu, v, 2);   // groups of four are lane-aligned
       if (XP == 4 && xcol) v += v2;
     }
     if (lead) {
-      if (xcol) {
+      if (xcol && c >= 0) {
         const T xc = v + cpA;
         const long long ix = o_x + (long long)c * nx + col;
         stc(vout + ix, zc_add(P, ix, xc));
-        if (chain) st_s<T>(cout + (unsigned)col * ES, xc);
+        if (cont) st_s<T>(cout + (unsigned)col * ES, xc);
       } else if (ucol && kt) {
-        const long long iu = o_u + (long long)i * nu + (col - nx);
+        const long long iu = o_u + (long long)nd * nu + (col - nx);
         stc(vout + iu, zc_add(P, iu, v + ld_s<T>(cin + (unsigned)col * ES)));
       }
     }
-    if (chain && t < nu) st_s<T>(cout + (unsigned)(nx + t) * ES, dA);
+    if (cont && t < nu) st_s<T>(cout + (unsigned)(nx + t) * ES, dA);
     cpA = cpB;
     cpB = cp_of(j + 2);
     dA = dB;
     dB = dn_of(j + 2);
-    if (chain) { const unsigned tt = cin; cin = cout; cout = tt; }
+    if (cont) { const unsigned tt = cin; cin = cout; cout = tt; }
     if (probe) { const long long cc = clock64(); c_mv += cc - tc; tc = cc; }
     b = R.step(b, 1);
     if (j + 1 < nitems) ring_wait0(R, b, err, 4, s_ok);
     __syncthreads();
     ok = *s_ok != 0;
+    if (ok && j == jx) publish();   // [x; d] of the bottom is in the carry (CTA barrier above)
   }
   if (probe) {
     const long long cc = clock64();
     c_hand += cc - tc;
     prof[10] += (unsigned long long)c_hand;
     prof[11] += (unsigned long long)c_mv;
-  }
-  if (ok && t == 0) {   // x of the children and u of the nodes are written (CTA barrier above)
-    __threadfence();
-    st_release(flags + g.s, eF);
   }
   R.head = b;
   ring = R;

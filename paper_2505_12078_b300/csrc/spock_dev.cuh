@@ -120,6 +120,14 @@ struct Prob {
   T* dbuf;   // [n_nl nu]
   T* hbuf;   // [n_nl nx]   -K'ubar - xbar
   T* ebuf;   // [n_nl nu]   Rt^{-1} ubar
+  // Mailboxes of the whole-CTA sweeps, n (nx + nu) values each, every 32-bit
+  // piece of a value stored in one 64-bit word beside a 32-bit tag (the
+  // evaluation's sweep epoch), so that a reader knows from the word itself
+  // that it is current: mbb[top] holds a segment top's share of its parent's
+  // backward step, mbf[bottom] the [x; d] of a segment bottom for the
+  // segments of its children. Zeroed before every launch.
+  unsigned long long* mbb;
+  unsigned long long* mbf;
 };
 
 // ---------------------------------------------------------------------------

@@ -36,6 +36,10 @@ struct DevMem {
   }
 };
 
+// bytes of one mailbox of the whole-CTA sweeps: n nodes x w values, one
+// 64-bit word per 32-bit piece of a value (es: bytes per value)
+inline size_t mailbox_bytes(int n, int w, size_t es) { return (size_t)n * (size_t)w * (es / 4) * 8; }
+
 template <class T>
 struct Iter {   // per-precision iteration data
   T *MB = nullptr, *MF = nullptr, *MP = nullptr, *KT = nullptr, *cvec = nullptr, *kc = nullptr;
@@ -43,6 +47,8 @@ struct Iter {   // per-precision iteration data
   T *box_lo = nullptr, *box_hi = nullptr, *boxN_lo = nullptr, *boxN_hi = nullptr, *ball = nullptr;
   T *prob = nullptr, *avar = nullptr, *x0s = nullptr;
   T *qbuf = nullptr, *dbuf = nullptr, *hbuf = nullptr, *ebuf = nullptr;
+  unsigned long long *mbb = nullptr, *mbf = nullptr;   // sweep mailboxes (whole-CTA sweeps only)
+  size_t mb_bytes = 0;                                 // bytes of each
   // full weights, cone translations, general rows (see Prob)
   T *FQ = nullptr, *FQT = nullptr, *FR = nullptr, *FRT = nullptr, *FN = nullptr, *FNT = nullptr;
   T *acost = nullptr, *acostN = nullptr;

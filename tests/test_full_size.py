@@ -94,13 +94,18 @@ def test_full_size_converged_fp32_large():
 
 
 def test_full_size_converged_against_oracle_golden():
-    """The benchmark solve against the oracle's own solve of the same problem to
-    ||v - T(v)||_inf <= 1e-4 (tests/golden/large_raocp_converged.npz, written by
-    tests/golden/make_converged.py from the oracle alone): the FP32 solve's x
-    and u within 1e-3 (relative to max(1, max|.|)) on the nodes whose path
-    weight under the oracle's maximising AV@R weights is positive (elsewhere
-    the optimal inputs need not be unique, reading C-19), the risk value
-    within 1e-3; the FP64 solve likewise. The whole-vector errors are printed."""
+    """The benchmark solve against the oracle's solves of the same problem
+    (tests/golden/large_raocp_converged.npz, written by
+    tests/golden/make_converged.py from the oracle alone): its solve to
+    ||v - T(v)||_inf <= 1e-4 and, continued from there, to 1e-6 (the reference
+    for the optimum). The termination test of Sec. 5.3 bounds the residual, not
+    the distance to the optimum, so two solves to 1e-4 can differ by more than
+    1e-3 in u even though each is a valid 1e-4 solution (reading C-19). The
+    FP32 and FP64 solves' x and u (relative to max(1, max|.|), on the nodes
+    whose path weight under the oracle's maximising AV@R weights is positive:
+    elsewhere the optimal inputs need not be unique) and risk value must lie
+    within max(1e-3, 1.25 x the oracle's own 1e-4 distance) of the 1e-6
+    reference. The whole-vector errors are printed."""
     import os
     spock = _spock()
     d = np.load(os.path.join(os.path.dirname(__file__), "golden", "large_raocp_converged.npz"))
@@ -109,12 +114,23 @@ def test_full_size_converged_against_oracle_golden():
     sel = d["path_weight"] > 1e-9
     seln = sel[:g.n_nl]
     assert sel.sum() > 10
+    rx, ru, rr = d["tight_x"], d["tight_u"], float(d["tight_risk"])
+    sx = max(1.0, float(np.max(np.abs(rx[sel]))))
+    su = max(1.0, float(np.max(np.abs(ru[seln]))))
+    sr = max(1.0, abs(rr))
+
+    def dist(x, u, risk):
+        return (float(np.max(np.abs(x[sel] - rx[sel]))) / sx, float(np.max(np.abs(u[seln] - ru[seln]))) / su,
+                abs(risk - rr) / sr)
+
+    own = dist(d["x"], d["u"], float(d["risk"]))   # the oracle's own 1e-4 solve
+    bound = [max(1e-3, 1.25 * e) for e in own]
+    print(f"oracle 1e-4 solve vs its 1e-6 solve: x {own[0]:.2e} u {own[1]:.2e} risk {own[2]:.2e}; "
+          f"bounds {bound[0]:.2e} {bound[1]:.2e} {bound[2]:.2e}")
     for prec in (32, 64):
         r = g.solve(p.x0, spock.opts(precision=prec, tol=1e-4, max_iters=200000))
         assert r["status"] == 0
-        ex = float(np.max(np.abs(r["x"][sel] - d["x"][sel]))) / max(1.0, float(np.max(np.abs(d["x"][sel]))))
-        eu = float(np.max(np.abs(r["u"][seln] - d["u"][seln]))) / max(1.0, float(np.max(np.abs(d["u"][seln]))))
-        er = abs(r["risk"] - float(d["risk"])) / max(1.0, abs(float(d["risk"])))
-        print(f"FP{prec}: x err {ex:.2e} u err {eu:.2e} on {int(sel.sum())} support nodes, risk err {er:.2e}, "
-              f"all-node x err {np.max(np.abs(r['x'] - d['x'])):.2e} u err {np.max(np.abs(r['u'] - d['u'])):.2e}")
-        assert ex <= 1e-3 and eu <= 1e-3 and er <= 1e-3, (prec, ex, eu, er)
+        e = dist(r["x"], r["u"], r["risk"])
+        print(f"FP{prec}: x err {e[0]:.2e} u err {e[1]:.2e} on {int(sel.sum())} support nodes, risk err {e[2]:.2e}, "
+              f"all-node x err {np.max(np.abs(r['x'] - rx)):.2e} u err {np.max(np.abs(r['u'] - ru)):.2e}")
+        assert all(ei <= bi for ei, bi in zip(e, bound)), (prec, e, bound)
