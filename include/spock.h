@@ -116,6 +116,14 @@ typedef struct spock_problem_desc {
     const double* GN;        /* [n_gN nx] */
     const double* gN_lo;     /* [n_l n_gN] */
     const double* gN_hi;     /* [n_l n_gN] */
+    double l1;               /* lambda_0 >= 0: every edge cost gets the term
+                                lambda_0 ||(x^anc, u^anc)||_1 (Prop. 2); 0: none. Solved through
+                                auxiliaries theta^i, lambda^i per non-leaf node (shared by the
+                                edge costs of its children, whose l1 terms are the same function of
+                                (x^i, u^i)) appended to z, and the rows theta - sum lambda,
+                                lambda - z, lambda + z in R_+ appended to eta. Single-problem
+                                calls only: the batched and serving calls return
+                                SPOCK_EUNSUPPORTED for such a problem */
 } spock_problem_desc;
 
 typedef struct spock_sizes {

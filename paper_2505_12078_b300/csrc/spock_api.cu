@@ -193,6 +193,38 @@ int build_tree(spock_problem* p, int n, const int* anc, const double* prob) {
   return SPOCK_OK;
 }
 
+// largest eigenvalue of a symmetric 3 x 3 matrix by cyclic Jacobi rotations
+// (each rotation zeroes one off-diagonal entry; the off-diagonal norm falls
+// quadratically once small)
+double sym3_max_eig(const double (&M)[3][3]) {
+  double a[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) a[i][j] = M[i][j];
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    const double dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= 1e-32 * dg) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (a[p][q] == 0.0) continue;
+        const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < 3; ++k) {   // columns p, q
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = c * akp - sn * akq;
+          a[k][q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < 3; ++k) {   // rows p, q
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = c * apk - sn * aqk;
+          a[q][k] = sn * apk + c * aqk;
+        }
+      }
+  }
+  return std::max(a[0][0], std::max(a[1][1], a[2][2]));
+}
+
 template <class T>
 void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   Prob<T>& P = it.P;
@@ -229,6 +261,7 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.Gg = it.Gg; P.GgT = it.GgT; P.GgN = it.GgN; P.GgNT = it.GgNT;
   P.gen_lo = it.gen_lo; P.gen_hi = it.gen_hi; P.genN_lo = it.genN_lo; P.genN_hi = it.genN_hi;
   P.alpha = (T)alpha;
+  P.l1 = (T)p->l1; P.o_th = p->o_th; P.o_lam = p->o_lam; P.e_l1 = p->e_l1; P.l1w = it.l1w;
   P.qbuf = it.qbuf; P.dbuf = it.dbuf; P.hbuf = it.hbuf; P.ebuf = it.ebuf;
   P.mbb = it.mbb; P.mbf = it.mbf;
 }
@@ -301,6 +334,7 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
   it.prob = m.alloc<T>(n);
   it.avar = m.alloc<T>(n_nl);
   it.x0s = m.alloc<T>(nx);
+  it.l1w = m.alloc<T>(nx + nu);
   it.qbuf = m.alloc<T>((long long)n * nx);
   it.dbuf = m.alloc<T>((long long)n_nl * nu);
   it.hbuf = m.alloc<T>((long long)n_nl * nx);
@@ -919,6 +953,8 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
     for (long long e = 0; e < (long long)n_l * d->n_gN; ++e)
       if (d->gN_lo[e] > d->gN_hi[e]) { delete p; return SPOCK_EINVAL; }
   }
+  if (!(d->l1 >= 0.0) || !isfinite(d->l1)) { delete p; return SPOCK_EINVAL; }
+  p->l1 = d->l1;
   p->full = full;
   p->has_lin = (d->q || d->r || d->qN) ? 1 : 0;
   p->n_g = d->n_g;
@@ -940,6 +976,15 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   p->e_cN = p->e_q + (long long)(n - 1) * (nx + nu + 2);
   p->e_qN = p->e_cN + (long long)n_l * p->n_cN;
   p->neta = p->e_qN + (long long)n_l * (nx + 2);
+  // l1 edge costs (Prop. 2): theta, lambda per non-leaf node after s in z, their
+  // rows after the leaf cost cones in eta
+  p->o_th = p->nz;
+  p->o_lam = p->o_th + (p->l1 > 0 ? n_nl : 0);
+  p->e_l1 = p->neta;
+  if (p->l1 > 0) {
+    p->nz = p->o_lam + (long long)n_nl * (nx + nu);
+    p->neta = p->e_l1 + (long long)n_nl * (1 + 2 * (nx + nu));
+  }
   p->nv = p->nz + p->neta;
   p->ldB = pad4(nx + nu); p->ldF = pad4(nx); p->ldP = pad4(nx + nu); p->ldK = pad4(nu);
   p->tw = pick_tw(nx, nu);
@@ -1122,6 +1167,7 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   a.MB = f.MB; a.MF = f.MF; a.MP = f.MP; a.KT = f.KT; a.Pc = dPcs; a.kc = f.kc;
   a.qh = f.qh; a.rh = f.rh; a.qNh = f.qNh; a.gx = f.gx; a.gu = f.gu; a.gN = f.gN;
   a.box_lo = f.box_lo; a.box_hi = f.box_hi; a.boxN_lo = f.boxN_lo; a.boxN_hi = f.boxN_hi; a.ball = f.ball;
+  a.xu_shift = (p->l1 > 0) ? 2.0 : 0.0;   // the l1 rows add 2 I to every (x^i, u^i) block of L'L
   cudaStream_t st = 0;
   cudaError_t e = launch_scale_dyn(a, st);
   if (e == cudaSuccess) e = launch_alg1(a, p->stage_off.data(), p->N, st);
@@ -1204,6 +1250,37 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   if (herr || herr2) { m.free_all(); delete p; return SPOCK_ENOTPD; }
   double l2;
   memcpy(&l2, &hnorm, sizeof(double));
+  if (p->l1 > 0) {
+    // the l1 auxiliaries of node i with the tau^c of its m children: L'L on
+    // (theta, lambda, tau) is [1 + m l^2/2, -w', -l/2 1'; -w, 2 I + w w', 0;
+    // -l/2 1, 0, I/2] (w = 1/s, l = lambda_0). Off span(theta, w, 1) its
+    // eigenvalues are 2 and 1/2; on it, the 3 x 3 matrix below.
+    double w2 = 0.0;
+    for (int k = 0; k < nx; ++k) w2 += 1.0 / (p->Sx[k] * p->Sx[k]);
+    for (int k = 0; k < nu; ++k) w2 += 1.0 / (p->Su[k] * p->Su[k]);
+    std::vector<int> ms;
+    for (int i = 0; i < n_nl; ++i) ms.push_back(p->ch_off[i + 1] - p->ch_off[i]);
+    std::sort(ms.begin(), ms.end());
+    ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
+    l2 = std::max(l2, 2.0);
+    for (int m : ms) {
+      const double lm = p->l1, sm = sqrt((double)m);
+      const double M3[3][3] = {{1.0 + 0.5 * m * lm * lm, -sqrt(w2), -0.5 * lm * sm},
+                               {-sqrt(w2), 2.0 + w2, 0.0},
+                               {-0.5 * lm * sm, 0.0, 0.5}};
+      l2 = std::max(l2, sym3_max_eig(M3));
+    }
+    std::vector<double> w64(nx + nu);
+    std::vector<float> w32(nx + nu);
+    for (int k = 0; k < nx + nu; ++k) {
+      w64[(size_t)k] = 1.0 / (k < nx ? p->Sx[k] : p->Su[k - nx]);
+      w32[(size_t)k] = (float)w64[(size_t)k];
+    }
+    if (cudaMemcpy(p->f64.l1w, w64.data(), w64.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->f32.l1w, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      m.free_all(); delete p; return SPOCK_EDEVICE;
+    }
+  }
   p->normL = sqrt(l2);
   p->alpha = 0.99 / p->normL;
   // FP32 copies of the iteration data

@@ -120,6 +120,15 @@ struct Prob {
   T* dbuf;   // [n_nl nu]
   T* hbuf;   // [n_nl nx]   -K'ubar - xbar
   T* ebuf;   // [n_nl nu]   Rt^{-1} ubar
+  // l1 edge-cost term lambda_0 ||(x^anc, u^anc)||_1 (Prop. 2; l1 = lambda_0,
+  // 0 = none): theta^i at o_th + i and lambda^i (scaled like (x^i, u^i)) at
+  // o_lam + i (nx + nu) in z; per non-leaf node the rows theta - sum_k l1w_k
+  // lambda_k, lambda - (x^i, u^i), lambda + (x^i, u^i), all in R_+, at
+  // e_l1 + i (1 + 2 (nx + nu)) in eta; the cost cone of every child c of i
+  // carries (tau^c - l1 theta^i)/2 in its last two entries.
+  T l1;
+  long long o_th, o_lam, e_l1;
+  const T* l1w;   // [nx + nu] 1/S^x, 1/S^u
   // Mailboxes of the whole-CTA sweeps, n (nx + nu) values each, every 32-bit
   // piece of a value stored in one 64-bit word beside a 32-bit tag (the
   // evaluation's sweep epoch), so that a reader knows from the word itself

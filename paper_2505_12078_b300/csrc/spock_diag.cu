@@ -155,6 +155,15 @@ __global__ void k_S3_diag(Prob<double> P, const double* __restrict__ lz, const d
         dot += h * x;
         sig += fmax(h * lo, h * hi);
       }
+      if (P.l1 != 0.0) {                                    // l1 rows (Prop. 2): R_+, support 0
+        const int nr = 1 + 2 * (P.nx + P.nu);
+        const long long le = P.e_l1 + (long long)i * nr;
+        for (int e = lane; e < nr; e += 32) {
+          const double x = lz[le + e];
+          inf = fmax(inf, fabs(x - fmax(x, 0.0)));
+          dot += ep[le + e] * x;
+        }
+      }
     } else if (b < P.n_nl + P.n - 1) {
       const long long c = b - P.n_nl + 1;
       soc_diag(lane, P.W, P.e_q + (c - 1) * P.W, lz, ep, P.acost ? P.acost + (c - 1) * P.W : nullptr, inf, dot,

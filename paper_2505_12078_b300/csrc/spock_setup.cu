@@ -379,7 +379,7 @@ __global__ void k_cost_con(int n, int n_nl, int nx, int nu, int nbx, int nbu, in
 }
 
 // ||L||^2 as the max over the diagonal-Gram blocks of L (see file header)
-__global__ void k_norm_L(int n, int n_nl, int nx, int nu, int nbx, int nub,
+__global__ void k_norm_L(int n, int n_nl, int nx, int nu, int nbx, int nub, double xu_shift,
                          const int* __restrict__ ch_off, const double* __restrict__ prob,
                          const double* __restrict__ qh, const double* __restrict__ rh,
                          const double* __restrict__ qNh, const double* __restrict__ gx,
@@ -390,12 +390,12 @@ __global__ void k_norm_L(int n, int n_nl, int nx, int nu, int nbx, int nub,
     if (i < n_nl) {
       const int c0 = ch_off[i], c1 = ch_off[i + 1];
       for (int k = 0; k < nx; ++k) {
-        double s = nbx ? gx[k] * gx[k] : 0.0;
+        double s = (nbx ? gx[k] * gx[k] : 0.0) + xu_shift;
         for (int c = c0; c < c1; ++c) s += qh[(long long)(c - 1) * nx + k] * qh[(long long)(c - 1) * nx + k];
         lam = fmax(lam, s);
       }
       for (int k = 0; k < nu; ++k) {
-        double s = nub * gu[k] * gu[k];
+        double s = nub * gu[k] * gu[k] + xu_shift;
         for (int c = c0; c < c1; ++c) s += rh[(long long)(c - 1) * nu + k] * rh[(long long)(c - 1) * nu + k];
         lam = fmax(lam, s);
       }
@@ -474,6 +474,7 @@ __global__ void k_apply_L(Prob<T> P, const int* __restrict__ ynode, const T* __r
         }
       } else {
         v = T(0.5) * z[P.o_tau + cm1];
+        if (P.l1 != T(0)) v -= T(0.5) * P.l1 * z[P.o_th + a];   // (tau^c - lambda_0 theta^a)/2 (Prop. 2)
       }
     } else if (e < P.e_qN) {               // leaf constraint rows
       const long long f = e - P.e_cN;
@@ -485,6 +486,20 @@ __global__ void k_apply_L(Prob<T> P, const int* __restrict__ ynode, const T* __r
       } else {
         const T* G = P.GgN + (size_t)(k - P.nbx) * nx;
         for (int q = 0; q < nx; ++q) v += G[q] * x[q];
+      }
+    } else if (e >= P.e_l1) {              // l1 rows of non-leaf node i (Prop. 2)
+      const int d = nx + nu;
+      const long long f = e - P.e_l1;
+      const long long i = f / (1 + 2 * d);
+      const int r = (int)(f % (1 + 2 * d));
+      const T* lam = z + P.o_lam + i * d;
+      if (r == 0) {                        // theta - sum_k w_k lambda_k
+        v = z[P.o_th + i];
+        for (int k = 0; k < d; ++k) v -= P.l1w[k] * lam[k];
+      } else {                             // lambda_k -/+ (x^i, u^i)_k
+        const int k = (r - 1) % d;
+        const T zk = (k < nx) ? z[P.o_x + i * nx + k] : z[P.o_u + i * nu + (k - nx)];
+        v = (r <= d) ? lam[k] - zk : lam[k] + zk;
       }
     } else {                               // leaf cost blocks
       const long long f = e - P.e_qN;
@@ -538,6 +553,10 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
         }
         const T* eg = ec + i * P.n_c + P.nbox + (P.has_ball ? nu : 0);
         for (int r = 0; r < P.n_g; ++r) v += P.GgT[(size_t)k * P.n_g + r] * eg[r];
+        if (P.l1 != T(0)) {                 // l1 rows lambda - x, lambda + x
+          const T* el = eta + P.e_l1 + i * (1 + 2 * (nx + nu));
+          v += el[1 + (nx + nu) + k] - el[1 + k];
+        }
       } else {
         const long long j = i - P.n_nl;
         if (P.nbx) v = P.gN[k] * ecN[j * P.n_cN + k];
@@ -565,6 +584,10 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
       }
       const T* eg = ec + i * P.n_c + P.nbox + (P.has_ball ? nu : 0);
       for (int r = 0; r < P.n_g; ++r) v += P.GgT[(size_t)(nx + k) * P.n_g + r] * eg[r];
+      if (P.l1 != T(0)) {                   // l1 rows lambda - u, lambda + u
+        const T* el = eta + P.e_l1 + i * (1 + 2 * (nx + nu));
+        v += el[1 + (nx + nu) + nx + k] - el[1 + nx + k];
+      }
     } else if (e < P.o_tau) {              // y
       const long long f = e - P.o_y;
       const int i = ynode[f];
@@ -575,7 +598,7 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
     } else if (e < P.o_s) {                // tau^c
       const long long cm1 = e - P.o_tau;
       v = T(0.5) * (eq[cm1 * P.W + nx + nu] + eq[cm1 * P.W + nx + nu + 1]);
-    } else {                               // s^c
+    } else if (e < P.o_th) {               // s^c
       const long long cm1 = e - P.o_s;
       const long long c = cm1 + 1;
       if (c < P.n_nl) v = es[c];
@@ -583,6 +606,18 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
         const long long j = c - P.n_nl;
         v = T(0.5) * (eqN[j * (nx + 2) + nx] + eqN[j * (nx + 2) + nx + 1]);
       }
+    } else if (e < P.o_lam) {              // theta^i: its l1 row and the children's cost cones
+      const long long i = e - P.o_th;
+      v = eta[P.e_l1 + i * (1 + 2 * (nx + nu))];
+      for (int c = P.ch_off[i]; c < P.ch_off[i + 1]; ++c)
+        v -= T(0.5) * P.l1 * (eq[(long long)(c - 1) * P.W + nx + nu] + eq[(long long)(c - 1) * P.W + nx + nu + 1]);
+    } else {                               // lambda^i_k: its l1 rows
+      const int d = nx + nu;
+      const long long f = e - P.o_lam;
+      const long long i = f / d;
+      const int k = (int)(f % d);
+      const T* el = eta + P.e_l1 + i * (1 + 2 * d);
+      v = -P.l1w[k] * el[0] + el[1 + k] + el[1 + d + k];
     }
     z[e] = v;
   }
@@ -639,7 +674,7 @@ cudaError_t launch_build(const SetupArgs& a, cudaStream_t s) {
 
 cudaError_t launch_norm_L(const SetupArgs& a, unsigned long long* out, cudaStream_t s) {
   k_norm_L<<<grid_for(a.n, 128), 128, 0, s>>>(a.n, a.n_nl, a.nx, a.nu, a.nbx,
-                                                (a.nbu ? 1 : 0) + (a.has_ball ? 1 : 0), a.ch_off,
+                                                (a.nbu ? 1 : 0) + (a.has_ball ? 1 : 0), a.xu_shift, a.ch_off,
                                                 a.prob, a.qh, a.rh, a.qNh, a.gx, a.gu, a.gN, out);
   return cudaGetLastError();
 }

@@ -183,11 +183,14 @@ __global__ void k_norm_L_blocks(Prob<double> P, int iters, double rtol, unsigned
         }
         __syncthreads();
       }
-      // selection rows: x box gx^2, u box and ball gu^2 each
+      // selection rows: x box gx^2, u box and ball gu^2 each; the l1 rows
+      // lambda - z, lambda + z add 2 I (their cross terms with lambda cancel)
       const int nub = (P.nbu ? 1 : 0) + (P.has_ball ? 1 : 0);
+      const double l1s = (P.l1 > 0) ? 2.0 : 0.0;
       for (int k = threadIdx.x; k < nx + nu; k += blockDim.x) {
         if (k < nx) { if (P.nbx) y[k] += P.gx[k] * P.gx[k] * v[k]; }
         else y[k] += nub * P.gu[k - nx] * P.gu[k - nx] * v[k];
+        y[k] += l1s * v[k];
       }
       __syncthreads();
       // general rows: G' (G v)

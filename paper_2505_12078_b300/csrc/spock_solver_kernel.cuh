@@ -142,6 +142,42 @@ __device__ void s2_block(const Prob<T>& P, int lane, int i, const T* __restrict_
   }
 }
 
+// The auxiliaries of the l1 edge costs of node i (Prop. 2): f does not
+// involve them, so their step is w = z - alpha L*eta. L* of theta^i: its l1
+// row minus lambda_0/2 times the last two entries of every child's cost cone;
+// of lambda^i_k: -w_k times the first l1 row plus the rows lambda_k - z_k and
+// lambda_k + z_k.
+template <class T>
+__device__ void l1_prep(const Prob<T>& P, int lane, int i, const T* __restrict__ vin, T* __restrict__ vout,
+                        const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu, d = nx + nu;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  const T al = P.alpha;
+  const T* el = eta + P.e_l1 + (long long)i * (1 + 2 * d);
+  const T e0 = ldc(el);
+  T sc = 0;
+  for (int c = P.ch_off[i] + lane; c < P.ch_off[i + 1]; c += 32) {
+    const T* eq = eta + P.e_q + (long long)(c - 1) * P.W + nx + nu;
+    sc += ldc(eq) + ldc(eq + 1);
+  }
+  sc = warp_sum(sc);
+  if (lane == 0) {
+    const long long idx = P.o_th + i;
+    const T o = ldc(z + idx);
+    const T n = zc_add(P, idx, o - al * (e0 - T(0.5) * P.l1 * sc));
+    stc(vout + idx, n);
+    ra.z(o, n, dirv(vref, idx));
+  }
+  for (int k = lane; k < d; k += 32) {
+    const long long idx = P.o_lam + (long long)i * d + k;
+    const T o = ldc(z + idx);
+    const T n = zc_add(P, idx, o - al * ((ldc(el + 1 + k) + ldc(el + 1 + d + k)) - ldr(P.l1w + k) * e0));
+    stc(vout + idx, n);
+    ra.z(o, n, dirv(vref, idx));
+  }
+}
+
 // one warp (a team of one warp) per non-leaf node
 template <class T, int CH>
 __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb, T* s_red, int i,
@@ -170,6 +206,10 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
     }
 #pragma unroll 8
     for (int r = 0; r < P.n_g; ++r) g = fma(ldr(P.GgT + (size_t)(nx + k) * P.n_g + r), ldc(eg + r), g);
+    if (P.l1 != T(0)) {   // l1 rows lambda - u, lambda + u (Prop. 2)
+      const T* el = eta + P.e_l1 + (long long)i * (1 + 2 * (nx + nu));
+      g += ldc(el + 1 + (nx + nu) + nx + k) - ldc(el + 1 + nx + k);
+    }
     s_in[k] = ldc(z + P.o_u + (long long)i * nu + k) - al * g;
   }
   for (int k = tw1.lane; k < nx; k += 32) {
@@ -186,6 +226,10 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
     }
 #pragma unroll 8
     for (int r = 0; r < P.n_g; ++r) g = fma(ldr(P.GgT + (size_t)k * P.n_g + r), ldc(eg + r), g);
+    if (P.l1 != T(0)) {   // l1 rows lambda - x, lambda + x (Prop. 2)
+      const T* el = eta + P.e_l1 + (long long)i * (1 + 2 * (nx + nu));
+      g += ldc(el + 1 + (nx + nu) + k) - ldc(el + 1 + k);
+    }
     s_xb[k] = ldc(z + P.o_x + (long long)i * nx + k) - al * g;
   }
   __syncwarp();
@@ -200,6 +244,7 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
     else stc(eb + (j - nx), s - ldr(kc + j));
   });
   s2_block(P, tw1.lane, i, vin, vout, vref, ra);
+  if (P.l1 != T(0)) l1_prep(P, tw1.lane, i, vin, vout, vref, ra);
 }
 
 template <class T>
@@ -782,6 +827,45 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
   }
 }
 
+// The l1 rows of non-leaf node i (Prop. 2): theta - sum_k w_k lambda_k,
+// lambda - z, lambda + z (z = (x^i, u^i)), each in R_+.
+template <class T>
+__device__ void eta_l1(const Prob<T>& P, int lane, int i, const T* __restrict__ vin, T* __restrict__ vout,
+                       const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu, d = nx + nu;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  T* eo = vout + P.nz;
+  const T* er = vref ? vref + P.nz : nullptr;
+  const T al = P.alpha;
+  const long long le = P.e_l1 + (long long)i * (1 + 2 * d);
+  const long long ol = P.o_lam + (long long)i * d;
+  auto pos = [](auto w) { return max(w, decltype(w)(0)); };
+  auto row = [&](long long ie, T Lo, T Ln, T Ld, T Lrd) {
+    const T eo_ = ldc(eta + ie);
+    const T eb = eo_ + al * (T(2) * Ln - Lo);
+    const T en = eta_prox(P, ie, eb, pos);
+    stc(eo + ie, en);
+    ra.eta(eo_, en, er ? ldc(er + ie) : T(0), Ld, Lrd);
+  };
+  T so = 0, sn = 0, sd = 0, sr = 0;
+  for (int k = lane; k < d; k += 32) {
+    const T w = ldr(P.l1w + k);
+    const T lo = ldc(z + ol + k), ln = ldc(vout + ol + k), lr = dirv(vref, ol + k);
+    so += w * lo; sn += w * ln; sd += w * (lo - ln); sr += w * lr;
+    const long long iz = (k < nx) ? P.o_x + (long long)i * nx + k : P.o_u + (long long)i * nu + (k - nx);
+    const T zo = ldc(z + iz), zn = ldc(vout + iz), zr = dirv(vref, iz);
+    row(le + 1 + k, lo - zo, ln - zn, (lo - ln) - (zo - zn), lr - zr);
+    row(le + 1 + d + k, lo + zo, ln + zn, (lo - ln) + (zo - zn), lr + zr);
+  }
+  so = warp_sum(so); sn = warp_sum(sn); sd = warp_sum(sd); sr = warp_sum(sr);
+  if (lane == 0) {
+    const long long ith = P.o_th + i;
+    const T tho = ldc(z + ith), thn = ldc(vout + ith), thr = dirv(vref, ith);
+    row(le, tho - so, thn - sn, (tho - thn) - sd, thr - sr);
+  }
+}
+
 // Cost cone block in the centred form: ebv holds the increments of
 // eta_bar = eta + alpha L(2 z+ - z) over the centre; w = eta_bar/alpha - a is
 // formed in FP64 about the centre (ctrA folds in -a), projected on the
@@ -981,7 +1065,11 @@ __device__ void eta_soc_full(const Prob<T>& P, int lane, int c, const T* __restr
   full_mv3<T, NE>(lane, nu, nx, P.FRT + (size_t)(c - 1) * nu * nu, z, vout, vref, P.o_u + (long long)i * nu, a1, a2,
                   a3);
   const long long it = P.o_tau + c - 1;
-  const T to = ldc(z + it), tn = ldc(vout + it), td = dirv(vref, it);
+  T to = ldc(z + it), tn = ldc(vout + it), td = dirv(vref, it);
+  if (P.l1 != T(0)) {   // (tau^c - lambda_0 theta^i)/2 (Prop. 2)
+    const long long ith = P.o_th + i;
+    to -= P.l1 * ldc(z + ith); tn -= P.l1 * ldc(vout + ith); td -= P.l1 * dirv(vref, ith);
+  }
   const T al = P.alpha;
   T ebv[NE];
 #pragma unroll
@@ -1038,6 +1126,12 @@ __device__ void eta_soc(const Prob<T>& P, int lane, int c, const T* __restrict__
   const long long it = P.o_tau + c - 1;
   const T* qh = P.qh + (long long)(c - 1) * nx;
   const T* rh = P.rh + (long long)(c - 1) * nu;
+  // with an l1 term the last two entries are (tau^c - lambda_0 theta^i)/2 (Prop. 2)
+  T tho = 0, thn = 0, thd = 0;
+  if (P.l1 != T(0)) {
+    const long long ith = P.o_th + i;
+    tho = P.l1 * ldc(z + ith); thn = P.l1 * ldc(vout + ith); thd = P.l1 * dirv(vref, ith);
+  }
   auto Lz = [&](int e, T& Lo, T& Ln, T& Ld, T& Lrd) {
     long long idx;
     T g;
@@ -1048,8 +1142,9 @@ __device__ void eta_soc(const Prob<T>& P, int lane, int c, const T* __restrict__
     } else {
       g = T(0.5); idx = it;
     }
-    const T o = ldc(z + idx), nn = ldc(vout + idx);
-    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * dirv(vref, idx);
+    T o = ldc(z + idx), nn = ldc(vout + idx), dd = dirv(vref, idx);
+    if (e >= nx + nu) { o -= tho; nn -= thn; dd -= thd; }
+    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * dd;
   };
   soc_block<T, NE>(P, lane, P.W, P.e_q + (long long)(c - 1) * P.W, vin + P.nz, vout + P.nz,
                    vref ? vref + P.nz : nullptr, Lz, ra, P.acost ? P.acost + (size_t)(c - 1) * P.W : nullptr);
@@ -1312,6 +1407,7 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
         z_resid(vin, vout, vref, P.o_x + b * P.nx, P.nx, lane, ra);
         z_resid(vin, vout, vref, P.o_u + b * P.nu, P.nu, lane, ra);
         eta_nonleaf(P, lane, (int)b, vin, vout, vref, ra);
+        if (P.l1 != T(0)) eta_l1(P, lane, (int)b, vin, vout, vref, ra);
       } else if (b < P.n_nl + P.n - 1) {
         if (P.full) eta_soc_full<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);
         else eta_soc<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);

@@ -44,7 +44,7 @@ class ProblemDesc(C.Structure):
                 ("x_lo", _dp), ("x_hi", _dp), ("u_lo", _dp), ("u_hi", _dp), ("u_ball", _dp),
                 ("avar", _dp), ("weights_full", C.c_int), ("q", _dp), ("r", _dp), ("qN", _dp),
                 ("n_g", C.c_int), ("Gx", _dp), ("Gu", _dp), ("g_lo", _dp), ("g_hi", _dp),
-                ("n_gN", C.c_int), ("GN", _dp), ("gN_lo", _dp), ("gN_hi", _dp)]
+                ("n_gN", C.c_int), ("GN", _dp), ("gN_lo", _dp), ("gN_hi", _dp), ("l1", C.c_double)]
 
 
 class Sizes(C.Structure):
@@ -222,6 +222,7 @@ class Problem:
         d.n_gN = 0 if arrs["GN"] is None else int(np.asarray(arrs["GN"]).shape[0])
         for k, v in conv.items():
             setattr(d, k, _ptr(v))
+        d.l1 = float(getattr(p, "l1", None) or 0.0)
         h = C.c_void_p()
         _check(lib.spock_problem_create(C.byref(d), C.byref(h)), "spock_problem_create")
         self.h = h

@@ -15,7 +15,7 @@ the tests a statement about the FP32 solution alone. How far a 1e-4 point may
 lie from the optimum depends on the problem (on `small` the oracle's own 1e-4
 point has u^0 1.19e-3 away from it), so the oracle's 1e-4 solve is stored too.
 
-Usage: python -m tests.golden.make_converged_cases   (a few minutes, one core)
+Usage: python -m tests.golden.make_converged_cases [--all]   (a few minutes, one core)
 """
 import json
 import os
@@ -30,13 +30,21 @@ for d in (ROOT, os.path.join(ROOT, "tests")):
 from oracle.spock_oracle import Oracle  # noqa: E402
 from test_gpu_parity import CASES  # noqa: E402
 
-NAMES = ["small", "ragged_37x19_ball", "chain_only", "full_lin_box", "rows_ball_diag_lin", "team_100x50"]
+NAMES = ["small", "ragged_37x19_ball", "chain_only", "full_lin_box", "rows_ball_diag_lin", "team_100x50",
+         "l1_box_ball"]
 TOL = 1e-7
 
 
 def main():
+    """Solves the cases missing from the file (every case with --all)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "converged_cases.json")
     out = {"tol": TOL, "cases": {}}
+    if "--all" not in sys.argv and os.path.exists(path):
+        with open(path) as f:
+            out = json.load(f)
     for name in NAMES:
+        if name in out["cases"]:
+            continue
         t = time.time()
         o = Oracle(CASES[name]())
         r = o.solve(tol=TOL, max_iters=400000)
@@ -46,7 +54,6 @@ def main():
                               "at_1e-4": {"iters": int(r4["iters"]), "risk": float(r4["risk"]),
                                           "u0": [float(x) for x in r4["u"][0]]}}
         print(name, r["iters"], f"{time.time() - t:.1f} s", flush=True)
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "converged_cases.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
 

@@ -51,7 +51,16 @@ CASES = {
     "team_150x50": lambda: constrained([2, 1], 150, 50, seed=28, avar=0.5),
     # correlated full weights on a chain: the (x, u) block of L'L sets ||L||
     "full_corr_chain": lambda: _correlated(general([1, 1, 1], 6, 2, seed=65, avar=1.0, n_g=1, box=True)),
+    # l1 edge costs (Prop. 2): whole-CTA sweeps with full weights, boxes and a
+    # ball; team sweeps with diagonal weights
+    "l1_box_ball": lambda: _with_l1(_with_ball(general([2, 2, 1], 5, 3, seed=66, avar=0.5, box=True), 1.5), 0.3),
+    "l1_team_100x50": lambda: _with_l1(constrained([2, 1], 100, 50, seed=67, avar=0.5, uball=3.0), 0.2),
 }
+
+
+def _with_l1(p, lam):
+    p.l1 = float(lam)
+    return p
 
 
 def _correlated(p):
@@ -223,7 +232,8 @@ def test_fixed_iterations_cp_fp64(name):
 
 
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "team_100x50",
-                                  "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "full_rows_100x50"])
+                                  "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "full_rows_100x50",
+                                  "l1_box_ball", "l1_team_100x50"])
 def test_fixed_iterations_spock_fp64(name):
     """SPOCK (Alg. 4 with Anderson directions) for a fixed iteration count in
     FP64: same branch sequence counts and iterate within 1e-10 relative."""
@@ -246,7 +256,8 @@ def test_fixed_iterations_spock_fp64(name):
 
 @pytest.mark.parametrize("name,recentre", [("small", 0.1), ("ragged_37x19_ball", 0.1), ("chain_only", 0.1),
                                            ("full_lin_box", 0.1), ("rows_ball_diag_lin", 0.1),
-                                           ("team_100x50", 0.1), ("small", 0.0), ("ragged_37x19_ball", 0.0)])
+                                           ("team_100x50", 0.1), ("small", 0.0), ("ragged_37x19_ball", 0.0),
+                                           ("l1_box_ball", 0.1), ("l1_box_ball", 0.0)])
 def test_converged_fp32_vs_oracle(name, recentre):
     """FP32 iteration to ||v - T(v)||_inf <= 1e-4 against the optimum: the
     oracle's FP64 solve to 1e-7 (tests/golden/converged_cases.json, written by
@@ -269,7 +280,7 @@ def test_converged_fp32_vs_oracle(name, recentre):
 
 
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "avar0_branch8",
-                                  "full_lin_box", "rows_ball_diag_lin", "full_rows_cta"])
+                                  "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "l1_box_ball"])
 def test_fp64_check_matches_oracle(name):
     """FP64 exit check (Sec. 5.3) through spock_check on the oracle's own
     iterate after 25 SPOCK iterations: xi1, xi2 (Eq. xi1k), the primal
@@ -358,3 +369,18 @@ def test_converged_fp32_qr_update(name):
     assert res["status"] == 0, res["info"]
     assert abs(res["risk"] - ref["risk"]) <= ref["tol_risk"]
     assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= ref["tol_u"]
+
+
+def test_l1_costs_are_single_problem_only():
+    """A problem with l1 edge costs (Prop. 2) is solved by the single-problem
+    calls; the batched and serving calls refuse it with SPOCK_EUNSUPPORTED
+    (-6) instead of running paths that do not carry its auxiliaries."""
+    spock = _spock()
+    p = CASES["l1_box_ball"]()
+    g = spock.Problem(p)
+    with pytest.raises(spock.SpockError) as e:
+        spock.Batch([g], precision=32)
+    assert e.value.code == -6
+    with pytest.raises(spock.SpockError) as e:
+        spock.Server([g], precision=32)
+    assert e.value.code == -6
