@@ -24,6 +24,7 @@ operator L"). Nodes are in breadth-first order, children contiguous; the
 first n_nl nodes are the non-leaf nodes, the last n_l the leaves.
 
   z   = [ s0 | x (n*nx) | u (n_nl*nu) | y (sum_i 2 n_i + 1) | tau (n-1) | s (n-1) ]
+        (with the total-variation risk, y^i has 3 n_i + 2 entries)
         x^i at 1 + i*nx, u^i at 1 + n*nx + i*nu, y^i at its block offset,
         tau^c and s^c (c >= 1) at index c-1 of their arrays.
   eta = [ eta_y (same blocks as y) | eta_s (n_nl) | eta_c (n_nl*n_c)
@@ -176,6 +177,51 @@ def conic_risk_data(p, a):
     return b, E
 
 
+def tv_risk(Z, p, r):
+    """Worst expectation of Z over the total-variation ball {mu in the simplex :
+    ||mu - p||_1 <= r} around the children's probabilities p: from mu = p, mass
+    min(r/2, 1 - p_top) moves onto an outcome with the largest cost, taken from
+    the smallest costs first (each outcome gives at most its p)."""
+    return float(tv_maximiser(Z, p, r) @ np.asarray(Z, dtype=np.float64))
+
+
+def tv_maximiser(Z, p, r):
+    """The maximising mu of tv_risk (see there)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    mu = np.asarray(p, dtype=np.float64).copy()
+    top = int(np.argmax(Z))
+    move = min(0.5 * r, 1.0 - mu[top])
+    mu[top] += move
+    for j in np.argsort(Z, kind="stable"):
+        if move <= 0.0:
+            break
+        if j == top:
+            continue
+        w = min(mu[j], move)
+        mu[j] -= w
+        move -= w
+    return mu
+
+
+def conic_risk_data_tv(p, r):
+    """b, E, F of the conic representation (Sec. 3.3, Eq. primal_risk) of the
+    total-variation risk: max mu'Z over mu in the simplex with ||mu - p||_1 <=
+    r, with an auxiliary nu >= |mu - p| (n_nu = n, so F != 0). Rows of
+    b - E mu - F nu in K = R^{3n+1}_+ x {0}:
+      nu - mu + p >= 0 (n), nu + mu - p >= 0 (n), r - 1'nu >= 0 (1),
+      mu >= 0 (n), 1 - 1'mu = 0 (1):
+    b = [p; -p; r; 0; 1], E = [I; -I; 0; -I; 1'], F = [-I; -I; 1'; 0; 0].
+    Returns b, E, F and the number of rows in R_+ (3n + 1)."""
+    p = np.asarray(p, dtype=np.float64)
+    n = p.shape[0]
+    I = np.eye(n)
+    Z0 = np.zeros((n, n))
+    b = np.concatenate([p, -p, [r], np.zeros(n), [1.0]])
+    E = np.vstack([I, -I, np.zeros((1, n)), -I, np.ones((1, n))])
+    F = np.vstack([-I, -I, np.ones((1, n)), Z0, np.zeros((1, n))])
+    return b, E, F, 3 * n + 1
+
+
 # ---------------------------------------------------------------------------
 # Projections onto the pieces of S3 (Sec. 4.3, Eq. S3-def)
 # ---------------------------------------------------------------------------
@@ -254,7 +300,9 @@ class Oracle:
     def _layout(self):
         tr = self.tree
         n, nx, nu, n_nl, n_l = tr.n, self.nx, self.nu, tr.n_nl, tr.n_l
-        self.ylen = 2 * tr.n_ch[:n_nl] + 1
+        self.tv = None if getattr(self.P, "tv", None) is None else np.asarray(self.P.tv, dtype=np.float64)
+        m_ = tr.n_ch[:n_nl]
+        self.ylen = (3 * m_ + 2) if self.tv is not None else (2 * m_ + 1)
         self.yoff = np.concatenate([[0], np.cumsum(self.ylen)]).astype(np.int64)
         n_y = int(self.yoff[-1])
         o_x = 1
@@ -281,7 +329,8 @@ class Oracle:
             n_eta = self.e_l1 + n_nl * (1 + 2 * (nx + nu))
         self.lay = Layout(n_y, n_z, n_eta, o_x, o_u, o_y, o_tau, o_s,
                           e_y, e_s, e_c, e_q, e_cN, e_qN)
-        # entries of eta_y that lie in R_+ (all but the last entry of each block)
+        # entries of eta_y that lie in R_+ (all but the last entry of each block:
+        # the zero cone's dual R of AV@R's and the total-variation risk's sums)
         mask = np.ones(n_y, dtype=bool)
         mask[self.yoff[1:] - 1] = False
         self.ypos = mask
@@ -546,32 +595,47 @@ class Oracle:
 
     # -- proj S2 -----------------------------------------------------------
     def proj_S2(self, y, tau, s):
-        """Projection of (y^i, tau^[i], s^[i]) onto ker[E_i', -I, -I] for every
-        non-leaf node (Sec. 4.3, S_2; F is absent for AV@R), written out as
-        v - G'(GG')^{-1} G v with the dense G = [E_i', -I, -I] of each node
-        (nodes with equal child counts are stacked into one batched solve)."""
+        """Projection of (y^i, tau^[i], s^[i]) onto ker[E_i', -I, -I; F_i', 0, 0]
+        for every non-leaf node (Sec. 4.3, S_2; F is absent for AV@R), written
+        out as v - G'(GG')^{-1} G v with the dense G of each node (nodes with
+        equal child counts are stacked into one batched solve)."""
         tr = self.tree
         y2, tau2, s2 = y.copy(), tau.copy(), s.copy()
         for m in np.unique(tr.n_ch[:tr.n_nl]):
             nodes = np.where(tr.n_ch[:tr.n_nl] == m)[0]
-            G = np.zeros((len(nodes), m, 4 * m + 1))
-            V = np.zeros((len(nodes), 4 * m + 1))
+            ly = int(self.ylen[nodes[0]])
+            rows = []
+            V = np.zeros((len(nodes), ly + 2 * m))
             for a, i in enumerate(nodes):
                 ch = tr.children[i]
-                _, E = conic_risk_data(tr.prob[ch], self.avar_level[i])
-                G[a] = np.hstack([E.T, -np.eye(m), -np.eye(m)])
+                _, E, F = self._risk_data(i)
+                Gi = np.hstack([E.T, -np.eye(m), -np.eye(m)])
+                if F.shape[1]:
+                    Gi = np.vstack([Gi, np.hstack([F.T, np.zeros((F.shape[1], 2 * m))])])
+                rows.append(Gi)
                 V[a] = np.concatenate([y[self.yoff[i]:self.yoff[i + 1]], tau[ch - 1], s[ch - 1]])
+            G = np.stack(rows)
             Gv = np.einsum("akj,aj->ak", G, V)
             lam = np.linalg.solve(G @ np.transpose(G, (0, 2, 1)), Gv[:, :, None])[:, :, 0]
             PV = V - np.einsum("akj,ak->aj", G, lam)
             for a, i in enumerate(nodes):
                 ch = tr.children[i]
-                y2[self.yoff[i]:self.yoff[i + 1]] = PV[a, :2 * m + 1]
-                tau2[ch - 1] = PV[a, 2 * m + 1:3 * m + 1]
-                s2[ch - 1] = PV[a, 3 * m + 1:]
+                y2[self.yoff[i]:self.yoff[i + 1]] = PV[a, :ly]
+                tau2[ch - 1] = PV[a, ly:ly + m]
+                s2[ch - 1] = PV[a, ly + m:]
         return y2, tau2, s2
 
     # -- linear operator L (Sec. 4.4) --------------------------------------
+    def _risk_data(self, i):
+        """b, E, F of node i's conic risk (Sec. 3.3): AV@R with the node's level
+        (F absent: an empty matrix), or the total-variation ball of radius tv[i]."""
+        ch = self.tree.children[i]
+        if self.tv is not None:
+            b, E, F, _ = conic_risk_data_tv(self.tree.prob[ch], self.tv[i])
+            return b, E, F
+        b, E = conic_risk_data(self.tree.prob[ch], self.avar_level[i])
+        return b, E, np.zeros((E.shape[0], 0))
+
     def _build_L(self):
         """L as an explicit sparse matrix, block by block as defined in Sec. 4.4:
         ((y^i, s^i - b^i'y^i, Gx x^i + Gu u^i)_{non-leaf i},
@@ -591,7 +655,7 @@ class Oracle:
 
         for i in range(tr.n_nl):
             ch = tr.children[i]
-            b, _ = conic_risk_data(tr.prob[ch], self.avar_level[i])
+            b, _, _ = self._risk_data(i)
             L_ = self.ylen[i]
             add_block(lay.e_y + self.yoff[i], lay.o_y + self.yoff[i], np.eye(L_))
             r = lay.e_s + i
@@ -978,7 +1042,8 @@ class Oracle:
         """Cost-to-go V^i of a trajectory under the nested risk (Eq.
         original-problem) with the original (unscaled) costs, and the
         maximising conditional weights mu^c of every non-root node (the
-        AV@R maximiser over the children of its ancestor, Sec. 3.3-3.4)."""
+        maximiser of the node's risk, AV@R or the total-variation ball, over
+        the children of its ancestor, Sec. 3.3-3.4)."""
         P, tr = self.P, self.tree
         V = np.zeros(tr.n)
         mu = np.zeros(tr.n)
@@ -993,8 +1058,12 @@ class Oracle:
                 for c in ch:
                     Z.append(self.edge_cost(c, x[i], u[i]) + V[c])
                 Z = np.asarray(Z)
-                V[i] = avar(Z, tr.prob[ch], self.avar_level[i])
-                mu[ch] = avar_maximiser(Z, tr.prob[ch], self.avar_level[i])
+                if self.tv is not None:
+                    V[i] = tv_risk(Z, tr.prob[ch], self.tv[i])
+                    mu[ch] = tv_maximiser(Z, tr.prob[ch], self.tv[i])
+                else:
+                    V[i] = avar(Z, tr.prob[ch], self.avar_level[i])
+                    mu[ch] = avar_maximiser(Z, tr.prob[ch], self.avar_level[i])
         return V, mu
 
     def path_weights(self, x, u):

@@ -72,6 +72,10 @@ class RAOCP:
     gN_hi: Optional[np.ndarray] = None
     l1: Optional[float] = None          # lambda_0 >= 0 of an l1 term lambda_0 ||(x^anc, u^anc)||_1 added
                                         # to every edge cost (Prop. 2); None or 0 = none
+    tv: Optional[np.ndarray] = None     # float64 [n_nonleaf] radius r >= 0: the risk of every non-leaf node
+                                        # is then the worst expectation over {mu in the simplex :
+                                        # ||mu - p||_1 <= r} (a conic risk with F != 0, Sec. 3.3)
+                                        # instead of AV@R; None = AV@R with the levels in avar
 
     @property
     def n(self) -> int:

@@ -948,3 +948,129 @@ def test_l1_problem_diagnostics_vanish():
     assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
     assert r["infeas"] < 1e-6 and r["gap"] < 1e-5
     assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * max(1.0, abs(r["risk"]))
+
+
+# --- a conic risk with F != 0: the total-variation ball (Sec. 3.3) ----------------------
+
+
+def _with_tv(p, r):
+    p.tv = np.full(p.n_nonleaf, float(r))
+    return p
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tv_risk_vs_lp_and_conic_primal_and_dual(seed):
+    """The closed form of the total-variation risk = max mu'Z over the ball
+    (LP in (mu, nu)) = the conic primal max{mu'Z : b - E mu - F nu in K} with
+    the b, E, F of conic_risk_data_tv = the conic dual min{y'b : E'y = Z,
+    F'y = 0, y in K*} (Eq. primal_risk and dual_risk, F != 0)."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 6))
+    Z = rng.standard_normal(n)
+    p = rng.dirichlet(np.ones(n))
+    r = float(rng.choice([0.0, rng.uniform(0.05, 1.0), 2.5]))
+    val = so_.tv_risk(Z, p, r)
+    # LP: max mu'Z, sum mu = 1, mu >= 0, -nu <= mu - p <= nu, sum nu <= r
+    c = np.concatenate([-Z, np.zeros(n)])
+    A_ub = np.vstack([np.hstack([np.eye(n), -np.eye(n)]), np.hstack([-np.eye(n), -np.eye(n)]),
+                      np.concatenate([np.zeros(n), np.ones(n)])[None, :]])
+    b_ub = np.concatenate([p, -p, [r]])
+    lp = so.linprog(c, A_ub=A_ub, b_ub=b_ub, A_eq=np.concatenate([np.ones(n), np.zeros(n)])[None, :],
+                    b_eq=[1.0], bounds=[(0, None)] * n + [(None, None)] * n, method="highs")
+    assert lp.status == 0 and abs(-lp.fun - val) < 1e-10
+    b, E, F, npos = so_.conic_risk_data_tv(p, r)
+    # conic primal: b - E mu - F nu >= 0 on the first npos rows, = 0 on the last
+    Ak = np.hstack([E, F])
+    prim = so.linprog(np.concatenate([-Z, np.zeros(n)]), A_ub=Ak[:npos], b_ub=b[:npos],
+                      A_eq=Ak[npos:], b_eq=b[npos:], bounds=[(None, None)] * (2 * n), method="highs")
+    assert prim.status == 0 and abs(-prim.fun - val) < 1e-9
+    dual = so.linprog(b, A_eq=np.vstack([E.T, F.T]), b_eq=np.concatenate([Z, np.zeros(n)]),
+                      bounds=[(0, None)] * npos + [(None, None)] * (len(b) - npos), method="highs")
+    assert dual.status == 0 and abs(dual.fun - val) < 1e-9
+    assert abs(so_.tv_risk(Z, p, 0.0) - p @ Z) < 1e-14
+    assert abs(so_.tv_risk(Z, p, 2.0) - Z.max()) < 1e-14
+
+
+def test_proj_S2_with_F_vs_nullspace_basis():
+    """With the total-variation risk S2^i = ker[E', -I, -I; F', 0, 0]: the
+    projection equals N N' v for an orthonormal basis N of that kernel (SVD)."""
+    p = _with_tv(constrained([3, 2, 1], 2, 1, seed=5, avar=0.5), 0.6)
+    o = Oracle(p)
+    rng = np.random.default_rng(6)
+    z = rng.standard_normal(o.lay.n_z)
+    s0, x, u, y, tau, s = o.split_z(z)
+    y2, tau2, s2 = o.proj_S2(y, tau, s)
+    tr = o.tree
+    for i in range(tr.n_nl):
+        ch = tr.children[i]
+        m = len(ch)
+        I, O = np.eye(m), np.zeros((m, m))
+        Et = np.hstack([I, -I, np.zeros((m, 1)), -I, np.ones((m, 1))])     # E'
+        Ft = np.hstack([-I, -I, np.ones((m, 1)), O, np.zeros((m, 1))])     # F'
+        G = np.vstack([np.hstack([Et, -I, -I]), np.hstack([Ft, O, O])])
+        Nb = sla.null_space(G)
+        v = np.concatenate([y[o.yoff[i]:o.yoff[i + 1]], tau[ch - 1], s[ch - 1]])
+        got = np.concatenate([y2[o.yoff[i]:o.yoff[i + 1]], tau2[ch - 1], s2[ch - 1]])
+        assert np.allclose(got, Nb @ (Nb.T @ v), atol=1e-12)
+
+
+def test_tv_radius_zero_is_risk_neutral_qp():
+    """A total-variation ball of radius 0 is the expectation: the oracle's
+    solution with the tv risk equals the risk-neutral QP (value; trajectory on
+    the likely nodes), through the y-blocks, S2 with F and the zero cone."""
+    p = _with_tv(general([2, 2, 1], 3, 2, seed=57), 0.0)
+    o = Oracle(p)
+    r = o.solve(tol=1e-9, max_iters=40000)
+    V, X, U = _risk_neutral_qp_general(p)
+    assert abs(r["risk"] - V) < 1e-7 * max(1.0, abs(V))
+    _check_on_likely_nodes(o, r, X, U, 1e-5)
+
+
+def test_one_stage_two_children_tv_bruteforce():
+    """N = 1, two children, total-variation radius 0.5, no constraints:
+    V* = max over the ball (a segment mu_1 in [p_1 - r/2, p_1 + r/2]) of the
+    inner LQ minimum, by golden section."""
+    p = _with_tv(unconstrained([2], 2, 2, seed=16, avar=1.0), 0.5)
+    o = Oracle(p)
+    r = o.solve(tol=1e-10, max_iters=50000, method="spock")
+    x0 = p.x0
+    pr = p.prob[1:]
+
+    def phi(m1):
+        mu = np.array([m1, 1 - m1])
+        H = np.zeros((p.nu, p.nu)); g = np.zeros(p.nu); const = 0.0
+        for j in range(2):
+            A, B = p.A[j], p.B[j]
+            QN = np.diag(p.QN[j])
+            H += mu[j] * (np.diag(p.R[j]) + B.T @ QN @ B)
+            g += mu[j] * (B.T @ QN @ A @ x0)
+            const += mu[j] * (x0 @ np.diag(p.Q[j]) @ x0 + (A @ x0) @ QN @ (A @ x0))
+        u = -np.linalg.solve(H, g)
+        return u @ H @ u + 2 * g @ u + const
+
+    lo, hi = max(0.0, pr[0] - 0.25), min(1.0, pr[0] + 0.25)
+    gr = (math.sqrt(5) - 1) / 2
+    x1, x2 = hi - gr * (hi - lo), lo + gr * (hi - lo)
+    f1, f2 = phi(x1), phi(x2)
+    for _ in range(200):
+        if f1 > f2:
+            hi, x2, f2 = x2, x1, f1
+            x1 = hi - gr * (hi - lo); f1 = phi(x1)
+        else:
+            lo, x1, f1 = x1, x2, f2
+            x2 = lo + gr * (hi - lo); f2 = phi(x2)
+    V = max(phi(lo), phi(hi), f1, f2)
+    assert abs(r["risk"] - V) < 1e-7 * max(1.0, abs(V))
+
+
+def test_tv_problem_diagnostics_vanish():
+    """Total-variation radius 0.4 with boxes and a ball: residual, xi1, xi2,
+    infeasibility and the complementarity gap vanish, and s0 equals the nested
+    total-variation risk of the trajectory."""
+    p = _with_tv(constrained([3, 2, 1], 3, 2, seed=58, avar=0.5, uball=1.5), 0.4)
+    o = Oracle(p)
+    r = o.solve(tol=1e-8, max_iters=40000)
+    assert r["res_inf"] <= 1e-8
+    assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
+    assert r["infeas"] < 1e-6 and r["gap"] < 1e-5
+    assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * max(1.0, abs(r["risk"]))
