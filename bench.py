@@ -759,8 +759,10 @@ def main():
         spock.load()
         p = synth.large_raocp()
         g = spock.Problem(p)
-        r = g.solve(p.x0, spock.opts(precision=args.precision, tol=0.0,
-                                      max_iters=args.profile_iters, fp64_check=False))
+        # the plain iteration (one launch of the iteration kernel for all of
+        # its T evaluations), so that a capture of that launch divides by a known T count
+        r = g.solve(p.x0, spock.opts(precision=args.precision, tol=0.0, max_iters=args.profile_iters,
+                                      fp64_check=False, recentre=0.0 if args.precision == 32 else None))
         print(json.dumps({"n_T": r["info"]["n_T"], "iters": r["info"]["iters"],
                           "n_T_iteration_kernel": r["info"]["n_T"] - r["info"]["n_recentre"],
                           "centres": r["info"]["n_recentre"],

@@ -124,6 +124,13 @@ typedef struct spock_problem_desc {
                                 lambda - z, lambda + z in R_+ appended to eta. Single-problem
                                 calls only: the batched and serving calls return
                                 SPOCK_EUNSUPPORTED for such a problem */
+    const double* tv;        /* [n_nl] radius r >= 0, or NULL. Non-NULL: the risk of every non-leaf
+                                node is the worst expectation over the total-variation ball
+                                {mu in the simplex : ||mu - p||_1 <= r} around its children's
+                                probabilities (r = 0: the expectation; r >= 2: the maximum), a
+                                conic risk with F != 0 (Sec. 3.3: nu >= |mu - p|, y^i of 3 n_i + 2
+                                entries, S2^i = ker[E', -I, -I; F', 0, 0]); avar is then unused.
+                                Single-problem calls only (as l1) */
 } spock_problem_desc;
 
 typedef struct spock_sizes {

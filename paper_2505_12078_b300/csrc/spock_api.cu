@@ -90,7 +90,7 @@ double mat_norm2(const std::vector<double>& M, int rows, int cols) {
 }
 
 // Validate the tree (Sec. 3.2) and build the node arrays and sweep schedule.
-int build_tree(spock_problem* p, int n, const int* anc, const double* prob) {
+int build_tree(spock_problem* p, int n, const int* anc, const double* prob, int tv) {
   if (n < 2 || !anc || !prob || anc[0] != -1) return SPOCK_EINVAL;
   std::vector<int> stage(n, 0);
   for (int i = 1; i < n; ++i) {
@@ -137,7 +137,7 @@ int build_tree(spock_problem* p, int n, const int* anc, const double* prob) {
   }
   p->stage_off[N + 1] = n;
   p->yoff.assign(n_nl + 1, 0);
-  for (int i = 0; i < n_nl; ++i) p->yoff[i + 1] = p->yoff[i] + 2 * nch[i] + 1;
+  for (int i = 0; i < n_nl; ++i) p->yoff[i + 1] = p->yoff[i] + (tv ? 3 * nch[i] + 2 : 2 * nch[i] + 1);
   p->n_y = p->yoff[n_nl];
   p->ynode.resize(p->n_y);
   for (int i = 0; i < n_nl; ++i)
@@ -261,6 +261,7 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.Gg = it.Gg; P.GgT = it.GgT; P.GgN = it.GgN; P.GgNT = it.GgNT;
   P.gen_lo = it.gen_lo; P.gen_hi = it.gen_hi; P.genN_lo = it.genN_lo; P.genN_hi = it.genN_hi;
   P.alpha = (T)alpha;
+  P.tv = p->tv; P.tvr = it.tvr;
   P.l1 = (T)p->l1; P.o_th = p->o_th; P.o_lam = p->o_lam; P.e_l1 = p->e_l1; P.l1w = it.l1w;
   P.qbuf = it.qbuf; P.dbuf = it.dbuf; P.hbuf = it.hbuf; P.ebuf = it.ebuf;
   P.mbb = it.mbb; P.mbf = it.mbf;
@@ -335,6 +336,7 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
   it.avar = m.alloc<T>(n_nl);
   it.x0s = m.alloc<T>(nx);
   it.l1w = m.alloc<T>(nx + nu);
+  it.tvr = m.alloc<T>(n_nl);
   it.qbuf = m.alloc<T>((long long)n * nx);
   it.dbuf = m.alloc<T>((long long)n_nl * nu);
   it.hbuf = m.alloc<T>((long long)n_nl * nx);
@@ -874,7 +876,7 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   if ((d->x_lo == nullptr) != (d->x_hi == nullptr)) return SPOCK_EINVAL;
   if ((d->u_lo == nullptr) != (d->u_hi == nullptr)) return SPOCK_EINVAL;
   spock_problem* p = new spock_problem();
-  int rc = build_tree(p, d->n_nodes, d->anc, d->prob);
+  int rc = build_tree(p, d->n_nodes, d->anc, d->prob, d->tv ? 1 : 0);
   if (rc) { delete p; return rc; }
   const int n = p->n, n_nl = p->n_nl, n_l = p->n_l, nx = d->nx, nu = d->nu;
   p->nx = nx; p->nu = nu;
@@ -955,6 +957,11 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   }
   if (!(d->l1 >= 0.0) || !isfinite(d->l1)) { delete p; return SPOCK_EINVAL; }
   p->l1 = d->l1;
+  if (d->tv) {
+    p->tv = 1;
+    p->tvr.assign(d->tv, d->tv + n_nl);
+    for (double r : p->tvr) if (!(r >= 0.0) || !isfinite(r)) { delete p; return SPOCK_EINVAL; }
+  }
   p->full = full;
   p->has_lin = (d->q || d->r || d->qN) ? 1 : 0;
   p->n_g = d->n_g;
@@ -1167,6 +1174,7 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   a.MB = f.MB; a.MF = f.MF; a.MP = f.MP; a.KT = f.KT; a.Pc = dPcs; a.kc = f.kc;
   a.qh = f.qh; a.rh = f.rh; a.qNh = f.qNh; a.gx = f.gx; a.gu = f.gu; a.gN = f.gN;
   a.box_lo = f.box_lo; a.box_hi = f.box_hi; a.boxN_lo = f.boxN_lo; a.boxN_hi = f.boxN_hi; a.ball = f.ball;
+  a.ys_block = p->tv ? 0 : 1;
   a.xu_shift = (p->l1 > 0) ? 2.0 : 0.0;   // the l1 rows add 2 I to every (x^i, u^i) block of L'L
   cudaStream_t st = 0;
   cudaError_t e = launch_scale_dyn(a, st);
@@ -1278,6 +1286,20 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
     }
     if (cudaMemcpy(p->f64.l1w, w64.data(), w64.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->f32.l1w, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      m.free_all(); delete p; return SPOCK_EDEVICE;
+    }
+  }
+  if (p->tv) {
+    // the (y^i, s^i) block of L'L, [I + b b', -b; -b', 1]: 1 + beta/2 + sqrt(beta + beta^2/4),
+    // beta = ||b||^2 = 2 ||p||^2 + r^2 + 1 for the total-variation risk
+    for (int i = 0; i < n_nl; ++i) {
+      double beta = 1.0 + p->tvr[(size_t)i] * p->tvr[(size_t)i];
+      for (int c = p->ch_off[i]; c < p->ch_off[i + 1]; ++c) beta += 2.0 * d->prob[c] * d->prob[c];
+      l2 = std::max(l2, 1.0 + 0.5 * beta + sqrt(beta + 0.25 * beta * beta));
+    }
+    std::vector<float> r32(p->tvr.begin(), p->tvr.end());
+    if (cudaMemcpy(p->f64.tvr, p->tvr.data(), (size_t)n_nl * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->f32.tvr, r32.data(), (size_t)n_nl * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
       m.free_all(); delete p; return SPOCK_EDEVICE;
     }
   }

@@ -126,6 +126,12 @@ struct Prob {
   // lambda_k, lambda - (x^i, u^i), lambda + (x^i, u^i), all in R_+, at
   // e_l1 + i (1 + 2 (nx + nu)) in eta; the cost cone of every child c of i
   // carries (tau^c - l1 theta^i)/2 in its last two entries.
+  // Risk of the non-leaf nodes (Sec. 3.3): tv = 0: AV@R with the levels in
+  // avar, y^i = 2 m + 1 entries, b = [p; 0; 1]; tv = 1: the total-variation
+  // ball of radius tvr[i], y^i = 3 m + 2 entries [y1 | y2 | y3 | y4 | y5] (m, m,
+  // 1, m, 1), b = [p; -p; r; 0; 1], every entry but the last in R_+.
+  int tv;
+  const T* tvr;
   T l1;
   long long o_th, o_lam, e_l1;
   const T* l1w;   // [nx + nu] 1/S^x, 1/S^u
@@ -138,6 +144,21 @@ struct Prob {
   unsigned long long* mbb;
   unsigned long long* mbf;
 };
+
+// entry k of b^i (conic risk data of node i with m children, first child c0)
+template <class T>
+__device__ __forceinline__ T risk_b(const Prob<T>& P, int i, int c0, int m, int k) {
+  if (!P.tv) return (k < m) ? P.prob[c0 + k] : (k == 2 * m ? T(1) : T(0));
+  if (k < m) return P.prob[c0 + k];
+  if (k < 2 * m) return -P.prob[c0 + k - m];
+  if (k == 2 * m) return P.tvr[i];
+  return (k == 3 * m + 1) ? T(1) : T(0);
+}
+// entries of y^i in R_+ (the rest, the last entry, is free: the zero cone's dual)
+template <class T>
+__device__ __forceinline__ int risk_npos(const Prob<T>& P, int m) {
+  return P.tv ? 3 * m + 1 : 2 * m;
+}
 
 // ---------------------------------------------------------------------------
 // memory helpers: data written inside a kernel is read through L2 (ld.cg) so a

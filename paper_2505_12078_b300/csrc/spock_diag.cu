@@ -107,9 +107,10 @@ __global__ void k_S3_diag(Prob<double> P, const double* __restrict__ lz, const d
       const int i = (int)b;
       const int m = P.ch_off[i + 1] - P.ch_off[i];
       const long long ye = P.e_y + P.yoff[i];
-      for (int e = lane; e < 2 * m + 1; e += 32) {        // (K^i)* = R^{2m}_+ x R
+      const int ly = (int)(P.yoff[i + 1] - P.yoff[i]), npos = risk_npos(P, m);
+      for (int e = lane; e < ly; e += 32) {                 // (K^i)* = R^{npos}_+ x R
         const double x = lz[ye + e];
-        const double p = (e < 2 * m) ? fmax(x, 0.0) : x;
+        const double p = (e < npos) ? fmax(x, 0.0) : x;
         inf = fmax(inf, fabs(x - p));
         dot += ep[ye + e] * x;
       }

@@ -379,7 +379,7 @@ __global__ void k_cost_con(int n, int n_nl, int nx, int nu, int nbx, int nbu, in
 }
 
 // ||L||^2 as the max over the diagonal-Gram blocks of L (see file header)
-__global__ void k_norm_L(int n, int n_nl, int nx, int nu, int nbx, int nub, double xu_shift,
+__global__ void k_norm_L(int n, int n_nl, int nx, int nu, int nbx, int nub, double xu_shift, int ys_block,
                          const int* __restrict__ ch_off, const double* __restrict__ prob,
                          const double* __restrict__ qh, const double* __restrict__ rh,
                          const double* __restrict__ qNh, const double* __restrict__ gx,
@@ -399,9 +399,11 @@ __global__ void k_norm_L(int n, int n_nl, int nx, int nu, int nbx, int nub, doub
         for (int c = c0; c < c1; ++c) s += rh[(long long)(c - 1) * nu + k] * rh[(long long)(c - 1) * nu + k];
         lam = fmax(lam, s);
       }
-      double beta = 1.0;
-      for (int c = c0; c < c1; ++c) beta += prob[c] * prob[c];
-      lam = fmax(lam, 1.0 + 0.5 * beta + sqrt(beta + 0.25 * beta * beta));
+      if (ys_block) {   // AV@R's (y, s) block, beta = ||b||^2 (other risks: on the host)
+        double beta = 1.0;
+        for (int c = c0; c < c1; ++c) beta += prob[c] * prob[c];
+        lam = fmax(lam, 1.0 + 0.5 * beta + sqrt(beta + 0.25 * beta * beta));
+      }
     } else {
       const int j = i - n_nl;
       for (int k = 0; k < nx; ++k) {
@@ -437,8 +439,8 @@ __global__ void k_apply_L(Prob<T> P, const int* __restrict__ ynode, const T* __r
       const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
       const T* y = z + P.o_y + P.yoff[i];
       T s = (i == 0) ? z[0] : z[P.o_s + i - 1];
-      for (int k = 0; k < m; ++k) s -= P.prob[c0 + k] * y[k];
-      s -= y[2 * m];
+      const int ly = (int)(P.yoff[i + 1] - P.yoff[i]);
+      for (int k = 0; k < ly; ++k) s -= risk_b(P, i, c0, m, k) * y[k];
       v = s;
     } else if (e < P.e_q) {                // constraint rows of non-leaf nodes
       const long long f = e - P.e_c;
@@ -593,8 +595,7 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
       const int i = ynode[f];
       const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
       const int k = (int)(f - P.yoff[i]);
-      T b = (k < m) ? P.prob[c0 + k] : (k == 2 * m ? T(1) : T(0));
-      v = ey[f] - b * es[i];
+      v = ey[f] - risk_b(P, i, c0, m, k) * es[i];
     } else if (e < P.o_s) {                // tau^c
       const long long cm1 = e - P.o_tau;
       v = T(0.5) * (eq[cm1 * P.W + nx + nu] + eq[cm1 * P.W + nx + nu + 1]);
@@ -674,7 +675,7 @@ cudaError_t launch_build(const SetupArgs& a, cudaStream_t s) {
 
 cudaError_t launch_norm_L(const SetupArgs& a, unsigned long long* out, cudaStream_t s) {
   k_norm_L<<<grid_for(a.n, 128), 128, 0, s>>>(a.n, a.n_nl, a.nx, a.nu, a.nbx,
-                                                (a.nbu ? 1 : 0) + (a.has_ball ? 1 : 0), a.xu_shift, a.ch_off,
+                                                (a.nbu ? 1 : 0) + (a.has_ball ? 1 : 0), a.xu_shift, a.ys_block, a.ch_off,
                                                 a.prob, a.qh, a.rh, a.qNh, a.gx, a.gu, a.gN, out);
   return cudaGetLastError();
 }

@@ -142,6 +142,85 @@ __device__ void s2_block(const Prob<T>& P, int lane, int i, const T* __restrict_
   }
 }
 
+// S2 with the total-variation risk (F != 0): projection of (y, tau^[i], s^[i])
+// on ker G, G = [E', -I, -I; F', 0, 0], y = [y1 | y2 | y3 | y4 | y5]. E'E = 3I +
+// 11', F'F = 2I + 11', E'F = 0, so GG' = blockdiag(5I + 11', 2I + 11') and
+// both blocks invert in closed form (Sherman-Morrison):
+//   g_E = y1 - y2 - y4 + y5 1 - tau - s,  g_F = -y1 - y2 + y3 1,
+//   l_E = (g_E - 1 (1'g_E)/(5 + m))/5,   l_F = (g_F - 1 (1'g_F)/(2 + m))/2,
+//   y1 -= l_E - l_F, y2 += l_E + l_F, y3 -= 1'l_F, y4 += l_E, y5 -= 1'l_E,
+//   tau += l_E, s += l_E.
+template <class T>
+__device__ void s2_block_tv(const Prob<T>& P, int lane, int i, const T* __restrict__ vin,
+                            T* __restrict__ vout, const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
+  const long long yo = P.o_y + P.yoff[i];
+  const T al = P.alpha;
+  const T eS = ldc(eta + P.e_s + i);
+  const T* ey = eta + P.e_y + P.yoff[i];
+  auto wy = [&](int k) -> T { return ldc(z + yo + k) - al * (ldc(ey + k) - risk_b(P, i, c0, m, k) * eS); };
+  auto wt = [&](int l) -> T {
+    const T* q = eta + P.e_q + (long long)(c0 + l - 1) * P.W;
+    T g = T(0.5) * (ldc(q + nx + nu) + ldc(q + nx + nu + 1));
+    return ldc(z + P.o_tau + c0 + l - 1) - al * g;
+  };
+  auto ws = [&](int l) -> T {
+    const int c = c0 + l;
+    T g;
+    if (c < P.n_nl) {
+      g = ldc(eta + P.e_s + c);
+    } else {
+      const T* q = eta + P.e_qN + (long long)(c - P.n_nl) * (nx + 2);
+      g = T(0.5) * (ldc(q + nx) + ldc(q + nx + 1));
+    }
+    return ldc(z + P.o_s + c - 1) - al * g;
+  };
+  const T y3 = wy(2 * m), y5 = wy(3 * m + 1);
+  T sE = 0, sF = 0;
+  for (int l = lane; l < m; l += 32) {
+    const T y1 = wy(l), y2 = wy(m + l), y4 = wy(2 * m + 1 + l);
+    sE += y1 - y2 - y4 + y5 - wt(l) - ws(l);
+    sF += y3 - y1 - y2;
+  }
+  sE = warp_sum(sE);
+  sF = warp_sum(sF);
+  const T cE = sE / (T(5) + T(m)), cF = sF / (T(2) + T(m));
+  T tE = 0, tF = 0;
+  auto put = [&](long long idx, T val) {
+    const T o = ldc(z + idx), nv = zc_add(P, idx, val);
+    stc(vout + idx, nv);
+    ra.z(o, nv, dirv(vref, idx));
+  };
+  for (int l = lane; l < m; l += 32) {
+    const T y1 = wy(l), y2 = wy(m + l), y4 = wy(2 * m + 1 + l), wtl = wt(l), wsl = ws(l);
+    const T lE = ((y1 - y2 - y4 + y5 - wtl - wsl) - cE) / T(5);
+    const T lF = ((y3 - y1 - y2) - cF) / T(2);
+    tE += lE;
+    tF += lF;
+    const int c = c0 + l;
+    put(yo + l, y1 - lE + lF);
+    put(yo + m + l, y2 + lE + lF);
+    put(yo + 2 * m + 1 + l, y4 + lE);
+    put(P.o_tau + c - 1, wtl + lE);
+    put(P.o_s + c - 1, wsl + lE);
+  }
+  tE = warp_sum(tE);
+  tF = warp_sum(tF);
+  if (lane == 0) {
+    put(yo + 2 * m, y3 - tF);
+    put(yo + 3 * m + 1, y5 - tE);
+    if (i == 0) {   // s0 <- s0 - alpha (eta_s^0) - alpha (the last term is constant: not in the linear part)
+      const T o0 = ldc(z);
+      const T n0 = zc_add(P, 0, P.lin ? (o0 - al * eS) : (o0 - al * eS) - al);
+      stc(vout, n0);
+      ra.z(o0, n0, dirv(vref, 0));
+    }
+  }
+}
+
 // The auxiliaries of the l1 edge costs of node i (Prop. 2): f does not
 // involve them, so their step is w = z - alpha L*eta. L* of theta^i: its l1
 // row minus lambda_0/2 times the last two entries of every child's cost cone;
@@ -243,7 +322,8 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
     if (j < nx) stc(hb + j, (-s - s_xb[j]) + ldr(kc + j));
     else stc(eb + (j - nx), s - ldr(kc + j));
   });
-  s2_block(P, tw1.lane, i, vin, vout, vref, ra);
+  if (P.tv) s2_block_tv(P, tw1.lane, i, vin, vout, vref, ra);
+  else s2_block(P, tw1.lane, i, vin, vout, vref, ra);
   if (P.l1 != T(0)) l1_prep(P, tw1.lane, i, vin, vout, vref, ra);
 }
 
@@ -695,12 +775,13 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
   const T al = P.alpha;
   const long long yo = P.o_y + P.yoff[i];
   const long long ye = P.e_y + P.yoff[i];
-  // y part: (K^i)* = R^{2m}_+ x R
-  for (int e = lane; e < 2 * m + 1; e += 32) {
+  // y part: (K^i)* = R^{npos}_+ x R (AV@R: npos = 2m; total variation: 3m + 1)
+  const int ly = (int)(P.yoff[i + 1] - P.yoff[i]), npos = risk_npos(P, m);
+  for (int e = lane; e < ly; e += 32) {
     const T Lo = ldc(z + yo + e), Ln = ldc(vout + yo + e);
     const T eo_ = ldc(eta + ye + e);
     const T eb = eo_ + al * (T(2) * Ln - Lo);
-    const bool cone = e < 2 * m;
+    const bool cone = e < npos;
     const T en = eta_prox(P, ye + e, eb, [&](auto w) { return cone ? max(w, decltype(w)(0)) : w; });
     stc(eo + ye + e, en);
     ra.eta(eo_, en, er ? ldc(er + ye + e) : T(0), Lo - Ln, dirv(vref, yo + e));
@@ -708,8 +789,8 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
   // s part: s^i - b'y^i in R_+
   {
     T bo = 0, bn = 0, bd = 0, brd = 0;   // b'y of old and new, b'(y_old - y_new), b'(direction y)
-    for (int k = lane; k < m; k += 32) {
-      const T p = P.prob[c0 + k];
+    for (int k = lane; k < ly; k += 32) {
+      const T p = risk_b(P, i, c0, m, k);
       const T o = ldc(z + yo + k), nn = ldc(vout + yo + k);
       bo += p * o;
       bn += p * nn;
@@ -719,13 +800,12 @@ __device__ void eta_nonleaf(const Prob<T>& P, int lane, int i, const T* __restri
     bo = warp_sum(bo); bn = warp_sum(bn); bd = warp_sum(bd); brd = warp_sum(brd);
     if (lane == 0) {
       const long long is = (i == 0) ? 0 : P.o_s + i - 1;
-      const T yo3 = ldc(z + yo + 2 * m);
       const T so = ldc(z + is);
-      const T sn = ldc(vout + is), yn3 = ldc(vout + yo + 2 * m);
-      const T Lo = so - bo - yo3;
-      const T Ln = sn - bn - yn3;
-      const T lrz = (so - sn) - bd - (yo3 - yn3);
-      const T lod = vref ? ldc(vref + is) - brd - ldc(vref + yo + 2 * m) : T(0);
+      const T sn = ldc(vout + is);
+      const T Lo = so - bo;
+      const T Ln = sn - bn;
+      const T lrz = (so - sn) - bd;
+      const T lod = vref ? ldc(vref + is) - brd : T(0);
       const long long ie = P.e_s + i;
       const T eo_ = ldc(eta + ie);
       const T eb = eo_ + al * (T(2) * Ln - Lo);

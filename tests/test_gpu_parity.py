@@ -55,7 +55,15 @@ CASES = {
     # ball; team sweeps with diagonal weights
     "l1_box_ball": lambda: _with_l1(_with_ball(general([2, 2, 1], 5, 3, seed=66, avar=0.5, box=True), 1.5), 0.3),
     "l1_team_100x50": lambda: _with_l1(constrained([2, 1], 100, 50, seed=67, avar=0.5, uball=3.0), 0.2),
+    # the total-variation risk (a conic risk with F != 0, Sec. 3.3): whole-CTA and team sweeps
+    "tv_box_ball": lambda: _with_tv(constrained([3, 2, 1], 6, 3, seed=68, avar=0.5, uball=2.0), 0.4),
+    "tv_team_100x50": lambda: _with_tv(constrained([2, 1], 100, 50, seed=69, avar=0.5), 0.3),
 }
+
+
+def _with_tv(p, r):
+    p.tv = np.full(p.n_nonleaf, float(r))
+    return p
 
 
 def _with_l1(p, lam):
@@ -233,7 +241,7 @@ def test_fixed_iterations_cp_fp64(name):
 
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "team_100x50",
                                   "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "full_rows_100x50",
-                                  "l1_box_ball", "l1_team_100x50"])
+                                  "l1_box_ball", "l1_team_100x50", "tv_box_ball", "tv_team_100x50"])
 def test_fixed_iterations_spock_fp64(name):
     """SPOCK (Alg. 4 with Anderson directions) for a fixed iteration count in
     FP64: same branch sequence counts and iterate within 1e-10 relative."""
@@ -257,7 +265,7 @@ def test_fixed_iterations_spock_fp64(name):
 @pytest.mark.parametrize("name,recentre", [("small", 0.1), ("ragged_37x19_ball", 0.1), ("chain_only", 0.1),
                                            ("full_lin_box", 0.1), ("rows_ball_diag_lin", 0.1),
                                            ("team_100x50", 0.1), ("small", 0.0), ("ragged_37x19_ball", 0.0),
-                                           ("l1_box_ball", 0.1), ("l1_box_ball", 0.0)])
+                                           ("l1_box_ball", 0.1), ("l1_box_ball", 0.0), ("tv_box_ball", 0.1)])
 def test_converged_fp32_vs_oracle(name, recentre):
     """FP32 iteration to ||v - T(v)||_inf <= 1e-4 against the optimum: the
     oracle's FP64 solve to 1e-7 (tests/golden/converged_cases.json, written by
@@ -280,7 +288,8 @@ def test_converged_fp32_vs_oracle(name, recentre):
 
 
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "avar0_branch8",
-                                  "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "l1_box_ball"])
+                                  "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "l1_box_ball",
+                                  "tv_box_ball"])
 def test_fp64_check_matches_oracle(name):
     """FP64 exit check (Sec. 5.3) through spock_check on the oracle's own
     iterate after 25 SPOCK iterations: xi1, xi2 (Eq. xi1k), the primal
@@ -371,12 +380,14 @@ def test_converged_fp32_qr_update(name):
     assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= ref["tol_u"]
 
 
-def test_l1_costs_are_single_problem_only():
-    """A problem with l1 edge costs (Prop. 2) is solved by the single-problem
-    calls; the batched and serving calls refuse it with SPOCK_EUNSUPPORTED
-    (-6) instead of running paths that do not carry its auxiliaries."""
+@pytest.mark.parametrize("name", ["l1_box_ball", "tv_box_ball"])
+def test_extended_problems_are_single_problem_only(name):
+    """A problem with l1 edge costs (Prop. 2) or total-variation risks is
+    solved by the single-problem calls; the batched and serving calls refuse it
+    with SPOCK_EUNSUPPORTED (-6) instead of running paths that do not carry its
+    auxiliaries or its risk data."""
     spock = _spock()
-    p = CASES["l1_box_ball"]()
+    p = CASES[name]()
     g = spock.Problem(p)
     with pytest.raises(spock.SpockError) as e:
         spock.Batch([g], precision=32)
