@@ -289,6 +289,8 @@ class Oracle:
                    (nu if self.has_uball else 0) + self.n_g
         self.n_cN = (nx if self.has_xbox else 0) + self.n_gN
         self.l1 = float(getattr(prob, "l1", None) or 0.0)
+        sm = getattr(prob, "soft_max", None)
+        self.soft = None if sm is None else np.asarray(sm, dtype=np.float64)
         self._layout()
         self._precondition()
         self._offline_s1()
@@ -327,6 +329,15 @@ class Oracle:
         if self.l1:
             n_z = self.o_lam + n_nl * (nx + nu)
             n_eta = self.e_l1 + n_nl * (1 + 2 * (nx + nu))
+        # soft-constraint costs (after Prop. 2): sigma^i and theta^i (nx + nu)
+        # per non-leaf node next in z; per non-leaf node the rows
+        # [theta/s, sigma/2, sigma/2] - a in SOC, theta >= 0, theta - z >= -s z_max
+        self.o_sg = n_z
+        self.o_sth = n_z + (n_nl if self.soft is not None else 0)
+        self.e_sf = n_eta
+        if self.soft is not None:
+            n_z = self.o_sth + n_nl * (nx + nu)
+            n_eta = self.e_sf + n_nl * (3 * (nx + nu) + 2)
         self.lay = Layout(n_y, n_z, n_eta, o_x, o_u, o_y, o_tau, o_s,
                           e_y, e_s, e_c, e_q, e_cN, e_qN)
         # entries of eta_y that lie in R_+ (all but the last entry of each block:
@@ -705,6 +716,27 @@ class Oracle:
                 add_block(r0 + 1 + d, ol, np.eye(d))
                 add_block(r0 + 1 + d, lay.o_x + i * nx, np.eye(d)[:, :nx])
                 add_block(r0 + 1 + d, lay.o_u + i * nu, np.eye(d)[:, nx:])
+        if self.soft is not None:
+            # the penalty ||max(0, z - z_max)||^2 of every child's edge cost is the
+            # same function of node i's z = (x^i, u^i): tau^c - sigma^i replaces
+            # tau^c in every child's cone, sigma^i >= ||theta^i||^2 (a cone of its
+            # own, Prop. 1 with Q = I), theta^i >= 0, theta^i >= z - z_max; theta is
+            # kept scaled like z (theta~_k = s_k theta_k)
+            d = nx + nu
+            for c in range(1, n):
+                base = lay.e_q + (c - 1) * w
+                add_block(base + nx + nu, self.o_sg + tr.anc[c], np.array([[-0.5], [-0.5]]))
+            for i in range(tr.n_nl):
+                sc = np.concatenate([self.Snode[i], self.Su])
+                r0 = self.e_sf + i * (3 * d + 2)
+                ot = self.o_sth + i * d
+                add_block(r0, ot, np.diag(1.0 / sc))
+                add_block(r0 + d, self.o_sg + i, np.array([[0.5], [0.5]]))
+                add_block(r0 + d + 2, ot, np.eye(d))
+                add_block(r0 + 2 * d + 2, ot, np.eye(d))
+                add_block(r0 + 2 * d + 2, lay.o_x + i * nx, -np.eye(d)[:, :nx])
+                add_block(r0 + 2 * d + 2, lay.o_u + i * nu, -np.eye(d)[:, nx:])
+            self.soft_lo = -np.concatenate([self.Snode[0], self.Su]) * self.soft   # scaled -s z_max
         rows = np.concatenate(rows); cols = np.concatenate(cols); vals = np.concatenate(vals)
         self.L = sp.csr_matrix((vals, (rows, cols)), shape=(lay.n_eta, lay.n_z))
         self.LT = self.L.T.tocsr()
@@ -779,7 +811,16 @@ class Oracle:
             out[lay.e_cN:lay.e_qN] = np.clip(CN, self.boxN_lo, self.boxN_hi).ravel()
         QN = v[lay.e_qN:self.e_l1].reshape(tr.n_l, nx + 2)
         out[lay.e_qN:self.e_l1] = (self.a_qN + proj_soc(QN - self.a_qN)).ravel()
-        out[self.e_l1:] = np.maximum(v[self.e_l1:], 0.0)     # l1 rows (Prop. 2): R_+
+        out[self.e_l1:self.e_sf] = np.maximum(v[self.e_l1:self.e_sf], 0.0)     # l1 rows (Prop. 2): R_+
+        if self.soft is not None:
+            d = nx + nu
+            B = v[self.e_sf:].reshape(tr.n_nl, 3 * d + 2)
+            O = B.copy()
+            a = np.zeros(d + 2); a[-2] = 0.5; a[-1] = -0.5
+            O[:, :d + 2] = a + proj_soc(B[:, :d + 2] - a)
+            O[:, d + 2:2 * d + 2] = np.maximum(B[:, d + 2:2 * d + 2], 0.0)
+            O[:, 2 * d + 2:] = np.maximum(B[:, 2 * d + 2:], self.soft_lo)
+            out[self.e_sf:] = O.ravel()
         return out
 
     def prox_gconj(self, v):
@@ -1036,7 +1077,13 @@ class Oracle:
             val += float(np.sum(np.maximum(CN * self.boxN_lo, CN * self.boxN_hi)))
         QN = eta[lay.e_qN:self.e_l1].reshape(tr.n_l, nx + 2)
         val += float(np.sum(QN * self.a_qN))
-        return val                 # the l1 rows are a cone: they contribute 0
+        if self.soft is not None:  # translated cone <eta, a>; rows z - theta >= .. : h lo for h <= 0
+            d = nx + nu
+            B = eta[self.e_sf:].reshape(tr.n_nl, 3 * d + 2)
+            val += float(np.sum(0.5 * B[:, d] - 0.5 * B[:, d + 1]))
+            H = B[:, 2 * d + 2:]
+            val += float(np.sum(np.where(H <= 0.0, H * self.soft_lo, np.inf)))
+        return val                 # the l1 rows and theta >= 0 are cones: they contribute 0
 
     def nested_values(self, x, u):
         """Cost-to-go V^i of a trajectory under the nested risk (Eq.
@@ -1091,6 +1138,8 @@ class Oracle:
             val += P.r[c - 1] @ u
         if self.l1:
             val += self.l1 * (np.sum(np.abs(x)) + np.sum(np.abs(u)))
+        if self.soft is not None:
+            val += float(np.sum(np.maximum(0.0, np.concatenate([x, u]) - self.soft) ** 2))
         return float(val)
 
     def terminal_cost(self, jj, x):

@@ -72,6 +72,9 @@ class RAOCP:
     gN_hi: Optional[np.ndarray] = None
     l1: Optional[float] = None          # lambda_0 >= 0 of an l1 term lambda_0 ||(x^anc, u^anc)||_1 added
                                         # to every edge cost (Prop. 2); None or 0 = none
+    soft_max: Optional[np.ndarray] = None   # float64 [nx + nu] finite: every edge cost gets the soft-constraint
+                                        # penalty ||max(0, (x^anc, u^anc) - soft_max)||^2 (the quadratic
+                                        # penalty after Prop. 2); None = none
     tv: Optional[np.ndarray] = None     # float64 [n_nonleaf] radius r >= 0: the risk of every non-leaf node
                                         # is then the worst expectation over {mu in the simplex :
                                         # ||mu - p||_1 <= r} (a conic risk with F != 0, Sec. 3.3)

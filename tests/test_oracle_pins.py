@@ -1074,3 +1074,140 @@ def test_tv_problem_diagnostics_vanish():
     assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
     assert r["infeas"] < 1e-6 and r["gap"] < 1e-5
     assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * max(1.0, abs(r["risk"]))
+
+
+# --- soft-constraint costs (the quadratic penalty after Prop. 2) ----------------------
+
+
+def _soft_problem(seed, avar=1.0, box=False, level=0.3, ball=None):
+    p = general([2, 2, 1], 3, 2, seed=seed, avar=avar, box=box, dense=False)
+    p.soft_max = np.full(p.nx + p.nu, float(level))
+    if ball is not None:
+        p.u_ball = np.full(p.n_nonleaf, ball)
+    return p
+
+
+def test_soft_rows_encode_the_penalised_epigraph():
+    """l(z) = z'Qz + q'z + ||max(0, z - z_max)||^2 <= tau exactly when some
+    sigma, theta with theta >= 0, theta >= z - z_max, ||theta||^2 <= sigma put
+    (z, tau - sigma) in the epigraph of the quadratic part. With the smallest
+    choice theta = max(0, z - z_max), sigma = ||theta||^2, the rows L gives the
+    child's cost cone and the parent's soft block lie in S3 exactly when the
+    full cost is at most tau; with sigma below ||theta||^2 the soft cone fails."""
+    p = _soft_problem(71)
+    o = Oracle(p)
+    tr, lay = o.tree, o.lay
+    nx, nu, d = o.nx, o.nu, o.nx + o.nu
+    rng = np.random.default_rng(8)
+    i = 1
+    c = tr.children[i][0]
+    sc = np.concatenate([o.Snode[i], o.Su])
+    w = nx + nu + 2
+    cone = slice(lay.e_q + (c - 1) * w, lay.e_q + c * w)
+    rows = slice(o.e_sf + i * (3 * d + 2), o.e_sf + (i + 1) * (3 * d + 2))
+    for trial in range(40):
+        x = rng.standard_normal(nx)
+        u = rng.standard_normal(nu)
+        cost = o.edge_cost(c, x, u)
+        tau = cost + rng.uniform(-0.5, 0.5)
+        zu = np.concatenate([x, u])
+        th = np.maximum(0.0, zu - p.soft_max)
+        z = np.zeros(lay.n_z)
+        z[lay.o_x + i * nx:lay.o_x + (i + 1) * nx] = o.Snode[i] * x
+        z[lay.o_u + i * nu:lay.o_u + (i + 1) * nu] = o.Su * u
+        z[lay.o_tau + c - 1] = tau
+        z[o.o_sg + i] = th @ th
+        z[o.o_sth + i * d:o.o_sth + (i + 1) * d] = sc * th
+        Lz = o.apply_L(z)
+        P3 = o.proj_S3(Lz)
+        inside = np.allclose(P3[cone], Lz[cone], atol=1e-12) and np.allclose(P3[rows], Lz[rows], atol=1e-12)
+        assert inside == (cost <= tau), (trial, cost, tau)
+        if th @ th > 1e-3:
+            z[o.o_sg + i] = 0.9 * (th @ th)
+            L2 = o.apply_L(z)
+            assert not np.allclose(o.proj_S3(L2)[rows], L2[rows], atol=1e-12)
+
+
+def _risk_neutral_soft_qp(p):
+    """min sum_c pi^c (x'Qx + u'Ru + q'x + r'u + ||t^a||^2) + sum_j pi^j l_N^j,
+    t^i >= 0, t^i >= (x^i, u^i) - z_max, dynamics eliminated: the penalty of
+    node i's children weighs pi^i; a QP in (u, t) by the interior-point method
+    above (diagonal weights). Returns (value, x, u)."""
+    tr = so_.Tree(p.anc, p.prob)
+    nx, nu, n = p.nx, p.nu, tr.n
+    nX = n * nx + tr.n_nl * nu
+    H = np.zeros((nX, nX))
+    f = np.zeros(nX)
+    for c in range(1, n):
+        a = tr.anc[c]
+        H[a * nx:(a + 1) * nx, a * nx:(a + 1) * nx] += tr.pi[c] * np.diag(p.Q[c - 1])
+        o = n * nx + a * nu
+        H[o:o + nu, o:o + nu] += tr.pi[c] * np.diag(p.R[c - 1])
+        if p.q is not None:
+            f[a * nx:(a + 1) * nx] += tr.pi[c] * p.q[c - 1]
+        if p.r is not None:
+            f[o:o + nu] += tr.pi[c] * p.r[c - 1]
+    for jj in range(tr.n_l):
+        j = tr.n_nl + jj
+        H[j * nx:(j + 1) * nx, j * nx:(j + 1) * nx] += tr.pi[j] * np.diag(p.QN[jj])
+        if p.qN is not None:
+            f[j * nx:(j + 1) * nx] += tr.pi[j] * p.qN[jj]
+    nU = tr.n_nl * nu
+    Pm = np.zeros((nX, nU)); p0 = np.zeros(nX)
+    Pm[n * nx:, :] = np.eye(nU)
+    p0[:nx] = p.x0
+    for c in range(1, n):
+        a = tr.anc[c]
+        Pm[c * nx:(c + 1) * nx] = p.A[c - 1] @ Pm[a * nx:(a + 1) * nx]
+        Pm[c * nx:(c + 1) * nx, a * nu:(a + 1) * nu] += p.B[c - 1]
+        p0[c * nx:(c + 1) * nx] = p.A[c - 1] @ p0[a * nx:(a + 1) * nx] + p.c[c - 1]
+    d = nx + nu
+    nT = tr.n_nl * d
+    Sel = np.zeros((nT, nX))
+    wt = np.zeros(nT)
+    zmax = np.tile(p.soft_max, tr.n_nl)
+    for i in range(tr.n_nl):
+        Sel[i * d:i * d + nx, i * nx:(i + 1) * nx] = np.eye(nx)
+        Sel[i * d + nx:(i + 1) * d, n * nx + i * nu:n * nx + (i + 1) * nu] = np.eye(nu)
+        wt[i * d:(i + 1) * d] = tr.pi[i]
+    Hw = np.zeros((nU + nT, nU + nT))
+    Hw[:nU, :nU] = 2 * Pm.T @ H @ Pm
+    Hw[nU:, nU:] = 2 * np.diag(wt)
+    fw = np.concatenate([Pm.T @ (2 * H @ p0 + f), np.zeros(nT)])
+    Zu = Sel @ Pm
+    G = np.vstack([np.hstack([Zu, -np.eye(nT)]), np.hstack([np.zeros((nT, nU)), -np.eye(nT)])])
+    h = np.concatenate([zmax - Sel @ p0, np.zeros(nT)])
+    wsol = _qp_interior_point(Hw, fw, G, h)
+    X = Pm @ wsol[:nU] + p0
+    pen = np.maximum(0.0, Sel @ X - zmax)
+    val = float(X @ H @ X + f @ X + wt @ (pen * pen))
+    return val, X[:n * nx].reshape(n, nx), X[n * nx:].reshape(tr.n_nl, nu)
+
+
+def test_risk_neutral_soft_costs_vs_qp():
+    """AV@R_1, no hard constraints, diagonal weights, linear terms and the soft
+    penalty ||max(0, (x, u) - z_max)||^2 in every edge cost: the oracle's SPOCK
+    solution equals the QP with t >= 0, t >= z - z_max (value; trajectory on
+    the likely nodes); some penalties are active."""
+    p = _soft_problem(72, level=0.2)
+    o = Oracle(p)
+    r = o.solve(tol=1e-9, max_iters=40000)
+    V, X, U = _risk_neutral_soft_qp(p)
+    assert abs(r["risk"] - V) < 1e-6 * max(1.0, abs(V))
+    _check_on_likely_nodes(o, r, X, U, 1e-4)
+    tr = o.tree
+    zs = np.hstack([X[:tr.n_nl], U])
+    assert np.any(zs > p.soft_max + 1e-6)
+
+
+def test_soft_problem_diagnostics_vanish():
+    """AV@R 0.5 with boxes, a ball and soft-constraint costs: the residual, xi1,
+    xi2, infeasibility and the complementarity gap vanish, and s0 equals the
+    nested risk of the trajectory with the penalties."""
+    p = _soft_problem(73, avar=0.5, box=True, level=0.25, ball=1.5)
+    o = Oracle(p)
+    r = o.solve(tol=1e-8, max_iters=40000)
+    assert r["res_inf"] <= 1e-8
+    assert r["xi1"] < 1e-5 and r["xi2"] < 1e-5
+    assert r["infeas"] < 1e-6 and r["gap"] < 1e-5
+    assert abs(r["risk"] - r["nested_risk"]) < 1e-5 * max(1.0, abs(r["risk"]))
