@@ -43,7 +43,7 @@ def test_sizes_match_hand_count():
             o.has_xbox, o.has_ubox, o.has_uball = True, True, p.u_ball is not None
             o.n_c = p.nx + p.nu + (p.nu if p.u_ball is not None else 0)
             o.n_cN = p.nx
-            o.l1 = 0.0
+            o.l1, o.soft = 0.0, None
             o._layout()
             assert (o.lay.n_z, o.lay.n_eta) == (ref["n_z"], ref["n_eta"])
 
