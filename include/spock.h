@@ -131,6 +131,14 @@ typedef struct spock_problem_desc {
                                 conic risk with F != 0 (Sec. 3.3: nu >= |mu - p|, y^i of 3 n_i + 2
                                 entries, S2^i = ker[E', -I, -I; F', 0, 0]); avar is then unused.
                                 Single-problem calls only (as l1) */
+    const double* soft_max;  /* [nx + nu] finite, or NULL. Non-NULL: every edge cost gets the
+                                soft-constraint penalty ||max(0, (x^anc, u^anc) - soft_max)||^2
+                                (the quadratic penalty after Prop. 2), through sigma^i >= ||theta^i||^2
+                                (a translated second-order cone), theta^i >= 0 and
+                                theta^i >= (x^i, u^i) - soft_max per non-leaf node (shared by its
+                                children's edge costs) and tau^c - sigma^i in the children's cost
+                                cones. Needs diagonal weights and l1 = 0 (SPOCK_EUNSUPPORTED
+                                otherwise); single-problem calls only */
 } spock_problem_desc;
 
 typedef struct spock_sizes {

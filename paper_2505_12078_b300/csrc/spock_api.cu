@@ -262,6 +262,7 @@ void fill_prob(spock_problem* p, Iter<T>& it, double alpha) {
   P.gen_lo = it.gen_lo; P.gen_hi = it.gen_hi; P.genN_lo = it.genN_lo; P.genN_hi = it.genN_hi;
   P.alpha = (T)alpha;
   P.tv = p->tv; P.tvr = it.tvr;
+  P.soft = p->soft; P.o_sg = p->o_sg; P.o_sth = p->o_sth; P.e_sf = p->e_sf; P.smw = it.smw; P.slo = it.slo;
   P.l1 = (T)p->l1; P.o_th = p->o_th; P.o_lam = p->o_lam; P.e_l1 = p->e_l1; P.l1w = it.l1w;
   P.qbuf = it.qbuf; P.dbuf = it.dbuf; P.hbuf = it.hbuf; P.ebuf = it.ebuf;
   P.mbb = it.mbb; P.mbf = it.mbf;
@@ -337,6 +338,8 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
   it.x0s = m.alloc<T>(nx);
   it.l1w = m.alloc<T>(nx + nu);
   it.tvr = m.alloc<T>(n_nl);
+  it.smw = m.alloc<T>(nx + nu);
+  it.slo = m.alloc<T>(nx + nu);
   it.qbuf = m.alloc<T>((long long)n * nx);
   it.dbuf = m.alloc<T>((long long)n_nl * nu);
   it.hbuf = m.alloc<T>((long long)n_nl * nx);
@@ -957,6 +960,12 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   }
   if (!(d->l1 >= 0.0) || !isfinite(d->l1)) { delete p; return SPOCK_EINVAL; }
   p->l1 = d->l1;
+  if (d->soft_max) {
+    if (d->l1 > 0 || full) { delete p; return SPOCK_EUNSUPPORTED; }
+    p->soft = 1;
+    p->soft_max.assign(d->soft_max, d->soft_max + nx + nu);
+    for (double v : p->soft_max) if (!isfinite(v)) { delete p; return SPOCK_EINVAL; }
+  }
   if (d->tv) {
     p->tv = 1;
     p->tvr.assign(d->tv, d->tv + n_nl);
@@ -991,6 +1000,14 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   if (p->l1 > 0) {
     p->nz = p->o_lam + (long long)n_nl * (nx + nu);
     p->neta = p->e_l1 + (long long)n_nl * (1 + 2 * (nx + nu));
+  }
+  // soft-constraint costs: sigma, theta per non-leaf node next in z, their rows next in eta
+  p->o_sg = p->nz;
+  p->o_sth = p->o_sg + (p->soft ? n_nl : 0);
+  p->e_sf = p->neta;
+  if (p->soft) {
+    p->nz = p->o_sth + (long long)n_nl * (nx + nu);
+    p->neta = p->e_sf + (long long)n_nl * (3 * (nx + nu) + 2);
   }
   p->nv = p->nz + p->neta;
   p->ldB = pad4(nx + nu); p->ldF = pad4(nx); p->ldP = pad4(nx + nu); p->ldK = pad4(nu);
@@ -1175,6 +1192,22 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
   a.qh = f.qh; a.rh = f.rh; a.qNh = f.qNh; a.gx = f.gx; a.gu = f.gu; a.gN = f.gN;
   a.box_lo = f.box_lo; a.box_hi = f.box_hi; a.boxN_lo = f.boxN_lo; a.boxN_hi = f.boxN_hi; a.ball = f.ball;
   a.ys_block = p->tv ? 0 : 1;
+  if (p->soft) {   // 1/s and the scaled lower bounds -s z_max of the soft rows, both precisions
+    std::vector<double> w64(nx + nu), l64(nx + nu);
+    for (int k = 0; k < nx + nu; ++k) {
+      const double sk = (k < nx) ? p->Sx[k] : p->Su[k - nx];
+      w64[(size_t)k] = 1.0 / sk;
+      l64[(size_t)k] = -sk * p->soft_max[(size_t)k];
+    }
+    std::vector<float> w32(w64.begin(), w64.end()), l32(l64.begin(), l64.end());
+    if (cudaMemcpy(p->f64.smw, w64.data(), w64.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->f64.slo, l64.data(), l64.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->f32.smw, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->f32.slo, l32.data(), l32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      tmp.free_all(); m.free_all(); delete p; return SPOCK_EDEVICE;
+    }
+    a.soft_w = p->f64.smw;
+  }
   a.xu_shift = (p->l1 > 0) ? 2.0 : 0.0;   // the l1 rows add 2 I to every (x^i, u^i) block of L'L
   cudaStream_t st = 0;
   cudaError_t e = launch_scale_dyn(a, st);
@@ -1287,6 +1320,15 @@ int spock_problem_create(const spock_problem_desc* d, spock_problem** out) {
     if (cudaMemcpy(p->f64.l1w, w64.data(), w64.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->f32.l1w, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
       m.free_all(); delete p; return SPOCK_EDEVICE;
+    }
+  }
+  if (p->soft) {
+    // sigma^i with the tau^c of its m children: [m/2 + 1/2, -1'/2; -1/2, I/2];
+    // off the symmetric tau combination 1/2, on it the 2 x 2 below
+    for (int i = 0; i < n_nl; ++i) {
+      const double m2 = (double)(p->ch_off[i + 1] - p->ch_off[i]);
+      const double a = 0.5 * m2 + 0.5, b = 0.5, c = -0.5 * sqrt(m2);
+      l2 = std::max(l2, 0.5 * (a + b) + sqrt(0.25 * (a - b) * (a - b) + c * c));
     }
   }
   if (p->tv) {

@@ -421,7 +421,7 @@ int spock_batch_create(spock_problem* const* problems, int count, int precision,
   for (int i = 0; i < count; ++i) {
     if (!problems[i]) return SPOCK_EINVAL;
     if (problems[i]->nx + problems[i]->nu > kMaxWidth) return SPOCK_EUNSUPPORTED;
-    if (problems[i]->l1 > 0 || problems[i]->tv) return SPOCK_EUNSUPPORTED;   // single-problem calls only
+    if (problems[i]->l1 > 0 || problems[i]->tv || problems[i]->soft) return SPOCK_EUNSUPPORTED;   // single-problem calls only
   }
   spock_batch* b = new spock_batch();
   b->count = count;

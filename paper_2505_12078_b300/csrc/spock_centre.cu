@@ -39,6 +39,10 @@ __global__ void k_centre(Prob<double> P, const double* __restrict__ c, const dou
       const long long r = e - P.e_qN;
       const int j = (int)(r % dN);
       a = P.acostN ? P.acostN[r] : (j == dN - 2 ? 0.5 : (j == dN - 1 ? -0.5 : 0.0));
+    } else if (P.soft && e >= P.e_sf) {   // the soft costs' cones: (0, 1/2, -1/2)
+      const int dS = P.nx + P.nu;
+      const int j = (int)((e - P.e_sf) % (3 * dS + 2));
+      a = (j == dS) ? 0.5 : (j == dS + 1 ? -0.5 : 0.0);
     }
     const double l = lz[e];
     A[e] = (c[nz + e] + alpha * l) / alpha - a;

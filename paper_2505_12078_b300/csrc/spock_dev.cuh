@@ -132,6 +132,16 @@ struct Prob {
   // 1, m, 1), b = [p; -p; r; 0; 1], every entry but the last in R_+.
   int tv;
   const T* tvr;
+  // soft-constraint costs ||max(0, (x^anc, u^anc) - z_max)||^2 (after Prop. 2;
+  // soft = 0: none): sigma^i at o_sg + i and theta^i (scaled like (x^i, u^i))
+  // at o_sth + i (nx + nu) in z; per non-leaf node at e_sf + i (3 d + 2), d =
+  // nx + nu, the rows [smw theta, sigma/2, sigma/2] in SOC_{d+2} + (0, 1/2,
+  // -1/2), theta in R_+^d, theta - (x^i, u^i) >= slo; the cost cone of every
+  // child c of i carries (tau^c - sigma^i)/2 in its last two entries.
+  int soft;
+  long long o_sg, o_sth, e_sf;
+  const T* smw;   // [d] 1/S^x, 1/S^u
+  const T* slo;   // [d] -S^x z_max, -S^u z_max
   T l1;
   long long o_th, o_lam, e_l1;
   const T* l1w;   // [nx + nu] 1/S^x, 1/S^u

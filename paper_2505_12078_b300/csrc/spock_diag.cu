@@ -156,6 +156,25 @@ __global__ void k_S3_diag(Prob<double> P, const double* __restrict__ lz, const d
         dot += h * x;
         sig += fmax(h * lo, h * hi);
       }
+      if (P.soft) {                                         // soft-cost rows
+        const int d = P.nx + P.nu;
+        const long long se = P.e_sf + (long long)i * (3 * d + 2);
+        soc_diag(lane, d + 2, se, lz, ep, nullptr, inf, dot, sig);   // translated cone (0, 1/2, -1/2)
+        for (int e = lane; e < d; e += 32) {
+          const double x0 = lz[se + d + 2 + e];             // theta >= 0: a cone, support 0
+          inf = fmax(inf, fabs(x0 - fmax(x0, 0.0)));
+          dot += ep[se + d + 2 + e] * x0;
+          const double x1 = lz[se + 2 * d + 2 + e], h = ep[se + 2 * d + 2 + e];
+          // [lo, inf): the support is h lo for h <= 0 and infinite above;
+          // eta+ = min(0, eta_bar - alpha lo) is <= 0 exactly, but eta_bar -
+          // alpha (eta_bar / alpha) can round to a few ulps above 0 where the
+          // bound is inactive, so h is taken on the polar side, min(h, 0)
+          const double lo = P.slo[e];
+          inf = fmax(inf, fabs(x1 - fmax(x1, lo)));
+          dot += h * x1;
+          sig += fmin(h, 0.0) * lo;
+        }
+      }
       if (P.l1 != 0.0) {                                    // l1 rows (Prop. 2): R_+, support 0
         const int nr = 1 + 2 * (P.nx + P.nu);
         const long long le = P.e_l1 + (long long)i * nr;

@@ -26,6 +26,7 @@ struct SetupArgs {
   double *MB, *MF, *MP, *KT, *Pc, *kc;
   double *qh, *rh, *qNh, *gx, *gu, *gN, *box_lo, *box_hi, *boxN_lo, *boxN_hi, *ball;
   int ys_block = 1;         // the closed form of AV@R's (y, s) blocks (0: computed on the host)
+  const double* soft_w = nullptr;   // soft costs: 1/s per component of (x, u), or null
   double xu_shift = 0.0;   // added to every diagonal entry of the (x^i, u^i) blocks of L'L (l1 rows)
 };
 

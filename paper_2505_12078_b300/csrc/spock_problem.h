@@ -47,6 +47,7 @@ struct Iter {   // per-precision iteration data
   T *box_lo = nullptr, *box_hi = nullptr, *boxN_lo = nullptr, *boxN_hi = nullptr, *ball = nullptr;
   T *prob = nullptr, *avar = nullptr, *x0s = nullptr;
   T *qbuf = nullptr, *dbuf = nullptr, *hbuf = nullptr, *ebuf = nullptr;
+  T *smw = nullptr, *slo = nullptr;                   // [nx + nu] soft costs: 1/s and -s z_max
   T* tvr = nullptr;                                   // [n_nl] total-variation radii (tv problems)
   T* l1w = nullptr;                                   // [nx + nu] weights 1/s of the l1 row theta - sum
   unsigned long long *mbb = nullptr, *mbf = nullptr;   // sweep mailboxes (whole-CTA sweeps only)
@@ -77,6 +78,9 @@ struct spock_problem {
   int n_g = 0, n_gN = 0;   // general constraint rows (non-leaf, leaf)
   double l1 = 0.0;         // lambda_0 of the l1 edge-cost term (Prop. 2), 0 = none
   int tv = 0;              // 1: total-variation risks (radius per non-leaf node in tvr), 0: AV@R
+  int soft = 0;            // soft-constraint costs (the penalty after Prop. 2)
+  std::vector<double> soft_max;
+  long long o_sg = 0, o_sth = 0, e_sf = 0;   // their blocks: sigma, theta in z; their rows in eta
   std::vector<double> tvr;
   long long o_th = 0, o_lam = 0, e_l1 = 0;   // its blocks: theta, lambda in z; its rows in eta
   long long n_y = 0, nz = 0, neta = 0, nv = 0;

@@ -260,7 +260,7 @@ int spock_server_create(spock_problem* const* plants, int count, int precision, 
     if (!plants[i]) return SPOCK_EINVAL;
     if (plants[i]->nx > SERVE_MAX_NX || plants[i]->nu > SERVE_MAX_NU || plants[i]->nx + plants[i]->nu > 126)
       return SPOCK_EUNSUPPORTED;
-    if (plants[i]->l1 > 0 || plants[i]->tv) return SPOCK_EUNSUPPORTED;   // single-problem calls only
+    if (plants[i]->l1 > 0 || plants[i]->tv || plants[i]->soft) return SPOCK_EUNSUPPORTED;   // single-problem calls only
   }
   spock_solve_opts o;
   if (opts) o = *opts;

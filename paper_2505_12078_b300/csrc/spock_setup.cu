@@ -378,8 +378,17 @@ __global__ void k_cost_con(int n, int n_nl, int nx, int nu, int nbx, int nbu, in
   }
 }
 
+// With soft-constraint costs, component k of (x^i, u^i) pairs with theta^i_k:
+// L'L on (z_k, theta_k) is [g + 1, -1; -1, w^2 + 2] (the row theta - z adds 1
+// and -1, theta >= 0 adds 1, the soft cone w^2): its largest eigenvalue.
+__device__ __forceinline__ double soft_pair(double g, double w) {
+  const double a = g + 1.0, b = w * w + 2.0;
+  return 0.5 * (a + b) + sqrt(0.25 * (a - b) * (a - b) + 1.0);
+}
+
 // ||L||^2 as the max over the diagonal-Gram blocks of L (see file header)
 __global__ void k_norm_L(int n, int n_nl, int nx, int nu, int nbx, int nub, double xu_shift, int ys_block,
+                         const double* __restrict__ soft_w,
                          const int* __restrict__ ch_off, const double* __restrict__ prob,
                          const double* __restrict__ qh, const double* __restrict__ rh,
                          const double* __restrict__ qNh, const double* __restrict__ gx,
@@ -392,12 +401,12 @@ __global__ void k_norm_L(int n, int n_nl, int nx, int nu, int nbx, int nub, doub
       for (int k = 0; k < nx; ++k) {
         double s = (nbx ? gx[k] * gx[k] : 0.0) + xu_shift;
         for (int c = c0; c < c1; ++c) s += qh[(long long)(c - 1) * nx + k] * qh[(long long)(c - 1) * nx + k];
-        lam = fmax(lam, s);
+        lam = fmax(lam, soft_w ? soft_pair(s, soft_w[k]) : s);
       }
       for (int k = 0; k < nu; ++k) {
         double s = nub * gu[k] * gu[k] + xu_shift;
         for (int c = c0; c < c1; ++c) s += rh[(long long)(c - 1) * nu + k] * rh[(long long)(c - 1) * nu + k];
-        lam = fmax(lam, s);
+        lam = fmax(lam, soft_w ? soft_pair(s, soft_w[nx + k]) : s);
       }
       if (ys_block) {   // AV@R's (y, s) block, beta = ||b||^2 (other risks: on the host)
         double beta = 1.0;
@@ -477,6 +486,7 @@ __global__ void k_apply_L(Prob<T> P, const int* __restrict__ ynode, const T* __r
       } else {
         v = T(0.5) * z[P.o_tau + cm1];
         if (P.l1 != T(0)) v -= T(0.5) * P.l1 * z[P.o_th + a];   // (tau^c - lambda_0 theta^a)/2 (Prop. 2)
+        if (P.soft) v -= T(0.5) * z[P.o_sg + a];                  // (tau^c - sigma^a)/2 (soft costs)
       }
     } else if (e < P.e_qN) {               // leaf constraint rows
       const long long f = e - P.e_cN;
@@ -488,6 +498,19 @@ __global__ void k_apply_L(Prob<T> P, const int* __restrict__ ynode, const T* __r
       } else {
         const T* G = P.GgN + (size_t)(k - P.nbx) * nx;
         for (int q = 0; q < nx; ++q) v += G[q] * x[q];
+      }
+    } else if (e >= P.e_sf) {              // soft-cost rows of non-leaf node i
+      const int d = nx + nu;
+      const long long f = e - P.e_sf;
+      const long long i = f / (3 * d + 2);
+      const int r = (int)(f % (3 * d + 2));
+      const T* th = z + P.o_sth + i * d;
+      if (r < d) v = P.smw[r] * th[r];                      // the cone: theta/s
+      else if (r < d + 2) v = T(0.5) * z[P.o_sg + i];       // sigma/2, sigma/2
+      else if (r < 2 * d + 2) v = th[r - d - 2];            // theta >= 0
+      else {                                                 // theta - (x^i, u^i) >= slo
+        const int k = r - 2 * d - 2;
+        v = th[k] - ((k < nx) ? z[P.o_x + i * nx + k] : z[P.o_u + i * nu + (k - nx)]);
       }
     } else if (e >= P.e_l1) {              // l1 rows of non-leaf node i (Prop. 2)
       const int d = nx + nu;
@@ -559,6 +582,7 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
           const T* el = eta + P.e_l1 + i * (1 + 2 * (nx + nu));
           v += el[1 + (nx + nu) + k] - el[1 + k];
         }
+        if (P.soft) v -= eta[P.e_sf + i * (3 * (nx + nu) + 2) + 2 * (nx + nu) + 2 + k];   // theta - x rows
       } else {
         const long long j = i - P.n_nl;
         if (P.nbx) v = P.gN[k] * ecN[j * P.n_cN + k];
@@ -590,6 +614,7 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
         const T* el = eta + P.e_l1 + i * (1 + 2 * (nx + nu));
         v += el[1 + (nx + nu) + nx + k] - el[1 + nx + k];
       }
+      if (P.soft) v -= eta[P.e_sf + i * (3 * (nx + nu) + 2) + 2 * (nx + nu) + 2 + nx + k];   // theta - u rows
     } else if (e < P.o_tau) {              // y
       const long long f = e - P.o_y;
       const int i = ynode[f];
@@ -612,6 +637,20 @@ __global__ void k_apply_Lt(Prob<T> P, const int* __restrict__ ynode, const T* __
       v = eta[P.e_l1 + i * (1 + 2 * (nx + nu))];
       for (int c = P.ch_off[i]; c < P.ch_off[i + 1]; ++c)
         v -= T(0.5) * P.l1 * (eq[(long long)(c - 1) * P.W + nx + nu] + eq[(long long)(c - 1) * P.W + nx + nu + 1]);
+    } else if (e >= P.o_sth) {             // theta^i_k of the soft costs: its cone entry and rows
+      const int d = nx + nu;
+      const long long f = e - P.o_sth;
+      const long long i = f / d;
+      const int k = (int)(f % d);
+      const T* es_ = eta + P.e_sf + i * (3 * d + 2);
+      v = P.smw[k] * es_[k] + es_[d + 2 + k] + es_[2 * d + 2 + k];
+    } else if (e >= P.o_sg) {              // sigma^i: its cone and the children's cost cones
+      const int d = nx + nu;
+      const long long i = e - P.o_sg;
+      const T* es_ = eta + P.e_sf + i * (3 * d + 2);
+      v = T(0.5) * (es_[d] + es_[d + 1]);
+      for (int c = P.ch_off[i]; c < P.ch_off[i + 1]; ++c)
+        v -= T(0.5) * (eq[(long long)(c - 1) * P.W + nx + nu] + eq[(long long)(c - 1) * P.W + nx + nu + 1]);
     } else {                               // lambda^i_k: its l1 rows
       const int d = nx + nu;
       const long long f = e - P.o_lam;
@@ -675,7 +714,7 @@ cudaError_t launch_build(const SetupArgs& a, cudaStream_t s) {
 
 cudaError_t launch_norm_L(const SetupArgs& a, unsigned long long* out, cudaStream_t s) {
   k_norm_L<<<grid_for(a.n, 128), 128, 0, s>>>(a.n, a.n_nl, a.nx, a.nu, a.nbx,
-                                                (a.nbu ? 1 : 0) + (a.has_ball ? 1 : 0), a.xu_shift, a.ys_block, a.ch_off,
+                                                (a.nbu ? 1 : 0) + (a.has_ball ? 1 : 0), a.xu_shift, a.ys_block, a.soft_w, a.ch_off,
                                                 a.prob, a.qh, a.rh, a.qNh, a.gx, a.gu, a.gN, out);
   return cudaGetLastError();
 }

@@ -221,6 +221,41 @@ __device__ void s2_block_tv(const Prob<T>& P, int lane, int i, const T* __restri
   }
 }
 
+// The auxiliaries of the soft-constraint costs of node i: f does not involve
+// them, so their step is w = z - alpha L*eta. L* of sigma^i: half the sum of
+// the last two entries of its own cone minus the same of every child's cost
+// cone; of theta^i_k: 1/s_k times its cone entry plus its rows theta >= 0 and
+// theta - z >= lo.
+template <class T>
+__device__ void soft_prep(const Prob<T>& P, int lane, int i, const T* __restrict__ vin, T* __restrict__ vout,
+                          const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu, d = nx + nu;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  const T al = P.alpha;
+  const T* es = eta + P.e_sf + (long long)i * (3 * d + 2);
+  T sc = 0;
+  for (int c = P.ch_off[i] + lane; c < P.ch_off[i + 1]; c += 32) {
+    const T* eq = eta + P.e_q + (long long)(c - 1) * P.W + nx + nu;
+    sc += ldc(eq) + ldc(eq + 1);
+  }
+  sc = warp_sum(sc);
+  if (lane == 0) {
+    const long long idx = P.o_sg + i;
+    const T o = ldc(z + idx);
+    const T n = zc_add(P, idx, o - al * (T(0.5) * (ldc(es + d) + ldc(es + d + 1)) - T(0.5) * sc));
+    stc(vout + idx, n);
+    ra.z(o, n, dirv(vref, idx));
+  }
+  for (int k = lane; k < d; k += 32) {
+    const long long idx = P.o_sth + (long long)i * d + k;
+    const T o = ldc(z + idx);
+    const T n = zc_add(P, idx, o - al * (ldr(P.smw + k) * ldc(es + k) + ldc(es + d + 2 + k) + ldc(es + 2 * d + 2 + k)));
+    stc(vout + idx, n);
+    ra.z(o, n, dirv(vref, idx));
+  }
+}
+
 // The auxiliaries of the l1 edge costs of node i (Prop. 2): f does not
 // involve them, so their step is w = z - alpha L*eta. L* of theta^i: its l1
 // row minus lambda_0/2 times the last two entries of every child's cost cone;
@@ -289,6 +324,7 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
       const T* el = eta + P.e_l1 + (long long)i * (1 + 2 * (nx + nu));
       g += ldc(el + 1 + (nx + nu) + nx + k) - ldc(el + 1 + nx + k);
     }
+    if (P.soft) g -= ldc(eta + P.e_sf + (long long)i * (3 * (nx + nu) + 2) + 2 * (nx + nu) + 2 + nx + k);
     s_in[k] = ldc(z + P.o_u + (long long)i * nu + k) - al * g;
   }
   for (int k = tw1.lane; k < nx; k += 32) {
@@ -309,6 +345,7 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
       const T* el = eta + P.e_l1 + (long long)i * (1 + 2 * (nx + nu));
       g += ldc(el + 1 + (nx + nu) + k) - ldc(el + 1 + k);
     }
+    if (P.soft) g -= ldc(eta + P.e_sf + (long long)i * (3 * (nx + nu) + 2) + 2 * (nx + nu) + 2 + k);
     s_xb[k] = ldc(z + P.o_x + (long long)i * nx + k) - al * g;
   }
   __syncwarp();
@@ -325,6 +362,7 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
   if (P.tv) s2_block_tv(P, tw1.lane, i, vin, vout, vref, ra);
   else s2_block(P, tw1.lane, i, vin, vout, vref, ra);
   if (P.l1 != T(0)) l1_prep(P, tw1.lane, i, vin, vout, vref, ra);
+  if (P.soft) soft_prep(P, tw1.lane, i, vin, vout, vref, ra);
 }
 
 template <class T>
@@ -1150,6 +1188,10 @@ __device__ void eta_soc_full(const Prob<T>& P, int lane, int c, const T* __restr
     const long long ith = P.o_th + i;
     to -= P.l1 * ldc(z + ith); tn -= P.l1 * ldc(vout + ith); td -= P.l1 * dirv(vref, ith);
   }
+  if (P.soft) {   // (tau^c - sigma^i)/2
+    const long long isg = P.o_sg + i;
+    to -= ldc(z + isg); tn -= ldc(vout + isg); td -= dirv(vref, isg);
+  }
   const T al = P.alpha;
   T ebv[NE];
 #pragma unroll
@@ -1211,6 +1253,10 @@ __device__ void eta_soc(const Prob<T>& P, int lane, int c, const T* __restrict__
   if (P.l1 != T(0)) {
     const long long ith = P.o_th + i;
     tho = P.l1 * ldc(z + ith); thn = P.l1 * ldc(vout + ith); thd = P.l1 * dirv(vref, ith);
+  }
+  if (P.soft) {   // (tau^c - sigma^i)/2
+    const long long isg = P.o_sg + i;
+    tho += ldc(z + isg); thn += ldc(vout + isg); thd += dirv(vref, isg);
   }
   auto Lz = [&](int e, T& Lo, T& Ln, T& Ld, T& Lrd) {
     long long idx;
@@ -1302,6 +1348,44 @@ __device__ void eta_leaf(const Prob<T>& P, int lane, int j, const T* __restrict_
   };
   soc_block<T, NE>(P, lane, nx + 2, P.e_qN + (long long)jj * (nx + 2), eta, eo, er, Lz, ra,
                    P.acostN ? P.acostN + (size_t)jj * (nx + 2) : nullptr);
+}
+
+// The soft-cost rows of non-leaf node i: [theta/s, sigma/2, sigma/2] in the
+// translated cone SOC + (0, 1/2, -1/2), theta >= 0, theta - (x^i, u^i) >= lo.
+template <class T, int NE>
+__device__ void eta_soft(const Prob<T>& P, int lane, int i, const T* __restrict__ vin, T* __restrict__ vout,
+                         const T* __restrict__ vref, RedAcc<T>& ra) {
+  const int nx = P.nx, nu = P.nu, d = nx + nu;
+  const T* z = vin;
+  const T* eta = vin + P.nz;
+  T* eo = vout + P.nz;
+  const T* er = vref ? vref + P.nz : nullptr;
+  const T al = P.alpha;
+  const long long se = P.e_sf + (long long)i * (3 * d + 2);
+  const long long ot = P.o_sth + (long long)i * d, isg = P.o_sg + i;
+  auto Lz = [&](int e, T& Lo, T& Ln, T& Ld, T& Lrd) {
+    long long idx;
+    T g;
+    if (e < d) { g = ldr(P.smw + e); idx = ot + e; }
+    else { g = T(0.5); idx = isg; }
+    const T o = ldc(z + idx), nn = ldc(vout + idx);
+    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * dirv(vref, idx);
+  };
+  soc_block<T, NE>(P, lane, d + 2, se, eta, eo, er, Lz, ra);
+  auto row = [&](long long ie, T Lo, T Ln, T Ld, T Lrd, T lo) {
+    const T eo_ = ldc(eta + ie);
+    const T eb = eo_ + al * (T(2) * Ln - Lo);
+    const T en = eta_prox(P, ie, eb, [&](auto w) { return max(w, (decltype(w))lo); });
+    stc(eo + ie, en);
+    ra.eta(eo_, en, er ? ldc(er + ie) : T(0), Ld, Lrd);
+  };
+  for (int k = lane; k < d; k += 32) {
+    const T to = ldc(z + ot + k), tn = ldc(vout + ot + k), tr = dirv(vref, ot + k);
+    const long long iz = (k < nx) ? P.o_x + (long long)i * nx + k : P.o_u + (long long)i * nu + (k - nx);
+    const T zo = ldc(z + iz), zn = ldc(vout + iz), zr = dirv(vref, iz);
+    row(se + d + 2 + k, to, tn, to - tn, tr, T(0));
+    row(se + 2 * d + 2 + k, to - zo, tn - zn, (to - tn) - (zo - zn), tr - zr, ldr(P.slo + k));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1488,6 +1572,7 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
         z_resid(vin, vout, vref, P.o_u + b * P.nu, P.nu, lane, ra);
         eta_nonleaf(P, lane, (int)b, vin, vout, vref, ra);
         if (P.l1 != T(0)) eta_l1(P, lane, (int)b, vin, vout, vref, ra);
+        if (P.soft) eta_soft<T, NE>(P, lane, (int)b, vin, vout, vref, ra);
       } else if (b < P.n_nl + P.n - 1) {
         if (P.full) eta_soc_full<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);
         else eta_soc<T, NE>(P, lane, (int)(b - P.n_nl + 1), vin, vout, vref, ra);

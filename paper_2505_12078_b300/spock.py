@@ -44,7 +44,8 @@ class ProblemDesc(C.Structure):
                 ("x_lo", _dp), ("x_hi", _dp), ("u_lo", _dp), ("u_hi", _dp), ("u_ball", _dp),
                 ("avar", _dp), ("weights_full", C.c_int), ("q", _dp), ("r", _dp), ("qN", _dp),
                 ("n_g", C.c_int), ("Gx", _dp), ("Gu", _dp), ("g_lo", _dp), ("g_hi", _dp),
-                ("n_gN", C.c_int), ("GN", _dp), ("gN_lo", _dp), ("gN_hi", _dp), ("l1", C.c_double), ("tv", _dp)]
+                ("n_gN", C.c_int), ("GN", _dp), ("gN_lo", _dp), ("gN_hi", _dp), ("l1", C.c_double), ("tv", _dp),
+                ("soft_max", _dp)]
 
 
 class Sizes(C.Structure):
@@ -210,7 +211,7 @@ class Problem:
         anc = np.ascontiguousarray(p.anc, dtype=np.int32)
         arrs = dict(prob=p.prob, A=p.A, B=p.B, c=p.c, Q=p.Q, R=p.R, QN=p.QN, x_lo=p.x_lo,
                     x_hi=p.x_hi, u_lo=p.u_lo, u_hi=p.u_hi, u_ball=p.u_ball, avar=p.avar)
-        for k in ("q", "r", "qN", "Gx", "Gu", "g_lo", "g_hi", "GN", "gN_lo", "gN_hi", "tv"):
+        for k in ("q", "r", "qN", "Gx", "Gu", "g_lo", "g_hi", "GN", "gN_lo", "gN_hi", "tv", "soft_max"):
             arrs[k] = getattr(p, k, None)
         conv = {k: _f64(v) for k, v in arrs.items()}
         self._keep += [anc] + list(conv.values())

@@ -31,7 +31,7 @@ from oracle.spock_oracle import Oracle  # noqa: E402
 from test_gpu_parity import CASES  # noqa: E402
 
 NAMES = ["small", "ragged_37x19_ball", "chain_only", "full_lin_box", "rows_ball_diag_lin", "team_100x50",
-         "l1_box_ball", "tv_box_ball"]
+         "l1_box_ball", "tv_box_ball", "soft_box_ball"]
 TOL = 1e-7
 
 

@@ -58,7 +58,16 @@ CASES = {
     # the total-variation risk (a conic risk with F != 0, Sec. 3.3): whole-CTA and team sweeps
     "tv_box_ball": lambda: _with_tv(constrained([3, 2, 1], 6, 3, seed=68, avar=0.5, uball=2.0), 0.4),
     "tv_team_100x50": lambda: _with_tv(constrained([2, 1], 100, 50, seed=69, avar=0.5), 0.3),
+    # soft-constraint costs (the penalty after Prop. 2), diagonal weights: whole-CTA and team sweeps
+    "soft_box_ball": lambda: _with_soft(_with_ball(general([2, 2, 1], 5, 3, seed=75, avar=0.5, box=True,
+                                                           dense=False), 1.5), 0.3),
+    "soft_team_100x50": lambda: _with_soft(constrained([2, 1], 100, 50, seed=76, avar=0.5), 0.5),
 }
+
+
+def _with_soft(p, level):
+    p.soft_max = np.full(p.nx + p.nu, float(level))
+    return p
 
 
 def _with_tv(p, r):
@@ -241,7 +250,8 @@ def test_fixed_iterations_cp_fp64(name):
 
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "team_100x50",
                                   "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "full_rows_100x50",
-                                  "l1_box_ball", "l1_team_100x50", "tv_box_ball", "tv_team_100x50"])
+                                  "l1_box_ball", "l1_team_100x50", "tv_box_ball", "tv_team_100x50",
+                                  "soft_box_ball", "soft_team_100x50"])
 def test_fixed_iterations_spock_fp64(name):
     """SPOCK (Alg. 4 with Anderson directions) for a fixed iteration count in
     FP64: same branch sequence counts and iterate within 1e-10 relative."""
@@ -265,7 +275,8 @@ def test_fixed_iterations_spock_fp64(name):
 @pytest.mark.parametrize("name,recentre", [("small", 0.1), ("ragged_37x19_ball", 0.1), ("chain_only", 0.1),
                                            ("full_lin_box", 0.1), ("rows_ball_diag_lin", 0.1),
                                            ("team_100x50", 0.1), ("small", 0.0), ("ragged_37x19_ball", 0.0),
-                                           ("l1_box_ball", 0.1), ("l1_box_ball", 0.0), ("tv_box_ball", 0.1)])
+                                           ("l1_box_ball", 0.1), ("l1_box_ball", 0.0), ("tv_box_ball", 0.1),
+                                           ("soft_box_ball", 0.1)])
 def test_converged_fp32_vs_oracle(name, recentre):
     """FP32 iteration to ||v - T(v)||_inf <= 1e-4 against the optimum: the
     oracle's FP64 solve to 1e-7 (tests/golden/converged_cases.json, written by
@@ -289,7 +300,7 @@ def test_converged_fp32_vs_oracle(name, recentre):
 
 @pytest.mark.parametrize("name", ["small", "ragged_37x19_ball", "unconstrained_c", "wide_70x40", "avar0_branch8",
                                   "full_lin_box", "rows_ball_diag_lin", "full_rows_cta", "l1_box_ball",
-                                  "tv_box_ball"])
+                                  "tv_box_ball", "soft_box_ball"])
 def test_fp64_check_matches_oracle(name):
     """FP64 exit check (Sec. 5.3) through spock_check on the oracle's own
     iterate after 25 SPOCK iterations: xi1, xi2 (Eq. xi1k), the primal
@@ -380,10 +391,11 @@ def test_converged_fp32_qr_update(name):
     assert np.max(np.abs(res["u"][0] - ref["u"][0])) <= ref["tol_u"]
 
 
-@pytest.mark.parametrize("name", ["l1_box_ball", "tv_box_ball"])
+@pytest.mark.parametrize("name", ["l1_box_ball", "tv_box_ball", "soft_box_ball"])
 def test_extended_problems_are_single_problem_only(name):
-    """A problem with l1 edge costs (Prop. 2) or total-variation risks is
-    solved by the single-problem calls; the batched and serving calls refuse it
+    """A problem with l1 edge costs (Prop. 2), total-variation risks or
+    soft-constraint costs is solved by the single-problem calls; the batched
+    and serving calls refuse it
     with SPOCK_EUNSUPPORTED (-6) instead of running paths that do not carry its
     auxiliaries or its risk data."""
     spock = _spock()
@@ -395,3 +407,23 @@ def test_extended_problems_are_single_problem_only(name):
     with pytest.raises(spock.SpockError) as e:
         spock.Server([g], precision=32)
     assert e.value.code == -6
+
+
+def test_soft_costs_need_diagonal_weights_and_no_l1():
+    """Soft-constraint costs are refused (SPOCK_EUNSUPPORTED, -6) with full
+    weights or together with an l1 term, and a non-finite level is invalid
+    (SPOCK_EINVAL, -1)."""
+    spock = _spock()
+    p = _with_soft(general([2, 1], 3, 2, seed=77, avar=0.5), 0.3)          # full weights
+    with pytest.raises(spock.SpockError) as e:
+        spock.Problem(p)
+    assert e.value.code == -6
+    q = _with_l1(CASES["soft_box_ball"](), 0.2)
+    with pytest.raises(spock.SpockError) as e:
+        spock.Problem(q)
+    assert e.value.code == -6
+    r = CASES["soft_box_ball"]()
+    r.soft_max[0] = np.inf
+    with pytest.raises(spock.SpockError) as e:
+        spock.Problem(r)
+    assert e.value.code == -1
