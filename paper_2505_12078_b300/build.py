@@ -4,6 +4,9 @@
     python -m paper_2505_12078_b300.build --force
     python -m paper_2505_12078_b300.build -v       # print ptxas register/spill report
 
+libspock_checked.so is the same library compiled with -DSPOCK_CHECKED (index
+checks in the iteration kernel, see spock_debug_last_check).
+
 Every translation unit (and every solver kernel variant) is compiled to an
 object in parallel, then linked into one shared library.
 """
@@ -16,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libspock.so")
+# the bounds-checked variant (-DSPOCK_CHECKED: index checks in the iteration kernel)
+OUT_CHECKED = os.path.join(HERE, "libspock_checked.so")
 HEADERS = ["spock_dev.cuh", "spock_internal.h", "spock_solver_kernel.cuh", "spock_cta.cuh", "spock_problem.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (object name, source, extra defines)
@@ -60,9 +65,9 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(unit, verbose):
+def _compile(unit, verbose, tag=""):
     name, src, defs = unit
-    obj = os.path.join(OBJ, name + ".o")
+    obj = os.path.join(OBJ, name + tag + ".o")
     cmd = [nvcc(), "-c", *FLAGS, *defs, "-o", obj + ".tmp", os.path.join(CSRC, src)]
     if verbose:
         cmd[2:2] = ["-Xptxas", "-v"]
@@ -73,22 +78,30 @@ def _compile(unit, verbose):
     return name, r.stderr
 
 
-def build(force=False, verbose=False):
-    os.makedirs(OBJ, exist_ok=True)
-    todo = [u for u in UNITS
-            if force or _stale(os.path.join(OBJ, u[0] + ".o"), _deps(u[1]))]
+def _build_one(out, units, tag, force, verbose):
+    todo = [u for u in units
+            if force or _stale(os.path.join(OBJ, u[0] + tag + ".o"), _deps(u[1]))]
     if todo:
         with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
-            for name, log in ex.map(lambda u: _compile(u, verbose), todo):
+            for name, log in ex.map(lambda u: _compile(u, verbose, tag), todo):
                 if verbose:
-                    sys.stderr.write(f"== {name}\n{log}")
-    objs = [os.path.join(OBJ, u[0] + ".o") for u in UNITS]
-    if todo or force or _stale(OUT, objs):
-        cmd = [nvcc(), "-shared", *ARCH, "-o", OUT + ".tmp", *objs]
+                    sys.stderr.write(f"== {name}{tag}\n{log}")
+    objs = [os.path.join(OBJ, u[0] + tag + ".o") for u in units]
+    if todo or force or _stale(out, objs):
+        cmd = [nvcc(), "-shared", *ARCH, "-o", out + ".tmp", *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc link failed:\n{r.stdout}{r.stderr}")
-        os.replace(OUT + ".tmp", OUT)
+        os.replace(out + ".tmp", out)
+    return out
+
+
+def build(force=False, verbose=False, checked=True):
+    """Builds libspock.so and (checked=True) the bounds-checked libspock_checked.so."""
+    os.makedirs(OBJ, exist_ok=True)
+    _build_one(OUT, UNITS, "", force, verbose)
+    if checked:
+        _build_one(OUT_CHECKED, [(n, src, d + ["-DSPOCK_CHECKED"]) for (n, src, d) in UNITS], "_chk", force, verbose)
     return OUT
 
 

@@ -436,6 +436,8 @@ int pipe_bytes_for(const spock_problem* p) {
 
 // cycle probes of the last solve (see SolveCtl::prof)
 static unsigned long long g_last_prof[16];
+// bounds-checked build: the site of the last failed index check (0: none)
+static int g_last_check = 0;
 
 // test hook of spock_debug_wait_fault: extra CTAs the grid barriers of a
 // single-problem launch wait for, and the limit of one barrier wait
@@ -476,6 +478,11 @@ int run_solver(spock_problem* p, Iter<T>& it, const SolveOpts& so_in, cudaStream
   if (cudaStreamSynchronize(st) != cudaSuccess) return SPOCK_EDEVICE;
   if (ms) cudaEventElapsedTime(ms, p->ev0, p->ev1);
   for (int q = 0; q < 16; ++q) g_last_prof[q] = h_ctl->prof[q];
+  if (h_ctl->check_site) {   // bounds-checked build: an index check failed
+    g_last_check = h_ctl->check_site;
+    if (getenv("SPOCK_DEBUG")) fprintf(stderr, "spock: index check %d failed\n", h_ctl->check_site);
+    return SPOCK_EDEVICE;
+  }
   if (h_ctl->status < 0) {
     if (getenv("SPOCK_DEBUG"))
       fprintf(stderr, "spock: device wait gave up: cta %d barrier 0x%x parity %d site %d\n",
@@ -569,6 +576,7 @@ int op_T_with_scratch(spock_problem* p, int precision, const void* v_in, void* v
   if (cudaMemcpyAsync(&h, ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return SPOCK_EDEVICE;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SPOCK_EDEVICE;
+  if (h.check_site) { g_last_check = h.check_site; return SPOCK_EDEVICE; }
   if (h.status < 0) return SPOCK_ETIMEOUT;
   if (stats)
     for (int k = 0; k < 8; ++k) stats[k] = h.stats[k];
@@ -834,6 +842,14 @@ static int solve_centred(spock_problem* p, const spock_solve_opts& o, const Solv
 extern "C" {
 
 int spock_version(void) { return 3; }
+
+int spock_debug_last_check(void) {
+#ifdef SPOCK_CHECKED
+  return g_last_check;
+#else
+  return -1;
+#endif
+}
 
 int spock_debug_wait_fault(int phantom_ctas, double wait_limit_s) {
   if (phantom_ctas < 0 || phantom_ctas > 4 || !(wait_limit_s >= 0.0) || wait_limit_s > 10.0) return SPOCK_EINVAL;

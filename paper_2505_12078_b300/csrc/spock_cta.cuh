@@ -391,8 +391,9 @@ template <class T>
 __device__ __forceinline__ void b_issue(const Prob<T>& P, const BIssue<T>& I, const Ring& R, const SegRef& g, int j,
                                         int b) {
   const int c = b_child(P, g, j);
-  ring_arm(R.bar(b), I.bytes);
-  ring_copy(R.buf(b), I.base + (size_t)(c - 1) * I.stride, I.bytes, R.bar(b));
+  const bool ok = SPOCK_CHK(c >= 1 && c < P.n, 1);   // (a failed check arms no bytes: the slot completes empty)
+  ring_arm(R.bar(b), ok ? I.bytes : 0u);
+  if (ok) ring_copy(R.buf(b), I.base + (size_t)(c - 1) * I.stride, I.bytes, R.bar(b));
 }
 // forward item j: the node whose [x; d] is the input, the child whose x is an
 // output (-1: none), and whether the node's u (KT) is an output
@@ -430,9 +431,11 @@ __device__ __forceinline__ void f_issue(const Prob<T>& P, const FIssue<T>& I, co
   int node, child;
   bool kt;
   f_item(P, g, j, node, child, kt);
-  ring_arm(R.bar(b), (kt ? I.kb : 0u) + (child >= 0 ? I.fb : 0u));
-  if (kt) ring_copy(R.buf(b), I.kt + (size_t)node * I.ks, I.kb, R.bar(b));
-  if (child >= 0) ring_copy(R.buf(b) + I.kb, I.mf + (size_t)(child - 1) * I.fs, I.fb, R.bar(b));
+  const bool okk = !kt || SPOCK_CHK(node >= 0 && node < P.n_nl, 2);
+  const bool okf = child < 0 || SPOCK_CHK(child >= 1 && child < P.n, 2);
+  ring_arm(R.bar(b), (kt && okk ? I.kb : 0u) + (child >= 0 && okf ? I.fb : 0u));
+  if (kt && okk) ring_copy(R.buf(b), I.kt + (size_t)node * I.ks, I.kb, R.bar(b));
+  if (child >= 0 && okf) ring_copy(R.buf(b) + I.kb, I.mf + (size_t)(child - 1) * I.fs, I.fb, R.bar(b));
 }
 // first items of the next segment (backward or forward), issued ahead of its call
 template <class T>
@@ -508,7 +511,8 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   if (owner) {
     for (int c = g.c0; c < g.c0 + nbn; ++c) {
       T sv;
-      if (!mb_wait<T>(P.mbb + ((long long)c * w + col) * MB<T>::WPV, eB, sv, err)) {
+      if (!SPOCK_CHK(c >= 1 && c < P.n_nl, 3) ||
+          !mb_wait<T>(P.mbb + ((long long)c * w + col) * MB<T>::WPV, eB, sv, err)) {
         *s_ok = 0;
         break;
       }
@@ -520,7 +524,8 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
     const int m = min(QS, nbl - j0);
     for (int e = t; e < m * nx; e += blockDim.x) {
       const int j = e / nx, k = e - j * nx;
-      st_s<T>(cm.qin + (unsigned)j * ldcb + (unsigned)k * ES, ldc(qbuf + (long long)(leaf0 + j0 + j) * nx + k));
+      if (SPOCK_CHK(leaf0 + j0 + j >= P.n_nl && leaf0 + j0 + j < P.n, 5))
+        st_s<T>(cm.qin + (unsigned)j * ldcb + (unsigned)k * ES, ldc(qbuf + (long long)(leaf0 + j0 + j) * nx + k));
     }
   };
   if (nbl > 0) load_children(0);
@@ -528,7 +533,7 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   int nout = 0;   // output nodes done (bottom = 0, then up the chain)
   auto epilogue = [&](T s) {
     const int i = g.nodes[len - 1 - nout];
-    if (owner) {
+    if (owner && SPOCK_CHK(i >= 0 && i < P.n_nl, 4)) {
       if (col < nx) {
         const T qq = s + preA;
         st_s<T>(cout + (unsigned)col * ES, qq);
@@ -577,7 +582,8 @@ __device__ bool bwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
       epilogue(acc);
       acc = T(0);
     } else {   // uplink: the top's share of its parent's step, to the parent's segment
-      if (owner) MB<T>::put(P.mbb + ((long long)top * w + col) * MB<T>::WPV, acc, eB);
+      if (owner && SPOCK_CHK(top >= 1 && top < P.n_nl, 3))
+        MB<T>::put(P.mbb + ((long long)top * w + col) * MB<T>::WPV, acc, eB);
       acc = T(0);
     }
     if (probe) { const long long c = clock64(); c_mv += c - tc; tc = c; }
@@ -678,7 +684,9 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
     return c >= 0 ? ldr(cvec + (long long)(c - 1) * nx + col) : T(0);
   };
   auto dn_of = [&](int j) -> T {   // d of the child of continuing item j, element t
-    return (j < ncont && t < nu) ? ldc(dbuf + (long long)child_of(j) * nu + t) : T(0);
+    if (!(j < ncont && t < nu)) return T(0);
+    const int ch = child_of(j);
+    return SPOCK_CHK(ch >= 0 && ch < P.n_nl, 8) ? ldc(dbuf + (long long)ch * nu + t) : T(0);
   };
   T cpA = cp_of(0), cpB = cp_of(1);
   T dA = dn_of(0), dB = dn_of(1);
@@ -688,7 +696,8 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   for (int k = t; k < w; k += blockDim.x) {
     T v = T(0);
     if (down) {
-      if (!mb_wait<T>(P.mbf + ((long long)par * w + k) * MB<T>::WPV, eF, v, err)) *s_ok = 0;
+      if (!SPOCK_CHK(par >= 0 && par < P.n_nl, 6) ||
+          !mb_wait<T>(P.mbf + ((long long)par * w + k) * MB<T>::WPV, eF, v, err)) *s_ok = 0;
     } else if (k < nx) {
       v = P.x0s[k];
       stc(vout + o_x + k, zc_add(P, o_x + k, v));
@@ -711,7 +720,8 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
   }
   // [x; d] of the bottom for the segments of its children
   auto publish = [&]() {
-    if (t < w) MB<T>::put(P.mbf + ((long long)bottom * w + t) * MB<T>::WPV, ld_s<T>(cin + (unsigned)t * ES), eF);
+    if (t < w && SPOCK_CHK(bottom >= 0 && bottom < P.n_nl, 6))
+      MB<T>::put(P.mbf + ((long long)bottom * w + t) * MB<T>::WPV, ld_s<T>(cin + (unsigned)t * ES), eF);
   };
   if (jx < 0) publish();   // the root alone: x0
   for (int j = 0; j < nitems && ok; ++j) {
@@ -729,12 +739,12 @@ __device__ bool fwd_cta(const Prob<T>& P, const CtaMem& cm, Ring& ring, int* err
       if (XP == 4 && xcol) v += v2;
     }
     if (lead) {
-      if (xcol && c >= 0) {
+      if (xcol && c >= 0 && SPOCK_CHK(c >= 1 && c < P.n, 7)) {
         const T xc = v + cpA;
         const long long ix = o_x + (long long)c * nx + col;
         stc(vout + ix, zc_add(P, ix, xc));
         if (cont) st_s<T>(cout + (unsigned)col * ES, xc);
-      } else if (ucol && kt) {
+      } else if (ucol && kt && SPOCK_CHK(nd >= 0 && nd < P.n_nl, 7)) {
         const long long iu = o_u + (long long)nd * nu + (col - nx);
         stc(vout + iu, zc_add(P, iu, v + ld_s<T>(cin + (unsigned)col * ES)));
       }

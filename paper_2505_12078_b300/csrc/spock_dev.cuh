@@ -155,6 +155,29 @@ struct Prob {
   unsigned long long* mbf;
 };
 
+// Bounds-checked build (-DSPOCK_CHECKED, libspock_checked.so): the indices
+// the iteration kernel derives from the tree (children, segment nodes,
+// mailbox slots, the factors a bulk copy reads) are checked before use. A
+// failing check records its site in the launch's control block, raises the
+// launch's error word (every CTA then leaves at its next wait) and skips the
+// access; nothing traps. Compiled out otherwise (SPOCK_CHK is true). One
+// launch at a time: the kernel publishes the control block through a
+// per-module global at entry.
+#ifdef SPOCK_CHECKED
+__device__ int* g_chk_err;
+__device__ int* g_chk_site;
+__device__ __forceinline__ bool chk_index(bool ok, int site) {
+  if (!ok && g_chk_err) {
+    atomicCAS(g_chk_site, 0, site);
+    atomicExch(g_chk_err, 3);
+  }
+  return ok;
+}
+#define SPOCK_CHK(ok, site) ::spock::chk_index((ok), (site))
+#else
+#define SPOCK_CHK(ok, site) true
+#endif
+
 // entry k of b^i (conic risk data of node i with m children, first child c0)
 template <class T>
 __device__ __forceinline__ T risk_b(const Prob<T>& P, int i, int c0, int m, int k) {

@@ -95,6 +95,7 @@ struct SolveCtl {
   int final_v;         // index (0..3 of V, TV, VT, TVT) holding the final iterate v
   int final_tv;        // index holding T(v)
   int diag[4];         // first bulk-copy wait that gave up: CTA, barrier, parity, site
+  int check_site;      // bounds-checked build: the first index check that failed (0: none)
   // device time per phase seen by CTA 0 (ns, barrier waits included):
   // 0 prep, 1 backward sweep, 2 forward sweep, 3 T reduction, 4 Anderson dots,
   // 5 direction pass, 6 K2/backtrack passes, 7 count of T evaluations;

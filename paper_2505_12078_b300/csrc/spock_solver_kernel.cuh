@@ -83,6 +83,7 @@ __device__ void s2_block(const Prob<T>& P, int lane, int i, const T* __restrict_
   const T* z = vin;
   const T* eta = vin + P.nz;
   const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
+  if (!SPOCK_CHK(c0 >= 1 && m >= 1 && c0 + m <= P.n && P.yoff[i + 1] - P.yoff[i] == 2 * m + 1, 9)) return;
   const long long yo = P.o_y + P.yoff[i];
   const T al = P.alpha, a = P.avar[i];
   const T eS = ldc(eta + P.e_s + i);
@@ -157,6 +158,7 @@ __device__ void s2_block_tv(const Prob<T>& P, int lane, int i, const T* __restri
   const T* z = vin;
   const T* eta = vin + P.nz;
   const int c0 = P.ch_off[i], m = P.ch_off[i + 1] - c0;
+  if (!SPOCK_CHK(c0 >= 1 && m >= 1 && c0 + m <= P.n && P.yoff[i + 1] - P.yoff[i] == 3 * m + 2, 9)) return;
   const long long yo = P.o_y + P.yoff[i];
   const T al = P.alpha;
   const T eS = ldc(eta + P.e_s + i);
@@ -301,6 +303,7 @@ __device__ void prep_nonleaf(const Prob<T>& P, const Team& tw1, T* s_in, T* s_xb
   const T* z = vin;
   const T* eta = vin + P.nz;
   const int c0 = P.ch_off[i], c1 = P.ch_off[i + 1];
+  if (!SPOCK_CHK(c0 >= 1 && c1 > c0 && c1 <= P.n, 10)) return;
   const T al = P.alpha;
   const T* ec = eta + P.e_c + (long long)i * P.n_c;
   const T* eg = ec + P.nbox + (P.has_ball ? nu : 0);   // general rows of node i
@@ -2249,6 +2252,10 @@ __global__ void __launch_bounds__(256, 1) k_solve(Prob<T> Pk, SolveBufs<T> B, So
     cs.epoch = 0;
   }
   SolveCtl* ctl = B.ctl;
+#ifdef SPOCK_CHECKED
+  if (threadIdx.x == 0) { g_chk_err = &ctl->bar.error; g_chk_site = &ctl->check_site; }
+  __syncthreads();
+#endif
   Grid g;
   g.ctl = &ctl->bar;
   g.flags = B.flags;
@@ -2337,6 +2344,9 @@ __global__ void __launch_bounds__(256, 1)
     k_batch(const Prob<T>* __restrict__ probs, const SolveBufs<T>* __restrict__ bufs,
             const int* __restrict__ tws, SolveOpts o, BatchPlan plan, long long* __restrict__ cycles) {
   extern __shared__ __align__(16) unsigned char smraw[];
+#ifdef SPOCK_CHECKED
+  if (threadIdx.x == 0) g_chk_err = nullptr;   // the checks cover the single-problem launch
+#endif
   __shared__ __align__(16) unsigned char s_prob[sizeof(Prob<T>)];
   __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
   __shared__ int s_ok[MAXTW];
@@ -2406,6 +2416,9 @@ __global__ void __launch_bounds__(256, 1)
             const ServeReq* ring, ServeRes* res, int cap, ServeCtl* ctl, ServeDev* dev,
             unsigned long long idle_ns) {
   extern __shared__ __align__(16) unsigned char smraw[];
+#ifdef SPOCK_CHECKED
+  if (threadIdx.x == 0) g_chk_err = nullptr;   // the checks cover the single-problem launch
+#endif
   __shared__ __align__(16) unsigned char s_prob[sizeof(Prob<T>)];
   __shared__ __align__(8) uint64_t s_bar[2 * MAXTW];
   __shared__ int s_ok[MAXTW];
