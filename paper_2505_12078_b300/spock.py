@@ -31,7 +31,7 @@ EXPORTED = [
     "spock_batch_autotune", "spock_batch_solve",
     "spock_server_create", "spock_server_submit", "spock_server_poll", "spock_server_outstanding",
     "spock_server_destroy", "spock_check", "spock_debug_wait_fault", "spock_server_evict",
-    "spock_server_admitted",
+    "spock_server_admitted", "spock_debug_last_check",
 ]
 
 _dp = C.POINTER(C.c_double)
@@ -152,6 +152,8 @@ def load(path: str = LIB_PATH):
     lib.spock_status_str.restype = C.c_char_p
     lib.spock_version.restype = C.c_int
     lib.spock_debug_wait_fault.argtypes = [C.c_int, C.c_double]
+    lib.spock_debug_last_check.argtypes = []
+    lib.spock_debug_last_check.restype = C.c_int
     _lib = lib
     return lib
 
