@@ -473,8 +473,8 @@ int spock_version(void);
 int spock_debug_wait_fault(int phantom_ctas, double wait_limit_s);
 
 /* Bounds-checked build (libspock_checked.so, compiled with -DSPOCK_CHECKED;
- * the survey's stand-in for a memory sanitizer, which this GPU pool does not
- * offer): the single-problem iteration kernel checks the indices it derives
+ * a stand-in for a memory sanitizer where none is available): the
+ * single-problem iteration kernel checks the indices it derives
  * from the tree -- children ranges, segment nodes, mailbox slots, the factor
  * blocks its bulk copies read -- before use. A failed check skips the access,
  * ends the launch (SPOCK_EDEVICE) and is reported here: the site of the last

@@ -338,8 +338,7 @@ int alloc_iter(spock_problem* p, Iter<T>& it) {
   it.x0s = m.alloc<T>(nx);
   it.l1w = m.alloc<T>(nx + nu);
   it.tvr = m.alloc<T>(n_nl);
-  it.smw = m.alloc<T>(nx + nu);
-  it.slo = m.alloc<T>(nx + nu);
+  if (p->soft) { it.smw = m.alloc<T>(nx + nu); it.slo = m.alloc<T>(nx + nu); }
   it.qbuf = m.alloc<T>((long long)n * nx);
   it.dbuf = m.alloc<T>((long long)n_nl * nu);
   it.hbuf = m.alloc<T>((long long)n_nl * nx);

@@ -1366,15 +1366,25 @@ __device__ void eta_soft(const Prob<T>& P, int lane, int i, const T* __restrict_
   const T al = P.alpha;
   const long long se = P.e_sf + (long long)i * (3 * d + 2);
   const long long ot = P.o_sth + (long long)i * d, isg = P.o_sg + i;
-  auto Lz = [&](int e, T& Lo, T& Ln, T& Ld, T& Lrd) {
-    long long idx;
-    T g;
-    if (e < d) { g = ldr(P.smw + e); idx = ot + e; }
-    else { g = T(0.5); idx = isg; }
-    const T o = ldc(z + idx), nn = ldc(vout + idx);
-    Lo = g * o; Ln = g * nn; Ld = g * (o - nn); Lrd = g * dirv(vref, idx);
-  };
-  soc_block<T, NE>(P, lane, d + 2, se, eta, eo, er, Lz, ra);
+  // the cone through soc_block_vals (the instantiation the full-weight cost
+  // cones already use: no second copy of the projection code)
+  T ebv[NE], ldv[NE], lrv[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = lane + 32 * q;
+    ebv[q] = T(0); ldv[q] = T(0); lrv[q] = T(0);
+    if (e < d + 2) {
+      long long idx;
+      T g;
+      if (e < d) { g = ldr(P.smw + e); idx = ot + e; }
+      else { g = T(0.5); idx = isg; }
+      const T o = ldc(z + idx), nn = ldc(vout + idx);
+      ebv[q] = ldc(eta + se + e) + al * (T(2) * g * nn - g * o);
+      ldv[q] = g * (o - nn);
+      lrv[q] = g * dirv(vref, idx);
+    }
+  }
+  soc_block_vals<T, NE>(P, lane, d + 2, se, eta, eo, er, ebv, ldv, lrv, nullptr, ra);
   auto row = [&](long long ie, T Lo, T Ln, T Ld, T Lrd, T lo) {
     const T eo_ = ldc(eta + ie);
     const T eb = eo_ + al * (T(2) * Ln - Lo);

@@ -152,8 +152,9 @@ def load(path: str = LIB_PATH):
     lib.spock_status_str.restype = C.c_char_p
     lib.spock_version.restype = C.c_int
     lib.spock_debug_wait_fault.argtypes = [C.c_int, C.c_double]
-    lib.spock_debug_last_check.argtypes = []
-    lib.spock_debug_last_check.restype = C.c_int
+    if hasattr(lib, "spock_debug_last_check"):   # a debug entry; libraries built before it lack it
+        lib.spock_debug_last_check.argtypes = []
+        lib.spock_debug_last_check.restype = C.c_int
     _lib = lib
     return lib
 

@@ -105,7 +105,10 @@ def test_full_size_converged_against_oracle_golden():
     whose path weight under the oracle's maximising AV@R weights is positive:
     elsewhere the optimal inputs need not be unique) and risk value must lie
     within max(1e-3, 1.25 x the oracle's own 1e-4 distance) of the 1e-6
-    reference. The whole-vector errors are printed."""
+    reference. A golden file without the 1e-6 solve compares with the 1e-4
+    solve instead, bound 2e-3: two 1e-4 solutions, each within the 1e-3
+    target of the optimum, lie within 2e-3 of each other. The whole-vector
+    errors are printed."""
     import os
     spock = _spock()
     d = np.load(os.path.join(os.path.dirname(__file__), "golden", "large_raocp_converged.npz"))
@@ -114,7 +117,11 @@ def test_full_size_converged_against_oracle_golden():
     sel = d["path_weight"] > 1e-9
     seln = sel[:g.n_nl]
     assert sel.sum() > 10
-    rx, ru, rr = d["tight_x"], d["tight_u"], float(d["tight_risk"])
+    tight = "tight_x" in d.files
+    if tight:
+        rx, ru, rr = d["tight_x"], d["tight_u"], float(d["tight_risk"])
+    else:
+        rx, ru, rr = d["x"], d["u"], float(d["risk"])
     sx = max(1.0, float(np.max(np.abs(rx[sel]))))
     su = max(1.0, float(np.max(np.abs(ru[seln]))))
     sr = max(1.0, abs(rr))
@@ -123,10 +130,13 @@ def test_full_size_converged_against_oracle_golden():
         return (float(np.max(np.abs(x[sel] - rx[sel]))) / sx, float(np.max(np.abs(u[seln] - ru[seln]))) / su,
                 abs(risk - rr) / sr)
 
-    own = dist(d["x"], d["u"], float(d["risk"]))   # the oracle's own 1e-4 solve
-    bound = [max(1e-3, 1.25 * e) for e in own]
-    print(f"oracle 1e-4 solve vs its 1e-6 solve: x {own[0]:.2e} u {own[1]:.2e} risk {own[2]:.2e}; "
-          f"bounds {bound[0]:.2e} {bound[1]:.2e} {bound[2]:.2e}")
+    if tight:
+        own = dist(d["x"], d["u"], float(d["risk"]))   # the oracle's own 1e-4 solve
+        bound = [max(1e-3, 1.25 * e) for e in own]
+        print(f"oracle 1e-4 solve vs its 1e-6 solve: x {own[0]:.2e} u {own[1]:.2e} risk {own[2]:.2e}; "
+              f"bounds {bound[0]:.2e} {bound[1]:.2e} {bound[2]:.2e}")
+    else:
+        bound = [2e-3, 2e-3, 2e-3]
     for prec in (32, 64):
         r = g.solve(p.x0, spock.opts(precision=prec, tol=1e-4, max_iters=200000))
         assert r["status"] == 0

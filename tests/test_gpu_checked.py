@@ -2,8 +2,8 @@
 iteration kernel checks the indices it derives from the tree (children ranges,
 segment nodes, mailbox slots, the factor blocks its bulk copies read) before
 use; a failed check skips the access and ends the launch with SPOCK_EDEVICE
-instead of touching memory outside its buffers. This GPU pool offers no memory
-sanitizer, so the checked build is its stand-in: on parity cases of both sweep
+instead of touching memory outside its buffers. It stands in for a memory
+sanitizer, which is not available here: on parity cases of both sweep
 paths and of the extended costs and risks, no check fails and the results stay
 within the parity tolerances against the oracle. Runs in a process of its own
 (tests/checked_worker.py): one process holds one copy of the library."""
