@@ -14,10 +14,13 @@ the reading taken is stated at the function.
 Pins (tests/test_oracle_pins.py): every step is checked against something
 other than itself (closed forms, dense KKT solves, LP solves of the risk,
 brute force on tiny trees, invariants). The converged solution of a
-constrained problem with AV@R level below 1 has no closed form: its parity is
-unpinned beyond the invariants that every run satisfies (residual, xi1, xi2
-and the complementarity gap vanish; the nested risk of the returned
-trajectory equals s0).
+constrained problem with AV@R level below 1 has no closed form: it is checked
+against the same problem solved as a smooth nonlinear program (the nested
+AV@R in its Rockafellar-Uryasev form, dynamics substituted, scipy's SLSQP)
+with the ball, the input box or the state box active, and against the
+invariants that every run satisfies (residual, xi1, xi2 and the
+complementarity gap vanish; the nested risk of the returned trajectory
+equals s0).
 
 Variable layout (scaled variables, Sec. 4.3 "Sets" and Sec. 4.4 "Linear
 operator L"). Nodes are in breadth-first order, children contiguous; the

@@ -431,6 +431,146 @@ def test_constrained_solution_diagnostics_vanish():
     assert np.all(np.abs(r["x"]) <= 5 + 1e-5) and np.all(np.abs(r["u"]) <= 2 + 1e-5)
 
 
+# --- constrained AV@R optima by a second method ------------------------------------
+def _nested_avar_nlp(p):
+    """The risk-averse problem (Sec. 3) with diagonal weights, boxes and a
+    ball, solved without the conic reformulation: the dynamics are substituted
+    (x^i affine in the stacked inputs U), and every conditional AV@R_a of the
+    nested risk is written as min_t t + (1/a) E_p[(Z - t)_+], the LP dual of
+    the maximisation over {mu in the simplex : mu <= p/a} (Sec. 3.3-3.4). With
+    one t per non-leaf node and one w >= (Z - t)_+ per edge, the problem is the
+    smooth convex program
+
+        min t^0 + (1/a^0) sum_{c child of 0} p^c w^c
+        s.t. w^c >= l^c(x^i, u^i) + V^c - t^i,  w^c >= 0   (i = anc(c)),
+             V^c = t^c + (1/a^c) sum_{d child of c} p^d w^d (non-leaf c),
+             V^c = x^c' Q_N x^c (leaf c), boxes on x^1.. and u, ||u^i|| <= r,
+
+    solved by scipy's SLSQP with exact gradients. Returns (value, u, worst
+    constraint violation)."""
+    n, nx, nu = len(p.anc), p.nx, p.nu
+    n_nl = len(p.avar)
+    nU = n_nl * nu
+    ch = [[] for _ in range(n)]
+    for c in range(1, n):
+        ch[p.anc[c]].append(c)
+    Phi = np.zeros((n, nx, nU))   # x^i = Phi[i] U + phi[i]
+    phi = np.zeros((n, nx))
+    phi[0] = p.x0
+    for c in range(1, n):
+        a = p.anc[c]
+        Phi[c] = p.A[c - 1] @ Phi[a]
+        Phi[c][:, a * nu:(a + 1) * nu] += p.B[c - 1]
+        phi[c] = p.A[c - 1] @ phi[a] + p.c[c - 1]
+    it, iw = nU, nU + n_nl
+    nz = nU + n_nl + (n - 1)
+
+    def edge_cost(U, c):
+        a = p.anc[c]
+        x = Phi[a] @ U + phi[a]
+        u = U[a * nu:(a + 1) * nu]
+        g = 2 * Phi[a].T @ (p.Q[c - 1] * x)
+        g[a * nu:(a + 1) * nu] += 2 * p.R[c - 1] * u
+        return x @ (p.Q[c - 1] * x) + u @ (p.R[c - 1] * u), g
+
+    def obj(z):
+        g = np.zeros(nz)
+        g[it] = 1.0
+        for c in ch[0]:
+            g[iw + c - 1] = p.prob[c] / p.avar[0]
+        return float(g @ z), g
+
+    def edges(z):
+        U, t, w = z[:nU], z[it:iw], z[iw:]
+        val = np.zeros(n - 1)
+        J = np.zeros((n - 1, nz))
+        for c in range(1, n):
+            a = p.anc[c]
+            lc, gl = edge_cost(U, c)
+            if c < n_nl:
+                V = t[c] + sum(p.prob[d] * w[d - 1] for d in ch[c]) / p.avar[c]
+                gV = np.zeros(nU)
+                J[c - 1, it + c] -= 1.0
+                for d in ch[c]:
+                    J[c - 1, iw + d - 1] -= p.prob[d] / p.avar[c]
+            else:
+                x = Phi[c] @ U + phi[c]
+                QN = p.QN[c - n_nl]
+                V, gV = x @ (QN * x), 2 * Phi[c].T @ (QN * x)
+            val[c - 1] = w[c - 1] - lc - V + t[a]
+            J[c - 1, :nU] = -gl - gV
+            J[c - 1, iw + c - 1] += 1.0
+            J[c - 1, it + a] += 1.0
+        return val, J
+
+    cons = [dict(type="ineq", fun=lambda z: edges(z)[0], jac=lambda z: edges(z)[1])]
+    G = np.zeros((2 * (n - 1) * nx, nz))
+    h = np.zeros(2 * (n - 1) * nx)
+    for i in range(1, n):
+        for k in range(nx):
+            r0 = 2 * ((i - 1) * nx + k)
+            G[r0, :nU], h[r0] = -Phi[i][k], p.x_hi[i, k] - phi[i][k]
+            G[r0 + 1, :nU], h[r0 + 1] = Phi[i][k], phi[i][k] - p.x_lo[i, k]
+    cons.append(dict(type="ineq", fun=lambda z: G @ z + h, jac=lambda z: G))
+    if p.u_ball is not None:
+        def ball(z):
+            Ui = z[:nU].reshape(n_nl, nu)
+            return p.u_ball ** 2 - np.sum(Ui * Ui, axis=1)
+
+        def ball_jac(z):
+            J = np.zeros((n_nl, nz))
+            for i in range(n_nl):
+                J[i, i * nu:(i + 1) * nu] = -2 * z[i * nu:(i + 1) * nu]
+            return J
+        cons.append(dict(type="ineq", fun=ball, jac=ball_jac))
+    bounds = [(None, None)] * nz
+    for i in range(n_nl):
+        for k in range(nu):
+            bounds[i * nu + k] = (p.u_lo[i, k], p.u_hi[i, k])
+    for c in range(1, n):
+        bounds[iw + c - 1] = (0.0, None)
+    z0 = np.zeros(nz)
+    z0[iw:] = 100.0
+    r = so.minimize(lambda z: obj(z)[0], z0, jac=lambda z: obj(z)[1], method="SLSQP", bounds=bounds,
+                    constraints=cons, options=dict(ftol=1e-15, maxiter=3000))
+    viol = max(0.0, -float(np.min(np.concatenate([c_["fun"](r.x) for c_ in cons]))))
+    return float(r.fun), r.x[:nU].reshape(n_nl, nu), viol
+
+
+@pytest.mark.parametrize("case", ["ball", "u_box", "x_box"])
+def test_constrained_avar_optimum_by_nonlinear_program(case):
+    """Constrained problems with AV@R levels below 1 (no closed form): the
+    oracle's converged risk value s0 and inputs against the same problem solved
+    as a smooth nonlinear program (_nested_avar_nlp: the nested AV@R by its
+    Rockafellar-Uryasev form, no cones, no preconditioning, no splitting), on
+    cases where the Euclidean ball, the input box or the state box is active
+    at the optimum."""
+    if case == "ball":
+        p = constrained([2, 2], 3, 2, seed=17, avar=0.5, uball=0.6)
+    else:
+        a, ubox, xbox = (0.3, 0.9, 1.2) if case == "u_box" else (0.5, 0.9, 1.1)
+        p = constrained([2, 2], 3, 2, seed=17, avar=a)
+        p.avar = np.full_like(p.avar, a)
+        p.u_lo = np.full_like(p.u_lo, -ubox)
+        p.u_hi = np.full_like(p.u_hi, ubox)
+        p.x_lo, p.x_hi = p.x_lo.copy(), p.x_hi.copy()
+        k = np.arange(1, len(p.anc))[:, None]   # a different box at neighbouring nodes
+        p.x_lo[1:], p.x_hi[1:] = -xbox - 0.04 * (k % 3), xbox + 0.04 * ((k + 1) % 3)
+    val, U, viol = _nested_avar_nlp(p)
+    assert viol < 1e-9
+    r = Oracle(p).solve(tol=1e-9, max_iters=30000, method="spock")
+    assert r["res_inf"] <= 1e-9
+    if case == "ball":   # the constraint under test is active at the optimum
+        assert np.max(np.linalg.norm(r["u"], axis=1)) >= 0.6 * (1 - 1e-6)
+    elif case == "u_box":
+        assert np.max(np.abs(r["u"])) >= 0.9 * (1 - 1e-6)
+    else:
+        xs = r["x"][1:]
+        assert np.any((xs >= p.x_hi[1:] - 1e-6) | (xs <= p.x_lo[1:] + 1e-6))
+    assert abs(r["risk"] - val) <= 1e-7 * abs(val)
+    assert np.max(np.abs(r["u"] - U)) <= 1e-6
+
+
 # --- preconditioning (Sec. 5.4), values worked out by hand ----------------------
 def _golden_precond():
     return json.load(open(os.path.join(GOLDEN, "precondition_tiny.json")))
