@@ -446,11 +446,17 @@ def _nested_avar_nlp(p):
              V^c = t^c + (1/a^c) sum_{d child of c} p^d w^d (non-leaf c),
              V^c = x^c' Q_N x^c (leaf c), boxes on x^1.. and u, ||u^i|| <= r,
 
-    solved by scipy's SLSQP with exact gradients. Returns (value, u, worst
-    constraint violation)."""
+    solved by scipy's SLSQP with exact gradients. An l1 term lambda_0 ||z^i||_1
+    (z^i = (x^i, u^i)) enters l^c through e^i >= |z^i| (lambda_0 1'e^i); a
+    soft-constraint penalty ||max(0, z^i - z_max)||^2 through q^i >= 0,
+    q^i >= z^i - z_max (||q^i||^2). Returns (value, u, worst constraint
+    violation)."""
     n, nx, nu = len(p.anc), p.nx, p.nu
+    d = nx + nu
     n_nl = len(p.avar)
     nU = n_nl * nu
+    lam = float(p.l1 or 0.0)
+    soft = p.soft_max is not None
     ch = [[] for _ in range(n)]
     for c in range(1, n):
         ch[p.anc[c]].append(c)
@@ -463,15 +469,33 @@ def _nested_avar_nlp(p):
         Phi[c][:, a * nu:(a + 1) * nu] += p.B[c - 1]
         phi[c] = p.A[c - 1] @ phi[a] + p.c[c - 1]
     it, iw = nU, nU + n_nl
-    nz = nU + n_nl + (n - 1)
+    ie = iw + (n - 1)                       # e^i (l1 term), d per non-leaf node
+    iq = ie + (n_nl * d if lam > 0 else 0)  # q^i (soft penalty)
+    nz = iq + (n_nl * d if soft else 0)
 
-    def edge_cost(U, c):
+    def zmap(i):   # z^i = Z U + z0
+        Z = np.zeros((d, nU))
+        Z[:nx] = Phi[i]
+        Z[nx:, i * nu:(i + 1) * nu] = np.eye(nu)
+        return Z, np.concatenate([phi[i], np.zeros(nu)])
+
+    def edge_cost(z, c):
         a = p.anc[c]
+        U = z[:nU]
         x = Phi[a] @ U + phi[a]
         u = U[a * nu:(a + 1) * nu]
-        g = 2 * Phi[a].T @ (p.Q[c - 1] * x)
+        g = np.zeros(nz)
+        g[:nU] = 2 * Phi[a].T @ (p.Q[c - 1] * x)
         g[a * nu:(a + 1) * nu] += 2 * p.R[c - 1] * u
-        return x @ (p.Q[c - 1] * x) + u @ (p.R[c - 1] * u), g
+        val = x @ (p.Q[c - 1] * x) + u @ (p.R[c - 1] * u)
+        if lam > 0:
+            val += lam * np.sum(z[ie + a * d:ie + (a + 1) * d])
+            g[ie + a * d:ie + (a + 1) * d] = lam
+        if soft:
+            q = z[iq + a * d:iq + (a + 1) * d]
+            val += q @ q
+            g[iq + a * d:iq + (a + 1) * d] = 2 * q
+        return val, g
 
     def obj(z):
         g = np.zeros(nz)
@@ -481,36 +505,44 @@ def _nested_avar_nlp(p):
         return float(g @ z), g
 
     def edges(z):
-        U, t, w = z[:nU], z[it:iw], z[iw:]
+        U, t, w = z[:nU], z[it:iw], z[iw:ie]
         val = np.zeros(n - 1)
         J = np.zeros((n - 1, nz))
         for c in range(1, n):
             a = p.anc[c]
-            lc, gl = edge_cost(U, c)
+            lc, gl = edge_cost(z, c)
+            J[c - 1] = -gl
             if c < n_nl:
-                V = t[c] + sum(p.prob[d] * w[d - 1] for d in ch[c]) / p.avar[c]
-                gV = np.zeros(nU)
+                V = t[c] + sum(p.prob[k] * w[k - 1] for k in ch[c]) / p.avar[c]
                 J[c - 1, it + c] -= 1.0
-                for d in ch[c]:
-                    J[c - 1, iw + d - 1] -= p.prob[d] / p.avar[c]
+                for k in ch[c]:
+                    J[c - 1, iw + k - 1] -= p.prob[k] / p.avar[c]
             else:
                 x = Phi[c] @ U + phi[c]
                 QN = p.QN[c - n_nl]
-                V, gV = x @ (QN * x), 2 * Phi[c].T @ (QN * x)
+                V = x @ (QN * x)
+                J[c - 1, :nU] -= 2 * Phi[c].T @ (QN * x)
             val[c - 1] = w[c - 1] - lc - V + t[a]
-            J[c - 1, :nU] = -gl - gV
             J[c - 1, iw + c - 1] += 1.0
             J[c - 1, it + a] += 1.0
         return val, J
 
     cons = [dict(type="ineq", fun=lambda z: edges(z)[0], jac=lambda z: edges(z)[1])]
-    G = np.zeros((2 * (n - 1) * nx, nz))
-    h = np.zeros(2 * (n - 1) * nx)
+    rows, rhs = [], []
     for i in range(1, n):
         for k in range(nx):
-            r0 = 2 * ((i - 1) * nx + k)
-            G[r0, :nU], h[r0] = -Phi[i][k], p.x_hi[i, k] - phi[i][k]
-            G[r0 + 1, :nU], h[r0 + 1] = Phi[i][k], phi[i][k] - p.x_lo[i, k]
+            r_ = np.zeros(nz); r_[:nU] = -Phi[i][k]; rows.append(r_); rhs.append(p.x_hi[i, k] - phi[i][k])
+            r_ = np.zeros(nz); r_[:nU] = Phi[i][k]; rows.append(r_); rhs.append(phi[i][k] - p.x_lo[i, k])
+    for i in range(n_nl):
+        Z, z0 = zmap(i)
+        for k in range(d):
+            if lam > 0:   # e - z >= 0, e + z >= 0
+                r_ = np.zeros(nz); r_[:nU] = -Z[k]; r_[ie + i * d + k] = 1.0; rows.append(r_); rhs.append(-z0[k])
+                r_ = np.zeros(nz); r_[:nU] = Z[k]; r_[ie + i * d + k] = 1.0; rows.append(r_); rhs.append(z0[k])
+            if soft:      # q - z + z_max >= 0
+                r_ = np.zeros(nz); r_[:nU] = -Z[k]; r_[iq + i * d + k] = 1.0; rows.append(r_)
+                rhs.append(p.soft_max[k] - z0[k])
+    G, h = np.asarray(rows), np.asarray(rhs)
     cons.append(dict(type="ineq", fun=lambda z: G @ z + h, jac=lambda z: G))
     if p.u_ball is not None:
         def ball(z):
@@ -527,17 +559,19 @@ def _nested_avar_nlp(p):
     for i in range(n_nl):
         for k in range(nu):
             bounds[i * nu + k] = (p.u_lo[i, k], p.u_hi[i, k])
-    for c in range(1, n):
-        bounds[iw + c - 1] = (0.0, None)
+    for k in range(iw, ie):
+        bounds[k] = (0.0, None)
+    for k in range(iq, nz):
+        bounds[k] = (0.0, None)
     z0 = np.zeros(nz)
-    z0[iw:] = 100.0
+    z0[iw:ie] = 100.0
     r = so.minimize(lambda z: obj(z)[0], z0, jac=lambda z: obj(z)[1], method="SLSQP", bounds=bounds,
                     constraints=cons, options=dict(ftol=1e-15, maxiter=3000))
     viol = max(0.0, -float(np.min(np.concatenate([c_["fun"](r.x) for c_ in cons]))))
     return float(r.fun), r.x[:nU].reshape(n_nl, nu), viol
 
 
-@pytest.mark.parametrize("case", ["ball", "u_box", "x_box"])
+@pytest.mark.parametrize("case", ["ball", "u_box", "x_box", "l1", "soft"])
 def test_constrained_avar_optimum_by_nonlinear_program(case):
     """Constrained problems with AV@R levels below 1 (no closed form): the
     oracle's converged risk value s0 and inputs against the same problem solved
@@ -547,6 +581,12 @@ def test_constrained_avar_optimum_by_nonlinear_program(case):
     at the optimum."""
     if case == "ball":
         p = constrained([2, 2], 3, 2, seed=17, avar=0.5, uball=0.6)
+    elif case in ("l1", "soft"):   # with the ball, AV@R 0.5
+        p = constrained([2, 2], 3, 2, seed=17, avar=0.5, uball=0.6)
+        if case == "l1":
+            p.l1 = 0.4
+        else:
+            p.soft_max = np.full(p.nx + p.nu, 0.3)
     else:
         a, ubox, xbox = (0.3, 0.9, 1.2) if case == "u_box" else (0.5, 0.9, 1.1)
         p = constrained([2, 2], 3, 2, seed=17, avar=a)
@@ -562,6 +602,10 @@ def test_constrained_avar_optimum_by_nonlinear_program(case):
     assert r["res_inf"] <= 1e-9
     if case == "ball":   # the constraint under test is active at the optimum
         assert np.max(np.linalg.norm(r["u"], axis=1)) >= 0.6 * (1 - 1e-6)
+    elif case == "l1":   # some entries sit at the kink of |.|
+        assert np.min(np.abs(r["u"])) <= 1e-6
+    elif case == "soft":   # the penalty is active
+        assert np.max(np.hstack([r["x"][:len(p.avar)], r["u"]])) > 0.3 + 1e-3
     elif case == "u_box":
         assert np.max(np.abs(r["u"])) >= 0.9 * (1 - 1e-6)
     else:
