@@ -449,14 +449,19 @@ def _nested_avar_nlp(p):
     solved by scipy's SLSQP with exact gradients. An l1 term lambda_0 ||z^i||_1
     (z^i = (x^i, u^i)) enters l^c through e^i >= |z^i| (lambda_0 1'e^i); a
     soft-constraint penalty ||max(0, z^i - z_max)||^2 through q^i >= 0,
-    q^i >= z^i - z_max (||q^i||^2). Returns (value, u, worst constraint
-    violation)."""
+    q^i >= z^i - z_max (||q^i||^2). With the total-variation risk (worst
+    expectation over {mu in the simplex : ||mu - p||_1 <= r}) the LP dual is
+    min t + lambda r + p'g over lambda >= 0, |g_c| <= lambda, g_c >= Z_c - t: w
+    plays g (free), one lambda per non-leaf node. Returns (value, u, worst
+    constraint violation)."""
     n, nx, nu = len(p.anc), p.nx, p.nu
     d = nx + nu
     n_nl = len(p.avar)
     nU = n_nl * nu
     lam = float(p.l1 or 0.0)
     soft = p.soft_max is not None
+    tv = p.tv is not None
+    wco = np.array([p.prob[c] / (1.0 if tv else p.avar[p.anc[c]]) for c in range(1, n)])   # w's weight in V
     ch = [[] for _ in range(n)]
     for c in range(1, n):
         ch[p.anc[c]].append(c)
@@ -471,7 +476,8 @@ def _nested_avar_nlp(p):
     it, iw = nU, nU + n_nl
     ie = iw + (n - 1)                       # e^i (l1 term), d per non-leaf node
     iq = ie + (n_nl * d if lam > 0 else 0)  # q^i (soft penalty)
-    nz = iq + (n_nl * d if soft else 0)
+    il = iq + (n_nl * d if soft else 0)     # lambda^i (total-variation risk)
+    nz = il + (n_nl if tv else 0)
 
     def zmap(i):   # z^i = Z U + z0
         Z = np.zeros((d, nU))
@@ -501,7 +507,9 @@ def _nested_avar_nlp(p):
         g = np.zeros(nz)
         g[it] = 1.0
         for c in ch[0]:
-            g[iw + c - 1] = p.prob[c] / p.avar[0]
+            g[iw + c - 1] = wco[c - 1]
+        if tv:
+            g[il] = p.tv[0]
         return float(g @ z), g
 
     def edges(z):
@@ -513,10 +521,13 @@ def _nested_avar_nlp(p):
             lc, gl = edge_cost(z, c)
             J[c - 1] = -gl
             if c < n_nl:
-                V = t[c] + sum(p.prob[k] * w[k - 1] for k in ch[c]) / p.avar[c]
+                V = t[c] + sum(wco[k - 1] * w[k - 1] for k in ch[c])
                 J[c - 1, it + c] -= 1.0
                 for k in ch[c]:
-                    J[c - 1, iw + k - 1] -= p.prob[k] / p.avar[c]
+                    J[c - 1, iw + k - 1] -= wco[k - 1]
+                if tv:
+                    V += p.tv[c] * z[il + c]
+                    J[c - 1, il + c] -= p.tv[c]
             else:
                 x = Phi[c] @ U + phi[c]
                 QN = p.QN[c - n_nl]
@@ -542,6 +553,10 @@ def _nested_avar_nlp(p):
             if soft:      # q - z + z_max >= 0
                 r_ = np.zeros(nz); r_[:nU] = -Z[k]; r_[iq + i * d + k] = 1.0; rows.append(r_)
                 rhs.append(p.soft_max[k] - z0[k])
+    if tv:   # lambda^a -/+ g_c >= 0
+        for c in range(1, n):
+            for sg in (-1.0, 1.0):
+                r_ = np.zeros(nz); r_[il + p.anc[c]] = 1.0; r_[iw + c - 1] = sg; rows.append(r_); rhs.append(0.0)
     G, h = np.asarray(rows), np.asarray(rhs)
     cons.append(dict(type="ineq", fun=lambda z: G @ z + h, jac=lambda z: G))
     if p.u_ball is not None:
@@ -559,19 +574,18 @@ def _nested_avar_nlp(p):
     for i in range(n_nl):
         for k in range(nu):
             bounds[i * nu + k] = (p.u_lo[i, k], p.u_hi[i, k])
-    for k in range(iw, ie):
-        bounds[k] = (0.0, None)
-    for k in range(iq, nz):
+    for k in list(range(iw if not tv else ie, ie)) + list(range(iq, nz)):
         bounds[k] = (0.0, None)
     z0 = np.zeros(nz)
     z0[iw:ie] = 100.0
+    z0[il:] = 100.0
     r = so.minimize(lambda z: obj(z)[0], z0, jac=lambda z: obj(z)[1], method="SLSQP", bounds=bounds,
                     constraints=cons, options=dict(ftol=1e-15, maxiter=3000))
     viol = max(0.0, -float(np.min(np.concatenate([c_["fun"](r.x) for c_ in cons]))))
     return float(r.fun), r.x[:nU].reshape(n_nl, nu), viol
 
 
-@pytest.mark.parametrize("case", ["ball", "u_box", "x_box", "l1", "soft"])
+@pytest.mark.parametrize("case", ["ball", "u_box", "x_box", "l1", "soft", "tv"])
 def test_constrained_avar_optimum_by_nonlinear_program(case):
     """Constrained problems with AV@R levels below 1 (no closed form): the
     oracle's converged risk value s0 and inputs against the same problem solved
@@ -581,12 +595,14 @@ def test_constrained_avar_optimum_by_nonlinear_program(case):
     at the optimum."""
     if case == "ball":
         p = constrained([2, 2], 3, 2, seed=17, avar=0.5, uball=0.6)
-    elif case in ("l1", "soft"):   # with the ball, AV@R 0.5
+    elif case in ("l1", "soft", "tv"):   # with the ball, AV@R 0.5
         p = constrained([2, 2], 3, 2, seed=17, avar=0.5, uball=0.6)
         if case == "l1":
             p.l1 = 0.4
-        else:
+        elif case == "soft":
             p.soft_max = np.full(p.nx + p.nu, 0.3)
+        else:   # total-variation risk of radius 0.4 at every non-leaf node
+            p.tv = np.full(len(p.avar), 0.4)
     else:
         a, ubox, xbox = (0.3, 0.9, 1.2) if case == "u_box" else (0.5, 0.9, 1.1)
         p = constrained([2, 2], 3, 2, seed=17, avar=a)
@@ -600,7 +616,7 @@ def test_constrained_avar_optimum_by_nonlinear_program(case):
     assert viol < 1e-9
     r = Oracle(p).solve(tol=1e-9, max_iters=30000, method="spock")
     assert r["res_inf"] <= 1e-9
-    if case == "ball":   # the constraint under test is active at the optimum
+    if case in ("ball", "tv"):   # the constraint under test is active at the optimum
         assert np.max(np.linalg.norm(r["u"], axis=1)) >= 0.6 * (1 - 1e-6)
     elif case == "l1":   # some entries sit at the kink of |.|
         assert np.min(np.abs(r["u"])) <= 1e-6
