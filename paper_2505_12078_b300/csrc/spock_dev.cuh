@@ -616,6 +616,127 @@ __device__ __forceinline__ bool grid_allreduce(Grid& g, double (&v)[NRED], doubl
 }
 
 // ---------------------------------------------------------------------------
+// The same reductions on float pairs for the FP32 kernels. A pair (h, l)
+// stands for h + l (double-float); the FP32 partials enter as (v, 0), a
+// compensated sum as (sum, error). FP64 issues at about 1/77 of the FP32 rate
+// on this part, and the FP64 warp, CTA and grid combines above cost several
+// thousand cycles per all-reduce; these run on the FP32 pipe. A sum step is an
+// error-free two-sum of the high parts (Knuth's TwoSum) with the low parts
+// added to its error term and the result renormalised by a fast two-sum
+// (Dekker): relative error about 2^-44 of the summands' magnitudes, far below
+// the FP32 partials' own. The max slot takes the maximum of the high parts'
+// bit patterns (non-negative values; a NaN wins). Fixed order throughout, so
+// every CTA gets bit-identical results; they are returned as doubles (h + l,
+// exact in FP64).
+// ---------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+
+__device__ __forceinline__ DF df_comb(DF a, DF b, bool is_max) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  const float t = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, t);
+  const DF sum{h, __fsub_rn(t, __fsub_rn(h, s))};
+  const DF mx{__int_as_float(max(__float_as_int(a.h), __float_as_int(b.h))), 0.0f};
+  return is_max ? mx : sum;
+}
+
+__device__ __forceinline__ DF df_shfl_xor(DF a, int m) {
+  return DF{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
+}
+
+// warp_reduce8 on pairs: the same butterfly, the same lane holding each total.
+__device__ __forceinline__ DF warp_reduce8_df(const DF (&v)[NRED], int max_slot) {
+  static_assert(NRED == 8, "warp_reduce8_df is written for 8 values");
+  const int lane = threadIdx.x & 31;
+  const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0, h2 = (lane & 4) != 0;
+  DF u[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const DF keep = h4 ? v[4 + j] : v[j];
+    const DF send = h4 ? v[j] : v[4 + j];
+    u[j] = df_comb(keep, df_shfl_xor(send, 16), (h4 ? 4 : 0) + j == max_slot);
+  }
+  DF w[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const DF keep = h3 ? u[2 + j] : u[j];
+    const DF send = h3 ? u[j] : u[2 + j];
+    w[j] = df_comb(keep, df_shfl_xor(send, 8), (h4 ? 4 : 0) + (h3 ? 2 : 0) + j == max_slot);
+  }
+  const bool mx = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0) == max_slot;
+  DF x = df_comb(h2 ? w[1] : w[0], df_shfl_xor(h2 ? w[0] : w[1], 4), mx);
+  x = df_comb(x, df_shfl_xor(x, 2), mx);
+  x = df_comb(x, df_shfl_xor(x, 1), mx);
+  return x;
+}
+
+// CTA totals of NRED pairs: on return (after a CTA barrier) scratch[k * 32]
+// holds the total of value k. scratch: NRED * 32 pairs of shared memory.
+__device__ __forceinline__ void block_reduce_df(const DF (&v)[NRED], DF* scratch, int max_slot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const DF x = warp_reduce8_df(v, max_slot);
+  if ((lane & 3) == 0) scratch[(lane >> 2) * 32 + w] = x;
+  __syncthreads();
+  if (w == 0 && lane < NRED) {   // lane k adds the warps' totals of value k
+    DF t = scratch[lane * 32];
+    for (int j = 1; j < nw; ++j) t = df_comb(t, scratch[lane * 32 + j], lane == max_slot);
+    scratch[lane * 32] = t;
+  }
+  __syncthreads();
+}
+
+// grid_allreduce on pairs: out[k] (every thread) = the grid total of value k
+// as a double. scratch: NRED * 32 pairs, tot: NRED doubles, both shared.
+__device__ __forceinline__ bool grid_allreduce_df(Grid& g, const DF (&v)[NRED], double (&out)[NRED], DF* scratch,
+                                                  double* tot, int max_slot) {
+  const bool probe = !g.local && g.prof && blockIdx.x == 0 && threadIdx.x == 0;
+  const long long t0 = probe ? clock64() : 0;
+  block_reduce_df(v, scratch, max_slot);
+  bool ok = true;
+  if (!g.local) {
+    const unsigned e = ++g.epoch;
+    float2* part = reinterpret_cast<float2*>(g.partials) + (size_t)(e & 1u) * g.size * NRED;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < NRED; ++k) {
+        const DF t = scratch[k * 32];
+        __stcg(part + (size_t)g.rank * NRED + k, make_float2(t.h, t.l));
+      }
+      st_release(g.flags + g.rank, e);
+    }
+    ok = poll_flags(g, e);
+    DF x[NRED];
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) x[k] = DF{0.0f, 0.0f};
+    for (int c = threadIdx.x; c < g.size; c += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < NRED; ++k) {
+        const float2 y = __ldcg(part + (size_t)c * NRED + k);
+        x[k] = df_comb(x[k], DF{y.x, y.y}, k == max_slot);
+      }
+    }
+    block_reduce_df(x, scratch, max_slot);
+  }
+  if (threadIdx.x < NRED) {
+    const DF t = scratch[threadIdx.x * 32];
+    tot[threadIdx.x] = (double)t.h + (double)t.l;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) out[k] = tot[k];
+  __syncthreads();   // the next call may overwrite scratch and tot
+  if (probe) {
+    g.prof[13] += (unsigned long long)(clock64() - t0);
+    g.prof[15] += 1;
+  }
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
 // mbarrier + bulk copy (cp.async.bulk, global -> shared) with a bounded wait
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) {

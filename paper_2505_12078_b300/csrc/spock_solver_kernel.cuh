@@ -1597,10 +1597,22 @@ __device__ __noinline__ bool evalT(const Prob<T>& P, const Team& tm, const Views
     }
   }
   double v[NRED];
-#pragma unroll
-  for (int k = 0; k < NRED; ++k) v[k] = (double)ra.v[k];
   __shared__ double scratch[NRED * 32];
-  const bool ok = grid_allreduce(g, v, scratch, R_MAX);
+  bool ok;
+  // FP32 partials combined as float pairs in the one-chunk kernels; the
+  // two-chunk FP32 kernel keeps the FP64 combine (with the pairs its team
+  // sweeps ran about 20 % slower on the 498-node, nx = 128 problem)
+  if constexpr (sizeof(T) == 4 && CH == 1) {
+    DF dv[NRED];
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) dv[k] = DF{ra.v[k], 0.0f};
+    __shared__ double s_tot[NRED];
+    ok = grid_allreduce_df(g, dv, v, reinterpret_cast<DF*>(scratch), s_tot, R_MAX);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) v[k] = (double)ra.v[k];
+    ok = grid_allreduce(g, v, scratch, R_MAX);
+  }
 #pragma unroll
   for (int k = 0; k < NRED; ++k) red[k] = v[k];
   pc.mark(ctl, 3);
@@ -2004,13 +2016,23 @@ __device__ void solve_loop(const Prob<T>& P, const SolveBufs<T>& B, const SolveO
           stc(B.VP + e, v);
           stc(B.RP + e, ro);
         }
-        if constexpr (sizeof(T) == 4) {
-          for (int a = 0; a < 2 * AA_M; ++a) acc[a] = (double)chi[a] + (double)clo[a];
-        }
-        for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? acc[a] : 0.0;
         {
           __shared__ double scratch2[NRED * 32];
-          if (!grid_allreduce(g, dd, scratch2, -1)) goto fail;
+          if constexpr (sizeof(T) == 4 && CH == 1) {   // the compensated sums enter as pairs (sum, error)
+            DF df[NRED];
+#pragma unroll
+            for (int a = 0; a < NRED; ++a) df[a] = DF{0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < 2 * AA_M; ++a) df[a] = DF{chi[a], clo[a]};
+            __shared__ double s_tot2[NRED];
+            if (!grid_allreduce_df(g, df, dd, reinterpret_cast<DF*>(scratch2), s_tot2, -1)) goto fail;
+          } else {
+            if constexpr (sizeof(T) == 4) {
+              for (int a = 0; a < 2 * AA_M; ++a) acc[a] = (double)chi[a] + (double)clo[a];
+            }
+            for (int a = 0; a < NRED; ++a) dd[a] = (a < 2 * AA_M) ? acc[a] : 0.0;
+            if (!grid_allreduce(g, dd, scratch2, -1)) goto fail;
+          }
         }
         if (push) {
           if (count < AA_M) ++count;
