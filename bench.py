@@ -167,6 +167,44 @@ def cpu_baseline(p, seconds=12.0):
                       f"workload from a cold start, FP64 numpy oracle, {el:.1f} s"}
 
 
+ORACLE_BATCH_ITERS = 10      # SPOCK iterations per problem in the oracle's all-core batched sample
+
+
+def _oracle_iters(task):
+    """One problem of the uneven draw through the oracle, in a spawned worker:
+    its set-up untimed, then ORACLE_BATCH_ITERS SPOCK iterations from a cold
+    start timed."""
+    i, iters = task
+    from oracle.spock_oracle import Oracle
+    o = Oracle(_gen(i))
+    t = time.time()
+    r = o.solve(tol=0.0, max_iters=iters)
+    return int(r["iters"]), time.time() - t
+
+
+def cpu_baseline_batched(probs):
+    """The oracle over the host's cores on the batched workload: the
+    PLAIN_SAMPLE problems spread over the draw's sizes (the sample the plain
+    FP64 GPU method is timed on), one spawned process per problem and core,
+    ORACLE_BATCH_ITERS iterations each. Reported: problem-iterations per
+    second of one core over the sample (sum of iterations / sum of times), and
+    that times the cores used (the problems are independent)."""
+    import multiprocessing as mp
+    idx = _stratified(probs, PLAIN_SAMPLE)
+    cores = max(1, min(len(idx), os.cpu_count() or 1))
+    t = time.time()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_iters, [(i, ORACLE_BATCH_ITERS) for i in idx], chunksize=1)
+    wall = time.time() - t
+    it = sum(r[0] for r in res)
+    sec = sum(r[1] for r in res)
+    return {"kind": "oracle", "cores": cores, "iters_per_s_one_core": it / sec,
+            "iters_per_s_all_cores": cores * it / sec, "unit": "iter/s",
+            "sample": f"{len(idx)} problems spread over the draw's sizes, {ORACLE_BATCH_ITERS} SPOCK "
+                      f"iterations each from a cold start, FP64 numpy oracle, one process per problem on "
+                      f"{cores} cores, {wall:.1f} s wall with set-up"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -691,6 +729,11 @@ def run_ours(args, rank, world, local_rank, dist):
                           "infeas": r["info"]["infeas"], "gap": r["info"]["gap"]}}
     launches = sum(launches_per_solve(prec, i) for i in infos)
     cpu = cpu_baseline(p) if world == 1 else None
+    if cpu is not None and bprobs is not None:
+        try:   # the oracle over all host cores on the batched workload
+            cpu["batched"] = cpu_baseline_batched(bprobs)
+        except Exception as e:   # noqa: BLE001
+            cpu["batched"] = {"error": f"{type(e).__name__}: {e}"}
     extras = {}
     t_extra = time.time()
 
