@@ -102,10 +102,12 @@ def test_full_size_converged_against_oracle_golden():
     the distance to the optimum, so two solves to 1e-4 can differ by more than
     1e-3 in u even though each is a valid 1e-4 solution (reading C-19). The
     FP32 and FP64 solves' x and u (relative to max(1, max|.|), on the nodes
-    whose path weight under the oracle's maximising AV@R weights is positive:
-    elsewhere the optimal inputs need not be unique) and risk value must lie
-    within max(1e-3, 1.25 x the oracle's own 1e-4 distance) of the 1e-6
-    reference. A golden file without the 1e-6 solve compares with the 1e-4
+    whose path weight under the 1e-6 solve's maximising AV@R weights is
+    positive: elsewhere the optimal inputs need not be unique) and risk value
+    must lie within max(1e-3, 1.25 x the oracle's own 1e-4 distance) of the
+    1e-6 reference. (On the 1012-node problem the oracle's 1e-4 solve is about
+    5 % from the 1e-6 solve in x and u on that support, and the two supports
+    share few nodes: the maximising weights move with the iterate.) A golden file without the 1e-6 solve compares with the 1e-4
     solve instead, bound 2e-3: two 1e-4 solutions, each within the 1e-3
     target of the optimum, lie within 2e-3 of each other. The whole-vector
     errors are printed."""
@@ -114,14 +116,15 @@ def test_full_size_converged_against_oracle_golden():
     d = np.load(os.path.join(os.path.dirname(__file__), "golden", "large_raocp_converged.npz"))
     p = synth.large_raocp()
     g = spock.Problem(p)
-    sel = d["path_weight"] > 1e-9
-    seln = sel[:g.n_nl]
-    assert sel.sum() > 10
     tight = "tight_x" in d.files
-    if tight:
+    if tight:   # the reference and its support: the 1e-6 solve's
         rx, ru, rr = d["tight_x"], d["tight_u"], float(d["tight_risk"])
+        sel = d["tight_path_weight"] > 1e-9
     else:
         rx, ru, rr = d["x"], d["u"], float(d["risk"])
+        sel = d["path_weight"] > 1e-9
+    seln = sel[:g.n_nl]
+    assert sel.sum() > 10
     sx = max(1.0, float(np.max(np.abs(rx[sel]))))
     su = max(1.0, float(np.max(np.abs(ru[seln]))))
     sr = max(1.0, abs(rr))
