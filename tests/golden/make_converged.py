@@ -17,7 +17,8 @@ the exact optimum than either 1e-4 solution.
 
 Usage: python -m tests.golden.make_converged large_raocp [--tight 1e-6]
        python -m tests.golden.make_converged tree_sweep_b4
-The large problem takes about 20-30 minutes on one core.
+The large problem took 60 minutes to 1e-4 (16 134 iterations) and 3.5 hours
+more to 1e-6 (55 702 iterations) on two cores of a CPU host.
 """
 import argparse
 import os
