@@ -17,9 +17,9 @@ brute force on tiny trees, invariants). The converged solution of a
 constrained problem with AV@R level below 1 has no closed form: it is checked
 against the same problem solved as a smooth nonlinear program (the nested
 AV@R in its Rockafellar-Uryasev form, dynamics substituted, scipy's SLSQP)
-with the ball, the input box or the state box active (also with l1 or
-soft-constraint costs, and with the total-variation risk through its LP
-dual), and against the
+with the ball, the input box, the state box or general rows active (also
+with full weights and linear terms, with l1 or soft-constraint costs, and
+with the total-variation risk through its LP dual), and against the
 invariants that every run satisfies (residual, xi1, xi2 and the
 complementarity gap vanish; the nested risk of the returned trajectory
 equals s0).

@@ -485,15 +485,24 @@ def _nested_avar_nlp(p):
         Z[nx:, i * nu:(i + 1) * nu] = np.eye(nu)
         return Z, np.concatenate([phi[i], np.zeros(nu)])
 
+    def quad(W, y):   # y'Wy and its gradient, W full or its diagonal
+        Wy = W @ y if W.ndim == 2 else W * y
+        return y @ Wy, 2 * Wy
+
     def edge_cost(z, c):
         a = p.anc[c]
         U = z[:nU]
         x = Phi[a] @ U + phi[a]
         u = U[a * nu:(a + 1) * nu]
+        vx, gx = quad(p.Q[c - 1], x)
+        vu, gu = quad(p.R[c - 1], u)
+        if p.q is not None:   # linear terms q'x + r'u
+            vx, gx = vx + p.q[c - 1] @ x, gx + p.q[c - 1]
+            vu, gu = vu + p.r[c - 1] @ u, gu + p.r[c - 1]
         g = np.zeros(nz)
-        g[:nU] = 2 * Phi[a].T @ (p.Q[c - 1] * x)
-        g[a * nu:(a + 1) * nu] += 2 * p.R[c - 1] * u
-        val = x @ (p.Q[c - 1] * x) + u @ (p.R[c - 1] * u)
+        g[:nU] = Phi[a].T @ gx
+        g[a * nu:(a + 1) * nu] += gu
+        val = vx + vu
         if lam > 0:
             val += lam * np.sum(z[ie + a * d:ie + (a + 1) * d])
             g[ie + a * d:ie + (a + 1) * d] = lam
@@ -530,9 +539,10 @@ def _nested_avar_nlp(p):
                     J[c - 1, il + c] -= p.tv[c]
             else:
                 x = Phi[c] @ U + phi[c]
-                QN = p.QN[c - n_nl]
-                V = x @ (QN * x)
-                J[c - 1, :nU] -= 2 * Phi[c].T @ (QN * x)
+                V, gV = quad(p.QN[c - n_nl], x)
+                if p.qN is not None:
+                    V, gV = V + p.qN[c - n_nl] @ x, gV + p.qN[c - n_nl]
+                J[c - 1, :nU] -= Phi[c].T @ gV
             val[c - 1] = w[c - 1] - lc - V + t[a]
             J[c - 1, iw + c - 1] += 1.0
             J[c - 1, it + a] += 1.0
@@ -540,10 +550,24 @@ def _nested_avar_nlp(p):
 
     cons = [dict(type="ineq", fun=lambda z: edges(z)[0], jac=lambda z: edges(z)[1])]
     rows, rhs = [], []
-    for i in range(1, n):
-        for k in range(nx):
-            r_ = np.zeros(nz); r_[:nU] = -Phi[i][k]; rows.append(r_); rhs.append(p.x_hi[i, k] - phi[i][k])
-            r_ = np.zeros(nz); r_[:nU] = Phi[i][k]; rows.append(r_); rhs.append(phi[i][k] - p.x_lo[i, k])
+
+    def two_sided(a_row, a0, lo, hi):   # lo <= a_row U + a0 <= hi
+        r_ = np.zeros(nz); r_[:nU] = -a_row; rows.append(r_); rhs.append(hi - a0)
+        r_ = np.zeros(nz); r_[:nU] = a_row; rows.append(r_); rhs.append(a0 - lo)
+    if p.x_lo is not None:
+        for i in range(1, n):
+            for k in range(nx):
+                two_sided(Phi[i][k], phi[i][k], p.x_lo[i, k], p.x_hi[i, k])
+    if p.Gx is not None:   # general rows at the non-leaf nodes
+        for i in range(n_nl):
+            Z, z0 = zmap(i)
+            Gz = np.hstack([p.Gx, p.Gu])
+            for k in range(Gz.shape[0]):
+                two_sided(Gz[k] @ Z, Gz[k] @ z0, p.g_lo[i, k], p.g_hi[i, k])
+    if p.GN is not None:   # general rows at the leaves
+        for j in range(n_nl, n):
+            for k in range(p.GN.shape[0]):
+                two_sided(p.GN[k] @ Phi[j], p.GN[k] @ phi[j], p.gN_lo[j - n_nl, k], p.gN_hi[j - n_nl, k])
     for i in range(n_nl):
         Z, z0 = zmap(i)
         for k in range(d):
@@ -571,9 +595,10 @@ def _nested_avar_nlp(p):
             return J
         cons.append(dict(type="ineq", fun=ball, jac=ball_jac))
     bounds = [(None, None)] * nz
-    for i in range(n_nl):
-        for k in range(nu):
-            bounds[i * nu + k] = (p.u_lo[i, k], p.u_hi[i, k])
+    if p.u_lo is not None:
+        for i in range(n_nl):
+            for k in range(nu):
+                bounds[i * nu + k] = (p.u_lo[i, k], p.u_hi[i, k])
     for k in list(range(iw if not tv else ie, ie)) + list(range(iq, nz)):
         bounds[k] = (0.0, None)
     z0 = np.zeros(nz)
@@ -585,7 +610,7 @@ def _nested_avar_nlp(p):
     return float(r.fun), r.x[:nU].reshape(n_nl, nu), viol
 
 
-@pytest.mark.parametrize("case", ["ball", "u_box", "x_box", "l1", "soft", "tv"])
+@pytest.mark.parametrize("case", ["ball", "u_box", "x_box", "l1", "soft", "tv", "general"])
 def test_constrained_avar_optimum_by_nonlinear_program(case):
     """Constrained problems with AV@R levels below 1 (no closed form): the
     oracle's converged risk value s0 and inputs against the same problem solved
@@ -595,6 +620,8 @@ def test_constrained_avar_optimum_by_nonlinear_program(case):
     at the optimum."""
     if case == "ball":
         p = constrained([2, 2], 3, 2, seed=17, avar=0.5, uball=0.6)
+    elif case == "general":   # full weights, linear terms, general rows at non-leaf nodes and leaves, boxes
+        p = general([2, 2], 3, 2, seed=23, avar=0.5, dense=True, linear=True, n_g=2, n_gN=1, box=True)
     elif case in ("l1", "soft", "tv"):   # with the ball, AV@R 0.5
         p = constrained([2, 2], 3, 2, seed=17, avar=0.5, uball=0.6)
         if case == "l1":
@@ -614,21 +641,31 @@ def test_constrained_avar_optimum_by_nonlinear_program(case):
         p.x_lo[1:], p.x_hi[1:] = -xbox - 0.04 * (k % 3), xbox + 0.04 * ((k + 1) % 3)
     val, U, viol = _nested_avar_nlp(p)
     assert viol < 1e-9
-    r = Oracle(p).solve(tol=1e-9, max_iters=30000, method="spock")
+    o = Oracle(p)
+    r = o.solve(tol=1e-9, max_iters=30000, method="spock")
     assert r["res_inf"] <= 1e-9
+    n_nl = len(p.avar)
     if case in ("ball", "tv"):   # the constraint under test is active at the optimum
         assert np.max(np.linalg.norm(r["u"], axis=1)) >= 0.6 * (1 - 1e-6)
     elif case == "l1":   # some entries sit at the kink of |.|
         assert np.min(np.abs(r["u"])) <= 1e-6
     elif case == "soft":   # the penalty is active
         assert np.max(np.hstack([r["x"][:len(p.avar)], r["u"]])) > 0.3 + 1e-3
+    elif case == "general":   # a general row is active at a non-leaf node and at a leaf
+        zs = np.hstack([r["x"][:n_nl], r["u"]]) @ np.hstack([p.Gx, p.Gu]).T
+        zN = r["x"][n_nl:] @ p.GN.T
+        assert np.min(np.minimum(zs - p.g_lo, p.g_hi - zs)) <= 1e-6
+        assert np.min(np.minimum(zN - p.gN_lo, p.gN_hi - zN)) <= 1e-6
     elif case == "u_box":
         assert np.max(np.abs(r["u"])) >= 0.9 * (1 - 1e-6)
     else:
         xs = r["x"][1:]
         assert np.any((xs >= p.x_hi[1:] - 1e-6) | (xs <= p.x_lo[1:] + 1e-6))
     assert abs(r["risk"] - val) <= 1e-7 * abs(val)
-    assert np.max(np.abs(r["u"] - U)) <= 1e-6
+    # inputs on the nodes the maximising AV@R weights reach (elsewhere the
+    # optimal inputs need not be unique)
+    sel = o.path_weights(r["x"], r["u"])[:n_nl] > 1e-9
+    assert sel[0] and np.max(np.abs(r["u"][sel] - U[sel])) <= 1e-6
 
 
 # --- preconditioning (Sec. 5.4), values worked out by hand ----------------------
