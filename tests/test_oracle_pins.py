@@ -610,7 +610,7 @@ def _nested_avar_nlp(p):
     return float(r.fun), r.x[:nU].reshape(n_nl, nu), viol
 
 
-@pytest.mark.parametrize("case", ["ball", "u_box", "x_box", "l1", "soft", "tv", "general"])
+@pytest.mark.parametrize("case", ["ball", "u_box", "x_box", "l1", "soft", "tv", "general", "deep"])
 def test_constrained_avar_optimum_by_nonlinear_program(case):
     """Constrained problems with AV@R levels below 1 (no closed form): the
     oracle's converged risk value s0 and inputs against the same problem solved
@@ -620,6 +620,9 @@ def test_constrained_avar_optimum_by_nonlinear_program(case):
     at the optimum."""
     if case == "ball":
         p = constrained([2, 2], 3, 2, seed=17, avar=0.5, uball=0.6)
+    elif case == "deep":   # three stages, a non-branching stage between branching ones, AV@R 0.4
+        p = constrained([2, 1, 2], 3, 2, seed=19, avar=0.4, uball=0.6)
+        p.avar = np.full_like(p.avar, 0.4)
     elif case == "general":   # full weights, linear terms, general rows at non-leaf nodes and leaves, boxes
         p = general([2, 2], 3, 2, seed=23, avar=0.5, dense=True, linear=True, n_g=2, n_gN=1, box=True)
     elif case in ("l1", "soft", "tv"):   # with the ball, AV@R 0.5
@@ -645,7 +648,7 @@ def test_constrained_avar_optimum_by_nonlinear_program(case):
     r = o.solve(tol=1e-9, max_iters=30000, method="spock")
     assert r["res_inf"] <= 1e-9
     n_nl = len(p.avar)
-    if case in ("ball", "tv"):   # the constraint under test is active at the optimum
+    if case in ("ball", "tv", "deep"):   # the constraint under test is active at the optimum
         assert np.max(np.linalg.norm(r["u"], axis=1)) >= 0.6 * (1 - 1e-6)
     elif case == "l1":   # some entries sit at the kink of |.|
         assert np.min(np.abs(r["u"])) <= 1e-6
